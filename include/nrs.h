@@ -1,0 +1,206 @@
+/*
+ * nrs.h -- C ABI of libnrs, the GB300 (sm_103a) implementation of the
+ * nearest-neighbour (NEAREST) regularized stokeslet method of Gallagher &
+ * Smith, "Passively parallel regularized stokeslets".
+ *
+ * One time step of the swimming problem (Sec. 4) is:
+ *   kinematics  -> nearest neighbours (Sec. 3, the argmin defining n-hat)
+ *   -> segments of nu -> assembly of A_s (Sec. 3, eq. nnrsbie; Sec. 4 step 1)
+ *   -> rigid-body border (Sec. 4 step 2) -> factor + solve (Sec. 4 step 3)
+ *   -> state update of Y = [X0; B] (Sec. 4).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every pointer argument is owned by the caller.  "device" pointers are CUDA
+ *   device memory on the context's device; "host" pointers are ordinary host
+ *   memory.  Nothing is retained after a call returns, except where stated.
+ * - Points are rows of 4 doubles: force points (x, y, z, 0), quadrature
+ *   points (x, y, z, w) with w the quadrature (area) weight.  Bodies occupy
+ *   contiguous ranges given by n_off / q_off.
+ * - Unknowns and rows: 3m+j for force point m (all bodies) and component j,
+ *   then 6 per free body in body order: columns [U(3), Omega(3)], rows
+ *   [force balance(3), moment balance(3)].  n = 3 N + 6 F.
+ * - Matrices are column-major with leading dimension lda >= n.
+ * - All work is enqueued on the context's stream and is asynchronous unless a
+ *   host output is requested.  Argument errors are detected before any work is
+ *   enqueued and leave outputs untouched.  Device-detected failures (no
+ *   convergence, non-finite values, a bounded device wait that ran out) are
+ *   recorded in a device status word and returned by the next call that
+ *   synchronises (nrs_solve with a report, nrs_step with a report,
+ *   nrs_sync).
+ * - No call aborts, traps or throws.  Errors return a negative nrs_status;
+ *   nrs_last_error() gives a message.
+ */
+#ifndef NRS_H
+#define NRS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NRS_OK = 0,
+    NRS_EINVAL = -1,      /* bad argument (size, null pointer, layout)     */
+    NRS_ENOMEM = -2,      /* device allocation failed                      */
+    NRS_ECUDA = -3,       /* CUDA runtime error                            */
+    NRS_ESINGULAR = -4,   /* exactly zero pivot in the factorisation       */
+    NRS_ENOCONV = -5,     /* refinement did not reach the tolerance        */
+    NRS_ENONFINITE = -6,  /* NaN/Inf met in the matrix or the iterates     */
+    NRS_ETIMEOUT = -7     /* a bounded device-side wait ran out            */
+} nrs_status;
+
+/* Precision of the LU factor used as the preconditioner. */
+typedef enum {
+    NRS_FP64 = 0,  /* plain path: FP64 factor                                     */
+    NRS_FP32 = 1,  /* FP32 factor, trailing updates on FP32 CUDA cores             */
+    NRS_TF32 = 2,  /* FP32 storage, trailing updates on tensor cores (3xTF32)      */
+    NRS_BF16 = 3   /* FP32 storage, trailing updates on tensor cores with BF16 ops */
+} nrs_prec;
+
+/* Body kinds (Sec. 4: swimmers are free; walls are static). */
+enum { NRS_FREE = 0, NRS_PRESCRIBED = 1, NRS_STATIC = 2 };
+
+typedef struct nrs_ctx nrs_ctx;
+
+/* Problem description, read only during nrs_create (host memory). */
+typedef struct {
+    int32_t nbodies;
+    const int64_t *n_off;  /* host [nbodies+1]: force-point ranges per body      */
+    const int64_t *q_off;  /* host [nbodies+1]: quadrature-point ranges per body */
+    const int32_t *kind;   /* host [nbodies]: NRS_FREE / NRS_PRESCRIBED / NRS_STATIC */
+    const int32_t *rigid;  /* host [nbodies] or NULL: 1 if the body-frame shape never changes
+                              (its nearest-neighbour map is then computed once and kept) */
+    const double *U;       /* host [nbodies*3] or NULL: prescribed translation velocity */
+    const double *Omega;   /* host [nbodies*3] or NULL: prescribed angular velocity     */
+    double eps;            /* regularisation parameter epsilon (> 0)  */
+    double mu;             /* viscosity (> 0)                         */
+    int32_t nn_global;     /* 0: nearest neighbour per body in the body frame;
+                              1: over all force points in the lab frame */
+    int32_t factor_prec;   /* nrs_prec used by nrs_step                */
+    int32_t nb;            /* LU block size (0 = default 64; 32/64/128) */
+    double tol;            /* refinement stops when ||dx||_inf <= tol ||x||_inf (0 = 1e-14) */
+    int32_t max_outer;     /* refinement steps (0 = 20)          */
+    int32_t max_inner;     /* GMRES iterations per step (0 = 30) */
+} nrs_problem_desc;
+
+typedef struct {
+    int32_t outer;          /* refinement steps taken                         */
+    int32_t inner;          /* total GMRES iterations                         */
+    int32_t converged;      /* 1 if the tolerance was met                     */
+    int32_t status;         /* nrs_status of the device status word           */
+    double backward_err;    /* ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) */
+    double last_update;     /* ||dx||_inf / ||x||_inf of the last step         */
+} nrs_solve_report;
+
+typedef struct {
+    nrs_solve_report stage[2];
+    double ms_total;        /* device time of the step (CUDA events)          */
+} nrs_step_report;
+
+/* Body-frame inputs of one stage (device memory):
+ *   xi    [N*4]  force points (x,y,z,0) in each body's frame
+ *   Xiw   [Q*4]  quadrature points (x,y,z,w) in each body's frame
+ *   xidot [N*4]  prescribed deformation velocity of the force points, body frame */
+typedef struct {
+    const double *xi;
+    const double *Xiw;
+    const double *xidot;
+} nrs_shapes;
+
+/* Create a context for one problem on the current CUDA device; all work is
+ * enqueued on ``stream`` (a cudaStream_t, NULL = legacy default stream).
+ * Allocates every device workspace (matrices of n x n in FP64 and in the
+ * factor precision, pivots, Krylov basis).  Returns NRS_EINVAL for an empty
+ * body table, non-increasing offsets, a body with quadrature points but no
+ * force points, eps <= 0 or mu <= 0; NRS_ENOMEM if the workspaces do not fit. */
+nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *desc, void *stream);
+
+/* Release every device workspace of the context (synchronises its stream). */
+nrs_status nrs_destroy(nrs_ctx *ctx);
+
+/* Message of the last failed call on this context ("" if none). */
+const char *nrs_last_error(const nrs_ctx *ctx);
+
+/* Problem sizes: N force points, Q quadrature points, F free bodies, n unknowns. */
+nrs_status nrs_sizes(const nrs_ctx *ctx, int64_t *N, int64_t *Q, int64_t *F, int64_t *n);
+
+/* Rigid-body state Y = [X0; B] (Sec. 4) per body: x0 [nbodies*3], B
+ * [nbodies*9] row-major with the body basis vectors as columns.  Host
+ * pointers.  nrs_set_state copies in; nrs_get_state synchronises and copies out. */
+nrs_status nrs_set_state(nrs_ctx *ctx, const double *x0, const double *B);
+nrs_status nrs_get_state(nrs_ctx *ctx, double *x0, double *B);
+
+/* External force and moment on each free body (host [F*6], NULL = zero),
+ * the right-hand side of the force/moment balance rows. */
+nrs_status nrs_set_external(nrs_ctx *ctx, const double *ext);
+
+/* Kinematics (Sec. 4): lab-frame clouds x = x0 + B xi, X = x0 + B Xi (w
+ * copied) from the context's state, and the right-hand side b: for force
+ * point m of body b, B xidot_m, plus U + Omega x (x_m - x0) for a prescribed
+ * body, zero for a static one; then the external force/moment per free body.
+ * Outputs (device): x [N*4], Xw [Q*4], b [n]. */
+nrs_status nrs_kinematics(nrs_ctx *ctx, const nrs_shapes *shapes, double *x, double *Xw,
+                          double *b);
+
+/* Nearest neighbours (Sec. 3, n-hat(q) = argmin_n |x[n] - X[q]|) and the
+ * segments of nu.  x [N*4], Xw [Q*4] device; per body (nn_global = 0) the
+ * search runs over the body's own force points, otherwise over all of them.
+ * Ties go to the lowest index: the decision is taken on the FP64 value
+ * ((dx*dx + dy*dy) + dz*dz) after an FP32 filter with a proven margin, so the
+ * indices equal those of an exhaustive FP64 search bit for bit.
+ * Outputs (device, each may be NULL): nn [Q] (global force index),
+ * seg_ptr [N+1] and perm [Q] (quadrature points of segment n, ascending q,
+ * at perm[seg_ptr[n] .. seg_ptr[n+1])).  The context keeps the segments for
+ * nrs_assemble. */
+nrs_status nrs_nearest_build(nrs_ctx *ctx, const double *x, const double *Xw, int32_t *nn,
+                             int32_t *seg_ptr, int32_t *perm);
+
+/* Assembly (Sec. 3 eq. nnrsbie; Sec. 4 steps 1-2) from lab-frame x [N*4] and
+ * Xw [Q*4] (device) with the segments of the last nrs_nearest_build:
+ *   A[3m+j, 3n+k] = (1/(8 pi mu)) sum_{q in seg(n)} S^eps_jk(x_m - X_q) w_q,
+ *   S^eps_jk(r) = (delta_jk (|r|^2 + 2 eps^2) + r_j r_k) / (|r|^2 + eps^2)^{3/2},
+ * then the rigid-body border of every free body (columns -I and [x_m - x0]x,
+ * rows W_n I and [R_n]x with W_n = sum_{seg n} w_q, R_n = sum_{seg n} w_q (X_q - x0)).
+ * The FP64 matrix is kept in the context; if A64 is not NULL it is also
+ * copied there (device, column-major, lda >= n). */
+nrs_status nrs_assemble(nrs_ctx *ctx, const double *x, const double *Xw, double *A64,
+                        int64_t lda);
+
+/* Factor the assembled matrix in precision ``prec`` (Sec. 4 step 3).  Block
+ * LU with row pivoting inside each diagonal block; for the FP32/TF32/BF16
+ * precisions the factor preconditions the FP64 refinement of nrs_solve.
+ * info (host, may be NULL) receives 0 or the 1-based column of the first
+ * exactly-zero pivot; that case also returns NRS_ESINGULAR.  Synchronises
+ * when info is requested. */
+nrs_status nrs_factor(nrs_ctx *ctx, int32_t prec, int32_t *info);
+
+/* Solve A x = b (device b, x [n*nrhs], column-major) by GMRES-based iterative
+ * refinement (Carson & Higham 2018): residual b - A x in FP64 with the FP64
+ * matrix, correction by GMRES preconditioned with the factor, x += d.
+ * x0 (device [n*nrhs] or NULL) is the starting guess, else x0 = LU^{-1} b.
+ * report (host, may be NULL; one per right-hand side) synchronises and
+ * returns the device status (NRS_ENOCONV when max_outer steps did not reach
+ * the tolerance). */
+nrs_status nrs_solve(nrs_ctx *ctx, const double *b, double *x, int32_t nrhs, const double *x0,
+                     nrs_solve_report *report);
+
+/* One explicit-midpoint (RK2) step of dY/dt = F(Y, t) (Sec. 4): stage 1 at
+ * the shapes ``s0`` (time t), stage 2 at ``s_half`` (time t + dt/2), each
+ * stage = kinematics, nearest neighbours (kept for rigid bodies), assembly,
+ * factor (desc.factor_prec), solve; then dX0/dt = U, dB/dt = [Omega]x B with B
+ * re-orthonormalised by modified Gram-Schmidt after each stage.  The state
+ * stays on the device.  sol (device [2*n] or NULL) receives both stages'
+ * solutions.  report (host or NULL) synchronises. */
+nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *s_half, double dt,
+                    double *sol, nrs_step_report *report);
+
+/* Wait for the context's stream and return the device status word. */
+nrs_status nrs_sync(nrs_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NRS_H */
