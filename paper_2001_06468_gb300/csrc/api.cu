@@ -1,0 +1,501 @@
+// api.cu -- the extern "C" entry points of libnrs (declared in include/nrs.h).
+//
+// The host code here validates arguments, owns the device workspaces and
+// enqueues kernels; every arithmetic step of the method runs in the kernels
+// of geometry.cu, assemble.cu, lu.cu, tc_gemm.cu and solve.cu.
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "nrs_internal.cuh"
+
+using nrs::Ctx;
+using nrs::D4;
+
+namespace {
+
+nrs_status fail(Ctx *c, nrs_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(c, NRS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, sizeof(T) * count);
+}
+
+nrs_status alloc_all(Ctx *c)
+{
+    const int64_t N = c->N, Q = c->Q, n = c->n, lda = c->lda, m = c->max_inner;
+    const int nb = c->nbodies;
+    struct {
+        void **p;
+        size_t bytes;
+    } req[] = {
+        {(void **)&c->d_body_x, sizeof(int32_t) * N},
+        {(void **)&c->d_body_X, sizeof(int32_t) * Q},
+        {(void **)&c->d_kind, sizeof(int32_t) * nb},
+        {(void **)&c->d_free_index, sizeof(int32_t) * (nb + c->F)},
+        {(void **)&c->d_n_off, sizeof(int64_t) * (nb + 1)},
+        {(void **)&c->d_q_off, sizeof(int64_t) * (nb + 1)},
+        {(void **)&c->d_U, sizeof(double) * 3 * nb},
+        {(void **)&c->d_Om, sizeof(double) * 3 * nb},
+        {(void **)&c->d_ext, sizeof(double) * 6 * c->F},
+        {(void **)&c->d_x0, sizeof(double) * 3 * nb},
+        {(void **)&c->d_B, sizeof(double) * 9 * nb},
+        {(void **)&c->d_x0_save, sizeof(double) * 3 * nb},
+        {(void **)&c->d_B_save, sizeof(double) * 9 * nb},
+        {(void **)&c->d_x, sizeof(D4) * N},
+        {(void **)&c->d_Xw, sizeof(D4) * Q},
+        {(void **)&c->d_b, sizeof(double) * lda},
+        {(void **)&c->d_sol, sizeof(double) * 2 * lda},
+        {(void **)&c->d_nn, sizeof(int32_t) * Q},
+        {(void **)&c->d_seg_ptr, sizeof(int32_t) * (N + 1)},
+        {(void **)&c->d_perm, sizeof(int32_t) * Q},
+        {(void **)&c->d_cursor, sizeof(int32_t) * (N + 1)},
+        {(void **)&c->d_Xs, sizeof(D4) * Q},
+        {(void **)&c->d_W, sizeof(double) * N},
+        {(void **)&c->d_R, sizeof(double) * 3 * N},
+        {(void **)&c->d_A64, sizeof(double) * lda * n},
+        {(void **)&c->d_A32, sizeof(float) * lda * n},
+        {(void **)&c->d_rowperm, sizeof(int32_t) * n},
+        {(void **)&c->d_lperm, sizeof(int32_t) * 64},
+        {(void **)&c->d_info, sizeof(int32_t)},
+        {(void **)&c->d_r, sizeof(double) * lda},
+        {(void **)&c->d_w, sizeof(double) * lda},
+        {(void **)&c->d_V, sizeof(double) * lda * (m + 1)},
+        {(void **)&c->d_H, sizeof(double) * (m + 1) * m},
+        {(void **)&c->d_gv, sizeof(double) * (4 * m + 2)},
+        {(void **)&c->d_scal, sizeof(double) * (16 + 2 * (m + 1))},
+        {(void **)&c->d_part, sizeof(double) * c->part_splits * n},
+        {(void **)&c->d_t32, sizeof(float) * 2 * lda},
+        {(void **)&c->d_t64, sizeof(double) * 2 * lda},
+        {(void **)&c->d_flags, sizeof(int32_t) * nrs::ceil_div(n, 64)},
+        {(void **)&c->d_status, sizeof(int32_t)},
+    };
+    for (auto &r : req) {
+        *r.p = nullptr;
+        cudaError_t e = cudaMalloc(r.p, r.bytes ? r.bytes : 1);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, NRS_ENOMEM,
+                        "device allocation of " + std::to_string(r.bytes) + " bytes failed");
+        }
+    }
+    return NRS_OK;
+}
+
+void free_all(Ctx *c)
+{
+    void *ptrs[] = {c->d_body_x, c->d_body_X, c->d_kind,   c->d_free_index, c->d_n_off,
+                    c->d_q_off,  c->d_U,      c->d_Om,     c->d_ext,        c->d_x0,
+                    c->d_B,      c->d_x0_save, c->d_B_save, c->d_tasks_all, c->d_tasks_deform,
+                    c->d_x,      c->d_Xw,     c->d_b,      c->d_sol,        c->d_nn,
+                    c->d_seg_ptr, c->d_perm,  c->d_cursor, c->d_Xs,         c->d_W,
+                    c->d_R,      c->d_A64,    c->d_A32,    c->d_LU64,       c->d_rowperm,
+                    c->d_lperm,  c->d_info,   c->d_r,      c->d_xk,         c->d_w,
+                    c->d_V,      c->d_H,      c->d_gv,     c->d_scal,       c->d_part,
+                    c->d_t32,    c->d_t64,    c->d_flags,  c->d_status};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+bool is_prec(int p) { return p == NRS_FP64 || p == NRS_FP32 || p == NRS_TF32 || p == NRS_BF16; }
+
+__global__ void k_cvt_f64_f32(int64_t count, const double *__restrict__ a, float *__restrict__ b)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) b[i] = (float)a[i];
+}
+
+nrs_status do_factor(Ctx *c, int prec)
+{
+    if (!c->assembled) return fail(c, NRS_EINVAL, "nrs_factor before nrs_assemble");
+    if ((prec == NRS_TF32 || prec == NRS_BF16) && !nrs::tc_available())
+        return fail(c, NRS_EINVAL, "tensor-core factor precision not available in this build");
+    const size_t elems = (size_t)c->lda * c->n;
+    if (prec == NRS_FP64) {
+        if (!c->d_LU64) {
+            cudaError_t e = cudaMalloc(&c->d_LU64, sizeof(double) * elems);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                c->d_LU64 = nullptr;
+                return fail(c, NRS_ENOMEM, "FP64 factor workspace does not fit");
+            }
+        }
+        CK(cudaMemcpyAsync(c->d_LU64, c->d_A64, sizeof(double) * elems, cudaMemcpyDeviceToDevice,
+                           c->stream));
+        nrs::run_lu_fp64(*c, c->d_LU64, c->lda);
+    } else {
+        if (!c->a32_fresh)
+            k_cvt_f64_f32<<<(unsigned)nrs::ceil_div((int64_t)elems, 256), 256, 0, c->stream>>>(
+                (int64_t)elems, c->d_A64, c->d_A32);
+        nrs::run_lu_fp32(*c, c->d_A32, c->lda, prec);
+        c->a32_fresh = false;
+    }
+    CK(cudaGetLastError());
+    c->factored_prec = prec;
+    return NRS_OK;
+}
+
+nrs_status do_segments_and_assemble(Ctx *c, const D4 *x_lab, const D4 *Xw_lab)
+{
+    nrs::launch_gather(*c, Xw_lab, c->d_seg_ptr, c->d_perm);
+    float *a32 = c->factor_prec == NRS_FP64 ? nullptr : c->d_A32;
+    nrs::launch_assemble(*c, x_lab, c->d_A64, a32, c->lda);
+    nrs::launch_border(*c, x_lab, c->d_A64, a32, c->lda);
+    CK(cudaGetLastError());
+    c->a32_fresh = a32 != nullptr;
+    c->assembled = true;
+    return NRS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
+{
+    Ctx *c = nullptr;
+    if (!out || !d) return NRS_EINVAL;
+    *out = nullptr;
+    if (d->nbodies <= 0 || !d->n_off || !d->q_off || !d->kind) return NRS_EINVAL;
+    if (!(d->eps > 0.0) || !(d->mu > 0.0)) return NRS_EINVAL;
+    if (d->n_off[0] != 0 || d->q_off[0] != 0) return NRS_EINVAL;
+    if (!is_prec(d->factor_prec)) return NRS_EINVAL;
+    for (int b = 0; b < d->nbodies; ++b) {
+        if (d->n_off[b + 1] < d->n_off[b] || d->q_off[b + 1] < d->q_off[b]) return NRS_EINVAL;
+        if (d->kind[b] < NRS_FREE || d->kind[b] > NRS_STATIC) return NRS_EINVAL;
+        if (d->q_off[b + 1] > d->q_off[b] && d->n_off[b + 1] == d->n_off[b] && !d->nn_global)
+            return NRS_EINVAL;
+    }
+    const int64_t N = d->n_off[d->nbodies], Q = d->q_off[d->nbodies];
+    if (N <= 0 || Q <= 0 || N > (1LL << 28) || Q > (1LL << 30)) return NRS_EINVAL;
+    c = new (std::nothrow) Ctx();
+    if (!c) return NRS_ENOMEM;
+    c->stream = (cudaStream_t)stream;
+    cudaGetDevice(&c->device);
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    c->nbodies = d->nbodies;
+    c->N = N;
+    c->Q = Q;
+    c->n_off.assign(d->n_off, d->n_off + d->nbodies + 1);
+    c->q_off.assign(d->q_off, d->q_off + d->nbodies + 1);
+    c->kind.assign(d->kind, d->kind + d->nbodies);
+    c->rigid.assign(d->nbodies, 0);
+    if (d->rigid)
+        for (int b = 0; b < d->nbodies; ++b) c->rigid[b] = d->rigid[b] ? 1 : 0;
+    c->free_index.assign(d->nbodies, -1);
+    std::vector<int32_t> free_body;
+    for (int b = 0; b < d->nbodies; ++b)
+        if (c->kind[b] == NRS_FREE) {
+            c->free_index[b] = (int32_t)free_body.size();
+            free_body.push_back(b);
+        }
+    c->F = (int64_t)free_body.size();
+    c->n = 3 * N + 6 * c->F;
+    c->lda = nrs::ceil_div(c->n, 32) * 32;
+    c->eps = d->eps;
+    c->mu = d->mu;
+    c->nn_global = d->nn_global ? 1 : 0;
+    c->factor_prec = d->factor_prec;
+    c->nb = 64;
+    c->tol = d->tol > 0 ? d->tol : 1e-14;
+    c->max_outer = d->max_outer > 0 ? d->max_outer : 20;
+    c->max_inner = d->max_inner > 0 ? d->max_inner : 30;
+    {
+        int64_t rowblocks = nrs::ceil_div(c->n, 128);
+        int64_t s = nrs::ceil_div(2 * (int64_t)c->num_sms, rowblocks);
+        c->part_splits = (int)std::max<int64_t>(1, std::min<int64_t>(s, 64));
+    }
+    nrs_status st = alloc_all(c);
+    if (st != NRS_OK) {
+        std::string msg = c->err;
+        free_all(c);
+        delete c;
+        return st;
+    }
+    // body tables
+    std::vector<int32_t> bx(N), bX(Q);
+    for (int b = 0; b < d->nbodies; ++b) {
+        for (int64_t i = d->n_off[b]; i < d->n_off[b + 1]; ++i) bx[i] = b;
+        for (int64_t i = d->q_off[b]; i < d->q_off[b + 1]; ++i) bX[i] = b;
+    }
+    std::vector<int32_t> fi(c->free_index);
+    fi.insert(fi.end(), free_body.begin(), free_body.end());
+    std::vector<double> U(3 * d->nbodies, 0.0), Om(3 * d->nbodies, 0.0);
+    if (d->U) memcpy(U.data(), d->U, sizeof(double) * 3 * d->nbodies);
+    if (d->Omega) memcpy(Om.data(), d->Omega, sizeof(double) * 3 * d->nbodies);
+    std::vector<double> x0(3 * d->nbodies, 0.0), B(9 * d->nbodies, 0.0);
+    for (int b = 0; b < d->nbodies; ++b) B[9 * b + 0] = B[9 * b + 4] = B[9 * b + 8] = 1.0;
+    // nearest-neighbour tasks: 128 quadrature points of one body each
+    std::vector<nrs::NNTask> all, deform;
+    for (int b = 0; b < d->nbodies; ++b)
+        for (int64_t q0 = d->q_off[b]; q0 < d->q_off[b + 1]; q0 += 128) {
+            nrs::NNTask t{b, (int32_t)q0, (int32_t)std::min<int64_t>(q0 + 128, d->q_off[b + 1]), 0};
+            all.push_back(t);
+            if (!c->rigid[b] || c->nn_global) deform.push_back(t);
+        }
+    c->n_tasks_all = (int)all.size();
+    c->n_tasks_deform = (int)deform.size();
+    cudaError_t e = cudaSuccess;
+    e = cudaMalloc(&c->d_tasks_all, sizeof(nrs::NNTask) * std::max<size_t>(1, all.size()));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&c->d_tasks_deform, sizeof(nrs::NNTask) * std::max<size_t>(1, deform.size()));
+    auto h2d = [&](void *dst, const void *src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    h2d(c->d_tasks_all, all.data(), sizeof(nrs::NNTask) * all.size());
+    h2d(c->d_tasks_deform, deform.data(), sizeof(nrs::NNTask) * deform.size());
+    h2d(c->d_body_x, bx.data(), sizeof(int32_t) * N);
+    h2d(c->d_body_X, bX.data(), sizeof(int32_t) * Q);
+    h2d(c->d_kind, c->kind.data(), sizeof(int32_t) * d->nbodies);
+    h2d(c->d_free_index, fi.data(), sizeof(int32_t) * fi.size());
+    h2d(c->d_n_off, d->n_off, sizeof(int64_t) * (d->nbodies + 1));
+    h2d(c->d_q_off, d->q_off, sizeof(int64_t) * (d->nbodies + 1));
+    h2d(c->d_U, U.data(), sizeof(double) * U.size());
+    h2d(c->d_Om, Om.data(), sizeof(double) * Om.size());
+    h2d(c->d_x0, x0.data(), sizeof(double) * x0.size());
+    h2d(c->d_B, B.data(), sizeof(double) * B.size());
+    if (e == cudaSuccess && c->F) e = cudaMemset(c->d_ext, 0, sizeof(double) * 6 * c->F);
+    if (e == cudaSuccess) e = cudaMemset(c->d_flags, 0, sizeof(int32_t) * nrs::ceil_div(c->n, 64));
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int32_t));
+    if (e != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return NRS_ECUDA;
+    }
+    *out = reinterpret_cast<nrs_ctx *>(c);
+    return NRS_OK;
+}
+
+nrs_status nrs_destroy(nrs_ctx *ctx)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return NRS_EINVAL;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+    return NRS_OK;
+}
+
+const char *nrs_last_error(const nrs_ctx *ctx)
+{
+    const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+    return c ? c->err.c_str() : "null context";
+}
+
+nrs_status nrs_sizes(const nrs_ctx *ctx, int64_t *N, int64_t *Q, int64_t *F, int64_t *n)
+{
+    const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+    if (!c) return NRS_EINVAL;
+    if (N) *N = c->N;
+    if (Q) *Q = c->Q;
+    if (F) *F = c->F;
+    if (n) *n = c->n;
+    return NRS_OK;
+}
+
+nrs_status nrs_set_state(nrs_ctx *ctx, const double *x0, const double *B)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !x0 || !B) return fail(c, NRS_EINVAL, "nrs_set_state: null argument");
+    CK(cudaMemcpyAsync(c->d_x0, x0, sizeof(double) * 3 * c->nbodies, cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(c->d_B, B, sizeof(double) * 9 * c->nbodies, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NRS_OK;
+}
+
+nrs_status nrs_get_state(nrs_ctx *ctx, double *x0, double *B)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !x0 || !B) return fail(c, NRS_EINVAL, "nrs_get_state: null argument");
+    CK(cudaMemcpyAsync(x0, c->d_x0, sizeof(double) * 3 * c->nbodies, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaMemcpyAsync(B, c->d_B, sizeof(double) * 9 * c->nbodies, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NRS_OK;
+}
+
+nrs_status nrs_set_external(nrs_ctx *ctx, const double *ext)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return NRS_EINVAL;
+    if (c->F == 0) return NRS_OK;
+    if (ext)
+        CK(cudaMemcpyAsync(c->d_ext, ext, sizeof(double) * 6 * c->F, cudaMemcpyHostToDevice,
+                           c->stream));
+    else
+        CK(cudaMemsetAsync(c->d_ext, 0, sizeof(double) * 6 * c->F, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NRS_OK;
+}
+
+nrs_status nrs_kinematics(nrs_ctx *ctx, const nrs_shapes *s, double *x, double *Xw, double *b)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !s || !s->xi || !s->Xiw || !s->xidot || !x || !Xw || !b)
+        return fail(c, NRS_EINVAL, "nrs_kinematics: null argument");
+    nrs::launch_kinematics(*c, (const D4 *)s->xi, (const D4 *)s->Xiw, (const D4 *)s->xidot, (D4 *)x,
+                           (D4 *)Xw, b);
+    CK(cudaGetLastError());
+    return NRS_OK;
+}
+
+nrs_status nrs_nearest_build(nrs_ctx *ctx, const double *x, const double *Xw, int32_t *nn,
+                             int32_t *seg_ptr, int32_t *perm)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !x || !Xw) return fail(c, NRS_EINVAL, "nrs_nearest_build: null argument");
+    nrs::launch_nearest(*c, (const D4 *)x, (const D4 *)Xw, c->d_nn, false);
+    nrs::launch_segments(*c, c->d_nn, c->d_seg_ptr, c->d_perm);
+    CK(cudaGetLastError());
+    if (nn) CK(cudaMemcpyAsync(nn, c->d_nn, sizeof(int32_t) * c->Q, cudaMemcpyDeviceToDevice, c->stream));
+    if (seg_ptr)
+        CK(cudaMemcpyAsync(seg_ptr, c->d_seg_ptr, sizeof(int32_t) * (c->N + 1),
+                           cudaMemcpyDeviceToDevice, c->stream));
+    if (perm)
+        CK(cudaMemcpyAsync(perm, c->d_perm, sizeof(int32_t) * c->Q, cudaMemcpyDeviceToDevice,
+                           c->stream));
+    c->seg_valid = true;
+    c->nn_valid = false;  // the step path recomputes its own map
+    return NRS_OK;
+}
+
+nrs_status nrs_assemble(nrs_ctx *ctx, const double *x, const double *Xw, double *A64, int64_t lda)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !x || !Xw) return fail(c, NRS_EINVAL, "nrs_assemble: null argument");
+    if (!c->seg_valid) return fail(c, NRS_EINVAL, "nrs_assemble before nrs_nearest_build");
+    if (A64 && lda < c->n) return fail(c, NRS_EINVAL, "nrs_assemble: lda < n");
+    nrs_status st = do_segments_and_assemble(c, (const D4 *)x, (const D4 *)Xw);
+    if (st != NRS_OK) return st;
+    if (A64)
+        CK(cudaMemcpy2DAsync(A64, sizeof(double) * lda, c->d_A64, sizeof(double) * c->lda,
+                             sizeof(double) * c->n, c->n, cudaMemcpyDeviceToDevice, c->stream));
+    return NRS_OK;
+}
+
+nrs_status nrs_factor(nrs_ctx *ctx, int32_t prec, int32_t *info)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return NRS_EINVAL;
+    if (!is_prec(prec)) return fail(c, NRS_EINVAL, "nrs_factor: unknown precision");
+    nrs_status st = do_factor(c, prec);
+    if (st != NRS_OK) return st;
+    if (info) {
+        CK(cudaMemcpyAsync(info, c->d_info, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (*info != 0) return fail(c, NRS_ESINGULAR, "exactly zero pivot");
+    }
+    return NRS_OK;
+}
+
+nrs_status nrs_solve(nrs_ctx *ctx, const double *b, double *x, int32_t nrhs, const double *x0,
+                     nrs_solve_report *report)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !b || !x || nrhs <= 0) return fail(c, NRS_EINVAL, "nrs_solve: bad argument");
+    if (c->factored_prec < 0) return fail(c, NRS_EINVAL, "nrs_solve before nrs_factor");
+    nrs_status worst = NRS_OK;
+    for (int k = 0; k < nrhs; ++k) {
+        nrs_status st = nrs::run_gmres_ir(*c, b + (int64_t)k * c->n, x + (int64_t)k * c->n,
+                                          x0 ? x0 + (int64_t)k * c->n : nullptr,
+                                          report ? report + k : nullptr);
+        if (st == NRS_ECUDA) return st;
+        if (st != NRS_OK && worst == NRS_OK) worst = st;
+    }
+    return worst;
+}
+
+nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *sh, double dt, double *sol,
+                    nrs_step_report *report)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !s0 || !sh || !s0->xi || !s0->Xiw || !s0->xidot || !sh->xi || !sh->Xiw || !sh->xidot)
+        return fail(c, NRS_EINVAL, "nrs_step: null argument");
+    if (!(dt > 0.0)) return fail(c, NRS_EINVAL, "nrs_step: dt must be positive");
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (report) {
+        CK(cudaEventCreate(&ev0));
+        CK(cudaEventCreate(&ev1));
+        CK(cudaEventRecord(ev0, c->stream));
+    }
+    CK(cudaMemcpyAsync(c->d_x0_save, c->d_x0, sizeof(double) * 3 * c->nbodies,
+                       cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_B_save, c->d_B, sizeof(double) * 9 * c->nbodies,
+                       cudaMemcpyDeviceToDevice, c->stream));
+    nrs_status worst = NRS_OK;
+    for (int stage = 0; stage < 2; ++stage) {
+        const nrs_shapes *s = stage ? sh : s0;
+        nrs::launch_kinematics(*c, (const D4 *)s->xi, (const D4 *)s->Xiw, (const D4 *)s->xidot,
+                               c->d_x, c->d_Xw, c->d_b);
+        bool ran = true;
+        if (c->nn_global) {
+            nrs::launch_nearest(*c, c->d_x, c->d_Xw, c->d_nn, false);
+        } else if (!c->nn_valid) {
+            nrs::launch_nearest(*c, (const D4 *)s->xi, (const D4 *)s->Xiw, c->d_nn, false);
+            c->nn_valid = true;
+        } else if (c->n_tasks_deform > 0) {
+            nrs::launch_nearest(*c, (const D4 *)s->xi, (const D4 *)s->Xiw, c->d_nn, true);
+        } else {
+            ran = false;
+        }
+        if (ran || !c->seg_valid) nrs::launch_segments(*c, c->d_nn, c->d_seg_ptr, c->d_perm);
+        c->seg_valid = true;
+        nrs_status st = do_segments_and_assemble(c, c->d_x, c->d_Xw);
+        if (st != NRS_OK) return st;
+        st = do_factor(c, c->factor_prec);
+        if (st != NRS_OK) return st;
+        double *out = c->d_sol + (int64_t)stage * c->lda;
+        st = nrs::run_gmres_ir(*c, c->d_b, out, nullptr, report ? &report->stage[stage] : nullptr);
+        if (st == NRS_ECUDA) return st;
+        if (st != NRS_OK && worst == NRS_OK) worst = st;
+        nrs::launch_rk2(*c, stage, dt, out);
+        CK(cudaGetLastError());
+    }
+    if (sol) {
+        CK(cudaMemcpyAsync(sol, c->d_sol, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(sol + c->n, c->d_sol + c->lda, sizeof(double) * c->n,
+                           cudaMemcpyDeviceToDevice, c->stream));
+    }
+    if (report) {
+        CK(cudaEventRecord(ev1, c->stream));
+        CK(cudaEventSynchronize(ev1));
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        report->ms_total = ms;
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+    }
+    return worst;
+}
+
+nrs_status nrs_sync(nrs_ctx *ctx)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return NRS_EINVAL;
+    CK(cudaStreamSynchronize(c->stream));
+    int32_t st = 0;
+    CK(cudaMemcpy(&st, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(c->d_status, 0, sizeof(int32_t)));
+    if (st & nrs::ST_TIMEOUT) return fail(c, NRS_ETIMEOUT, "a device wait ran out");
+    if (st & nrs::ST_NONFINITE) return fail(c, NRS_ENONFINITE, "non-finite value");
+    return NRS_OK;
+}
+
+}  // extern "C"

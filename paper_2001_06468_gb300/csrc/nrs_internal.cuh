@@ -1,0 +1,130 @@
+// nrs_internal.cuh -- shared declarations of the libnrs CUDA sources.
+//
+// Layout conventions (see include/nrs.h): points are rows of 4 doubles,
+// matrices column-major with leading dimension lda, unknown 3m+j for force
+// point m, then 6 per free body.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/nrs.h"
+
+namespace nrs {
+
+struct __align__(32) D4 {
+    double x, y, z, w;
+};
+
+// Device status word bits (ORed by kernels, read by the host after a sync).
+enum : int32_t {
+    ST_SINGULAR = 1,
+    ST_NOCONV = 2,
+    ST_NONFINITE = 4,
+    ST_TIMEOUT = 8,
+};
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Upper bound on spins of any device-side wait (each spin sleeps ~100 ns):
+// a wait that runs out sets ST_TIMEOUT and returns instead of hanging.
+constexpr long long kSpinLimit = 1LL << 24;
+
+// Nearest-neighbour block task: quadrature points [q0, q1) of body b.
+struct NNTask {
+    int32_t body, q0, q1, pad;
+};
+
+struct Ctx;
+
+// ---- geometry kernels (geometry.cu) -------------------------------------
+void launch_kinematics(Ctx &c, const D4 *xi, const D4 *Xiw, const D4 *xidot, D4 *x, D4 *Xw,
+                       double *b);
+void launch_nearest(Ctx &c, const D4 *x, const D4 *Xw, int32_t *nn, bool only_deforming);
+void launch_segments(Ctx &c, const int32_t *nn, int32_t *seg_ptr, int32_t *perm);
+void launch_gather(Ctx &c, const D4 *Xw_lab, const int32_t *seg_ptr, const int32_t *perm);
+void launch_border(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t lda);
+void launch_rk2(Ctx &c, int stage, double dt, const double *sol);
+
+// ---- assembly (assemble.cu) ----------------------------------------------
+void launch_assemble(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t lda);
+
+// ---- factorisation (lu.cu) -------------------------------------------------
+int run_lu_fp64(Ctx &c, double *A, int64_t lda);
+int run_lu_fp32(Ctx &c, float *A, int64_t lda, int prec);
+
+bool tc_available();
+
+// ---- solve (solve.cu) ------------------------------------------------------
+nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0,
+                        nrs_solve_report *rep);
+
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    std::string err;
+
+    // problem
+    int nbodies = 0;
+    int64_t N = 0, Q = 0, F = 0, n = 0, lda = 0;
+    std::vector<int64_t> n_off, q_off;
+    std::vector<int32_t> kind, rigid, free_index;
+    double eps = 0, mu = 0;
+    int nn_global = 0, factor_prec = NRS_FP32, nb = 64;
+    double tol = 1e-14;
+    int max_outer = 20, max_inner = 30;
+
+    // device body tables
+    int32_t *d_body_x = nullptr, *d_body_X = nullptr, *d_kind = nullptr, *d_free_index = nullptr;
+    int64_t *d_n_off = nullptr, *d_q_off = nullptr;
+    double *d_U = nullptr, *d_Om = nullptr, *d_ext = nullptr;
+    double *d_x0 = nullptr, *d_B = nullptr, *d_x0_save = nullptr, *d_B_save = nullptr;
+    NNTask *d_tasks_all = nullptr, *d_tasks_deform = nullptr;
+    int n_tasks_all = 0, n_tasks_deform = 0;
+    bool nn_valid = false;
+
+    // clouds and right-hand side (lab frame)
+    D4 *d_x = nullptr, *d_Xw = nullptr;
+    double *d_b = nullptr, *d_sol = nullptr;
+
+    // nearest neighbours and segments
+    int32_t *d_nn = nullptr, *d_seg_ptr = nullptr, *d_perm = nullptr, *d_cursor = nullptr;
+    D4 *d_Xs = nullptr;        // lab-frame quadrature points in segment order
+    double *d_W = nullptr;     // W_n
+    double *d_R = nullptr;     // R_n (N x 3)
+    bool seg_valid = false;
+
+    // matrices
+    double *d_A64 = nullptr;   // FP64 system (residual)
+    float *d_A32 = nullptr;    // FP32 copy, factored in place for the FP32/TF32/BF16 paths
+    double *d_LU64 = nullptr;  // FP64 factor (plain path)
+    int32_t *d_rowperm = nullptr;  // row order after pivoting: position i holds original row
+    int32_t *d_lperm = nullptr;    // row exchange of the current diagonal block
+    bool a32_fresh = false;        // d_A32 holds the last assembly (not yet factored)
+    int32_t *d_info = nullptr;
+    int factored_prec = -1;
+    bool assembled = false;
+
+    // solve workspaces
+    double *d_r = nullptr, *d_xk = nullptr, *d_w = nullptr, *d_V = nullptr, *d_H = nullptr;
+    double *d_gv = nullptr;    // Givens state: cs[m], sn[m], g[m+1], y[m]
+    double *d_scal = nullptr;  // scalars (norms, flags as doubles)
+    double *d_part = nullptr;  // partial sums of matrix-vector products
+    int part_splits = 1;
+    float *d_t32 = nullptr;    // FP32 work vector for the triangular solves
+    double *d_t64 = nullptr;   // FP64 work vector for the triangular solves
+    int32_t *d_flags = nullptr;
+    int32_t *d_status = nullptr;
+    int32_t *h_pinned = nullptr;  // pinned host mirror of small status values
+    int trsv_epoch = 0;
+    int trsv_grid = 0;
+};
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace nrs

@@ -1,0 +1,282 @@
+"""Thin ctypes binding of libnrs (include/nrs.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of ``csrc/``.  Tensors are torch CUDA tensors (device memory); the context's
+work is enqueued on the torch stream that is current when it is created.
+If libnrs.so has not been built, importing this module raises: there is no
+CPU or library fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnrs.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -m paper_2001_06468_gb300.build`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+NRS_OK, NRS_EINVAL, NRS_ENOMEM, NRS_ECUDA = 0, -1, -2, -3
+NRS_ESINGULAR, NRS_ENOCONV, NRS_ENONFINITE, NRS_ETIMEOUT = -4, -5, -6, -7
+STATUS_NAMES = {0: "NRS_OK", -1: "NRS_EINVAL", -2: "NRS_ENOMEM", -3: "NRS_ECUDA",
+                -4: "NRS_ESINGULAR", -5: "NRS_ENOCONV", -6: "NRS_ENONFINITE", -7: "NRS_ETIMEOUT"}
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+FREE, PRESCRIBED, STATIC = 0, 1, 2
+
+EXPORTS = ["nrs_create", "nrs_destroy", "nrs_last_error", "nrs_sizes", "nrs_set_state",
+           "nrs_get_state", "nrs_set_external", "nrs_kinematics", "nrs_nearest_build",
+           "nrs_assemble", "nrs_factor", "nrs_solve", "nrs_step", "nrs_sync"]
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("nbodies", ctypes.c_int32),
+                ("n_off", ctypes.POINTER(ctypes.c_int64)),
+                ("q_off", ctypes.POINTER(ctypes.c_int64)),
+                ("kind", ctypes.POINTER(ctypes.c_int32)),
+                ("rigid", ctypes.POINTER(ctypes.c_int32)),
+                ("U", ctypes.POINTER(ctypes.c_double)),
+                ("Omega", ctypes.POINTER(ctypes.c_double)),
+                ("eps", ctypes.c_double),
+                ("mu", ctypes.c_double),
+                ("nn_global", ctypes.c_int32),
+                ("factor_prec", ctypes.c_int32),
+                ("nb", ctypes.c_int32),
+                ("tol", ctypes.c_double),
+                ("max_outer", ctypes.c_int32),
+                ("max_inner", ctypes.c_int32)]
+
+
+class SolveReport(ctypes.Structure):
+    _fields_ = [("outer", ctypes.c_int32), ("inner", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("backward_err", ctypes.c_double), ("last_update", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class StepReport(ctypes.Structure):
+    _fields_ = [("stage", SolveReport * 2), ("ms_total", ctypes.c_double)]
+
+
+class Shapes(ctypes.Structure):
+    _fields_ = [("xi", ctypes.c_void_p), ("Xiw", ctypes.c_void_p), ("xidot", ctypes.c_void_p)]
+
+
+_P = ctypes.c_void_p
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_sig = {
+    "nrs_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(ProblemDesc), _P]),
+    "nrs_destroy": (ctypes.c_int, [_P]),
+    "nrs_last_error": (ctypes.c_char_p, [_P]),
+    "nrs_sizes": (ctypes.c_int, [_P, _I64P, _I64P, _I64P, _I64P]),
+    "nrs_set_state": (ctypes.c_int, [_P, _P, _P]),
+    "nrs_get_state": (ctypes.c_int, [_P, _P, _P]),
+    "nrs_set_external": (ctypes.c_int, [_P, _P]),
+    "nrs_kinematics": (ctypes.c_int, [_P, ctypes.POINTER(Shapes), _P, _P, _P]),
+    "nrs_nearest_build": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "nrs_assemble": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64]),
+    "nrs_factor": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "nrs_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P, ctypes.POINTER(SolveReport)]),
+    "nrs_step": (ctypes.c_int, [_P, ctypes.POINTER(Shapes), ctypes.POINTER(Shapes), ctypes.c_double,
+                                _P, ctypes.POINTER(StepReport)]),
+    "nrs_sync": (ctypes.c_int, [_P]),
+}
+for _name, (_res, _args) in _sig.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+class NrsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(t: Optional[torch.Tensor], dtype=None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _np_ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+class Context:
+    """One NEAREST problem on the current CUDA device (see include/nrs.h)."""
+
+    def __init__(self, n_off: Sequence[int], q_off: Sequence[int], kind: Sequence[int],
+                 eps: float, mu: float = 1.0, rigid: Optional[Sequence[int]] = None,
+                 U=None, Omega=None, nn_global: bool = False, factor_prec: str = "fp32",
+                 tol: float = 0.0, max_outer: int = 0, max_inner: int = 0,
+                 stream: Optional[torch.cuda.Stream] = None):
+        self._n_off = np.ascontiguousarray(n_off, dtype=np.int64)
+        self._q_off = np.ascontiguousarray(q_off, dtype=np.int64)
+        self._kind = np.ascontiguousarray(kind, dtype=np.int32)
+        nb = len(self._kind)
+        self._rigid = None if rigid is None else np.ascontiguousarray(rigid, dtype=np.int32)
+        self._U = None if U is None else np.ascontiguousarray(U, dtype=np.float64).reshape(nb * 3)
+        self._Om = None if Omega is None else np.ascontiguousarray(Omega, dtype=np.float64).reshape(nb * 3)
+        d = ProblemDesc()
+        d.nbodies = nb
+        d.n_off = _np_ptr(self._n_off, ctypes.c_int64)
+        d.q_off = _np_ptr(self._q_off, ctypes.c_int64)
+        d.kind = _np_ptr(self._kind, ctypes.c_int32)
+        d.rigid = None if self._rigid is None else _np_ptr(self._rigid, ctypes.c_int32)
+        d.U = None if self._U is None else _np_ptr(self._U, ctypes.c_double)
+        d.Omega = None if self._Om is None else _np_ptr(self._Om, ctypes.c_double)
+        d.eps, d.mu = float(eps), float(mu)
+        d.nn_global = int(bool(nn_global))
+        d.factor_prec = PREC[factor_prec]
+        d.nb = 0
+        d.tol = float(tol)
+        d.max_outer, d.max_inner = int(max_outer), int(max_inner)
+        self.stream = stream or torch.cuda.current_stream()
+        self._h = ctypes.c_void_p()
+        st = _lib.nrs_create(ctypes.byref(self._h), ctypes.byref(d),
+                             ctypes.c_void_p(self.stream.cuda_stream))
+        if st != NRS_OK:
+            raise NrsError(st, "nrs_create failed")
+        N, Q, F, n = (ctypes.c_int64() for _ in range(4))
+        _lib.nrs_sizes(self._h, ctypes.byref(N), ctypes.byref(Q), ctypes.byref(F), ctypes.byref(n))
+        self.N, self.Q, self.F, self.n = N.value, Q.value, F.value, n.value
+        self.nbodies = nb
+
+    @classmethod
+    def from_problem(cls, problem, factor_prec: str = "fp32", **kw) -> "Context":
+        """Context for a ``synth.geometry.Problem`` (its body table and eps, mu)."""
+        n_off = np.cumsum([0] + [b.N for b in problem.bodies])
+        q_off = np.cumsum([0] + [b.Q for b in problem.bodies])
+        return cls(n_off, q_off, [b.kind for b in problem.bodies], problem.eps, problem.mu,
+                   rigid=[int(b.rigid) for b in problem.bodies],
+                   U=np.array([b.U for b in problem.bodies]),
+                   Omega=np.array([b.Omega for b in problem.bodies]),
+                   nn_global=problem.nn_global, factor_prec=factor_prec, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.nrs_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != NRS_OK:
+            raise NrsError(st, (_lib.nrs_last_error(self._h) or b"").decode())
+        return st
+
+    def last_error(self) -> str:
+        return (_lib.nrs_last_error(self._h) or b"").decode()
+
+    # -- state -------------------------------------------------------------
+    def set_state(self, x0, B):
+        x0 = np.ascontiguousarray(x0, dtype=np.float64).reshape(self.nbodies * 3)
+        B = np.ascontiguousarray(B, dtype=np.float64).reshape(self.nbodies * 9)
+        self._check(_lib.nrs_set_state(self._h, x0.ctypes.data, B.ctypes.data))
+
+    def get_state(self):
+        x0 = np.empty(self.nbodies * 3)
+        B = np.empty(self.nbodies * 9)
+        self._check(_lib.nrs_get_state(self._h, x0.ctypes.data, B.ctypes.data))
+        return {"x0": x0.reshape(-1, 3), "B": B.reshape(-1, 3, 3)}
+
+    def set_external(self, ext=None):
+        if ext is None:
+            self._check(_lib.nrs_set_external(self._h, None))
+        else:
+            e = np.ascontiguousarray(ext, dtype=np.float64).reshape(self.F * 6)
+            self._check(_lib.nrs_set_external(self._h, e.ctypes.data))
+
+    # -- the steps of the method --------------------------------------------
+    @staticmethod
+    def shapes(xi: torch.Tensor, Xiw: torch.Tensor, xidot: torch.Tensor) -> Shapes:
+        s = Shapes()
+        s.xi = _ptr(xi, torch.float64).value
+        s.Xiw = _ptr(Xiw, torch.float64).value
+        s.xidot = _ptr(xidot, torch.float64).value
+        s._keep = (xi, Xiw, xidot)
+        return s
+
+    def kinematics(self, xi, Xiw, xidot):
+        dev = xi.device
+        x = torch.empty((self.N, 4), dtype=torch.float64, device=dev)
+        Xw = torch.empty((self.Q, 4), dtype=torch.float64, device=dev)
+        b = torch.empty(self.n, dtype=torch.float64, device=dev)
+        s = self.shapes(xi, Xiw, xidot)
+        self._check(_lib.nrs_kinematics(self._h, ctypes.byref(s), _ptr(x), _ptr(Xw), _ptr(b)))
+        return x, Xw, b
+
+    def nearest_build(self, x, Xw):
+        dev = x.device
+        nn = torch.empty(self.Q, dtype=torch.int32, device=dev)
+        seg_ptr = torch.empty(self.N + 1, dtype=torch.int32, device=dev)
+        perm = torch.empty(self.Q, dtype=torch.int32, device=dev)
+        self._check(_lib.nrs_nearest_build(self._h, _ptr(x, torch.float64), _ptr(Xw, torch.float64),
+                                           _ptr(nn), _ptr(seg_ptr), _ptr(perm)))
+        return nn, seg_ptr, perm
+
+    def assemble(self, x, Xw, want_matrix: bool = True):
+        """Assemble A (kept in the context); returns the n x n FP64 matrix as a
+        tensor At with At[j, i] = A[i, j] (column-major storage) if asked."""
+        At = torch.empty((self.n, self.n), dtype=torch.float64, device=x.device) if want_matrix else None
+        self._check(_lib.nrs_assemble(self._h, _ptr(x, torch.float64), _ptr(Xw, torch.float64),
+                                      _ptr(At), self.n))
+        return At
+
+    def factor(self, prec: str = "fp32") -> int:
+        info = ctypes.c_int32(0)
+        st = _lib.nrs_factor(self._h, PREC[prec], ctypes.byref(info))
+        if st not in (NRS_OK, NRS_ESINGULAR):
+            self._check(st)
+        return info.value
+
+    def solve(self, b: torch.Tensor, x0: Optional[torch.Tensor] = None, check: bool = True):
+        nrhs = 1 if b.dim() == 1 else b.shape[0]
+        x = torch.empty_like(b)
+        reps = (SolveReport * nrhs)()
+        st = _lib.nrs_solve(self._h, _ptr(b, torch.float64), _ptr(x), nrhs, _ptr(x0), reps)
+        if check:
+            self._check(st)
+        return x, [r.as_dict() for r in reps]
+
+    def step(self, s0: Shapes, s_half: Shapes, dt: float, sol: Optional[torch.Tensor] = None,
+             report: bool = True, check: bool = True):
+        rep = StepReport() if report else None
+        st = _lib.nrs_step(self._h, ctypes.byref(s0), ctypes.byref(s_half), float(dt), _ptr(sol),
+                           ctypes.byref(rep) if rep is not None else None)
+        if check:
+            self._check(st)
+        if rep is None:
+            return None
+        return {"stages": [rep.stage[0].as_dict(), rep.stage[1].as_dict()], "ms": rep.ms_total,
+                "status": st}
+
+    def sync(self):
+        return self._check(_lib.nrs_sync(self._h))
+
+
+def shapes_to_device(shapes: dict, device="cuda"):
+    """Copy packed body-frame arrays (synth.geometry.pack_shapes) to the device."""
+    return tuple(torch.from_numpy(np.ascontiguousarray(shapes[k])).to(device)
+                 for k in ("x", "Xw", "xidot"))
