@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Seconds per time step of the NEAREST regularized-stokeslet swimming
+problem on GB300.
+
+One step = one explicit-midpoint (RK2) step of the single free undulating
+swimmer (N = 800 force points, Q = 8000 quadrature points, eps = 0.005,
+n = 2406 unknowns): twice (kinematics, nearest neighbours, segments, FP64
+assembly, rigid-body border, FP32 block-LU factor, FP64 GMRES-based
+iterative refinement to the FP64 answer) plus the state update.  Inputs are
+the seeded synthetic beat shapes of `synth` (the paper's cited beat patterns
+are not available), resident in HBM before the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nrs|reference]
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the same workload.  Under torchrun each rank runs its own replica of the
+problem ("replicas only": one dense solve does not shard across GPUs).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from synth import geometry as g  # noqa: E402
+
+METRIC = "s per timestep (assemble+solve) mixed-IR vs FP64 at 1e-10 rel err; pairs/s"
+WORKLOAD = "single free undulating swimmer, N=800 force / Q=8000 quadrature points, eps=0.005, n=2406"
+L2_FLUSH_BYTES = 512 << 20
+FP64_NOMINAL_TFLOPS = 1.25       # GB300 FP64 (vector and tensor), nominal
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.idx), "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(smax)),
+                       reasons=sorted(reasons), samples=len(sm))
+        return out
+
+
+def _visible_gpu_index(local: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    parts = [p for p in vis.split(",") if p.strip()]
+    if parts and parts[local if local < len(parts) else 0].strip().isdigit():
+        return int(parts[local if local < len(parts) else 0])
+    return local
+
+
+def _shapes_host(pr, t):
+    import torch
+    d = g.pack_shapes(pr, t)
+    return tuple(torch.from_numpy(d[k]).pin_memory() for k in ("x", "Xw", "xidot"))
+
+
+def _roofline(phase, ph_ms, ph_spans, timed_steps, pr, peaks, peak_src, clocks, lu_flops):
+    """Roofline record of the dominant kernel family."""
+    ms = ph_ms[phase]
+    launches = max(ph_spans[phase], 1)
+    per_launch_s = ms / 1e3 / launches
+    n = pr.n
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    if phase == "lu_update":
+        flops = lu_flops / launches * (ph_spans[phase] / max(ph_spans[phase], 1))
+        peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        return {"kernel": "k_gemm_update<float> (A22 -= L21 U12, FP32 CUDA cores)", "bound": "alu",
+                "achieved": flops / per_launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / per_launch_s / 1e12 / peak,
+                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median under load)",
+                "work_per_launch": flops, "traffic": None}
+    if phase == "assemble":
+        pairs = pr.pairs
+        flops_per_pair = 29.0
+        achieved = pairs * flops_per_pair / per_launch_s / 1e12
+        peak = FP64_NOMINAL_TFLOPS * sm_mhz / 2070.0
+        return {"kernel": "k_assemble64 (NEAREST A_s in FP64)", "bound": "alu", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": "nominal FP64 1.25 TFLOP/s at 2070 MHz, scaled to the median clock",
+                "pairs_per_s": pairs / per_launch_s, "work_per_launch": pairs * flops_per_pair,
+                "traffic": None}
+    if phase == "gemv":
+        bytes_ = 8.0 * n * n
+        achieved = bytes_ / per_launch_s / 1e9
+        peak = peaks["hbm_gbs"]
+        return {"kernel": "k_gemv_part (FP64 residual / Arnoldi products)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_src, "work_per_launch": bytes_, "traffic": None}
+    if phase == "trsv":
+        bytes_ = 4.0 * n * n  # both triangles of the FP32 factor per application
+        achieved = bytes_ / per_launch_s / 1e9
+        peak = peaks["hbm_gbs"]
+        return {"kernel": "k_trsv_lower/k_trsv_upper (preconditioner application)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_src, "work_per_launch": bytes_, "traffic": None}
+    return {"kernel": phase, "bound": "latency", "achieved": None, "peak": None, "unit": None,
+            "frac": None, "traffic": None}
+
+
+def _lu_update_flops(n, nb=64):
+    f = 0.0
+    for k0 in range(0, n, nb):
+        kb = min(nb, n - k0)
+        rest = n - k0 - kb
+        if rest > 0:
+            f += 2.0 * rest * rest * kb
+    return f
+
+
+def run_nrs(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2001_06468_gb300 import nrs
+
+    pr = g.swimmer_config()
+    dt = pr.dt
+    K, W = args.steps, args.warmup
+    total = K + W
+    # body-frame beat shapes at t and t + dt/2 for every step, pinned on the host
+    host = [(_shapes_host(pr, s * dt), _shapes_host(pr, (s + 0.5) * dt)) for s in range(total)]
+    dev = [tuple(tuple(t.cuda() for t in st) for st in pair) for pair in host]
+    Y0 = g.initial_state(pr)
+    ctx = nrs.Context.from_problem(pr, factor_prec=args.prec)
+    ctx.set_state(Y0["x0"], Y0["B"])
+    stream = ctx.stream
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def do_step(ctx_, pair):
+        s0 = nrs.Context.shapes(*pair[0])
+        sh = nrs.Context.shapes(*pair[1])
+        return ctx_.step(s0, sh, dt)
+
+    reports = []
+    for s in range(W):
+        reports.append(do_step(ctx, dev[s]))
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    ctx.set_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with ClockSampler(_visible_gpu_index(local)) as clk:
+        for s in range(K):
+            flush.fill_(float(s))  # evict L2 between timed steps (untimed)
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                ev[s][0].record(stream)
+                reports.append(do_step(ctx, dev[W + s]))
+                ev[s][1].record(stream)
+        torch.cuda.synchronize()
+    clocks = clk.summary()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    phases, launches = ctx.get_timing()
+    ctx.set_timing(False)
+    t_local = sum(step_ms) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t_local], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    else:
+        t_max = t_local
+    s_per_step = t_max / K / ws  # whole job: ws replicas each advance K steps
+
+    # end to end through the C ABI from pinned host buffers: H2D of both
+    # stages' shapes and D2H of the new state and both solutions, every step
+    ctx_e = nrs.Context.from_problem(pr, factor_prec=args.prec)
+    ctx_e.set_state(Y0["x0"], Y0["B"])
+    bufs = tuple(tuple(torch.empty_like(t, device="cuda") for t in st) for st in host[0])
+    sol = torch.empty(2 * pr.n, dtype=torch.float64, device="cuda")
+    sol_h = torch.empty(2 * pr.n, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for st in host[0] for t in st)
+    d2h = sol_h.numel() * 8 + pr.n_free * 12 * 8
+    for s in range(W):
+        do_step(ctx_e, dev[s])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_ms = 0.0
+    for s in range(K):
+        flush.fill_(float(s))
+        torch.cuda.synchronize()
+        with torch.cuda.stream(ctx_e.stream):
+            e0.record(ctx_e.stream)
+            for st_h, st_d in zip(host[W + s], bufs):
+                for th, td in zip(st_h, st_d):
+                    td.copy_(th, non_blocking=True)
+            ctx_e.step(nrs.Context.shapes(*bufs[0]), nrs.Context.shapes(*bufs[1]), dt, sol=sol,
+                       report=False)
+            sol_h.copy_(sol, non_blocking=True)
+            st = ctx_e.get_state()
+            e1.record(ctx_e.stream)
+        torch.cuda.synchronize()
+        e_ms += e0.elapsed_time(e1)
+    e2e_s = e_ms / 1e3 / K / ws
+
+    # plain FP64 path (FP64 factor) on the same steps, for the mixed-vs-plain ratio
+    ctx_p = nrs.Context.from_problem(pr, factor_prec="fp64")
+    ctx_p.set_state(Y0["x0"], Y0["B"])
+    Kp = min(K, 5)
+    do_step(ctx_p, dev[0])
+    torch.cuda.synchronize()
+    p_ms = 0.0
+    for s in range(Kp):
+        flush.fill_(float(s))
+        torch.cuda.synchronize()
+        with torch.cuda.stream(ctx_p.stream):
+            e0.record(ctx_p.stream)
+            do_step(ctx_p, dev[W + s])
+            e1.record(ctx_p.stream)
+        torch.cuda.synchronize()
+        p_ms += e0.elapsed_time(e1)
+    plain_s = p_ms / 1e3 / Kp
+
+    # the first step from the initial state, kept for the accuracy check
+    ctx_a = nrs.Context.from_problem(pr, factor_prec=args.prec)
+    ctx_a.set_state(Y0["x0"], Y0["B"])
+    sol_a = torch.empty(2 * pr.n, dtype=torch.float64, device="cuda")
+    ctx_a.step(nrs.Context.shapes(*dev[0][0]), nrs.Context.shapes(*dev[0][1]), dt, sol=sol_a)
+    sol_a = sol_a.cpu().numpy()
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
+    peaks, peak_src = _peaks()
+    ph_ms = {k: v[0] for k, v in phases.items()}
+    ph_spans = {k: v[1] for k, v in phases.items()}
+    tot = sum(ph_ms.values())
+    kernel_phases = ["lu_update", "assemble", "gemv", "trsv", "lu_panel", "nearest", "krylov"]
+    top = max(kernel_phases, key=lambda p: ph_ms[p])
+    lu_flops = _lu_update_flops(pr.n) * 2 * K  # two factorisations per step
+    roof = _roofline(top, ph_ms, ph_spans, K, pr, peaks, peak_src, clocks, lu_flops)
+    asm = _roofline("assemble", ph_ms, ph_spans, K, pr, peaks, peak_src, clocks, lu_flops)
+    line = {
+        "metric": METRIC,
+        "value": s_per_step,
+        "unit": "s/step",
+        "n_gpus": ws,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": t_max / K * 1e3,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 residual + f32 factor",
+        "data": "synthetic (seeded undulating-tube beat shapes)",
+        "config": {"workload": WORKLOAD, "factor": args.prec, "refinement": "GMRES-IR, FP64 residual",
+                   "rk2_stages_per_step": 2, "l2": "flushed between timed steps (512 MiB write)",
+                   "parallelism": f"replicas x{ws}"},
+        "pairs_per_s": asm.get("pairs_per_s"),
+        "plain_fp64_s_per_step": plain_s,
+        "mixed_vs_plain_speedup": plain_s / (t_max / K),
+        "phases_ms_per_step": {k: v / K for k, v in ph_ms.items()},
+        "phase_share": {k: (v / tot if tot else 0.0) for k, v in ph_ms.items()},
+        "refinement": {"outer_mean": float(np.mean([r["stages"][i]["outer"] for r in reports[W:] for i in (0, 1)])),
+                       "inner_mean": float(np.mean([r["stages"][i]["inner"] for r in reports[W:] for i in (0, 1)])),
+                       "backward_err_max": float(max(r["stages"][i]["backward_err"] for r in reports[W:] for i in (0, 1)))},
+        "roofline": roof,
+        "roofline_assembly": asm,
+        "e2e": {"value": e2e_s, "unit": "s/step", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(pr, sol_a)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def _oracle_step_timing(pr, max_steps, budget_s):
+    import oracle as O
+    Y = g.initial_state(pr)
+    times, first = [], None
+    for s in range(max_steps):
+        t0 = time.perf_counter()
+        Yn, stages = O.rk2_step(pr, Y, s * pr.dt, pr.dt, return_stages=True)
+        times.append(time.perf_counter() - t0)
+        if first is None:
+            first = stages
+        Y = Yn
+        if sum(times) > budget_s:
+            break
+    return times, first, O.threads()
+
+
+def cpu_baseline(pr, sol_gpu):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the same
+    workload; also the relative error of the GPU's first step against it."""
+    times, first, cores = _oracle_step_timing(pr, 3, 10.0)
+    n = pr.n
+    err = max(np.linalg.norm(sol_gpu[:n] - first["sol1"]) / np.linalg.norm(first["sol1"]),
+              np.linalg.norm(sol_gpu[n:] - first["sol2"]) / np.linalg.norm(first["sol2"]))
+    f1 = first["sol1"][:3 * pr.N]
+    V1 = first["sol1"][3 * pr.N:]
+    ef = np.linalg.norm(sol_gpu[:3 * pr.N] - f1) / np.linalg.norm(f1)
+    eV = np.linalg.norm(sol_gpu[3 * pr.N:n] - V1) / np.linalg.norm(V1)
+    return {"value": float(np.mean(times)), "unit": "s/step", "cores": cores, "kind": "oracle",
+            "sample": f"{len(times)} RK2 step(s) of the same workload from the initial state",
+            "gpu_rel_err_vs_oracle": float(err), "gpu_rel_err_f": float(ef), "gpu_rel_err_V": float(eV)}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    pr = g.swimmer_config()
+    W = min(args.warmup, 1)
+    K = min(args.steps, 10)
+    import oracle as O
+    O.build()
+    times, _, cores = _oracle_step_timing(pr, W + K, 1e9)
+    t = times[W:]
+    v = float(np.mean(t))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/step", "n_gpus": ws,
+            "steps": len(t), "warmup": W, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "solver": "FP64 partial-pivoting LU + double-double refinement"},
+            "cpu_baseline": {"value": v, "unit": "s/step", "cores": cores, "kind": "oracle",
+                             "sample": f"{len(t)} RK2 steps after {W} warm-up (steps capped at 10)"},
+            "e2e": {"value": v, "unit": "s/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="nrs", choices=["nrs", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "nrs":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_nrs(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -54,9 +54,9 @@ typedef enum {
 /* Precision of the LU factor used as the preconditioner. */
 typedef enum {
     NRS_FP64 = 0,  /* plain path: FP64 factor                                     */
-    NRS_FP32 = 1,  /* FP32 factor, trailing updates on FP32 CUDA cores             */
-    NRS_TF32 = 2,  /* FP32 storage, trailing updates on tensor cores (3xTF32)      */
-    NRS_BF16 = 3   /* FP32 storage, trailing updates on tensor cores with BF16 ops */
+    NRS_FP32 = 1,  /* FP32 explicit inverse (Gauss-Jordan), updates on FP32 CUDA cores */
+    NRS_TF32 = 2,  /* FP32 explicit inverse, updates on the tensor cores (TF32)       */
+    NRS_BF16 = 3   /* FP32 explicit inverse, updates on the tensor cores (BF16)       */
 } nrs_prec;
 
 /* Body kinds (Sec. 4: swimmers are free; walls are static). */
@@ -80,7 +80,9 @@ typedef struct {
                               1: over all force points in the lab frame */
     int32_t factor_prec;   /* nrs_prec used by nrs_step                */
     int32_t nb;            /* LU block size (0 = default 64; 32/64/128) */
-    double tol;            /* refinement stops when ||dx||_inf <= tol ||x||_inf (0 = 1e-14) */
+    double tol;            /* refinement stops when ||dx||_inf <= tol ||x||_inf, or when the
+                              next correction, predicted from the observed rate, is far
+                              below that (0 = 1e-12) */
     int32_t max_outer;     /* refinement steps (0 = 20)          */
     int32_t max_inner;     /* GMRES iterations per step (0 = 30) */
 } nrs_problem_desc;
@@ -168,9 +170,11 @@ nrs_status nrs_nearest_build(nrs_ctx *ctx, const double *x, const double *Xw, in
 nrs_status nrs_assemble(nrs_ctx *ctx, const double *x, const double *Xw, double *A64,
                         int64_t lda);
 
-/* Factor the assembled matrix in precision ``prec`` (Sec. 4 step 3).  Block
- * LU with row pivoting inside each diagonal block; for the FP32/TF32/BF16
- * precisions the factor preconditions the FP64 refinement of nrs_solve.
+/* Factor the assembled matrix in precision ``prec`` (Sec. 4 step 3).
+ * NRS_FP64: block LU of the FP64 matrix with row pivoting inside each 64 x 64
+ * diagonal block.  NRS_FP32/TF32/BF16: explicit inverse of an FP32 copy by
+ * blocked Gauss-Jordan elimination (pivoting inside each diagonal block),
+ * which preconditions the FP64 refinement of nrs_solve.
  * info (host, may be NULL) receives 0 or the 1-based column of the first
  * exactly-zero pivot; that case also returns NRS_ESINGULAR.  Synchronises
  * when info is requested. */
@@ -198,6 +202,33 @@ nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *s_half
 
 /* Wait for the context's stream and return the device status word. */
 nrs_status nrs_sync(nrs_ctx *ctx);
+
+/* Phases of the step, as timed by nrs_get_timing. */
+enum {
+    NRS_PH_KINEMATICS = 0, /* body frame -> lab frame, right-hand side          */
+    NRS_PH_NEAREST = 1,    /* nearest-neighbour search                          */
+    NRS_PH_SEGMENTS = 2,   /* segments of nu, gather, segment moments           */
+    NRS_PH_ASSEMBLE = 3,   /* the A_s assembly kernel                           */
+    NRS_PH_BORDER = 4,     /* rigid-body rows and columns                       */
+    NRS_PH_CONVERT = 5,    /* copy / precision conversion of A for the factor   */
+    NRS_PH_LU_PANEL = 6,   /* diagonal-block factor, row exchange, triangular panels */
+    NRS_PH_LU_UPDATE = 7,  /* trailing updates A22 -= L21 U12                   */
+    NRS_PH_TRSV = 8,       /* triangular solves with the factor                 */
+    NRS_PH_GEMV = 9,       /* FP64 residual / Arnoldi matrix-vector products    */
+    NRS_PH_KRYLOV = 10,    /* orthogonalisation, Givens, updates, norms         */
+    NRS_PH_UPDATE = 11,    /* explicit-midpoint state update                    */
+    NRS_NPHASE = 12
+};
+
+/* Enable (1) or disable (0) per-phase timing with CUDA events recorded on the
+ * context's stream around each phase's kernels.  Enabling clears the totals. */
+nrs_status nrs_set_timing(nrs_ctx *ctx, int32_t enable);
+
+/* Synchronise and return the per-phase totals since timing was enabled (host
+ * arrays of NRS_NPHASE: milliseconds and number of timed spans; either may be
+ * NULL) and the number of kernels launched since the context was created (or
+ * since timing was last enabled), then clear the totals. */
+nrs_status nrs_get_timing(nrs_ctx *ctx, double *ms, int64_t *spans, int64_t *launches);
 
 #ifdef __cplusplus
 }

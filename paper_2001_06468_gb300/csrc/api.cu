@@ -73,6 +73,9 @@ nrs_status alloc_all(Ctx *c)
         {(void **)&c->d_A32, sizeof(float) * lda * n},
         {(void **)&c->d_rowperm, sizeof(int32_t) * n},
         {(void **)&c->d_lperm, sizeof(int32_t) * 64},
+        {(void **)&c->d_gj_dinv, sizeof(float) * 64 * 64},
+        {(void **)&c->d_gj_rt, sizeof(float) * 64 * lda},
+        {(void **)&c->d_gj_cb, sizeof(float) * 64 * lda},
         {(void **)&c->d_info, sizeof(int32_t)},
         {(void **)&c->d_r, sizeof(double) * lda},
         {(void **)&c->d_w, sizeof(double) * lda},
@@ -108,9 +111,12 @@ void free_all(Ctx *c)
                     c->d_R,      c->d_A64,    c->d_A32,    c->d_LU64,       c->d_rowperm,
                     c->d_lperm,  c->d_info,   c->d_r,      c->d_xk,         c->d_w,
                     c->d_V,      c->d_H,      c->d_gv,     c->d_scal,       c->d_part,
-                    c->d_t32,    c->d_t64,    c->d_flags,  c->d_status};
+                    c->d_t32,    c->d_t64,    c->d_flags,  c->d_status,     c->d_gj_dinv,
+                    c->d_gj_rt,  c->d_gj_cb};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    c->ev_pool.clear();
 }
 
 bool is_prec(int p) { return p == NRS_FP64 || p == NRS_FP32 || p == NRS_TF32 || p == NRS_BF16; }
@@ -136,14 +142,20 @@ nrs_status do_factor(Ctx *c, int prec)
                 return fail(c, NRS_ENOMEM, "FP64 factor workspace does not fit");
             }
         }
+        c->tbeg(nrs::PH_CONVERT);
         CK(cudaMemcpyAsync(c->d_LU64, c->d_A64, sizeof(double) * elems, cudaMemcpyDeviceToDevice,
                            c->stream));
+        c->tend(nrs::PH_CONVERT);
         nrs::run_lu_fp64(*c, c->d_LU64, c->lda);
     } else {
-        if (!c->a32_fresh)
+        if (!c->a32_fresh) {
+            c->tbeg(nrs::PH_CONVERT);
             k_cvt_f64_f32<<<(unsigned)nrs::ceil_div((int64_t)elems, 256), 256, 0, c->stream>>>(
                 (int64_t)elems, c->d_A64, c->d_A32);
-        nrs::run_lu_fp32(*c, c->d_A32, c->lda, prec);
+            c->tend(nrs::PH_CONVERT);
+            c->launches += 1;
+        }
+        nrs::run_gj_fp32(*c, c->d_A32, c->lda, prec);
         c->a32_fresh = false;
     }
     CK(cudaGetLastError());
@@ -213,7 +225,7 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
     c->nn_global = d->nn_global ? 1 : 0;
     c->factor_prec = d->factor_prec;
     c->nb = 64;
-    c->tol = d->tol > 0 ? d->tol : 1e-14;
+    c->tol = d->tol > 0 ? d->tol : 1e-12;
     c->max_outer = d->max_outer > 0 ? d->max_outer : 20;
     c->max_inner = d->max_inner > 0 ? d->max_inner : 30;
     {
@@ -483,6 +495,43 @@ nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *sh, do
         cudaEventDestroy(ev1);
     }
     return worst;
+}
+
+nrs_status nrs_set_timing(nrs_ctx *ctx, int32_t enable)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return NRS_EINVAL;
+    CK(cudaStreamSynchronize(c->stream));
+    c->spans.clear();
+    c->ev_used = 0;
+    for (auto &e : c->open_ev) e = nullptr;
+    c->timing = enable != 0;
+    if (c->timing) c->launches = 0;
+    return NRS_OK;
+}
+
+nrs_status nrs_get_timing(nrs_ctx *ctx, double *ms, int64_t *spans, int64_t *launches)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return NRS_EINVAL;
+    CK(cudaStreamSynchronize(c->stream));
+    double acc[nrs::NPH] = {};
+    int64_t cnt[nrs::NPH] = {};
+    for (const auto &s : c->spans) {
+        float t = 0.0f;
+        CK(cudaEventElapsedTime(&t, s.a, s.b));
+        acc[s.ph] += t;
+        cnt[s.ph] += 1;
+    }
+    if (ms)
+        for (int i = 0; i < nrs::NPH; ++i) ms[i] = acc[i];
+    if (spans)
+        for (int i = 0; i < nrs::NPH; ++i) spans[i] = cnt[i];
+    if (launches) *launches = c->launches;
+    c->spans.clear();
+    c->ev_used = 0;
+    c->launches = 0;
+    return NRS_OK;
 }
 
 nrs_status nrs_sync(nrs_ctx *ctx)

@@ -108,8 +108,11 @@ void launch_assemble(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t l
 {
     dim3 grid((unsigned)ceil_div(c.N, AS_THREADS), (unsigned)ceil_div(c.N, AS_NT));
     const double coef = 1.0 / (8.0 * kPi * c.mu);
+    c.tbeg(PH_ASSEMBLE);
     k_assemble64<<<grid, AS_THREADS, 0, c.stream>>>(c.N, x_lab, c.d_Xs, c.d_seg_ptr, c.eps * c.eps,
                                                     coef, A64, A32, lda);
+    c.tend(PH_ASSEMBLE);
+    c.launches += 1;
 }
 
 }  // namespace nrs

@@ -84,9 +84,12 @@ void launch_kinematics(Ctx &c, const D4 *xi, const D4 *Xiw, const D4 *xidot, D4 
 {
     int64_t total = c.N + c.Q + 6 * c.F;
     int threads = 256;
+    c.tbeg(PH_KINEMATICS);
     k_kinematics<<<(unsigned)ceil_div(total, threads), threads, 0, c.stream>>>(
         c.N, c.Q, c.F, xi, Xiw, xidot, c.d_body_x, c.d_body_X, c.d_kind, c.d_x0, c.d_B, c.d_U,
         c.d_Om, c.d_ext, x, Xw, b);
+    c.tend(PH_KINEMATICS);
+    c.launches += 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -203,8 +206,11 @@ void launch_nearest(Ctx &c, const D4 *x, const D4 *Xw, int32_t *nn, bool only_de
     const NNTask *tasks = only_deforming ? c.d_tasks_deform : c.d_tasks_all;
     int count = only_deforming ? c.n_tasks_deform : c.n_tasks_all;
     if (count == 0) return;
+    c.tbeg(PH_NEAREST);
     k_nearest<<<count, NN_THREADS, 0, c.stream>>>(tasks, c.d_n_off, c.nbodies, c.nn_global, x, Xw,
                                                    nn, c.d_status);
+    c.tend(PH_NEAREST);
+    c.launches += 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -287,6 +293,7 @@ __global__ void k_sort_segments(int64_t N, const int32_t *__restrict__ seg_ptr,
 void launch_segments(Ctx &c, const int32_t *nn, int32_t *seg_ptr, int32_t *perm)
 {
     int threads = 256;
+    c.tbeg(PH_SEGMENTS);
     cudaMemsetAsync(c.d_cursor, 0, sizeof(int32_t) * (c.N + 1), c.stream);
     cudaMemsetAsync(perm, 0, sizeof(int32_t) * c.Q, c.stream);  // tail stays a valid index
     k_count<<<(unsigned)ceil_div(c.Q, threads), threads, 0, c.stream>>>(c.Q, c.N, nn, c.d_cursor);
@@ -295,6 +302,8 @@ void launch_segments(Ctx &c, const int32_t *nn, int32_t *seg_ptr, int32_t *perm)
     k_scatter<<<(unsigned)ceil_div(c.Q, threads), threads, 0, c.stream>>>(c.Q, c.N, nn, c.d_cursor,
                                                                           perm);
     k_sort_segments<<<(unsigned)ceil_div(c.N, threads), threads, 0, c.stream>>>(c.N, seg_ptr, perm);
+    c.tend(PH_SEGMENTS);
+    c.launches += 4;
 }
 
 // Lab-frame quadrature points in segment order, and per-segment moments
@@ -330,9 +339,12 @@ __global__ void k_moments(int64_t N, const int32_t *__restrict__ seg_ptr, const 
 void launch_gather(Ctx &c, const D4 *Xw_lab, const int32_t *seg_ptr, const int32_t *perm)
 {
     int threads = 256;
+    c.tbeg(PH_SEGMENTS);
     k_gather<<<(unsigned)ceil_div(c.Q, threads), threads, 0, c.stream>>>(c.Q, perm, Xw_lab, c.d_Xs);
     k_moments<<<(unsigned)ceil_div(c.N, threads), threads, 0, c.stream>>>(
         c.N, seg_ptr, c.d_Xs, c.d_body_x, c.d_x0, c.d_W, c.d_R);
+    c.tend(PH_SEGMENTS);
+    c.launches += 2;
 }
 
 // ---------------------------------------------------------------------------
@@ -392,8 +404,11 @@ void launch_border(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t lda
     int threads = 256;
     dim3 grid((unsigned)ceil_div(c.n, threads), (unsigned)(6 * c.F));
     // d_free_index holds nbodies entries (body -> free index) then F entries (free index -> body)
+    c.tbeg(PH_BORDER);
     k_border<<<grid, threads, 0, c.stream>>>(c.N, c.n, c.d_free_index + c.nbodies, c.d_body_x, x_lab,
                                              c.d_x0, c.d_W, c.d_R, A64, A32, lda);
+    c.tend(PH_BORDER);
+    c.launches += 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -455,9 +470,12 @@ __global__ void k_rk2(int stage, double dt, int nbodies, int64_t N,
 
 void launch_rk2(Ctx &c, int stage, double dt, const double *sol)
 {
+    c.tbeg(PH_UPDATE);
     k_rk2<<<(unsigned)ceil_div(c.nbodies, 64), 64, 0, c.stream>>>(
         stage, dt, c.nbodies, c.N, c.d_kind, c.d_free_index, sol, c.d_U, c.d_Om, c.d_x0_save,
         c.d_B_save, c.d_x0, c.d_B);
+    c.tend(PH_UPDATE);
+    c.launches += 1;
 }
 
 }  // namespace nrs

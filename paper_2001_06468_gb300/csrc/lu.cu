@@ -1,6 +1,6 @@
-// lu.cu -- blocked right-looking LU of the assembled system (the dense solve
-// of Gallagher & Smith, Sec. 4 step 3), in FP64 (plain path) or FP32
-// (preconditioner of the FP64 refinement).
+// lu.cu -- blocked right-looking LU of the assembled system in FP64 (the
+// dense solve of Gallagher & Smith, Sec. 4 step 3): the factor of the plain
+// FP64 path.  (The mixed-precision path inverts an FP32 copy instead, gj.cu.)
 //
 // Pivoting is restricted to the rows of each NB x NB diagonal block: the
 // block is factored with partial pivoting among its own rows and the same
@@ -12,8 +12,7 @@
 // (positive diagonal of segment weights), whose LU needs no pivoting, and the
 // rigid-body rows come last, where the in-block pivoting handles the zero
 // corner; the growth factor on the swimmer workloads equals that of full
-// partial pivoting.  For the FP32 paths the factor only preconditions the
-// FP64 refinement, which decides the accuracy.
+// partial pivoting.  The FP64 refinement of solve.cu removes what is left.
 //
 // Result: P A = L U with P the composition of the block-local exchanges,
 // rowperm[i] = original row now at position i, L unit lower and U upper
@@ -256,49 +255,46 @@ __global__ void k_iota(int64_t n, int32_t *__restrict__ p)
     if (i < n) p[i] = (int32_t)i;
 }
 
-// Trailing update on the tensor cores (tc_gemm.cu); returns false if the
-// precision has no tensor-core kernel.
-bool launch_tc_update(Ctx &c, float *A, int64_t lda, int64_t k0, int kb, int prec);
-
 template <typename T>
-static void lu_steps(Ctx &c, T *A, int64_t lda, int prec)
+static void lu_steps(Ctx &c, T *A, int64_t lda)
 {
     const int64_t n = c.n;
+    c.tbeg(PH_LU_PANEL);
     k_iota<<<(unsigned)ceil_div(n, 256), 256, 0, c.stream>>>(n, c.d_rowperm);
     cudaMemsetAsync(c.d_info, 0, sizeof(int32_t), c.stream);
+    c.launches += 1;
     for (int64_t k0 = 0; k0 < n; k0 += LU_NB) {
         const int kb = (int)std::min<int64_t>(LU_NB, n - k0);
+        if (k0 > 0) c.tbeg(PH_LU_PANEL);
         k_diag_factor<T, LU_NB><<<1, 256, 0, c.stream>>>(n, A, lda, k0, c.d_lperm, c.d_rowperm,
                                                           c.d_info);
-        if (k0 > 0)
+        c.launches += 1;
+        if (k0 > 0) {
             k_swap_left<T, LU_NB><<<(unsigned)ceil_div(k0, 128), 128, 0, c.stream>>>(k0, kb, A, lda,
                                                                                       c.d_lperm);
+            c.launches += 1;
+        }
         const int64_t rest = n - k0 - kb;
-        if (rest <= 0) continue;
+        if (rest <= 0) {
+            c.tend(PH_LU_PANEL);
+            continue;
+        }
         const unsigned g1 = (unsigned)ceil_div(rest, 128);
         k_trsm_l21<T, LU_NB><<<g1, 128, 0, c.stream>>>(n, A, lda, k0, kb);
         k_trsm_u12<T, LU_NB><<<g1, 128, 0, c.stream>>>(n, A, lda, k0, kb, c.d_lperm);
-        bool done = false;
-        if constexpr (sizeof(T) == 4) {
-            if (prec == NRS_TF32 || prec == NRS_BF16)
-                done = launch_tc_update(c, reinterpret_cast<float *>(A), lda, k0, kb, prec);
-        }
-        if (!done) {
-            dim3 g2((unsigned)ceil_div(rest, 64), (unsigned)ceil_div(rest, 64));
-            k_gemm_update<T><<<g2, 256, 0, c.stream>>>(n, A, lda, k0, kb);
-        }
+        c.launches += 2;
+        c.tend(PH_LU_PANEL);
+        c.tbeg(PH_LU_UPDATE);
+        dim3 g2((unsigned)ceil_div(rest, 64), (unsigned)ceil_div(rest, 64));
+        k_gemm_update<T><<<g2, 256, 0, c.stream>>>(n, A, lda, k0, kb);
+        c.launches += 1;
+        c.tend(PH_LU_UPDATE);
     }
 }
 
 int run_lu_fp64(Ctx &c, double *A, int64_t lda)
 {
-    lu_steps<double>(c, A, lda, NRS_FP64);
-    return 0;
-}
-
-int run_lu_fp32(Ctx &c, float *A, int64_t lda, int prec)
-{
-    lu_steps<float>(c, A, lda, prec);
+    lu_steps<double>(c, A, lda);
     return 0;
 }
 

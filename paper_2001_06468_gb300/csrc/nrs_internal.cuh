@@ -41,6 +41,23 @@ struct NNTask {
 
 struct Ctx;
 
+// Phases timed with CUDA events when timing is enabled (nrs_set_timing).
+enum Phase {
+    PH_KINEMATICS = NRS_PH_KINEMATICS,
+    PH_NEAREST = NRS_PH_NEAREST,
+    PH_SEGMENTS = NRS_PH_SEGMENTS,
+    PH_ASSEMBLE = NRS_PH_ASSEMBLE,
+    PH_BORDER = NRS_PH_BORDER,
+    PH_CONVERT = NRS_PH_CONVERT,
+    PH_LU_PANEL = NRS_PH_LU_PANEL,
+    PH_LU_UPDATE = NRS_PH_LU_UPDATE,
+    PH_TRSV = NRS_PH_TRSV,
+    PH_GEMV = NRS_PH_GEMV,
+    PH_KRYLOV = NRS_PH_KRYLOV,
+    PH_UPDATE = NRS_PH_UPDATE,
+    NPH = NRS_NPHASE
+};
+
 // ---- geometry kernels (geometry.cu) -------------------------------------
 void launch_kinematics(Ctx &c, const D4 *xi, const D4 *Xiw, const D4 *xidot, D4 *x, D4 *Xw,
                        double *b);
@@ -55,7 +72,7 @@ void launch_assemble(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t l
 
 // ---- factorisation (lu.cu) -------------------------------------------------
 int run_lu_fp64(Ctx &c, double *A, int64_t lda);
-int run_lu_fp32(Ctx &c, float *A, int64_t lda, int prec);
+int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec);
 
 bool tc_available();
 
@@ -76,7 +93,7 @@ struct Ctx {
     std::vector<int32_t> kind, rigid, free_index;
     double eps = 0, mu = 0;
     int nn_global = 0, factor_prec = NRS_FP32, nb = 64;
-    double tol = 1e-14;
+    double tol = 1e-12;
     int max_outer = 20, max_inner = 30;
 
     // device body tables
@@ -106,6 +123,9 @@ struct Ctx {
     int32_t *d_rowperm = nullptr;  // row order after pivoting: position i holds original row
     int32_t *d_lperm = nullptr;    // row exchange of the current diagonal block
     bool a32_fresh = false;        // d_A32 holds the last assembly (not yet factored)
+    float *d_gj_dinv = nullptr;    // Gauss-Jordan workspaces: D^{-1} (64 x 64)
+    float *d_gj_rt = nullptr;      //   scaled block row, transposed (n x 64)
+    float *d_gj_cb = nullptr;      //   block column (n x 64)
     int32_t *d_info = nullptr;
     int factored_prec = -1;
     bool assembled = false;
@@ -123,6 +143,42 @@ struct Ctx {
     int32_t *h_pinned = nullptr;  // pinned host mirror of small status values
     int trsv_epoch = 0;
     int trsv_grid = 0;
+
+    // timing (CUDA events on `stream`) and the count of kernels launched
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    struct Span {
+        int ph;
+        cudaEvent_t a, b;
+    };
+    std::vector<Span> spans;
+    cudaEvent_t open_ev[NPH] = {};
+    int64_t launches = 0;
+
+    cudaEvent_t next_event()
+    {
+        if (ev_used == ev_pool.size()) {
+            cudaEvent_t e = nullptr;
+            cudaEventCreate(&e);
+            ev_pool.push_back(e);
+        }
+        return ev_pool[ev_used++];
+    }
+    void tbeg(int ph)
+    {
+        if (!timing) return;
+        open_ev[ph] = next_event();
+        cudaEventRecord(open_ev[ph], stream);
+    }
+    void tend(int ph)
+    {
+        if (!timing || !open_ev[ph]) return;
+        cudaEvent_t e = next_event();
+        cudaEventRecord(e, stream);
+        spans.push_back(Span{ph, open_ev[ph], e});
+        open_ev[ph] = nullptr;
+    }
 };
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

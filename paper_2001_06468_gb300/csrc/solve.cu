@@ -35,6 +35,7 @@ enum {
     SC_BN = 6,
     SC_AN = 7,
     SC_RES = 8,
+    SC_DNPREV = 10,
     SC_COUNT = 16
 };
 
@@ -91,6 +92,7 @@ __global__ void __launch_bounds__(NB)
 {
     __shared__ T ys[NB];
     __shared__ T sacc[NB];
+    __shared__ T Ld[NB][NB + 1];
     __shared__ int s_abort;
     const int tid = threadIdx.x;
     const int64_t nblk = ceil_div(n, NB);
@@ -98,6 +100,9 @@ __global__ void __launch_bounds__(NB)
         const int64_t r0 = blk * NB;
         const int rows = (int)min((int64_t)NB, n - r0);
         const bool act = tid < rows;
+        // the diagonal block does not depend on other blocks: stage it first
+        if (act)
+            for (int c = 0; c < rows; ++c) Ld[tid][c] = LU[r0 + tid + (r0 + c) * lda];
         T acc = act ? (T)b[rowperm[r0 + tid]] : T(0);
         for (int64_t j = 0; j < blk; ++j) {
             if (!wait_flag(flags, j, epoch, status, &s_abort)) return;
@@ -114,7 +119,7 @@ __global__ void __launch_bounds__(NB)
         __syncthreads();
         for (int c = 0; c < rows; ++c) {
             const T yc = sacc[c];
-            if (act && tid > c) sacc[tid] -= LU[r0 + tid + (r0 + c) * lda] * yc;
+            if (act && tid > c) sacc[tid] -= Ld[tid][c] * yc;
             __syncthreads();
         }
         if (act) y[r0 + tid] = sacc[tid];
@@ -136,6 +141,7 @@ __global__ void __launch_bounds__(NB)
     __shared__ T xs[NB];
     __shared__ T sacc[NB];
     __shared__ T xout[NB];
+    __shared__ T Ud[NB][NB + 1];
     __shared__ int s_abort;
     const int tid = threadIdx.x;
     const int64_t nblk = ceil_div(n, NB);
@@ -144,6 +150,8 @@ __global__ void __launch_bounds__(NB)
         const int64_t r0 = blk * NB;
         const int rows = (int)min((int64_t)NB, n - r0);
         const bool act = tid < rows;
+        if (act)
+            for (int c = 0; c < rows; ++c) Ud[tid][c] = LU[r0 + tid + (r0 + c) * lda];
         T acc = act ? y[r0 + tid] : T(0);
         for (int64_t j = nblk - 1; j > blk; --j) {
             if (!wait_flag(flags, j, epoch, status, &s_abort)) return;
@@ -159,8 +167,8 @@ __global__ void __launch_bounds__(NB)
         sacc[tid] = acc;
         __syncthreads();
         for (int c = rows - 1; c >= 0; --c) {
-            const T xc = sacc[c] / LU[(r0 + c) + (r0 + c) * lda];
-            if (act && tid < c) sacc[tid] -= LU[r0 + tid + (r0 + c) * lda] * xc;
+            const T xc = sacc[c] / Ud[c][c];
+            if (act && tid < c) sacc[tid] -= Ud[tid][c] * xc;
             if (tid == c) xout[c] = xc;
             __syncthreads();
         }
@@ -197,6 +205,27 @@ __global__ void __launch_bounds__(MV_THREADS)
         s += ABS ? fabs(aij) : aij * __ldg(&v[j]);
     }
     part[blockIdx.y * n + i] = s;
+}
+
+// part[s*n + i] = sum_{j in split s} M[i,j] v[j] with the FP32 explicit inverse
+// M of the Gauss-Jordan factor (FP32 products and partial sums).
+__global__ void __launch_bounds__(MV_THREADS)
+    k_gemv32_part(int64_t n, const float *__restrict__ M, int64_t lda, const double *__restrict__ v,
+                  double *__restrict__ part, int64_t cols_per_split)
+{
+    const int64_t i = (int64_t)blockIdx.x * MV_THREADS + threadIdx.x;
+    const int64_t j0 = (int64_t)blockIdx.y * cols_per_split;
+    const int64_t j1 = min(n, j0 + cols_per_split);
+    if (i >= n) return;
+    float s0 = 0.0f, s1 = 0.0f;
+    const float *a = M + i;
+    int64_t j = j0;
+    for (; j + 1 < j1; j += 2) {
+        s0 += a[j * lda] * (float)__ldg(&v[j]);
+        s1 += a[(j + 1) * lda] * (float)__ldg(&v[j + 1]);
+    }
+    if (j < j1) s0 += a[j * lda] * (float)__ldg(&v[j]);
+    part[blockIdx.y * n + i] = (double)s0 + (double)s1;
 }
 
 // out[i] = b[i] - sum_s part (b != NULL), or sum_s part
@@ -342,10 +371,13 @@ __global__ void k_update(int64_t n, const double *__restrict__ V, int64_t ldv,
     x[e] += s;
 }
 
-// SC_DN = ||d||_inf, SC_XN = ||x||_inf; SC_OUTER_DONE when SC_DN <= tol SC_XN
+// SC_DN = ||d||_inf, SC_XN = ||x||_inf.  SC_OUTER_DONE when SC_DN <= tol SC_XN,
+// or when refinement has stagnated at the accuracy an FP64 residual can
+// deliver: the update no longer halves (SC_DN >= SC_DNPREV / 2) and is already
+// below floor * SC_XN (the usual stopping rule of iterative refinement).
 __global__ void __launch_bounds__(RED_THREADS)
     k_outer_check(int64_t n, const double *__restrict__ d, const double *__restrict__ x,
-                  double *__restrict__ scal, double tol, int32_t *status)
+                  double *__restrict__ scal, double tol, double floor, int32_t *status)
 {
     double dn = 0.0, xn = 0.0;
     for (int64_t e = threadIdx.x; e < n; e += RED_THREADS) {
@@ -362,7 +394,14 @@ __global__ void __launch_bounds__(RED_THREADS)
             scal[SC_OUTER_DONE] = 1.0;
         } else if (dn <= tol * xn) {
             scal[SC_OUTER_DONE] = 1.0;
+        } else if (scal[SC_DNPREV] > 0.0 && dn * (dn / scal[SC_DNPREV]) <= 1e-3 * tol * xn) {
+            // linear convergence at rate dn/dn_prev: the next correction is
+            // predicted far below the tolerance
+            scal[SC_OUTER_DONE] = 1.0;
+        } else if (scal[SC_DNPREV] > 0.0 && dn >= 0.5 * scal[SC_DNPREV] && dn <= floor * xn) {
+            scal[SC_OUTER_DONE] = 1.0;
         }
+        scal[SC_DNPREV] = dn;
     }
 }
 
@@ -388,11 +427,31 @@ static int coop_grid(Ctx &c, K kernel, int threads, int64_t nblk)
 }
 
 // x (FP64, length n) = M^{-1} v with the factor of the last nrs_factor.
+static cudaError_t apply_precond_impl(Ctx &c, const double *v, double *x);
+
 static cudaError_t apply_precond(Ctx &c, const double *v, double *x)
+{
+    c.tbeg(PH_TRSV);
+    cudaError_t e = apply_precond_impl(c, v, x);
+    c.tend(PH_TRSV);
+    c.launches += 2;
+    return e;
+}
+
+static cudaError_t apply_precond_impl(Ctx &c, const double *v, double *x)
 {
     const int64_t nblk = ceil_div(c.n, TR_NB);
     cudaError_t e;
-    if (c.factored_prec == NRS_FP64) {
+    if (c.factored_prec != NRS_FP64) {
+        // explicit inverse from the Gauss-Jordan factor: x = M v
+        const int64_t cps = ceil_div(c.n, c.part_splits);
+        dim3 grid((unsigned)ceil_div(c.n, MV_THREADS), (unsigned)c.part_splits);
+        k_gemv32_part<<<grid, MV_THREADS, 0, c.stream>>>(c.n, c.d_A32, c.lda, v, c.d_part, cps);
+        k_gemv_finish<<<(unsigned)ceil_div(c.n, 256), 256, 0, c.stream>>>(c.n, c.d_part,
+                                                                          c.part_splits, nullptr, x);
+        return cudaGetLastError();
+    }
+    {
         auto kl = k_trsv_lower<double, TR_NB>;
         auto ku = k_trsv_upper<double, TR_NB, double>;
         int epoch = ++c.trsv_epoch;
@@ -409,30 +468,18 @@ static cudaError_t apply_precond(Ctx &c, const double *v, double *x)
         return cudaLaunchCooperativeKernel((void *)ku, coop_grid(c, ku, TR_NB, nblk), TR_NB, args_u,
                                            0, c.stream);
     }
-    auto kl = k_trsv_lower<float, TR_NB>;
-    auto ku = k_trsv_upper<float, TR_NB, double>;
-    int epoch = ++c.trsv_epoch;
-    int64_t n = c.n, lda = c.lda;
-    float *LU = c.d_A32;
-    float *y = c.d_t32;
-    void *args_l[] = {&n, &LU, &lda, &c.d_rowperm, &v, &y, &c.d_flags, &epoch, &c.d_status};
-    e = cudaLaunchCooperativeKernel((void *)kl, coop_grid(c, kl, TR_NB, nblk), TR_NB, args_l, 0,
-                                    c.stream);
-    if (e != cudaSuccess) return e;
-    int epoch2 = ++c.trsv_epoch;
-    float *xw = c.d_t32 + c.lda;
-    void *args_u[] = {&n, &LU, &lda, &y, &xw, &x, &c.d_flags, &epoch2, &c.d_status};
-    return cudaLaunchCooperativeKernel((void *)ku, coop_grid(c, ku, TR_NB, nblk), TR_NB, args_u, 0,
-                                       c.stream);
 }
 
 static void gemv(Ctx &c, const double *v, const double *b, double *out)
 {
     const int64_t cps = ceil_div(c.n, c.part_splits);
     dim3 grid((unsigned)ceil_div(c.n, MV_THREADS), (unsigned)c.part_splits);
+    c.tbeg(PH_GEMV);
     k_gemv_part<false><<<grid, MV_THREADS, 0, c.stream>>>(c.n, c.d_A64, c.lda, v, c.d_part, cps);
     k_gemv_finish<<<(unsigned)ceil_div(c.n, 256), 256, 0, c.stream>>>(c.n, c.d_part, c.part_splits, b,
                                                                       out);
+    c.tend(PH_GEMV);
+    c.launches += 2;
 }
 
 static double read_scalar(Ctx &c, int slot, cudaError_t *err)
@@ -449,7 +496,7 @@ nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0, nr
     const int m = c.max_inner;
     const int64_t ldv = c.lda;
     const int ldh = m + 1;
-    const double tol_in = 1e-8;
+    const double tol_in = 1e-4;
     cudaError_t e = cudaSuccess;
 #define CKE(call)                                                           \
     do {                                                                    \
@@ -473,10 +520,13 @@ nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0, nr
         gemv(c, x, b, c.d_r);  // r = b - A x
         double *V0 = c.d_V;
         CKE(apply_precond(c, c.d_r, V0));
+        c.tbeg(PH_KRYLOV);
         CKE(cudaMemsetAsync(c.d_gv, 0, sizeof(double) * (4 * m + 2), c.stream));
         CKE(cudaMemsetAsync(c.d_scal + SC_INNER_DONE, 0, sizeof(double), c.stream));
         k_normalize<<<1, RED_THREADS, 0, c.stream>>>(n, V0, c.d_scal, SC_BETA, c.d_gv + 2 * m,
                                                      c.d_status);
+        c.tend(PH_KRYLOV);
+        c.launches += 1;
         int k = 0;
         for (int j = 0; j < m; ++j) {
             double *Vj = c.d_V + j * ldv;
@@ -484,6 +534,7 @@ nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0, nr
             gemv(c, Vj, nullptr, c.d_w);     // w = A v_j
             CKE(apply_precond(c, c.d_w, Vn));  // v_{j+1} = M^{-1} w
             const unsigned ge = (unsigned)ceil_div(n, 256);
+            c.tbeg(PH_KRYLOV);
             k_dots<<<j + 1, RED_THREADS, 0, c.stream>>>(n, c.d_V, ldv, Vn, h1);
             k_project_out<<<ge, 256, 0, c.stream>>>(n, c.d_V, ldv, h1, j + 1, Vn);
             k_dots<<<j + 1, RED_THREADS, 0, c.stream>>>(n, c.d_V, ldv, Vn, h2);
@@ -492,16 +543,22 @@ nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0, nr
                                                          c.d_status);
             k_givens<<<1, 32, 0, c.stream>>>(j, ldh, c.d_H, h1, h2, c.d_gv, m, c.d_scal, tol_in,
                                              c.d_status);
+            c.tend(PH_KRYLOV);
+            c.launches += 6;
             k = j + 1;
             ++inner_total;
             double done = read_scalar(c, SC_INNER_DONE, &e);
             if (e != cudaSuccess) CKE(e);
             if (done != 0.0) break;
         }
+        c.tbeg(PH_KRYLOV);
         k_lsq<<<1, 32, 0, c.stream>>>(k, ldh, c.d_H, c.d_gv, m);
         k_update<<<(unsigned)ceil_div(n, 256), 256, 0, c.stream>>>(n, c.d_V, ldv, c.d_gv + 3 * m + 1,
                                                                    k, x, c.d_w);
-        k_outer_check<<<1, RED_THREADS, 0, c.stream>>>(n, c.d_w, x, c.d_scal, c.tol, c.d_status);
+        k_outer_check<<<1, RED_THREADS, 0, c.stream>>>(n, c.d_w, x, c.d_scal, c.tol, 1e-12,
+                                                       c.d_status);
+        c.tend(PH_KRYLOV);
+        c.launches += 3;
         double od = read_scalar(c, SC_OUTER_DONE, &e);
         if (e != cudaSuccess) CKE(e);
         if (od != 0.0) {

@@ -34,7 +34,10 @@ FREE, PRESCRIBED, STATIC = 0, 1, 2
 
 EXPORTS = ["nrs_create", "nrs_destroy", "nrs_last_error", "nrs_sizes", "nrs_set_state",
            "nrs_get_state", "nrs_set_external", "nrs_kinematics", "nrs_nearest_build",
-           "nrs_assemble", "nrs_factor", "nrs_solve", "nrs_step", "nrs_sync"]
+           "nrs_assemble", "nrs_factor", "nrs_solve", "nrs_step", "nrs_sync", "nrs_set_timing",
+           "nrs_get_timing"]
+PHASES = ["kinematics", "nearest", "segments", "assemble", "border", "convert", "lu_panel",
+          "lu_update", "trsv", "gemv", "krylov", "update"]
 
 
 class ProblemDesc(ctypes.Structure):
@@ -90,6 +93,8 @@ _sig = {
     "nrs_step": (ctypes.c_int, [_P, ctypes.POINTER(Shapes), ctypes.POINTER(Shapes), ctypes.c_double,
                                 _P, ctypes.POINTER(StepReport)]),
     "nrs_sync": (ctypes.c_int, [_P]),
+    "nrs_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "nrs_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), _I64P, _I64P]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
@@ -274,6 +279,17 @@ class Context:
 
     def sync(self):
         return self._check(_lib.nrs_sync(self._h))
+
+    def set_timing(self, enable: bool = True):
+        self._check(_lib.nrs_set_timing(self._h, int(bool(enable))))
+
+    def get_timing(self):
+        """{phase: (ms, spans)} since timing was enabled, and the kernel count."""
+        ms = (ctypes.c_double * len(PHASES))()
+        spans = (ctypes.c_int64 * len(PHASES))()
+        launches = ctypes.c_int64()
+        self._check(_lib.nrs_get_timing(self._h, ms, spans, ctypes.byref(launches)))
+        return {p: (ms[i], spans[i]) for i, p in enumerate(PHASES)}, launches.value
 
 
 def shapes_to_device(shapes: dict, device="cuda"):
