@@ -83,7 +83,7 @@ nrs_status alloc_all(Ctx *c)
         {(void **)&c->d_H, sizeof(double) * (m + 1) * m},
         {(void **)&c->d_gv, sizeof(double) * (4 * m + 2)},
         {(void **)&c->d_scal, sizeof(double) * (16 + 2 * (m + 1))},
-        {(void **)&c->d_part, sizeof(double) * c->part_splits * n},
+        {(void **)&c->d_part, sizeof(double) * 64 * lda},
         {(void **)&c->d_t32, sizeof(float) * 2 * lda},
         {(void **)&c->d_t64, sizeof(double) * 2 * lda},
         {(void **)&c->d_flags, sizeof(int32_t) * nrs::ceil_div(n, 64)},
@@ -229,9 +229,14 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
     c->max_outer = d->max_outer > 0 ? d->max_outer : 20;
     c->max_inner = d->max_inner > 0 ? d->max_inner : 30;
     {
-        int64_t rowblocks = nrs::ceil_div(c->n, 128);
-        int64_t s = nrs::ceil_div(2 * (int64_t)c->num_sms, rowblocks);
-        c->part_splits = (int)std::max<int64_t>(1, std::min<int64_t>(s, 64));
+        // enough column splits for about two CTAs per SM in the matrix-vector products
+        auto splits = [&](int64_t rows_per_cta) {
+            int64_t rowblocks = nrs::ceil_div(c->n, rows_per_cta);
+            int64_t s = nrs::ceil_div(2 * (int64_t)c->num_sms, rowblocks);
+            return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(s, 64), c->n));
+        };
+        c->splits64 = splits(256);
+        c->splits32 = splits(512);
     }
     nrs_status st = alloc_all(c);
     if (st != NRS_OK) {

@@ -21,81 +21,90 @@ namespace nrs {
 
 constexpr int GJ_NB = 64;
 
-// D^{-1} by Gauss-Jordan on [D | I] with partial pivoting (one CTA).
-// Dinv is row-major kb x kb (pitch GJ_NB).  A zero pivot records info.
+// D^{-1} by Gauss-Jordan on [D | I] with partial pivoting (one CTA of 256
+// threads).  Thread (r, s) = (tid / 4, tid % 4) keeps columns s + 4 i
+// (i = 0..31) of augmented row r in registers; the column loop is unrolled so
+// every register index is static.  Rows are never moved: the pivot of column c
+// is the unused row of largest |value| (lowest row on ties), and logical row c
+// of D^{-1} is the right half of that physical row.  Padding rows/columns
+// (kb < 64) are identity.  Dinv is row-major 64 x 64; a zero pivot records info.
 __global__ void __launch_bounds__(256)
     k_gj_diag(int64_t n, const float *__restrict__ M, int64_t lda, int64_t k0,
               float *__restrict__ Dinv, int32_t *__restrict__ info)
 {
     constexpr int NB = GJ_NB;
-    __shared__ float W[NB][2 * NB + 1];
-    __shared__ float F[NB];
+    __shared__ float colc[2][NB];
+    __shared__ float prow[2 * NB];
+    __shared__ int used[NB];
+    __shared__ int pos[NB];
     __shared__ int s_piv;
     const int tid = threadIdx.x;
+    const int r = tid >> 2, s = tid & 3;
     const int kb = (int)min((int64_t)NB, n - k0);
-    for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
-        const int r = idx % kb, c = idx / kb;
-        W[r][c] = M[(k0 + r) + (k0 + c) * lda];
-        W[r][kb + c] = (r == c) ? 1.0f : 0.0f;
+    float own[32];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int j = s + 4 * i;
+        own[i] = (r < kb && j < kb) ? M[(k0 + r) + (k0 + j) * lda] : (r == j ? 1.0f : 0.0f);
+        own[16 + i] = (r == j) ? 1.0f : 0.0f;
     }
+    if (tid < NB) used[tid] = 0;
     __syncthreads();
-    const int w2 = 2 * kb;
-    for (int c = 0; c < kb; ++c) {
+#pragma unroll
+    for (int c = 0; c < NB; ++c) {
+        if (s == (c & 3)) colc[c & 1][r] = own[c >> 2];
+        __syncthreads();
         if (tid < 32) {
-            float best = -1.0f;
-            int br = c;
-            for (int r = c + tid; r < kb; r += 32) {
-                const float a = fabsf(W[r][c]);
-                if (a > best) {
-                    best = a;
-                    br = r;
-                }
+            float v0 = used[tid] ? -1.0f : fabsf(colc[c & 1][tid]);
+            float v1 = used[tid + 32] ? -1.0f : fabsf(colc[c & 1][tid + 32]);
+            int b = tid;
+            float bv = v0;
+            if (v1 > bv) {
+                bv = v1;
+                b = tid + 32;
             }
             for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int orr = __shfl_xor_sync(0xffffffffu, br, o);
-                if (ob > best || (ob == best && orr < br)) {
-                    best = ob;
-                    br = orr;
+                const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int ob = __shfl_xor_sync(0xffffffffu, b, o);
+                if (ov > bv || (ov == bv && ob < b)) {
+                    bv = ov;
+                    b = ob;
                 }
             }
-            if (tid == 0) s_piv = br;
+            if (tid == 0) {
+                s_piv = b;
+                used[b] = 1;
+                pos[b] = c;
+                if (colc[c & 1][b] == 0.0f && info) atomicCAS(info, 0, (int)(k0 + c + 1));
+            }
         }
         __syncthreads();
         const int p = s_piv;
-        if (p != c)
-            for (int j = tid; j < w2; j += blockDim.x) {
-                const float t = W[c][j];
-                W[c][j] = W[p][j];
-                W[p][j] = t;
+        const float inv = 1.0f / colc[c & 1][p];
+        if (r == p) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                own[i] *= inv;
+                prow[s + 4 * i] = own[i];
             }
-        __syncthreads();
-        const float pv = W[c][c];
-        if (pv == 0.0f) {
-            if (tid == 0 && info) atomicCAS(info, 0, (int)(k0 + c + 1));
-            __syncthreads();
-            continue;
-        }
-        const float inv = 1.0f / pv;
-        for (int j = tid; j < w2; j += blockDim.x) W[c][j] *= inv;
-        if (tid < kb) F[tid] = W[tid][c];
-        __syncthreads();
-        for (int idx = tid; idx < kb * w2; idx += blockDim.x) {
-            const int r = idx / w2, j = idx % w2;
-            if (r != c) W[r][j] -= F[r] * W[c][j];
         }
         __syncthreads();
+        if (r != p) {
+            const float f = colc[c & 1][r];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) own[i] -= f * prow[s + 4 * i];
+        }
     }
-    for (int idx = tid; idx < kb * kb; idx += blockDim.x) {
-        const int r = idx / kb, c = idx % kb;
-        Dinv[r * NB + c] = W[r][kb + c];
-    }
+    __syncthreads();
+    const int lr = pos[r];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) Dinv[lr * NB + s + 4 * i] = own[16 + i];
 }
 
-// R[:, j] = D^{-1} M[K, j] for one tile of 64 columns (R[:,K] = 0), written
-// transposed: Rt[j * NB + r] (column j's kb entries contiguous).  The CTAs of
-// the last grid row copy the block column C = M[:, K] into Cb (row-major,
-// Cb[i * NB + c], rows of K set to zero).
+// Prep of step K.  grid.y = 0: R[:, j] = D^{-1} M[K, j] for one 64-column tile
+// (R[:,K] = 0), stored transposed Rt[j * 64 + r].  grid.y = 1: the block column
+// C = M[:, K] for one 64-row tile, stored row-major Cb[i * 64 + c] (rows of K
+// zero).  Both through shared memory so every global access is coalesced.
 __global__ void __launch_bounds__(256)
     k_gj_prep(int64_t n, const float *__restrict__ M, int64_t lda, int64_t k0,
               const float *__restrict__ Dinv, float *__restrict__ Rt, float *__restrict__ Cb)
@@ -105,35 +114,53 @@ __global__ void __launch_bounds__(256)
     __shared__ float Ms[NB][NB + 1];
     const int tid = threadIdx.x;
     const int kb = (int)min((int64_t)NB, n - k0);
+    const int64_t t0 = (int64_t)blockIdx.x * NB;
+    if (t0 >= n) return;
+    const int nt = (int)min((int64_t)NB, n - t0);
     if (blockIdx.y == 1) {
-        // block column copy: rows i = blockIdx.x * 256 + tid
-        const int64_t i = (int64_t)blockIdx.x * 256 + tid;
-        if (i >= n) return;
-        const bool in_k = i >= k0 && i < k0 + kb;
-        for (int c = 0; c < NB; ++c)
-            Cb[i * NB + c] = (c < kb && !in_k) ? M[i + (k0 + c) * lda] : 0.0f;
+        const bool in_k = (t0 == k0);
+        for (int idx = tid; idx < NB * NB; idx += 256) {
+            const int i = idx & 63, c = idx >> 6;
+            Ms[i][c] = (i < nt && c < kb && !in_k) ? M[(t0 + i) + (k0 + c) * lda] : 0.0f;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < NB * NB; idx += 256) {
+            const int c = idx & 63, i = idx >> 6;
+            if (i < nt) Cb[(t0 + i) * NB + c] = Ms[i][c];
+        }
         return;
     }
-    const int64_t j0 = (int64_t)blockIdx.x * NB;
-    if (j0 >= n) return;
-    const int nj = (int)min((int64_t)NB, n - j0);
-    for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
-        const int r = idx / NB, c = idx % NB;
-        Ds[r][c] = (r < kb && c < kb) ? Dinv[r * NB + c] : 0.0f;
-        const int rr = idx % NB, cc = idx / NB;  // coalesced over rows of M
-        Ms[rr][cc] = (rr < kb && cc < nj) ? M[(k0 + rr) + (j0 + cc) * lda] : 0.0f;
+    const bool tile_is_k = (t0 == k0);
+    for (int idx = tid; idx < NB * NB; idx += 256) {
+        const int a = idx & 63, b = idx >> 6;
+        Ds[b][a] = Dinv[b * NB + a];
+        Ms[a][b] = (a < kb && b < nt) ? M[(k0 + a) + (t0 + b) * lda] : 0.0f;
     }
     __syncthreads();
-    const bool tile_is_k = (j0 == k0);
-    for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
-        const int c = idx / NB, r = idx % NB;  // output Rt[(j0+c)*NB + r]
-        if (c >= nj) continue;
-        float s = 0.0f;
-        if (!tile_is_k && r < kb) {
-#pragma unroll 16
-            for (int t = 0; t < NB; ++t) s += Ds[r][t] * Ms[t][c];
+    // thread computes R[r, t0 + c] for r = tr + 16 rr, c = tc + 16 cc (4 x 4)
+    const int tr = tid & 15, tc = tid >> 4;
+    float acc[4][4] = {};
+#pragma unroll 8
+    for (int t = 0; t < NB; ++t) {
+        float a[4], b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[q] = Ds[tr + 16 * q][t];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) b[q] = Ms[t][tc + 16 * q];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * b[y];
+    }
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+        const int c = tc + 16 * y;
+        if (c >= nt) continue;
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int rr = tr + 16 * x;
+            Rt[(t0 + c) * NB + rr] = (tile_is_k || rr >= kb) ? 0.0f : acc[x][y];
         }
-        Rt[(j0 + c) * NB + r] = s;
     }
 }
 
@@ -185,8 +212,9 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// Block row K <- R, block column K <- -C D^{-1}, M[K,K] <- D^{-1}.
-// Grid x over 256-wide chunks; y = 0: columns j (block row), y = 1: rows i.
+// Block row K <- R, block column K <- -C D^{-1}, M[K,K] <- D^{-1}, in 64-wide
+// tiles.  grid.y = 0: column tile t0 of block row K; grid.y = 1: row tile t0
+// of block column K.
 __global__ void __launch_bounds__(256)
     k_gj_finish(int64_t n, float *__restrict__ M, int64_t lda, int64_t k0,
                 const float *__restrict__ Dinv, const float *__restrict__ Rt,
@@ -194,33 +222,51 @@ __global__ void __launch_bounds__(256)
 {
     constexpr int NB = GJ_NB;
     __shared__ float Ds[NB][NB + 1];
+    __shared__ float Cs[NB][NB + 1];
     const int tid = threadIdx.x;
     const int kb = (int)min((int64_t)NB, n - k0);
-    for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
-        const int r = idx / NB, c = idx % NB;
-        Ds[r][c] = (r < kb && c < kb) ? Dinv[r * NB + c] : 0.0f;
+    const int64_t t0 = (int64_t)blockIdx.x * NB;
+    if (t0 >= n) return;
+    const int nt = (int)min((int64_t)NB, n - t0);
+    if (blockIdx.y == 0) {
+        const bool tile_is_k = (t0 == k0);
+        for (int idx = tid; idx < NB * NB; idx += 256) {
+            const int rr = idx & 63, c = idx >> 6;
+            if (rr >= kb || c >= nt) continue;
+            M[(k0 + rr) + (t0 + c) * lda] = tile_is_k ? Dinv[rr * NB + c] : Rt[(t0 + c) * NB + rr];
+        }
+        return;
+    }
+    if (t0 == k0) return;
+    for (int idx = tid; idx < NB * NB; idx += 256) {
+        const int a = idx & 63, b = idx >> 6;
+        Ds[b][a] = Dinv[b * NB + a];
+        Cs[b][a] = b < nt ? Cb[(t0 + b) * NB + a] : 0.0f;
     }
     __syncthreads();
-    const int64_t t = (int64_t)blockIdx.x * 256 + tid;
-    if (t >= n) return;
-    if (blockIdx.y == 0) {
-        const int64_t j = t;  // block row K, column j
-        if (j >= k0 && j < k0 + kb) {
-            for (int r = 0; r < kb; ++r) M[(k0 + r) + j * lda] = Ds[r][j - k0];
-        } else {
-            for (int r = 0; r < kb; ++r) M[(k0 + r) + j * lda] = Rt[j * NB + r];
-        }
-    } else {
-        const int64_t i = t;  // block column K, row i
-        if (i >= k0 && i < k0 + kb) return;
-        float cr[NB];
+    // thread computes out[i][c] = -sum_t C[i][t] Dinv[t][c], i = tr + 16 x, c = tc + 16 y
+    const int tr = tid & 15, tc = tid >> 4;
+    float acc[4][4] = {};
+#pragma unroll 8
+    for (int t = 0; t < NB; ++t) {
+        float a[4], b[4];
 #pragma unroll
-        for (int c = 0; c < NB; ++c) cr[c] = Cb[i * NB + c];
-        for (int c = 0; c < kb; ++c) {
-            float s = 0.0f;
+        for (int q = 0; q < 4; ++q) a[q] = Cs[tr + 16 * q][t];
 #pragma unroll
-            for (int t2 = 0; t2 < NB; ++t2) s += cr[t2] * Ds[t2][c];
-            M[i + (k0 + c) * lda] = -s;
+        for (int q = 0; q < 4; ++q) b[q] = Ds[t][tc + 16 * q];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * b[y];
+    }
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+        const int c = tc + 16 * y;
+        if (c >= kb) continue;
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int i = tr + 16 * x;
+            if (i < nt) M[(t0 + i) + (k0 + c) * lda] = -acc[x][y];
         }
     }
 }
@@ -235,12 +281,11 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
     const int64_t n = c.n;
     cudaMemsetAsync(c.d_info, 0, sizeof(int32_t), c.stream);
     const unsigned gcols = (unsigned)ceil_div(n, GJ_NB);
-    const unsigned g256 = (unsigned)ceil_div(n, 256);
     for (int64_t k0 = 0; k0 < n; k0 += GJ_NB) {
         c.tbeg(PH_LU_PANEL);
         k_gj_diag<<<1, 256, 0, c.stream>>>(n, M, lda, k0, c.d_gj_dinv, c.d_info);
-        k_gj_prep<<<dim3(std::max(gcols, g256), 2), 256, 0, c.stream>>>(n, M, lda, k0, c.d_gj_dinv,
-                                                                         c.d_gj_rt, c.d_gj_cb);
+        k_gj_prep<<<dim3(gcols, 2), 256, 0, c.stream>>>(n, M, lda, k0, c.d_gj_dinv, c.d_gj_rt,
+                                                         c.d_gj_cb);
         c.tend(PH_LU_PANEL);
         c.tbeg(PH_LU_UPDATE);
         bool done = false;
@@ -251,8 +296,8 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
                                                                         c.d_gj_rt);
         c.tend(PH_LU_UPDATE);
         c.tbeg(PH_LU_PANEL);
-        k_gj_finish<<<dim3(g256, 2), 256, 0, c.stream>>>(n, M, lda, k0, c.d_gj_dinv, c.d_gj_rt,
-                                                         c.d_gj_cb);
+        k_gj_finish<<<dim3(gcols, 2), 256, 0, c.stream>>>(n, M, lda, k0, c.d_gj_dinv, c.d_gj_rt,
+                                                           c.d_gj_cb);
         c.tend(PH_LU_PANEL);
         c.launches += 4;
     }

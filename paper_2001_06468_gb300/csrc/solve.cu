@@ -188,44 +188,63 @@ __global__ void __launch_bounds__(NB)
 
 constexpr int MV_THREADS = 128;
 
-// part[s*n + i] = sum_{j in split s} A[i,j] v[j]   (or |A[i,j]| when ABS)
+// part[s*n + i] = sum_{j in split s} A[i,j] v[j] (|A[i,j]| when ABS) for the
+// FP64 matrix.  Each thread owns two adjacent rows (one 16-byte load per
+// column), so a warp reads 512 contiguous bytes per column; rows i+1 >= n read
+// the padding rows below n (allocated, results discarded).
 template <bool ABS>
 __global__ void __launch_bounds__(MV_THREADS)
     k_gemv_part(int64_t n, const double *__restrict__ A, int64_t lda, const double *__restrict__ v,
                 double *__restrict__ part, int64_t cols_per_split)
 {
-    const int64_t i = (int64_t)blockIdx.x * MV_THREADS + threadIdx.x;
+    const int64_t i = ((int64_t)blockIdx.x * MV_THREADS + threadIdx.x) * 2;
     const int64_t j0 = (int64_t)blockIdx.y * cols_per_split;
     const int64_t j1 = min(n, j0 + cols_per_split);
     if (i >= n) return;
-    double s = 0.0;
+    double s0 = 0.0, s1 = 0.0;
     const double *a = A + i;
+#pragma unroll 8
     for (int64_t j = j0; j < j1; ++j) {
-        const double aij = a[j * lda];
-        s += ABS ? fabs(aij) : aij * __ldg(&v[j]);
+        const double2 x = __ldg(reinterpret_cast<const double2 *>(a + j * lda));
+        if (ABS) {
+            s0 += fabs(x.x);
+            s1 += fabs(x.y);
+        } else {
+            const double vj = __ldg(&v[j]);
+            s0 += x.x * vj;
+            s1 += x.y * vj;
+        }
     }
-    part[blockIdx.y * n + i] = s;
+    part[blockIdx.y * n + i] = s0;
+    if (i + 1 < n) part[blockIdx.y * n + i + 1] = s1;
 }
 
-// part[s*n + i] = sum_{j in split s} M[i,j] v[j] with the FP32 explicit inverse
-// M of the Gauss-Jordan factor (FP32 products and partial sums).
+// Same with the FP32 explicit inverse of the Gauss-Jordan factor: four rows
+// per thread (one 16-byte load per column), FP32 products and partial sums.
 __global__ void __launch_bounds__(MV_THREADS)
     k_gemv32_part(int64_t n, const float *__restrict__ M, int64_t lda, const double *__restrict__ v,
                   double *__restrict__ part, int64_t cols_per_split)
 {
-    const int64_t i = (int64_t)blockIdx.x * MV_THREADS + threadIdx.x;
+    const int64_t i = ((int64_t)blockIdx.x * MV_THREADS + threadIdx.x) * 4;
     const int64_t j0 = (int64_t)blockIdx.y * cols_per_split;
     const int64_t j1 = min(n, j0 + cols_per_split);
     if (i >= n) return;
-    float s0 = 0.0f, s1 = 0.0f;
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
     const float *a = M + i;
-    int64_t j = j0;
-    for (; j + 1 < j1; j += 2) {
-        s0 += a[j * lda] * (float)__ldg(&v[j]);
-        s1 += a[(j + 1) * lda] * (float)__ldg(&v[j + 1]);
+#pragma unroll 8
+    for (int64_t j = j0; j < j1; ++j) {
+        const float4 x = __ldg(reinterpret_cast<const float4 *>(a + j * lda));
+        const float vj = (float)__ldg(&v[j]);
+        s0 += x.x * vj;
+        s1 += x.y * vj;
+        s2 += x.z * vj;
+        s3 += x.w * vj;
     }
-    if (j < j1) s0 += a[j * lda] * (float)__ldg(&v[j]);
-    part[blockIdx.y * n + i] = (double)s0 + (double)s1;
+    double *p = part + blockIdx.y * n + i;
+    p[0] = s0;
+    if (i + 1 < n) p[1] = s1;
+    if (i + 2 < n) p[2] = s2;
+    if (i + 3 < n) p[3] = s3;
 }
 
 // out[i] = b[i] - sum_s part (b != NULL), or sum_s part
@@ -444,11 +463,11 @@ static cudaError_t apply_precond_impl(Ctx &c, const double *v, double *x)
     cudaError_t e;
     if (c.factored_prec != NRS_FP64) {
         // explicit inverse from the Gauss-Jordan factor: x = M v
-        const int64_t cps = ceil_div(c.n, c.part_splits);
-        dim3 grid((unsigned)ceil_div(c.n, MV_THREADS), (unsigned)c.part_splits);
+        const int64_t cps = ceil_div(c.n, c.splits32);
+        dim3 grid((unsigned)ceil_div(c.n, 4 * MV_THREADS), (unsigned)c.splits32);
         k_gemv32_part<<<grid, MV_THREADS, 0, c.stream>>>(c.n, c.d_A32, c.lda, v, c.d_part, cps);
-        k_gemv_finish<<<(unsigned)ceil_div(c.n, 256), 256, 0, c.stream>>>(c.n, c.d_part,
-                                                                          c.part_splits, nullptr, x);
+        k_gemv_finish<<<(unsigned)ceil_div(c.n, 256), 256, 0, c.stream>>>(c.n, c.d_part, c.splits32,
+                                                                          nullptr, x);
         return cudaGetLastError();
     }
     {
@@ -472,11 +491,11 @@ static cudaError_t apply_precond_impl(Ctx &c, const double *v, double *x)
 
 static void gemv(Ctx &c, const double *v, const double *b, double *out)
 {
-    const int64_t cps = ceil_div(c.n, c.part_splits);
-    dim3 grid((unsigned)ceil_div(c.n, MV_THREADS), (unsigned)c.part_splits);
+    const int64_t cps = ceil_div(c.n, c.splits64);
+    dim3 grid((unsigned)ceil_div(c.n, 2 * MV_THREADS), (unsigned)c.splits64);
     c.tbeg(PH_GEMV);
     k_gemv_part<false><<<grid, MV_THREADS, 0, c.stream>>>(c.n, c.d_A64, c.lda, v, c.d_part, cps);
-    k_gemv_finish<<<(unsigned)ceil_div(c.n, 256), 256, 0, c.stream>>>(c.n, c.d_part, c.part_splits, b,
+    k_gemv_finish<<<(unsigned)ceil_div(c.n, 256), 256, 0, c.stream>>>(c.n, c.d_part, c.splits64, b,
                                                                       out);
     c.tend(PH_GEMV);
     c.launches += 2;
@@ -577,12 +596,12 @@ nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0, nr
         k_nrm_inf<<<1, RED_THREADS, 0, c.stream>>>(n, c.d_r, c.d_scal, SC_RN);
         k_nrm_inf<<<1, RED_THREADS, 0, c.stream>>>(n, b, c.d_scal, SC_BN);
         {
-            const int64_t cps = ceil_div(c.n, c.part_splits);
-            dim3 grid((unsigned)ceil_div(c.n, MV_THREADS), (unsigned)c.part_splits);
+            const int64_t cps = ceil_div(c.n, c.splits64);
+            dim3 grid((unsigned)ceil_div(c.n, 2 * MV_THREADS), (unsigned)c.splits64);
             k_gemv_part<true><<<grid, MV_THREADS, 0, c.stream>>>(c.n, c.d_A64, c.lda, nullptr,
                                                                  c.d_part, cps);
             k_gemv_finish<<<(unsigned)ceil_div(c.n, 256), 256, 0, c.stream>>>(
-                c.n, c.d_part, c.part_splits, nullptr, c.d_w);
+                c.n, c.d_part, c.splits64, nullptr, c.d_w);
             k_nrm_inf<<<1, RED_THREADS, 0, c.stream>>>(n, c.d_w, c.d_scal, SC_AN);
         }
         double sc[SC_COUNT];
