@@ -22,12 +22,16 @@ namespace nrs {
 constexpr int GJ_NB = 64;
 
 // D^{-1} by Gauss-Jordan on [D | I] with partial pivoting (one CTA of 256
-// threads).  Thread (r, s) = (tid / 4, tid % 4) keeps columns s + 4 i
-// (i = 0..31) of augmented row r in registers; the column loop is unrolled so
-// every register index is static.  Rows are never moved: the pivot of column c
-// is the unused row of largest |value| (lowest row on ties), and logical row c
-// of D^{-1} is the right half of that physical row.  Padding rows/columns
-// (kb < 64) are identity.  Dinv is row-major 64 x 64; a zero pivot records info.
+// threads).  Thread (r, s) = (tid / 4, tid % 4) keeps, in registers, row r of
+// the augmented matrix restricted to columns s + 4 i: the left half in L[16]
+// and the right half in Rr[16].  Column c = 4 cc + s' is owned by slot s' and
+// sits in L[0]: after each group of four columns the finished left columns
+// are shifted out (L[i] <- L[i+1]), so every register index is static while
+// only four column steps are unrolled (the instruction footprint stays small).
+// Rows are never moved: the pivot of column c is the unused row of largest
+// |value| (lowest row on ties), and logical row c of D^{-1} is the right half
+// of that physical row.  Padding rows/columns (kb < 64) are identity.  Dinv
+// is row-major 64 x 64; a zero pivot records info.
 __global__ void __launch_bounds__(256)
     k_gj_diag(int64_t n, const float *__restrict__ M, int64_t lda, int64_t k0,
               float *__restrict__ Dinv, int32_t *__restrict__ info)
@@ -37,68 +41,81 @@ __global__ void __launch_bounds__(256)
     __shared__ float prow[2 * NB];
     __shared__ int used[NB];
     __shared__ int pos[NB];
-    __shared__ int s_piv;
+    __shared__ int s_piv[2];
     const int tid = threadIdx.x;
     const int r = tid >> 2, s = tid & 3;
     const int kb = (int)min((int64_t)NB, n - k0);
-    float own[32];
+    float L[16], Rr[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         const int j = s + 4 * i;
-        own[i] = (r < kb && j < kb) ? M[(k0 + r) + (k0 + j) * lda] : (r == j ? 1.0f : 0.0f);
-        own[16 + i] = (r == j) ? 1.0f : 0.0f;
+        L[i] = (r < kb && j < kb) ? M[(k0 + r) + (k0 + j) * lda] : (r == j ? 1.0f : 0.0f);
+        Rr[i] = (r == j) ? 1.0f : 0.0f;
     }
     if (tid < NB) used[tid] = 0;
     __syncthreads();
+    for (int cc = 0; cc < NB / 4; ++cc) {
 #pragma unroll
-    for (int c = 0; c < NB; ++c) {
-        if (s == (c & 3)) colc[c & 1][r] = own[c >> 2];
-        __syncthreads();
-        if (tid < 32) {
-            float v0 = used[tid] ? -1.0f : fabsf(colc[c & 1][tid]);
-            float v1 = used[tid + 32] ? -1.0f : fabsf(colc[c & 1][tid + 32]);
-            int b = tid;
-            float bv = v0;
-            if (v1 > bv) {
-                bv = v1;
-                b = tid + 32;
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                const int ob = __shfl_xor_sync(0xffffffffu, b, o);
-                if (ov > bv || (ov == bv && ob < b)) {
-                    bv = ov;
-                    b = ob;
+        for (int sp = 0; sp < 4; ++sp) {
+            const int c = 4 * cc + sp;
+            const int buf = sp & 1;
+            if (s == sp) colc[buf][r] = L[0];
+            __syncthreads();
+            if (tid < 32) {
+                const float v0 = used[tid] ? -1.0f : fabsf(colc[buf][tid]);
+                const float v1 = used[tid + 32] ? -1.0f : fabsf(colc[buf][tid + 32]);
+                int b = tid;
+                float bv = v0;
+                if (v1 > bv) {
+                    bv = v1;
+                    b = tid + 32;
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                    const int ob = __shfl_xor_sync(0xffffffffu, b, o);
+                    if (ov > bv || (ov == bv && ob < b)) {
+                        bv = ov;
+                        b = ob;
+                    }
+                }
+                if (tid == 0) {
+                    s_piv[buf] = b;
+                    used[b] = 1;
+                    pos[b] = c;
+                    if (colc[buf][b] == 0.0f && info) atomicCAS(info, 0, (int)(k0 + c + 1));
                 }
             }
-            if (tid == 0) {
-                s_piv = b;
-                used[b] = 1;
-                pos[b] = c;
-                if (colc[c & 1][b] == 0.0f && info) atomicCAS(info, 0, (int)(k0 + c + 1));
+            __syncthreads();
+            const int p = s_piv[buf];
+            const float inv = 1.0f / colc[buf][p];
+            if (r == p) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    L[i] *= inv;
+                    Rr[i] *= inv;
+                    prow[s + 4 * i] = L[i];
+                    prow[NB + s + 4 * i] = Rr[i];
+                }
+            }
+            __syncthreads();
+            if (r != p) {
+                const float f = colc[buf][r];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    L[i] -= f * prow[s + 4 * i];
+                    Rr[i] -= f * prow[NB + s + 4 * i];
+                }
             }
         }
-        __syncthreads();
-        const int p = s_piv;
-        const float inv = 1.0f / colc[c & 1][p];
-        if (r == p) {
+        // columns 4 cc .. 4 cc + 3 are finished: shift them out of L
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                own[i] *= inv;
-                prow[s + 4 * i] = own[i];
-            }
-        }
-        __syncthreads();
-        if (r != p) {
-            const float f = colc[c & 1][r];
-#pragma unroll
-            for (int i = 0; i < 32; ++i) own[i] -= f * prow[s + 4 * i];
-        }
+        for (int i = 0; i < 15; ++i) L[i] = L[i + 1];
+        L[15] = 0.0f;
+        __syncthreads();  // prow / colc reuse across groups
     }
-    __syncthreads();
     const int lr = pos[r];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) Dinv[lr * NB + s + 4 * i] = own[16 + i];
+    for (int i = 0; i < 16; ++i) Dinv[lr * NB + s + 4 * i] = Rr[i];
 }
 
 // Prep of step K.  grid.y = 0: R[:, j] = D^{-1} M[K, j] for one 64-column tile
