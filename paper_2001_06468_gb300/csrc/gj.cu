@@ -22,27 +22,32 @@ namespace nrs {
 constexpr int GJ_NB = 64;
 
 // D^{-1} by Gauss-Jordan on [D | I] with partial pivoting (one CTA of 256
-// threads).  Thread (r, s) = (tid / 4, tid % 4) keeps, in registers, row r of
-// the augmented matrix restricted to columns s + 4 i: the left half in L[16]
-// and the right half in Rr[16].  Column c = 4 cc + s' is owned by slot s' and
-// sits in L[0]: after each group of four columns the finished left columns
-// are shifted out (L[i] <- L[i+1]), so every register index is static while
-// only four column steps are unrolled (the instruction footprint stays small).
-// Rows are never moved: the pivot of column c is the unused row of largest
-// |value| (lowest row on ties), and logical row c of D^{-1} is the right half
-// of that physical row.  Padding rows/columns (kb < 64) are identity.  Dinv
-// is row-major 64 x 64; a zero pivot records info.
+// threads, one barrier per column).
+//  * Thread (r, s) = (tid / 4, tid % 4) keeps row r of the augmented matrix,
+//    columns s + 4 i, in registers: the left half in L[16], the right half in
+//    Rr[16].  After each group of four columns the finished left columns are
+//    shifted out (L[i] <- L[i+1]) so that every register index is static.
+//  * A shared mirror W of the matrix serves the pivot row to every thread.
+//  * Column c is published in colbuf[c & 1] by its owners during step c-1, so
+//    every warp finds the pivot of column c on its own (warp reductions): the
+//    unused row of largest |value|, lowest row on ties.
+//  * Rows are never moved or scaled during the sweep: step c subtracts
+//    (W[r][c] / W[p][c]) W[p] from every row r != p.  At the end the left half
+//    of pivot row p_c is pv_c e_c, so logical row c of D^{-1} is the right
+//    half of physical row p_c divided by pv_c.
+// Padding rows/columns (kb < 64) are identity.  Dinv is row-major 64 x 64; a
+// zero pivot records info.
 __global__ void __launch_bounds__(256)
     k_gj_diag(int64_t n, const float *__restrict__ M, int64_t lda, int64_t k0,
               float *__restrict__ Dinv, int32_t *__restrict__ info)
 {
     constexpr int NB = GJ_NB;
-    __shared__ float colc[2][NB];
-    __shared__ float prow[2 * NB];
-    __shared__ int used[NB];
+    constexpr int WP = 2 * NB + 4;  // mirror pitch: conflict-free row-slot writes
+    __shared__ float W[NB][WP];
+    __shared__ float colbuf[2][NB];
     __shared__ int pos[NB];
-    __shared__ int s_piv[2];
-    const int tid = threadIdx.x;
+    __shared__ float pivval[NB];
+    const int tid = threadIdx.x, lane = tid & 31;
     const int r = tid >> 2, s = tid & 3;
     const int kb = (int)min((int64_t)NB, n - k0);
     float L[16], Rr[16];
@@ -51,71 +56,59 @@ __global__ void __launch_bounds__(256)
         const int j = s + 4 * i;
         L[i] = (r < kb && j < kb) ? M[(k0 + r) + (k0 + j) * lda] : (r == j ? 1.0f : 0.0f);
         Rr[i] = (r == j) ? 1.0f : 0.0f;
+        W[r][j] = L[i];
+        W[r][NB + j] = Rr[i];
     }
-    if (tid < NB) used[tid] = 0;
+    if (s == 0) colbuf[0][r] = L[0];
+    unsigned long long used = 0ull;
     __syncthreads();
     for (int cc = 0; cc < NB / 4; ++cc) {
 #pragma unroll
         for (int sp = 0; sp < 4; ++sp) {
             const int c = 4 * cc + sp;
             const int buf = sp & 1;
-            if (s == sp) colc[buf][r] = L[0];
-            __syncthreads();
-            if (tid < 32) {
-                const float v0 = used[tid] ? -1.0f : fabsf(colc[buf][tid]);
-                const float v1 = used[tid + 32] ? -1.0f : fabsf(colc[buf][tid + 32]);
-                int b = tid;
-                float bv = v0;
-                if (v1 > bv) {
-                    bv = v1;
-                    b = tid + 32;
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                    const int ob = __shfl_xor_sync(0xffffffffu, b, o);
-                    if (ov > bv || (ov == bv && ob < b)) {
-                        bv = ov;
-                        b = ob;
-                    }
-                }
-                if (tid == 0) {
-                    s_piv[buf] = b;
-                    used[b] = 1;
-                    pos[b] = c;
-                    if (colc[buf][b] == 0.0f && info) atomicCAS(info, 0, (int)(k0 + c + 1));
-                }
+            // pivot: warp-wide max of |value| over unused rows, then lowest row
+            const float a0 = fabsf(colbuf[buf][lane]), a1 = fabsf(colbuf[buf][lane + 32]);
+            const bool u0 = (used >> lane) & 1ull, u1 = (used >> (lane + 32)) & 1ull;
+            const unsigned k0v = u0 ? 0u : (0x80000000u | __float_as_uint(a0));
+            const unsigned k1v = u1 ? 0u : (0x80000000u | __float_as_uint(a1));
+            const unsigned key = k0v >= k1v ? k0v : k1v;
+            const int row = k0v >= k1v ? lane : lane + 32;
+            const unsigned mx = __reduce_max_sync(0xffffffffu, key);
+            const int p = (int)__reduce_min_sync(0xffffffffu, key == mx ? (unsigned)row : 64u);
+            used |= 1ull << p;
+            const float pv = colbuf[buf][p];
+            if (tid == 0) {
+                pos[p] = c;
+                pivval[c] = pv;
+                if (pv == 0.0f && info) atomicCAS(info, 0, (int)(k0 + c + 1));
             }
-            __syncthreads();
-            const int p = s_piv[buf];
-            const float inv = 1.0f / colc[buf][p];
-            if (r == p) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    L[i] *= inv;
-                    Rr[i] *= inv;
-                    prow[s + 4 * i] = L[i];
-                    prow[NB + s + 4 * i] = Rr[i];
-                }
-            }
-            __syncthreads();
             if (r != p) {
-                const float f = colc[buf][r];
+                const float g = colbuf[buf][r] / pv;
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
-                    L[i] -= f * prow[s + 4 * i];
-                    Rr[i] -= f * prow[NB + s + 4 * i];
+                    L[i] -= g * W[p][s + 4 * (i + cc) < NB ? s + 4 * (i + cc) : 0];
+                    Rr[i] -= g * W[p][NB + s + 4 * i];
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    if (i + cc < 16) W[r][s + 4 * (i + cc)] = L[i];
+                    W[r][NB + s + 4 * i] = Rr[i];
                 }
             }
+            // publish column c + 1 for the next step
+            if (s == ((sp + 1) & 3)) colbuf[buf ^ 1][r] = (sp < 3) ? L[0] : L[1];
+            __syncthreads();
         }
         // columns 4 cc .. 4 cc + 3 are finished: shift them out of L
 #pragma unroll
         for (int i = 0; i < 15; ++i) L[i] = L[i + 1];
         L[15] = 0.0f;
-        __syncthreads();  // prow / colc reuse across groups
     }
     const int lr = pos[r];
+    const float d = 1.0f / pivval[lr];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) Dinv[lr * NB + s + 4 * i] = Rr[i];
+    for (int i = 0; i < 16; ++i) Dinv[lr * NB + s + 4 * i] = Rr[i] * d;
 }
 
 // Prep of step K.  grid.y = 0: R[:, j] = D^{-1} M[K, j] for one 64-column tile

@@ -1,16 +1,299 @@
-// tc_gemm.cu -- the rank-64 update M -= C R of the Gauss-Jordan inverse on the
-// tensor cores.  Placeholder until the tcgen05 kernel lands: reports that no
-// tensor-core kernel is available, so the factor entry point rejects the
-// TF32 and BF16 precisions instead of silently using another path.
+// tc_gemm.cu -- the rank-64 update M -= C R of the Gauss-Jordan inverse
+// (gj.cu) on the 5th-generation tensor cores: tcgen05.mma kind::tf32 with
+// FP32 accumulation in tensor memory.
+//
+// One CTA (4 warps) per 128 x 128 output tile:
+//   * thread 0 loads the A tile (128 rows of Cb, K = 64) and the B tile (128
+//     rows of Rt, K = 64) with four TMA copies (two 32-wide K blocks each,
+//     128-byte swizzle) onto one mbarrier,
+//   * thread 0 issues eight 128 x 128 x 8 MMAs (A, B K-major in shared
+//     memory, D in 128 TMEM columns) and commits them to a second mbarrier,
+//   * every warp reads its 32 TMEM lanes (rows) with tcgen05.ld and subtracts
+//     them from M (column-major: a warp writes 32 consecutive rows of a column).
+// Every wait is bounded: a wait that runs out sets ST_TIMEOUT, the kernel
+// skips the MMA / epilogue, waits once more (bounded) for its own copies and
+// frees its tensor memory before returning.
+#include <cuda.h>
+
 #include "nrs_internal.cuh"
 
 namespace nrs {
 
-bool tc_available() { return false; }
+namespace {
 
-bool launch_tc_gj_update(Ctx &, float *, int64_t, int64_t, const float *, const float *, int)
+constexpr int TC_BM = 128, TC_BN = 128, TC_KB = 32;  // K block = 32 fp32 = 128 bytes
+constexpr uint32_t TC_TILE_BYTES = TC_BM * TC_KB * 4;  // 16 KB per K block
+constexpr uint32_t TC_LOAD_BYTES = 4 * TC_TILE_BYTES;  // A and B, two K blocks each
+constexpr int TC_SMEM = 4 * TC_TILE_BYTES + 1024;      // + alignment slack
+constexpr long long kMbarSpin = 1LL << 22;
+
+// Instruction descriptor of tcgen05.mma kind::tf32: D = F32 (bits 4-5 = 1),
+// A = B = TF32 (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+constexpr uint32_t idesc_tf32(int M, int N)
 {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor, K-major operand with 128-byte swizzle as
+// written by TMA: start address >> 4 (bits 0-13), leading byte offset 16 B
+// (unused for swizzled K-major), stride byte offset 1024 B between 8-row
+// groups (bits 32-45), descriptor version 1 (bit 46), SWIZZLE_128B (bits 61-63 = 2).
+__device__ __forceinline__ uint64_t desc_sw128_kmajor(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)2u << 61;
+    return d;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase)
+{
+    for (long long i = 0; i < kMbarSpin; ++i)
+        if (mbar_try_wait(bar, phase)) return true;
     return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x, int y,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+          "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gj_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   int64_t n, float *__restrict__ M, int64_t lda, int32_t *status)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t bar_load, bar_mma;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_ok;
+    uint8_t *base = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint8_t *sA = base;                      // [2 K blocks][128 rows][128 bytes]
+    uint8_t *sB = base + 2 * TC_TILE_BYTES;  // same for B
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row0 = (int64_t)blockIdx.x * TC_BM, col0 = (int64_t)blockIdx.y * TC_BN;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar_load, 1);
+        mbar_init(&bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_ok = 1;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_slot)),
+                     "r"(TC_BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bar_load, TC_LOAD_BYTES);
+        tma_load_2d(sA, &tmA, 0, (int)row0, &bar_load);
+        tma_load_2d(sA + TC_TILE_BYTES, &tmA, TC_KB, (int)row0, &bar_load);
+        tma_load_2d(sB, &tmB, 0, (int)col0, &bar_load);
+        tma_load_2d(sB + TC_TILE_BYTES, &tmB, TC_KB, (int)col0, &bar_load);
+        if (mbar_wait(&bar_load, 0)) {
+            tc_fence_after();
+            constexpr uint32_t idesc = idesc_tf32(TC_BM, TC_BN);
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const uint32_t kofs = (uint32_t)(kk >> 2) * TC_TILE_BYTES + (uint32_t)(kk & 3) * 32u;
+                mma_tf32(tmem, desc_sw128_kmajor(smem_u32(sA) + kofs),
+                         desc_sw128_kmajor(smem_u32(sB) + kofs), idesc, kk > 0 ? 1u : 0u);
+            }
+            mma_commit(&bar_mma);
+        } else {
+            atomicOr(status, ST_TIMEOUT);
+            s_ok = 0;
+            mbar_wait(&bar_load, 0);  // bounded second wait for the copies in flight
+        }
+    }
+    __syncthreads();
+    bool ok = s_ok != 0;
+    if (ok && !mbar_wait(&bar_mma, 0)) {
+        atomicOr(status, ST_TIMEOUT);
+        ok = false;
+    }
+    tc_fence_after();
+    if (ok) {
+        const int64_t row = row0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int chunk = 0; chunk < TC_BN / 32; ++chunk) {
+            uint32_t v[32];
+            tmem_ld_32cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(chunk * 32), v);
+            if (row < n) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int64_t col = col0 + chunk * 32 + j;
+                    if (col < n) M[row + col * lda] -= __uint_as_float(v[j]);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN)
+                     : "memory");
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2-D map over a row-major [rows][64] FP32 panel, boxes of 32 x 128 with
+// 128-byte swizzle; rows >= `rows` read as zero.
+bool make_panel_map(CUtensorMap *tm, const float *ptr, int64_t rows)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {64, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {64 * sizeof(float)};
+    cuuint32_t box[2] = {TC_KB, TC_BM};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct TcMaps {
+    const float *cb = nullptr, *rt = nullptr;
+    int64_t rows = 0;
+    CUtensorMap a, b;
+    bool ok = false;
+};
+
+}  // namespace
+
+bool tc_available()
+{
+    int dev = 0, major = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess)
+        return false;
+    return major >= 10 && encode_fn() != nullptr;
+}
+
+bool launch_tc_gj_update(Ctx &c, float *M, int64_t lda, int64_t k0, const float *Cb,
+                         const float *Rt, int prec)
+{
+    (void)k0;
+    if (prec != NRS_TF32) return false;
+    static TcMaps maps;  // rebuilt when the workspaces change
+    if (!maps.ok || maps.cb != Cb || maps.rt != Rt || maps.rows != c.n) {
+        maps.ok = make_panel_map(&maps.a, Cb, c.n) && make_panel_map(&maps.b, Rt, c.n);
+        maps.cb = Cb;
+        maps.rt = Rt;
+        maps.rows = c.n;
+        if (!maps.ok) return false;
+        cudaFuncSetAttribute(k_tc_gj_update, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    }
+    dim3 grid((unsigned)ceil_div(c.n, TC_BM), (unsigned)ceil_div(c.n, TC_BN));
+    k_tc_gj_update<<<grid, 128, TC_SMEM, c.stream>>>(maps.a, maps.b, c.n, M, lda, c.d_status);
+    return true;
 }
 
 }  // namespace nrs
