@@ -200,6 +200,17 @@ nrs_status nrs_solve(nrs_ctx *ctx, const double *b, double *x, int32_t nrhs, con
 nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *s_half, double dt,
                     double *sol, nrs_step_report *report);
 
+/* The rank-64 update of the Gauss-Jordan inverse on its own (the kernel that
+ * nrs_factor runs once per 64-column block):
+ *   M[i, j] -= sum_{c < 64} C[i*64 + c] * Rt[j*64 + c]      for 0 <= i, j < n,
+ * M column-major (device, lda >= n), C and Rt row-major n x 64 (device, 16-byte
+ * aligned).  prec = NRS_FP32 runs it on the CUDA cores, NRS_TF32 on the tensor
+ * cores (tcgen05, TF32 operands, FP32 accumulation).  Enqueued on the context's
+ * stream.  NRS_EINVAL for bad sizes, misaligned panels or a precision without
+ * a kernel on this device. */
+nrs_status nrs_rank64_update(nrs_ctx *ctx, float *M, int64_t lda, int64_t n, const float *C,
+                             const float *Rt, int32_t prec);
+
 /* Wait for the context's stream and return the device status word. */
 nrs_status nrs_sync(nrs_ctx *ctx);
 

@@ -539,6 +539,26 @@ nrs_status nrs_get_timing(nrs_ctx *ctx, double *ms, int64_t *spans, int64_t *lau
     return NRS_OK;
 }
 
+nrs_status nrs_rank64_update(nrs_ctx *ctx, float *M, int64_t lda, int64_t n, const float *C,
+                             const float *Rt, int32_t prec)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !M || !C || !Rt || n <= 0 || lda < n || n > (1LL << 31))
+        return fail(c, NRS_EINVAL, "nrs_rank64_update: bad argument");
+    if ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(Rt)) & 15u)
+        return fail(c, NRS_EINVAL, "nrs_rank64_update: panels must be 16-byte aligned");
+    if (prec == NRS_FP32) {
+        nrs::launch_simt_rank64(*c, M, lda, n, C, Rt);
+    } else if (prec == NRS_TF32) {
+        if (!nrs::tc_available() || !nrs::launch_tc_rank64(*c, M, lda, n, C, Rt, prec))
+            return fail(c, NRS_EINVAL, "nrs_rank64_update: no tensor-core kernel on this device");
+    } else {
+        return fail(c, NRS_EINVAL, "nrs_rank64_update: precision must be NRS_FP32 or NRS_TF32");
+    }
+    CK(cudaGetLastError());
+    return NRS_OK;
+}
+
 nrs_status nrs_sync(nrs_ctx *ctx)
 {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);

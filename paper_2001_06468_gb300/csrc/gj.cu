@@ -286,6 +286,14 @@ __global__ void __launch_bounds__(256)
 bool launch_tc_gj_update(Ctx &c, float *M, int64_t lda, int64_t k0, const float *Cb,
                          const float *Rt, int prec);
 
+void launch_simt_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb, const float *Rt)
+{
+    const unsigned g = (unsigned)ceil_div(n, GJ_NB);
+    // k0 = -GJ_NB: no tile is skipped
+    k_gj_update_simt<<<dim3(g, g), 256, 0, c.stream>>>(n, M, lda, -GJ_NB, Cb, Rt);
+    c.launches += 1;
+}
+
 int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
 {
     const int64_t n = c.n;

@@ -75,6 +75,9 @@ int run_lu_fp64(Ctx &c, double *A, int64_t lda);
 int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec);
 
 bool tc_available();
+bool launch_tc_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb, const float *Rt,
+                      int prec);
+void launch_simt_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb, const float *Rt);
 
 // ---- solve (solve.cu) ------------------------------------------------------
 nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0,

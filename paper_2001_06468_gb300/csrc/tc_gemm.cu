@@ -1,15 +1,19 @@
 // tc_gemm.cu -- the rank-64 update M -= C R of the Gauss-Jordan inverse
 // (gj.cu) on the 5th-generation tensor cores: tcgen05.mma kind::tf32 with
-// FP32 accumulation in tensor memory.
+// FP32 accumulation in tensor memory, in split precision (3xTF32: every
+// operand x = hi + lo, products hi*hi + hi*lo + lo*hi), which keeps FP32
+// accuracy.  A single TF32 pass loses too much in the rigid-body Schur
+// complement of the bordered system and can leave a useless preconditioner.
 //
-// One CTA (4 warps) per 128 x 128 output tile:
-//   * thread 0 loads the A tile (128 rows of Cb, K = 64) and the B tile (128
-//     rows of Rt, K = 64) with four TMA copies (two 32-wide K blocks each,
-//     128-byte swizzle) onto one mbarrier,
-//   * thread 0 issues eight 128 x 128 x 8 MMAs (A, B K-major in shared
-//     memory, D in 128 TMEM columns) and commits them to a second mbarrier,
-//   * every warp reads its 32 TMEM lanes (rows) with tcgen05.ld and subtracts
-//     them from M (column-major: a warp writes 32 consecutive rows of a column).
+// One CTA (4 warps) per 128 x 128 output tile; for each of the two 32-wide
+// K blocks:
+//   * thread 0 loads the A tile (128 rows of Cb) and the B tile (128 rows of
+//     Rt) with TMA (128-byte swizzle) onto an mbarrier,
+//   * all threads split both tiles in shared memory into hi and lo parts,
+//   * thread 0 issues 4 x 3 MMAs of 128 x 128 x 8 (A, B K-major in shared
+//     memory, D in 128 TMEM columns) and commits them to an mbarrier;
+// then every warp reads its 32 TMEM lanes (rows) with tcgen05.ld and
+// subtracts them from M (column-major: a warp writes 32 consecutive rows).
 // Every wait is bounded: a wait that runs out sets ST_TIMEOUT, the kernel
 // skips the MMA / epilogue, waits once more (bounded) for its own copies and
 // frees its tensor memory before returning.
@@ -23,8 +27,7 @@ namespace {
 
 constexpr int TC_BM = 128, TC_BN = 128, TC_KB = 32;  // K block = 32 fp32 = 128 bytes
 constexpr uint32_t TC_TILE_BYTES = TC_BM * TC_KB * 4;  // 16 KB per K block
-constexpr uint32_t TC_LOAD_BYTES = 4 * TC_TILE_BYTES;  // A and B, two K blocks each
-constexpr int TC_SMEM = 4 * TC_TILE_BYTES + 1024;      // + alignment slack
+constexpr int TC_SMEM = 4 * TC_TILE_BYTES + 1024;      // A, B, A lo, B lo + alignment slack
 constexpr long long kMbarSpin = 1LL << 22;
 
 // Instruction descriptor of tcgen05.mma kind::tf32: D = F32 (bits 4-5 = 1),
@@ -136,24 +139,40 @@ __device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, uint32_t (&v)[32]
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Split x into hi = x rounded to TF32 (cvt.rna.tf32.f32) and lo = x - hi
+// (exact in FP32).  hi * hi + hi * lo + lo * hi reproduces x * y to about
+// 2^-21 relative: the dropped lo * lo term and the TF32 reading of lo.
+__device__ __forceinline__ void split_tf32(float x, float &hi, float &lo)
+{
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    hi = __uint_as_float(h);
+    lo = x - hi;
+}
+
 __global__ void __launch_bounds__(128, 1)
     k_tc_gj_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    int64_t n, float *__restrict__ M, int64_t lda, int32_t *status)
 {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t bar_load, bar_mma;
+    __shared__ uint64_t bar_load[2], bar_mma[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int s_ok;
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    uint8_t *sA = base;                      // [2 K blocks][128 rows][128 bytes]
-    uint8_t *sB = base + 2 * TC_TILE_BYTES;  // same for B
+    // one 32-wide K block at a time: A (hi after the split), B (hi), A lo, B lo
+    float *sA = reinterpret_cast<float *>(base);
+    float *sB = reinterpret_cast<float *>(base + TC_TILE_BYTES);
+    float *sAl = reinterpret_cast<float *>(base + 2 * TC_TILE_BYTES);
+    float *sBl = reinterpret_cast<float *>(base + 3 * TC_TILE_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row0 = (int64_t)blockIdx.x * TC_BM, col0 = (int64_t)blockIdx.y * TC_BN;
 
     if (threadIdx.x == 0) {
-        mbar_init(&bar_load, 1);
-        mbar_init(&bar_mma, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bar_load[i], 1);
+            mbar_init(&bar_mma[i], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_ok = 1;
     }
@@ -168,34 +187,70 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
+    constexpr uint32_t idesc = idesc_tf32(TC_BM, TC_BN);
+    constexpr int kElems = TC_BM * TC_KB;  // floats per tile
 
-    if (threadIdx.x == 0) {
-        mbar_expect_tx(&bar_load, TC_LOAD_BYTES);
-        tma_load_2d(sA, &tmA, 0, (int)row0, &bar_load);
-        tma_load_2d(sA + TC_TILE_BYTES, &tmA, TC_KB, (int)row0, &bar_load);
-        tma_load_2d(sB, &tmB, 0, (int)col0, &bar_load);
-        tma_load_2d(sB + TC_TILE_BYTES, &tmB, TC_KB, (int)col0, &bar_load);
-        if (mbar_wait(&bar_load, 0)) {
-            tc_fence_after();
-            constexpr uint32_t idesc = idesc_tf32(TC_BM, TC_BN);
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                const uint32_t kofs = (uint32_t)(kk >> 2) * TC_TILE_BYTES + (uint32_t)(kk & 3) * 32u;
-                mma_tf32(tmem, desc_sw128_kmajor(smem_u32(sA) + kofs),
-                         desc_sw128_kmajor(smem_u32(sB) + kofs), idesc, kk > 0 ? 1u : 0u);
+    for (int kb = 0; kb < 2; ++kb) {
+        if (threadIdx.x == 0) {
+            // the previous K block's MMAs must have finished reading shared memory
+            if (kb == 1 && s_ok && !mbar_wait(&bar_mma[0], 0)) {
+                atomicOr(status, ST_TIMEOUT);
+                s_ok = 0;
             }
-            mma_commit(&bar_mma);
-        } else {
+            if (s_ok) {
+                mbar_expect_tx(&bar_load[kb], 2 * TC_TILE_BYTES);
+                tma_load_2d(sA, &tmA, kb * TC_KB, (int)row0, &bar_load[kb]);
+                tma_load_2d(sB, &tmB, kb * TC_KB, (int)col0, &bar_load[kb]);
+            }
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        if (!mbar_wait(&bar_load[kb], 0)) {
             atomicOr(status, ST_TIMEOUT);
             s_ok = 0;
-            mbar_wait(&bar_load, 0);  // bounded second wait for the copies in flight
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        // split both tiles in place (element-wise: the swizzled layout is kept)
+        for (int i = threadIdx.x; i < kElems; i += 128) {
+            float h, l;
+            split_tf32(sA[i], h, l);
+            sA[i] = h;
+            sAl[i] = l;
+            split_tf32(sB[i], h, l);
+            sB[i] = h;
+            sBl[i] = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t kofs = (uint32_t)kk * 32u;
+                const uint64_t ah = desc_sw128_kmajor(smem_u32(sA) + kofs);
+                const uint64_t bh = desc_sw128_kmajor(smem_u32(sB) + kofs);
+                const uint64_t al = desc_sw128_kmajor(smem_u32(sAl) + kofs);
+                const uint64_t bl = desc_sw128_kmajor(smem_u32(sBl) + kofs);
+                mma_tf32(tmem, al, bh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                mma_tf32(tmem, ah, bl, idesc, 1u);
+                mma_tf32(tmem, ah, bh, idesc, 1u);
+            }
+            mma_commit(&bar_mma[kb]);
         }
     }
     __syncthreads();
     bool ok = s_ok != 0;
-    if (ok && !mbar_wait(&bar_mma, 0)) {
+    if (ok && !mbar_wait(&bar_mma[1], 0)) {
         atomicOr(status, ST_TIMEOUT);
         ok = false;
+    }
+    if (!ok && threadIdx.x == 0) {
+        // bounded waits for whatever copies or MMAs may still be in flight
+        mbar_wait(&bar_load[0], 0);
+        mbar_wait(&bar_load[1], 0);
+        mbar_wait(&bar_mma[0], 0);
+        mbar_wait(&bar_mma[1], 0);
     }
     tc_fence_after();
     if (ok) {
@@ -277,23 +332,28 @@ bool tc_available()
     return major >= 10 && encode_fn() != nullptr;
 }
 
+bool launch_tc_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb, const float *Rt,
+                      int prec)
+{
+    if (prec != NRS_TF32) return false;
+    CUtensorMap a, b;
+    if (!make_panel_map(&a, Cb, n) || !make_panel_map(&b, Rt, n)) return false;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_tc_gj_update, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        attr = true;
+    }
+    dim3 grid((unsigned)ceil_div(n, TC_BM), (unsigned)ceil_div(n, TC_BN));
+    k_tc_gj_update<<<grid, 128, TC_SMEM, c.stream>>>(a, b, n, M, lda, c.d_status);
+    c.launches += 1;
+    return true;
+}
+
 bool launch_tc_gj_update(Ctx &c, float *M, int64_t lda, int64_t k0, const float *Cb,
                          const float *Rt, int prec)
 {
     (void)k0;
-    if (prec != NRS_TF32) return false;
-    static TcMaps maps;  // rebuilt when the workspaces change
-    if (!maps.ok || maps.cb != Cb || maps.rt != Rt || maps.rows != c.n) {
-        maps.ok = make_panel_map(&maps.a, Cb, c.n) && make_panel_map(&maps.b, Rt, c.n);
-        maps.cb = Cb;
-        maps.rt = Rt;
-        maps.rows = c.n;
-        if (!maps.ok) return false;
-        cudaFuncSetAttribute(k_tc_gj_update, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    }
-    dim3 grid((unsigned)ceil_div(c.n, TC_BM), (unsigned)ceil_div(c.n, TC_BN));
-    k_tc_gj_update<<<grid, 128, TC_SMEM, c.stream>>>(maps.a, maps.b, c.n, M, lda, c.d_status);
-    return true;
+    return launch_tc_rank64(c, M, lda, c.n, Cb, Rt, prec);
 }
 
 }  // namespace nrs

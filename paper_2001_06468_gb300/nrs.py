@@ -35,7 +35,7 @@ FREE, PRESCRIBED, STATIC = 0, 1, 2
 EXPORTS = ["nrs_create", "nrs_destroy", "nrs_last_error", "nrs_sizes", "nrs_set_state",
            "nrs_get_state", "nrs_set_external", "nrs_kinematics", "nrs_nearest_build",
            "nrs_assemble", "nrs_factor", "nrs_solve", "nrs_step", "nrs_sync", "nrs_set_timing",
-           "nrs_get_timing"]
+           "nrs_get_timing", "nrs_rank64_update"]
 PHASES = ["kinematics", "nearest", "segments", "assemble", "border", "convert", "lu_panel",
           "lu_update", "trsv", "gemv", "krylov", "update"]
 
@@ -94,6 +94,8 @@ _sig = {
                                 _P, ctypes.POINTER(StepReport)]),
     "nrs_sync": (ctypes.c_int, [_P]),
     "nrs_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "nrs_rank64_update": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P,
+                                         ctypes.c_int32]),
     "nrs_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), _I64P, _I64P]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -279,6 +281,14 @@ class Context:
 
     def sync(self):
         return self._check(_lib.nrs_sync(self._h))
+
+    def rank64_update(self, Mt: torch.Tensor, C: torch.Tensor, Rt: torch.Tensor, prec: str = "tf32"):
+        """M -= C Rt^T in place; Mt is the (n_cols, lda) storage of the
+        column-major M (Mt[j, i] = M[i, j]); C and Rt are (n, 64) float32."""
+        n = C.shape[0]
+        self._check(_lib.nrs_rank64_update(self._h, _ptr(Mt, torch.float32), Mt.shape[1], n,
+                                           _ptr(C, torch.float32), _ptr(Rt, torch.float32),
+                                           PREC[prec]))
 
     def set_timing(self, enable: bool = True):
         self._check(_lib.nrs_set_timing(self._h, int(bool(enable))))

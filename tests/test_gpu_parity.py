@@ -111,7 +111,7 @@ def test_nearest_ties_on_nested_cube_spheres(N):
     assert np.array_equal(nn.cpu().numpy(), nn_or)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "tf32"])
 def test_sphere_resistance_solve(N, prec):
     pr = g.sphere_config()
     ctx, sh, Y, dev = _setup(N, pr, prec=prec)
@@ -125,7 +125,8 @@ def test_sphere_resistance_solve(N, prec):
 
 
 @pytest.mark.parametrize("name,prec", [("swimmer_small", "fp32"), ("swimmer", "fp32"),
-                                       ("swimmer", "fp64"), ("sperm2", "fp32")])
+                                       ("swimmer", "fp64"), ("swimmer", "tf32"), ("sperm2", "fp32"),
+                                       ("sperm2", "tf32")])
 def test_swimming_solve_matches_oracle(N, name, prec):
     pr = PROBLEMS[name]()
     ctx, sh, Y, dev = _setup(N, pr, t=0.25, prec=prec)
@@ -154,11 +155,12 @@ def test_warm_start_and_multiple_rhs(N):
     assert _rel(X3.cpu().numpy(), X2[0].cpu().numpy()) < 1e-13
 
 
-@pytest.mark.parametrize("name", ["swimmer_small", "sperm2"])
-def test_rk2_step_matches_oracle(N, name):
+@pytest.mark.parametrize("name,prec", [("swimmer_small", "fp32"), ("sperm2", "fp32"),
+                                       ("swimmer", "tf32")])
+def test_rk2_step_matches_oracle(N, name, prec):
     pr = PROBLEMS[name]()
     t, dt = 0.05, 0.01
-    ctx, sh, Y, dev0 = _setup(N, pr, t=t)
+    ctx, sh, Y, dev0 = _setup(N, pr, t=t, prec=prec)
     devh = N.shapes_to_device(g.pack_shapes(pr, t + 0.5 * dt))
     s0, shf = N.Context.shapes(*dev0), N.Context.shapes(*devh)
     sol = torch.empty(2 * pr.n, dtype=torch.float64, device="cuda")
@@ -172,13 +174,14 @@ def test_rk2_step_matches_oracle(N, name):
     assert np.allclose(Yg["B"], Yo["B"], rtol=0, atol=1e-13)
 
 
-def test_two_steps_keep_rigid_nearest_map(N):
-    # the wall's nearest-neighbour map is computed once and reused
-    pr = PROBLEMS["sperm2"]()
+@pytest.mark.parametrize("name,prec", [("sperm2", "fp32"), ("swimmer", "tf32")])
+def test_consecutive_steps_match_oracle(N, name, prec):
+    # several steps in a row (for the channel: the wall's map is computed once and kept)
+    pr = PROBLEMS[name]()
     dt = 0.01
-    ctx, sh, Y, dev = _setup(N, pr, t=0.0)
+    ctx, sh, Y, dev = _setup(N, pr, t=0.0, prec=prec)
     Yo = Y
-    for k in range(2):
+    for k in range(3):
         t = k * dt
         d0 = N.shapes_to_device(g.pack_shapes(pr, t))
         dh = N.shapes_to_device(g.pack_shapes(pr, t + 0.5 * dt))
