@@ -22,15 +22,15 @@ namespace nrs {
 constexpr int GJ_NB = 64;
 
 // D^{-1} by Gauss-Jordan on [D | I] with partial pivoting (one CTA of 256
-// threads, one barrier per column).
+// threads, two barriers per column).
 //  * Thread (r, s) = (tid / 4, tid % 4) keeps row r of the augmented matrix,
 //    columns s + 4 i, in registers: the left half in L[16], the right half in
 //    Rr[16].  After each group of four columns the finished left columns are
 //    shifted out (L[i] <- L[i+1]) so that every register index is static.
-//  * A shared mirror W of the matrix serves the pivot row to every thread.
-//  * Column c is published in colbuf[c & 1] by its owners during step c-1, so
-//    every warp finds the pivot of column c on its own (warp reductions): the
-//    unused row of largest |value|, lowest row on ties.
+//  * Column c is published in colbuf[c & 1] by its owners during step c-1;
+//    every warp then finds the pivot on its own with warp reductions: the
+//    unused row of largest |value|, lowest row on ties.  Only the pivot row is
+//    copied to shared memory for the others.
 //  * Rows are never moved or scaled during the sweep: step c subtracts
 //    (W[r][c] / W[p][c]) W[p] from every row r != p.  At the end the left half
 //    of pivot row p_c is pv_c e_c, so logical row c of D^{-1} is the right
@@ -42,9 +42,8 @@ __global__ void __launch_bounds__(256)
               float *__restrict__ Dinv, int32_t *__restrict__ info)
 {
     constexpr int NB = GJ_NB;
-    constexpr int WP = 2 * NB + 4;  // mirror pitch: conflict-free row-slot writes
-    __shared__ float W[NB][WP];
     __shared__ float colbuf[2][NB];
+    __shared__ float prow[2 * NB];
     __shared__ int pos[NB];
     __shared__ float pivval[NB];
     const int tid = threadIdx.x, lane = tid & 31;
@@ -56,8 +55,6 @@ __global__ void __launch_bounds__(256)
         const int j = s + 4 * i;
         L[i] = (r < kb && j < kb) ? M[(k0 + r) + (k0 + j) * lda] : (r == j ? 1.0f : 0.0f);
         Rr[i] = (r == j) ? 1.0f : 0.0f;
-        W[r][j] = L[i];
-        W[r][NB + j] = Rr[i];
     }
     if (s == 0) colbuf[0][r] = L[0];
     unsigned long long used = 0ull;
@@ -67,7 +64,6 @@ __global__ void __launch_bounds__(256)
         for (int sp = 0; sp < 4; ++sp) {
             const int c = 4 * cc + sp;
             const int buf = sp & 1;
-            // pivot: warp-wide max of |value| over unused rows, then lowest row
             const float a0 = fabsf(colbuf[buf][lane]), a1 = fabsf(colbuf[buf][lane + 32]);
             const bool u0 = (used >> lane) & 1ull, u1 = (used >> (lane + 32)) & 1ull;
             const unsigned k0v = u0 ? 0u : (0x80000000u | __float_as_uint(a0));
@@ -83,17 +79,20 @@ __global__ void __launch_bounds__(256)
                 pivval[c] = pv;
                 if (pv == 0.0f && info) atomicCAS(info, 0, (int)(k0 + c + 1));
             }
+            if (r == p) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    prow[s + 4 * i] = L[i];
+                    prow[NB + s + 4 * i] = Rr[i];
+                }
+            }
+            __syncthreads();
             if (r != p) {
                 const float g = colbuf[buf][r] / pv;
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
-                    L[i] -= g * W[p][s + 4 * (i + cc) < NB ? s + 4 * (i + cc) : 0];
-                    Rr[i] -= g * W[p][NB + s + 4 * i];
-                }
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    if (i + cc < 16) W[r][s + 4 * (i + cc)] = L[i];
-                    W[r][NB + s + 4 * i] = Rr[i];
+                    L[i] -= g * prow[s + 4 * i];
+                    Rr[i] -= g * prow[NB + s + 4 * i];
                 }
             }
             // publish column c + 1 for the next step
@@ -129,9 +128,16 @@ __global__ void __launch_bounds__(256)
     const int nt = (int)min((int64_t)NB, n - t0);
     if (blockIdx.y == 1) {
         const bool in_k = (t0 == k0);
-        for (int idx = tid; idx < NB * NB; idx += 256) {
-            const int i = idx & 63, c = idx >> 6;
-            Ms[i][c] = (i < nt && c < kb && !in_k) ? M[(t0 + i) + (k0 + c) * lda] : 0.0f;
+        float v[16];  // all loads in flight before the first shared store
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int idx = tid + 256 * q, i = idx & 63, c = idx >> 6;
+            v[q] = (i < nt && c < kb && !in_k) ? M[(t0 + i) + (k0 + c) * lda] : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int idx = tid + 256 * q;
+            Ms[idx & 63][idx >> 6] = v[q];
         }
         __syncthreads();
         for (int idx = tid; idx < NB * NB; idx += 256) {
@@ -141,10 +147,20 @@ __global__ void __launch_bounds__(256)
         return;
     }
     const bool tile_is_k = (t0 == k0);
-    for (int idx = tid; idx < NB * NB; idx += 256) {
-        const int a = idx & 63, b = idx >> 6;
-        Ds[b][a] = Dinv[b * NB + a];
-        Ms[a][b] = (a < kb && b < nt) ? M[(k0 + a) + (t0 + b) * lda] : 0.0f;
+    {
+        float dv[16], mv[16];  // all loads in flight before the first shared store
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
+            dv[q] = Dinv[b * NB + a];
+            mv[q] = (a < kb && b < nt) ? M[(k0 + a) + (t0 + b) * lda] : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
+            Ds[b][a] = dv[q];
+            Ms[a][b] = mv[q];
+        }
     }
     __syncthreads();
     // thread computes R[r, t0 + c] for r = tr + 16 rr, c = tc + 16 cc (4 x 4)
@@ -188,12 +204,19 @@ __global__ void __launch_bounds__(256)
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     float acc[4][4] = {};
     for (int kk = 0; kk < NB; kk += BK) {
-        for (int e = threadIdx.x; e < BK * BM; e += 256) {
-            const int k = e % BK, i = e / BK;
-            const int64_t gi = row0 + i;
-            As[k][i] = gi < n ? Cb[gi * NB + kk + k] : 0.0f;
-            const int64_t gj = col0 + i;
-            Bs[k][i] = gj < n ? Rt[gj * NB + kk + k] : 0.0f;
+        float av[4], bv[4];  // all loads in flight before the shared stores
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = threadIdx.x + 256 * q, k = e % BK, i = e / BK;
+            const int64_t gi = row0 + i, gj = col0 + i;
+            av[q] = gi < n ? Cb[gi * NB + kk + k] : 0.0f;
+            bv[q] = gj < n ? Rt[gj * NB + kk + k] : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = threadIdx.x + 256 * q, k = e % BK, i = e / BK;
+            As[k][i] = av[q];
+            Bs[k][i] = bv[q];
         }
         __syncthreads();
 #pragma unroll
@@ -240,18 +263,35 @@ __global__ void __launch_bounds__(256)
     const int nt = (int)min((int64_t)NB, n - t0);
     if (blockIdx.y == 0) {
         const bool tile_is_k = (t0 == k0);
-        for (int idx = tid; idx < NB * NB; idx += 256) {
-            const int rr = idx & 63, c = idx >> 6;
-            if (rr >= kb || c >= nt) continue;
-            M[(k0 + rr) + (t0 + c) * lda] = tile_is_k ? Dinv[rr * NB + c] : Rt[(t0 + c) * NB + rr];
+        float v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int idx = tid + 256 * q, rr = idx & 63, c = idx >> 6;
+            const bool in = rr < kb && c < nt;
+            v[q] = !in ? 0.0f : (tile_is_k ? Dinv[rr * NB + c] : Rt[(t0 + c) * NB + rr]);
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int idx = tid + 256 * q, rr = idx & 63, c = idx >> 6;
+            if (rr < kb && c < nt) M[(k0 + rr) + (t0 + c) * lda] = v[q];
         }
         return;
     }
     if (t0 == k0) return;
-    for (int idx = tid; idx < NB * NB; idx += 256) {
-        const int a = idx & 63, b = idx >> 6;
-        Ds[b][a] = Dinv[b * NB + a];
-        Cs[b][a] = b < nt ? Cb[(t0 + b) * NB + a] : 0.0f;
+    {
+        float dv[16], cv[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
+            dv[q] = Dinv[b * NB + a];
+            cv[q] = b < nt ? Cb[(t0 + b) * NB + a] : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
+            Ds[b][a] = dv[q];
+            Cs[b][a] = cv[q];
+        }
     }
     __syncthreads();
     // thread computes out[i][c] = -sum_t C[i][t] Dinv[t][c], i = tr + 16 x, c = tc + 16 y

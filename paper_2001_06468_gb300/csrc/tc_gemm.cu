@@ -260,11 +260,14 @@ __global__ void __launch_bounds__(128, 1)
             uint32_t v[32];
             tmem_ld_32cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(chunk * 32), v);
             if (row < n) {
+                float old[32];  // all 32 loads in flight before the stores
+                float *p = M + row + (col0 + chunk * 32) * lda;
+                const int64_t ncol = n - (col0 + chunk * 32);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int64_t col = col0 + chunk * 32 + j;
-                    if (col < n) M[row + col * lda] -= __uint_as_float(v[j]);
-                }
+                for (int j = 0; j < 32; ++j) old[j] = j < ncol ? p[j * lda] : 0.0f;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (j < ncol) p[j * lda] = old[j] - __uint_as_float(v[j]);
             }
         }
     }
