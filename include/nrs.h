@@ -214,6 +214,40 @@ nrs_status nrs_rank64_update(nrs_ctx *ctx, float *M, int64_t lda, int64_t n, con
 /* Wait for the context's stream and return the device status word. */
 nrs_status nrs_sync(nrs_ctx *ctx);
 
+/* Largest problem nrs_nearest_build_static accepts. */
+#define NRS_STATIC_MAX_N 65536       /* force points      */
+#define NRS_STATIC_MAX_Q 1048576     /* quadrature points */
+#define NRS_STATIC_MAX_BODIES 1024   /* bodies            */
+
+/* Nearest neighbours and segments of nu, as nrs_nearest_build computes them
+ * (same kernels, same bit-exact result), for callers that cannot allocate
+ * device memory: code running inside a memory pool or arena it does not own,
+ * time-critical loops where cudaMalloc would synchronise the device,
+ * processes that reserved all device memory up front.  The paper has no
+ * counterpart: this is a deployment variant of nrs_nearest_build.
+ *
+ * No context, no cudaMalloc/cudaFree, no allocating library call.  The
+ * caller passes the inputs and outputs; the scratch (segment counters, the
+ * block task table, the body offsets, a status word; about 0.4 MB) lives in
+ * file-scope device arrays of fixed size that every GPU loading the library
+ * holds until the process exits.
+ *   x [N*4], Xw [Q*4]      device, as for nrs_nearest_build (body frame for
+ *                          global == 0, lab frame for global != 0)
+ *   nbodies, n_off, q_off  host offsets as in nrs_problem_desc
+ *   nn [Q], seg_ptr [N+1], perm [Q]   device outputs
+ *   stream                 cudaStream_t (NULL = legacy default stream)
+ * Returns NRS_EINVAL for sizes above NRS_STATIC_MAX_N / _Q / _BODIES or bad
+ * offsets, before any work is enqueued.  The first call on a device looks up
+ * the scratch's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call shares
+ * the same scratch, which keeps the last call's contents (each call clears
+ * what must start at zero): calls that overlap on the GPU -- on different
+ * streams, or from several threads -- race and must be serialised by the
+ * caller. */
+nrs_status nrs_nearest_build_static(const double *x, const double *Xw, int32_t nbodies,
+                                    const int64_t *n_off, const int64_t *q_off, int32_t global,
+                                    int32_t *nn, int32_t *seg_ptr, int32_t *perm, void *stream);
+
 /* Phases of the step, as timed by nrs_get_timing. */
 enum {
     NRS_PH_KINEMATICS = 0, /* body frame -> lab frame, right-hand side          */

@@ -30,12 +30,14 @@ NRS_ESINGULAR, NRS_ENOCONV, NRS_ENONFINITE, NRS_ETIMEOUT = -4, -5, -6, -7
 STATUS_NAMES = {0: "NRS_OK", -1: "NRS_EINVAL", -2: "NRS_ENOMEM", -3: "NRS_ECUDA",
                 -4: "NRS_ESINGULAR", -5: "NRS_ENOCONV", -6: "NRS_ENONFINITE", -7: "NRS_ETIMEOUT"}
 PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+# largest sizes nrs_nearest_build_static accepts (NRS_STATIC_MAX_* in include/nrs.h)
+NRS_STATIC_LIMITS = {"N": 65536, "Q": 1048576, "bodies": 1024}
 FREE, PRESCRIBED, STATIC = 0, 1, 2
 
 EXPORTS = ["nrs_create", "nrs_destroy", "nrs_last_error", "nrs_sizes", "nrs_set_state",
            "nrs_get_state", "nrs_set_external", "nrs_kinematics", "nrs_nearest_build",
            "nrs_assemble", "nrs_factor", "nrs_solve", "nrs_step", "nrs_sync", "nrs_set_timing",
-           "nrs_get_timing", "nrs_rank64_update"]
+           "nrs_get_timing", "nrs_rank64_update", "nrs_nearest_build_static"]
 PHASES = ["kinematics", "nearest", "segments", "assemble", "border", "convert", "lu_panel",
           "lu_update", "trsv", "gemv", "krylov", "update"]
 
@@ -96,6 +98,8 @@ _sig = {
     "nrs_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
     "nrs_rank64_update": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P,
                                          ctypes.c_int32]),
+    "nrs_nearest_build_static": (ctypes.c_int, [_P, _P, ctypes.c_int32, _I64P, _I64P, ctypes.c_int32,
+                                                _P, _P, _P, _P]),
     "nrs_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), _I64P, _I64P]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -300,6 +304,32 @@ class Context:
         launches = ctypes.c_int64()
         self._check(_lib.nrs_get_timing(self._h, ms, spans, ctypes.byref(launches)))
         return {p: (ms[i], spans[i]) for i, p in enumerate(PHASES)}, launches.value
+
+
+def nearest_build_static(x: torch.Tensor, Xw: torch.Tensor, n_off, q_off, global_: bool = False,
+                         nn: Optional[torch.Tensor] = None, seg_ptr: Optional[torch.Tensor] = None,
+                         perm: Optional[torch.Tensor] = None,
+                         stream: Optional[torch.cuda.Stream] = None):
+    """nrs_nearest_build_static: the nearest-neighbour map and segments with
+    no device allocation inside the library (the outputs are the caller's;
+    pass preallocated tensors to allocate nothing at all).  Returns
+    (nn, seg_ptr, perm)."""
+    n_off = np.ascontiguousarray(n_off, dtype=np.int64)
+    q_off = np.ascontiguousarray(q_off, dtype=np.int64)
+    N, Q = int(n_off[-1]), int(q_off[-1])
+    dev = x.device
+    nn = nn if nn is not None else torch.empty(Q, dtype=torch.int32, device=dev)
+    seg_ptr = seg_ptr if seg_ptr is not None else torch.empty(N + 1, dtype=torch.int32, device=dev)
+    perm = perm if perm is not None else torch.empty(Q, dtype=torch.int32, device=dev)
+    st = stream or torch.cuda.current_stream()
+    rc = _lib.nrs_nearest_build_static(_ptr(x, torch.float64), _ptr(Xw, torch.float64),
+                                       len(n_off) - 1, _np_ptr(n_off, ctypes.c_int64),
+                                       _np_ptr(q_off, ctypes.c_int64), int(bool(global_)),
+                                       _ptr(nn, torch.int32), _ptr(seg_ptr, torch.int32),
+                                       _ptr(perm, torch.int32), ctypes.c_void_p(st.cuda_stream))
+    if rc != NRS_OK:
+        raise NrsError(rc, "nrs_nearest_build_static failed")
+    return nn, seg_ptr, perm
 
 
 def shapes_to_device(shapes: dict, device="cuda"):
