@@ -262,7 +262,9 @@ enum {
     NRS_PH_GEMV = 9,       /* FP64 residual / Arnoldi matrix-vector products    */
     NRS_PH_KRYLOV = 10,    /* orthogonalisation, Givens, updates, norms         */
     NRS_PH_UPDATE = 11,    /* explicit-midpoint state update                    */
-    NRS_NPHASE = 12
+    NRS_PH_LU_DIAG = 12,   /* next diagonal block: its update and inverse (timed on the
+                              factorisation's second stream, overlapping the others) */
+    NRS_NPHASE = 13
 };
 
 /* Enable (1) or disable (0) per-phase timing with CUDA events recorded on the

@@ -73,7 +73,7 @@ nrs_status alloc_all(Ctx *c)
         {(void **)&c->d_A32, sizeof(float) * lda * n},
         {(void **)&c->d_rowperm, sizeof(int32_t) * n},
         {(void **)&c->d_lperm, sizeof(int32_t) * 64},
-        {(void **)&c->d_gj_dinv, sizeof(float) * 64 * 64},
+        {(void **)&c->d_gj_dinv, sizeof(float) * 2 * 64 * 64},
         {(void **)&c->d_gj_rt, sizeof(float) * 64 * lda},
         {(void **)&c->d_gj_cb, sizeof(float) * 64 * lda},
         {(void **)&c->d_info, sizeof(int32_t)},
@@ -117,6 +117,11 @@ void free_all(Ctx *c)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     c->ev_pool.clear();
+    if (c->ev_prep) cudaEventDestroy(c->ev_prep);
+    if (c->ev_diag) cudaEventDestroy(c->ev_diag);
+    if (c->stream2) cudaStreamDestroy(c->stream2);
+    c->ev_prep = c->ev_diag = nullptr;
+    c->stream2 = nullptr;
 }
 
 bool is_prec(int p) { return p == NRS_FP64 || p == NRS_FP32 || p == NRS_TF32 || p == NRS_BF16; }
@@ -290,6 +295,9 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
     if (e == cudaSuccess && c->F) e = cudaMemset(c->d_ext, 0, sizeof(double) * 6 * c->F);
     if (e == cudaSuccess) e = cudaMemset(c->d_flags, 0, sizeof(int32_t) * nrs::ceil_div(c->n, 64));
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_prep, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_diag, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         free_all(c);
         delete c;
@@ -550,7 +558,7 @@ nrs_status nrs_rank64_update(nrs_ctx *ctx, float *M, int64_t lda, int64_t n, con
     if (prec == NRS_FP32) {
         nrs::launch_simt_rank64(*c, M, lda, n, C, Rt);
     } else if (prec == NRS_TF32) {
-        if (!nrs::tc_available() || !nrs::launch_tc_rank64(*c, M, lda, n, C, Rt, prec))
+        if (!nrs::tc_available() || !nrs::launch_tc_rank64(*c, M, lda, n, C, Rt, prec, -64))
             return fail(c, NRS_EINVAL, "nrs_rank64_update: no tensor-core kernel on this device");
     } else {
         return fail(c, NRS_EINVAL, "nrs_rank64_update: precision must be NRS_FP32 or NRS_TF32");

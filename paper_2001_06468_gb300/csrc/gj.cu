@@ -191,14 +191,15 @@ __global__ void __launch_bounds__(256)
 }
 
 // M[i, j] -= sum_c Cb[i,c] Rt[j,c] on the CUDA cores (64 x 64 tiles); tiles in
-// block row or column K are skipped (their update is zero by construction).
+// block row or column K are skipped (their update is zero by construction),
+// and so is the diagonal tile at skip0 (updated separately by the lookahead).
 __global__ void __launch_bounds__(256)
     k_gj_update_simt(int64_t n, float *__restrict__ M, int64_t lda, int64_t k0,
-                     const float *__restrict__ Cb, const float *__restrict__ Rt)
+                     const float *__restrict__ Cb, const float *__restrict__ Rt, int64_t skip0)
 {
     constexpr int NB = GJ_NB, BM = 64, BN = 64, BK = 16;
     const int64_t row0 = (int64_t)blockIdx.x * BM, col0 = (int64_t)blockIdx.y * BN;
-    if (row0 == k0 || col0 == k0) return;
+    if (row0 == k0 || col0 == k0 || (row0 == skip0 && col0 == skip0)) return;
     __shared__ float As[BK][BM + 4];
     __shared__ float Bs[BK][BN + 4];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -321,43 +322,120 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Lookahead: the rank-64 update of the next diagonal block only,
+// M[K1, K1] -= C[K1, :] R[:, K1] (one CTA), so that its inverse can be taken
+// while the rest of the update runs on the main stream.
+__global__ void __launch_bounds__(256)
+    k_gj_diag_update(int64_t n, float *__restrict__ M, int64_t lda, int64_t k1,
+                     const float *__restrict__ Cb, const float *__restrict__ Rt)
+{
+    constexpr int NB = GJ_NB;
+    __shared__ float Cs[NB][NB + 1];
+    __shared__ float Rs[NB][NB + 1];
+    const int tid = threadIdx.x;
+    const int kb = (int)min((int64_t)NB, n - k1);
+    {
+        float cv[16], rv[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
+            cv[q] = b < kb ? Cb[(k1 + b) * NB + a] : 0.0f;
+            rv[q] = b < kb ? Rt[(k1 + b) * NB + a] : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
+            Cs[b][a] = cv[q];
+            Rs[b][a] = rv[q];
+        }
+    }
+    __syncthreads();
+    const int tr = tid & 15, tc = tid >> 4;
+    float acc[4][4] = {};
+#pragma unroll 8
+    for (int t = 0; t < NB; ++t) {
+        float a[4], b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[q] = Cs[tr + 16 * q][t];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) b[q] = Rs[tc + 16 * q][t];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * b[y];
+    }
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+        const int j = tc + 16 * y;
+        if (j >= kb) continue;
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int i = tr + 16 * x;
+            if (i < kb) M[(k1 + i) + (k1 + j) * lda] -= acc[x][y];
+        }
+    }
+}
+
 // Tensor-core version of the update (tc_gemm.cu); false if not available for
 // this precision.
 bool launch_tc_gj_update(Ctx &c, float *M, int64_t lda, int64_t k0, const float *Cb,
-                         const float *Rt, int prec);
+                         const float *Rt, int prec, int64_t skip0);
 
 void launch_simt_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb, const float *Rt)
 {
     const unsigned g = (unsigned)ceil_div(n, GJ_NB);
     // k0 = -GJ_NB: no tile is skipped
-    k_gj_update_simt<<<dim3(g, g), 256, 0, c.stream>>>(n, M, lda, -GJ_NB, Cb, Rt);
+    k_gj_update_simt<<<dim3(g, g), 256, 0, c.stream>>>(n, M, lda, -GJ_NB, Cb, Rt, -GJ_NB);
     c.launches += 1;
 }
 
+// One inversion.  Main stream, step k: prep_k, update_k (all of M but the
+// next diagonal block), finish_k.  Side stream, as soon as prep_k is done:
+// update of the next diagonal block alone, then its inverse (k_gj_diag into
+// the other D^{-1} buffer), which so overlaps update_k and finish_k; prep_{k+1}
+// waits for it.
 int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
 {
     const int64_t n = c.n;
     cudaMemsetAsync(c.d_info, 0, sizeof(int32_t), c.stream);
     const unsigned gcols = (unsigned)ceil_div(n, GJ_NB);
-    for (int64_t k0 = 0; k0 < n; k0 += GJ_NB) {
+    float *dinv[2] = {c.d_gj_dinv, c.d_gj_dinv + GJ_NB * GJ_NB};
+    c.tbeg(PH_LU_DIAG);
+    k_gj_diag<<<1, 256, 0, c.stream>>>(n, M, lda, 0, dinv[0], c.d_info);
+    c.tend(PH_LU_DIAG);
+    c.launches += 1;
+    int kstep = 0;
+    for (int64_t k0 = 0; k0 < n; k0 += GJ_NB, ++kstep) {
+        float *dk = dinv[kstep & 1];
+        const int64_t k1 = k0 + GJ_NB;
+        const bool next = k1 < n;
         c.tbeg(PH_LU_PANEL);
-        k_gj_diag<<<1, 256, 0, c.stream>>>(n, M, lda, k0, c.d_gj_dinv, c.d_info);
-        k_gj_prep<<<dim3(gcols, 2), 256, 0, c.stream>>>(n, M, lda, k0, c.d_gj_dinv, c.d_gj_rt,
-                                                         c.d_gj_cb);
+        k_gj_prep<<<dim3(gcols, 2), 256, 0, c.stream>>>(n, M, lda, k0, dk, c.d_gj_rt, c.d_gj_cb);
         c.tend(PH_LU_PANEL);
+        if (next) {
+            cudaEventRecord(c.ev_prep, c.stream);
+            cudaStreamWaitEvent(c.stream2, c.ev_prep, 0);
+            c.tbeg(PH_LU_DIAG, c.stream2);
+            k_gj_diag_update<<<1, 256, 0, c.stream2>>>(n, M, lda, k1, c.d_gj_cb, c.d_gj_rt);
+            k_gj_diag<<<1, 256, 0, c.stream2>>>(n, M, lda, k1, dinv[(kstep + 1) & 1], c.d_info);
+            c.tend(PH_LU_DIAG, c.stream2);
+            cudaEventRecord(c.ev_diag, c.stream2);
+            c.launches += 2;
+        }
+        const int64_t skip0 = next ? k1 : -GJ_NB;
         c.tbeg(PH_LU_UPDATE);
         bool done = false;
         if (prec == NRS_TF32 || prec == NRS_BF16)
-            done = launch_tc_gj_update(c, M, lda, k0, c.d_gj_cb, c.d_gj_rt, prec);
+            done = launch_tc_gj_update(c, M, lda, k0, c.d_gj_cb, c.d_gj_rt, prec, skip0);
         if (!done)
             k_gj_update_simt<<<dim3(gcols, gcols), 256, 0, c.stream>>>(n, M, lda, k0, c.d_gj_cb,
-                                                                        c.d_gj_rt);
+                                                                        c.d_gj_rt, skip0);
         c.tend(PH_LU_UPDATE);
         c.tbeg(PH_LU_PANEL);
-        k_gj_finish<<<dim3(gcols, 2), 256, 0, c.stream>>>(n, M, lda, k0, c.d_gj_dinv, c.d_gj_rt,
-                                                           c.d_gj_cb);
+        k_gj_finish<<<dim3(gcols, 2), 256, 0, c.stream>>>(n, M, lda, k0, dk, c.d_gj_rt, c.d_gj_cb);
         c.tend(PH_LU_PANEL);
-        c.launches += 4;
+        if (next) cudaStreamWaitEvent(c.stream, c.ev_diag, 0);
+        c.launches += 3;
     }
     return 0;
 }

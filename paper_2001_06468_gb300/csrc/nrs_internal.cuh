@@ -55,6 +55,7 @@ enum Phase {
     PH_GEMV = NRS_PH_GEMV,
     PH_KRYLOV = NRS_PH_KRYLOV,
     PH_UPDATE = NRS_PH_UPDATE,
+    PH_LU_DIAG = NRS_PH_LU_DIAG,
     NPH = NRS_NPHASE
 };
 
@@ -76,7 +77,7 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec);
 
 bool tc_available();
 bool launch_tc_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb, const float *Rt,
-                      int prec);
+                      int prec, int64_t skip0);
 void launch_simt_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb, const float *Rt);
 
 // ---- solve (solve.cu) ------------------------------------------------------
@@ -86,6 +87,8 @@ nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0,
 struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t stream2 = nullptr;              // lookahead stream of the factorisation
+    cudaEvent_t ev_prep = nullptr, ev_diag = nullptr;
     int num_sms = 0;
     std::string err;
 
@@ -168,17 +171,17 @@ struct Ctx {
         }
         return ev_pool[ev_used++];
     }
-    void tbeg(int ph)
+    void tbeg(int ph, cudaStream_t s = nullptr)
     {
         if (!timing) return;
         open_ev[ph] = next_event();
-        cudaEventRecord(open_ev[ph], stream);
+        cudaEventRecord(open_ev[ph], s ? s : stream);
     }
-    void tend(int ph)
+    void tend(int ph, cudaStream_t s = nullptr)
     {
         if (!timing || !open_ev[ph]) return;
         cudaEvent_t e = next_event();
-        cudaEventRecord(e, stream);
+        cudaEventRecord(e, s ? s : stream);
         spans.push_back(Span{ph, open_ev[ph], e});
         open_ev[ph] = nullptr;
     }

@@ -152,7 +152,7 @@ __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo)
 
 __global__ void __launch_bounds__(128, 1)
     k_tc_gj_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   int64_t n, float *__restrict__ M, int64_t lda, int32_t *status)
+                   int64_t n, float *__restrict__ M, int64_t lda, int32_t *status, int64_t skip0)
 {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bar_load[2], bar_mma[2];
@@ -261,13 +261,18 @@ __global__ void __launch_bounds__(128, 1)
             tmem_ld_32cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(chunk * 32), v);
             if (row < n) {
                 float old[32];  // all 32 loads in flight before the stores
-                float *p = M + row + (col0 + chunk * 32) * lda;
-                const int64_t ncol = n - (col0 + chunk * 32);
+                const int64_t cbeg = col0 + chunk * 32;
+                float *p = M + row + cbeg * lda;
+                const int64_t ncol = n - cbeg;
+                // the 64 x 64 block at (skip0, skip0) is updated separately
+                const bool row_skip = row >= skip0 && row < skip0 + 64;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) old[j] = j < ncol ? p[j * lda] : 0.0f;
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (j < ncol) p[j * lda] = old[j] - __uint_as_float(v[j]);
+                for (int j = 0; j < 32; ++j) {
+                    const bool skip = row_skip && cbeg + j >= skip0 && cbeg + j < skip0 + 64;
+                    if (j < ncol && !skip) p[j * lda] = old[j] - __uint_as_float(v[j]);
+                }
             }
         }
     }
@@ -336,7 +341,7 @@ bool tc_available()
 }
 
 bool launch_tc_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb, const float *Rt,
-                      int prec)
+                      int prec, int64_t skip0)
 {
     if (prec != NRS_TF32) return false;
     CUtensorMap a, b;
@@ -347,16 +352,16 @@ bool launch_tc_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb,
         attr = true;
     }
     dim3 grid((unsigned)ceil_div(n, TC_BM), (unsigned)ceil_div(n, TC_BN));
-    k_tc_gj_update<<<grid, 128, TC_SMEM, c.stream>>>(a, b, n, M, lda, c.d_status);
+    k_tc_gj_update<<<grid, 128, TC_SMEM, c.stream>>>(a, b, n, M, lda, c.d_status, skip0);
     c.launches += 1;
     return true;
 }
 
 bool launch_tc_gj_update(Ctx &c, float *M, int64_t lda, int64_t k0, const float *Cb,
-                         const float *Rt, int prec)
+                         const float *Rt, int prec, int64_t skip0)
 {
     (void)k0;
-    return launch_tc_rank64(c, M, lda, c.n, Cb, Rt, prec);
+    return launch_tc_rank64(c, M, lda, c.n, Cb, Rt, prec, skip0);
 }
 
 }  // namespace nrs

@@ -39,7 +39,7 @@ EXPORTS = ["nrs_create", "nrs_destroy", "nrs_last_error", "nrs_sizes", "nrs_set_
            "nrs_assemble", "nrs_factor", "nrs_solve", "nrs_step", "nrs_sync", "nrs_set_timing",
            "nrs_get_timing", "nrs_rank64_update", "nrs_nearest_build_static"]
 PHASES = ["kinematics", "nearest", "segments", "assemble", "border", "convert", "lu_panel",
-          "lu_update", "trsv", "gemv", "krylov", "update"]
+          "lu_update", "trsv", "gemv", "krylov", "update", "lu_diag"]
 
 
 class ProblemDesc(ctypes.Structure):
