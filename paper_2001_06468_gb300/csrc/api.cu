@@ -295,7 +295,13 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
     if (e == cudaSuccess && c->F) e = cudaMemset(c->d_ext, 0, sizeof(double) * 6 * c->F);
     if (e == cudaSuccess) e = cudaMemset(c->d_flags, 0, sizeof(int32_t) * nrs::ceil_div(c->n, 64));
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        // the lookahead stream runs single-CTA kernels on the critical path:
+        // highest priority, so the block scheduler serves them first
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        e = cudaStreamCreateWithPriority(&c->stream2, cudaStreamNonBlocking, greatest);
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_prep, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_diag, cudaEventDisableTiming);
     if (e != cudaSuccess) {

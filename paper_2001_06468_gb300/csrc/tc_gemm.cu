@@ -123,18 +123,15 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, uint32_t (&v)[32])
+// 16 consecutive TMEM columns of this warp's 32 lanes (one row per thread).
+__device__ __forceinline__ void tmem_ld_16cols(uint32_t taddr, uint32_t (&v)[16])
 {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
-          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
-          "=r"(v[31])
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -255,21 +252,21 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_after();
     if (ok) {
         const int64_t row = row0 + warp * 32 + lane;
+        // the 64 x 64 block at (skip0, skip0) is updated separately (lookahead)
+        const bool row_skip = row >= skip0 && row < skip0 + 64;
 #pragma unroll 1
-        for (int chunk = 0; chunk < TC_BN / 32; ++chunk) {
-            uint32_t v[32];
-            tmem_ld_32cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(chunk * 32), v);
+        for (int chunk = 0; chunk < TC_BN / 16; ++chunk) {
+            uint32_t v[16];
+            tmem_ld_16cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(chunk * 16), v);
             if (row < n) {
-                float old[32];  // all 32 loads in flight before the stores
-                const int64_t cbeg = col0 + chunk * 32;
+                float old[16];  // all 16 loads in flight before the stores
+                const int64_t cbeg = col0 + chunk * 16;
                 float *p = M + row + cbeg * lda;
                 const int64_t ncol = n - cbeg;
-                // the 64 x 64 block at (skip0, skip0) is updated separately
-                const bool row_skip = row >= skip0 && row < skip0 + 64;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) old[j] = j < ncol ? p[j * lda] : 0.0f;
+                for (int j = 0; j < 16; ++j) old[j] = j < ncol ? p[j * lda] : 0.0f;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
+                for (int j = 0; j < 16; ++j) {
                     const bool skip = row_skip && cbeg + j >= skip0 && cbeg + j < skip0 + 64;
                     if (j < ncol && !skip) p[j * lda] = old[j] - __uint_as_float(v[j]);
                 }
