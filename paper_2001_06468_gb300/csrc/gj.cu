@@ -21,195 +21,126 @@ namespace nrs {
 
 constexpr int GJ_NB = 64;
 
-// D^{-1} by Gauss-Jordan on [D | I] with partial pivoting, eight columns at a
-// time (one CTA of 256 threads, three barriers per panel of eight columns).
-//  * Thread (r, s) = (tid / 4, tid % 4) keeps row r of the augmented matrix in
-//    registers: left columns [16 s, 16 s + 16) in Lc, right columns
-//    [64 + 16 s, ...) in Rc.  The panel loop is unrolled, so every index is static.
-//  * Panel P (columns 8P .. 8P+7): the owners publish the panel columns; warp 0
-//    runs partial pivoting on the 64 x 8 panel alone (unused row of largest
-//    |value|, lowest row on ties, exactly the choices column-by-column
-//    Gauss-Jordan makes) and inverts Pv, the 8 x 8 panel block of the chosen
-//    pivot rows, in pivot order.  Then every row is updated at once:
-//        pivot rows  W_P <- Pv^{-1} W_P,
-//        other rows  W_r <- W_r - (W_r[panel] Pv^{-1}) W_P,
-//    which zeroes the panel columns outside the pivot rows and turns the pivot
-//    rows' panel block into the identity.
-//  * Rows are never moved: at the end the left half of pivot row p_c is e_c,
-//    so logical row c of D^{-1} is the right half of physical row p_c.
+// D^{-1} by Gauss-Jordan on [D | I] with partial pivoting (one CTA of 256
+// threads, two barriers per column).
+//  * Thread (r, s) = (tid / 4, tid % 4) keeps row r of the augmented matrix,
+//    columns s + 4 i, in registers: the left half in L[16], the right half in
+//    Rr[16].  After each group of four columns the finished left columns are
+//    shifted out (L[i] <- L[i+1]) so that every register index is static.
+//  * Column c is published in colbuf[c & 1] by its owners during step c-1;
+//    every warp then finds the pivot on its own with warp reductions: the
+//    unused row of largest |value|, lowest row on ties.  Only the pivot row is
+//    copied to shared memory for the others.
+//  * Rows are never moved or scaled during the sweep: step c subtracts
+//    (W[r][c] / W[p][c]) W[p] from every row r != p.  At the end the left half
+//    of pivot row p_c is pv_c e_c, so logical row c of D^{-1} is the right
+//    half of physical row p_c divided by pv_c.
 // Padding rows/columns (kb < 64) are identity.  Dinv is row-major 64 x 64; a
 // zero pivot records info.
+//
+// With Cb and Rt given (the lookahead), the block is first brought up to date,
+// D = M[K,K] - C[K,:] R[:,K]: the part of the previous step's rank-64 update
+// that the main stream skips.  (Nothing reads M[K,K] afterwards: it is
+// overwritten with D^{-1} at the end of the step.)
 __global__ void __launch_bounds__(256)
     k_gj_diag(int64_t n, const float *__restrict__ M, int64_t lda, int64_t k0,
-              float *__restrict__ Dinv, int32_t *__restrict__ info)
+              float *__restrict__ Dinv, int32_t *__restrict__ info,
+              const float *__restrict__ Cb, const float *__restrict__ Rt)
 {
-    constexpr int NB = GJ_NB, PW = 8, RP = 2 * NB + 4;
-    __shared__ float colp[NB][PW + 1];
-    __shared__ __align__(16) float prows[PW][RP];
-    __shared__ float Pinv[PW][PW];
-    __shared__ int piv_s[PW];
+    constexpr int NB = GJ_NB;
+    __shared__ float colbuf[2][NB];
+    __shared__ float prow[2 * NB];
     __shared__ int pos[NB];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ float pivval[NB];
+    __shared__ float Cs[NB][NB + 1];
+    __shared__ float Rs[NB][NB + 1];
+    const int tid = threadIdx.x, lane = tid & 31;
     const int r = tid >> 2, s = tid & 3;
     const int kb = (int)min((int64_t)NB, n - k0);
-    float Lc[16], Rc[16];
+    float L[16], Rr[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        const int j = 16 * s + i;
-        Lc[i] = (r < kb && j < kb) ? M[(k0 + r) + (k0 + j) * lda] : (r == j ? 1.0f : 0.0f);
-        Rc[i] = (r == j) ? 1.0f : 0.0f;
+        const int j = s + 4 * i;
+        L[i] = (r < kb && j < kb) ? M[(k0 + r) + (k0 + j) * lda] : (r == j ? 1.0f : 0.0f);
+        Rr[i] = (r == j) ? 1.0f : 0.0f;
     }
-    unsigned long long used = 0ull;  // warp 0 only
+    if (Cb) {
+        float cv[16], rv[16];
 #pragma unroll
-    for (int P = 0; P < NB / PW; ++P) {
-        const int slotP = P >> 1, base = (P & 1) * PW;
-        __syncwarp();  // this row's readers of colp (previous panel) are done
-        if (s == slotP) {
+        for (int q = 0; q < 16; ++q) {
+            const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
+            cv[q] = b < kb ? Cb[(k0 + b) * NB + a] : 0.0f;
+            rv[q] = b < kb ? Rt[(k0 + b) * NB + a] : 0.0f;
+        }
 #pragma unroll
-            for (int k = 0; k < PW; ++k) colp[r][k] = Lc[base + k];
+        for (int q = 0; q < 16; ++q) {
+            const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
+            Cs[b][a] = cv[q];
+            Rs[b][a] = rv[q];
         }
         __syncthreads();
-        if (warp == 0) {
-            float va[PW], vb[PW];
+        // L[i] (row r, column j = s + 4 i) -= sum_t C[r][t] R[j][t]
 #pragma unroll
-            for (int k = 0; k < PW; ++k) {
-                va[k] = colp[lane][k];
-                vb[k] = colp[lane + 32][k];
-            }
-#pragma unroll
-            for (int k = 0; k < PW; ++k) {
-                const bool u0 = (used >> lane) & 1ull, u1 = (used >> (lane + 32)) & 1ull;
-                const unsigned k0v = u0 ? 0u : (0x80000000u | __float_as_uint(fabsf(va[k])));
-                const unsigned k1v = u1 ? 0u : (0x80000000u | __float_as_uint(fabsf(vb[k])));
-                const unsigned key = k0v >= k1v ? k0v : k1v;
-                const int row = k0v >= k1v ? lane : lane + 32;
-                const unsigned mx = __reduce_max_sync(0xffffffffu, key);
-                const int p = (int)__reduce_min_sync(0xffffffffu, key == mx ? (unsigned)row : 64u);
-                used |= 1ull << p;
-                const int owner = p & 31;
-                const bool upper = p >= 32;
-                float pv[PW];
-#pragma unroll
-                for (int j = 0; j < PW; ++j)
-                    pv[j] = __shfl_sync(0xffffffffu, upper ? vb[j] : va[j], owner);
-                const float d = pv[k];
-                if (lane == 0) {
-                    piv_s[k] = p;
-                    pos[p] = PW * P + k;
-                    if (d == 0.0f && info) atomicCAS(info, 0, (int)(k0 + PW * P + k + 1));
-                }
-                if (lane != p) {
-                    const float g = va[k] / d;
-#pragma unroll
-                    for (int j = 0; j < PW; ++j) va[j] -= g * pv[j];
-                }
-                if (lane + 32 != p) {
-                    const float g = vb[k] / d;
-#pragma unroll
-                    for (int j = 0; j < PW; ++j) vb[j] -= g * pv[j];
-                }
-            }
-            __syncwarp();
-            // Pinv = inverse of the pivot rows' original panel block, in pivot
-            // order (lane k < 8 holds row k of [Pv | I]; no further pivoting)
-            float a[PW], e[PW];
-            const int pr = lane < PW ? piv_s[lane] : 0;
-#pragma unroll
-            for (int j = 0; j < PW; ++j) {
-                a[j] = lane < PW ? colp[pr][j] : 0.0f;
-                e[j] = (lane == j) ? 1.0f : 0.0f;
-            }
-#pragma unroll
-            for (int k = 0; k < PW; ++k) {
-                float bk[2 * PW];
-#pragma unroll
-                for (int j = 0; j < PW; ++j) {
-                    bk[j] = __shfl_sync(0xffffffffu, a[j], k);
-                    bk[PW + j] = __shfl_sync(0xffffffffu, e[j], k);
-                }
-                if (lane != k) {
-                    const float f = a[k] / bk[k];
-#pragma unroll
-                    for (int j = 0; j < PW; ++j) {
-                        a[j] -= f * bk[j];
-                        e[j] -= f * bk[PW + j];
-                    }
-                }
-            }
-            if (lane < PW) {
-                float al = 1.0f;  // a[lane] with a static index
-#pragma unroll
-                for (int j = 0; j < PW; ++j)
-                    if (lane == j) al = a[j];
-                const float dd = 1.0f / al;
-#pragma unroll
-                for (int j = 0; j < PW; ++j) Pinv[lane][j] = e[j] * dd;
-            }
-        }
-        __syncthreads();
-        // pivot rows publish their (old) rows
-        int kr = -1;
-#pragma unroll
-        for (int k = 0; k < PW; ++k)
-            if (piv_s[k] == r) kr = k;
-        if (kr >= 0) {
-#pragma unroll
-            for (int i = 0; i < 16; i += 4) {
-                *reinterpret_cast<float4 *>(&prows[kr][16 * s + i]) =
-                    make_float4(Lc[i], Lc[i + 1], Lc[i + 2], Lc[i + 3]);
-                *reinterpret_cast<float4 *>(&prows[kr][NB + 16 * s + i]) =
-                    make_float4(Rc[i], Rc[i + 1], Rc[i + 2], Rc[i + 3]);
-            }
-        }
-        __syncthreads();
-        float coef[PW];  // pivot rows: Pinv[kr][k]; others: -(W_r[panel] Pinv)[k]
-        if (kr >= 0) {
-#pragma unroll
-            for (int k = 0; k < PW; ++k) coef[k] = Pinv[kr][k];
-        } else {
-            float w[PW];
-#pragma unroll
-            for (int j = 0; j < PW; ++j) w[j] = colp[r][j];
-#pragma unroll
-            for (int k = 0; k < PW; ++k) {
-                float t = 0.0f;
-#pragma unroll
-                for (int j = 0; j < PW; ++j) t += w[j] * Pinv[j][k];
-                coef[k] = -t;
-            }
-        }
-        const float keep = kr >= 0 ? 0.0f : 1.0f;
-#pragma unroll
-        for (int i = 0; i < 16; i += 4) {
-            float4 accl = make_float4(keep * Lc[i], keep * Lc[i + 1], keep * Lc[i + 2], keep * Lc[i + 3]);
-            float4 accr = make_float4(keep * Rc[i], keep * Rc[i + 1], keep * Rc[i + 2], keep * Rc[i + 3]);
-#pragma unroll
-            for (int k = 0; k < PW; ++k) {
-                const float4 pl = *reinterpret_cast<const float4 *>(&prows[k][16 * s + i]);
-                const float4 pr4 = *reinterpret_cast<const float4 *>(&prows[k][NB + 16 * s + i]);
-                accl.x += coef[k] * pl.x;
-                accl.y += coef[k] * pl.y;
-                accl.z += coef[k] * pl.z;
-                accl.w += coef[k] * pl.w;
-                accr.x += coef[k] * pr4.x;
-                accr.y += coef[k] * pr4.y;
-                accr.z += coef[k] * pr4.z;
-                accr.w += coef[k] * pr4.w;
-            }
-            Lc[i] = accl.x;
-            Lc[i + 1] = accl.y;
-            Lc[i + 2] = accl.z;
-            Lc[i + 3] = accl.w;
-            Rc[i] = accr.x;
-            Rc[i + 1] = accr.y;
-            Rc[i + 2] = accr.z;
-            Rc[i + 3] = accr.w;
+        for (int i = 0; i < 16; ++i) {
+            const int j = s + 4 * i;
+            float acc = 0.0f;
+#pragma unroll 16
+            for (int t = 0; t < NB; ++t) acc += Cs[r][t] * Rs[j][t];
+            if (r < kb && j < kb) L[i] -= acc;
         }
     }
+    if (s == 0) colbuf[0][r] = L[0];
+    unsigned long long used = 0ull;
     __syncthreads();
-    const int lr = pos[r];
+    for (int cc = 0; cc < NB / 4; ++cc) {
 #pragma unroll
-    for (int i = 0; i < 16; ++i) Dinv[lr * NB + 16 * s + i] = Rc[i];
+        for (int sp = 0; sp < 4; ++sp) {
+            const int c = 4 * cc + sp;
+            const int buf = sp & 1;
+            const float a0 = fabsf(colbuf[buf][lane]), a1 = fabsf(colbuf[buf][lane + 32]);
+            const bool u0 = (used >> lane) & 1ull, u1 = (used >> (lane + 32)) & 1ull;
+            const unsigned k0v = u0 ? 0u : (0x80000000u | __float_as_uint(a0));
+            const unsigned k1v = u1 ? 0u : (0x80000000u | __float_as_uint(a1));
+            const unsigned key = k0v >= k1v ? k0v : k1v;
+            const int row = k0v >= k1v ? lane : lane + 32;
+            const unsigned mx = __reduce_max_sync(0xffffffffu, key);
+            const int p = (int)__reduce_min_sync(0xffffffffu, key == mx ? (unsigned)row : 64u);
+            used |= 1ull << p;
+            const float pv = colbuf[buf][p];
+            if (tid == 0) {
+                pos[p] = c;
+                pivval[c] = pv;
+                if (pv == 0.0f && info) atomicCAS(info, 0, (int)(k0 + c + 1));
+            }
+            if (r == p) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    prow[s + 4 * i] = L[i];
+                    prow[NB + s + 4 * i] = Rr[i];
+                }
+            }
+            __syncthreads();
+            if (r != p) {
+                const float g = colbuf[buf][r] / pv;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    L[i] -= g * prow[s + 4 * i];
+                    Rr[i] -= g * prow[NB + s + 4 * i];
+                }
+            }
+            // publish column c + 1 for the next step
+            if (s == ((sp + 1) & 3)) colbuf[buf ^ 1][r] = (sp < 3) ? L[0] : L[1];
+            __syncthreads();
+        }
+        // columns 4 cc .. 4 cc + 3 are finished: shift them out of L
+#pragma unroll
+        for (int i = 0; i < 15; ++i) L[i] = L[i + 1];
+        L[15] = 0.0f;
+    }
+    const int lr = pos[r];
+    const float d = 1.0f / pivval[lr];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) Dinv[lr * NB + s + 4 * i] = Rr[i] * d;
 }
 
 // Prep of step K.  grid.y = 0: R[:, j] = D^{-1} M[K, j] for one 64-column tile
@@ -424,60 +355,6 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// Lookahead: the rank-64 update of the next diagonal block only,
-// M[K1, K1] -= C[K1, :] R[:, K1] (one CTA), so that its inverse can be taken
-// while the rest of the update runs on the main stream.
-__global__ void __launch_bounds__(256)
-    k_gj_diag_update(int64_t n, float *__restrict__ M, int64_t lda, int64_t k1,
-                     const float *__restrict__ Cb, const float *__restrict__ Rt)
-{
-    constexpr int NB = GJ_NB;
-    __shared__ float Cs[NB][NB + 1];
-    __shared__ float Rs[NB][NB + 1];
-    const int tid = threadIdx.x;
-    const int kb = (int)min((int64_t)NB, n - k1);
-    {
-        float cv[16], rv[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
-            cv[q] = b < kb ? Cb[(k1 + b) * NB + a] : 0.0f;
-            rv[q] = b < kb ? Rt[(k1 + b) * NB + a] : 0.0f;
-        }
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
-            Cs[b][a] = cv[q];
-            Rs[b][a] = rv[q];
-        }
-    }
-    __syncthreads();
-    const int tr = tid & 15, tc = tid >> 4;
-    float acc[4][4] = {};
-#pragma unroll 8
-    for (int t = 0; t < NB; ++t) {
-        float a[4], b[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) a[q] = Cs[tr + 16 * q][t];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) b[q] = Rs[tc + 16 * q][t];
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-            for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * b[y];
-    }
-#pragma unroll
-    for (int y = 0; y < 4; ++y) {
-        const int j = tc + 16 * y;
-        if (j >= kb) continue;
-#pragma unroll
-        for (int x = 0; x < 4; ++x) {
-            const int i = tr + 16 * x;
-            if (i < kb) M[(k1 + i) + (k1 + j) * lda] -= acc[x][y];
-        }
-    }
-}
-
 // Tensor-core version of the update (tc_gemm.cu); false if not available for
 // this precision.
 bool launch_tc_gj_update(Ctx &c, float *M, int64_t lda, int64_t k0, const float *Cb,
@@ -503,7 +380,7 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
     const unsigned gcols = (unsigned)ceil_div(n, GJ_NB);
     float *dinv[2] = {c.d_gj_dinv, c.d_gj_dinv + GJ_NB * GJ_NB};
     c.tbeg(PH_LU_DIAG);
-    k_gj_diag<<<1, 256, 0, c.stream>>>(n, M, lda, 0, dinv[0], c.d_info);
+    k_gj_diag<<<1, 256, 0, c.stream>>>(n, M, lda, 0, dinv[0], c.d_info, nullptr, nullptr);
     c.tend(PH_LU_DIAG);
     c.launches += 1;
     int kstep = 0;
@@ -518,11 +395,11 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
             cudaEventRecord(c.ev_prep, c.stream);
             cudaStreamWaitEvent(c.stream2, c.ev_prep, 0);
             c.tbeg(PH_LU_DIAG, c.stream2);
-            k_gj_diag_update<<<1, 256, 0, c.stream2>>>(n, M, lda, k1, c.d_gj_cb, c.d_gj_rt);
-            k_gj_diag<<<1, 256, 0, c.stream2>>>(n, M, lda, k1, dinv[(kstep + 1) & 1], c.d_info);
+            k_gj_diag<<<1, 256, 0, c.stream2>>>(n, M, lda, k1, dinv[(kstep + 1) & 1], c.d_info,
+                                                 c.d_gj_cb, c.d_gj_rt);
             c.tend(PH_LU_DIAG, c.stream2);
             cudaEventRecord(c.ev_diag, c.stream2);
-            c.launches += 2;
+            c.launches += 1;
         }
         const int64_t skip0 = next ? k1 : -GJ_NB;
         c.tbeg(PH_LU_UPDATE);
