@@ -5,12 +5,15 @@ problem on GB300.
 One step = one explicit-midpoint (RK2) step of the single free undulating
 swimmer (N = 800 force points, Q = 8000 quadrature points, eps = 0.005,
 n = 2406 unknowns): twice (kinematics, nearest neighbours, segments, FP64
-assembly, rigid-body border, FP32 block-LU factor, FP64 GMRES-based
-iterative refinement to the FP64 answer) plus the state update.  Inputs are
-the seeded synthetic beat shapes of `synth` (the paper's cited beat patterns
-are not available), resident in HBM before the timed region.
+assembly, rigid-body border, explicit FP32 inverse by blocked Gauss-Jordan
+with split-TF32 tensor-core updates, FP64 GMRES-based iterative refinement to
+the FP64 answer) plus the state update.  Inputs are the seeded synthetic beat
+shapes of `synth` (the paper's cited beat patterns are not available),
+resident in HBM before the timed region.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nrs|reference]
+                    [--prec tf32|fp32|fp64]
+    python bench.py --profile-solve --workload swimmer_mid   # one solve, for ncu
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 on the same workload.  Under torchrun each rank runs its own replica of the
@@ -40,6 +43,7 @@ METRIC = "s per timestep (assemble+solve) mixed-IR vs FP64 at 1e-10 rel err; pai
 WORKLOAD = "single free undulating swimmer, N=800 force / Q=8000 quadrature points, eps=0.005, n=2406"
 L2_FLUSH_BYTES = 512 << 20
 FP64_NOMINAL_TFLOPS = 1.25       # GB300 FP64 (vector and tensor), nominal
+TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 tensor throughput
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 
@@ -131,57 +135,89 @@ def _shapes_host(pr, t):
     return tuple(torch.from_numpy(d[k]).pin_memory() for k in ("x", "Xw", "xidot"))
 
 
-def _roofline(phase, ph_ms, ph_spans, timed_steps, pr, peaks, peak_src, clocks, lu_flops):
-    """Roofline record of the dominant kernel family."""
-    ms = ph_ms[phase]
-    launches = max(ph_spans[phase], 1)
-    per_launch_s = ms / 1e3 / launches
+# DRAM bytes per launch from one ncu capture (profiles/), valid while the
+# kernel's source file is unchanged (first 12 hex digits of its SHA-1).
+NCU_TRAFFIC = {
+    "k_gj_diag": {"bytes": 94464, "file": "paper_2001_06468_gb300/csrc/gj.cu",
+                  "sha1": "f6b73d0d7440", "scale": "none (a 64 x 64 block at any n)"},
+    "k_tc_gj_update": {"bytes": 147643904 + 83535616, "n": 6006,
+                       "file": "paper_2001_06468_gb300/csrc/tc_gemm.cu", "sha1": "0d98b55bdd8d",
+                       "scale": "n^2 (captured at n = 6006)"},
+    "k_assemble64": {"bytes": None, "file": "paper_2001_06468_gb300/csrc/assemble.cu",
+                     "sha1": "fcf536ee0b72", "scale": None},
+}
+
+
+def _traffic(kernel, n):
+    import hashlib
+    rec = NCU_TRAFFIC.get(kernel)
+    if not rec or rec["bytes"] is None:
+        return None
+    src = open(os.path.join(ROOT, rec["file"]), "rb").read()
+    if hashlib.sha1(src).hexdigest()[:12] != rec["sha1"]:
+        return None  # the kernel changed since the counters were taken
+    if "n" in rec:
+        return rec["bytes"] * (n / rec["n"]) ** 2
+    return rec["bytes"]
+
+
+def _rooflines(ph_ms, ph_spans, pr, peaks, peak_src, clocks):
+    """Roofline records of the kernel families of the step, from the live
+    per-phase CUDA-event times.  Algorithmic work per launch:
+      k_gj_diag       2*64^3 flops (inverse) + 2*64^3 (lookahead block update)
+      k_tc_gj_update  8 n^2 bytes (read and write of the FP32 matrix), HBM-bound at K = 64
+      k_assemble64    29 FP64 operations per (force point, quadrature point) pair
+      k_gemv_part     8 n^2 bytes (FP64 matrix)
+      k_gemv32_part   4 n^2 bytes (FP32 explicit inverse)"""
     n = pr.n
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    if phase == "lu_update":
-        flops = lu_flops / launches * (ph_spans[phase] / max(ph_spans[phase], 1))
-        peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-        return {"kernel": "k_gemm_update<float> (A22 -= L21 U12, FP32 CUDA cores)", "bound": "alu",
-                "achieved": flops / per_launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "frac": flops / per_launch_s / 1e12 / peak,
-                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median under load)",
-                "work_per_launch": flops, "traffic": None}
-    if phase == "assemble":
-        pairs = pr.pairs
-        flops_per_pair = 29.0
-        achieved = pairs * flops_per_pair / per_launch_s / 1e12
-        peak = FP64_NOMINAL_TFLOPS * sm_mhz / 2070.0
-        return {"kernel": "k_assemble64 (NEAREST A_s in FP64)", "bound": "alu", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": "nominal FP64 1.25 TFLOP/s at 2070 MHz, scaled to the median clock",
-                "pairs_per_s": pairs / per_launch_s, "work_per_launch": pairs * flops_per_pair,
-                "traffic": None}
-    if phase == "gemv":
-        bytes_ = 8.0 * n * n
-        achieved = bytes_ / per_launch_s / 1e9
-        peak = peaks["hbm_gbs"]
-        return {"kernel": "k_gemv_part (FP64 residual / Arnoldi products)", "bound": "hbm",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_src, "work_per_launch": bytes_, "traffic": None}
-    if phase == "trsv":
-        bytes_ = 4.0 * n * n  # both triangles of the FP32 factor per application
-        achieved = bytes_ / per_launch_s / 1e9
-        peak = peaks["hbm_gbs"]
-        return {"kernel": "k_trsv_lower/k_trsv_upper (preconditioner application)", "bound": "hbm",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_src, "work_per_launch": bytes_, "traffic": None}
-    return {"kernel": phase, "bound": "latency", "achieved": None, "peak": None, "unit": None,
-            "frac": None, "traffic": None}
+    fp32_peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    fp64_peak = FP64_NOMINAL_TFLOPS * sm_mhz / 2070.0
+    tf32_peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
 
+    def per_launch(ph):
+        return ph_ms[ph] / 1e3 / max(ph_spans[ph], 1)
 
-def _lu_update_flops(n, nb=64):
-    f = 0.0
-    for k0 in range(0, n, nb):
-        kb = min(nb, n - k0)
-        rest = n - k0 - kb
-        if rest > 0:
-            f += 2.0 * rest * rest * kb
-    return f
+    recs = {}
+    t = per_launch("lu_diag")
+    w = 4.0 * 64 ** 3
+    recs["lu_diag"] = {"kernel": "k_gj_diag (64 x 64 diagonal-block inverse, one CTA)",
+                       "bound": "alu", "achieved": w / t / 1e12, "peak": fp32_peak,
+                       "unit": "TFLOP/s", "frac": w / t / 1e12 / fp32_peak,
+                       "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
+                       "work_per_launch": w, "launches": ph_spans["lu_diag"],
+                       "traffic": _traffic("k_gj_diag", n)}
+    t = per_launch("lu_update")
+    b = 8.0 * n * n
+    recs["lu_update"] = {"kernel": "k_tc_gj_update (tcgen05 3xTF32 rank-64 update)",
+                         "bound": "hbm", "achieved": b / t / 1e9, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": b / t / 1e9 / peaks["hbm_gbs"],
+                         "peak_source": peak_src + " (HBM copy)", "work_per_launch": b,
+                         "tensor_tflops": 2.0 * n * n * 64 / t / 1e12,
+                         "tensor_frac_of_tf32": 2.0 * n * n * 64 / t / 1e12 / tf32_peak,
+                         "launches": ph_spans["lu_update"], "traffic": _traffic("k_tc_gj_update", n)}
+    t = per_launch("assemble")
+    f = pr.pairs * 29.0
+    recs["assemble"] = {"kernel": "k_assemble64 (NEAREST A_s, FP64)", "bound": "alu",
+                        "achieved": f / t / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                        "frac": f / t / 1e12 / fp64_peak,
+                        "peak_source": "nominal FP64 1.25 TFLOP/s at 2070 MHz, scaled to the clock",
+                        "pairs_per_s": pr.pairs / t, "work_per_launch": f,
+                        "launches": ph_spans["assemble"], "traffic": _traffic("k_assemble64", n)}
+    t = per_launch("gemv")
+    b = 8.0 * n * n
+    recs["gemv"] = {"kernel": "k_gemv_part (FP64 residual / Arnoldi products)", "bound": "hbm",
+                    "achieved": b / t / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": b / t / 1e9 / peaks["hbm_gbs"], "peak_source": peak_src,
+                    "work_per_launch": b, "launches": ph_spans["gemv"], "traffic": None}
+    t = per_launch("trsv")
+    b = 4.0 * n * n
+    recs["precond"] = {"kernel": "k_gemv32_part (explicit-inverse preconditioner)",
+                       "bound": "hbm", "achieved": b / t / 1e9, "peak": peaks["hbm_gbs"],
+                       "unit": "GB/s", "frac": b / t / 1e9 / peaks["hbm_gbs"],
+                       "peak_source": peak_src, "work_per_launch": b,
+                       "launches": ph_spans["trsv"], "traffic": None}
+    return recs
 
 
 def run_nrs(args):
@@ -308,11 +344,10 @@ def run_nrs(args):
     ph_ms = {k: v[0] for k, v in phases.items()}
     ph_spans = {k: v[1] for k, v in phases.items()}
     tot = sum(ph_ms.values())
-    kernel_phases = ["lu_update", "assemble", "gemv", "trsv", "lu_panel", "nearest", "krylov"]
-    top = max(kernel_phases, key=lambda p: ph_ms[p])
-    lu_flops = _lu_update_flops(pr.n) * 2 * K  # two factorisations per step
-    roof = _roofline(top, ph_ms, ph_spans, K, pr, peaks, peak_src, clocks, lu_flops)
-    asm = _roofline("assemble", ph_ms, ph_spans, K, pr, peaks, peak_src, clocks, lu_flops)
+    recs = _rooflines(ph_ms, ph_spans, pr, peaks, peak_src, clocks)
+    top = max(recs, key=lambda p: ph_ms["trsv" if p == "precond" else p])
+    roof = recs[top]
+    asm = recs["assemble"]
     line = {
         "metric": METRIC,
         "value": s_per_step,
@@ -324,7 +359,8 @@ def run_nrs(args):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64 residual + f32 factor",
+        "dtype": "f64 residual + " + {"tf32": "split-TF32 tensor-core", "fp32": "fp32",
+                                     "fp64": "fp64", "bf16": "bf16"}[args.prec] + " factor",
         "data": "synthetic (seeded undulating-tube beat shapes)",
         "config": {"workload": WORKLOAD, "factor": args.prec, "refinement": "GMRES-IR, FP64 residual",
                    "rk2_stages_per_step": 2, "l2": "flushed between timed steps (512 MiB write)",
@@ -334,11 +370,12 @@ def run_nrs(args):
         "mixed_vs_plain_speedup": plain_s / (t_max / K),
         "phases_ms_per_step": {k: v / K for k, v in ph_ms.items()},
         "phase_share": {k: (v / tot if tot else 0.0) for k, v in ph_ms.items()},
+        "phase_note": "lu_diag runs on a second stream, overlapping lu_update and lu_panel",
         "refinement": {"outer_mean": float(np.mean([r["stages"][i]["outer"] for r in reports[W:] for i in (0, 1)])),
                        "inner_mean": float(np.mean([r["stages"][i]["inner"] for r in reports[W:] for i in (0, 1)])),
                        "backward_err_max": float(max(r["stages"][i]["backward_err"] for r in reports[W:] for i in (0, 1)))},
         "roofline": roof,
-        "roofline_assembly": asm,
+        "rooflines": recs,
         "e2e": {"value": e2e_s, "unit": "s/step", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clocks,
@@ -405,15 +442,51 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+PROFILE_WORKLOADS = {
+    "swimmer": lambda: g.swimmer_config(),
+    # n = 6006: FP64 matrix 289 MB, FP32 copy 144 MB, both larger than L2
+    "swimmer_mid": lambda: g.swimmer_config(ns_f=200, nth_f=10, ns_q=1000, nth_q=20),
+    "swimmers4": lambda: g.swimmers_config(),
+    "sperm_channel": lambda: g.sperm_channel_config(),
+}
+
+
+def profile_solve(args):
+    """One solve of one stage (no timing loop): the command ncu captures."""
+    import torch
+    from paper_2001_06468_gb300 import nrs
+    torch.cuda.set_device(0)
+    pr = PROFILE_WORKLOADS[args.workload]()
+    sh = g.pack_shapes(pr, 0.25)
+    ctx = nrs.Context.from_problem(pr, factor_prec=args.prec)
+    Y = g.initial_state(pr)
+    ctx.set_state(Y["x0"], Y["B"])
+    xi, Xiw, xidot = nrs.shapes_to_device(sh)
+    x, Xw, b = ctx.kinematics(xi, Xiw, xidot)
+    ctx.nearest_build(xi, Xiw)
+    ctx.assemble(x, Xw, want_matrix=False)
+    ctx.factor(args.prec)
+    _, rep = ctx.solve(b, check=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": args.workload, "n": pr.n, "prec": args.prec, "report": rep[0]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="nrs", choices=["nrs", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16", "fp64"])
+    ap.add_argument("--prec", default="tf32", choices=["fp32", "tf32", "bf16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="one kinematics + nearest + assemble + factor + solve on --workload, "
+                         "then exit (for ncu captures)")
+    ap.add_argument("--workload", default="swimmer", choices=sorted(PROFILE_WORKLOADS))
     args = ap.parse_args()
+    if args.profile_solve:
+        profile_solve(args)
+        return
     if args.warmup < 3 and args.impl == "nrs":
         args.warmup = 3
     if args.impl == "reference":
