@@ -85,6 +85,14 @@ typedef struct {
                               below that (0 = 1e-12) */
     int32_t max_outer;     /* refinement steps (0 = 20)          */
     int32_t max_inner;     /* GMRES iterations per step (0 = 30) */
+    int32_t reuse_factor;  /* nrs_step: 0 = factor at every stage; 1 = keep the factor (the
+                              FP32 inverse or the FP64 LU) across stages as the preconditioner
+                              and refactor only when the previous solve needed more than
+                              reuse_max_inner GMRES iterations or after reuse_max_stages
+                              stages.  The FP64 residual always uses the current matrix. */
+    int32_t reuse_max_inner;   /* 0 = 8  */
+    int32_t reuse_max_stages;  /* 0 = 16 */
+    int32_t warm_start;    /* nrs_step: start each solve from the previous stage's solution */
 } nrs_problem_desc;
 
 typedef struct {
@@ -99,6 +107,7 @@ typedef struct {
 typedef struct {
     nrs_solve_report stage[2];
     double ms_total;        /* device time of the step (CUDA events)          */
+    int32_t factorizations; /* factorisations done in this step (0..2)        */
 } nrs_step_report;
 
 /* Body-frame inputs of one stage (device memory):

@@ -165,13 +165,17 @@ nrs_status do_factor(Ctx *c, int prec)
     }
     CK(cudaGetLastError());
     c->factored_prec = prec;
+    c->factorizations += 1;
     return NRS_OK;
 }
 
-nrs_status do_segments_and_assemble(Ctx *c, const D4 *x_lab, const D4 *Xw_lab)
+// write_lo: also write the FP32 copy (which a Gauss-Jordan factor replaces by
+// its inverse: writing it destroys that factor).
+nrs_status do_segments_and_assemble(Ctx *c, const D4 *x_lab, const D4 *Xw_lab, bool write_lo = true)
 {
     nrs::launch_gather(*c, Xw_lab, c->d_seg_ptr, c->d_perm);
-    float *a32 = c->factor_prec == NRS_FP64 ? nullptr : c->d_A32;
+    float *a32 = (c->factor_prec == NRS_FP64 || !write_lo) ? nullptr : c->d_A32;
+    if (a32 && c->factored_prec != NRS_FP64) c->factored_prec = -1;
     nrs::launch_assemble(*c, x_lab, c->d_A64, a32, c->lda);
     nrs::launch_border(*c, x_lab, c->d_A64, a32, c->lda);
     CK(cudaGetLastError());
@@ -233,6 +237,10 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
     c->tol = d->tol > 0 ? d->tol : 1e-12;
     c->max_outer = d->max_outer > 0 ? d->max_outer : 20;
     c->max_inner = d->max_inner > 0 ? d->max_inner : 30;
+    c->reuse_factor = d->reuse_factor ? 1 : 0;
+    c->reuse_max_inner = d->reuse_max_inner > 0 ? d->reuse_max_inner : 8;
+    c->reuse_max_stages = d->reuse_max_stages > 0 ? d->reuse_max_stages : 16;
+    c->warm_start = d->warm_start ? 1 : 0;
     {
         // enough column splits for about two CTAs per SM in the matrix-vector products
         auto splits = [&](int64_t rows_per_cta) {
@@ -471,6 +479,7 @@ nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *sh, do
     CK(cudaMemcpyAsync(c->d_B_save, c->d_B, sizeof(double) * 9 * c->nbodies,
                        cudaMemcpyDeviceToDevice, c->stream));
     nrs_status worst = NRS_OK;
+    const int64_t fact0 = c->factorizations;
     for (int stage = 0; stage < 2; ++stage) {
         const nrs_shapes *s = stage ? sh : s0;
         nrs::launch_kinematics(*c, (const D4 *)s->xi, (const D4 *)s->Xiw, (const D4 *)s->xidot,
@@ -488,14 +497,27 @@ nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *sh, do
         }
         if (ran || !c->seg_valid) nrs::launch_segments(*c, c->d_nn, c->d_seg_ptr, c->d_perm);
         c->seg_valid = true;
-        nrs_status st = do_segments_and_assemble(c, c->d_x, c->d_Xw);
+        const bool need_factor = !c->reuse_factor || c->factored_prec != c->factor_prec ||
+                                 c->stages_since_factor >= c->reuse_max_stages ||
+                                 c->last_inner > c->reuse_max_inner;
+        nrs_status st = do_segments_and_assemble(c, c->d_x, c->d_Xw, need_factor);
         if (st != NRS_OK) return st;
-        st = do_factor(c, c->factor_prec);
-        if (st != NRS_OK) return st;
+        if (need_factor) {
+            st = do_factor(c, c->factor_prec);
+            if (st != NRS_OK) return st;
+            c->stages_since_factor = 0;
+        } else {
+            c->stages_since_factor += 1;
+        }
         double *out = c->d_sol + (int64_t)stage * c->lda;
-        st = nrs::run_gmres_ir(*c, c->d_b, out, nullptr, report ? &report->stage[stage] : nullptr);
+        const double *x0 = (c->warm_start && c->have_sol) ? c->d_sol + (int64_t)(1 - stage) * c->lda
+                                                         : nullptr;
+        int inner = 0;
+        st = nrs::run_gmres_ir(*c, c->d_b, out, x0, report ? &report->stage[stage] : nullptr, &inner);
         if (st == NRS_ECUDA) return st;
         if (st != NRS_OK && worst == NRS_OK) worst = st;
+        c->last_inner = inner;
+        c->have_sol = true;
         nrs::launch_rk2(*c, stage, dt, out);
         CK(cudaGetLastError());
     }
@@ -510,6 +532,7 @@ nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *sh, do
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, ev0, ev1);
         report->ms_total = ms;
+        report->factorizations = (int32_t)(c->factorizations - fact0);
         cudaEventDestroy(ev0);
         cudaEventDestroy(ev1);
     }

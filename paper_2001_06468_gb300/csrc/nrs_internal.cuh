@@ -82,7 +82,7 @@ void launch_simt_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *C
 
 // ---- solve (solve.cu) ------------------------------------------------------
 nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0,
-                        nrs_solve_report *rep);
+                        nrs_solve_report *rep, int *inner_out = nullptr);
 
 struct Ctx {
     int device = 0;
@@ -135,6 +135,11 @@ struct Ctx {
     int32_t *d_info = nullptr;
     int factored_prec = -1;
     bool assembled = false;
+    // factor reuse across stages (nrs_step)
+    int reuse_factor = 0, reuse_max_inner = 8, reuse_max_stages = 16, warm_start = 0;
+    int stages_since_factor = 0, last_inner = 0;
+    bool have_sol = false;
+    int64_t factorizations = 0;
 
     // solve workspaces
     double *d_r = nullptr, *d_xk = nullptr, *d_w = nullptr, *d_V = nullptr, *d_H = nullptr;

@@ -511,7 +511,8 @@ static double read_scalar(Ctx &c, int slot, cudaError_t *err)
     return v;
 }
 
-nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0, nrs_solve_report *rep)
+nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0, nrs_solve_report *rep,
+                        int *inner_out)
 {
     const int64_t n = c.n;
     const int m = c.max_inner;
@@ -592,6 +593,7 @@ nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0, nr
     CKE(cudaMemcpyAsync(&st, c.d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
     CKE(cudaStreamSynchronize(c.stream));
     CKE(cudaMemsetAsync(c.d_status, 0, sizeof(int32_t), c.stream));  // reported: clear
+    if (inner_out) *inner_out = inner_total;
     if (rep) {
         // backward error ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf)
         gemv(c, x, b, c.d_r);

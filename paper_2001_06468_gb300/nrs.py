@@ -57,7 +57,11 @@ class ProblemDesc(ctypes.Structure):
                 ("nb", ctypes.c_int32),
                 ("tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int32),
-                ("max_inner", ctypes.c_int32)]
+                ("max_inner", ctypes.c_int32),
+                ("reuse_factor", ctypes.c_int32),
+                ("reuse_max_inner", ctypes.c_int32),
+                ("reuse_max_stages", ctypes.c_int32),
+                ("warm_start", ctypes.c_int32)]
 
 
 class SolveReport(ctypes.Structure):
@@ -70,7 +74,8 @@ class SolveReport(ctypes.Structure):
 
 
 class StepReport(ctypes.Structure):
-    _fields_ = [("stage", SolveReport * 2), ("ms_total", ctypes.c_double)]
+    _fields_ = [("stage", SolveReport * 2), ("ms_total", ctypes.c_double),
+                ("factorizations", ctypes.c_int32)]
 
 
 class Shapes(ctypes.Structure):
@@ -137,7 +142,8 @@ class Context:
                  eps: float, mu: float = 1.0, rigid: Optional[Sequence[int]] = None,
                  U=None, Omega=None, nn_global: bool = False, factor_prec: str = "fp32",
                  tol: float = 0.0, max_outer: int = 0, max_inner: int = 0,
-                 stream: Optional[torch.cuda.Stream] = None):
+                 reuse_factor: bool = False, reuse_max_inner: int = 0, reuse_max_stages: int = 0,
+                 warm_start: bool = False, stream: Optional[torch.cuda.Stream] = None):
         self._n_off = np.ascontiguousarray(n_off, dtype=np.int64)
         self._q_off = np.ascontiguousarray(q_off, dtype=np.int64)
         self._kind = np.ascontiguousarray(kind, dtype=np.int32)
@@ -159,6 +165,8 @@ class Context:
         d.nb = 0
         d.tol = float(tol)
         d.max_outer, d.max_inner = int(max_outer), int(max_inner)
+        d.reuse_factor, d.warm_start = int(bool(reuse_factor)), int(bool(warm_start))
+        d.reuse_max_inner, d.reuse_max_stages = int(reuse_max_inner), int(reuse_max_stages)
         self.stream = stream or torch.cuda.current_stream()
         self._h = ctypes.c_void_p()
         st = _lib.nrs_create(ctypes.byref(self._h), ctypes.byref(d),
@@ -281,7 +289,7 @@ class Context:
         if rep is None:
             return None
         return {"stages": [rep.stage[0].as_dict(), rep.stage[1].as_dict()], "ms": rep.ms_total,
-                "status": st}
+                "status": st, "factorizations": rep.factorizations}
 
     def sync(self):
         return self._check(_lib.nrs_sync(self._h))

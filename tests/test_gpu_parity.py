@@ -192,6 +192,33 @@ def test_consecutive_steps_match_oracle(N, name, prec):
     assert np.allclose(Yg["B"], Yo["B"], rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("prec", ["tf32", "fp64"])
+def test_factor_reuse_and_warm_start_keep_the_oracle_trajectory(N, prec):
+    # the previous stages' factor preconditions later stages; each solve still
+    # meets the FP64 residual, so the trajectory stays on the oracle's
+    pr = PROBLEMS["swimmer"]()
+    dt = 0.01
+    ctx, sh, Y, dev = _setup(N, pr, t=0.0, prec=prec, reuse_factor=True, warm_start=True)
+    Yo = Y
+    facts = 0
+    for k in range(3):
+        t = k * dt
+        d0 = N.shapes_to_device(g.pack_shapes(pr, t))
+        dh = N.shapes_to_device(g.pack_shapes(pr, t + 0.5 * dt))
+        sol = torch.empty(2 * pr.n, dtype=torch.float64, device="cuda")
+        rep = ctx.step(N.Context.shapes(*d0), N.Context.shapes(*dh), dt, sol=sol)
+        facts += rep["factorizations"]
+        Yn, stages = O.rk2_step(pr, Yo, t, dt, return_stages=True)
+        s = sol.cpu().numpy()
+        assert _rel(s[:pr.n], stages["sol1"]) <= TOL_SOL, rep
+        assert _rel(s[pr.n:], stages["sol2"]) <= TOL_SOL, rep
+        Yo = Yn
+    assert facts < 6  # at least one stage reused an earlier factor
+    Yg = ctx.get_state()
+    assert np.allclose(Yg["x0"], Yo["x0"], rtol=0, atol=1e-12)
+    assert np.allclose(Yg["B"], Yo["B"], rtol=0, atol=1e-12)
+
+
 def test_external_force_mobility(N):
     # rigid free body pushed by (F, M) from the oracle's resistance problem
     pr = PROBLEMS["swimmer_small"]()
