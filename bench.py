@@ -38,6 +38,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 from synth import geometry as g  # noqa: E402
+from synth import mlp_init  # noqa: E402
 
 METRIC = "s per timestep (assemble+solve) mixed-IR vs FP64 at 1e-10 rel err; pairs/s"
 WORKLOAD = "single free undulating swimmer, N=800 force / Q=8000 quadrature points, eps=0.005, n=2406"
@@ -45,6 +46,8 @@ L2_FLUSH_BYTES = 512 << 20
 FP64_NOMINAL_TFLOPS = 1.25       # GB300 FP64 (vector and tensor), nominal
 TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 tensor throughput
 SM_COUNT_NOMINAL = 152
+MLP_TRAIN_ITERS = 4              # Adam steps per stage for the learned starting vector
+MLP_LR = 3e-3
 FP32_LANES_PER_SM = 128
 
 
@@ -355,6 +358,35 @@ def run_nrs(args):
     reuse_reports = reports[nrep:]
     reuse_s = float(np.sum(r_ms)) / 1e3 / K / ws
 
+    # starting vectors of the refinement: cold (M^{-1} b), the previous stage's
+    # solution, and the MLP prediction (trained during the run, on every
+    # stage's solution; the timed steps include its training and selection)
+    starts = {}
+    for reuse in (False, True):
+        for mode in ("cold", "previous", "learned"):
+            ctx_s = nrs.Context.from_problem(pr, factor_prec=args.prec, reuse_factor=reuse,
+                                             warm_start=(mode == "previous"))
+            ctx_s.set_state(Y0["x0"], Y0["B"])
+            if mode == "learned":
+                ctx_s.mlp_set_params(mlp_init(0))
+                ctx_s.mlp_config(train_iters=MLP_TRAIN_ITERS, predict=False, lr=MLP_LR)
+            for s in range(W):
+                do_step(ctx_s, dev[s])
+            if mode == "learned":
+                ctx_s.mlp_config(train_iters=MLP_TRAIN_ITERS, predict=True, lr=MLP_LR)
+            torch.cuda.synchronize()
+            nrep = len(reports)
+            m_ms = timed_pass(ctx_s, W)
+            reps = reports[nrep:]
+            kinds = [k for r in reps for k in r["start"]]
+            starts[("reuse_" if reuse else "fresh_") + mode] = {
+                "s_per_step": float(np.sum(m_ms)) / 1e3 / K / ws,
+                "inner_mean": float(np.mean([r["stages"][i]["inner"] for r in reps for i in (0, 1)])),
+                "starts_used": {k: kinds.count(k) for k in sorted(set(kinds))},
+                "mlp_rel_err_last": reps[-1]["mlp_rel_err"] if mode == "learned" else None,
+            }
+            ctx_s.close()
+
     # the first steps from the initial state, kept for the accuracy check
     # (fresh factor every stage, and factor reuse)
     sols = {}
@@ -408,6 +440,11 @@ def run_nrs(args):
                          "inner_mean": float(np.mean([r["stages"][i]["inner"] for r in reuse_reports for i in (0, 1)])),
                          "note": "the previous stages' factor preconditions the refinement until its GMRES "
                                  "count exceeds 8 or 16 stages pass; each solve from the previous solution"},
+        "starts": starts,
+        "starts_note": ("fresh_*: factor every stage; reuse_*: factor reuse. learned: "
+                        f"{MLP_TRAIN_ITERS} Adam steps per stage (lr {MLP_LR}) on each stage's "
+                        "solution, prediction used only where its residual beats the cold start's; "
+                        "mlp_rel_err_last = held-out relative RMS error of the prediction of f"),
         "phases_ms_per_step": {k: v / K for k, v in ph_ms.items()},
         "phase_share": {k: (v / tot if tot else 0.0) for k, v in ph_ms.items()},
         "phase_note": "lu_diag runs on a second stream, overlapping lu_update and lu_panel",

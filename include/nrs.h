@@ -108,6 +108,13 @@ typedef struct {
     nrs_solve_report stage[2];
     double ms_total;        /* device time of the step (CUDA events)          */
     int32_t factorizations; /* factorisations done in this step (0..2)        */
+    int32_t start[2];       /* start of each stage's refinement: 0 = M^{-1} b (cold),
+                               1 = the previous stage's solution (warm_start),
+                               2 = the MLP prediction (nrs_mlp_config)          */
+    double mlp_rel_err;     /* relative RMS error sqrt(sum (y - t)^2 / sum t^2) of the
+                               MLP on the targets of the step's last training stage,
+                               before that stage's updates (a held-out error);
+                               -1 if the step did not train                     */
 } nrs_step_report;
 
 /* Body-frame inputs of one stage (device memory):
@@ -256,6 +263,78 @@ nrs_status nrs_sync(nrs_ctx *ctx);
 nrs_status nrs_nearest_build_static(const double *x, const double *Xw, int32_t nbodies,
                                     const int64_t *n_off, const int64_t *q_off, int32_t global,
                                     int32_t *nn, int32_t *seg_ptr, int32_t *perm, void *stream);
+
+/* ---- learned starting guess -------------------------------------------------
+ * The paper has no learned component: this is an extension of the refinement
+ * of Sec. 4 step 3, whose start vector it predicts from the stage's geometry.
+ * It never changes what the refinement converges to.
+ *
+ * A point-wise MLP, 17 -> 64 -> SiLU -> 64 -> SiLU -> 3 (SiLU(z) = z/(1+e^-z)),
+ * maps the features of force point m of body b (body frame) to B^T f_m / F:
+ *   0-2 xi_m/L, 3-5 xidot_m/V, 6 s = (m - n_off[b]) / max(1, N_b - 1),
+ *   7 W_m / mean over body b of W, 8-10 one-hot kind (free, prescribed, static),
+ *   11-13 B^T U / V, 14-16 B^T Omega L / V,
+ * (U, Omega) = the previous stage's solution (free body), the prescribed
+ * motion (prescribed body) or zero (static body); W_m = sum of the
+ * quadrature weights of segment m (Sec. 3).  Scales L, V, F: given by
+ * nrs_mlp_config, or taken from the first training sample as L = max |xi_m|,
+ * V = max |b_m| over the force rows of the right-hand side, F = RMS of |f_m|.
+ * Parameters (FP32, NRS_MLP_PARAMS): W1 [64][17] row-major, b1 [64],
+ * W2 [64][64], b2 [64], W3 [3][64], b3 [3].  Loss: mean squared error over
+ * points and components.  Optimiser: Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * Sums over points run in a fixed order: results are deterministic. */
+#define NRS_MLP_IN 17
+#define NRS_MLP_HID 64
+#define NRS_MLP_OUT 3
+#define NRS_MLP_PARAMS (NRS_MLP_HID * NRS_MLP_IN + NRS_MLP_HID + NRS_MLP_HID * NRS_MLP_HID + \
+                        NRS_MLP_HID + NRS_MLP_OUT * NRS_MLP_HID + NRS_MLP_OUT)
+
+/* Load the MLP state (host arrays of NRS_MLP_PARAMS floats): parameters, and
+ * the Adam moments (NULL = zero) after t Adam steps (t >= 0).  The first
+ * nrs_mlp_* call on a context allocates the MLP workspaces (about 1 KB per
+ * force point).  NRS_EINVAL for a NULL params or t < 0. */
+nrs_status nrs_mlp_set_params(nrs_ctx *ctx, const float *params, const float *adam_m,
+                              const float *adam_v, int32_t t);
+
+/* Synchronise and copy the MLP state out (host; each may be NULL): parameters,
+ * Adam moments, the step count and the scales (L, V, F; zeros if not set). */
+nrs_status nrs_mlp_get_params(nrs_ctx *ctx, float *params, float *adam_m, float *adam_v,
+                              int32_t *t, double *scales);
+
+/* Use the MLP inside nrs_step.  train_iters > 0: after each stage's solve,
+ * that many Adam steps (learning rate lr) on the stage's features and solved
+ * f.  predict != 0: each stage's refinement starts from the prediction
+ * (f_m = F B y_m; (U, Omega) of the previous stage) or from the cold start
+ * M^{-1} b, whichever has the smaller ||b - A x||_inf; and after a stage
+ * that started from the prediction and needed more GMRES iterations than the
+ * running mean of the cold-started stages plus 2, the prediction is skipped
+ * for the next 8 stages.  The prediction replaces warm_start while enabled.
+ * scales (host [3] or NULL): L, V, F; NULL keeps the current ones, or takes
+ * them from the first training sample.  NRS_EINVAL when parameters were not
+ * set, lr <= 0 with training, or prediction without scales or training. */
+nrs_status nrs_mlp_config(nrs_ctx *ctx, int32_t train_iters, int32_t predict, float lr,
+                          const double *scales);
+
+/* One evaluation on caller data (device): X [npts*17] features, Y [npts*3]
+ * outputs; with T [npts*3] targets also the loss (host double, may be NULL;
+ * synchronises) and, if G [NRS_MLP_PARAMS] is not NULL, the gradient of the
+ * loss with respect to the parameters.  1 <= npts <= N of the context. */
+nrs_status nrs_mlp_eval(nrs_ctx *ctx, const float *X, const float *T, int64_t npts, float *Y,
+                        float *G, double *loss);
+
+/* One Adam step with the gradient G (device [NRS_MLP_PARAMS]). */
+nrs_status nrs_mlp_adam(nrs_ctx *ctx, const float *G, float lr);
+
+/* Features X (device [N*17]) of the shapes s (xi, xidot used) with the
+ * context's state, the W_n of the last nrs_assemble and previous rigid
+ * velocities vprev (device [6F] or NULL = zero); with sol (device [n]) also
+ * the targets T (device [N*3]).  Needs the scales (nrs_mlp_config). */
+nrs_status nrs_mlp_features(nrs_ctx *ctx, const nrs_shapes *s, const double *vprev,
+                            const double *sol, float *X, float *T);
+
+/* Start vector x0 (device [n]) from predictions Y (device [N*3]): f_m = F B y_m
+ * with the context's B, then (U, Omega) = vprev (device [6F] or NULL = zero). */
+nrs_status nrs_mlp_start(nrs_ctx *ctx, const float *Y, const double *vprev, double *x0);
 
 /* Phases of the step, as timed by nrs_get_timing. */
 enum {

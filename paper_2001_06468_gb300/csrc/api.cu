@@ -3,6 +3,7 @@
 // The host code here validates arguments, owns the device workspaces and
 // enqueues kernels; every arithmetic step of the method runs in the kernels
 // of geometry.cu, assemble.cu, lu.cu, tc_gemm.cu and solve.cu.
+#include <math.h>
 #include <string.h>
 
 #include <new>
@@ -115,6 +116,14 @@ void free_all(Ctx *c)
                     c->d_gj_rt,  c->d_gj_cb};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    void *mlp[] = {c->d_mlp_params, c->d_mlp_m,  c->d_mlp_v,     c->d_mlp_g,    c->d_mlp_x,
+                   c->d_mlp_t,      c->d_mlp_y,  c->d_mlp_z1,    c->d_mlp_z2,   c->d_mlp_dy,
+                   c->d_mlp_d1,     c->d_mlp_d2, c->d_mlp_part,  c->d_mlp_wmean, c->d_mlp_scal,
+                   c->d_mlp_xp,     c->d_mlp_xc, c->d_mlp_x0,    c->d_mlp_used};
+    for (void *p : mlp)
+        if (p) cudaFree(p);
+    if (c->h_mlp_used) cudaFreeHost(c->h_mlp_used);
+    if (c->h_mlp_loss) cudaFreeHost(c->h_mlp_loss);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     c->ev_pool.clear();
     if (c->ev_prep) cudaEventDestroy(c->ev_prep);
@@ -181,6 +190,51 @@ nrs_status do_segments_and_assemble(Ctx *c, const D4 *x_lab, const D4 *Xw_lab, b
     CK(cudaGetLastError());
     c->a32_fresh = a32 != nullptr;
     c->assembled = true;
+    return NRS_OK;
+}
+
+// Workspaces of the learned starting guess, allocated by the first nrs_mlp_* call.
+nrs_status mlp_alloc(Ctx *c)
+{
+    if (c->mlp_alloc) return NRS_OK;
+    const int64_t N = c->N, P = NRS_MLP_PARAMS, H = NRS_MLP_HID;
+    struct {
+        void **p;
+        size_t bytes;
+    } req[] = {
+        {(void **)&c->d_mlp_params, sizeof(float) * P},
+        {(void **)&c->d_mlp_m, sizeof(float) * P},
+        {(void **)&c->d_mlp_v, sizeof(float) * P},
+        {(void **)&c->d_mlp_g, sizeof(float) * P},
+        {(void **)&c->d_mlp_x, sizeof(float) * N * NRS_MLP_IN},
+        {(void **)&c->d_mlp_t, sizeof(float) * N * NRS_MLP_OUT},
+        {(void **)&c->d_mlp_y, sizeof(float) * N * NRS_MLP_OUT},
+        {(void **)&c->d_mlp_z1, sizeof(float) * N * H},
+        {(void **)&c->d_mlp_z2, sizeof(float) * N * H},
+        {(void **)&c->d_mlp_dy, sizeof(float) * N * NRS_MLP_OUT},
+        {(void **)&c->d_mlp_d1, sizeof(float) * N * H},
+        {(void **)&c->d_mlp_d2, sizeof(float) * N * H},
+        {(void **)&c->d_mlp_part, sizeof(float) * P * nrs::mlp_grad_chunks(N)},
+        {(void **)&c->d_mlp_wmean, sizeof(double) * c->nbodies},
+        {(void **)&c->d_mlp_scal, sizeof(double) * 8},
+        {(void **)&c->d_mlp_xp, sizeof(double) * c->lda},
+        {(void **)&c->d_mlp_xc, sizeof(double) * c->lda},
+        {(void **)&c->d_mlp_x0, sizeof(double) * c->lda},
+        {(void **)&c->d_mlp_used, sizeof(int32_t) * 2},
+    };
+    for (auto &r : req) {
+        cudaError_t e = cudaMalloc(r.p, r.bytes ? r.bytes : 1);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *r.p = nullptr;
+            return fail(c, NRS_ENOMEM, "MLP workspace allocation failed");
+        }
+    }
+    CK(cudaHostAlloc((void **)&c->h_mlp_used, sizeof(int32_t) * 2, cudaHostAllocDefault));
+    CK(cudaHostAlloc((void **)&c->h_mlp_loss, sizeof(double) * 2, cudaHostAllocDefault));
+    CK(cudaMemsetAsync(c->d_mlp_scal, 0, sizeof(double) * 8, c->stream));
+    CK(cudaMemsetAsync(c->d_mlp_used, 0, sizeof(int32_t) * 2, c->stream));
+    c->mlp_alloc = true;
     return NRS_OK;
 }
 
@@ -480,6 +534,8 @@ nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *sh, do
                        cudaMemcpyDeviceToDevice, c->stream));
     nrs_status worst = NRS_OK;
     const int64_t fact0 = c->factorizations;
+    bool trained = false;
+    if (report) report->mlp_rel_err = -1.0;
     for (int stage = 0; stage < 2; ++stage) {
         const nrs_shapes *s = stage ? sh : s0;
         nrs::launch_kinematics(*c, (const D4 *)s->xi, (const D4 *)s->Xiw, (const D4 *)s->xidot,
@@ -510,12 +566,62 @@ nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *sh, do
             c->stages_since_factor += 1;
         }
         double *out = c->d_sol + (int64_t)stage * c->lda;
-        const double *x0 = (c->warm_start && c->have_sol) ? c->d_sol + (int64_t)(1 - stage) * c->lda
-                                                         : nullptr;
+        const double *prev = c->have_sol ? c->d_sol + (int64_t)(1 - stage) * c->lda : nullptr;
+        const double *vprev = (prev && c->F) ? prev + 3 * c->N : nullptr;
+        const double *x0 = (c->warm_start && prev) ? prev : nullptr;
+        int start = x0 ? 1 : 0;
+        // learned starting guess: prediction or cold start, whichever has the smaller residual
+        bool learned = false;
+        if (c->mlp_predict && c->mlp_scales_set) {
+            if (c->mlp_backoff > 0) {
+                c->mlp_backoff -= 1;
+            } else {
+                learned = true;
+                nrs::mlp_features(*c, (const D4 *)s->xi, (const D4 *)s->xidot, vprev, nullptr,
+                                  c->d_mlp_x, nullptr);
+                nrs::mlp_eval(*c, c->d_mlp_x, c->N, nullptr, c->d_mlp_y, nullptr, nullptr);
+                nrs::mlp_start(*c, c->d_mlp_y, vprev, c->d_mlp_xp);
+                CK(nrs::choose_start(*c, c->d_b, c->d_mlp_xp, c->d_mlp_xc, c->d_mlp_x0,
+                                     c->d_mlp_scal + 3));
+                CK(cudaMemcpyAsync(c->h_mlp_used, c->d_mlp_used, sizeof(int32_t) * 2,
+                                   cudaMemcpyDeviceToHost, c->stream));
+                x0 = c->d_mlp_x0;
+                start = 0;
+            }
+        }
         int inner = 0;
         st = nrs::run_gmres_ir(*c, c->d_b, out, x0, report ? &report->stage[stage] : nullptr, &inner);
         if (st == NRS_ECUDA) return st;
         if (st != NRS_OK && worst == NRS_OK) worst = st;
+        // run_gmres_ir synchronised the stream: the pinned copy of the choice has landed
+        if (learned && c->h_mlp_used[0]) {
+            start = 2;
+            if (c->cold_inner_cnt > 0 &&
+                inner > c->cold_inner_sum / (double)c->cold_inner_cnt + 2.0)
+                c->mlp_backoff = 8;
+        }
+        if (start == 0) {
+            c->cold_inner_sum += inner;
+            c->cold_inner_cnt += 1;
+        }
+        if (report) report->start[stage] = start;
+        if (c->mlp_train_iters > 0 && st == NRS_OK) {
+            if (!c->mlp_scales_set) {
+                nrs::mlp_scales(*c, (const D4 *)s->xi, c->d_b, out, c->d_mlp_scal);
+                c->mlp_scales_set = true;
+            }
+            nrs::mlp_features(*c, (const D4 *)s->xi, (const D4 *)s->xidot, vprev, out, c->d_mlp_x,
+                              c->d_mlp_t);
+            if (report) {  // error on this stage before training on it (held out)
+                nrs::mlp_eval(*c, c->d_mlp_x, c->N, c->d_mlp_t, c->d_mlp_y, nullptr,
+                              c->d_mlp_scal + 5);
+                CK(cudaMemcpyAsync(c->h_mlp_loss, c->d_mlp_scal + 5, sizeof(double) * 2,
+                                   cudaMemcpyDeviceToHost, c->stream));
+                trained = true;
+            }
+            for (int it = 0; it < c->mlp_train_iters; ++it)
+                nrs::mlp_train_step(*c, c->d_mlp_x, c->N, c->d_mlp_t, nullptr, c->mlp_lr);
+        }
         c->last_inner = inner;
         c->have_sol = true;
         nrs::launch_rk2(*c, stage, dt, out);
@@ -533,6 +639,9 @@ nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *sh, do
         cudaEventElapsedTime(&ms, ev0, ev1);
         report->ms_total = ms;
         report->factorizations = (int32_t)(c->factorizations - fact0);
+        if (trained)
+            report->mlp_rel_err = c->h_mlp_loss[1] > 0.0 ? sqrt(c->h_mlp_loss[0] / c->h_mlp_loss[1])
+                                                         : 0.0;
         cudaEventDestroy(ev0);
         cudaEventDestroy(ev1);
     }
@@ -592,6 +701,121 @@ nrs_status nrs_rank64_update(nrs_ctx *ctx, float *M, int64_t lda, int64_t n, con
     } else {
         return fail(c, NRS_EINVAL, "nrs_rank64_update: precision must be NRS_FP32 or NRS_TF32");
     }
+    CK(cudaGetLastError());
+    return NRS_OK;
+}
+
+nrs_status nrs_mlp_set_params(nrs_ctx *ctx, const float *params, const float *adam_m,
+                              const float *adam_v, int32_t t)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !params || t < 0) return fail(c, NRS_EINVAL, "nrs_mlp_set_params: bad argument");
+    nrs_status st = mlp_alloc(c);
+    if (st != NRS_OK) return st;
+    const size_t bytes = sizeof(float) * NRS_MLP_PARAMS;
+    CK(cudaMemcpyAsync(c->d_mlp_params, params, bytes, cudaMemcpyHostToDevice, c->stream));
+    if (adam_m) CK(cudaMemcpyAsync(c->d_mlp_m, adam_m, bytes, cudaMemcpyHostToDevice, c->stream));
+    else CK(cudaMemsetAsync(c->d_mlp_m, 0, bytes, c->stream));
+    if (adam_v) CK(cudaMemcpyAsync(c->d_mlp_v, adam_v, bytes, cudaMemcpyHostToDevice, c->stream));
+    else CK(cudaMemsetAsync(c->d_mlp_v, 0, bytes, c->stream));
+    CK(cudaStreamSynchronize(c->stream));  // the host arrays may be freed on return
+    c->mlp_t = t;
+    c->mlp_params_set = true;
+    c->mlp_backoff = 0;
+    return NRS_OK;
+}
+
+nrs_status nrs_mlp_get_params(nrs_ctx *ctx, float *params, float *adam_m, float *adam_v,
+                              int32_t *t, double *scales)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return NRS_EINVAL;
+    if (!c->mlp_params_set) return fail(c, NRS_EINVAL, "nrs_mlp_get_params: no parameters set");
+    const size_t bytes = sizeof(float) * NRS_MLP_PARAMS;
+    CK(cudaStreamSynchronize(c->stream));
+    if (params) CK(cudaMemcpy(params, c->d_mlp_params, bytes, cudaMemcpyDeviceToHost));
+    if (adam_m) CK(cudaMemcpy(adam_m, c->d_mlp_m, bytes, cudaMemcpyDeviceToHost));
+    if (adam_v) CK(cudaMemcpy(adam_v, c->d_mlp_v, bytes, cudaMemcpyDeviceToHost));
+    if (t) *t = c->mlp_t;
+    if (scales) CK(cudaMemcpy(scales, c->d_mlp_scal, sizeof(double) * 3, cudaMemcpyDeviceToHost));
+    return NRS_OK;
+}
+
+nrs_status nrs_mlp_config(nrs_ctx *ctx, int32_t train_iters, int32_t predict, float lr,
+                          const double *scales)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || train_iters < 0) return fail(c, NRS_EINVAL, "nrs_mlp_config: bad argument");
+    if (!c->mlp_params_set) return fail(c, NRS_EINVAL, "nrs_mlp_config: no parameters set");
+    if (train_iters > 0 && !(lr > 0.0f)) return fail(c, NRS_EINVAL, "nrs_mlp_config: lr <= 0");
+    if (scales) {
+        for (int k = 0; k < 3; ++k)
+            if (!(scales[k] > 0.0) || !(scales[k] < 1e300))
+                return fail(c, NRS_EINVAL, "nrs_mlp_config: scales must be positive and finite");
+        CK(cudaMemcpyAsync(c->d_mlp_scal, scales, sizeof(double) * 3, cudaMemcpyHostToDevice,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        c->mlp_scales_set = true;
+    }
+    if (predict && !c->mlp_scales_set && train_iters == 0)
+        return fail(c, NRS_EINVAL, "nrs_mlp_config: prediction needs scales or training");
+    c->mlp_train_iters = train_iters;
+    c->mlp_predict = predict ? 1 : 0;
+    c->mlp_lr = lr;
+    c->mlp_backoff = 0;
+    return NRS_OK;
+}
+
+nrs_status nrs_mlp_eval(nrs_ctx *ctx, const float *X, const float *T, int64_t npts, float *Y,
+                        float *G, double *loss)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !X || !Y || npts <= 0) return fail(c, NRS_EINVAL, "nrs_mlp_eval: bad argument");
+    if (!c->mlp_params_set) return fail(c, NRS_EINVAL, "nrs_mlp_eval: no parameters set");
+    if (npts > c->N) return fail(c, NRS_EINVAL, "nrs_mlp_eval: npts exceeds the context's N");
+    if ((G || loss) && !T) return fail(c, NRS_EINVAL, "nrs_mlp_eval: gradient or loss needs T");
+    nrs::mlp_eval(*c, X, npts, T, Y, G, loss ? c->d_mlp_scal + 5 : nullptr);
+    CK(cudaGetLastError());
+    if (loss) {
+        CK(cudaMemcpyAsync(c->h_mlp_loss, c->d_mlp_scal + 5, sizeof(double),
+                           cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        *loss = *c->h_mlp_loss;
+    }
+    return NRS_OK;
+}
+
+nrs_status nrs_mlp_adam(nrs_ctx *ctx, const float *G, float lr)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !G || !(lr > 0.0f)) return fail(c, NRS_EINVAL, "nrs_mlp_adam: bad argument");
+    if (!c->mlp_params_set) return fail(c, NRS_EINVAL, "nrs_mlp_adam: no parameters set");
+    nrs::mlp_adam(*c, G, lr);
+    CK(cudaGetLastError());
+    return NRS_OK;
+}
+
+nrs_status nrs_mlp_features(nrs_ctx *ctx, const nrs_shapes *s, const double *vprev,
+                            const double *sol, float *X, float *T)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !s || !s->xi || !s->xidot || !X || (T && !sol))
+        return fail(c, NRS_EINVAL, "nrs_mlp_features: bad argument");
+    if (!c->mlp_alloc || !c->mlp_scales_set)
+        return fail(c, NRS_EINVAL, "nrs_mlp_features: scales not set");
+    if (!c->assembled) return fail(c, NRS_EINVAL, "nrs_mlp_features before nrs_assemble");
+    nrs::mlp_features(*c, (const D4 *)s->xi, (const D4 *)s->xidot, vprev, sol, X, T);
+    CK(cudaGetLastError());
+    return NRS_OK;
+}
+
+nrs_status nrs_mlp_start(nrs_ctx *ctx, const float *Y, const double *vprev, double *x0)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !Y || !x0) return fail(c, NRS_EINVAL, "nrs_mlp_start: bad argument");
+    if (!c->mlp_alloc || !c->mlp_scales_set)
+        return fail(c, NRS_EINVAL, "nrs_mlp_start: scales not set");
+    nrs::mlp_start(*c, Y, vprev, x0);
     CK(cudaGetLastError());
     return NRS_OK;
 }

@@ -83,6 +83,25 @@ void launch_simt_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *C
 // ---- solve (solve.cu) ------------------------------------------------------
 nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0,
                         nrs_solve_report *rep, int *inner_out = nullptr);
+// x0 = whichever of xp and the cold start xc = M^{-1} b has the smaller
+// ||b - A x||_inf (norms[0], norms[1]); c.d_mlp_used[0] records the choice.
+cudaError_t choose_start(Ctx &c, const double *b, const double *xp, double *xc, double *x0,
+                         double *norms);
+
+// ---- learned starting guess (mlp.cu) ---------------------------------------
+void mlp_eval(Ctx &c, const float *X, int64_t npts, const float *T, float *Y, float *G,
+              double *loss_dev);
+void mlp_adam(Ctx &c, const float *G, float lr);
+// one training iteration: forward, backward, gradient (into G if not NULL)
+// and, for lr > 0, an Adam step
+void mlp_train_step(Ctx &c, const float *X, int64_t npts, const float *T, float *G, float lr,
+                    float *Y = nullptr);
+void mlp_scales(Ctx &c, const D4 *xi, const double *b, const double *sol, double *out);
+void mlp_features(Ctx &c, const D4 *xi, const D4 *xidot, const double *vprev, const double *sol,
+                  float *X, float *T);
+void mlp_start(Ctx &c, const float *Y, const double *vprev, double *x0);
+void pick_start(Ctx &c, const double *xp, const double *xc, const double *norms, double *x0);
+int mlp_grad_chunks(int64_t npts);
 
 struct Ctx {
     int device = 0;
@@ -140,6 +159,25 @@ struct Ctx {
     int stages_since_factor = 0, last_inner = 0;
     bool have_sol = false;
     int64_t factorizations = 0;
+
+    // learned starting guess (mlp.cu); allocated by the first nrs_mlp_* call
+    bool mlp_alloc = false, mlp_params_set = false, mlp_scales_set = false;
+    float *d_mlp_params = nullptr, *d_mlp_m = nullptr, *d_mlp_v = nullptr, *d_mlp_g = nullptr;
+    float *d_mlp_x = nullptr, *d_mlp_t = nullptr, *d_mlp_y = nullptr;   // features, targets, output
+    float *d_mlp_z1 = nullptr, *d_mlp_z2 = nullptr;                      // pre-activations
+    float *d_mlp_dy = nullptr, *d_mlp_d1 = nullptr, *d_mlp_d2 = nullptr; // back-propagated terms
+    float *d_mlp_part = nullptr;    // per-chunk partial gradients
+    double *d_mlp_wmean = nullptr;  // mean W_n per body
+    double *d_mlp_scal = nullptr;   // [0..2] scales L, V, F; [3..4] residual norms;
+                                    // [5] loss, [6] mean square of the targets
+    double *d_mlp_xp = nullptr, *d_mlp_xc = nullptr, *d_mlp_x0 = nullptr;  // start vectors
+    int32_t *d_mlp_used = nullptr;  // [0] prediction chosen, [1] prediction not finite
+    int32_t *h_mlp_used = nullptr;  // pinned host copy of d_mlp_used
+    double *h_mlp_loss = nullptr;   // pinned host copy of the loss and mean square target
+    int mlp_t = 0, mlp_train_iters = 0, mlp_predict = 0, mlp_backoff = 0;
+    float mlp_lr = 1e-3f;
+    double cold_inner_sum = 0.0;
+    int64_t cold_inner_cnt = 0;
 
     // solve workspaces
     double *d_r = nullptr, *d_xk = nullptr, *d_w = nullptr, *d_V = nullptr, *d_H = nullptr;

@@ -511,6 +511,24 @@ static double read_scalar(Ctx &c, int slot, cudaError_t *err)
     return v;
 }
 
+cudaError_t choose_start(Ctx &c, const double *b, const double *xp, double *xc, double *x0,
+                         double *norms)
+{
+    cudaError_t e = apply_precond(c, b, xc);
+    if (e != cudaSuccess) return e;
+    gemv(c, xp, b, c.d_r);
+    c.tbeg(PH_KRYLOV);
+    k_nrm_inf<<<1, RED_THREADS, 0, c.stream>>>(c.n, c.d_r, norms, 0);
+    c.tend(PH_KRYLOV);
+    gemv(c, xc, b, c.d_r);
+    c.tbeg(PH_KRYLOV);
+    k_nrm_inf<<<1, RED_THREADS, 0, c.stream>>>(c.n, c.d_r, norms, 1);
+    pick_start(c, xp, xc, norms, x0);
+    c.tend(PH_KRYLOV);
+    c.launches += 2;
+    return cudaGetLastError();
+}
+
 nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0, nrs_solve_report *rep,
                         int *inner_out)
 {

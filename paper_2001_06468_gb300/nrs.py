@@ -37,7 +37,13 @@ FREE, PRESCRIBED, STATIC = 0, 1, 2
 EXPORTS = ["nrs_create", "nrs_destroy", "nrs_last_error", "nrs_sizes", "nrs_set_state",
            "nrs_get_state", "nrs_set_external", "nrs_kinematics", "nrs_nearest_build",
            "nrs_assemble", "nrs_factor", "nrs_solve", "nrs_step", "nrs_sync", "nrs_set_timing",
-           "nrs_get_timing", "nrs_rank64_update", "nrs_nearest_build_static"]
+           "nrs_get_timing", "nrs_rank64_update", "nrs_nearest_build_static",
+           "nrs_mlp_set_params", "nrs_mlp_get_params", "nrs_mlp_config", "nrs_mlp_eval",
+           "nrs_mlp_adam", "nrs_mlp_features", "nrs_mlp_start"]
+# the learned starting guess (NRS_MLP_* in include/nrs.h)
+MLP_IN, MLP_HID, MLP_OUT = 17, 64, 3
+MLP_PARAMS = MLP_HID * MLP_IN + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_OUT * MLP_HID + MLP_OUT
+START_KINDS = {0: "cold", 1: "previous", 2: "learned"}
 PHASES = ["kinematics", "nearest", "segments", "assemble", "border", "convert", "lu_panel",
           "lu_update", "trsv", "gemv", "krylov", "update", "lu_diag"]
 
@@ -75,7 +81,8 @@ class SolveReport(ctypes.Structure):
 
 class StepReport(ctypes.Structure):
     _fields_ = [("stage", SolveReport * 2), ("ms_total", ctypes.c_double),
-                ("factorizations", ctypes.c_int32)]
+                ("factorizations", ctypes.c_int32), ("start", ctypes.c_int32 * 2),
+                ("mlp_rel_err", ctypes.c_double)]
 
 
 class Shapes(ctypes.Structure):
@@ -106,6 +113,14 @@ _sig = {
     "nrs_nearest_build_static": (ctypes.c_int, [_P, _P, ctypes.c_int32, _I64P, _I64P, ctypes.c_int32,
                                                 _P, _P, _P, _P]),
     "nrs_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), _I64P, _I64P]),
+    "nrs_mlp_set_params": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32]),
+    "nrs_mlp_get_params": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int32), _P]),
+    "nrs_mlp_config": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _P]),
+    "nrs_mlp_eval": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P,
+                                    ctypes.POINTER(ctypes.c_double)]),
+    "nrs_mlp_adam": (ctypes.c_int, [_P, _P, ctypes.c_float]),
+    "nrs_mlp_features": (ctypes.c_int, [_P, ctypes.POINTER(Shapes), _P, _P, _P, _P]),
+    "nrs_mlp_start": (ctypes.c_int, [_P, _P, _P, _P]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
@@ -289,7 +304,10 @@ class Context:
         if rep is None:
             return None
         return {"stages": [rep.stage[0].as_dict(), rep.stage[1].as_dict()], "ms": rep.ms_total,
-                "status": st, "factorizations": rep.factorizations}
+                "status": st, "factorizations": rep.factorizations,
+                "start": [START_KINDS.get(rep.start[0], rep.start[0]),
+                          START_KINDS.get(rep.start[1], rep.start[1])],
+                "mlp_rel_err": rep.mlp_rel_err}
 
     def sync(self):
         return self._check(_lib.nrs_sync(self._h))
@@ -301,6 +319,66 @@ class Context:
         self._check(_lib.nrs_rank64_update(self._h, _ptr(Mt, torch.float32), Mt.shape[1], n,
                                            _ptr(C, torch.float32), _ptr(Rt, torch.float32),
                                            PREC[prec]))
+
+    # -- learned starting guess ---------------------------------------------
+    def mlp_set_params(self, params, adam_m=None, adam_v=None, t: int = 0):
+        """Load the MLP parameters (and Adam state) from host arrays."""
+        def f32(a):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float32).reshape(MLP_PARAMS)
+            return a
+        p, m, v = f32(params), f32(adam_m), f32(adam_v)
+        self._check(_lib.nrs_mlp_set_params(self._h, p.ctypes.data,
+                                            None if m is None else m.ctypes.data,
+                                            None if v is None else v.ctypes.data, int(t)))
+
+    def mlp_get_params(self):
+        """{'params', 'adam_m', 'adam_v', 't', 'scales'} (host copies)."""
+        p = np.empty(MLP_PARAMS, np.float32)
+        m = np.empty(MLP_PARAMS, np.float32)
+        v = np.empty(MLP_PARAMS, np.float32)
+        sc = np.empty(3, np.float64)
+        t = ctypes.c_int32()
+        self._check(_lib.nrs_mlp_get_params(self._h, p.ctypes.data, m.ctypes.data, v.ctypes.data,
+                                            ctypes.byref(t), sc.ctypes.data))
+        return {"params": p, "adam_m": m, "adam_v": v, "t": t.value, "scales": sc}
+
+    def mlp_config(self, train_iters: int = 0, predict: bool = False, lr: float = 1e-3,
+                   scales=None):
+        sc = None if scales is None else np.ascontiguousarray(scales, dtype=np.float64).reshape(3)
+        self._check(_lib.nrs_mlp_config(self._h, int(train_iters), int(bool(predict)), float(lr),
+                                        None if sc is None else sc.ctypes.data))
+
+    def mlp_eval(self, X: torch.Tensor, T: Optional[torch.Tensor] = None, grad: bool = False,
+                 loss: bool = False):
+        """Forward (and, with T, loss and gradient) on device features X (npts, 17)."""
+        npts = X.shape[0]
+        Y = torch.empty((npts, MLP_OUT), dtype=torch.float32, device=X.device)
+        G = torch.empty(MLP_PARAMS, dtype=torch.float32, device=X.device) if grad else None
+        lo = ctypes.c_double(0.0)
+        self._check(_lib.nrs_mlp_eval(self._h, _ptr(X, torch.float32), _ptr(T, torch.float32),
+                                      npts, _ptr(Y), _ptr(G),
+                                      ctypes.byref(lo) if loss else None))
+        return Y, G, (lo.value if loss else None)
+
+    def mlp_adam(self, G: torch.Tensor, lr: float):
+        self._check(_lib.nrs_mlp_adam(self._h, _ptr(G, torch.float32), float(lr)))
+
+    def mlp_features(self, s: Shapes, vprev: Optional[torch.Tensor] = None,
+                     sol: Optional[torch.Tensor] = None, device="cuda"):
+        """Features (N, 17) of the shapes s and, with sol, the targets (N, 3)."""
+        X = torch.empty((self.N, MLP_IN), dtype=torch.float32, device=device)
+        T = torch.empty((self.N, MLP_OUT), dtype=torch.float32, device=device) if sol is not None else None
+        self._check(_lib.nrs_mlp_features(self._h, ctypes.byref(s), _ptr(vprev, torch.float64),
+                                          _ptr(sol, torch.float64), _ptr(X), _ptr(T)))
+        return X, T
+
+    def mlp_start(self, Y: torch.Tensor, vprev: Optional[torch.Tensor] = None):
+        x0 = torch.empty(self.n, dtype=torch.float64, device=Y.device)
+        self._check(_lib.nrs_mlp_start(self._h, _ptr(Y, torch.float32), _ptr(vprev, torch.float64),
+                                       _ptr(x0)))
+        return x0
 
     def set_timing(self, enable: bool = True):
         self._check(_lib.nrs_set_timing(self._h, int(bool(enable))))

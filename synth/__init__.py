@@ -27,3 +27,4 @@ from .geometry import (  # noqa: F401
     initial_state,
     WORKLOADS,
 )
+from .mlp_inputs import mlp_init, mlp_batch, mlp_perturb  # noqa: F401,E402

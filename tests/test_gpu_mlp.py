@@ -1,0 +1,243 @@
+"""Parity of the learned starting guess (CUDA, through the C ABI) with the
+FP64 oracle MLP, and its use inside the time step.
+
+Tolerances follow from the arithmetic.  The kernels evaluate the network in
+FP32 (dot products of at most 64 terms with fused multiply-adds, CUDA's expf)
+and sum gradients over points in FP32 within chunks of 32 points, then in
+FP64 across chunks:
+* outputs within 3e-5 of the magnitude sum |b3| + |W3| (|h2| + ...) that
+  bounds every term (three layers of FP32 dot products, each within
+  64 * 2^-24 of its absolute sum, plus a few ulp from expf);
+* gradients within 1e-4 of the sum of the absolute values of their terms;
+* features and targets within one FP32 ulp of the FP64 value (both sides
+  compute in FP64 and round once), plus 1e-12 for terms that cancel;
+* start vectors to FP64 rounding.
+Whatever the prediction, the solution of each stage must equal the oracle's
+to the solver's 1e-10: the start changes the iterations, not the answer.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle import mlp as OM
+from synth import geometry as g
+from synth import mlp_batch, mlp_init, mlp_perturb
+
+pytestmark = pytest.mark.gpu
+
+TOL_SOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def N():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2001_06468_gb300 import nrs
+    return nrs
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+SMALL = lambda: g.swimmer_config(ns_f=20, nth_f=4, ns_q=100, nth_q=8)  # noqa: E731
+SPERM2 = lambda: g.sperm_channel_config(count=2, n_head=40, q_head=400, n_flag=60,  # noqa: E731
+                                        q_flag=600, wall_f=(20, 6, 3), wall_q=(60, 18, 9))
+
+
+def _ctx(N, pr, params=None, **kw):
+    ctx = N.Context.from_problem(pr, factor_prec=kw.pop("prec", "fp32"), **kw)
+    Y = g.initial_state(pr)
+    ctx.set_state(Y["x0"], Y["B"])
+    ctx.mlp_set_params(mlp_init(0) if params is None else params)
+    return ctx, Y
+
+
+@pytest.mark.parametrize("npts", [1, 333, 800])
+def test_forward_loss_gradient_match_oracle(N, npts):
+    pr = g.swimmer_config()  # N = 800 force points bound npts
+    P = mlp_perturb(1, mlp_init(2), 0.1)
+    ctx, _ = _ctx(N, pr, P)
+    X, T = mlp_batch(5 + npts, npts)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    Y, G, lo = ctx.mlp_eval(Xd, Td, grad=True, loss=True)
+    Yo, _ = OM.forward(P.astype(np.float64), X.astype(np.float64))
+    Ya = OM.forward_abs(P.astype(np.float64), X.astype(np.float64))
+    assert np.all(np.abs(Y.cpu().numpy() - Yo) <= 3e-5 * Ya)
+    Go, loo = OM.grad(P.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    Ga = OM.grad_abs(P.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    assert np.all(np.abs(G.cpu().numpy() - Go) <= 1e-4 * Ga + 1e-30)
+    assert abs(lo - loo) <= 1e-5 * loo
+    # forward without gradient gives the same outputs bit for bit
+    Y2, _, _ = ctx.mlp_eval(Xd)
+    assert torch.equal(Y, Y2)
+
+
+def test_gradient_is_deterministic(N):
+    pr = g.swimmer_config()
+    ctx, _ = _ctx(N, pr, mlp_perturb(3, mlp_init(1), 0.1))
+    X, T = mlp_batch(8, 800)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    _, G1, _ = ctx.mlp_eval(Xd, Td, grad=True)
+    _, G2, _ = ctx.mlp_eval(Xd, Td, grad=True)
+    assert torch.equal(G1, G2)
+
+
+def test_adam_matches_oracle_and_checkpoint_resumes(N):
+    pr = g.swimmer_config()
+    P = mlp_perturb(4, mlp_init(4), 0.1)
+    ctx, _ = _ctx(N, pr, P)
+    X, T = mlp_batch(12, 500)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    lr = 3e-3
+    Po, mo, vo = P.astype(np.float64), np.zeros(OM.NPARAM), np.zeros(OM.NPARAM)
+    for t in (1, 2):
+        _, G, _ = ctx.mlp_eval(Xd, Td, grad=True)
+        before = ctx.mlp_get_params()
+        ctx.mlp_adam(G, lr)
+        after = ctx.mlp_get_params()
+        # one step from the GPU's own state and gradient, in FP64
+        Gh = G.cpu().numpy().astype(np.float64)
+        Pn, mn, vn = OM.adam(before["params"].astype(np.float64), before["adam_m"],
+                             before["adam_v"], Gh, lr, t)
+        ulp = np.spacing(np.abs(Pn).astype(np.float32)).astype(np.float64)
+        assert np.all(np.abs(after["params"] - Pn) <= 4 * ulp + 1e-6 * lr)
+        # FP32 moments: a few roundings of terms of size 0.9 |m| + 0.1 |g| (m may cancel)
+        mscale = 0.9 * np.abs(before["adam_m"]) + 0.1 * np.abs(Gh)
+        assert np.all(np.abs(after["adam_m"] - mn) <= 4 * 2.0 ** -24 * mscale + 1e-30)
+        assert np.allclose(after["adam_v"], vn, rtol=1e-6, atol=1e-30)
+        assert after["t"] == t
+        Po, mo, vo = OM.adam(Po, mo, vo, OM.grad(Po, X.astype(np.float64),
+                                                 T.astype(np.float64))[0], lr, t)
+    # two steps in FP32 stay close to two steps in FP64 from the same start
+    assert np.max(np.abs(after["params"] - Po)) <= 1e-3 * lr * 2 + 1e-6
+    # checkpoint / resume: a second context loaded with the state continues identically
+    ctx2, _ = _ctx(N, pr, after["params"])
+    ctx2.mlp_set_params(after["params"], after["adam_m"], after["adam_v"], after["t"])
+    for c in (ctx, ctx2):
+        _, G, _ = c.mlp_eval(Xd, Td, grad=True)
+        c.mlp_adam(G, lr)
+    a, b = ctx.mlp_get_params(), ctx2.mlp_get_params()
+    assert np.array_equal(a["params"], b["params"]) and a["t"] == b["t"] == 3
+
+
+@pytest.mark.parametrize("name", ["small", "sperm2", "sphere"])
+def test_features_targets_start_match_oracle(N, name):
+    pr = {"small": SMALL, "sperm2": SPERM2, "sphere": lambda: g.sphere_config()}[name]()
+    t = 0.21
+    sh = g.pack_shapes(pr, t)
+    ctx, Y = _ctx(N, pr)
+    Rm = np.array([[0.36, 0.48, -0.8], [-0.8, 0.6, 0.0], [0.48, 0.64, 0.6]])
+    Y = {"x0": Y["x0"] + np.array([0.1, 0.2, -0.3]), "B": np.array([Rm for _ in pr.bodies])}
+    ctx.set_state(Y["x0"], Y["B"])
+    xi, Xiw, xidot = N.shapes_to_device(sh)
+    x, Xw, b = ctx.kinematics(xi, Xiw, xidot)
+    ctx.nearest_build(xi, Xiw)
+    ctx.assemble(x, Xw, want_matrix=False)
+    scl = np.array([0.9, 1.7, 0.35])
+    ctx.mlp_config(scales=scl)
+    rng = np.random.Generator(np.random.PCG64(17))
+    nfree = ctx.F
+    vprev = rng.normal(size=6 * nfree) if nfree else None
+    sol = rng.normal(size=ctx.n)
+    s = N.Context.shapes(xi, Xiw, xidot)
+    vd = torch.from_numpy(vprev).cuda() if nfree else None
+    Xg, Tg = ctx.mlp_features(s, vd, torch.from_numpy(sol).cuda())
+    # oracle: W_n = sum of the weights of the quadrature points whose nearest force point is n
+    nn = O.nearest(sh["x"], sh["Xw"], sh["n_off"], sh["q_off"], False)
+    W = np.bincount(nn, weights=sh["Xw"][:, 3], minlength=ctx.N)
+    tab = g.body_table(pr)
+    Xo = OM.features(sh["x"], sh["xidot"], W, sh["n_off"], tab["kind"], Y["B"], tab["U"],
+                     tab["Omega"], vprev, scl)
+    To = OM.targets(sol[:3 * ctx.N], sh["n_off"], Y["B"], scl[2])
+    assert np.all(np.abs(Xg.cpu().numpy() - Xo) <= 2.4e-7 * np.abs(Xo) + 1e-12)
+    assert np.all(np.abs(Tg.cpu().numpy() - To) <= 2.4e-7 * np.abs(To) + 1e-12)
+    Yp = rng.uniform(-1, 1, size=(ctx.N, 3)).astype(np.float32)
+    x0 = ctx.mlp_start(torch.from_numpy(Yp).cuda(), vd).cpu().numpy()
+    x0o = OM.start_vector(Yp.astype(np.float64), sh["n_off"], Y["B"], scl[2], vprev, nfree)
+    assert np.all(np.abs(x0 - x0o) <= 1e-14 * scl[2] * 3)
+
+
+def _run_steps(N, ctx, pr, nsteps, dt=0.01, t0=0.0):
+    reps, sols = [], []
+    for k in range(nsteps):
+        t = t0 + k * dt
+        d0 = N.shapes_to_device(g.pack_shapes(pr, t))
+        dh = N.shapes_to_device(g.pack_shapes(pr, t + 0.5 * dt))
+        sol = torch.empty(2 * ctx.n, dtype=torch.float64, device="cuda")
+        reps.append(ctx.step(N.Context.shapes(*d0), N.Context.shapes(*dh), dt, sol=sol))
+        sols.append(sol.cpu().numpy())
+    return reps, sols
+
+
+def test_training_in_the_step_lowers_the_error_and_keeps_the_trajectory(N):
+    pr = SMALL()
+    ctx, Y = _ctx(N, pr)
+    ctx.mlp_config(train_iters=20, predict=False, lr=3e-3)
+    reps, sols = _run_steps(N, ctx, pr, 4)
+    errs = [r["mlp_rel_err"] for r in reps]
+    assert all(e >= 0 for e in errs) and errs[-1] < errs[0], errs
+    assert all(r["start"] == ["cold", "cold"] for r in reps)
+    # the scales come from the first stage: L = max |xi|, V = max |b|, F = RMS |f|
+    st = ctx.mlp_get_params()
+    sh0 = g.pack_shapes(pr, 0.0)
+    A, b, *_ = O.system(pr, sh0, g.body_table(pr), Y)
+    f1 = O.solve(A, b)[:3 * pr.N]
+    so = OM.scales(sh0["x"], b, f1)
+    assert np.allclose(st["scales"], so, rtol=1e-10, atol=0)
+    Yo = Y
+    for k in range(4):
+        Yn, stg = O.rk2_step(pr, Yo, k * 0.01, 0.01, return_stages=True)
+        assert _rel(sols[k][:pr.n], stg["sol1"]) <= TOL_SOL
+        assert _rel(sols[k][pr.n:], stg["sol2"]) <= TOL_SOL
+        Yo = Yn
+
+
+@pytest.mark.parametrize("prec,reuse", [("fp32", False), ("tf32", True)])
+def test_learned_start_keeps_the_oracle_trajectory(N, prec, reuse):
+    pr = g.swimmer_config()
+    ctx, Y = _ctx(N, pr, prec=prec, reuse_factor=reuse)
+    ctx.mlp_config(train_iters=30, predict=False, lr=3e-3)
+    _run_steps(N, ctx, pr, 3)
+    Yo = Y
+    for k in range(3):
+        Yo = O.rk2_step(pr, Yo, k * 0.01, 0.01)
+    ctx.mlp_config(train_iters=10, predict=True, lr=1e-3)
+    reps, sols = _run_steps(N, ctx, pr, 2, t0=0.03)
+    for k in range(2):
+        Yn, stg = O.rk2_step(pr, Yo, 0.03 + k * 0.01, 0.01, return_stages=True)
+        assert _rel(sols[k][:pr.n], stg["sol1"]) <= TOL_SOL, reps[k]
+        assert _rel(sols[k][pr.n:], stg["sol2"]) <= TOL_SOL, reps[k]
+        Yo = Yn
+    assert all(s in ("cold", "learned") for r in reps for s in r["start"])
+
+
+@pytest.mark.parametrize("bad", ["huge", "nan"])
+def test_bad_prediction_falls_back_to_the_cold_start(N, bad):
+    pr = SMALL()
+    P = mlp_init(0).copy()
+    P[-3:] = 1e30 if bad == "huge" else np.nan
+    ctx, Y = _ctx(N, pr, P)
+    ctx.mlp_config(train_iters=0, predict=True, scales=[1.0, 1.0, 1.0])
+    reps, sols = _run_steps(N, ctx, pr, 1)
+    assert reps[0]["start"] == ["cold", "cold"]
+    Yn, stg = O.rk2_step(pr, Y, 0.0, 0.01, return_stages=True)
+    assert _rel(sols[0][:pr.n], stg["sol1"]) <= TOL_SOL
+    assert _rel(sols[0][pr.n:], stg["sol2"]) <= TOL_SOL
+
+
+def test_mlp_arguments_are_rejected(N):
+    pr = SMALL()
+    ctx = N.Context.from_problem(pr)
+    with pytest.raises(N.NrsError):   # no parameters yet
+        ctx.mlp_config(train_iters=1)
+    ctx.mlp_set_params(mlp_init(0))
+    with pytest.raises(N.NrsError):   # prediction without scales or training
+        ctx.mlp_config(train_iters=0, predict=True)
+    with pytest.raises(N.NrsError):   # non-positive scale
+        ctx.mlp_config(scales=[1.0, 0.0, 1.0])
+    with pytest.raises(N.NrsError):   # more points than the context holds
+        ctx.mlp_eval(torch.zeros((ctx.N + 1, 17), dtype=torch.float32, device="cuda"))
