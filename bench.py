@@ -164,14 +164,15 @@ def _traffic(kernel, n):
     return rec["bytes"]
 
 
-def _rooflines(ph_ms, ph_spans, pr, peaks, peak_src, clocks):
+def _rooflines(ph_ms, ph_spans, pr, peaks, peak_src, clocks, solve_stats=None):
     """Roofline records of the kernel families of the step, from the live
     per-phase CUDA-event times.  Algorithmic work per launch:
       k_gj_diag       2*64^3 flops (inverse) + 2*64^3 (lookahead block update)
       k_tc_gj_update  8 n^2 bytes (read and write of the FP32 matrix), HBM-bound at K = 64
       k_assemble64    29 FP64 operations per (force point, quadrature point) pair
       k_gemv_part     8 n^2 bytes (FP64 matrix)
-      k_gemv32_part   4 n^2 bytes (FP32 explicit inverse)"""
+      k_gemv32_part   4 n^2 bytes (FP32 explicit inverse)
+      k_gmres_ir      8 n^2 (outer + inner) + 4 n^2 (outer + inner + 1) bytes per solve"""
     n = pr.n
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
@@ -207,19 +208,34 @@ def _rooflines(ph_ms, ph_spans, pr, peaks, peak_src, clocks):
                         "peak_source": "nominal FP64 1.25 TFLOP/s at 2070 MHz, scaled to the clock",
                         "pairs_per_s": pr.pairs / t, "work_per_launch": f,
                         "launches": ph_spans["assemble"], "traffic": _traffic("k_assemble64", n)}
-    t = per_launch("gemv")
-    b = 8.0 * n * n
-    recs["gemv"] = {"kernel": "k_gemv_part (FP64 residual / Arnoldi products)", "bound": "hbm",
-                    "achieved": b / t / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": b / t / 1e9 / peaks["hbm_gbs"], "peak_source": peak_src,
-                    "work_per_launch": b, "launches": ph_spans["gemv"], "traffic": None}
-    t = per_launch("trsv")
-    b = 4.0 * n * n
-    recs["precond"] = {"kernel": "k_gemv32_part (explicit-inverse preconditioner)",
-                       "bound": "hbm", "achieved": b / t / 1e9, "peak": peaks["hbm_gbs"],
-                       "unit": "GB/s", "frac": b / t / 1e9 / peaks["hbm_gbs"],
-                       "peak_source": peak_src, "work_per_launch": b,
-                       "launches": ph_spans["trsv"], "traffic": None}
+    if ph_spans["trsv"] > 0:  # host-driven refinement: separate product kernels
+        t = per_launch("gemv")
+        b = 8.0 * n * n
+        recs["gemv"] = {"kernel": "k_gemv_part (FP64 residual / Arnoldi products)", "bound": "hbm",
+                        "achieved": b / t / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": b / t / 1e9 / peaks["hbm_gbs"], "peak_source": peak_src,
+                        "work_per_launch": b, "launches": ph_spans["gemv"], "traffic": None}
+        t = per_launch("trsv")
+        b = 4.0 * n * n
+        recs["precond"] = {"kernel": "k_gemv32_part (explicit-inverse preconditioner)",
+                           "bound": "hbm", "achieved": b / t / 1e9, "peak": peaks["hbm_gbs"],
+                           "unit": "GB/s", "frac": b / t / 1e9 / peaks["hbm_gbs"],
+                           "peak_source": peak_src, "work_per_launch": b,
+                           "launches": ph_spans["trsv"], "traffic": None}
+    elif solve_stats and ph_spans["krylov"] > 0:
+        # one persistent launch per solve: (outer + inner) FP64 products with A and
+        # (outer + inner + 1) FP32 products with the explicit inverse per launch
+        o, i = solve_stats["outer_mean"], solve_stats["inner_mean"]
+        t = per_launch("krylov")
+        b = 8.0 * n * n * (o + i) + 4.0 * n * n * (o + i + 1)
+        recs["solve"] = {"kernel": "k_gmres_ir (persistent GMRES-IR, one cooperative launch per solve)",
+                         "bound": "hbm", "achieved": b / t / 1e9, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": b / t / 1e9 / peaks["hbm_gbs"],
+                         "peak_source": peak_src, "work_per_launch": b,
+                         "fp64_tflops": 2.0 * n * n * (o + i) / t / 1e12,
+                         "fp64_frac": 2.0 * n * n * (o + i) / t / 1e12 / fp64_peak,
+                         "us_per_launch": t * 1e6,
+                         "launches": ph_spans["krylov"], "traffic": _traffic("k_gmres_ir", n)}
     return recs
 
 
@@ -286,8 +302,13 @@ def run_nrs(args):
         do_step(ctx_t, dev[s])
     torch.cuda.synchronize()
     ctx_t.set_timing(True)
+    nrep_t = len(reports)
     step_ms_instr = timed_pass(ctx_t, W)
     phases, launches = ctx_t.get_timing()
+    instr_reports = reports[nrep_t:]
+    solve_stats = {
+        "outer_mean": float(np.mean([r["stages"][i]["outer"] for r in instr_reports for i in (0, 1)])),
+        "inner_mean": float(np.mean([r["stages"][i]["inner"] for r in instr_reports for i in (0, 1)]))}
     ctx_t.set_timing(False)
     t_local = sum(step_ms) / 1e3
     if ws > 1:
@@ -346,6 +367,16 @@ def run_nrs(args):
         torch.cuda.synchronize()
         p_ms += e0.elapsed_time(e1)
     plain_s = p_ms / 1e3 / Kp
+
+    # the same mixed path with the host-driven refinement loop (one host
+    # synchronisation per GMRES iteration) instead of the persistent solve
+    ctx_h = nrs.Context.from_problem(pr, factor_prec=args.prec, solve_mode="host")
+    ctx_h.set_state(Y0["x0"], Y0["B"])
+    for s in range(W):
+        do_step(ctx_h, dev[s])
+    torch.cuda.synchronize()
+    host_loop_s = float(np.sum(timed_pass(ctx_h, W))) / 1e3 / K / ws
+    ctx_h.close()
 
     # factor reuse across stages + warm start (same inputs, same timing rules)
     ctx_r = nrs.Context.from_problem(pr, factor_prec=args.prec, reuse_factor=True, warm_start=True)
@@ -409,8 +440,8 @@ def run_nrs(args):
     ph_ms = {k: v[0] for k, v in phases.items()}
     ph_spans = {k: v[1] for k, v in phases.items()}
     tot = sum(ph_ms.values())
-    recs = _rooflines(ph_ms, ph_spans, pr, peaks, peak_src, clocks)
-    top = max(recs, key=lambda p: ph_ms["trsv" if p == "precond" else p])
+    recs = _rooflines(ph_ms, ph_spans, pr, peaks, peak_src, clocks, solve_stats)
+    top = max(recs, key=lambda p: ph_ms[{"precond": "trsv", "solve": "krylov"}.get(p, p)])
     roof = recs[top]
     asm = recs["assemble"]
     line = {
@@ -434,6 +465,7 @@ def run_nrs(args):
         "pairs_per_s": asm.get("pairs_per_s"),
         "plain_fp64_s_per_step": plain_s,
         "mixed_vs_plain_speedup": plain_s / (t_max / K),
+        "host_loop_refinement_s_per_step": host_loop_s,
         "value_factor_reuse": reuse_s,
         "factor_reuse": {"s_per_step": reuse_s, "vs_plain_speedup": plain_s / (reuse_s * ws),
                          "factorizations_per_step": float(np.mean([r["factorizations"] for r in reuse_reports])),

@@ -93,6 +93,10 @@ typedef struct {
     int32_t reuse_max_inner;   /* 0 = 8  */
     int32_t reuse_max_stages;  /* 0 = 16 */
     int32_t warm_start;    /* nrs_step: start each solve from the previous stage's solution */
+    int32_t solve_mode;    /* 0: with an explicit-inverse factor (FP32/TF32) and max_inner <= 64,
+                              the whole refinement of one right-hand side is one cooperative
+                              launch (no host round trip inside a solve); 1: host-driven loop
+                              (one synchronisation per GMRES iteration), the FP64 path's mode */
 } nrs_problem_desc;
 
 typedef struct {

@@ -89,6 +89,9 @@ nrs_status alloc_all(Ctx *c)
         {(void **)&c->d_t64, sizeof(double) * 2 * lda},
         {(void **)&c->d_flags, sizeof(int32_t) * nrs::ceil_div(n, 64)},
         {(void **)&c->d_status, sizeof(int32_t)},
+        {(void **)&c->d_dpart, sizeof(double) * nrs::pg_dpart_doubles(c->max_inner)},
+        {(void **)&c->d_bar, sizeof(int32_t) * 2},
+        {(void **)&c->d_pg_stats, sizeof(double) * 8},
     };
     for (auto &r : req) {
         *r.p = nullptr;
@@ -113,7 +116,7 @@ void free_all(Ctx *c)
                     c->d_lperm,  c->d_info,   c->d_r,      c->d_xk,         c->d_w,
                     c->d_V,      c->d_H,      c->d_gv,     c->d_scal,       c->d_part,
                     c->d_t32,    c->d_t64,    c->d_flags,  c->d_status,     c->d_gj_dinv,
-                    c->d_gj_rt,  c->d_gj_cb};
+                    c->d_gj_rt,  c->d_gj_cb,  c->d_dpart,  c->d_bar,        c->d_pg_stats};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *mlp[] = {c->d_mlp_params, c->d_mlp_m,  c->d_mlp_v,     c->d_mlp_g,    c->d_mlp_x,
@@ -295,6 +298,7 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
     c->reuse_max_inner = d->reuse_max_inner > 0 ? d->reuse_max_inner : 8;
     c->reuse_max_stages = d->reuse_max_stages > 0 ? d->reuse_max_stages : 16;
     c->warm_start = d->warm_start ? 1 : 0;
+    c->solve_mode = d->solve_mode ? 1 : 0;
     {
         // enough column splits for about two CTAs per SM in the matrix-vector products
         auto splits = [&](int64_t rows_per_cta) {

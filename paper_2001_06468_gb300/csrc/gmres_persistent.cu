@@ -1,0 +1,534 @@
+// gmres_persistent.cu -- the GMRES-based iterative refinement of solve.cu
+// (Carson & Higham 2018; the solve of Gallagher & Smith, Sec. 4 step 3) as
+// ONE cooperative launch per right-hand side, for the factors that leave an
+// explicit FP32 inverse M (Gauss-Jordan): the preconditioner is then a
+// matrix-vector product, and the whole refinement -- FP64 residuals, Arnoldi
+// with classical Gram-Schmidt applied twice, Givens rotations, the FP64
+// update and the stopping rule -- runs on the device with no host round trip.
+//
+// Work split.  Matrix-vector products (A in FP64, M in FP32) are tiled over
+// all CTAs as (row chunk, column split) tiles that write partial sums.  The
+// length-n vector work (finishing the products, dot products, projections,
+// norms, the update) is owned by the first DCH CTAs, CTA d owning elements
+// [d*ED, (d+1)*ED): the same CTA that finishes a vector chunk also projects
+// and normalises it, so only grid-wide quantities need a grid barrier.  GB300
+// runs FP64 at a small fraction of its FP32 rate, so even the dot products
+// are spread over many SMs.  Small state (the Hessenberg matrix, the Givens
+// rotations, the least-squares solution, the stopping decisions) is kept in
+// every CTA's shared memory and computed redundantly in the same order from
+// the same values, so all CTAs take the same branches without a broadcast.
+// Every reduction has a fixed order: the result is deterministic.
+//
+// Grid barriers are bounded: a CTA that waits more than kSpinLimit polls sets
+// ST_TIMEOUT and returns, and every CTA returns at its next barrier once the
+// flag is set.  The launch is cooperative, so all CTAs are co-resident.
+#include <math.h>
+
+#include <algorithm>
+
+#include "nrs_internal.cuh"
+
+namespace nrs {
+
+constexpr int PG_THREADS = 256;
+constexpr int PG_MAXM = 64;      // largest restart length of this kernel
+constexpr int PG_MAXCH = 128;    // most chunk-owner CTAs
+constexpr int MV_GROUPS = PG_THREADS / 32;  // column groups inside a product tile
+constexpr int MV64_ROWS = 64;   // rows of an FP64 product tile: 32 row pairs x 8 column groups
+constexpr int MV32_ROWS = 128;  // rows of an FP32 product tile: 32 row quads x 8 column groups
+
+struct PgArgs {
+    int64_t n, lda, ldv;
+    const double *A;      // FP64 system matrix, column-major
+    const float *M;       // explicit FP32 inverse (the preconditioner), column-major
+    const double *b;
+    double *x;            // in: starting guess unless cold; out: solution
+    double *V;            // Krylov basis, n x (m+1), leading dimension ldv
+    double *w;            // n: A v, then the residual
+    double *part;         // matrix-vector partial sums [splits][n]
+    double *dpart;        // reduction partials [3][PG_MAXCH][m+2]
+    int32_t *bar;         // grid barrier: [0] arrivals, [1] generation
+    int32_t *status;
+    double *out;          // [0] outer steps, [1] inner iterations, [2] converged,
+                          // [3] ||d||_inf, [4] ||x||_inf
+    double tol, floor, tol_in;
+    int m, max_outer, cold, dch;
+    int rc64, s64, rc32, s32;
+    int64_t cps64, cps32, ed;
+};
+
+__device__ __forceinline__ int32_t pg_ld_acquire(const int32_t *p)
+{
+    int32_t v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void pg_st_release(int32_t *p, int32_t v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int32_t pg_ld_relaxed(const int32_t *p)
+{
+    int32_t v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier (bounded).  Returns false when the solve must stop.
+__device__ bool grid_sync(const PgArgs &a, int *s_ok)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        const int32_t gen = pg_ld_acquire(&a.bar[1]);
+        if (atomicAdd(&a.bar[0], 1) == (int)gridDim.x - 1) {
+            atomicExch(&a.bar[0], 0);
+            pg_st_release(&a.bar[1], gen + 1);
+        } else {
+            long long spins = 0;
+            while (pg_ld_acquire(&a.bar[1]) == gen) {
+                ++spins;
+                if (spins > kSpinLimit ||
+                    ((spins & 1023) == 0 && (pg_ld_relaxed(a.status) & ST_TIMEOUT))) {
+                    atomicOr(a.status, ST_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// part[s][i] = scale * sum_{j in split s} A[i, j] v[j].  A tile is 64 rows x
+// one column split; lane l of warp g takes rows 2l, 2l+1 (one 16-byte load per
+// column, 512 contiguous bytes per warp) and columns j0+g, j0+g+8, ...; the 8
+// column groups are summed in shared memory in a fixed order.
+__device__ void mv64_partial(const PgArgs &a, const double *v, double scale, double *sm)
+{
+    const int64_t tiles = (int64_t)a.rc64 * a.s64;
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t rc = t % a.rc64, s = t / a.rc64;
+        const int64_t i = rc * MV64_ROWS + 2 * lane;
+        const int64_t j0 = s * a.cps64, j1 = min(a.n, j0 + a.cps64);
+        double s0 = 0.0, s1 = 0.0;
+        if (i < a.n) {
+            const double *col = a.A + i;
+#pragma unroll 4
+            for (int64_t j = j0 + grp; j < j1; j += MV_GROUPS) {
+                const double2 x = __ldg(reinterpret_cast<const double2 *>(col + j * a.lda));
+                const double vj = __ldcg(v + j);
+                s0 = fma(x.x, vj, s0);
+                s1 = fma(x.y, vj, s1);
+            }
+        }
+        sm[grp * MV64_ROWS + 2 * lane] = s0;
+        sm[grp * MV64_ROWS + 2 * lane + 1] = s1;
+        __syncthreads();
+        if (threadIdx.x < MV64_ROWS) {
+            const int64_t r = rc * MV64_ROWS + threadIdx.x;
+            double acc = 0.0;
+#pragma unroll
+            for (int g = 0; g < MV_GROUPS; ++g) acc += sm[g * MV64_ROWS + threadIdx.x];
+            if (r < a.n) a.part[s * a.n + r] = acc * scale;
+        }
+        __syncthreads();
+    }
+}
+
+// part[s][i] = sum_{j in split s} M[i, j] v[j] (FP32 products and sums): 128
+// rows per tile, lane l takes rows 4l..4l+3 (one 16-byte load per column).
+__device__ void mv32_partial(const PgArgs &a, const double *v, float *sm)
+{
+    const int64_t tiles = (int64_t)a.rc32 * a.s32;
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t rc = t % a.rc32, s = t / a.rc32;
+        const int64_t i = rc * MV32_ROWS + 4 * lane;
+        const int64_t j0 = s * a.cps32, j1 = min(a.n, j0 + a.cps32);
+        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+        if (i < a.n) {
+            const float *col = a.M + i;
+#pragma unroll 4
+            for (int64_t j = j0 + grp; j < j1; j += MV_GROUPS) {
+                const float4 x = __ldg(reinterpret_cast<const float4 *>(col + j * a.lda));
+                const float vj = (float)__ldcg(v + j);
+                s0 = fmaf(x.x, vj, s0);
+                s1 = fmaf(x.y, vj, s1);
+                s2 = fmaf(x.z, vj, s2);
+                s3 = fmaf(x.w, vj, s3);
+            }
+        }
+        float *q = sm + grp * MV32_ROWS + 4 * lane;
+        q[0] = s0;
+        q[1] = s1;
+        q[2] = s2;
+        q[3] = s3;
+        __syncthreads();
+        if (threadIdx.x < MV32_ROWS) {
+            const int64_t r = rc * MV32_ROWS + threadIdx.x;
+            float acc = 0.0f;
+#pragma unroll
+            for (int g = 0; g < MV_GROUPS; ++g) acc += sm[g * MV32_ROWS + threadIdx.x];
+            if (r < a.n) a.part[s * a.n + r] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ double sum_parts(const PgArgs &a, int splits, int64_t e)
+{
+    double s = 0.0;
+    for (int k = 0; k < splits; ++k) s += __ldcg(a.part + k * a.n + e);
+    return s;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum in a fixed order; the result is returned to every thread.
+__device__ double block_sum_all(double v, double *sred)
+{
+    v = warp_sum_d(v);
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int i = 0; i < PG_THREADS / 32; ++i) s += sred[i];
+    __syncthreads();
+    return s;
+}
+
+__device__ double block_max_all(double v, double *sred)
+{
+    v = warp_max_d(v);
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int i = 0; i < PG_THREADS / 32; ++i) s = fmax(s, sred[i]);
+    __syncthreads();
+    return s;
+}
+
+// dpart[region][d][i] = V_i . u over this CTA's chunk, for i <= j (one warp per i)
+__device__ void chunk_dots(const PgArgs &a, int region, int j, const double *u, int64_t e0,
+                           int64_t e1)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double *dp = a.dpart + ((int64_t)region * PG_MAXCH + blockIdx.x) * (a.m + 2);
+    for (int i = wid; i <= j; i += PG_THREADS / 32) {
+        const double *vi = a.V + (int64_t)i * a.ldv;
+        double s = 0.0;
+        for (int64_t e = e0 + lane; e < e1; e += 32) s = fma(__ldcg(vi + e), __ldcg(u + e), s);
+        s = warp_sum_d(s);
+        if (lane == 0) dp[i] = s;
+    }
+}
+
+// Sum (or maximum) over chunks of dpart[region][d][slot], d < dch <= 256:
+// thread d loads chunk d, then a fixed-order block reduction; every thread
+// of the CTA gets the value.
+__device__ double chunk_total(const PgArgs &a, int region, int slot, bool is_max, double *sred)
+{
+    double v = 0.0;
+    if ((int)threadIdx.x < a.dch)
+        v = __ldcg(a.dpart + ((int64_t)region * PG_MAXCH + threadIdx.x) * (a.m + 2) + slot);
+    return is_max ? block_max_all(v, sred) : block_sum_all(v, sred);
+}
+
+// h[i] = sum over chunks d of dpart[region][d][i], i <= j, into shared memory
+// (warp i sums the chunks with its lanes, then a fixed-order warp reduction)
+__device__ void sum_dots(const PgArgs &a, int region, int j, double *h)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = wid; i <= j; i += PG_THREADS / 32) {
+        double s = 0.0;
+        for (int d = lane; d < a.dch; d += 32)
+            s += __ldcg(a.dpart + ((int64_t)region * PG_MAXCH + d) * (a.m + 2) + i);
+        s = warp_sum_d(s);
+        if (lane == 0) h[i] = s;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
+{
+    __shared__ double sH[(PG_MAXM + 1) * PG_MAXM];  // column-major, leading dimension PG_MAXM+1
+    __shared__ double scs[PG_MAXM], ssn[PG_MAXM], sg[PG_MAXM + 1], sy[PG_MAXM];
+    __shared__ double sh1[PG_MAXM + 1], sh2[PG_MAXM + 1];
+    __shared__ double sred[PG_THREADS / 32];
+    __shared__ __align__(16) double smv[MV_GROUPS * MV64_ROWS];  // product tiles (FP64 or FP32 view)
+    __shared__ int s_ok;
+    float *smv32 = reinterpret_cast<float *>(smv);
+    static_assert(MV_GROUPS * MV32_ROWS * sizeof(float) <= sizeof(double) * MV_GROUPS * MV64_ROWS,
+                  "shared product tile");
+    constexpr int LDH = PG_MAXM + 1;
+    const int m = a.m;
+    const int64_t n = a.n;
+    const bool owner = (int)blockIdx.x < a.dch;
+    const int64_t e0 = owner ? min(n, (int64_t)blockIdx.x * a.ed) : n;
+    const int64_t e1 = owner ? min(n, e0 + a.ed) : n;
+    const int nslot = m + 1;  // slot of norms in region 2 / maxima in region 0
+    double *dp0 = a.dpart + (0 * PG_MAXCH + (int64_t)blockIdx.x) * (m + 2);
+    double *dp2 = a.dpart + (2 * PG_MAXCH + (int64_t)blockIdx.x) * (m + 2);
+
+    if (a.cold) {  // x = M b
+        mv32_partial(a, a.b, smv32);
+        if (!grid_sync(a, &s_ok)) return;
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) a.x[e] = sum_parts(a, a.s32, e);
+        if (!grid_sync(a, &s_ok)) return;
+    }
+    int outer = 0, inner_total = 0, converged = 0;
+    double dn = 0.0, xn = 0.0, dn_prev = 0.0;
+    for (outer = 0; outer < a.max_outer; ++outer) {
+        // r = b - A x (FP64)
+        mv64_partial(a, a.x, 1.0, smv);
+        if (!grid_sync(a, &s_ok)) return;
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS)
+            a.w[e] = __ldg(a.b + e) - sum_parts(a, a.s64, e);
+        if (!grid_sync(a, &s_ok)) return;
+        // V_0 = M r (raw), beta = ||V_0||
+        mv32_partial(a, a.w, smv32);
+        if (!grid_sync(a, &s_ok)) return;
+        {
+            double s = 0.0;
+            for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
+                const double v = sum_parts(a, a.s32, e);
+                a.V[e] = v;
+                s = fma(v, v, s);
+            }
+            s = block_sum_all(s, sred);
+            if (owner && threadIdx.x == 0) dp2[nslot] = s;
+        }
+        if (!grid_sync(a, &s_ok)) return;
+        const double beta = sqrt(chunk_total(a, 2, nslot, false, sred));
+        if (!isfinite(beta)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.status, ST_NONFINITE);
+            break;
+        }
+        for (int i = threadIdx.x; i <= m; i += PG_THREADS) sg[i] = i == 0 ? beta : 0.0;
+        __syncthreads();
+        double sv = beta > 0.0 ? 1.0 / beta : 0.0;  // scale of the raw V_j
+        int k = 0;
+        bool bad = false;
+        for (int j = 0; j < m; ++j) {
+            double *Vj = a.V + (int64_t)j * a.ldv;
+            double *u = a.V + (int64_t)(j + 1) * a.ldv;
+            // w = A v_j
+            mv64_partial(a, Vj, sv, smv);
+            if (!grid_sync(a, &s_ok)) return;
+            for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
+                Vj[e] = __ldcg(Vj + e) * sv;  // v_j normalised in place (own chunk)
+                a.w[e] = sum_parts(a, a.s64, e);
+            }
+            if (!grid_sync(a, &s_ok)) return;
+            // u = M w, then two classical Gram-Schmidt passes and the norm
+            mv32_partial(a, a.w, smv32);
+            if (!grid_sync(a, &s_ok)) return;
+            for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) u[e] = sum_parts(a, a.s32, e);
+            __syncthreads();
+            if (owner) chunk_dots(a, 0, j, u, e0, e1);
+            if (!grid_sync(a, &s_ok)) return;
+            sum_dots(a, 0, j, sh1);
+            for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
+                double s = __ldcg(u + e);
+                for (int i = 0; i <= j; ++i) s = fma(-sh1[i], __ldcg(a.V + (int64_t)i * a.ldv + e), s);
+                u[e] = s;
+            }
+            __syncthreads();
+            if (owner) chunk_dots(a, 1, j, u, e0, e1);
+            if (!grid_sync(a, &s_ok)) return;
+            sum_dots(a, 1, j, sh2);
+            {
+                double s2 = 0.0;
+                for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
+                    double s = __ldcg(u + e);
+                    for (int i = 0; i <= j; ++i)
+                        s = fma(-sh2[i], __ldcg(a.V + (int64_t)i * a.ldv + e), s);
+                    u[e] = s;
+                    s2 = fma(s, s, s2);
+                }
+                s2 = block_sum_all(s2, sred);
+                if (owner && threadIdx.x == 0) dp2[nslot] = s2;
+            }
+            if (!grid_sync(a, &s_ok)) return;
+            const double hn = sqrt(chunk_total(a, 2, nslot, false, sred));
+            // column j of H, previous rotations, the new rotation (every CTA, same order)
+            double res = 0.0;
+            if (threadIdx.x == 0) {
+                double *col = sH + (int64_t)j * LDH;
+                for (int i = 0; i <= j; ++i) col[i] = sh1[i] + sh2[i];
+                col[j + 1] = hn;
+                for (int i = 0; i < j; ++i) {
+                    const double p = col[i], q = col[i + 1];
+                    col[i] = scs[i] * p + ssn[i] * q;
+                    col[i + 1] = -ssn[i] * p + scs[i] * q;
+                }
+                const double p = col[j], q = col[j + 1];
+                const double r = hypot(p, q);
+                const double c = r > 0.0 ? p / r : 1.0, s = r > 0.0 ? q / r : 0.0;
+                scs[j] = c;
+                ssn[j] = s;
+                col[j] = r;
+                col[j + 1] = 0.0;
+                sg[j + 1] = -s * sg[j];
+                sg[j] = c * sg[j];
+                sred[0] = fabs(sg[j + 1]);
+            }
+            __syncthreads();
+            res = sred[0];
+            __syncthreads();
+            k = j + 1;
+            ++inner_total;
+            if (!isfinite(res) || !isfinite(hn)) {
+                bad = true;
+                break;
+            }
+            sv = hn > 0.0 ? 1.0 / hn : 0.0;
+            if (res <= a.tol_in * beta || hn == 0.0) break;
+        }
+        if (bad) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.status, ST_NONFINITE);
+            break;
+        }
+        // y = R^{-1} g (k x k), then x += d = V y on the own chunk
+        if (threadIdx.x == 0) {
+            for (int i = k - 1; i >= 0; --i) {
+                double s = sg[i];
+                for (int l = i + 1; l < k; ++l) s -= sH[(int64_t)l * LDH + i] * sy[l];
+                sy[i] = s / sH[(int64_t)i * LDH + i];
+            }
+        }
+        __syncthreads();
+        {
+            double dmax = 0.0, xmax = 0.0;
+            for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
+                double s = 0.0;
+                for (int i = 0; i < k; ++i) s = fma(sy[i], __ldcg(a.V + (int64_t)i * a.ldv + e), s);
+                const double xe = __ldcg(a.x + e) + s;
+                a.x[e] = xe;
+                dmax = fmax(dmax, fabs(s));
+                xmax = fmax(xmax, fabs(xe));
+                if (!isfinite(s) || !isfinite(xe)) dmax = INFINITY;
+            }
+            dmax = block_max_all(dmax, sred);
+            xmax = block_max_all(xmax, sred);
+            if (owner && threadIdx.x == 0) {
+                dp0[0] = dmax;
+                dp0[1] = xmax;
+            }
+        }
+        if (!grid_sync(a, &s_ok)) return;
+        dn = chunk_total(a, 0, 0, true, sred);
+        xn = chunk_total(a, 0, 1, true, sred);
+        // stopping rule of k_outer_check (solve.cu)
+        bool done = false;
+        if (!isfinite(dn) || !isfinite(xn)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.status, ST_NONFINITE);
+            done = true;
+        } else if (dn <= a.tol * xn) {
+            done = true;
+        } else if (dn_prev > 0.0 && dn * (dn / dn_prev) <= 1e-3 * a.tol * xn) {
+            done = true;
+        } else if (dn_prev > 0.0 && dn >= 0.5 * dn_prev && dn <= a.floor * xn) {
+            done = true;
+        }
+        dn_prev = dn;
+        if (done) {
+            converged = 1;
+            ++outer;
+            break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.out[0] = outer;
+        a.out[1] = inner_total;
+        a.out[2] = converged;
+        a.out[3] = dn;
+        a.out[4] = xn;
+    }
+}
+
+// ---- host side ---------------------------------------------------------------
+
+bool pg_supported(const Ctx &c) { return c.factored_prec != NRS_FP64 && c.max_inner <= PG_MAXM; }
+
+int pg_grid(Ctx &c)
+{
+    if (c.pg_grid > 0) return c.pg_grid;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gmres_ir, PG_THREADS, 0);
+    per_sm = std::max(1, std::min(per_sm, 1));
+    c.pg_grid = per_sm * c.num_sms;
+    return c.pg_grid;
+}
+
+size_t pg_dpart_doubles(int max_inner) { return (size_t)3 * PG_MAXCH * (max_inner + 2); }
+
+// One refinement of A x = b on the device.  Fills stats[0..4] (device) as
+// described in PgArgs::out.
+cudaError_t launch_gmres_persistent(Ctx &c, const double *b, double *x, bool cold, double *stats)
+{
+    PgArgs a{};
+    const int G = pg_grid(c);
+    a.n = c.n;
+    a.lda = c.lda;
+    a.ldv = c.lda;
+    a.A = c.d_A64;
+    a.M = c.d_A32;
+    a.b = b;
+    a.x = x;
+    a.V = c.d_V;
+    a.w = c.d_w;
+    a.part = c.d_part;
+    a.dpart = c.d_dpart;
+    a.bar = c.d_bar;
+    a.status = c.d_status;
+    a.out = stats;
+    a.tol = c.tol;
+    a.floor = 1e-11;
+    a.tol_in = 1e-4;
+    a.m = c.max_inner;
+    a.max_outer = c.max_outer;
+    a.cold = cold ? 1 : 0;
+    a.rc64 = (int)ceil_div(c.n, MV64_ROWS);
+    a.rc32 = (int)ceil_div(c.n, MV32_ROWS);
+    a.s64 = (int)std::max<int64_t>(1, std::min<int64_t>(64, ceil_div(G, a.rc64)));
+    a.s32 = (int)std::max<int64_t>(1, std::min<int64_t>(64, ceil_div(G, a.rc32)));
+    a.s64 = (int)std::min<int64_t>(a.s64, c.n);
+    a.s32 = (int)std::min<int64_t>(a.s32, c.n);
+    a.cps64 = ceil_div(c.n, a.s64);
+    a.cps32 = ceil_div(c.n, a.s32);
+    // chunk owners: at most PG_MAXCH CTAs, about 64 elements each
+    a.dch = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(PG_MAXCH, G),
+                                                        ceil_div(c.n, 64)));
+    a.ed = ceil_div(c.n, a.dch);
+    a.dch = (int)ceil_div(c.n, a.ed);
+    cudaError_t e = cudaMemsetAsync(c.d_bar, 0, 2 * sizeof(int32_t), c.stream);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&a};
+    c.tbeg(PH_KRYLOV);
+    e = cudaLaunchCooperativeKernel((void *)k_gmres_ir, G, PG_THREADS, args, 0, c.stream);
+    c.tend(PH_KRYLOV);
+    c.launches += 1;
+    return e;
+}
+
+}  // namespace nrs

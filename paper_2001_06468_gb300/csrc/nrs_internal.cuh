@@ -83,6 +83,11 @@ void launch_simt_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *C
 // ---- solve (solve.cu) ------------------------------------------------------
 nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0,
                         nrs_solve_report *rep, int *inner_out = nullptr);
+// The whole refinement as one cooperative launch (gmres_persistent.cu), for
+// explicit-inverse factors and restart lengths up to 64.
+bool pg_supported(const Ctx &c);
+size_t pg_dpart_doubles(int max_inner);
+cudaError_t launch_gmres_persistent(Ctx &c, const double *b, double *x, bool cold, double *stats);
 // x0 = whichever of xp and the cold start xc = M^{-1} b has the smaller
 // ||b - A x||_inf (norms[0], norms[1]); c.d_mlp_used[0] records the choice.
 cudaError_t choose_start(Ctx &c, const double *b, const double *xp, double *xc, double *x0,
@@ -180,6 +185,11 @@ struct Ctx {
     int64_t cold_inner_cnt = 0;
 
     // solve workspaces
+    int solve_mode = 0;        // 0: persistent device loop where supported; 1: host-driven loop
+    double *d_dpart = nullptr; // reduction partials of the persistent solve
+    int32_t *d_bar = nullptr;  // its grid barrier
+    double *d_pg_stats = nullptr;  // its outcome: outer, inner, converged, ||d||, ||x||
+    int pg_grid = 0;           // its CTA count (0 = from occupancy)
     double *d_r = nullptr, *d_xk = nullptr, *d_w = nullptr, *d_V = nullptr, *d_H = nullptr;
     double *d_gv = nullptr;    // Givens state: cs[m], sn[m], g[m+1], y[m]
     double *d_scal = nullptr;  // scalars (norms, flags as doubles)

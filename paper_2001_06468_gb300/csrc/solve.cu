@@ -529,9 +529,31 @@ cudaError_t choose_start(Ctx &c, const double *b, const double *xp, double *xc, 
     return cudaGetLastError();
 }
 
+static nrs_status finish_solve(Ctx &c, const double *b, double *x, nrs_solve_report *rep,
+                               int *inner_out, int outer, int inner_total, bool converged,
+                               const double *dn_xn = nullptr);
+
+static nrs_status run_gmres_ir_device(Ctx &c, const double *b, double *x, const double *x0,
+                                      nrs_solve_report *rep, int *inner_out)
+{
+    cudaError_t e = cudaSuccess;
+    if (x0) e = cudaMemcpyAsync(x, x0, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.stream);
+    if (e == cudaSuccess) e = launch_gmres_persistent(c, b, x, x0 == nullptr, c.d_pg_stats);
+    double st[5] = {0, 0, 0, 0, 0};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(st, c.d_pg_stats, sizeof(st), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) {
+        c.err = std::string("CUDA error in solve: ") + cudaGetErrorString(e);
+        return NRS_ECUDA;
+    }
+    return finish_solve(c, b, x, rep, inner_out, (int)st[0], (int)st[1], st[2] != 0.0, st + 3);
+}
+
 nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0, nrs_solve_report *rep,
                         int *inner_out)
 {
+    if (c.solve_mode == 0 && pg_supported(c)) return run_gmres_ir_device(c, b, x, x0, rep, inner_out);
     const int64_t n = c.n;
     const int m = c.max_inner;
     const int64_t ldv = c.lda;
@@ -607,6 +629,27 @@ nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0, nr
             break;
         }
     }
+#undef CKE
+    return finish_solve(c, b, x, rep, inner_out, outer, inner_total, converged);
+}
+
+// Status word, statistics and (when asked) the backward error of a finished
+// solve; dn_xn (host, or NULL to read them from d_scal) = ||d||_inf, ||x||_inf
+// of the last refinement step.
+static nrs_status finish_solve(Ctx &c, const double *b, double *x, nrs_solve_report *rep,
+                               int *inner_out, int outer, int inner_total, bool converged,
+                               const double *dn_xn)
+{
+    const int64_t n = c.n;
+    cudaError_t e = cudaSuccess;
+#define CKE(call)                                                           \
+    do {                                                                    \
+        e = (call);                                                         \
+        if (e != cudaSuccess) {                                             \
+            c.err = std::string("CUDA error in solve: ") + cudaGetErrorString(e); \
+            return NRS_ECUDA;                                               \
+        }                                                                   \
+    } while (0)
     int32_t st = 0;
     CKE(cudaMemcpyAsync(&st, c.d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
     CKE(cudaStreamSynchronize(c.stream));
@@ -632,8 +675,9 @@ nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0, nr
         rep->outer = outer;
         rep->inner = inner_total;
         rep->converged = converged ? 1 : 0;
-        rep->backward_err = sc[SC_RN] / (sc[SC_AN] * sc[SC_XN] + sc[SC_BN]);
-        rep->last_update = sc[SC_XN] > 0 ? sc[SC_DN] / sc[SC_XN] : 0.0;
+        const double dn = dn_xn ? dn_xn[0] : sc[SC_DN], xn = dn_xn ? dn_xn[1] : sc[SC_XN];
+        rep->backward_err = sc[SC_RN] / (sc[SC_AN] * xn + sc[SC_BN]);
+        rep->last_update = xn > 0 ? dn / xn : 0.0;
         rep->status = NRS_OK;
     }
 #undef CKE
@@ -643,7 +687,7 @@ nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0, nr
     else if (!converged) out = NRS_ENOCONV;
     if (rep) rep->status = out;
     if (out != NRS_OK) {
-        c.err = out == NRS_ETIMEOUT     ? "a triangular-solve wait ran out"
+        c.err = out == NRS_ETIMEOUT     ? "a bounded device wait ran out"
                 : out == NRS_ENONFINITE ? "non-finite value in the refinement"
                                         : "refinement did not reach the tolerance";
     }

@@ -67,7 +67,8 @@ class ProblemDesc(ctypes.Structure):
                 ("reuse_factor", ctypes.c_int32),
                 ("reuse_max_inner", ctypes.c_int32),
                 ("reuse_max_stages", ctypes.c_int32),
-                ("warm_start", ctypes.c_int32)]
+                ("warm_start", ctypes.c_int32),
+                ("solve_mode", ctypes.c_int32)]
 
 
 class SolveReport(ctypes.Structure):
@@ -158,7 +159,8 @@ class Context:
                  U=None, Omega=None, nn_global: bool = False, factor_prec: str = "fp32",
                  tol: float = 0.0, max_outer: int = 0, max_inner: int = 0,
                  reuse_factor: bool = False, reuse_max_inner: int = 0, reuse_max_stages: int = 0,
-                 warm_start: bool = False, stream: Optional[torch.cuda.Stream] = None):
+                 warm_start: bool = False, solve_mode: str = "device",
+                 stream: Optional[torch.cuda.Stream] = None):
         self._n_off = np.ascontiguousarray(n_off, dtype=np.int64)
         self._q_off = np.ascontiguousarray(q_off, dtype=np.int64)
         self._kind = np.ascontiguousarray(kind, dtype=np.int32)
@@ -182,6 +184,7 @@ class Context:
         d.max_outer, d.max_inner = int(max_outer), int(max_inner)
         d.reuse_factor, d.warm_start = int(bool(reuse_factor)), int(bool(warm_start))
         d.reuse_max_inner, d.reuse_max_stages = int(reuse_max_inner), int(reuse_max_stages)
+        d.solve_mode = {"device": 0, "host": 1}[solve_mode]
         self.stream = stream or torch.cuda.current_stream()
         self._h = ctypes.c_void_p()
         st = _lib.nrs_create(ctypes.byref(self._h), ctypes.byref(d),
