@@ -7,13 +7,18 @@ swimmer (N = 800 force points, Q = 8000 quadrature points, eps = 0.005,
 n = 2406 unknowns): twice (kinematics, nearest neighbours, segments, FP64
 assembly, rigid-body border, explicit FP32 inverse by blocked Gauss-Jordan
 with split-TF32 tensor-core updates, FP64 GMRES-based iterative refinement to
-the FP64 answer) plus the state update.  Inputs are the seeded synthetic beat
-shapes of `synth` (the paper's cited beat patterns are not available),
-resident in HBM before the timed region.
+the FP64 answer as one cooperative launch) plus the state update, recorded once
+into a CUDA graph and replayed.  Inputs are the seeded synthetic beat shapes of
+`synth` (the paper's cited beat patterns are not available), resident in HBM
+before the timed region.  Beside the headline: the same step launched kernel by
+kernel, with the host-driven refinement loop, with factor reuse, with the
+learned start, the plain FP64 path, and (N = 1) the batch workload of many
+uneven problems in one graph.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nrs|reference]
                     [--prec tf32|fp32|fp64]
     python bench.py --profile-solve --workload swimmer_mid   # one solve, for ncu
+    python bench.py --no-batch --no-cpu-baseline             # the C1 lines only
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 on the same workload.  Under torchrun each rank runs its own replica of the
@@ -258,41 +263,60 @@ def run_nrs(args):
     host = [(_shapes_host(pr, s * dt), _shapes_host(pr, (s + 0.5) * dt)) for s in range(total)]
     dev = [tuple(tuple(t.cuda() for t in st) for st in pair) for pair in host]
     Y0 = g.initial_state(pr)
-    ctx = nrs.Context.from_problem(pr, factor_prec=args.prec)
+    # the product path: the step recorded once into a CUDA graph and replayed
+    # (graph mode); each step's shapes are first copied into the fixed
+    # buffers the graph reads, inside the timed region
+    ctx = nrs.Context.from_problem(pr, factor_prec=args.prec, graph=True)
     ctx.set_state(Y0["x0"], Y0["B"])
     stream = ctx.stream
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    gbuf = tuple(tuple(torch.empty_like(t) for t in st) for st in dev[0])
 
     def do_step(ctx_, pair):
         s0 = nrs.Context.shapes(*pair[0])
         sh = nrs.Context.shapes(*pair[1])
         return ctx_.step(s0, sh, dt)
 
+    def graph_step(ctx_, pair):
+        for st_src, st_dst in zip(pair, gbuf):
+            for src, dst in zip(st_src, st_dst):
+                dst.copy_(src, non_blocking=True)
+        return ctx_.step(nrs.Context.shapes(*gbuf[0]), nrs.Context.shapes(*gbuf[1]), dt,
+                         report=False)
+
+    def eager_step(ctx_, pair):
+        return ctx_.step(nrs.Context.shapes(*pair[0]), nrs.Context.shapes(*pair[1]), dt,
+                         report=False)
+
     reports = []
     for s in range(W):
-        reports.append(do_step(ctx, dev[s]))
+        graph_step(ctx, dev[s])
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
 
-    def timed_pass(ctx_, first):
+    def timed_pass(ctx_, first, fn=do_step):
         ms = []
         for s in range(K):
             flush.fill_(float(s))  # evict L2 between timed steps (untimed)
             torch.cuda.synchronize()
             with torch.cuda.stream(stream):
                 ev[s][0].record(stream)
-                reports.append(do_step(ctx_, dev[first + s]))
+                r = fn(ctx_, dev[first + s])
                 ev[s][1].record(stream)
+            if r is not None:
+                reports.append(r)
             torch.cuda.synchronize()
             ms.append(ev[s][0].elapsed_time(ev[s][1]))
         return ms
 
     # the timed region: K steps, no instrumentation inside the library
+    ctx.get_timing()  # clears the kernel count
     with ClockSampler(_visible_gpu_index(local)) as clk:
-        step_ms = timed_pass(ctx, W)
+        step_ms = timed_pass(ctx, W, graph_step)
     clocks = clk.summary()
+    _, launches = ctx.get_timing()
     # a second pass over the same inputs with CUDA events around every phase of
     # the step (on the stream each phase runs on): per-kernel durations for
     # the roofline, and the kernel count
@@ -304,7 +328,7 @@ def run_nrs(args):
     ctx_t.set_timing(True)
     nrep_t = len(reports)
     step_ms_instr = timed_pass(ctx_t, W)
-    phases, launches = ctx_t.get_timing()
+    phases, _ = ctx_t.get_timing()
     instr_reports = reports[nrep_t:]
     solve_stats = {
         "outer_mean": float(np.mean([r["stages"][i]["outer"] for r in instr_reports for i in (0, 1)])),
@@ -321,7 +345,7 @@ def run_nrs(args):
 
     # end to end through the C ABI from pinned host buffers: H2D of both
     # stages' shapes and D2H of the new state and both solutions, every step
-    ctx_e = nrs.Context.from_problem(pr, factor_prec=args.prec)
+    ctx_e = nrs.Context.from_problem(pr, factor_prec=args.prec, graph=True)
     ctx_e.set_state(Y0["x0"], Y0["B"])
     bufs = tuple(tuple(torch.empty_like(t, device="cuda") for t in st) for st in host[0])
     sol = torch.empty(2 * pr.n, dtype=torch.float64, device="cuda")
@@ -329,7 +353,11 @@ def run_nrs(args):
     h2d = sum(t.numel() * t.element_size() for st in host[0] for t in st)
     d2h = sol_h.numel() * 8 + pr.n_free * 12 * 8
     for s in range(W):
-        do_step(ctx_e, dev[s])
+        for st_h, st_d in zip(host[s], bufs):
+            for th, td in zip(st_h, st_d):
+                td.copy_(th, non_blocking=True)
+        ctx_e.step(nrs.Context.shapes(*bufs[0]), nrs.Context.shapes(*bufs[1]), dt, sol=sol,
+                   report=False)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e_ms = 0.0
@@ -377,6 +405,15 @@ def run_nrs(args):
     torch.cuda.synchronize()
     host_loop_s = float(np.sum(timed_pass(ctx_h, W))) / 1e3 / K / ws
     ctx_h.close()
+
+    # the same step without the graph (kernels launched one by one)
+    ctx_eg = nrs.Context.from_problem(pr, factor_prec=args.prec)
+    ctx_eg.set_state(Y0["x0"], Y0["B"])
+    for s in range(W):
+        eager_step(ctx_eg, dev[s])
+    torch.cuda.synchronize()
+    eager_s = float(np.sum(timed_pass(ctx_eg, W, eager_step))) / 1e3 / K / ws
+    ctx_eg.close()
 
     # factor reuse across stages + warm start (same inputs, same timing rules)
     ctx_r = nrs.Context.from_problem(pr, factor_prec=args.prec, reuse_factor=True, warm_start=True)
@@ -466,6 +503,7 @@ def run_nrs(args):
         "plain_fp64_s_per_step": plain_s,
         "mixed_vs_plain_speedup": plain_s / (t_max / K),
         "host_loop_refinement_s_per_step": host_loop_s,
+        "eager_s_per_step": eager_s,
         "value_factor_reuse": reuse_s,
         "factor_reuse": {"s_per_step": reuse_s, "vs_plain_speedup": plain_s / (reuse_s * ws),
                          "factorizations_per_step": float(np.mean([r["factorizations"] for r in reuse_reports])),
@@ -480,16 +518,18 @@ def run_nrs(args):
         "phases_ms_per_step": {k: v / K for k, v in ph_ms.items()},
         "phase_share": {k: (v / tot if tot else 0.0) for k, v in ph_ms.items()},
         "phase_note": "lu_diag runs on a second stream, overlapping lu_update and lu_panel",
-        "refinement": {"outer_mean": float(np.mean([r["stages"][i]["outer"] for r in reports[W:W + K] for i in (0, 1)])),
-                       "inner_mean": float(np.mean([r["stages"][i]["inner"] for r in reports[W:W + K] for i in (0, 1)])),
-                       "backward_err_max": float(max(r["stages"][i]["backward_err"] for r in reports[W:W + K] for i in (0, 1)))},
+        "refinement": {"outer_mean": solve_stats["outer_mean"], "inner_mean": solve_stats["inner_mean"],
+                       "backward_err_max": float(max(r["stages"][i]["backward_err"] for r in instr_reports for i in (0, 1))),
+                       "from": "the instrumented eager pass (same kernels, same inputs)"},
         "roofline": roof,
         "rooflines": recs,
         "e2e": {"value": e2e_s, "unit": "s/step", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "gpu_launches_note": "counted by the library during the instrumented pass of the same K steps",
+        "gpu_launches_note": "kernels of the recorded step graph replayed in the timed region, counted by the library",
         "clocks": clocks,
     }
+    if not args.no_batch and ws == 1:
+        line["batch"] = batch_bench(nrs, args)
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(pr, sols)
     print(json.dumps(line), flush=True)
@@ -511,6 +551,99 @@ def _oracle_step_timing(pr, max_steps, budget_s):
         if sum(times) > budget_s:
             break
     return times, all_stages, O.threads()
+
+
+def _batch_case(nrs, probs, prec, steps, tune=True):
+    """Seconds per batch step of ``probs`` through one recorded graph (K and G
+    from the autotuner), and the same problems stepped one after the other
+    on eager contexts, from the same initial states and inputs."""
+    import torch
+    dt = probs[0].dt
+    host = [[tuple(torch.from_numpy(np.ascontiguousarray(sh[k])).cuda() for k in ("x", "Xw", "xidot"))
+             for sh in (g.pack_shapes(pr, s * dt), g.pack_shapes(pr, (s + 0.5) * dt))]
+            for s in range(steps + 2) for pr in probs]
+    nprob = len(probs)
+
+    def pairs_at(s):
+        return [tuple(host[s * nprob + i]) for i in range(nprob)]
+
+    batch = nrs.Batch(probs, factor_prec=prec)
+    for c, pr in zip(batch.contexts, probs):
+        Y = g.initial_state(pr)
+        c.set_state(Y["x0"], Y["B"])
+    bufs = [tuple(tuple(torch.empty_like(t) for t in st) for st in pair) for pair in pairs_at(0)]
+
+    def load(s):
+        for pair, buf in zip(pairs_at(s), bufs):
+            for st_src, st_dst in zip(pair, buf):
+                for src, dst in zip(st_src, st_dst):
+                    dst.copy_(src, non_blocking=True)
+        return bufs
+
+    batch.step(load(0), dt)  # first step: nearest-neighbour maps, eager
+    tuned = batch.tune(load(1), dt) if tune else batch.info()
+    batch.step(load(1), dt)  # records the graph with the tuned plan
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st = torch.cuda.current_stream()
+    ms = 0.0
+    for s in range(steps):
+        torch.cuda.synchronize()
+        e0.record(st)
+        batch.step(load(2 + s), dt)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    info = batch.info()
+    batch.close()
+    # eager, one problem after the other
+    ctxs = []
+    for pr in probs:
+        c = nrs.Context.from_problem(pr, factor_prec=prec)
+        Y = g.initial_state(pr)
+        c.set_state(Y["x0"], Y["B"])
+        ctxs.append(c)
+    for s in range(2):
+        for i, c in enumerate(ctxs):
+            a, b = pairs_at(s)[i]
+            c.step(nrs.Context.shapes(*a), nrs.Context.shapes(*b), dt, report=False)
+    torch.cuda.synchronize()
+    ms_seq = 0.0
+    for s in range(steps):
+        torch.cuda.synchronize()
+        e0.record(st)
+        for i, c in enumerate(ctxs):
+            a, b = pairs_at(2 + s)[i]
+            c.step(nrs.Context.shapes(*a), nrs.Context.shapes(*b), dt, report=False)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms_seq += e0.elapsed_time(e1)
+    for c in ctxs:
+        c.close()
+    ns = [pr.n for pr in probs]
+    return {"problems": nprob, "n_min": min(ns), "n_max": max(ns), "n_mean": float(np.mean(ns)),
+            "pairs": int(sum(pr.pairs for pr in probs)),
+            "s_per_batch_step": ms / 1e3 / steps,
+            "problem_steps_per_s": nprob * steps / (ms / 1e3),
+            "sequential_eager_s_per_batch_step": ms_seq / 1e3 / steps,
+            "speedup_vs_sequential": ms_seq / ms, "steps": steps,
+            "chains": info["chains"], "solve_grid": info["grid"],
+            "graph_kernels": info["graph_kernels"],
+            "tuned_ms": tuned.get("ms")}
+
+
+def batch_bench(nrs, args):
+    """The batch workload: 128 ventral-node-like problems at reduced sizes
+    (all of them), and the first 8 at the full sizes."""
+    small = [g.node_config(i, cilia=(4, 12), floor=(160, 500), n_rod=10, q_rod=100, n_sphere=2,
+                           q_sphere=8) for i in range(128)]
+    full = [g.node_config(i) for i in range(8)]
+    return {"workload": "ventral-node batch: cilia rotating on tilted cones, static floor disc, "
+                        "5 free spheres; eps 0.005",
+            "reduced_128": dict(_batch_case(nrs, small, args.prec, 3),
+                                recipe="cilia 4-12 (10/100 points), floor 160-500 (x10), spheres 26/386"),
+            "full_first8": dict(_batch_case(nrs, full, args.prec, 2),
+                                recipe="the batch recipe at full size, problems 0-7")}
 
 
 def cpu_baseline(pr, sols):
@@ -596,6 +729,7 @@ def main():
     ap.add_argument("--impl", default="nrs", choices=["nrs", "reference"])
     ap.add_argument("--prec", default="tf32", choices=["fp32", "tf32", "bf16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batch workload section")
     ap.add_argument("--profile-solve", action="store_true",
                     help="one kinematics + nearest + assemble + factor + solve on --workload, "
                          "then exit (for ncu captures)")

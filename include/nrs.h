@@ -97,6 +97,16 @@ typedef struct {
                               the whole refinement of one right-hand side is one cooperative
                               launch (no host round trip inside a solve); 1: host-driven loop
                               (one synchronisation per GMRES iteration), the FP64 path's mode */
+    int32_t graph;         /* 1: nrs_step records the whole step into a CUDA graph and replays it
+                              (from the second call on: the first call builds the nearest-
+                              neighbour maps of the rigid bodies).  The recording is keyed by
+                              the six shape pointers, dt and whether a report is asked for; a
+                              call with another key records again, so callers reuse the same
+                              shape buffers.  Needs factor_prec FP32/TF32, solve_mode 0,
+                              reuse_factor 0, max_inner <= 64 (else nrs_create returns
+                              NRS_EINVAL); the learned start and phase timing run the step
+                              without the graph.  backward_err is reported as computed in the
+                              graph. */
 } nrs_problem_desc;
 
 typedef struct {
@@ -339,6 +349,71 @@ nrs_status nrs_mlp_features(nrs_ctx *ctx, const nrs_shapes *s, const double *vpr
 /* Start vector x0 (device [n]) from predictions Y (device [N*3]): f_m = F B y_m
  * with the context's B, then (U, Omega) = vprev (device [6F] or NULL = zero). */
 nrs_status nrs_mlp_start(nrs_ctx *ctx, const float *Y, const double *vprev, double *x0);
+
+/* ---- batches of independent problems ----------------------------------------
+ * Many problems of uneven size stepped together (the paper solves one problem
+ * at a time; this is how a GB300 is filled with many smaller ones).  Each
+ * problem is an nrs_ctx owned by the batch, on a stream of its own.  From the
+ * second nrs_batch_step on, the steps of ALL problems are recorded into one
+ * CUDA graph and replayed by one cudaGraphLaunch per batch step: the problems
+ * are split into K chains by longest-processing-time-first on an estimate of
+ * their step time (the problems of a chain run in sequence, the chains
+ * concurrently), and every refinement is one cooperative launch of G CTAs
+ * with K * G at most the co-resident CTA count of that kernel.  The graph is
+ * keyed by all shape pointers, dt and whether reports are asked for; reuse
+ * the same shape buffers between steps to replay it. */
+typedef struct nrs_batch nrs_batch;
+
+/* Create a batch of count problems (host array of descriptions, read during
+ * the call).  Every description must allow the recorded step: factor_prec
+ * FP32 or TF32, solve_mode 0, reuse_factor 0, max_inner <= 64 (else
+ * NRS_EINVAL); its graph field is ignored.  stream: the caller's cudaStream_t
+ * (NULL = legacy default stream), on which nrs_batch_step's work is ordered.
+ * Starts with K = min(count, 4) chains. */
+nrs_status nrs_batch_create(nrs_batch **out, const nrs_problem_desc *descs, int32_t count,
+                            void *stream);
+/* Destroy the batch and all its contexts (synchronises). */
+nrs_status nrs_batch_destroy(nrs_batch *b);
+const char *nrs_batch_last_error(const nrs_batch *b);
+
+/* The context of problem i, for nrs_set_state / nrs_get_state /
+ * nrs_set_external / nrs_sizes.  The batch owns it: do not destroy it, and do
+ * not step it on its own while the batch is in use. */
+nrs_status nrs_batch_context(nrs_batch *b, int32_t i, nrs_ctx **ctx);
+
+/* One RK2 step of every problem: s0[i], s_half[i] as for nrs_step (device
+ * shapes), sol (host array of count device pointers [2 n_i], or NULL; an
+ * entry may be NULL), reports (host array of count, or NULL; synchronises).
+ * The first call runs the problems' steps one after the other without the
+ * graph.  Returns the worst status over the problems. */
+nrs_status nrs_batch_step(nrs_batch *b, const nrs_shapes *s0, const nrs_shapes *s_half, double dt,
+                          double *const *sol, nrs_step_report *reports);
+
+/* Set K (1 <= K <= count) and G (K * G <= co-resident CTAs of the solve
+ * kernel) and re-plan; chain_of (host [count] or NULL) receives each
+ * problem's chain.  The next step records the graph again. */
+nrs_status nrs_batch_config(nrs_batch *b, int32_t chains, int32_t grid, int32_t *chain_of);
+
+/* Autotune (K, G): time one replayed batch step for each K in {1, 2, 4, 8,
+ * 16} (<= count) and G in {SMs, SMs/2, SMs/4} (capped by the co-residency
+ * bound), keep the fastest.  Every trial starts from the batch's state at
+ * the call, which is restored afterwards.  Needs one nrs_batch_step first.
+ * cache_path (or NULL): text file of "<key> <K> <G> <ms>" lines; the key
+ * names the device and the sorted problem sizes.  A cached entry is used
+ * without timing (ms_out = -1); a new result is appended. */
+nrs_status nrs_batch_tune(nrs_batch *b, const nrs_shapes *s0, const nrs_shapes *s_half, double dt,
+                          const char *cache_path, int32_t *chains_out, int32_t *grid_out,
+                          double *ms_out);
+
+/* Current K, G and the number of kernels in the recorded graph (0 if none). */
+nrs_status nrs_batch_info(const nrs_batch *b, int32_t *chains, int32_t *grid,
+                          int64_t *graph_kernels);
+
+/* Longest-processing-time-first plan on its own (host only, no device):
+ * order = problems by decreasing cost (ties: lower index first), each given
+ * to the chain with the least cost so far (ties: lower chain). */
+nrs_status nrs_batch_plan(const double *cost, int32_t count, int32_t chains, int32_t *chain_of,
+                          int32_t *order);
 
 /* Phases of the step, as timed by nrs_get_timing. */
 enum {

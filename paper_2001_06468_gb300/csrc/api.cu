@@ -92,6 +92,7 @@ nrs_status alloc_all(Ctx *c)
         {(void **)&c->d_dpart, sizeof(double) * nrs::pg_dpart_doubles(c->max_inner)},
         {(void **)&c->d_bar, sizeof(int32_t) * 2},
         {(void **)&c->d_pg_stats, sizeof(double) * 8},
+        {(void **)&c->d_step_stats, sizeof(double) * 16},
     };
     for (auto &r : req) {
         *r.p = nullptr;
@@ -116,7 +117,8 @@ void free_all(Ctx *c)
                     c->d_lperm,  c->d_info,   c->d_r,      c->d_xk,         c->d_w,
                     c->d_V,      c->d_H,      c->d_gv,     c->d_scal,       c->d_part,
                     c->d_t32,    c->d_t64,    c->d_flags,  c->d_status,     c->d_gj_dinv,
-                    c->d_gj_rt,  c->d_gj_cb,  c->d_dpart,  c->d_bar,        c->d_pg_stats};
+                    c->d_gj_rt,  c->d_gj_cb,  c->d_dpart,  c->d_bar,        c->d_pg_stats,
+                    c->d_step_stats};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *mlp[] = {c->d_mlp_params, c->d_mlp_m,  c->d_mlp_v,     c->d_mlp_g,    c->d_mlp_x,
@@ -132,8 +134,12 @@ void free_all(Ctx *c)
     if (c->ev_prep) cudaEventDestroy(c->ev_prep);
     if (c->ev_diag) cudaEventDestroy(c->ev_diag);
     if (c->stream2) cudaStreamDestroy(c->stream2);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
     c->ev_prep = c->ev_diag = nullptr;
     c->stream2 = nullptr;
+    c->gexec = nullptr;
+    c->gstream = nullptr;
 }
 
 bool is_prec(int p) { return p == NRS_FP64 || p == NRS_FP32 || p == NRS_TF32 || p == NRS_BF16; }
@@ -243,6 +249,145 @@ nrs_status mlp_alloc(Ctx *c)
 
 }  // namespace
 
+namespace nrs {
+
+bool graph_capable(const Ctx &c)
+{
+    return c.factor_prec != NRS_FP64 && c.solve_mode == 0 && c.max_inner <= 64 &&
+           !c.reuse_factor && !c.mlp_predict && c.mlp_train_iters == 0 && !c.timing &&
+           c.nn_valid && c.seg_valid;
+}
+
+nrs_status enqueue_step(Ctx *c, const nrs_shapes *s0, const nrs_shapes *sh, double dt,
+                        double *stats, bool berr)
+{
+    CK(cudaMemcpyAsync(c->d_x0_save, c->d_x0, sizeof(double) * 3 * c->nbodies,
+                       cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_B_save, c->d_B, sizeof(double) * 9 * c->nbodies,
+                       cudaMemcpyDeviceToDevice, c->stream));
+    for (int stage = 0; stage < 2; ++stage) {
+        const nrs_shapes *s = stage ? sh : s0;
+        launch_kinematics(*c, (const D4 *)s->xi, (const D4 *)s->Xiw, (const D4 *)s->xidot, c->d_x,
+                          c->d_Xw, c->d_b);
+        if (c->nn_global) {
+            launch_nearest(*c, c->d_x, c->d_Xw, c->d_nn, false);
+            launch_segments(*c, c->d_nn, c->d_seg_ptr, c->d_perm);
+        } else if (c->n_tasks_deform > 0) {
+            launch_nearest(*c, (const D4 *)s->xi, (const D4 *)s->Xiw, c->d_nn, true);
+            launch_segments(*c, c->d_nn, c->d_seg_ptr, c->d_perm);
+        }
+        nrs_status st = do_segments_and_assemble(c, c->d_x, c->d_Xw, true);
+        if (st != NRS_OK) return st;
+        st = do_factor(c, c->factor_prec);
+        if (st != NRS_OK) return st;
+        double *out = c->d_sol + (int64_t)stage * c->lda;
+        const double *prev = c->have_sol ? c->d_sol + (int64_t)(1 - stage) * c->lda : nullptr;
+        const bool warm = c->warm_start && prev;
+        if (warm)
+            CK(cudaMemcpyAsync(out, prev, sizeof(double) * c->n, cudaMemcpyDeviceToDevice,
+                               c->stream));
+        double *so = stats + 8 * stage;
+        CK(launch_gmres_persistent(*c, c->d_b, out, !warm, so));
+        if (berr) enqueue_backward_error(*c, c->d_b, out, so + 5);
+        launch_rk2(*c, stage, dt, out);
+        CK(cudaGetLastError());
+    }
+    return NRS_OK;
+}
+
+}  // namespace nrs
+
+namespace {
+
+// nrs_step through a recorded CUDA graph (graph mode, see include/nrs.h).
+nrs_status step_graph(Ctx *c, const nrs_shapes *s0, const nrs_shapes *sh, double dt, double *sol,
+                      nrs_step_report *report)
+{
+    Ctx::GraphKey key{{s0->xi, s0->Xiw, s0->xidot, sh->xi, sh->Xiw, sh->xidot}, dt,
+                      report != nullptr};
+    if (!c->gexec || !(key == c->gkey)) {
+        cudaStream_t user = c->stream;
+        c->stream = c->gstream;
+        const int64_t l0 = c->launches;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        nrs_status st = e == cudaSuccess ? nrs::enqueue_step(c, s0, sh, dt, c->d_step_stats,
+                                                             key.berr)
+                                         : NRS_ECUDA;
+        cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(c->stream, &g) : e;
+        c->stream = user;
+        c->graph_launches = c->launches - l0;
+        c->launches = l0;
+        if (st != NRS_OK || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return fail(c, st != NRS_OK ? st : NRS_ECUDA,
+                        std::string("recording the step graph failed: ") + cudaGetErrorString(e2));
+        }
+        if (c->gexec) cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+        e = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->gexec = nullptr;
+            return fail(c, NRS_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        }
+        c->gkey = key;
+        c->graph_captures += 1;
+    }
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (report) {
+        CK(cudaEventCreate(&ev0));
+        CK(cudaEventCreate(&ev1));
+        CK(cudaEventRecord(ev0, c->stream));
+    }
+    CK(cudaGraphLaunch(c->gexec, c->stream));
+    c->launches += c->graph_launches;
+    c->have_sol = true;
+    c->factored_prec = c->factor_prec;
+    c->factorizations += 2;
+    if (sol) {
+        CK(cudaMemcpyAsync(sol, c->d_sol, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(sol + c->n, c->d_sol + c->lda, sizeof(double) * c->n,
+                           cudaMemcpyDeviceToDevice, c->stream));
+    }
+    if (!report) return NRS_OK;
+    CK(cudaEventRecord(ev1, c->stream));
+    CK(cudaEventSynchronize(ev1));
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    double st[16];
+    int32_t word = 0;
+    CK(cudaMemcpy(st, c->d_step_stats, sizeof(st), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&word, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(c->d_status, 0, sizeof(int32_t)));
+    nrs_status worst = NRS_OK;
+    for (int k = 0; k < 2; ++k) {
+        const double *q = st + 8 * k;
+        nrs_solve_report &r = report->stage[k];
+        r.outer = (int32_t)q[0];
+        r.inner = (int32_t)q[1];
+        r.converged = q[2] != 0.0;
+        r.last_update = q[4] > 0 ? q[3] / q[4] : 0.0;
+        r.backward_err = q[5] / (q[6] * q[4] + q[7]);
+        r.status = (word & nrs::ST_TIMEOUT)     ? NRS_ETIMEOUT
+                   : (word & nrs::ST_NONFINITE) ? NRS_ENONFINITE
+                   : !r.converged               ? NRS_ENOCONV
+                                                : NRS_OK;
+        if (r.status != NRS_OK && worst == NRS_OK) worst = (nrs_status)r.status;
+        report->start[k] = c->warm_start ? 1 : 0;
+    }
+    report->ms_total = ms;
+    report->factorizations = 2;
+    report->mlp_rel_err = -1.0;
+    if (worst != NRS_OK) c->err = "a stage of the recorded step did not converge cleanly";
+    return worst;
+}
+
+}  // namespace
+
 extern "C" {
 
 nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
@@ -299,6 +444,12 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
     c->reuse_max_stages = d->reuse_max_stages > 0 ? d->reuse_max_stages : 16;
     c->warm_start = d->warm_start ? 1 : 0;
     c->solve_mode = d->solve_mode ? 1 : 0;
+    c->graph_mode = d->graph ? 1 : 0;
+    if (c->graph_mode && (d->factor_prec == NRS_FP64 || c->solve_mode != 0 || d->reuse_factor ||
+                          (d->max_inner > 64))) {
+        delete c;
+        return NRS_EINVAL;
+    }
     {
         // enough column splits for about two CTAs per SM in the matrix-vector products
         auto splits = [&](int64_t rows_per_cta) {
@@ -368,6 +519,8 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
         cudaDeviceGetStreamPriorityRange(&least, &greatest);
         e = cudaStreamCreateWithPriority(&c->stream2, cudaStreamNonBlocking, greatest);
     }
+    if (e == cudaSuccess && c->graph_mode)
+        e = cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_prep, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_diag, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -526,6 +679,7 @@ nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *sh, do
     if (!c || !s0 || !sh || !s0->xi || !s0->Xiw || !s0->xidot || !sh->xi || !sh->Xiw || !sh->xidot)
         return fail(c, NRS_EINVAL, "nrs_step: null argument");
     if (!(dt > 0.0)) return fail(c, NRS_EINVAL, "nrs_step: dt must be positive");
+    if (c->graph_mode && nrs::graph_capable(*c)) return step_graph(c, s0, sh, dt, sol, report);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (report) {
         CK(cudaEventCreate(&ev0));

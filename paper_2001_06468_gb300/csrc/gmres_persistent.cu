@@ -480,6 +480,13 @@ int pg_grid(Ctx &c)
     return c.pg_grid;
 }
 
+int pg_max_coresident(const Ctx &c)
+{
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gmres_ir, PG_THREADS, 0);
+    return std::max(1, per_sm) * c.num_sms;
+}
+
 size_t pg_dpart_doubles(int max_inner) { return (size_t)3 * PG_MAXCH * (max_inner + 2); }
 
 // One refinement of A x = b on the device.  Fills stats[0..4] (device) as

@@ -87,7 +87,16 @@ nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0,
 // explicit-inverse factors and restart lengths up to 64.
 bool pg_supported(const Ctx &c);
 size_t pg_dpart_doubles(int max_inner);
+int pg_max_coresident(const Ctx &c);  // CTAs of the solve kernel that fit on the device at once
 cudaError_t launch_gmres_persistent(Ctx &c, const double *b, double *x, bool cold, double *stats);
+// out3[0..2] (device) = ||b - A x||_inf, ||A||_inf, ||b||_inf
+void enqueue_backward_error(Ctx &c, const double *b, const double *x, double *out3);
+// One RK2 step enqueued with no host synchronisation (api.cu); valid when
+// graph_capable(c).  stats: 8 doubles per stage (outer, inner, converged,
+// ||d||, ||x||, then with berr ||b - A x||, ||A||, ||b||).
+bool graph_capable(const Ctx &c);
+nrs_status enqueue_step(Ctx *c, const nrs_shapes *s0, const nrs_shapes *sh, double dt,
+                        double *stats, bool berr);
 // x0 = whichever of xp and the cold start xc = M^{-1} b has the smaller
 // ||b - A x||_inf (norms[0], norms[1]); c.d_mlp_used[0] records the choice.
 cudaError_t choose_start(Ctx &c, const double *b, const double *xp, double *xc, double *x0,
@@ -190,6 +199,26 @@ struct Ctx {
     int32_t *d_bar = nullptr;  // its grid barrier
     double *d_pg_stats = nullptr;  // its outcome: outer, inner, converged, ||d||, ||x||
     int pg_grid = 0;           // its CTA count (0 = from occupancy)
+
+    // CUDA-graph replay of nrs_step (graph mode)
+    struct GraphKey {
+        const void *p[6];
+        double dt;
+        bool berr;
+        bool operator==(const GraphKey &o) const
+        {
+            for (int i = 0; i < 6; ++i)
+                if (p[i] != o.p[i]) return false;
+            return dt == o.dt && berr == o.berr;
+        }
+    };
+    int graph_mode = 0;
+    cudaStream_t gstream = nullptr;     // capture stream (the legacy stream cannot be captured)
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey{};
+    int64_t graph_launches = 0;         // kernels in the recorded step
+    int64_t graph_captures = 0;
+    double *d_step_stats = nullptr;     // 16 doubles: per stage outcome of the device solve
     double *d_r = nullptr, *d_xk = nullptr, *d_w = nullptr, *d_V = nullptr, *d_H = nullptr;
     double *d_gv = nullptr;    // Givens state: cs[m], sn[m], g[m+1], y[m]
     double *d_scal = nullptr;  // scalars (norms, flags as doubles)

@@ -511,6 +511,20 @@ static double read_scalar(Ctx &c, int slot, cudaError_t *err)
     return v;
 }
 
+void enqueue_backward_error(Ctx &c, const double *b, const double *x, double *out3)
+{
+    gemv(c, x, b, c.d_r);
+    k_nrm_inf<<<1, RED_THREADS, 0, c.stream>>>(c.n, c.d_r, out3, 0);
+    const int64_t cps = ceil_div(c.n, c.splits64);
+    dim3 grid((unsigned)ceil_div(c.n, 2 * MV_THREADS), (unsigned)c.splits64);
+    k_gemv_part<true><<<grid, MV_THREADS, 0, c.stream>>>(c.n, c.d_A64, c.lda, nullptr, c.d_part, cps);
+    k_gemv_finish<<<(unsigned)ceil_div(c.n, 256), 256, 0, c.stream>>>(c.n, c.d_part, c.splits64,
+                                                                      nullptr, c.d_w);
+    k_nrm_inf<<<1, RED_THREADS, 0, c.stream>>>(c.n, c.d_w, out3, 1);
+    k_nrm_inf<<<1, RED_THREADS, 0, c.stream>>>(c.n, b, out3, 2);
+    c.launches += 5;
+}
+
 cudaError_t choose_start(Ctx &c, const double *b, const double *xp, double *xc, double *x0,
                          double *norms)
 {

@@ -39,7 +39,10 @@ EXPORTS = ["nrs_create", "nrs_destroy", "nrs_last_error", "nrs_sizes", "nrs_set_
            "nrs_assemble", "nrs_factor", "nrs_solve", "nrs_step", "nrs_sync", "nrs_set_timing",
            "nrs_get_timing", "nrs_rank64_update", "nrs_nearest_build_static",
            "nrs_mlp_set_params", "nrs_mlp_get_params", "nrs_mlp_config", "nrs_mlp_eval",
-           "nrs_mlp_adam", "nrs_mlp_features", "nrs_mlp_start"]
+           "nrs_mlp_adam", "nrs_mlp_features", "nrs_mlp_start",
+           "nrs_batch_create", "nrs_batch_destroy", "nrs_batch_last_error", "nrs_batch_context",
+           "nrs_batch_step", "nrs_batch_config", "nrs_batch_tune", "nrs_batch_info",
+           "nrs_batch_plan"]
 # the learned starting guess (NRS_MLP_* in include/nrs.h)
 MLP_IN, MLP_HID, MLP_OUT = 17, 64, 3
 MLP_PARAMS = MLP_HID * MLP_IN + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_OUT * MLP_HID + MLP_OUT
@@ -68,7 +71,8 @@ class ProblemDesc(ctypes.Structure):
                 ("reuse_max_inner", ctypes.c_int32),
                 ("reuse_max_stages", ctypes.c_int32),
                 ("warm_start", ctypes.c_int32),
-                ("solve_mode", ctypes.c_int32)]
+                ("solve_mode", ctypes.c_int32),
+                ("graph", ctypes.c_int32)]
 
 
 class SolveReport(ctypes.Structure):
@@ -122,6 +126,24 @@ _sig = {
     "nrs_mlp_adam": (ctypes.c_int, [_P, _P, ctypes.c_float]),
     "nrs_mlp_features": (ctypes.c_int, [_P, ctypes.POINTER(Shapes), _P, _P, _P, _P]),
     "nrs_mlp_start": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nrs_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(ProblemDesc),
+                                        ctypes.c_int32, _P]),
+    "nrs_batch_destroy": (ctypes.c_int, [_P]),
+    "nrs_batch_last_error": (ctypes.c_char_p, [_P]),
+    "nrs_batch_context": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
+    "nrs_batch_step": (ctypes.c_int, [_P, ctypes.POINTER(Shapes), ctypes.POINTER(Shapes),
+                                      ctypes.c_double, ctypes.POINTER(_P), ctypes.POINTER(StepReport)]),
+    "nrs_batch_config": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_int32)]),
+    "nrs_batch_tune": (ctypes.c_int, [_P, ctypes.POINTER(Shapes), ctypes.POINTER(Shapes),
+                                      ctypes.c_double, ctypes.c_char_p,
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "nrs_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32), _I64P]),
+    "nrs_batch_plan": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32)]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
@@ -159,58 +181,36 @@ class Context:
                  U=None, Omega=None, nn_global: bool = False, factor_prec: str = "fp32",
                  tol: float = 0.0, max_outer: int = 0, max_inner: int = 0,
                  reuse_factor: bool = False, reuse_max_inner: int = 0, reuse_max_stages: int = 0,
-                 warm_start: bool = False, solve_mode: str = "device",
-                 stream: Optional[torch.cuda.Stream] = None):
-        self._n_off = np.ascontiguousarray(n_off, dtype=np.int64)
-        self._q_off = np.ascontiguousarray(q_off, dtype=np.int64)
-        self._kind = np.ascontiguousarray(kind, dtype=np.int32)
-        nb = len(self._kind)
-        self._rigid = None if rigid is None else np.ascontiguousarray(rigid, dtype=np.int32)
-        self._U = None if U is None else np.ascontiguousarray(U, dtype=np.float64).reshape(nb * 3)
-        self._Om = None if Omega is None else np.ascontiguousarray(Omega, dtype=np.float64).reshape(nb * 3)
-        d = ProblemDesc()
-        d.nbodies = nb
-        d.n_off = _np_ptr(self._n_off, ctypes.c_int64)
-        d.q_off = _np_ptr(self._q_off, ctypes.c_int64)
-        d.kind = _np_ptr(self._kind, ctypes.c_int32)
-        d.rigid = None if self._rigid is None else _np_ptr(self._rigid, ctypes.c_int32)
-        d.U = None if self._U is None else _np_ptr(self._U, ctypes.c_double)
-        d.Omega = None if self._Om is None else _np_ptr(self._Om, ctypes.c_double)
-        d.eps, d.mu = float(eps), float(mu)
-        d.nn_global = int(bool(nn_global))
-        d.factor_prec = PREC[factor_prec]
-        d.nb = 0
-        d.tol = float(tol)
-        d.max_outer, d.max_inner = int(max_outer), int(max_inner)
-        d.reuse_factor, d.warm_start = int(bool(reuse_factor)), int(bool(warm_start))
-        d.reuse_max_inner, d.reuse_max_stages = int(reuse_max_inner), int(reuse_max_stages)
-        d.solve_mode = {"device": 0, "host": 1}[solve_mode]
+                 warm_start: bool = False, solve_mode: str = "device", graph: bool = False,
+                 stream: Optional[torch.cuda.Stream] = None, _handle=None):
+        d, self._keep = _make_desc(n_off, q_off, kind, eps, mu, rigid, U, Omega, nn_global,
+                                   factor_prec, tol, max_outer, max_inner, reuse_factor,
+                                   reuse_max_inner, reuse_max_stages, warm_start, solve_mode,
+                                   graph)
         self.stream = stream or torch.cuda.current_stream()
-        self._h = ctypes.c_void_p()
-        st = _lib.nrs_create(ctypes.byref(self._h), ctypes.byref(d),
-                             ctypes.c_void_p(self.stream.cuda_stream))
-        if st != NRS_OK:
-            raise NrsError(st, "nrs_create failed")
+        self._owner = _handle is None
+        if _handle is None:
+            self._h = ctypes.c_void_p()
+            st = _lib.nrs_create(ctypes.byref(self._h), ctypes.byref(d),
+                                 ctypes.c_void_p(self.stream.cuda_stream))
+            if st != NRS_OK:
+                raise NrsError(st, "nrs_create failed")
+        else:
+            self._h = _handle
         N, Q, F, n = (ctypes.c_int64() for _ in range(4))
         _lib.nrs_sizes(self._h, ctypes.byref(N), ctypes.byref(Q), ctypes.byref(F), ctypes.byref(n))
         self.N, self.Q, self.F, self.n = N.value, Q.value, F.value, n.value
-        self.nbodies = nb
+        self.nbodies = d.nbodies
 
     @classmethod
     def from_problem(cls, problem, factor_prec: str = "fp32", **kw) -> "Context":
         """Context for a ``synth.geometry.Problem`` (its body table and eps, mu)."""
-        n_off = np.cumsum([0] + [b.N for b in problem.bodies])
-        q_off = np.cumsum([0] + [b.Q for b in problem.bodies])
-        return cls(n_off, q_off, [b.kind for b in problem.bodies], problem.eps, problem.mu,
-                   rigid=[int(b.rigid) for b in problem.bodies],
-                   U=np.array([b.U for b in problem.bodies]),
-                   Omega=np.array([b.Omega for b in problem.bodies]),
-                   nn_global=problem.nn_global, factor_prec=factor_prec, **kw)
+        return cls(*_problem_args(problem), factor_prec=factor_prec, **kw)
 
     def close(self):
-        if getattr(self, "_h", None) and self._h.value:
+        if getattr(self, "_h", None) and self._h.value and getattr(self, "_owner", True):
             _lib.nrs_destroy(self._h)
-            self._h = ctypes.c_void_p()
+        self._h = ctypes.c_void_p()
 
     def __del__(self):
         try:
@@ -393,6 +393,146 @@ class Context:
         launches = ctypes.c_int64()
         self._check(_lib.nrs_get_timing(self._h, ms, spans, ctypes.byref(launches)))
         return {p: (ms[i], spans[i]) for i, p in enumerate(PHASES)}, launches.value
+
+
+def _problem_args(problem):
+    n_off = np.cumsum([0] + [b.N for b in problem.bodies])
+    q_off = np.cumsum([0] + [b.Q for b in problem.bodies])
+    return (n_off, q_off, [b.kind for b in problem.bodies], problem.eps, problem.mu,
+            [int(b.rigid) for b in problem.bodies], np.array([b.U for b in problem.bodies]),
+            np.array([b.Omega for b in problem.bodies]), problem.nn_global)
+
+
+def _make_desc(n_off, q_off, kind, eps, mu=1.0, rigid=None, U=None, Omega=None, nn_global=False,
+               factor_prec="fp32", tol=0.0, max_outer=0, max_inner=0, reuse_factor=False,
+               reuse_max_inner=0, reuse_max_stages=0, warm_start=False, solve_mode="device",
+               graph=False):
+    """An nrs_problem_desc and the host arrays it points to (keep them alive)."""
+    n_off = np.ascontiguousarray(n_off, dtype=np.int64)
+    q_off = np.ascontiguousarray(q_off, dtype=np.int64)
+    kind = np.ascontiguousarray(kind, dtype=np.int32)
+    nb = len(kind)
+    rigid = None if rigid is None else np.ascontiguousarray(rigid, dtype=np.int32)
+    U = None if U is None else np.ascontiguousarray(U, dtype=np.float64).reshape(nb * 3)
+    Om = None if Omega is None else np.ascontiguousarray(Omega, dtype=np.float64).reshape(nb * 3)
+    d = ProblemDesc()
+    d.nbodies = nb
+    d.n_off = _np_ptr(n_off, ctypes.c_int64)
+    d.q_off = _np_ptr(q_off, ctypes.c_int64)
+    d.kind = _np_ptr(kind, ctypes.c_int32)
+    d.rigid = None if rigid is None else _np_ptr(rigid, ctypes.c_int32)
+    d.U = None if U is None else _np_ptr(U, ctypes.c_double)
+    d.Omega = None if Om is None else _np_ptr(Om, ctypes.c_double)
+    d.eps, d.mu = float(eps), float(mu)
+    d.nn_global = int(bool(nn_global))
+    d.factor_prec = PREC[factor_prec]
+    d.nb = 0
+    d.tol = float(tol)
+    d.max_outer, d.max_inner = int(max_outer), int(max_inner)
+    d.reuse_factor, d.warm_start = int(bool(reuse_factor)), int(bool(warm_start))
+    d.reuse_max_inner, d.reuse_max_stages = int(reuse_max_inner), int(reuse_max_stages)
+    d.solve_mode = {"device": 0, "host": 1}[solve_mode]
+    d.graph = int(bool(graph))
+    return d, (n_off, q_off, kind, rigid, U, Om)
+
+
+class Batch:
+    """Many independent problems stepped together through one CUDA graph
+    (nrs_batch_* in include/nrs.h)."""
+
+    def __init__(self, problems, factor_prec: str = "tf32", stream=None, **kw):
+        descs = (ProblemDesc * len(problems))()
+        self._keep = []
+        for i, pr in enumerate(problems):
+            d, keep = _make_desc(*_problem_args(pr), factor_prec=factor_prec, **kw)
+            descs[i] = d
+            self._keep.append(keep)
+        self.stream = stream or torch.cuda.current_stream()
+        self._h = ctypes.c_void_p()
+        st = _lib.nrs_batch_create(ctypes.byref(self._h), descs, len(problems),
+                                   ctypes.c_void_p(self.stream.cuda_stream))
+        if st != NRS_OK:
+            raise NrsError(st, "nrs_batch_create failed")
+        self.count = len(problems)
+        self.contexts = []
+        for i, pr in enumerate(problems):
+            h = ctypes.c_void_p()
+            self._check(_lib.nrs_batch_context(self._h, i, ctypes.byref(h)))
+            self.contexts.append(Context(*_problem_args(pr), factor_prec=factor_prec,
+                                         stream=self.stream, _handle=h, **kw))
+
+    def _check(self, st):
+        if st != NRS_OK:
+            raise NrsError(st, (_lib.nrs_batch_last_error(self._h) or b"").decode())
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            for c in self.contexts:
+                c._h = ctypes.c_void_p()
+            _lib.nrs_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _shapes(pairs):
+        s0 = (Shapes * len(pairs))()
+        sh = (Shapes * len(pairs))()
+        for i, (a, b) in enumerate(pairs):
+            s0[i] = Context.shapes(*a)
+            sh[i] = Context.shapes(*b)
+        return s0, sh
+
+    def step(self, pairs, dt: float, sols=None, report: bool = False, check: bool = True):
+        """pairs[i] = ((xi, Xiw, xidot) at t, (xi, Xiw, xidot) at t + dt/2) device tensors."""
+        s0, sh = self._shapes(pairs)
+        sp = None
+        if sols is not None:
+            sp = (_P * self.count)(*[None if x is None else _ptr(x, torch.float64).value
+                                     for x in sols])
+        reps = (StepReport * self.count)() if report else None
+        st = _lib.nrs_batch_step(self._h, s0, sh, float(dt), sp, reps)
+        if check:
+            self._check(st)
+        if not report:
+            return None
+        return [{"stages": [r.stage[0].as_dict(), r.stage[1].as_dict()], "ms": r.ms_total,
+                 "factorizations": r.factorizations} for r in reps]
+
+    def config(self, chains: int, grid: int):
+        ch = (ctypes.c_int32 * self.count)()
+        self._check(_lib.nrs_batch_config(self._h, int(chains), int(grid), ch))
+        return list(ch)
+
+    def tune(self, pairs, dt: float, cache_path: Optional[str] = None):
+        s0, sh = self._shapes(pairs)
+        k, g, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        self._check(_lib.nrs_batch_tune(self._h, s0, sh, float(dt),
+                                        None if cache_path is None else cache_path.encode(),
+                                        ctypes.byref(k), ctypes.byref(g), ctypes.byref(ms)))
+        return {"chains": k.value, "grid": g.value, "ms": ms.value}
+
+    def info(self):
+        k, g, nk = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        self._check(_lib.nrs_batch_info(self._h, ctypes.byref(k), ctypes.byref(g), ctypes.byref(nk)))
+        return {"chains": k.value, "grid": g.value, "graph_kernels": nk.value}
+
+
+def batch_plan(cost, chains: int):
+    """nrs_batch_plan: (chain of each problem, order) of the LPT plan (host only)."""
+    c = np.ascontiguousarray(cost, dtype=np.float64)
+    ch = np.zeros(len(c), np.int32)
+    order = np.zeros(len(c), np.int32)
+    st = _lib.nrs_batch_plan(_np_ptr(c, ctypes.c_double), len(c), int(chains),
+                             _np_ptr(ch, ctypes.c_int32), _np_ptr(order, ctypes.c_int32))
+    if st != NRS_OK:
+        raise NrsError(st, "nrs_batch_plan failed")
+    return ch, order
 
 
 def nearest_build_static(x: torch.Tensor, Xw: torch.Tensor, n_off, q_off, global_: bool = False,

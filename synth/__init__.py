@@ -22,6 +22,10 @@ from .geometry import (  # noqa: F401
     swimmer_config,
     swimmers_config,
     sperm_channel_config,
+    node_config,
+    node_batch,
+    vogel_disc,
+    rod_line,
     workload,
     pack_shapes,
     initial_state,

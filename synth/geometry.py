@@ -19,6 +19,10 @@ with synthetic bodies standing in for the cited beat patterns):
 * ``swimmers4``     four such tubes at 2000/20000 points each: 24024 unknowns.
 * ``sperm_channel`` eight sperm-like swimmers (ellipsoid head + beating
                     flagellum) in a closed static box: 27648 unknowns.
+* ``node``          one problem of the batch workload: 10-60 tilted cilia
+                    rotating on cones over a static floor disc, plus five free
+                    spheres (n = 120 c + 3 N_f + 1500, 5100-16200 unknowns);
+                    ``node_batch(128)`` is the batch.
 """
 
 from __future__ import annotations
@@ -431,12 +435,106 @@ def sperm_channel_config(count: int = 8, n_head: int = 150, q_head: int = 1500,
     return Problem("sperm_channel", bodies, eps, 1.0, dt=0.01, steps=200)
 
 
+def vogel_disc(npts: int, R: float):
+    """Vogel spiral on the disc of radius R in the plane z = 0: point k at
+    radius R sqrt((k + 1/2) / npts), angle k times the golden angle
+    pi (3 - sqrt 5); equal weights pi R^2 / npts."""
+    k = np.arange(npts, dtype=np.float64)
+    r = R * np.sqrt((k + 0.5) / npts)
+    th = k * (math.pi * (3.0 - math.sqrt(5.0)))
+    P = np.stack([r * np.cos(th), r * np.sin(th), np.zeros(npts)], axis=1)
+    return P, np.full(npts, math.pi * R * R / npts)
+
+
+def rod_line(npts: int, length: float):
+    """Midpoints of npts equal segments of the body x-axis from 0 to length,
+    with the segment length as weight."""
+    s = (np.arange(npts, dtype=np.float64) + 0.5) * (length / npts)
+    P = np.stack([s, np.zeros(npts), np.zeros(npts)], axis=1)
+    return P, np.full(npts, length / npts)
+
+
+def node_config(index: int = 0, cilia=(10, 60), floor=(800, 2500), n_rod: int = 40,
+                q_rod: int = 400, rod_len: float = 0.5, n_sphere: int = 4, q_sphere: int = 16,
+                n_spheres: int = 5, eps: float = 0.005) -> Problem:
+    """One ventral-node-like problem of the batch workload, seeded by (4, index).
+    Draws, in order: the cilium count c in [cilia], the floor count N_f in
+    [floor]; c cilium bases uniform in the disc r <= 1.6 (redrawn while closer
+    than 0.4 to an earlier base; after 1000 redraws in a row the spacing
+    shrinks by 10 %, since random packing cannot place more than about 35
+    bases 0.4 apart in that disc); per cilium a tilt theta in [30, 45] degrees
+    and a starting phase in [0, 2 pi); per sphere a centre (x, y) uniform in
+    r <= 1.6 and a height in [0.7, 0.9].
+
+    * floor: static disc of radius 2, Vogel spirals with N_f force points and
+      10 N_f quadrature points;
+    * cilia: rigid rods of length rod_len (n_rod / q_rod points on a line),
+      prescribed rotation about the base at 2 pi clockwise seen from above,
+      on a cone of semi-angle 30 degrees whose axis is tilted by theta
+      towards -y; the body x-axis is the rod;
+    * spheres: free rigid spheres of radius 0.05 (cube-sphere vertex clouds).
+    n = 3 (n_rod c + N_f + n_spheres N_sphere) + 6 n_spheres."""
+    rng = SplitMix64((4 << 32) | (index & 0xFFFFFFFF))
+    c = int(cilia[0] + min(cilia[1] - cilia[0], int(rng.uniform() * (cilia[1] - cilia[0] + 1))))
+    nf = int(floor[0] + min(floor[1] - floor[0], int(rng.uniform() * (floor[1] - floor[0] + 1))))
+    bases: List[np.ndarray] = []
+    sep, misses = 0.4, 0
+    while len(bases) < c:
+        r = 1.6 * math.sqrt(rng.uniform())
+        th = rng.uniform(0.0, 2.0 * math.pi)
+        p = np.array([r * math.cos(th), r * math.sin(th), 0.0])
+        if all(np.linalg.norm(p - o) >= sep for o in bases):
+            bases.append(p)
+            misses = 0
+        else:
+            misses += 1
+            if misses == 1000:  # random packing at this spacing is full: shrink it
+                sep *= 0.9
+                misses = 0
+    tilts = []
+    for _ in range(c):
+        tilts.append((math.radians(rng.uniform(30.0, 45.0)), rng.uniform(0.0, 2.0 * math.pi)))
+    fx, fw = vogel_disc(nf, 2.0)
+    fX, fwq = vogel_disc(10 * nf, 2.0)
+    bodies = [Body(STATIC, nf, 10 * nf, _rigid(fx, fX, fwq), True, np.zeros(3), np.eye(3),
+                   name="floor")]
+    rx, _ = rod_line(n_rod, rod_len)
+    rX, rw = rod_line(q_rod, rod_len)
+    cone = math.radians(30.0)
+    for i, (theta, phi) in enumerate(tilts):
+        a = np.array([0.0, -math.sin(theta), math.cos(theta)])
+        e1 = np.array([1.0, 0.0, 0.0])
+        e2 = np.cross(a, e1)
+        d = math.cos(cone) * a + math.sin(cone) * (math.cos(phi) * e1 + math.sin(phi) * e2)
+        b2 = np.cross(a, d)
+        b2 /= np.linalg.norm(b2)
+        B = np.stack([d, b2, np.cross(d, b2)], axis=1)
+        bodies.append(Body(PRESCRIBED, n_rod, q_rod, _rigid(rx, rX, rw), True, bases[i].copy(), B,
+                           np.zeros(3), -2.0 * math.pi * a, name=f"cilium{i}"))
+    sx, _ = cube_sphere_vertices(n_sphere, 0.05)
+    sX, sw = cube_sphere_vertices(q_sphere, 0.05)
+    for k in range(n_spheres):
+        r = 1.6 * math.sqrt(rng.uniform())
+        th = rng.uniform(0.0, 2.0 * math.pi)
+        z = rng.uniform(0.7, 0.9)
+        bodies.append(Body(FREE, len(sx), len(sX), _rigid(sx, sX, sw), True,
+                           np.array([r * math.cos(th), r * math.sin(th), z]), np.eye(3),
+                           name=f"sphere{k}"))
+    return Problem(f"node{index}", bodies, eps, 1.0, dt=0.01, steps=20)
+
+
+def node_batch(count: int = 128, **kw) -> List[Problem]:
+    """The batch workload: node_config(i) for i < count."""
+    return [node_config(i, **kw) for i in range(count)]
+
+
 WORKLOADS: Dict[str, Callable[..., Problem]] = {
     "sphere": sphere_config,
     "sphere_cells": sphere_cells_config,
     "swimmer": swimmer_config,
     "swimmers4": swimmers_config,
     "sperm_channel": sperm_channel_config,
+    "node": node_config,
 }
 
 
