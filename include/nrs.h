@@ -97,6 +97,10 @@ typedef struct {
                               the whole refinement of one right-hand side is one cooperative
                               launch (no host round trip inside a solve); 1: host-driven loop
                               (one synchronisation per GMRES iteration), the FP64 path's mode */
+    double inner_tol;      /* GMRES tolerance of each refinement step, relative to the
+                              preconditioned residual (0 = 1e-4).  Very ill-conditioned
+                              systems need a tighter one: the preconditioned residual then
+                              says little about the true residual. */
     int32_t graph;         /* 1: nrs_step records the whole step into a CUDA graph and replays it
                               (from the second call on: the first call builds the nearest-
                               neighbour maps of the rigid bodies).  The recording is keyed by

@@ -444,6 +444,11 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
     c->reuse_max_stages = d->reuse_max_stages > 0 ? d->reuse_max_stages : 16;
     c->warm_start = d->warm_start ? 1 : 0;
     c->solve_mode = d->solve_mode ? 1 : 0;
+    if (d->inner_tol < 0.0 || !(d->inner_tol < 1.0)) {
+        delete c;
+        return NRS_EINVAL;
+    }
+    c->tol_in = d->inner_tol > 0.0 ? d->inner_tol : 1e-4;
     c->graph_mode = d->graph ? 1 : 0;
     if (c->graph_mode && (d->factor_prec == NRS_FP64 || c->solve_mode != 0 || d->reuse_factor ||
                           (d->max_inner > 64))) {

@@ -21,126 +21,146 @@ namespace nrs {
 
 constexpr int GJ_NB = 64;
 
-// D^{-1} by Gauss-Jordan on [D | I] with partial pivoting (one CTA of 256
-// threads, two barriers per column).
-//  * Thread (r, s) = (tid / 4, tid % 4) keeps row r of the augmented matrix,
-//    columns s + 4 i, in registers: the left half in L[16], the right half in
-//    Rr[16].  After each group of four columns the finished left columns are
-//    shifted out (L[i] <- L[i+1]) so that every register index is static.
-//  * Column c is published in colbuf[c & 1] by its owners during step c-1;
-//    every warp then finds the pivot on its own with warp reductions: the
-//    unused row of largest |value|, lowest row on ties.  Only the pivot row is
-//    copied to shared memory for the others.
-//  * Rows are never moved or scaled during the sweep: step c subtracts
-//    (W[r][c] / W[p][c]) W[p] from every row r != p.  At the end the left half
-//    of pivot row p_c is pv_c e_c, so logical row c of D^{-1} is the right
-//    half of physical row p_c divided by pv_c.
+// D^{-1} of the 64 x 64 diagonal block by Gauss-Jordan elimination with
+// partial pivoting, written for the latency of one pivot step (this kernel is
+// the critical path of the factorisation: one launch per block column).
+//
+// All 256 threads first stage the block (and, with Cb and Rt given, bring it
+// up to date for the lookahead: D = M[K,K] - C[K,:] R[:,K], the part of the
+// previous rank-64 update that the main stream skips).  Then two warps do the
+// elimination, lane l of warp w holding row r = 32 w + l in registers T[64]:
+//  * exchange (sweep) form, in place: at the step for column c with pivot row
+//    p, every other row i gets T_i[j] -= (T_i[c] / T_p[c]) T_p[j] (j != c) and
+//    T_i[c] = -T_i[c] / T_p[c]; the pivot row is divided by T_p[c] and gets
+//    T_p[c] = 1 / T_p[c].  After the 64 steps row p_c holds row c of D^{-1}
+//    with column d standing for original row p_d.
+//  * the pivot row's division is deferred: it keeps its values, sets
+//    T_p[c] = 1 and records s_p = 1 / T_p[c]; later updates of that row are
+//    the same formula on the unscaled values, and s_p is applied at the end;
+//  * the registers rotate by one column per step, so the current column is
+//    always T[0] (static register indices) and after 64 steps every column
+//    is back in place;
+//  * pivot: the unused row of largest |T[c]|, lowest row on ties (warp
+//    reductions, then the two warps' candidates); each warp's candidate
+//    writes its row to a double-buffered shared slot before the one 64-thread
+//    barrier of the step, and every lane reads the winner's row from there.
 // Padding rows/columns (kb < 64) are identity.  Dinv is row-major 64 x 64; a
 // zero pivot records info.
-//
-// With Cb and Rt given (the lookahead), the block is first brought up to date,
-// D = M[K,K] - C[K,:] R[:,K]: the part of the previous step's rank-64 update
-// that the main stream skips.  (Nothing reads M[K,K] afterwards: it is
-// overwritten with D^{-1} at the end of the step.)
 __global__ void __launch_bounds__(256)
     k_gj_diag(int64_t n, const float *__restrict__ M, int64_t lda, int64_t k0,
               float *__restrict__ Dinv, int32_t *__restrict__ info,
               const float *__restrict__ Cb, const float *__restrict__ Rt)
 {
     constexpr int NB = GJ_NB;
-    __shared__ float colbuf[2][NB];
-    __shared__ float prow[2 * NB];
-    __shared__ int pos[NB];
-    __shared__ float pivval[NB];
-    __shared__ float Cs[NB][NB + 1];
-    __shared__ float Rs[NB][NB + 1];
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int r = tid >> 2, s = tid & 3;
+    __shared__ float sm[2][NB][NB + 1];  // Cs, Rs; then the updated block in sm[0]
+    __shared__ __align__(16) float cand[2][2][NB];  // [step parity][warp][column]
+    __shared__ unsigned ckey[2][2];
+    __shared__ float cpiv[2][2];
+    __shared__ int crow[2][2];
+    __shared__ int pivrow[NB];
+    const int tid = threadIdx.x;
     const int kb = (int)min((int64_t)NB, n - k0);
-    float L[16], Rr[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const int j = s + 4 * i;
-        L[i] = (r < kb && j < kb) ? M[(k0 + r) + (k0 + j) * lda] : (r == j ? 1.0f : 0.0f);
-        Rr[i] = (r == j) ? 1.0f : 0.0f;
-    }
-    if (Cb) {
-        float cv[16], rv[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
-            cv[q] = b < kb ? Cb[(k0 + b) * NB + a] : 0.0f;
-            rv[q] = b < kb ? Rt[(k0 + b) * NB + a] : 0.0f;
-        }
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
-            Cs[b][a] = cv[q];
-            Rs[b][a] = rv[q];
-        }
-        __syncthreads();
-        // L[i] (row r, column j = s + 4 i) -= sum_t C[r][t] R[j][t]
+    {
+        const int r = tid >> 2, s = tid & 3;
+        float L[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             const int j = s + 4 * i;
-            float acc = 0.0f;
+            L[i] = (r < kb && j < kb) ? M[(k0 + r) + (k0 + j) * lda] : (r == j ? 1.0f : 0.0f);
+        }
+        if (Cb) {
+            float cv[16], rv[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
+                cv[q] = b < kb ? Cb[(k0 + b) * NB + a] : 0.0f;
+                rv[q] = b < kb ? Rt[(k0 + b) * NB + a] : 0.0f;
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
+                sm[0][b][a] = cv[q];
+                sm[1][b][a] = rv[q];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int j = s + 4 * i;
+                float acc = 0.0f;
 #pragma unroll 16
-            for (int t = 0; t < NB; ++t) acc += Cs[r][t] * Rs[j][t];
-            if (r < kb && j < kb) L[i] -= acc;
+                for (int t = 0; t < NB; ++t) acc = fmaf(sm[0][r][t], sm[1][j][t], acc);
+                if (r < kb && j < kb) L[i] -= acc;
+            }
+            __syncthreads();  // everyone is done with Cs, Rs
         }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sm[0][r][s + 4 * i] = L[i];
     }
-    if (s == 0) colbuf[0][r] = L[0];
-    unsigned long long used = 0ull;
     __syncthreads();
-    for (int cc = 0; cc < NB / 4; ++cc) {
+    if (tid >= 64) return;
+    const int w = tid >> 5, r = tid;
+    float T[NB];
 #pragma unroll
-        for (int sp = 0; sp < 4; ++sp) {
-            const int c = 4 * cc + sp;
-            const int buf = sp & 1;
-            const float a0 = fabsf(colbuf[buf][lane]), a1 = fabsf(colbuf[buf][lane + 32]);
-            const bool u0 = (used >> lane) & 1ull, u1 = (used >> (lane + 32)) & 1ull;
-            const unsigned k0v = u0 ? 0u : (0x80000000u | __float_as_uint(a0));
-            const unsigned k1v = u1 ? 0u : (0x80000000u | __float_as_uint(a1));
-            const unsigned key = k0v >= k1v ? k0v : k1v;
-            const int row = k0v >= k1v ? lane : lane + 32;
-            const unsigned mx = __reduce_max_sync(0xffffffffu, key);
-            const int p = (int)__reduce_min_sync(0xffffffffu, key == mx ? (unsigned)row : 64u);
-            used |= 1ull << p;
-            const float pv = colbuf[buf][p];
-            if (tid == 0) {
-                pos[p] = c;
-                pivval[c] = pv;
-                if (pv == 0.0f && info) atomicCAS(info, 0, (int)(k0 + c + 1));
-            }
-            if (r == p) {
+    for (int j = 0; j < NB; ++j) T[j] = sm[0][r][j];
+    bool used = false;
+    float scale = 1.0f;
+    int mypos = 0;
+#pragma unroll 4
+    for (int c = 0; c < NB; ++c) {
+        const int b = c & 1;
+        const float colv = T[0];
+        const unsigned key = used ? 0u : (0x80000000u | __float_as_uint(fabsf(colv)));
+        const unsigned mx = __reduce_max_sync(0xffffffffu, key);
+        const int best = (int)__reduce_min_sync(0xffffffffu, key == mx ? (unsigned)r : 255u);
+        if (r == best) {
+            float4 *dst = reinterpret_cast<float4 *>(&cand[b][w][0]);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    prow[s + 4 * i] = L[i];
-                    prow[NB + s + 4 * i] = Rr[i];
-                }
-            }
-            __syncthreads();
-            if (r != p) {
-                const float g = colbuf[buf][r] / pv;
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    L[i] -= g * prow[s + 4 * i];
-                    Rr[i] -= g * prow[NB + s + 4 * i];
-                }
-            }
-            // publish column c + 1 for the next step
-            if (s == ((sp + 1) & 3)) colbuf[buf ^ 1][r] = (sp < 3) ? L[0] : L[1];
-            __syncthreads();
+            for (int q = 0; q < NB / 4; ++q)
+                dst[q] = make_float4(T[4 * q], T[4 * q + 1], T[4 * q + 2], T[4 * q + 3]);
+            ckey[b][w] = mx;
+            cpiv[b][w] = colv;
+            crow[b][w] = best;
         }
-        // columns 4 cc .. 4 cc + 3 are finished: shift them out of L
+        asm volatile("bar.sync 1, 64;" ::: "memory");
+        const unsigned kw0 = ckey[b][0], kw1 = ckey[b][1];
+        const float pv0 = cpiv[b][0], pv1 = cpiv[b][1];
+        const int rw0 = crow[b][0], rw1 = crow[b][1];
+        const int win = kw0 >= kw1 ? 0 : 1;  // warp 0 (the lower rows) on ties
+        const float piv = win ? pv1 : pv0;
+        const int p = win ? rw1 : rw0;
+        const float rpiv = 1.0f / piv;
+        const bool is_piv = (r == p);
+        if (is_piv) {
+            used = true;
+            scale = rpiv;
+            mypos = c;
+        }
+        if (tid == 0) {
+            pivrow[c] = p;
+            if (piv == 0.0f && info) atomicCAS(info, 0, (int)(k0 + c + 1));
+        }
+        const float f = is_piv ? 0.0f : colv * rpiv;
+        const float newc = is_piv ? 1.0f : -f;
+        const float4 *pr4 = reinterpret_cast<const float4 *>(&cand[b][win][0]);
 #pragma unroll
-        for (int i = 0; i < 15; ++i) L[i] = L[i + 1];
-        L[15] = 0.0f;
+        for (int q = 0; q < NB / 4; ++q) {
+            const float4 v = pr4[q];
+            if (q > 0) T[4 * q] = fmaf(-f, v.x, T[4 * q]);
+            T[4 * q + 1] = fmaf(-f, v.y, T[4 * q + 1]);
+            T[4 * q + 2] = fmaf(-f, v.z, T[4 * q + 2]);
+            T[4 * q + 3] = fmaf(-f, v.w, T[4 * q + 3]);
+        }
+#pragma unroll
+        for (int j = 0; j < NB - 1; ++j) T[j] = T[j + 1];
+        T[NB - 1] = newc;
     }
-    const int lr = pos[r];
-    const float d = 1.0f / pivval[lr];
+    asm volatile("bar.sync 1, 64;" ::: "memory");  // pivrow complete
+    // row mypos of D^{-1}, column pivrow[d] = T[d] * scale: through shared
+    // memory (sm[1] is free) so that the global stores are coalesced
 #pragma unroll
-    for (int i = 0; i < 16; ++i) Dinv[lr * NB + s + 4 * i] = Rr[i] * d;
+    for (int d = 0; d < NB; ++d) sm[1][mypos][pivrow[d]] = T[d] * scale;
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+    for (int i = 0; i < NB; ++i) Dinv[i * NB + tid] = sm[1][i][tid];
 }
 
 // Prep of step K.  grid.y = 0: R[:, j] = D^{-1} M[K, j] for one 64-column tile

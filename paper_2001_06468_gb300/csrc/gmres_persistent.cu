@@ -19,6 +19,11 @@
 // the same values, so all CTAs take the same branches without a broadcast.
 // Every reduction has a fixed order: the result is deterministic.
 //
+// Stopping rule: that of k_outer_check (solve.cu), plus one for very
+// ill-conditioned systems, where an FP64 residual leaves corrections of about
+// kappa(A) u that never shrink: once the corrections stagnate, the iteration
+// also stops when the normwise backward error of x is at most 1e-15.
+//
 // Grid barriers are bounded: a CTA that waits more than kSpinLimit polls sets
 // ST_TIMEOUT and returns, and every CTA returns at its next barrier once the
 // flag is set.  The launch is cooperative, so all CTAs are co-resident.
@@ -106,10 +111,11 @@ __device__ bool grid_sync(const PgArgs &a, int *s_ok)
     return *s_ok != 0;
 }
 
-// part[s][i] = scale * sum_{j in split s} A[i, j] v[j].  A tile is 64 rows x
+// part[s][i] = scale * sum_{j in split s} A[i, j] v[j] (|A[i, j]| when ABS).  A tile is 64 rows x
 // one column split; lane l of warp g takes rows 2l, 2l+1 (one 16-byte load per
 // column, 512 contiguous bytes per warp) and columns j0+g, j0+g+8, ...; the 8
 // column groups are summed in shared memory in a fixed order.
+template <bool ABS>
 __device__ void mv64_partial(const PgArgs &a, const double *v, double scale, double *sm)
 {
     const int64_t tiles = (int64_t)a.rc64 * a.s64;
@@ -124,9 +130,14 @@ __device__ void mv64_partial(const PgArgs &a, const double *v, double scale, dou
 #pragma unroll 4
             for (int64_t j = j0 + grp; j < j1; j += MV_GROUPS) {
                 const double2 x = __ldg(reinterpret_cast<const double2 *>(col + j * a.lda));
-                const double vj = __ldcg(v + j);
-                s0 = fma(x.x, vj, s0);
-                s1 = fma(x.y, vj, s1);
+                if (ABS) {  // row sums of |A|
+                    s0 += fabs(x.x);
+                    s1 += fabs(x.y);
+                } else {
+                    const double vj = __ldcg(v + j);
+                    s0 = fma(x.x, vj, s0);
+                    s1 = fma(x.y, vj, s1);
+                }
             }
         }
         sm[grp * MV64_ROWS + 2 * lane] = s0;
@@ -174,9 +185,9 @@ __device__ void mv32_partial(const PgArgs &a, const double *v, float *sm)
         __syncthreads();
         if (threadIdx.x < MV32_ROWS) {
             const int64_t r = rc * MV32_ROWS + threadIdx.x;
-            float acc = 0.0f;
+            double acc = 0.0;
 #pragma unroll
-            for (int g = 0; g < MV_GROUPS; ++g) acc += sm[g * MV32_ROWS + threadIdx.x];
+            for (int g = 0; g < MV_GROUPS; ++g) acc += (double)sm[g * MV32_ROWS + threadIdx.x];
             if (r < a.n) a.part[s * a.n + r] = acc;
         }
         __syncthreads();
@@ -287,6 +298,7 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
     const int64_t e1 = owner ? min(n, e0 + a.ed) : n;
     const int nslot = m + 1;  // slot of norms in region 2 / maxima in region 0
     double *dp0 = a.dpart + (0 * PG_MAXCH + (int64_t)blockIdx.x) * (m + 2);
+    double *dp1 = a.dpart + (1 * PG_MAXCH + (int64_t)blockIdx.x) * (m + 2);
     double *dp2 = a.dpart + (2 * PG_MAXCH + (int64_t)blockIdx.x) * (m + 2);
 
     if (a.cold) {  // x = M b
@@ -296,14 +308,52 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
         if (!grid_sync(a, &s_ok)) return;
     }
     int outer = 0, inner_total = 0, converged = 0;
-    double dn = 0.0, xn = 0.0, dn_prev = 0.0;
+    double dn = 0.0, xn = 0.0, dn_prev = 0.0, normA = -1.0;
+    bool stagnant = false;
     for (outer = 0; outer < a.max_outer; ++outer) {
-        // r = b - A x (FP64)
-        mv64_partial(a, a.x, 1.0, smv);
+        // r = b - A x (FP64), with ||r||_inf and ||b||_inf per chunk
+        mv64_partial<false>(a, a.x, 1.0, smv);
         if (!grid_sync(a, &s_ok)) return;
-        for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS)
-            a.w[e] = __ldg(a.b + e) - sum_parts(a, a.s64, e);
+        {
+            double rmax = 0.0, bmax = 0.0;
+            for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
+                const double be = __ldg(a.b + e), re = be - sum_parts(a, a.s64, e);
+                a.w[e] = re;
+                rmax = fmax(rmax, fabs(re));
+                bmax = fmax(bmax, fabs(be));
+                if (!isfinite(re)) rmax = INFINITY;
+            }
+            rmax = block_max_all(rmax, sred);
+            bmax = block_max_all(bmax, sred);
+            if (owner && threadIdx.x == 0) {
+                dp1[0] = rmax;
+                dp1[1] = bmax;
+            }
+        }
         if (!grid_sync(a, &s_ok)) return;
+        if (stagnant) {
+            // The corrections stopped shrinking.  If x already solves a nearby
+            // system to working precision (normwise backward error
+            // ||r|| / (||A|| ||x|| + ||b||) <= 1e-15), further steps only
+            // chase rounding noise: stop.  ||A||_inf is computed once, here.
+            if (normA < 0.0) {
+                mv64_partial<true>(a, nullptr, 1.0, smv);
+                if (!grid_sync(a, &s_ok)) return;
+                double amax = 0.0;
+                for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS)
+                    amax = fmax(amax, sum_parts(a, a.s64, e));
+                amax = block_max_all(amax, sred);
+                if (owner && threadIdx.x == 0) dp1[2] = amax;
+                if (!grid_sync(a, &s_ok)) return;
+                normA = chunk_total(a, 1, 2, true, sred);
+            }
+            const double rn = chunk_total(a, 1, 0, true, sred);
+            const double bn = chunk_total(a, 1, 1, true, sred);
+            if (rn <= 1e-15 * (normA * xn + bn)) {
+                converged = 1;
+                break;
+            }
+        }
         // V_0 = M r (raw), beta = ||V_0||
         mv32_partial(a, a.w, smv32);
         if (!grid_sync(a, &s_ok)) return;
@@ -332,7 +382,7 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
             double *Vj = a.V + (int64_t)j * a.ldv;
             double *u = a.V + (int64_t)(j + 1) * a.ldv;
             // w = A v_j
-            mv64_partial(a, Vj, sv, smv);
+            mv64_partial<false>(a, Vj, sv, smv);
             if (!grid_sync(a, &s_ok)) return;
             for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
                 Vj[e] = __ldcg(Vj + e) * sv;  // v_j normalised in place (own chunk)
@@ -450,6 +500,7 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
         } else if (dn_prev > 0.0 && dn >= 0.5 * dn_prev && dn <= a.floor * xn) {
             done = true;
         }
+        stagnant = dn_prev > 0.0 && dn >= 0.5 * dn_prev;
         dn_prev = dn;
         if (done) {
             converged = 1;
@@ -511,14 +562,16 @@ cudaError_t launch_gmres_persistent(Ctx &c, const double *b, double *x, bool col
     a.out = stats;
     a.tol = c.tol;
     a.floor = 1e-11;
-    a.tol_in = 1e-4;
+    a.tol_in = c.tol_in;
     a.m = c.max_inner;
     a.max_outer = c.max_outer;
     a.cold = cold ? 1 : 0;
     a.rc64 = (int)ceil_div(c.n, MV64_ROWS);
     a.rc32 = (int)ceil_div(c.n, MV32_ROWS);
     a.s64 = (int)std::max<int64_t>(1, std::min<int64_t>(64, ceil_div(G, a.rc64)));
-    a.s32 = (int)std::max<int64_t>(1, std::min<int64_t>(64, ceil_div(G, a.rc32)));
+    // at least 8 column splits for the FP32 product: each FP32 partial sum then
+    // covers at most n / 64 columns, and the splits are added in FP64
+    a.s32 = (int)std::max<int64_t>(8, std::min<int64_t>(64, ceil_div(G, a.rc32)));
     a.s64 = (int)std::min<int64_t>(a.s64, c.n);
     a.s32 = (int)std::min<int64_t>(a.s32, c.n);
     a.cps64 = ceil_div(c.n, a.s64);

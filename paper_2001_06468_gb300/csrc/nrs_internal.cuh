@@ -133,6 +133,7 @@ struct Ctx {
     double eps = 0, mu = 0;
     int nn_global = 0, factor_prec = NRS_FP32, nb = 64;
     double tol = 1e-12;
+    double tol_in = 1e-4;      // GMRES tolerance of each refinement step (preconditioned residual)
     int max_outer = 20, max_inner = 30;
 
     // device body tables

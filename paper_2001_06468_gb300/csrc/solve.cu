@@ -36,6 +36,7 @@ enum {
     SC_AN = 7,
     SC_RES = 8,
     SC_DNPREV = 10,
+    SC_STAG = 11,  // the last correction did not halve
     SC_COUNT = 16
 };
 
@@ -390,7 +391,8 @@ __global__ void k_update(int64_t n, const double *__restrict__ V, int64_t ldv,
     x[e] += s;
 }
 
-// SC_DN = ||d||_inf, SC_XN = ||x||_inf.  SC_OUTER_DONE when SC_DN <= tol SC_XN,
+// SC_DN = ||d||_inf, SC_XN = ||x||_inf, SC_STAG = the correction did not
+// halve.  SC_OUTER_DONE when SC_DN <= tol SC_XN,
 // when the next correction predicted from the observed rate is far below that,
 // or when refinement has stagnated at the accuracy an FP64 residual can
 // deliver: the update no longer halves (SC_DN >= SC_DNPREV / 2) and is already
@@ -422,6 +424,7 @@ __global__ void __launch_bounds__(RED_THREADS)
         } else if (scal[SC_DNPREV] > 0.0 && dn >= 0.5 * scal[SC_DNPREV] && dn <= floor * xn) {
             scal[SC_OUTER_DONE] = 1.0;
         }
+        scal[SC_STAG] = (scal[SC_DNPREV] > 0.0 && dn >= 0.5 * scal[SC_DNPREV]) ? 1.0 : 0.0;
         scal[SC_DNPREV] = dn;
     }
 }
@@ -572,7 +575,7 @@ nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0, nr
     const int m = c.max_inner;
     const int64_t ldv = c.lda;
     const int ldh = m + 1;
-    const double tol_in = 1e-4;
+    const double tol_in = c.tol_in;
     cudaError_t e = cudaSuccess;
 #define CKE(call)                                                           \
     do {                                                                    \
@@ -592,8 +595,38 @@ nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0, nr
     bool converged = false;
     double *h1 = c.d_scal + SC_COUNT;
     double *h2 = h1 + (m + 1);
+    bool have_an = false;
     for (outer = 0; outer < c.max_outer; ++outer) {
         gemv(c, x, b, c.d_r);  // r = b - A x
+        if (outer > 0) {
+            // stagnating corrections: stop once the normwise backward error of
+            // x is at most 1e-15 (as in gmres_persistent.cu)
+            const double stag = read_scalar(c, SC_STAG, &e);
+            if (e != cudaSuccess) CKE(e);
+            if (stag != 0.0) {
+                k_nrm_inf<<<1, RED_THREADS, 0, c.stream>>>(n, c.d_r, c.d_scal, SC_RN);
+                k_nrm_inf<<<1, RED_THREADS, 0, c.stream>>>(n, b, c.d_scal, SC_BN);
+                c.launches += 2;
+                if (!have_an) {
+                    const int64_t cps = ceil_div(c.n, c.splits64);
+                    dim3 grid((unsigned)ceil_div(c.n, 2 * MV_THREADS), (unsigned)c.splits64);
+                    k_gemv_part<true><<<grid, MV_THREADS, 0, c.stream>>>(c.n, c.d_A64, c.lda,
+                                                                         nullptr, c.d_part, cps);
+                    k_gemv_finish<<<(unsigned)ceil_div(c.n, 256), 256, 0, c.stream>>>(
+                        c.n, c.d_part, c.splits64, nullptr, c.d_w);
+                    k_nrm_inf<<<1, RED_THREADS, 0, c.stream>>>(n, c.d_w, c.d_scal, SC_AN);
+                    c.launches += 3;
+                    have_an = true;
+                }
+                double sc[SC_COUNT];
+                CKE(cudaMemcpyAsync(sc, c.d_scal, sizeof(sc), cudaMemcpyDeviceToHost, c.stream));
+                CKE(cudaStreamSynchronize(c.stream));
+                if (sc[SC_RN] <= 1e-15 * (sc[SC_AN] * sc[SC_XN] + sc[SC_BN])) {
+                    converged = true;
+                    break;
+                }
+            }
+        }
         double *V0 = c.d_V;
         CKE(apply_precond(c, c.d_r, V0));
         c.tbeg(PH_KRYLOV);

@@ -72,6 +72,7 @@ class ProblemDesc(ctypes.Structure):
                 ("reuse_max_stages", ctypes.c_int32),
                 ("warm_start", ctypes.c_int32),
                 ("solve_mode", ctypes.c_int32),
+                ("inner_tol", ctypes.c_double),
                 ("graph", ctypes.c_int32)]
 
 
@@ -182,11 +183,12 @@ class Context:
                  tol: float = 0.0, max_outer: int = 0, max_inner: int = 0,
                  reuse_factor: bool = False, reuse_max_inner: int = 0, reuse_max_stages: int = 0,
                  warm_start: bool = False, solve_mode: str = "device", graph: bool = False,
+                 inner_tol: float = 0.0,
                  stream: Optional[torch.cuda.Stream] = None, _handle=None):
         d, self._keep = _make_desc(n_off, q_off, kind, eps, mu, rigid, U, Omega, nn_global,
                                    factor_prec, tol, max_outer, max_inner, reuse_factor,
                                    reuse_max_inner, reuse_max_stages, warm_start, solve_mode,
-                                   graph)
+                                   graph, inner_tol)
         self.stream = stream or torch.cuda.current_stream()
         self._owner = _handle is None
         if _handle is None:
@@ -406,7 +408,7 @@ def _problem_args(problem):
 def _make_desc(n_off, q_off, kind, eps, mu=1.0, rigid=None, U=None, Omega=None, nn_global=False,
                factor_prec="fp32", tol=0.0, max_outer=0, max_inner=0, reuse_factor=False,
                reuse_max_inner=0, reuse_max_stages=0, warm_start=False, solve_mode="device",
-               graph=False):
+               graph=False, inner_tol=0.0):
     """An nrs_problem_desc and the host arrays it points to (keep them alive)."""
     n_off = np.ascontiguousarray(n_off, dtype=np.int64)
     q_off = np.ascontiguousarray(q_off, dtype=np.int64)
@@ -433,6 +435,7 @@ def _make_desc(n_off, q_off, kind, eps, mu=1.0, rigid=None, U=None, Omega=None, 
     d.reuse_max_inner, d.reuse_max_stages = int(reuse_max_inner), int(reuse_max_stages)
     d.solve_mode = {"device": 0, "host": 1}[solve_mode]
     d.graph = int(bool(graph))
+    d.inner_tol = float(inner_tol)
     return d, (n_off, q_off, kind, rigid, U, Om)
 
 

@@ -1,0 +1,111 @@
+"""The full-size configurations (four interacting swimmers, n = 24024; eight
+sperm-like swimmers in a closed channel, n = 27648) through the C ABI, with
+the launch configuration of the time step, checked against the FP64 oracle
+where it is affordable at these sizes:
+
+* nearest neighbours: the whole map, bit for bit (the oracle's exhaustive
+  search per body is cheap);
+* the assembled matrix: a seeded sample of 3 x 3 blocks against the
+  definition of eq. nnrsbie summed in numpy over the block's segment, within
+  1e-13 of the sum of the absolute values of its terms;
+* the solve: the GPU solution put into the oracle's own FP64 system (its
+  assembly, border and right-hand side), backward error
+  ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= 1e-14 with a
+  double-double residual; a solution of that quality has forward error at
+  most kappa(A) times it, the property that holds at any size.  (These
+  systems are ill-conditioned -- kappa_1 about 1e13 for the four swimmers --
+  so the forward error an FP64 residual can deliver is bounded by that, for
+  any solver; the oracle itself refines with a double-double residual.)
+"""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from synth import geometry as g
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "swimmers4": lambda: g.swimmers_config(),
+    "sperm_channel": lambda: g.sperm_channel_config(),
+}
+# The four-swimmer system is far more ill-conditioned (kappa_1 about 1e13,
+# against about 5e8 for one swimmer): its GMRES steps need a tighter
+# tolerance and a longer restart for the refinement to reach working accuracy.
+SOLVER = {
+    "swimmers4": dict(inner_tol=1e-8, max_inner=60, max_outer=30),
+    "sperm_channel": {},
+}
+
+
+@pytest.fixture(scope="module")
+def N():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2001_06468_gb300 import nrs
+    return nrs
+
+
+def _stokeslet_block(xm, Xs, w, eps):
+    """sum_q S^eps(xm - X_q) w_q for one segment (3 x 3) and the sum of the
+    absolute values of the terms, from the definition."""
+    r = xm[None, :] - Xs
+    r2 = np.sum(r * r, axis=1)
+    den = (r2 + eps * eps) ** 1.5
+    S = np.zeros((3, 3))
+    Sa = np.zeros((3, 3))
+    for j in range(3):
+        for k in range(3):
+            term = ((r2 + 2 * eps * eps) * (j == k) + r[:, j] * r[:, k]) / den * w
+            S[j, k] = term.sum()
+            Sa[j, k] = np.abs(term).sum()
+    return S, Sa
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_full_size_nearest_assembly_and_solve(N, name):
+    pr = CASES[name]()
+    t = 0.3
+    sh = g.pack_shapes(pr, t)
+    tab = g.body_table(pr)
+    Y = g.initial_state(pr)
+    ctx = N.Context.from_problem(pr, factor_prec="tf32", **SOLVER[name])
+    ctx.set_state(Y["x0"], Y["B"])
+    xi, Xiw, xidot = N.shapes_to_device(sh)
+    x, Xw, b = ctx.kinematics(xi, Xiw, xidot)
+    nn, seg_ptr, perm = ctx.nearest_build(xi, Xiw)
+    At = ctx.assemble(x, Xw)  # At[j, i] = A[i, j]
+    # nearest neighbours: all of them, bit for bit
+    nn_or = O.nearest(sh["x"], sh["Xw"], sh["n_off"], sh["q_off"], False)
+    assert np.array_equal(nn.cpu().numpy(), nn_or)
+    # sampled blocks of A_s against the definition
+    x_lab, Xw_lab = O.lab_frame(sh, Y)
+    assert np.array_equal(x.cpu().numpy(), x_lab)
+    seg_or, perm_or = O.segments(nn_or, pr.N)
+    coef = 1.0 / (8.0 * math.pi * pr.mu)
+    rng = np.random.Generator(np.random.PCG64(20))
+    ms = rng.integers(0, pr.N, size=300)
+    ns = rng.integers(0, pr.N, size=300)
+    # half of the sample on the diagonal and its neighbours, where the terms are largest
+    ns[:150] = np.clip(ms[:150] + rng.integers(-2, 3, size=150), 0, pr.N - 1)
+    for m, nseg in zip(ms, ns):
+        q = perm_or[seg_or[nseg]:seg_or[nseg + 1]]
+        S, Sa = _stokeslet_block(x_lab[m, :3], Xw_lab[q, :3], Xw_lab[q, 3], pr.eps)
+        blk = At[3 * nseg:3 * nseg + 3, 3 * m:3 * m + 3].T.cpu().numpy()  # A[3m+j, 3n+k]
+        assert np.all(np.abs(blk - coef * S) <= 1e-13 * coef * Sa + 1e-300), (m, nseg)
+    del At
+    # the solve, judged in the oracle's own FP64 system
+    assert ctx.factor("tf32") == 0
+    xg, rep = ctx.solve(b)
+    assert rep[0]["converged"], rep
+    A_or, b_or, *_ = O.system(pr, sh, tab, Y, nn=nn_or)
+    xs = xg.cpu().numpy()
+    r = O.residual_dd(A_or, xs, b_or)
+    berr = np.max(np.abs(r)) / (np.max(np.sum(np.abs(A_or), axis=1)) * np.max(np.abs(xs))
+                                + np.max(np.abs(b_or)))
+    assert berr <= 1e-14, berr
+    assert rep[0]["backward_err"] <= 1e-14, rep

@@ -141,6 +141,24 @@ def test_swimming_solve_matches_oracle(N, name, prec):
     assert _rel(Vg, V) <= TOL_SOL, (rep, _rel(Vg, V))
 
 
+@pytest.mark.parametrize("name,prec", [("swimmer", "fp32"), ("swimmer", "tf32"),
+                                       ("sperm2", "tf32"), ("sphere", "tf32")])
+def test_explicit_inverse_is_accurate(N, name, prec):
+    # The FP32 inverse preconditions GMRES: with M ~ A^{-1} to FP32 accuracy,
+    # M A = I + E with ||E|| ~ 1e-5, so each refinement step's GMRES meets its
+    # 1e-4 tolerance in one or two iterations.  A wrong inverse (a misplaced
+    # pivot, a transposed block) still converges -- GMRES is robust -- but
+    # needs many more iterations, which this catches.
+    pr = PROBLEMS[name]()
+    ctx, sh, Y, dev = _setup(N, pr, t=0.25, prec=prec)
+    _gpu_system(N, ctx, dev)
+    b = ctx.kinematics(*dev)[2]
+    assert ctx.factor(prec) == 0
+    _, rep = ctx.solve(b)
+    assert rep[0]["converged"] and rep[0]["outer"] <= 4, rep
+    assert rep[0]["inner"] <= 2 * rep[0]["outer"], rep
+
+
 def test_warm_start_and_multiple_rhs(N):
     pr = PROBLEMS["swimmer_small"]()
     ctx, sh, Y, dev = _setup(N, pr, t=0.1)
