@@ -101,6 +101,13 @@ typedef struct {
                               preconditioned residual (0 = 1e-4).  Very ill-conditioned
                               systems need a tighter one: the preconditioned residual then
                               says little about the true residual. */
+    int32_t factor_input;  /* the FP32 matrix the mixed-precision factorisation inverts:
+                              0 = evaluated in FP32 (differences x_m - X_q in FP64), so the
+                              factorisation starts at once while the FP64 assembly runs on a
+                              low-priority stream beside it; 1 = the FP64 entries rounded to
+                              FP32 (one FP64 pass first).  Very ill-conditioned systems (kappa
+                              near 1/u_fp32^2) need 1: the FP32 evaluation's extra error then
+                              spoils the preconditioner. */
     int32_t graph;         /* 1: nrs_step records the whole step into a CUDA graph and replays it
                               (from the second call on: the first call builds the nearest-
                               neighbour maps of the rigid bodies).  The recording is keyed by
@@ -435,7 +442,10 @@ enum {
     NRS_PH_UPDATE = 11,    /* explicit-midpoint state update                    */
     NRS_PH_LU_DIAG = 12,   /* next diagonal block: its update and inverse (timed on the
                               factorisation's second stream, overlapping the others) */
-    NRS_NPHASE = 13
+    NRS_PH_ASSEMBLE32 = 13, /* the FP32 copy of A_s for the factorisation (mixed path); the
+                              FP64 assembly then runs on a third stream, overlapping the
+                              factorisation (timed there) */
+    NRS_NPHASE = 14
 };
 
 /* Enable (1) or disable (0) per-phase timing with CUDA events recorded on the

@@ -93,6 +93,10 @@ nrs_status alloc_all(Ctx *c)
         {(void **)&c->d_bar, sizeof(int32_t) * 2},
         {(void **)&c->d_pg_stats, sizeof(double) * 8},
         {(void **)&c->d_step_stats, sizeof(double) * 16},
+        {(void **)&c->d_Xsh, sizeof(float4) * Q},
+        {(void **)&c->d_Xsl, sizeof(float4) * Q},
+        {(void **)&c->d_xh, sizeof(float4) * N},
+        {(void **)&c->d_xl, sizeof(float4) * N},
     };
     for (auto &r : req) {
         *r.p = nullptr;
@@ -118,7 +122,7 @@ void free_all(Ctx *c)
                     c->d_V,      c->d_H,      c->d_gv,     c->d_scal,       c->d_part,
                     c->d_t32,    c->d_t64,    c->d_flags,  c->d_status,     c->d_gj_dinv,
                     c->d_gj_rt,  c->d_gj_cb,  c->d_dpart,  c->d_bar,        c->d_pg_stats,
-                    c->d_step_stats};
+                    c->d_step_stats, c->d_Xsh, c->d_Xsl, c->d_xh, c->d_xl};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *mlp[] = {c->d_mlp_params, c->d_mlp_m,  c->d_mlp_v,     c->d_mlp_g,    c->d_mlp_x,
@@ -134,10 +138,15 @@ void free_all(Ctx *c)
     if (c->ev_prep) cudaEventDestroy(c->ev_prep);
     if (c->ev_diag) cudaEventDestroy(c->ev_diag);
     if (c->stream2) cudaStreamDestroy(c->stream2);
+    if (c->stream3) cudaStreamSynchronize(c->stream3), cudaStreamDestroy(c->stream3);
+    if (c->ev_asm) cudaEventDestroy(c->ev_asm);
+    if (c->ev_asm_done) cudaEventDestroy(c->ev_asm_done);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->gstream) cudaStreamDestroy(c->gstream);
     c->ev_prep = c->ev_diag = nullptr;
     c->stream2 = nullptr;
+    c->stream3 = nullptr;
+    c->ev_asm = c->ev_asm_done = nullptr;
     c->gexec = nullptr;
     c->gstream = nullptr;
 }
@@ -157,6 +166,7 @@ nrs_status do_factor(Ctx *c, int prec)
         return fail(c, NRS_EINVAL, "tensor-core factor precision not available in this build");
     const size_t elems = (size_t)c->lda * c->n;
     if (prec == NRS_FP64) {
+        nrs::join_assembly(*c);
         if (!c->d_LU64) {
             cudaError_t e = cudaMalloc(&c->d_LU64, sizeof(double) * elems);
             if (e != cudaSuccess) {
@@ -172,6 +182,7 @@ nrs_status do_factor(Ctx *c, int prec)
         nrs::run_lu_fp64(*c, c->d_LU64, c->lda);
     } else {
         if (!c->a32_fresh) {
+            nrs::join_assembly(*c);  // the conversion reads the FP64 matrix
             c->tbeg(nrs::PH_CONVERT);
             k_cvt_f64_f32<<<(unsigned)nrs::ceil_div((int64_t)elems, 256), 256, 0, c->stream>>>(
                 (int64_t)elems, c->d_A64, c->d_A32);
@@ -194,7 +205,22 @@ nrs_status do_segments_and_assemble(Ctx *c, const D4 *x_lab, const D4 *Xw_lab, b
     nrs::launch_gather(*c, Xw_lab, c->d_seg_ptr, c->d_perm);
     float *a32 = (c->factor_prec == NRS_FP64 || !write_lo) ? nullptr : c->d_A32;
     if (a32 && c->factored_prec != NRS_FP64) c->factored_prec = -1;
-    nrs::launch_assemble(*c, x_lab, c->d_A64, a32, c->lda);
+    nrs::join_assembly(*c);  // an earlier FP64 assembly must not overlap this one
+    if (a32 && c->lo_eval == 0) {
+        // the FP32 copy first, alone on the GPU, so the factorisation can start;
+        // then the FP64 matrix on the side stream beside the factorisation,
+        // joined before the refinement uses it
+        nrs::launch_assemble32(*c, x_lab, a32, c->lda);
+        CK(cudaEventRecord(c->ev_asm, c->stream));
+        CK(cudaStreamWaitEvent(c->stream3, c->ev_asm, 0));
+        nrs::launch_assemble(*c, x_lab, c->d_A64, nullptr, c->lda, c->stream3);
+        CK(cudaEventRecord(c->ev_asm_done, c->stream3));
+        c->asm_pending = true;
+    } else {
+        // one FP64 pass; with an FP32 copy, that copy is the rounded FP64 entries
+        nrs::launch_assemble(*c, x_lab, c->d_A64, a32, c->lda);
+    }
+    // the border rows and columns: disjoint from the block the side stream writes
     nrs::launch_border(*c, x_lab, c->d_A64, a32, c->lda);
     CK(cudaGetLastError());
     c->a32_fresh = a32 != nullptr;
@@ -251,6 +277,13 @@ nrs_status mlp_alloc(Ctx *c)
 
 namespace nrs {
 
+void join_assembly(Ctx &c)
+{
+    if (!c.asm_pending) return;
+    cudaStreamWaitEvent(c.stream, c.ev_asm_done, 0);
+    c.asm_pending = false;
+}
+
 bool graph_capable(const Ctx &c)
 {
     return c.factor_prec != NRS_FP64 && c.solve_mode == 0 && c.max_inner <= 64 &&
@@ -287,6 +320,7 @@ nrs_status enqueue_step(Ctx *c, const nrs_shapes *s0, const nrs_shapes *sh, doub
             CK(cudaMemcpyAsync(out, prev, sizeof(double) * c->n, cudaMemcpyDeviceToDevice,
                                c->stream));
         double *so = stats + 8 * stage;
+        join_assembly(*c);
         CK(launch_gmres_persistent(*c, c->d_b, out, !warm, so));
         if (berr) enqueue_backward_error(*c, c->d_b, out, so + 5);
         launch_rk2(*c, stage, dt, out);
@@ -449,6 +483,7 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
         return NRS_EINVAL;
     }
     c->tol_in = d->inner_tol > 0.0 ? d->inner_tol : 1e-4;
+    c->lo_eval = d->factor_input ? 1 : 0;
     c->graph_mode = d->graph ? 1 : 0;
     if (c->graph_mode && (d->factor_prec == NRS_FP64 || c->solve_mode != 0 || d->reuse_factor ||
                           (d->max_inner > 64))) {
@@ -526,6 +561,14 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
     }
     if (e == cudaSuccess && c->graph_mode)
         e = cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        // the FP64 assembly fills what the latency-bound factorisation leaves idle
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        e = cudaStreamCreateWithPriority(&c->stream3, cudaStreamNonBlocking, least);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_asm, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_asm_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_prep, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_diag, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -639,9 +682,11 @@ nrs_status nrs_assemble(nrs_ctx *ctx, const double *x, const double *Xw, double 
     if (A64 && lda < c->n) return fail(c, NRS_EINVAL, "nrs_assemble: lda < n");
     nrs_status st = do_segments_and_assemble(c, (const D4 *)x, (const D4 *)Xw);
     if (st != NRS_OK) return st;
-    if (A64)
+    if (A64) {
+        nrs::join_assembly(*c);
         CK(cudaMemcpy2DAsync(A64, sizeof(double) * lda, c->d_A64, sizeof(double) * c->lda,
                              sizeof(double) * c->n, c->n, cudaMemcpyDeviceToDevice, c->stream));
+    }
     return NRS_OK;
 }
 
@@ -987,6 +1032,7 @@ nrs_status nrs_sync(nrs_ctx *ctx)
 {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c) return NRS_EINVAL;
+    nrs::join_assembly(*c);
     CK(cudaStreamSynchronize(c->stream));
     int32_t st = 0;
     CK(cudaMemcpy(&st, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));

@@ -12,7 +12,15 @@
 // whose quadrature points are staged through shared memory.  Six distinct
 // products r_j r_k t and one diagonal term (|r|^2 + 2 eps^2) t are
 // accumulated per (m, n); no atomics.
+//
+// For the mixed-precision path the FP32 copy that the factorisation inverts
+// comes from k_assemble32 (FP32 arithmetic after an FP64 difference), so the
+// factorisation can start at once; k_assemble64 then builds the FP64 matrix
+// that only the refinement's residuals need, on a low-priority stream that
+// overlaps the factorisation.
 #include <math.h>
+
+#include <algorithm>
 
 #include "nrs_internal.cuh"
 
@@ -44,15 +52,21 @@ __device__ __forceinline__ void flush_block(int64_t m, int64_t n, const Acc7 &a,
     }
 }
 
+// One tile = AS_THREADS collocation points x AS_NT segments; tiles are taken
+// in grid-stride order (tile = mx + gx * ny), so the kernel also runs on a
+// capped grid beside the factorisation.
 __global__ void __launch_bounds__(AS_THREADS)
     k_assemble64(int64_t N, const D4 *__restrict__ x, const D4 *__restrict__ Xs,
                  const int32_t *__restrict__ seg_ptr, double eps2, double c,
-                 double *__restrict__ A64, float *__restrict__ A32, int64_t lda)
+                 double *__restrict__ A64, float *__restrict__ A32, int64_t lda, int64_t gx,
+                 int64_t tiles)
 {
     __shared__ D4 sX[AS_CHUNK];
     __shared__ int32_t sp[AS_NT + 1];
-    const int64_t m = (int64_t)blockIdx.x * AS_THREADS + threadIdx.x;
-    const int64_t n0 = (int64_t)blockIdx.y * AS_NT;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    __syncthreads();  // the previous tile is done with sp and sX
+    const int64_t m = (tile % gx) * AS_THREADS + threadIdx.x;
+    const int64_t n0 = (tile / gx) * AS_NT;
     const int nt = (int)min((int64_t)AS_NT, N - n0);
     if (threadIdx.x <= nt) sp[threadIdx.x] = seg_ptr[n0 + threadIdx.x];
     const bool active = m < N;
@@ -102,17 +116,133 @@ __global__ void __launch_bounds__(AS_THREADS)
         a = Acc7{0, 0, 0, 0, 0, 0, 0};
         ++cur;
     }
+    }  // tile loop
 }
 
-void launch_assemble(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t lda)
+// Coordinates as pairs of floats: p = hi + lo with hi = (float)p and
+// lo = (float)(p - hi), so that differences of nearby points are formed in
+// FP32 without losing the digits that the FP64 difference keeps.
+__global__ void k_split_points(int64_t count, const D4 *__restrict__ p, float4 *__restrict__ hi,
+                               float4 *__restrict__ lo)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const D4 v = p[i];
+    const float hx = (float)v.x, hy = (float)v.y, hz = (float)v.z;
+    hi[i] = make_float4(hx, hy, hz, (float)v.w);
+    lo[i] = make_float4((float)(v.x - (double)hx), (float)(v.y - (double)hy),
+                        (float)(v.z - (double)hz), 0.0f);
+}
+
+// The FP32 copy that the factorisation inverts, on its own: the same sums in
+// FP32, with x_m - X_q = (x_hi - X_hi) + (x_lo - X_lo) from the float pairs
+// (the hi difference is exact for points closer than their own magnitude),
+// so each entry carries a few FP32 roundings.
+__global__ void __launch_bounds__(AS_THREADS)
+    k_assemble32(int64_t N, const float4 *__restrict__ xh, const float4 *__restrict__ xl,
+                 const float4 *__restrict__ Xh, const float4 *__restrict__ Xl,
+                 const int32_t *__restrict__ seg_ptr, float eps2, float c, float *__restrict__ A32,
+                 int64_t lda)
+{
+    __shared__ float4 sH[AS_CHUNK], sL[AS_CHUNK];
+    __shared__ int32_t sp[AS_NT + 1];
+    const int64_t m = (int64_t)blockIdx.x * AS_THREADS + threadIdx.x;
+    const int64_t n0 = (int64_t)blockIdx.y * AS_NT;
+    const int nt = (int)min((int64_t)AS_NT, N - n0);
+    if (threadIdx.x <= nt) sp[threadIdx.x] = seg_ptr[n0 + threadIdx.x];
+    const bool active = m < N;
+    float4 ph = make_float4(0.f, 0.f, 0.f, 0.f), pl = ph;
+    if (active) {
+        ph = xh[m];
+        pl = xl[m];
+    }
+    const float two_e2 = 2.0f * eps2;
+    float axx = 0, axy = 0, axz = 0, ayy = 0, ayz = 0, azz = 0, ad = 0;
+    auto flush = [&](int64_t nn) {
+        const float v[9] = {c * (axx + ad), c * axy,        c * axz,
+                            c * axy,        c * (ayy + ad), c * ayz,
+                            c * axz,        c * ayz,        c * (azz + ad)};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int64_t col = (3 * nn + k) * lda + 3 * m;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) A32[col + j] = v[3 * j + k];
+        }
+    };
+    __syncthreads();
+    int cur = 0;
+    const int32_t qbeg = sp[0], qend = sp[nt];
+    for (int32_t c0 = qbeg; c0 < qend; c0 += AS_CHUNK) {
+        const int cnt = min(AS_CHUNK, qend - c0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt; i += AS_THREADS) {
+            sH[i] = Xh[c0 + i];
+            sL[i] = Xl[c0 + i];
+        }
+        __syncthreads();
+        int32_t next = sp[cur + 1];
+        for (int i = 0; i < cnt; ++i) {
+            const int32_t q = c0 + i;
+            while (q >= next) {  // uniform across the block
+                if (active) flush(n0 + cur);
+                axx = axy = axz = ayy = ayz = azz = ad = 0.0f;
+                ++cur;
+                next = sp[cur + 1];
+            }
+            const float4 H = sH[i], Lo = sL[i];
+            const float rx = (ph.x - H.x) + (pl.x - Lo.x);
+            const float ry = (ph.y - H.y) + (pl.y - Lo.y);
+            const float rz = (ph.z - H.z) + (pl.z - Lo.z);
+            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+            const float inv = rsqrtf(r2 + eps2);
+            const float t = H.w * (inv * inv * inv);
+            const float tx = rx * t, ty = ry * t, tz = rz * t;
+            axx = fmaf(rx, tx, axx);
+            axy = fmaf(rx, ty, axy);
+            axz = fmaf(rx, tz, axz);
+            ayy = fmaf(ry, ty, ayy);
+            ayz = fmaf(ry, tz, ayz);
+            azz = fmaf(rz, tz, azz);
+            ad = fmaf(r2 + two_e2, t, ad);
+        }
+    }
+    while (cur < nt) {
+        if (active) flush(n0 + cur);
+        axx = axy = axz = ayy = ayz = azz = ad = 0.0f;
+        ++cur;
+    }
+}
+
+void launch_assemble(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t lda,
+                     cudaStream_t s)
+{
+    const bool side = s != nullptr;
+    s = side ? s : c.stream;
+    const int64_t gx = ceil_div(c.N, AS_THREADS), tiles = gx * ceil_div(c.N, AS_NT);
+    // beside the factorisation: one CTA of four warps per SM, grid-stride over the
+    // tiles, so the factorisation's kernels keep most of every SM
+    const int64_t grid = side ? std::min<int64_t>(tiles, c.num_sms) : tiles;
+    const double coef = 1.0 / (8.0 * kPi * c.mu);
+    c.tbeg(PH_ASSEMBLE, s);
+    k_assemble64<<<(unsigned)grid, AS_THREADS, 0, s>>>(c.N, x_lab, c.d_Xs, c.d_seg_ptr,
+                                                       c.eps * c.eps, coef, A64, A32, lda, gx,
+                                                       tiles);
+    c.tend(PH_ASSEMBLE, s);
+    c.launches += 1;
+}
+
+void launch_assemble32(Ctx &c, const D4 *x_lab, float *A32, int64_t lda)
 {
     dim3 grid((unsigned)ceil_div(c.N, AS_THREADS), (unsigned)ceil_div(c.N, AS_NT));
-    const double coef = 1.0 / (8.0 * kPi * c.mu);
-    c.tbeg(PH_ASSEMBLE);
-    k_assemble64<<<grid, AS_THREADS, 0, c.stream>>>(c.N, x_lab, c.d_Xs, c.d_seg_ptr, c.eps * c.eps,
-                                                    coef, A64, A32, lda);
-    c.tend(PH_ASSEMBLE);
-    c.launches += 1;
+    const float coef = (float)(1.0 / (8.0 * kPi * c.mu));
+    c.tbeg(PH_ASSEMBLE32);
+    k_split_points<<<(unsigned)ceil_div(c.N, 256), 256, 0, c.stream>>>(c.N, x_lab, c.d_xh, c.d_xl);
+    k_split_points<<<(unsigned)ceil_div(c.Q, 256), 256, 0, c.stream>>>(c.Q, c.d_Xs, c.d_Xsh, c.d_Xsl);
+    k_assemble32<<<grid, AS_THREADS, 0, c.stream>>>(c.N, c.d_xh, c.d_xl, c.d_Xsh, c.d_Xsl,
+                                                    c.d_seg_ptr, (float)(c.eps * c.eps), coef, A32,
+                                                    lda);
+    c.tend(PH_ASSEMBLE32);
+    c.launches += 3;
 }
 
 }  // namespace nrs

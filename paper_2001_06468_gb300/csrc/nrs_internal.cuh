@@ -56,6 +56,7 @@ enum Phase {
     PH_KRYLOV = NRS_PH_KRYLOV,
     PH_UPDATE = NRS_PH_UPDATE,
     PH_LU_DIAG = NRS_PH_LU_DIAG,
+    PH_ASSEMBLE32 = NRS_PH_ASSEMBLE32,
     NPH = NRS_NPHASE
 };
 
@@ -69,7 +70,11 @@ void launch_border(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t lda
 void launch_rk2(Ctx &c, int stage, double dt, const double *sol);
 
 // ---- assembly (assemble.cu) ----------------------------------------------
-void launch_assemble(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t lda);
+void launch_assemble(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t lda,
+                     cudaStream_t s = nullptr);
+void launch_assemble32(Ctx &c, const D4 *x_lab, float *A32, int64_t lda);
+// make c.stream wait for the FP64 assembly running on the side stream, if any
+void join_assembly(Ctx &c);
 
 // ---- factorisation (lu.cu) -------------------------------------------------
 int run_lu_fp64(Ctx &c, double *A, int64_t lda);
@@ -121,6 +126,10 @@ struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t stream2 = nullptr;              // lookahead stream of the factorisation
+    cudaStream_t stream3 = nullptr;              // FP64 assembly overlapping the factorisation
+    cudaEvent_t ev_asm = nullptr, ev_asm_done = nullptr;
+    bool asm_pending = false;                    // stream3 holds an FP64 assembly not yet joined
+    int lo_eval = 0;  // FP32 copy for the factor: 0 evaluated in FP32 (overlapped), 1 rounded FP64
     cudaEvent_t ev_prep = nullptr, ev_diag = nullptr;
     int num_sms = 0;
     std::string err;
@@ -152,6 +161,8 @@ struct Ctx {
     // nearest neighbours and segments
     int32_t *d_nn = nullptr, *d_seg_ptr = nullptr, *d_perm = nullptr, *d_cursor = nullptr;
     D4 *d_Xs = nullptr;        // lab-frame quadrature points in segment order
+    float4 *d_Xsh = nullptr, *d_Xsl = nullptr;  // the same as float pairs (FP32 assembly)
+    float4 *d_xh = nullptr, *d_xl = nullptr;    // force points as float pairs
     double *d_W = nullptr;     // W_n
     double *d_R = nullptr;     // R_n (N x 3)
     bool seg_valid = false;

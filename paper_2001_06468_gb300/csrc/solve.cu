@@ -531,6 +531,7 @@ void enqueue_backward_error(Ctx &c, const double *b, const double *x, double *ou
 cudaError_t choose_start(Ctx &c, const double *b, const double *xp, double *xc, double *x0,
                          double *norms)
 {
+    join_assembly(c);
     cudaError_t e = apply_precond(c, b, xc);
     if (e != cudaSuccess) return e;
     gemv(c, xp, b, c.d_r);
@@ -570,6 +571,7 @@ static nrs_status run_gmres_ir_device(Ctx &c, const double *b, double *x, const 
 nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0, nrs_solve_report *rep,
                         int *inner_out)
 {
+    join_assembly(c);  // the FP64 matrix of the residuals
     if (c.solve_mode == 0 && pg_supported(c)) return run_gmres_ir_device(c, b, x, x0, rep, inner_out);
     const int64_t n = c.n;
     const int m = c.max_inner;

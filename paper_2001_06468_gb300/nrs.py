@@ -48,7 +48,7 @@ MLP_IN, MLP_HID, MLP_OUT = 17, 64, 3
 MLP_PARAMS = MLP_HID * MLP_IN + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_OUT * MLP_HID + MLP_OUT
 START_KINDS = {0: "cold", 1: "previous", 2: "learned"}
 PHASES = ["kinematics", "nearest", "segments", "assemble", "border", "convert", "lu_panel",
-          "lu_update", "trsv", "gemv", "krylov", "update", "lu_diag"]
+          "lu_update", "trsv", "gemv", "krylov", "update", "lu_diag", "assemble32"]
 
 
 class ProblemDesc(ctypes.Structure):
@@ -73,6 +73,7 @@ class ProblemDesc(ctypes.Structure):
                 ("warm_start", ctypes.c_int32),
                 ("solve_mode", ctypes.c_int32),
                 ("inner_tol", ctypes.c_double),
+                ("factor_input", ctypes.c_int32),
                 ("graph", ctypes.c_int32)]
 
 
@@ -183,12 +184,12 @@ class Context:
                  tol: float = 0.0, max_outer: int = 0, max_inner: int = 0,
                  reuse_factor: bool = False, reuse_max_inner: int = 0, reuse_max_stages: int = 0,
                  warm_start: bool = False, solve_mode: str = "device", graph: bool = False,
-                 inner_tol: float = 0.0,
+                 inner_tol: float = 0.0, factor_input: str = "fp32",
                  stream: Optional[torch.cuda.Stream] = None, _handle=None):
         d, self._keep = _make_desc(n_off, q_off, kind, eps, mu, rigid, U, Omega, nn_global,
                                    factor_prec, tol, max_outer, max_inner, reuse_factor,
                                    reuse_max_inner, reuse_max_stages, warm_start, solve_mode,
-                                   graph, inner_tol)
+                                   graph, inner_tol, factor_input)
         self.stream = stream or torch.cuda.current_stream()
         self._owner = _handle is None
         if _handle is None:
@@ -408,7 +409,7 @@ def _problem_args(problem):
 def _make_desc(n_off, q_off, kind, eps, mu=1.0, rigid=None, U=None, Omega=None, nn_global=False,
                factor_prec="fp32", tol=0.0, max_outer=0, max_inner=0, reuse_factor=False,
                reuse_max_inner=0, reuse_max_stages=0, warm_start=False, solve_mode="device",
-               graph=False, inner_tol=0.0):
+               graph=False, inner_tol=0.0, factor_input="fp32"):
     """An nrs_problem_desc and the host arrays it points to (keep them alive)."""
     n_off = np.ascontiguousarray(n_off, dtype=np.int64)
     q_off = np.ascontiguousarray(q_off, dtype=np.int64)
@@ -436,6 +437,7 @@ def _make_desc(n_off, q_off, kind, eps, mu=1.0, rigid=None, U=None, Omega=None, 
     d.solve_mode = {"device": 0, "host": 1}[solve_mode]
     d.graph = int(bool(graph))
     d.inner_tol = float(inner_tol)
+    d.factor_input = {"fp32": 0, "rounded": 1}[factor_input]
     return d, (n_off, q_off, kind, rigid, U, Om)
 
 
