@@ -51,8 +51,14 @@ __global__ void __launch_bounds__(256)
               float *__restrict__ Dinv, int32_t *__restrict__ info,
               const float *__restrict__ Cb, const float *__restrict__ Rt)
 {
-    constexpr int NB = GJ_NB;
-    __shared__ float sm[2][NB][NB + 1];  // Cs, Rs; then the updated block in sm[0]
+    constexpr int NB = GJ_NB, LDT = NB + 4;
+    // the panels, transposed (C^T and R, rows of 68 floats for 16-byte loads);
+    // then the updated block D (rows of 65 floats) in the same storage
+    __shared__ __align__(16) float sraw[2 * NB * LDT];
+    float(*CT)[LDT] = reinterpret_cast<float(*)[LDT]>(sraw);
+    float(*RT)[LDT] = reinterpret_cast<float(*)[LDT]>(sraw + NB * LDT);
+    float(*sm0)[NB + 1] = reinterpret_cast<float(*)[NB + 1]>(sraw);
+    float(*sm1)[NB + 1] = reinterpret_cast<float(*)[NB + 1]>(sraw + NB * LDT);  // for the output
     __shared__ __align__(16) float cand[2][2][NB];  // [step parity][warp][column]
     __shared__ unsigned ckey[2][2];
     __shared__ float cpiv[2][2];
@@ -61,47 +67,73 @@ __global__ void __launch_bounds__(256)
     const int tid = threadIdx.x;
     const int kb = (int)min((int64_t)NB, n - k0);
     {
-        const int r = tid >> 2, s = tid & 3;
-        float L[16];
+        // thread owns the 4 x 4 tile rows r0..r0+3, columns j0..j0+3
+        const int r0 = 4 * (tid >> 4), j0 = 4 * (tid & 15);
+        float L[4][4];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int j = s + 4 * i;
-            L[i] = (r < kb && j < kb) ? M[(k0 + r) + (k0 + j) * lda] : (r == j ? 1.0f : 0.0f);
+        for (int jj = 0; jj < 4; ++jj) {
+            const int j = j0 + jj;
+            if (r0 + 3 < kb && j < kb) {
+                const float4 v = *reinterpret_cast<const float4 *>(M + (k0 + r0) + (k0 + j) * lda);
+                L[0][jj] = v.x;
+                L[1][jj] = v.y;
+                L[2][jj] = v.z;
+                L[3][jj] = v.w;
+            } else {
+#pragma unroll
+                for (int ii = 0; ii < 4; ++ii) {
+                    const int r = r0 + ii;
+                    L[ii][jj] = (r < kb && j < kb) ? M[(k0 + r) + (k0 + j) * lda]
+                                                   : (r == j ? 1.0f : 0.0f);
+                }
+            }
         }
         if (Cb) {
             float cv[16], rv[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
-                cv[q] = b < kb ? Cb[(k0 + b) * NB + a] : 0.0f;
-                rv[q] = b < kb ? Rt[(k0 + b) * NB + a] : 0.0f;
+                cv[q] = b < kb ? Cb[(k0 + b) * NB + a] : 0.0f;   // C[b][a]
+                rv[q] = b < kb ? Rt[(k0 + b) * NB + a] : 0.0f;   // R[a][b]
             }
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
-                sm[0][b][a] = cv[q];
-                sm[1][b][a] = rv[q];
+                CT[a][b] = cv[q];
+                RT[a][b] = rv[q];
             }
             __syncthreads();
+            // L -= C[K,:] R[:,K] on the tile: per t one 16-byte load of C^T and of R
+            float acc[4][4] = {};
+#pragma unroll 8
+            for (int t = 0; t < NB; ++t) {
+                const float4 c4 = *reinterpret_cast<const float4 *>(&CT[t][r0]);
+                const float4 r4 = *reinterpret_cast<const float4 *>(&RT[t][j0]);
+                const float cc[4] = {c4.x, c4.y, c4.z, c4.w};
+                const float rr[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int j = s + 4 * i;
-                float acc = 0.0f;
-#pragma unroll 16
-                for (int t = 0; t < NB; ++t) acc = fmaf(sm[0][r][t], sm[1][j][t], acc);
-                if (r < kb && j < kb) L[i] -= acc;
+                for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = fmaf(cc[ii], rr[jj], acc[ii][jj]);
             }
-            __syncthreads();  // everyone is done with Cs, Rs
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    if (r0 + ii < kb && j0 + jj < kb) L[ii][jj] -= acc[ii][jj];
+            __syncthreads();  // everyone is done with the panels
         }
 #pragma unroll
-        for (int i = 0; i < 16; ++i) sm[0][r][s + 4 * i] = L[i];
+        for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) sm0[r0 + ii][j0 + jj] = L[ii][jj];
     }
     __syncthreads();
     if (tid >= 64) return;
     const int w = tid >> 5, r = tid;
     float T[NB];
 #pragma unroll
-    for (int j = 0; j < NB; ++j) T[j] = sm[0][r][j];
+    for (int j = 0; j < NB; ++j) T[j] = sm0[r][j];
     bool used = false;
     float scale = 1.0f;
     int mypos = 0;
@@ -156,11 +188,11 @@ __global__ void __launch_bounds__(256)
     }
     asm volatile("bar.sync 1, 64;" ::: "memory");  // pivrow complete
     // row mypos of D^{-1}, column pivrow[d] = T[d] * scale: through shared
-    // memory (sm[1] is free) so that the global stores are coalesced
+    // memory (sm1 is free) so that the global stores are coalesced
 #pragma unroll
-    for (int d = 0; d < NB; ++d) sm[1][mypos][pivrow[d]] = T[d] * scale;
+    for (int d = 0; d < NB; ++d) sm1[mypos][pivrow[d]] = T[d] * scale;
     asm volatile("bar.sync 1, 64;" ::: "memory");
-    for (int i = 0; i < NB; ++i) Dinv[i * NB + tid] = sm[1][i][tid];
+    for (int i = 0; i < NB; ++i) Dinv[i * NB + tid] = sm1[i][tid];
 }
 
 // Prep of step K.  grid.y = 0: R[:, j] = D^{-1} M[K, j] for one 64-column tile
