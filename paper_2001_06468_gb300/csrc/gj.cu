@@ -204,8 +204,8 @@ __global__ void __launch_bounds__(256)
               const float *__restrict__ Dinv, float *__restrict__ Rt, float *__restrict__ Cb)
 {
     constexpr int NB = GJ_NB;
-    __shared__ float Ds[NB][NB + 1];
-    __shared__ float Ms[NB][NB + 1];
+    __shared__ __align__(16) float Ds[NB][NB + 4];
+    __shared__ __align__(16) float Ms[NB][NB + 4];
     const int tid = threadIdx.x;
     const int kb = (int)min((int64_t)NB, n - k0);
     const int64_t t0 = (int64_t)blockIdx.x * NB;
@@ -232,46 +232,47 @@ __global__ void __launch_bounds__(256)
         return;
     }
     const bool tile_is_k = (t0 == k0);
+    // D^{-1} transposed and the block row, rows of 68 floats (16-byte loads)
+    float(*DT)[NB + 4] = reinterpret_cast<float(*)[NB + 4]>(&Ds[0][0]);
+    float(*MK)[NB + 4] = reinterpret_cast<float(*)[NB + 4]>(&Ms[0][0]);
     {
         float dv[16], mv[16];  // all loads in flight before the first shared store
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
-            dv[q] = Dinv[b * NB + a];
-            mv[q] = (a < kb && b < nt) ? M[(k0 + a) + (t0 + b) * lda] : 0.0f;
+            dv[q] = Dinv[b * NB + a];                                           // D^{-1}[b][a]
+            mv[q] = (a < kb && b < nt) ? M[(k0 + a) + (t0 + b) * lda] : 0.0f;  // M[K+a][t0+b]
         }
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
-            Ds[b][a] = dv[q];
-            Ms[a][b] = mv[q];
+            DT[a][b] = dv[q];
+            MK[a][b] = mv[q];
         }
     }
     __syncthreads();
-    // thread computes R[r, t0 + c] for r = tr + 16 rr, c = tc + 16 cc (4 x 4)
-    const int tr = tid & 15, tc = tid >> 4;
+    // thread computes R[r0 + x][t0 + c0 + y] for the 4 x 4 tile at (r0, c0)
+    const int r0 = 4 * (tid & 15), c0 = 4 * (tid >> 4);
     float acc[4][4] = {};
 #pragma unroll 8
     for (int t = 0; t < NB; ++t) {
-        float a[4], b[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) a[q] = Ds[tr + 16 * q][t];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) b[q] = Ms[t][tc + 16 * q];
+        const float4 a4 = *reinterpret_cast<const float4 *>(&DT[t][r0]);
+        const float4 b4 = *reinterpret_cast<const float4 *>(&MK[t][c0]);
+        const float a[4] = {a4.x, a4.y, a4.z, a4.w};
+        const float b[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-            for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * b[y];
+            for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
     }
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
-        const int c = tc + 16 * y;
+        const int c = c0 + y;
         if (c >= nt) continue;
+        float v[4];
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
-            const int rr = tr + 16 * x;
-            Rt[(t0 + c) * NB + rr] = (tile_is_k || rr >= kb) ? 0.0f : acc[x][y];
-        }
+        for (int x = 0; x < 4; ++x) v[x] = (tile_is_k || r0 + x >= kb) ? 0.0f : acc[x][y];
+        *reinterpret_cast<float4 *>(&Rt[(t0 + c) * NB + r0]) = make_float4(v[0], v[1], v[2], v[3]);
     }
 }
 
@@ -340,8 +341,8 @@ __global__ void __launch_bounds__(256)
                 const float *__restrict__ Cb)
 {
     constexpr int NB = GJ_NB;
-    __shared__ float Ds[NB][NB + 1];
-    __shared__ float Cs[NB][NB + 1];
+    __shared__ __align__(16) float Ds[NB][NB + 4];
+    __shared__ __align__(16) float Cs[NB][NB + 4];
     const int tid = threadIdx.x;
     const int kb = (int)min((int64_t)NB, n - k0);
     const int64_t t0 = (int64_t)blockIdx.x * NB;
@@ -364,45 +365,51 @@ __global__ void __launch_bounds__(256)
         return;
     }
     if (t0 == k0) return;
+    // C transposed and D^{-1}, rows of 68 floats (16-byte loads)
+    float(*CT)[NB + 4] = reinterpret_cast<float(*)[NB + 4]>(&Cs[0][0]);
+    float(*DD)[NB + 4] = reinterpret_cast<float(*)[NB + 4]>(&Ds[0][0]);
     {
         float dv[16], cv[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
-            dv[q] = Dinv[b * NB + a];
-            cv[q] = b < nt ? Cb[(t0 + b) * NB + a] : 0.0f;
+            dv[q] = Dinv[b * NB + a];                             // D^{-1}[b][a]
+            cv[q] = b < nt ? Cb[(t0 + b) * NB + a] : 0.0f;       // C[t0+b][a]
         }
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
-            Ds[b][a] = dv[q];
-            Cs[b][a] = cv[q];
+            DD[b][a] = dv[q];
+            CT[a][b] = cv[q];
         }
     }
     __syncthreads();
-    // thread computes out[i][c] = -sum_t C[i][t] Dinv[t][c], i = tr + 16 x, c = tc + 16 y
-    const int tr = tid & 15, tc = tid >> 4;
+    // thread computes out[i0 + x][c0 + y] = -sum_t C[i][t] D^{-1}[t][c] on its 4 x 4 tile
+    const int i0 = 4 * (tid & 15), c0 = 4 * (tid >> 4);
     float acc[4][4] = {};
 #pragma unroll 8
     for (int t = 0; t < NB; ++t) {
-        float a[4], b[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) a[q] = Cs[tr + 16 * q][t];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) b[q] = Ds[t][tc + 16 * q];
+        const float4 a4 = *reinterpret_cast<const float4 *>(&CT[t][i0]);
+        const float4 b4 = *reinterpret_cast<const float4 *>(&DD[t][c0]);
+        const float a[4] = {a4.x, a4.y, a4.z, a4.w};
+        const float b[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-            for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * b[y];
+            for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
     }
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
-        const int c = tc + 16 * y;
+        const int c = c0 + y;
         if (c >= kb) continue;
+        float *col = M + t0 + (k0 + c) * lda;
+        if (i0 + 3 < nt) {
+            *reinterpret_cast<float4 *>(col + i0) =
+                make_float4(-acc[0][y], -acc[1][y], -acc[2][y], -acc[3][y]);
+        } else {
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
-            const int i = tr + 16 * x;
-            if (i < nt) M[(t0 + i) + (k0 + c) * lda] = -acc[x][y];
+            for (int x = 0; x < 4; ++x)
+                if (i0 + x < nt) col[i0 + x] = -acc[x][y];
         }
     }
 }
