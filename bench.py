@@ -196,10 +196,14 @@ def _rooflines(ph_ms, ph_spans, pr, peaks, peak_src, clocks, solve_stats=None):
     recs = {}
     t = per_launch("lu_diag")
     w = 4.0 * 64 ** 3
+    sm_peak = fp32_peak / SM_COUNT_NOMINAL
     recs["lu_diag"] = {"kernel": "k_gj_diag (64 x 64 diagonal-block inverse, one CTA)",
-                       "bound": "alu", "achieved": w / t / 1e12, "peak": fp32_peak,
-                       "unit": "TFLOP/s", "frac": w / t / 1e12 / fp32_peak,
-                       "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
+                       "bound": "alu", "achieved": w / t / 1e12, "peak": sm_peak,
+                       "unit": "TFLOP/s", "frac": w / t / 1e12 / sm_peak,
+                       "peak_source": f"derived: ONE SM (the kernel is one CTA by construction: "
+                                      f"64 dependent pivot steps), 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz; "
+                                      f"{w / t / 1e12 / fp32_peak:.5f} of the whole GPU's FP32 peak",
+                       "latency_bound": True,
                        "work_per_launch": w, "launches": ph_spans["lu_diag"],
                        "traffic": _traffic("k_gj_diag", n)}
     t = per_launch("lu_update")
