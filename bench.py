@@ -19,6 +19,7 @@ uneven problems in one graph.
                     [--prec tf32|fp32|fp64]
     python bench.py --profile-solve --workload swimmer_mid   # one solve, for ncu
     python bench.py --no-batch --no-cpu-baseline             # the C1 lines only
+    python bench.py --batch-full                             # all 128 full-size batch problems
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 on the same workload.  Under torchrun each rank runs its own replica of the
@@ -563,7 +564,7 @@ def _oracle_step_timing(pr, max_steps, budget_s):
     return times, all_stages, O.threads()
 
 
-def _batch_case(nrs, probs, prec, steps, tune=True):
+def _batch_case(nrs, probs, prec, steps, tune=True, plan=None, seq_steps=None):
     """Seconds per batch step of ``probs`` through one recorded graph (K and G
     from the autotuner), and the same problems stepped one after the other
     on eager contexts, from the same initial states and inputs."""
@@ -591,6 +592,8 @@ def _batch_case(nrs, probs, prec, steps, tune=True):
         return bufs
 
     batch.step(load(0), dt)  # first step: nearest-neighbour maps, eager
+    if plan is not None:
+        batch.config(*plan)
     tuned = batch.tune(load(1), dt) if tune else batch.info()
     batch.step(load(1), dt)  # records the graph with the tuned plan
     torch.cuda.synchronize()
@@ -613,13 +616,14 @@ def _batch_case(nrs, probs, prec, steps, tune=True):
         Y = g.initial_state(pr)
         c.set_state(Y["x0"], Y["B"])
         ctxs.append(c)
+    seq_steps = steps if seq_steps is None else seq_steps
     for s in range(2):
         for i, c in enumerate(ctxs):
             a, b = pairs_at(s)[i]
             c.step(nrs.Context.shapes(*a), nrs.Context.shapes(*b), dt, report=False)
     torch.cuda.synchronize()
     ms_seq = 0.0
-    for s in range(steps):
+    for s in range(seq_steps):
         torch.cuda.synchronize()
         e0.record(st)
         for i, c in enumerate(ctxs):
@@ -635,8 +639,8 @@ def _batch_case(nrs, probs, prec, steps, tune=True):
             "pairs": int(sum(pr.pairs for pr in probs)),
             "s_per_batch_step": ms / 1e3 / steps,
             "problem_steps_per_s": nprob * steps / (ms / 1e3),
-            "sequential_eager_s_per_batch_step": ms_seq / 1e3 / steps,
-            "speedup_vs_sequential": ms_seq / ms, "steps": steps,
+            "sequential_eager_s_per_batch_step": ms_seq / 1e3 / seq_steps,
+            "speedup_vs_sequential": (ms_seq / seq_steps) / (ms / steps), "steps": steps,
             "chains": info["chains"], "solve_grid": info["grid"],
             "graph_kernels": info["graph_kernels"],
             "tuned_ms": tuned.get("ms")}
@@ -654,6 +658,25 @@ def batch_bench(nrs, args):
                                 recipe="cilia 4-12 (10/100 points), floor 160-500 (x10), spheres 26/386"),
             "full_first8": dict(_batch_case(nrs, full, args.prec, 2),
                                 recipe="the batch recipe at full size, problems 0-7")}
+
+
+def batch_full(args):
+    """The whole batch workload at full size (128 ventral-node problems, n 5322-15771,
+    about 173 GB of FP64 + FP32 matrices on the device): seconds per batch step through
+    one graph with a fixed plan (K = 8 chains, G = 38: the autotuner's choice on the
+    first 8 problems; tuning all 128 would take minutes), and one step of the same
+    problems one after the other.  Not part of the default run."""
+    import torch
+    from paper_2001_06468_gb300 import nrs
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    probs = g.node_batch(128)
+    gen_s = time.time() - t0
+    res = _batch_case(nrs, probs, args.prec, 2, tune=False, plan=(8, 38), seq_steps=1)
+    res.update({"workload": "ventral-node batch, all 128 problems at full size",
+                "generator_s": gen_s,
+                "matrix_bytes": int(sum(12 * pr.n * pr.n for pr in probs))})
+    print(json.dumps(res), flush=True)
 
 
 def cpu_baseline(pr, sols):
@@ -740,6 +763,8 @@ def main():
     ap.add_argument("--prec", default="tf32", choices=["fp32", "tf32", "bf16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch workload section")
+    ap.add_argument("--batch-full", action="store_true",
+                    help="only the full-size batch of 128 problems (one JSON line)")
     ap.add_argument("--profile-solve", action="store_true",
                     help="one kinematics + nearest + assemble + factor + solve on --workload, "
                          "then exit (for ncu captures)")
@@ -747,6 +772,9 @@ def main():
     args = ap.parse_args()
     if args.profile_solve:
         profile_solve(args)
+        return
+    if args.batch_full:
+        batch_full(args)
         return
     if args.warmup < 3 and args.impl == "nrs":
         args.warmup = 3

@@ -71,3 +71,37 @@ def test_pack_layout():
     assert sh["x"].shape == (pr.N, 4) and sh["Xw"].shape == (pr.Q, 4)
     assert list(sh["n_off"]) == [0, 6000, 6400, 6800]
     assert np.all(sh["Xw"][:, 3] > 0)
+
+
+def test_node_batch_sizes_and_structure():
+    # n = 3 (40 c + N_f + 5 * 98) + 6 * 5 = 120 c + 3 N_f + 1500 for every problem
+    for i in (0, 5, 77):
+        pr = g.node_config(i)
+        c = sum(1 for b in pr.bodies if b.name.startswith("cilium"))
+        nf = pr.bodies[0].N
+        assert 10 <= c <= 60 and 800 <= nf <= 2500
+        assert pr.bodies[0].Q == 10 * nf and pr.n == 120 * c + 3 * nf + 1500
+        assert [b.kind for b in pr.bodies].count(g.FREE) == 5
+    # seeded: the same index gives the same problem, another index another one
+    a, b, c2 = g.node_config(3), g.node_config(3), g.node_config(4)
+    assert a.n == b.n and np.array_equal(a.bodies[1].x0, b.bodies[1].x0)
+    assert (a.n, a.bodies[1].x0.tolist()) != (c2.n, c2.bodies[1].x0.tolist())
+
+
+def test_node_cilia_rotate_on_their_cone():
+    pr = g.node_config(2, cilia=(3, 3), floor=(100, 100), n_rod=8, q_rod=40)
+    for b in pr.bodies[1:4]:
+        a = -b.Omega / np.linalg.norm(b.Omega)       # cone axis (clockwise from above)
+        d = b.B[:, 0]                                  # the rod, body x-axis, lab frame
+        assert abs(np.linalg.norm(b.Omega) - 2 * np.pi) < 1e-12
+        assert abs(np.dot(a, d) - np.cos(np.radians(30.0))) < 1e-12   # semi-angle 30 degrees
+        tilt = np.degrees(np.arccos(a[2]))
+        assert 30.0 - 1e-9 <= tilt <= 45.0 + 1e-9 and a[1] <= 0.0     # tilted towards -y
+        assert np.allclose(b.B.T @ b.B, np.eye(3), atol=1e-14)
+        assert b.x0[2] == 0.0 and np.hypot(*b.x0[:2]) <= 1.6 + 1e-12  # base on the floor disc
+
+
+def test_vogel_disc_weights_sum_to_the_area():
+    P, w = g.vogel_disc(1000, 2.0)
+    assert abs(w.sum() - np.pi * 4.0) < 1e-12
+    assert np.max(np.hypot(P[:, 0], P[:, 1])) < 2.0 and np.all(P[:, 2] == 0.0)
