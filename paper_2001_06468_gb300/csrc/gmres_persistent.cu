@@ -127,7 +127,7 @@ __device__ void mv64_partial(const PgArgs &a, const double *v, double scale, dou
         double s0 = 0.0, s1 = 0.0;
         if (i < a.n) {
             const double *col = a.A + i;
-#pragma unroll 4
+#pragma unroll 8
             for (int64_t j = j0 + grp; j < j1; j += MV_GROUPS) {
                 const double2 x = __ldg(reinterpret_cast<const double2 *>(col + j * a.lda));
                 if (ABS) {  // row sums of |A|
@@ -167,7 +167,7 @@ __device__ void mv32_partial(const PgArgs &a, const double *v, float *sm)
         float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
         if (i < a.n) {
             const float *col = a.M + i;
-#pragma unroll 4
+#pragma unroll 8
             for (int64_t j = j0 + grp; j < j1; j += MV_GROUPS) {
                 const float4 x = __ldg(reinterpret_cast<const float4 *>(col + j * a.lda));
                 const float vj = (float)__ldcg(v + j);
@@ -526,7 +526,9 @@ int pg_grid(Ctx &c)
     if (c.pg_grid > 0) return c.pg_grid;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gmres_ir, PG_THREADS, 0);
-    per_sm = std::max(1, std::min(per_sm, 1));
+    // one CTA per SM while barriers dominate (matrices in L2); two once the
+    // products stream the matrices from HBM and need more bytes in flight
+    per_sm = std::max(1, std::min(per_sm, c.n >= 4096 ? 2 : 1));
     c.pg_grid = per_sm * c.num_sms;
     return c.pg_grid;
 }

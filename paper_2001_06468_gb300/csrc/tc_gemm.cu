@@ -254,23 +254,33 @@ __global__ void __launch_bounds__(128, 1)
         const int64_t row = row0 + warp * 32 + lane;
         // the 64 x 64 block at (skip0, skip0) is updated separately (lookahead)
         const bool row_skip = row >= skip0 && row < skip0 + 64;
+        // software-pipelined read-modify-write of this thread's row: the loads
+        // of chunk c + 1 are issued before chunk c is subtracted and stored
+        float cur[16], nxt[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) cur[j] = (row < n && col0 + j < n) ? M[row + (col0 + j) * lda] : 0.0f;
 #pragma unroll 1
         for (int chunk = 0; chunk < TC_BN / 16; ++chunk) {
+            const int64_t cbeg = col0 + chunk * 16;
+            if (chunk + 1 < TC_BN / 16) {
+                const int64_t nbeg = cbeg + 16;
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    nxt[j] = (row < n && nbeg + j < n) ? M[row + (nbeg + j) * lda] : 0.0f;
+            }
             uint32_t v[16];
             tmem_ld_16cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(chunk * 16), v);
             if (row < n) {
-                float old[16];  // all 16 loads in flight before the stores
-                const int64_t cbeg = col0 + chunk * 16;
                 float *p = M + row + cbeg * lda;
                 const int64_t ncol = n - cbeg;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) old[j] = j < ncol ? p[j * lda] : 0.0f;
-#pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const bool skip = row_skip && cbeg + j >= skip0 && cbeg + j < skip0 + 64;
-                    if (j < ncol && !skip) p[j * lda] = old[j] - __uint_as_float(v[j]);
+                    if (j < ncol && !skip) p[j * lda] = cur[j] - __uint_as_float(v[j]);
                 }
             }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) cur[j] = nxt[j];
         }
     }
     tc_fence_before();
