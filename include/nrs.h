@@ -458,6 +458,16 @@ nrs_status nrs_set_timing(nrs_ctx *ctx, int32_t enable);
  * since timing was last enabled), then clear the totals. */
 nrs_status nrs_get_timing(nrs_ctx *ctx, double *ms, int64_t *spans, int64_t *launches);
 
+/* The timed spans since timing was enabled, in the order they were recorded,
+ * as a trace: phase[i] (an NRS_PH_* value) and begin_ms[i], end_ms[i]
+ * (milliseconds from the begin of the first span; spans on the factorisation's
+ * side streams overlap those on the main stream).  Host arrays of `capacity`
+ * entries (any may be NULL); the first min(capacity, *count) spans are
+ * written and *count is set to the number recorded.  Synchronises; clears
+ * nothing, so call it before nrs_get_timing. */
+nrs_status nrs_get_trace(nrs_ctx *ctx, int32_t *phase, double *begin_ms, double *end_ms,
+                         int64_t capacity, int64_t *count);
+
 #ifdef __cplusplus
 }
 #endif

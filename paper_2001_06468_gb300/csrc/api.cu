@@ -6,6 +6,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -75,8 +76,9 @@ nrs_status alloc_all(Ctx *c)
         {(void **)&c->d_rowperm, sizeof(int32_t) * n},
         {(void **)&c->d_lperm, sizeof(int32_t) * 64},
         {(void **)&c->d_gj_dinv, sizeof(float) * 2 * 64 * 64},
-        {(void **)&c->d_gj_rt, sizeof(float) * 64 * lda},
-        {(void **)&c->d_gj_cb, sizeof(float) * 64 * lda},
+        {(void **)&c->d_gj_rt, sizeof(float) * 2 * 64 * lda},
+        {(void **)&c->d_gj_cb, sizeof(float) * 2 * 64 * lda},
+        {(void **)&c->d_gj_stage, sizeof(float) * 4 * 64 * 64},
         {(void **)&c->d_info, sizeof(int32_t)},
         {(void **)&c->d_r, sizeof(double) * lda},
         {(void **)&c->d_w, sizeof(double) * lda},
@@ -122,7 +124,7 @@ void free_all(Ctx *c)
                     c->d_V,      c->d_H,      c->d_gv,     c->d_scal,       c->d_part,
                     c->d_t32,    c->d_t64,    c->d_flags,  c->d_status,     c->d_gj_dinv,
                     c->d_gj_rt,  c->d_gj_cb,  c->d_dpart,  c->d_bar,        c->d_pg_stats,
-                    c->d_step_stats, c->d_Xsh, c->d_Xsl, c->d_xh, c->d_xl};
+                    c->d_step_stats, c->d_Xsh, c->d_Xsl, c->d_xh, c->d_xl, c->d_gj_stage};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *mlp[] = {c->d_mlp_params, c->d_mlp_m,  c->d_mlp_v,     c->d_mlp_g,    c->d_mlp_x,
@@ -135,16 +137,22 @@ void free_all(Ctx *c)
     if (c->h_mlp_loss) cudaFreeHost(c->h_mlp_loss);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     c->ev_pool.clear();
-    if (c->ev_prep) cudaEventDestroy(c->ev_prep);
+    if (c->ev_upd) cudaEventDestroy(c->ev_upd);
     if (c->ev_diag) cudaEventDestroy(c->ev_diag);
+    if (c->ev_fin_ready) cudaEventDestroy(c->ev_fin_ready);
+    for (auto &e : c->ev_fin)
+        if (e) cudaEventDestroy(e);
     if (c->stream2) cudaStreamDestroy(c->stream2);
+    if (c->stream4) cudaStreamDestroy(c->stream4);
     if (c->stream3) cudaStreamSynchronize(c->stream3), cudaStreamDestroy(c->stream3);
     if (c->ev_asm) cudaEventDestroy(c->ev_asm);
     if (c->ev_asm_done) cudaEventDestroy(c->ev_asm_done);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->gstream) cudaStreamDestroy(c->gstream);
-    c->ev_prep = c->ev_diag = nullptr;
+    c->ev_upd = c->ev_diag = nullptr;
+    c->ev_fin_ready = c->ev_fin[0] = c->ev_fin[1] = nullptr;
     c->stream2 = nullptr;
+    c->stream4 = nullptr;
     c->stream3 = nullptr;
     c->ev_asm = c->ev_asm_done = nullptr;
     c->gexec = nullptr;
@@ -558,6 +566,8 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
         int least = 0, greatest = 0;
         cudaDeviceGetStreamPriorityRange(&least, &greatest);
         e = cudaStreamCreateWithPriority(&c->stream2, cudaStreamNonBlocking, greatest);
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithPriority(&c->stream4, cudaStreamNonBlocking, greatest);
     }
     if (e == cudaSuccess && c->graph_mode)
         e = cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking);
@@ -569,8 +579,11 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_asm, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_asm_done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_prep, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_upd, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_diag, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fin_ready, cudaEventDisableTiming);
+    for (auto &ev : c->ev_fin)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         free_all(c);
         delete c;
@@ -869,6 +882,26 @@ nrs_status nrs_set_timing(nrs_ctx *ctx, int32_t enable)
     return NRS_OK;
 }
 
+nrs_status nrs_get_trace(nrs_ctx *ctx, int32_t *phase, double *begin_ms, double *end_ms,
+                         int64_t capacity, int64_t *count)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || capacity < 0) return NRS_EINVAL;
+    CK(cudaStreamSynchronize(c->stream));
+    const int64_t m = std::min<int64_t>(capacity, (int64_t)c->spans.size());
+    for (int64_t i = 0; i < m; ++i) {
+        const auto &s = c->spans[i];
+        float t0 = 0.0f, t1 = 0.0f;
+        CK(cudaEventElapsedTime(&t0, c->spans[0].a, s.a));
+        CK(cudaEventElapsedTime(&t1, c->spans[0].a, s.b));
+        if (phase) phase[i] = s.ph;
+        if (begin_ms) begin_ms[i] = t0;
+        if (end_ms) end_ms[i] = t1;
+    }
+    if (count) *count = (int64_t)c->spans.size();
+    return NRS_OK;
+}
+
 nrs_status nrs_get_timing(nrs_ctx *ctx, double *ms, int64_t *spans, int64_t *launches)
 {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
@@ -904,7 +937,7 @@ nrs_status nrs_rank64_update(nrs_ctx *ctx, float *M, int64_t lda, int64_t n, con
     if (prec == NRS_FP32) {
         nrs::launch_simt_rank64(*c, M, lda, n, C, Rt);
     } else if (prec == NRS_TF32) {
-        if (!nrs::tc_available() || !nrs::launch_tc_rank64(*c, M, lda, n, C, Rt, prec, -64))
+        if (!nrs::tc_available() || !nrs::launch_tc_rank64(*c, M, lda, n, C, Rt, prec, -64, -64))
             return fail(c, NRS_EINVAL, "nrs_rank64_update: no tensor-core kernel on this device");
     } else {
         return fail(c, NRS_EINVAL, "nrs_rank64_update: precision must be NRS_FP32 or NRS_TF32");

@@ -25,10 +25,19 @@ constexpr int GJ_NB = 64;
 // partial pivoting, written for the latency of one pivot step (this kernel is
 // the critical path of the factorisation: one launch per block column).
 //
-// All 256 threads first stage the block (and, with Cb and Rt given, bring it
-// up to date for the lookahead: D = M[K,K] - C[K,:] R[:,K], the part of the
-// previous rank-64 update that the main stream skips).  Then two warps do the
-// elimination, lane l of warp w holding row r = 32 w + l in registers T[64]:
+// Lookahead (Dprev given, P = the previous block, K = this one): the block is
+// first brought up to date by the part of step P's rank-64 update that the
+// main stream skips, from the un-finished block row and column P of M:
+//     R_PK = Dprev M[P,K],   D = M[K,K] - M[K,P] R_PK,
+// both 4 x 4 register-tiled over 256 threads, the same products (and the same
+// order of operations) as the prep and finish kernels.  Two tiles of step P's
+// finish depend on nothing else and are written here to `stage` instead of M
+// (the finish of step P skips them, and the prep of step K reads them from
+// there): stage[0..4096) = R_PK (column-major, 64 x 64) is M[P,K] after step
+// P, and stage[4096..8192) = -M[K,P] Dprev is M[K,P] after step P; the latter
+// is computed by warps 2, 3, 6 and 7 while warps 0 and 1 do the elimination.
+// The elimination: two warps, lane l of warp w holding row r = 32 w + l in
+// registers T[64]:
 //  * exchange (sweep) form, in place: at the step for column c with pivot row
 //    p, every other row i gets T_i[j] -= (T_i[c] / T_p[c]) T_p[j] (j != c) and
 //    T_i[c] = -T_i[c] / T_p[c]; the pivot row is divided by T_p[c] and gets
@@ -49,16 +58,15 @@ constexpr int GJ_NB = 64;
 __global__ void __launch_bounds__(256)
     k_gj_diag(int64_t n, const float *__restrict__ M, int64_t lda, int64_t k0,
               float *__restrict__ Dinv, int32_t *__restrict__ info,
-              const float *__restrict__ Cb, const float *__restrict__ Rt)
+              const float *__restrict__ Dprev, float *__restrict__ stage)
 {
     constexpr int NB = GJ_NB, LDT = NB + 4;
-    // the panels, transposed (C^T and R, rows of 68 floats for 16-byte loads);
-    // then the updated block D (rows of 65 floats) in the same storage
+    // two 64 x 68 buffers: B0 = Dprev^T, then R_PK, then the block D (rows of
+    // 65 floats), then the output; B1 = M[P,K], then M[K,P]^T
     __shared__ __align__(16) float sraw[2 * NB * LDT];
-    float(*CT)[LDT] = reinterpret_cast<float(*)[LDT]>(sraw);
-    float(*RT)[LDT] = reinterpret_cast<float(*)[LDT]>(sraw + NB * LDT);
+    float(*B0)[LDT] = reinterpret_cast<float(*)[LDT]>(sraw);
+    float(*B1)[LDT] = reinterpret_cast<float(*)[LDT]>(sraw + NB * LDT);
     float(*sm0)[NB + 1] = reinterpret_cast<float(*)[NB + 1]>(sraw);
-    float(*sm1)[NB + 1] = reinterpret_cast<float(*)[NB + 1]>(sraw + NB * LDT);  // for the output
     __shared__ __align__(16) float cand[2][2][NB];  // [step parity][warp][column]
     __shared__ unsigned ckey[2][2];
     __shared__ float cpiv[2][2];
@@ -66,6 +74,7 @@ __global__ void __launch_bounds__(256)
     __shared__ int pivrow[NB];
     const int tid = threadIdx.x;
     const int kb = (int)min((int64_t)NB, n - k0);
+    const int64_t kp = k0 - NB;
     {
         // thread owns the 4 x 4 tile rows r0..r0+3, columns j0..j0+3
         const int r0 = 4 * (tid >> 4), j0 = 4 * (tid & 15);
@@ -88,40 +97,70 @@ __global__ void __launch_bounds__(256)
                 }
             }
         }
-        if (Cb) {
-            float cv[16], rv[16];
+        if (Dprev) {
+            float dv[16], mv[16], cv[16];  // all loads in flight before the first shared store
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
-                cv[q] = b < kb ? Cb[(k0 + b) * NB + a] : 0.0f;   // C[b][a]
-                rv[q] = b < kb ? Rt[(k0 + b) * NB + a] : 0.0f;   // R[a][b]
+                dv[q] = Dprev[b * NB + a];                                        // Dprev[b][a]
+                mv[q] = b < kb ? M[(kp + a) + (k0 + b) * lda] : 0.0f;            // M[P+a][K+b]
+                cv[q] = a < kb ? M[(k0 + a) + (kp + b) * lda] : 0.0f;            // M[K+a][P+b]
             }
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
-                CT[a][b] = cv[q];
-                RT[a][b] = rv[q];
+                B0[a][b] = dv[q];
+                B1[a][b] = mv[q];
             }
             __syncthreads();
-            // L -= C[K,:] R[:,K] on the tile: per t one 16-byte load of C^T and of R
+            // R_PK[s0 + x][t0 + y] = sum_t Dprev[s0 + x][t] M[P+t][K + t0 + y]
+            const int s0 = 4 * (tid & 15), c0 = 4 * (tid >> 4);
             float acc[4][4] = {};
 #pragma unroll 8
             for (int t = 0; t < NB; ++t) {
-                const float4 c4 = *reinterpret_cast<const float4 *>(&CT[t][r0]);
-                const float4 r4 = *reinterpret_cast<const float4 *>(&RT[t][j0]);
+                const float4 a4 = *reinterpret_cast<const float4 *>(&B0[t][s0]);
+                const float4 b4 = *reinterpret_cast<const float4 *>(&B1[t][c0]);
+                const float x4[4] = {a4.x, a4.y, a4.z, a4.w};
+                const float y4[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(x4[x], y4[y], acc[x][y]);
+            }
+            __syncthreads();  // B0 and B1 are free
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+                *reinterpret_cast<float4 *>(&B0[s0 + x][c0]) =
+                    make_float4(acc[x][0], acc[x][1], acc[x][2], acc[x][3]);
+#pragma unroll
+            for (int y = 0; y < 4; ++y)
+                *reinterpret_cast<float4 *>(&stage[(s0) + (c0 + y) * NB]) =
+                    make_float4(acc[0][y], acc[1][y], acc[2][y], acc[3][y]);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int idx = tid + 256 * q;
+                B1[idx >> 6][idx & 63] = cv[q];  // B1[t][i] = M[K+i][P+t]
+            }
+            __syncthreads();
+            // L -= M[K,P] R_PK on the tile: per t one 16-byte load of each operand
+            float acc2[4][4] = {};
+#pragma unroll 8
+            for (int t = 0; t < NB; ++t) {
+                const float4 c4 = *reinterpret_cast<const float4 *>(&B1[t][r0]);
+                const float4 r4 = *reinterpret_cast<const float4 *>(&B0[t][j0]);
                 const float cc[4] = {c4.x, c4.y, c4.z, c4.w};
                 const float rr[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
                 for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = fmaf(cc[ii], rr[jj], acc[ii][jj]);
+                    for (int jj = 0; jj < 4; ++jj) acc2[ii][jj] = fmaf(cc[ii], rr[jj], acc2[ii][jj]);
             }
 #pragma unroll
             for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj)
-                    if (r0 + ii < kb && j0 + jj < kb) L[ii][jj] -= acc[ii][jj];
-            __syncthreads();  // everyone is done with the panels
+                    if (r0 + ii < kb && j0 + jj < kb) L[ii][jj] -= acc2[ii][jj];
+            __syncthreads();  // everyone is done with R_PK in B0
         }
 #pragma unroll
         for (int ii = 0; ii < 4; ++ii)
@@ -129,7 +168,33 @@ __global__ void __launch_bounds__(256)
             for (int jj = 0; jj < 4; ++jj) sm0[r0 + ii][j0 + jj] = L[ii][jj];
     }
     __syncthreads();
-    if (tid >= 64) return;
+    if (tid >= 64) {
+        // warps 2, 3, 6, 7 (the scheduler partitions that warps 0 and 1 do not
+        // use): stage[4096 + i + 64 c] = -sum_t M[K+i][P+t] Dprev[t][c] on a
+        // 4 x 8 tile per thread (M[K,P] transposed in B1, Dprev from global)
+        const int wq = tid >> 5;
+        if (!Dprev || wq == 4 || wq == 5) return;
+        const int u = wq < 4 ? tid - 64 : tid - 128, i0 = 4 * (u & 15), c0 = 8 * (u >> 4);
+        float acc[4][8] = {};
+#pragma unroll 4
+        for (int t = 0; t < NB; ++t) {
+            const float4 a4 = *reinterpret_cast<const float4 *>(&B1[t][i0]);
+            const float4 d0 = __ldg(reinterpret_cast<const float4 *>(Dprev + t * NB + c0));
+            const float4 d1 = __ldg(reinterpret_cast<const float4 *>(Dprev + t * NB + c0 + 4));
+            const float x4[4] = {a4.x, a4.y, a4.z, a4.w};
+            const float y8[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(x4[x], y8[y], acc[x][y]);
+        }
+        float *stx = stage + NB * NB;
+#pragma unroll
+        for (int y = 0; y < 8; ++y)
+            *reinterpret_cast<float4 *>(&stx[i0 + (c0 + y) * NB]) =
+                make_float4(-acc[0][y], -acc[1][y], -acc[2][y], -acc[3][y]);
+        return;
+    }
     const int w = tid >> 5, r = tid;
     float T[NB];
 #pragma unroll
@@ -188,20 +253,25 @@ __global__ void __launch_bounds__(256)
     }
     asm volatile("bar.sync 1, 64;" ::: "memory");  // pivrow complete
     // row mypos of D^{-1}, column pivrow[d] = T[d] * scale: through shared
-    // memory (sm1 is free) so that the global stores are coalesced
+    // memory (B0, read into the registers before the loop) so that the global
+    // stores are coalesced
 #pragma unroll
-    for (int d = 0; d < NB; ++d) sm1[mypos][pivrow[d]] = T[d] * scale;
+    for (int d = 0; d < NB; ++d) sm0[mypos][pivrow[d]] = T[d] * scale;
     asm volatile("bar.sync 1, 64;" ::: "memory");
-    for (int i = 0; i < NB; ++i) Dinv[i * NB + tid] = sm1[i][tid];
+    for (int i = 0; i < NB; ++i) Dinv[i * NB + tid] = sm0[i][tid];
 }
 
 // Prep of step K.  grid.y = 0: R[:, j] = D^{-1} M[K, j] for one 64-column tile
 // (R[:,K] = 0), stored transposed Rt[j * 64 + r].  grid.y = 1: the block column
 // C = M[:, K] for one 64-row tile, stored row-major Cb[i * 64 + c] (rows of K
 // zero).  Both through shared memory so every global access is coalesced.
+// With `stage` given (K > 0), the tiles M[K-1,K] and M[K,K-1] as left by step
+// K-1 are read from there (the diagonal inverse of this step wrote them; the
+// finish of step K-1 skips them in M).
 __global__ void __launch_bounds__(256)
     k_gj_prep(int64_t n, const float *__restrict__ M, int64_t lda, int64_t k0,
-              const float *__restrict__ Dinv, float *__restrict__ Rt, float *__restrict__ Cb)
+              const float *__restrict__ Dinv, float *__restrict__ Rt, float *__restrict__ Cb,
+              const float *__restrict__ stage)
 {
     constexpr int NB = GJ_NB;
     __shared__ __align__(16) float Ds[NB][NB + 4];
@@ -211,13 +281,17 @@ __global__ void __launch_bounds__(256)
     const int64_t t0 = (int64_t)blockIdx.x * NB;
     if (t0 >= n) return;
     const int nt = (int)min((int64_t)NB, n - t0);
+    const bool staged = stage && t0 == k0 - NB;
     if (blockIdx.y == 1) {
         const bool in_k = (t0 == k0);
+        // M[t0 + i][K + c], or column-major 64 x 64 in stage for the tile above
+        const float *src = staged ? stage : M + t0 + k0 * lda;
+        const int64_t ld = staged ? NB : lda;
         float v[16];  // all loads in flight before the first shared store
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const int idx = tid + 256 * q, i = idx & 63, c = idx >> 6;
-            v[q] = (i < nt && c < kb && !in_k) ? M[(t0 + i) + (k0 + c) * lda] : 0.0f;
+            v[q] = (i < nt && c < kb && !in_k) ? src[i + c * ld] : 0.0f;
         }
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
@@ -236,12 +310,15 @@ __global__ void __launch_bounds__(256)
     float(*DT)[NB + 4] = reinterpret_cast<float(*)[NB + 4]>(&Ds[0][0]);
     float(*MK)[NB + 4] = reinterpret_cast<float(*)[NB + 4]>(&Ms[0][0]);
     {
+        // M[K + a][t0 + b], or column-major 64 x 64 in stage for the tile left of K
+        const float *src = staged ? stage + NB * NB : M + k0 + t0 * lda;
+        const int64_t ld = staged ? NB : lda;
         float dv[16], mv[16];  // all loads in flight before the first shared store
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
-            dv[q] = Dinv[b * NB + a];                                           // D^{-1}[b][a]
-            mv[q] = (a < kb && b < nt) ? M[(k0 + a) + (t0 + b) * lda] : 0.0f;  // M[K+a][t0+b]
+            dv[q] = Dinv[b * NB + a];                               // D^{-1}[b][a]
+            mv[q] = (a < kb && b < nt) ? src[a + b * ld] : 0.0f;  // M[K+a][t0+b]
         }
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
@@ -334,11 +411,12 @@ __global__ void __launch_bounds__(256)
 
 // Block row K <- R, block column K <- -C D^{-1}, M[K,K] <- D^{-1}, in 64-wide
 // tiles.  grid.y = 0: column tile t0 of block row K; grid.y = 1: row tile t0
-// of block column K.
+// of block column K.  The tiles at skip_t0 (the next block, whose diagonal
+// inverse computes them and leaves them for the next prep) are not written.
 __global__ void __launch_bounds__(256)
     k_gj_finish(int64_t n, float *__restrict__ M, int64_t lda, int64_t k0,
                 const float *__restrict__ Dinv, const float *__restrict__ Rt,
-                const float *__restrict__ Cb)
+                const float *__restrict__ Cb, int64_t skip_t0)
 {
     constexpr int NB = GJ_NB;
     __shared__ __align__(16) float Ds[NB][NB + 4];
@@ -346,7 +424,7 @@ __global__ void __launch_bounds__(256)
     const int tid = threadIdx.x;
     const int kb = (int)min((int64_t)NB, n - k0);
     const int64_t t0 = (int64_t)blockIdx.x * NB;
-    if (t0 >= n) return;
+    if (t0 >= n || t0 == skip_t0) return;
     const int nt = (int)min((int64_t)NB, n - t0);
     if (blockIdx.y == 0) {
         const bool tile_is_k = (t0 == k0);
@@ -427,52 +505,86 @@ void launch_simt_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *C
     c.launches += 1;
 }
 
-// One inversion.  Main stream, step k: prep_k, update_k (all of M but the
-// next diagonal block), finish_k.  Side stream, as soon as prep_k is done:
-// update of the next diagonal block alone, then its inverse (k_gj_diag into
-// the other D^{-1} buffer), which so overlaps update_k and finish_k; prep_{k+1}
-// waits for it.
+// One inversion.  Streams: main (S), lookahead (S2), finish (S4).  Step k
+// (block K, next block K+1):
+//   S2: (waits the update of step k-1 and the finish of step k-1) the
+//       diagonal inverse of K+1 with its lookahead from D_K^{-1} and the
+//       un-finished block row and column K; it also leaves the two finished
+//       tiles M[K,K+1], M[K+1,K] in stage[k+1 mod 2]              -> ev_diag
+//   S : prep_k: the panels R = D_K^{-1} M[K,:], C = M[:,K]    -> ev_fin_ready
+//   S4: finish_k: block row K <- R, block column K <- -C D_K^{-1},
+//       M[K,K] <- D_K^{-1}, all but the two staged tiles      -> ev_fin[k mod 2]
+//   S : (waits finish_{k-1}) update_k, M -= C R over all of M but block row
+//       and column K and the block (K+1,K+1)                       -> ev_upd
+//   S : waits ev_diag before prep_{k+1}.
+// Per block the diagonal chain is one inverse and the update chain one prep
+// and one update; finish runs beside the update.  D^{-1}, the panels and the
+// staged tiles alternate between two buffers, and every reuse of a buffer
+// is ordered after the last reader of its previous contents.
+// The diagonal inverse is one latency-bound CTA on the critical path; it asks
+// for (and leaves unused) enough dynamic shared memory that no other CTA of
+// the factorisation fits beside it on its SM.
+constexpr int GJ_DIAG_EXCL_SMEM = 188 * 1024;
+
 int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
 {
+    static bool diag_attr = false;
+    if (!diag_attr) {
+        cudaFuncSetAttribute(k_gj_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             GJ_DIAG_EXCL_SMEM);
+        diag_attr = true;
+    }
     const int64_t n = c.n;
     cudaMemsetAsync(c.d_info, 0, sizeof(int32_t), c.stream);
     const unsigned gcols = (unsigned)ceil_div(n, GJ_NB);
     float *dinv[2] = {c.d_gj_dinv, c.d_gj_dinv + GJ_NB * GJ_NB};
+    float *rt[2] = {c.d_gj_rt, c.d_gj_rt + (size_t)GJ_NB * c.lda};
+    float *cb[2] = {c.d_gj_cb, c.d_gj_cb + (size_t)GJ_NB * c.lda};
+    float *stg[2] = {c.d_gj_stage, c.d_gj_stage + 2 * GJ_NB * GJ_NB};
     c.tbeg(PH_LU_DIAG);
-    k_gj_diag<<<1, 256, 0, c.stream>>>(n, M, lda, 0, dinv[0], c.d_info, nullptr, nullptr);
+    k_gj_diag<<<1, 256, GJ_DIAG_EXCL_SMEM, c.stream>>>(n, M, lda, 0, dinv[0], c.d_info, nullptr, nullptr);
     c.tend(PH_LU_DIAG);
+    cudaEventRecord(c.ev_upd, c.stream);
     c.launches += 1;
     int kstep = 0;
     for (int64_t k0 = 0; k0 < n; k0 += GJ_NB, ++kstep) {
-        float *dk = dinv[kstep & 1];
+        const int b = kstep & 1;
         const int64_t k1 = k0 + GJ_NB;
         const bool next = k1 < n;
-        c.tbeg(PH_LU_PANEL);
-        k_gj_prep<<<dim3(gcols, 2), 256, 0, c.stream>>>(n, M, lda, k0, dk, c.d_gj_rt, c.d_gj_cb);
-        c.tend(PH_LU_PANEL);
         if (next) {
-            cudaEventRecord(c.ev_prep, c.stream);
-            cudaStreamWaitEvent(c.stream2, c.ev_prep, 0);
+            cudaStreamWaitEvent(c.stream2, c.ev_upd, 0);
+            if (kstep > 0) cudaStreamWaitEvent(c.stream2, c.ev_fin[b ^ 1], 0);
             c.tbeg(PH_LU_DIAG, c.stream2);
-            k_gj_diag<<<1, 256, 0, c.stream2>>>(n, M, lda, k1, dinv[(kstep + 1) & 1], c.d_info,
-                                                 c.d_gj_cb, c.d_gj_rt);
+            k_gj_diag<<<1, 256, GJ_DIAG_EXCL_SMEM, c.stream2>>>(n, M, lda, k1, dinv[b ^ 1], c.d_info, dinv[b],
+                                                stg[b ^ 1]);
             c.tend(PH_LU_DIAG, c.stream2);
             cudaEventRecord(c.ev_diag, c.stream2);
             c.launches += 1;
         }
+        c.tbeg(PH_LU_PANEL);
+        k_gj_prep<<<dim3(gcols, 2), 256, 0, c.stream>>>(n, M, lda, k0, dinv[b], rt[b], cb[b],
+                                                        kstep > 0 ? stg[b] : nullptr);
+        c.tend(PH_LU_PANEL);
+        cudaEventRecord(c.ev_fin_ready, c.stream);
+        cudaStreamWaitEvent(c.stream4, c.ev_fin_ready, 0);
+        c.tbeg(PH_LU_PANEL, c.stream4);
+        k_gj_finish<<<dim3(gcols, 2), 256, 0, c.stream4>>>(n, M, lda, k0, dinv[b], rt[b], cb[b],
+                                                           next ? k1 : -1);
+        c.tend(PH_LU_PANEL, c.stream4);
+        cudaEventRecord(c.ev_fin[b], c.stream4);
+        if (kstep > 0) cudaStreamWaitEvent(c.stream, c.ev_fin[b ^ 1], 0);
         const int64_t skip0 = next ? k1 : -GJ_NB;
         c.tbeg(PH_LU_UPDATE);
         bool done = false;
         if (prec == NRS_TF32 || prec == NRS_BF16)
-            done = launch_tc_gj_update(c, M, lda, k0, c.d_gj_cb, c.d_gj_rt, prec, skip0);
+            done = launch_tc_gj_update(c, M, lda, k0, cb[b], rt[b], prec, skip0);
         if (!done)
-            k_gj_update_simt<<<dim3(gcols, gcols), 256, 0, c.stream>>>(n, M, lda, k0, c.d_gj_cb,
-                                                                        c.d_gj_rt, skip0);
+            k_gj_update_simt<<<dim3(gcols, gcols), 256, 0, c.stream>>>(n, M, lda, k0, cb[b], rt[b],
+                                                                        skip0);
         c.tend(PH_LU_UPDATE);
-        c.tbeg(PH_LU_PANEL);
-        k_gj_finish<<<dim3(gcols, 2), 256, 0, c.stream>>>(n, M, lda, k0, dk, c.d_gj_rt, c.d_gj_cb);
-        c.tend(PH_LU_PANEL);
+        cudaEventRecord(c.ev_upd, c.stream);
         if (next) cudaStreamWaitEvent(c.stream, c.ev_diag, 0);
+        else cudaStreamWaitEvent(c.stream, c.ev_fin[b], 0);
         c.launches += 3;
     }
     return 0;

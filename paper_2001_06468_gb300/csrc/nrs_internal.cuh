@@ -82,7 +82,7 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec);
 
 bool tc_available();
 bool launch_tc_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb, const float *Rt,
-                      int prec, int64_t skip0);
+                      int prec, int64_t skip0, int64_t kblk);
 void launch_simt_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb, const float *Rt);
 
 // ---- solve (solve.cu) ------------------------------------------------------
@@ -130,7 +130,9 @@ struct Ctx {
     cudaEvent_t ev_asm = nullptr, ev_asm_done = nullptr;
     bool asm_pending = false;                    // stream3 holds an FP64 assembly not yet joined
     int lo_eval = 0;  // FP32 copy for the factor: 0 evaluated in FP32 (overlapped), 1 rounded FP64
-    cudaEvent_t ev_prep = nullptr, ev_diag = nullptr;
+    cudaEvent_t ev_upd = nullptr, ev_diag = nullptr;
+    cudaStream_t stream4 = nullptr;              // finish step of the factorisation
+    cudaEvent_t ev_fin_ready = nullptr, ev_fin[2] = {nullptr, nullptr};
     int num_sms = 0;
     std::string err;
 
@@ -175,8 +177,9 @@ struct Ctx {
     int32_t *d_lperm = nullptr;    // row exchange of the current diagonal block
     bool a32_fresh = false;        // d_A32 holds the last assembly (not yet factored)
     float *d_gj_dinv = nullptr;    // Gauss-Jordan workspaces: D^{-1} (64 x 64)
-    float *d_gj_rt = nullptr;      //   scaled block row, transposed (n x 64)
-    float *d_gj_cb = nullptr;      //   block column (n x 64)
+    float *d_gj_rt = nullptr;      //   scaled block row, transposed (2 buffers of n x 64)
+    float *d_gj_cb = nullptr;      //   block column (2 buffers of n x 64)
+    float *d_gj_stage = nullptr;   //   two finished 64 x 64 tiles (2 buffers)
     int32_t *d_info = nullptr;
     int factored_prec = -1;
     bool assembled = false;

@@ -149,7 +149,8 @@ __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo)
 
 __global__ void __launch_bounds__(128, 1)
     k_tc_gj_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   int64_t n, float *__restrict__ M, int64_t lda, int32_t *status, int64_t skip0)
+                   int64_t n, float *__restrict__ M, int64_t lda, int32_t *status, int64_t skip0,
+                   int64_t kblk)
 {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bar_load[2], bar_mma[2];
@@ -254,6 +255,9 @@ __global__ void __launch_bounds__(128, 1)
         const int64_t row = row0 + warp * 32 + lane;
         // the 64 x 64 block at (skip0, skip0) is updated separately (lookahead)
         const bool row_skip = row >= skip0 && row < skip0 + 64;
+        // block row and column kblk are written by the finish step, which may
+        // run concurrently (C R is zero there): this kernel leaves them alone
+        const bool row_k = row >= kblk && row < kblk + 64;
         // software-pipelined read-modify-write of this thread's row: the loads
         // of chunk c + 1 are issued before chunk c is subtracted and stored
         float cur[16], nxt[16];
@@ -270,7 +274,7 @@ __global__ void __launch_bounds__(128, 1)
             }
             uint32_t v[16];
             tmem_ld_16cols(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(chunk * 16), v);
-            if (row < n) {
+            if (row < n && !row_k && !(cbeg >= kblk && cbeg < kblk + 64)) {
                 float *p = M + row + cbeg * lda;
                 const int64_t ncol = n - cbeg;
 #pragma unroll
@@ -348,7 +352,7 @@ bool tc_available()
 }
 
 bool launch_tc_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb, const float *Rt,
-                      int prec, int64_t skip0)
+                      int prec, int64_t skip0, int64_t kblk)
 {
     if (prec != NRS_TF32) return false;
     CUtensorMap a, b;
@@ -359,7 +363,7 @@ bool launch_tc_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb,
         attr = true;
     }
     dim3 grid((unsigned)ceil_div(n, TC_BM), (unsigned)ceil_div(n, TC_BN));
-    k_tc_gj_update<<<grid, 128, TC_SMEM, c.stream>>>(a, b, n, M, lda, c.d_status, skip0);
+    k_tc_gj_update<<<grid, 128, TC_SMEM, c.stream>>>(a, b, n, M, lda, c.d_status, skip0, kblk);
     c.launches += 1;
     return true;
 }
@@ -367,8 +371,7 @@ bool launch_tc_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb,
 bool launch_tc_gj_update(Ctx &c, float *M, int64_t lda, int64_t k0, const float *Cb,
                          const float *Rt, int prec, int64_t skip0)
 {
-    (void)k0;
-    return launch_tc_rank64(c, M, lda, c.n, Cb, Rt, prec, skip0);
+    return launch_tc_rank64(c, M, lda, c.n, Cb, Rt, prec, skip0, k0);
 }
 
 }  // namespace nrs

@@ -37,7 +37,7 @@ FREE, PRESCRIBED, STATIC = 0, 1, 2
 EXPORTS = ["nrs_create", "nrs_destroy", "nrs_last_error", "nrs_sizes", "nrs_set_state",
            "nrs_get_state", "nrs_set_external", "nrs_kinematics", "nrs_nearest_build",
            "nrs_assemble", "nrs_factor", "nrs_solve", "nrs_step", "nrs_sync", "nrs_set_timing",
-           "nrs_get_timing", "nrs_rank64_update", "nrs_nearest_build_static",
+           "nrs_get_timing", "nrs_get_trace", "nrs_rank64_update", "nrs_nearest_build_static",
            "nrs_mlp_set_params", "nrs_mlp_get_params", "nrs_mlp_config", "nrs_mlp_eval",
            "nrs_mlp_adam", "nrs_mlp_features", "nrs_mlp_start",
            "nrs_batch_create", "nrs_batch_destroy", "nrs_batch_last_error", "nrs_batch_context",
@@ -120,6 +120,9 @@ _sig = {
     "nrs_nearest_build_static": (ctypes.c_int, [_P, _P, ctypes.c_int32, _I64P, _I64P, ctypes.c_int32,
                                                 _P, _P, _P, _P]),
     "nrs_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), _I64P, _I64P]),
+    "nrs_get_trace": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.c_int64, _I64P]),
     "nrs_mlp_set_params": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32]),
     "nrs_mlp_get_params": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int32), _P]),
     "nrs_mlp_config": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _P]),
@@ -388,6 +391,18 @@ class Context:
 
     def set_timing(self, enable: bool = True):
         self._check(_lib.nrs_set_timing(self._h, int(bool(enable))))
+
+    def get_trace(self):
+        """[(phase, begin_ms, end_ms)] of the spans timed since timing was
+        enabled, in recording order; call before get_timing (which clears)."""
+        cnt = ctypes.c_int64()
+        self._check(_lib.nrs_get_trace(self._h, None, None, None, 0, ctypes.byref(cnt)))
+        m = cnt.value
+        ph = (ctypes.c_int32 * max(m, 1))()
+        t0 = (ctypes.c_double * max(m, 1))()
+        t1 = (ctypes.c_double * max(m, 1))()
+        self._check(_lib.nrs_get_trace(self._h, ph, t0, t1, m, ctypes.byref(cnt)))
+        return [(PHASES[ph[i]], t0[i], t1[i]) for i in range(min(m, cnt.value))]
 
     def get_timing(self):
         """{phase: (ms, spans)} since timing was enabled, and the kernel count."""
