@@ -218,6 +218,14 @@ void launch_assemble(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t l
 {
     const bool side = s != nullptr;
     s = side ? s : c.stream;
+    static bool attr = false;
+    if (!attr) {
+        // beside the factorisation, whose diagonal inverse needs a large
+        // shared-memory carveout on the SM it lands on
+        cudaFuncSetAttribute(k_assemble64, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        attr = true;
+    }
     const int64_t gx = ceil_div(c.N, AS_THREADS), tiles = gx * ceil_div(c.N, AS_NT);
     // beside the factorisation: one CTA of four warps per SM, grid-stride over the
     // tiles, so the factorisation's kernels keep most of every SM

@@ -523,8 +523,12 @@ void launch_simt_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *C
 // is ordered after the last reader of its previous contents.
 // The diagonal inverse is one latency-bound CTA on the critical path; it asks
 // for (and leaves unused) enough dynamic shared memory that no other CTA of
-// the factorisation fits beside it on its SM.
-constexpr int GJ_DIAG_EXCL_SMEM = 188 * 1024;
+// the factorisation (prep and finish 35 KB, update 66.5 KB) fits beside it on
+// its SM, while one CTA of the FP64 assembly (16.5 KB) that may run beside the
+// factorisation still does.  Every kernel that runs beside it prefers the
+// largest shared-memory carveout, so that an SM running one of them can
+// still take the diagonal inverse.
+constexpr int GJ_DIAG_EXCL_SMEM = 164 * 1024;
 
 int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
 {
@@ -532,6 +536,11 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
     if (!diag_attr) {
         cudaFuncSetAttribute(k_gj_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              GJ_DIAG_EXCL_SMEM);
+        const void *fns[] = {(const void *)k_gj_diag, (const void *)k_gj_prep,
+                             (const void *)k_gj_finish, (const void *)k_gj_update_simt};
+        for (const void *f : fns)
+            cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
         diag_attr = true;
     }
     const int64_t n = c.n;

@@ -360,6 +360,8 @@ bool launch_tc_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb,
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_tc_gj_update, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        cudaFuncSetAttribute(k_tc_gj_update, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
         attr = true;
     }
     dim3 grid((unsigned)ceil_div(n, TC_BM), (unsigned)ceil_div(n, TC_BN));
