@@ -202,10 +202,14 @@ __global__ void __launch_bounds__(256)
     bool used = false;
     float scale = 1.0f;
     int mypos = 0;
+    unsigned zero_at = 0xffffffffu;  // step of a zero pivot in this row, if any
 #pragma unroll 4
     for (int c = 0; c < NB; ++c) {
         const int b = c & 1;
         const float colv = T[0];
+        // the reciprocal is formed before the search, so that the winner can
+        // publish it with its row and nobody divides after the barrier
+        const float myr = 1.0f / colv;
         const unsigned key = used ? 0u : (0x80000000u | __float_as_uint(fabsf(colv)));
         const unsigned mx = __reduce_max_sync(0xffffffffu, key);
         const int best = (int)__reduce_min_sync(0xffffffffu, key == mx ? (unsigned)r : 255u);
@@ -215,7 +219,7 @@ __global__ void __launch_bounds__(256)
             for (int q = 0; q < NB / 4; ++q)
                 dst[q] = make_float4(T[4 * q], T[4 * q + 1], T[4 * q + 2], T[4 * q + 3]);
             ckey[b][w] = mx;
-            cpiv[b][w] = colv;
+            cpiv[b][w] = myr;
             crow[b][w] = best;
         }
         asm volatile("bar.sync 1, 64;" ::: "memory");
@@ -223,18 +227,14 @@ __global__ void __launch_bounds__(256)
         const float pv0 = cpiv[b][0], pv1 = cpiv[b][1];
         const int rw0 = crow[b][0], rw1 = crow[b][1];
         const int win = kw0 >= kw1 ? 0 : 1;  // warp 0 (the lower rows) on ties
-        const float piv = win ? pv1 : pv0;
+        const float rpiv = win ? pv1 : pv0;
         const int p = win ? rw1 : rw0;
-        const float rpiv = 1.0f / piv;
         const bool is_piv = (r == p);
         if (is_piv) {
             used = true;
             scale = rpiv;
             mypos = c;
-        }
-        if (tid == 0) {
-            pivrow[c] = p;
-            if (piv == 0.0f && info) atomicCAS(info, 0, (int)(k0 + c + 1));
+            if (colv == 0.0f) zero_at = (unsigned)c;
         }
         const float f = is_piv ? 0.0f : colv * rpiv;
         const float newc = is_piv ? 1.0f : -f;
@@ -251,7 +251,16 @@ __global__ void __launch_bounds__(256)
         for (int j = 0; j < NB - 1; ++j) T[j] = T[j + 1];
         T[NB - 1] = newc;
     }
+    // the pivot order (row pivoted at step c) and the first zero pivot, from
+    // the rows' own records: no per-step bookkeeping in the loop
+    pivrow[mypos] = r;
+    zero_at = __reduce_min_sync(0xffffffffu, zero_at);
+    if ((tid & 31) == 0) crow[0][w] = (int)zero_at;
     asm volatile("bar.sync 1, 64;" ::: "memory");  // pivrow complete
+    if (tid == 0 && info) {
+        const unsigned z = min((unsigned)crow[0][0], (unsigned)crow[0][1]);
+        if (z != 0xffffffffu) atomicCAS(info, 0, (int)(k0 + z + 1));
+    }
     // row mypos of D^{-1}, column pivrow[d] = T[d] * scale: through shared
     // memory (B0, read into the registers before the loop) so that the global
     // stores are coalesced
