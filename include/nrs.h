@@ -118,6 +118,13 @@ typedef struct {
                               NRS_EINVAL); the learned start and phase timing run the step
                               without the graph.  backward_err is reported as computed in the
                               graph. */
+    int32_t factor_schedule; /* FP32/TF32 factorisation (Gauss-Jordan explicit inverse):
+                              0 = separate kernels on three streams (the chain of diagonal
+                              inverses on one of them); 1 = with TF32 on a device with tensor
+                              memory, the whole inversion as ONE cooperative launch taking
+                              every SM (the chain of diagonal inverses on one CTA, the updates
+                              on the others, hand-offs by counters in global memory), else as
+                              0.  Both give the same result bit for bit. */
 } nrs_problem_desc;
 
 typedef struct {

@@ -29,6 +29,11 @@ namespace nrs {
 constexpr int AS_THREADS = 128;
 constexpr int AS_NT = 16;
 constexpr int AS_CHUNK = 512;
+// the FP64 kernel runs beside the fused factorisation, whose CTA takes about
+// 195 KB of an SM's shared memory: its staging chunk is kept at 8 KB so that
+// up to three of its CTAs still fit beside one (the order of the sums over q
+// does not depend on the chunk)
+constexpr int AS64_CHUNK = 256;
 
 struct Acc7 {
     double xx, xy, xz, yy, yz, zz, d;
@@ -61,7 +66,7 @@ __global__ void __launch_bounds__(AS_THREADS)
                  double *__restrict__ A64, float *__restrict__ A32, int64_t lda, int64_t gx,
                  int64_t tiles)
 {
-    __shared__ D4 sX[AS_CHUNK];
+    __shared__ D4 sX[AS64_CHUNK];
     __shared__ int32_t sp[AS_NT + 1];
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     __syncthreads();  // the previous tile is done with sp and sX
@@ -82,8 +87,8 @@ __global__ void __launch_bounds__(AS_THREADS)
     __syncthreads();
     int cur = 0;
     const int32_t qbeg = sp[0], qend = sp[nt];
-    for (int32_t c0 = qbeg; c0 < qend; c0 += AS_CHUNK) {
-        const int cnt = min(AS_CHUNK, qend - c0);
+    for (int32_t c0 = qbeg; c0 < qend; c0 += AS64_CHUNK) {
+        const int cnt = min(AS64_CHUNK, qend - c0);
         __syncthreads();
         for (int i = threadIdx.x; i < cnt; i += AS_THREADS) sX[i] = Xs[c0 + i];
         __syncthreads();

@@ -273,7 +273,12 @@ nrs_status nrs_batch_create(nrs_batch **out, const nrs_problem_desc *descs, int3
         d.graph = 0;
         nrs_ctx *h = nullptr;
         st = nrs_create(&h, &d, s);
-        if (st == NRS_OK) b->ctx.push_back(reinterpret_cast<Ctx *>(h));
+        if (st == NRS_OK) {
+            b->ctx.push_back(reinterpret_cast<Ctx *>(h));
+            // the problems of a batch run side by side: the fused factorisation
+            // (which takes every SM) would serialise them
+            b->ctx.back()->gj_fused = false;
+        }
     }
     if (e != cudaSuccess && st == NRS_OK) st = NRS_ECUDA;
     if (st == NRS_OK) {

@@ -15,7 +15,7 @@
 // kernel of tc_gemm.cu when available -- and applying the preconditioner is
 // one bandwidth-bound matrix-vector product instead of a chain of dependent
 // triangular solves.
-#include "nrs_internal.cuh"
+#include "tc_prims.cuh"
 
 namespace nrs {
 
@@ -55,15 +55,17 @@ constexpr int GJ_NB = 64;
 //    barrier of the step, and every lane reads the winner's row from there.
 // Padding rows/columns (kb < 64) are identity.  Dinv is row-major 64 x 64; a
 // zero pivot records info.
-__global__ void __launch_bounds__(256)
-    k_gj_diag(int64_t n, const float *__restrict__ M, int64_t lda, int64_t k0,
-              float *__restrict__ Dinv, int32_t *__restrict__ info,
-              const float *__restrict__ Dprev, float *__restrict__ stage)
+// All 256 threads of the CTA enter and leave together.  Every read of data
+// that other CTAs write is an L2 load (ld.global.cg), so the same code runs
+// inside the fused factorisation.  sraw: two 64 x 68 float buffers in shared
+// memory.
+__device__ __forceinline__ void gj_diag_block(int64_t n, const float *M, int64_t lda,
+                                              int64_t k0, float *Dinv, int32_t *info,
+                                              const float *Dprev, float *stage, float *sraw)
 {
     constexpr int NB = GJ_NB, LDT = NB + 4;
     // two 64 x 68 buffers: B0 = Dprev^T, then R_PK, then the block D (rows of
     // 65 floats), then the output; B1 = M[P,K], then M[K,P]^T
-    __shared__ __align__(16) float sraw[2 * NB * LDT];
     float(*B0)[LDT] = reinterpret_cast<float(*)[LDT]>(sraw);
     float(*B1)[LDT] = reinterpret_cast<float(*)[LDT]>(sraw + NB * LDT);
     float(*sm0)[NB + 1] = reinterpret_cast<float(*)[NB + 1]>(sraw);
@@ -83,7 +85,7 @@ __global__ void __launch_bounds__(256)
         for (int jj = 0; jj < 4; ++jj) {
             const int j = j0 + jj;
             if (r0 + 3 < kb && j < kb) {
-                const float4 v = *reinterpret_cast<const float4 *>(M + (k0 + r0) + (k0 + j) * lda);
+                const float4 v = __ldcg(reinterpret_cast<const float4 *>(M + (k0 + r0) + (k0 + j) * lda));
                 L[0][jj] = v.x;
                 L[1][jj] = v.y;
                 L[2][jj] = v.z;
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
                 for (int ii = 0; ii < 4; ++ii) {
                     const int r = r0 + ii;
-                    L[ii][jj] = (r < kb && j < kb) ? M[(k0 + r) + (k0 + j) * lda]
+                    L[ii][jj] = (r < kb && j < kb) ? __ldcg(M + (k0 + r) + (k0 + j) * lda)
                                                    : (r == j ? 1.0f : 0.0f);
                 }
             }
@@ -102,9 +104,9 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
-                dv[q] = Dprev[b * NB + a];                                        // Dprev[b][a]
-                mv[q] = b < kb ? M[(kp + a) + (k0 + b) * lda] : 0.0f;            // M[P+a][K+b]
-                cv[q] = a < kb ? M[(k0 + a) + (kp + b) * lda] : 0.0f;            // M[K+a][P+b]
+                dv[q] = __ldcg(Dprev + b * NB + a);                              // Dprev[b][a]
+                mv[q] = b < kb ? __ldcg(M + (kp + a) + (k0 + b) * lda) : 0.0f;  // M[P+a][K+b]
+                cv[q] = a < kb ? __ldcg(M + (k0 + a) + (kp + b) * lda) : 0.0f;  // M[K+a][P+b]
             }
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
@@ -173,101 +175,111 @@ __global__ void __launch_bounds__(256)
         // use): stage[4096 + i + 64 c] = -sum_t M[K+i][P+t] Dprev[t][c] on a
         // 4 x 8 tile per thread (M[K,P] transposed in B1, Dprev from global)
         const int wq = tid >> 5;
-        if (!Dprev || wq == 4 || wq == 5) return;
-        const int u = wq < 4 ? tid - 64 : tid - 128, i0 = 4 * (u & 15), c0 = 8 * (u >> 4);
-        float acc[4][8] = {};
+        if (Dprev && wq != 4 && wq != 5) {
+            const int u = wq < 4 ? tid - 64 : tid - 128, i0 = 4 * (u & 15), c0 = 8 * (u >> 4);
+            float acc[4][8] = {};
 #pragma unroll 4
-        for (int t = 0; t < NB; ++t) {
-            const float4 a4 = *reinterpret_cast<const float4 *>(&B1[t][i0]);
-            const float4 d0 = __ldg(reinterpret_cast<const float4 *>(Dprev + t * NB + c0));
-            const float4 d1 = __ldg(reinterpret_cast<const float4 *>(Dprev + t * NB + c0 + 4));
-            const float x4[4] = {a4.x, a4.y, a4.z, a4.w};
-            const float y8[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+            for (int t = 0; t < NB; ++t) {
+                const float4 a4 = *reinterpret_cast<const float4 *>(&B1[t][i0]);
+                const float4 d0 = __ldcg(reinterpret_cast<const float4 *>(Dprev + t * NB + c0));
+                const float4 d1 = __ldcg(reinterpret_cast<const float4 *>(Dprev + t * NB + c0 + 4));
+                const float x4[4] = {a4.x, a4.y, a4.z, a4.w};
+                const float y8[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
+                for (int x = 0; x < 4; ++x)
 #pragma unroll
-                for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(x4[x], y8[y], acc[x][y]);
+                    for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(x4[x], y8[y], acc[x][y]);
+            }
+            float *stx = stage + NB * NB;
+#pragma unroll
+            for (int y = 0; y < 8; ++y)
+                *reinterpret_cast<float4 *>(&stx[i0 + (c0 + y) * NB]) =
+                    make_float4(-acc[0][y], -acc[1][y], -acc[2][y], -acc[3][y]);
         }
-        float *stx = stage + NB * NB;
+    } else {
+        const int w = tid >> 5, r = tid;
+        float T[NB];
 #pragma unroll
-        for (int y = 0; y < 8; ++y)
-            *reinterpret_cast<float4 *>(&stx[i0 + (c0 + y) * NB]) =
-                make_float4(-acc[0][y], -acc[1][y], -acc[2][y], -acc[3][y]);
-        return;
-    }
-    const int w = tid >> 5, r = tid;
-    float T[NB];
-#pragma unroll
-    for (int j = 0; j < NB; ++j) T[j] = sm0[r][j];
-    bool used = false;
-    float scale = 1.0f;
-    int mypos = 0;
-    unsigned zero_at = 0xffffffffu;  // step of a zero pivot in this row, if any
+        for (int j = 0; j < NB; ++j) T[j] = sm0[r][j];
+        bool used = false;
+        float scale = 1.0f;
+        int mypos = 0;
+        unsigned zero_at = 0xffffffffu;  // step of a zero pivot in this row, if any
 #pragma unroll 4
-    for (int c = 0; c < NB; ++c) {
-        const int b = c & 1;
-        const float colv = T[0];
-        // the reciprocal is formed before the search, so that the winner can
-        // publish it with its row and nobody divides after the barrier
-        const float myr = 1.0f / colv;
-        const unsigned key = used ? 0u : (0x80000000u | __float_as_uint(fabsf(colv)));
-        const unsigned mx = __reduce_max_sync(0xffffffffu, key);
-        const int best = (int)__reduce_min_sync(0xffffffffu, key == mx ? (unsigned)r : 255u);
-        if (r == best) {
-            float4 *dst = reinterpret_cast<float4 *>(&cand[b][w][0]);
+        for (int c = 0; c < NB; ++c) {
+            const int b = c & 1;
+            const float colv = T[0];
+            // the reciprocal is formed before the search, so that the winner can
+            // publish it with its row and nobody divides after the barrier
+            const float myr = 1.0f / colv;
+            const unsigned key = used ? 0u : (0x80000000u | __float_as_uint(fabsf(colv)));
+            const unsigned mx = __reduce_max_sync(0xffffffffu, key);
+            const int best = (int)__reduce_min_sync(0xffffffffu, key == mx ? (unsigned)r : 255u);
+            if (r == best) {
+                float4 *dst = reinterpret_cast<float4 *>(&cand[b][w][0]);
 #pragma unroll
-            for (int q = 0; q < NB / 4; ++q)
-                dst[q] = make_float4(T[4 * q], T[4 * q + 1], T[4 * q + 2], T[4 * q + 3]);
-            ckey[b][w] = mx;
-            cpiv[b][w] = myr;
-            crow[b][w] = best;
+                for (int q = 0; q < NB / 4; ++q)
+                    dst[q] = make_float4(T[4 * q], T[4 * q + 1], T[4 * q + 2], T[4 * q + 3]);
+                ckey[b][w] = mx;
+                cpiv[b][w] = myr;
+                crow[b][w] = best;
+            }
+            asm volatile("bar.sync 1, 64;" ::: "memory");
+            const unsigned kw0 = ckey[b][0], kw1 = ckey[b][1];
+            const float pv0 = cpiv[b][0], pv1 = cpiv[b][1];
+            const int rw0 = crow[b][0], rw1 = crow[b][1];
+            const int win = kw0 >= kw1 ? 0 : 1;  // warp 0 (the lower rows) on ties
+            const float rpiv = win ? pv1 : pv0;
+            const int p = win ? rw1 : rw0;
+            const bool is_piv = (r == p);
+            if (is_piv) {
+                used = true;
+                scale = rpiv;
+                mypos = c;
+                if (colv == 0.0f) zero_at = (unsigned)c;
+            }
+            const float f = is_piv ? 0.0f : colv * rpiv;
+            const float newc = is_piv ? 1.0f : -f;
+            const float4 *pr4 = reinterpret_cast<const float4 *>(&cand[b][win][0]);
+#pragma unroll
+            for (int q = 0; q < NB / 4; ++q) {
+                const float4 v = pr4[q];
+                if (q > 0) T[4 * q] = fmaf(-f, v.x, T[4 * q]);
+                T[4 * q + 1] = fmaf(-f, v.y, T[4 * q + 1]);
+                T[4 * q + 2] = fmaf(-f, v.z, T[4 * q + 2]);
+                T[4 * q + 3] = fmaf(-f, v.w, T[4 * q + 3]);
+            }
+#pragma unroll
+            for (int j = 0; j < NB - 1; ++j) T[j] = T[j + 1];
+            T[NB - 1] = newc;
         }
+        // the pivot order (row pivoted at step c) and the first zero pivot, from
+        // the rows' own records: no per-step bookkeeping in the loop
+        pivrow[mypos] = r;
+        zero_at = __reduce_min_sync(0xffffffffu, zero_at);
+        if ((tid & 31) == 0) crow[0][w] = (int)zero_at;
+        asm volatile("bar.sync 1, 64;" ::: "memory");  // pivrow complete
+        if (tid == 0 && info) {
+            const unsigned z = min((unsigned)crow[0][0], (unsigned)crow[0][1]);
+            if (z != 0xffffffffu) atomicCAS(info, 0, (int)(k0 + z + 1));
+        }
+        // row mypos of D^{-1}, column pivrow[d] = T[d] * scale: through shared
+        // memory (B0, read into the registers before the loop) so that the global
+        // stores are coalesced
+#pragma unroll
+        for (int d = 0; d < NB; ++d) sm0[mypos][pivrow[d]] = T[d] * scale;
         asm volatile("bar.sync 1, 64;" ::: "memory");
-        const unsigned kw0 = ckey[b][0], kw1 = ckey[b][1];
-        const float pv0 = cpiv[b][0], pv1 = cpiv[b][1];
-        const int rw0 = crow[b][0], rw1 = crow[b][1];
-        const int win = kw0 >= kw1 ? 0 : 1;  // warp 0 (the lower rows) on ties
-        const float rpiv = win ? pv1 : pv0;
-        const int p = win ? rw1 : rw0;
-        const bool is_piv = (r == p);
-        if (is_piv) {
-            used = true;
-            scale = rpiv;
-            mypos = c;
-            if (colv == 0.0f) zero_at = (unsigned)c;
-        }
-        const float f = is_piv ? 0.0f : colv * rpiv;
-        const float newc = is_piv ? 1.0f : -f;
-        const float4 *pr4 = reinterpret_cast<const float4 *>(&cand[b][win][0]);
-#pragma unroll
-        for (int q = 0; q < NB / 4; ++q) {
-            const float4 v = pr4[q];
-            if (q > 0) T[4 * q] = fmaf(-f, v.x, T[4 * q]);
-            T[4 * q + 1] = fmaf(-f, v.y, T[4 * q + 1]);
-            T[4 * q + 2] = fmaf(-f, v.z, T[4 * q + 2]);
-            T[4 * q + 3] = fmaf(-f, v.w, T[4 * q + 3]);
-        }
-#pragma unroll
-        for (int j = 0; j < NB - 1; ++j) T[j] = T[j + 1];
-        T[NB - 1] = newc;
+        for (int i = 0; i < NB; ++i) Dinv[i * NB + tid] = sm0[i][tid];
     }
-    // the pivot order (row pivoted at step c) and the first zero pivot, from
-    // the rows' own records: no per-step bookkeeping in the loop
-    pivrow[mypos] = r;
-    zero_at = __reduce_min_sync(0xffffffffu, zero_at);
-    if ((tid & 31) == 0) crow[0][w] = (int)zero_at;
-    asm volatile("bar.sync 1, 64;" ::: "memory");  // pivrow complete
-    if (tid == 0 && info) {
-        const unsigned z = min((unsigned)crow[0][0], (unsigned)crow[0][1]);
-        if (z != 0xffffffffu) atomicCAS(info, 0, (int)(k0 + z + 1));
-    }
-    // row mypos of D^{-1}, column pivrow[d] = T[d] * scale: through shared
-    // memory (B0, read into the registers before the loop) so that the global
-    // stores are coalesced
-#pragma unroll
-    for (int d = 0; d < NB; ++d) sm0[mypos][pivrow[d]] = T[d] * scale;
-    asm volatile("bar.sync 1, 64;" ::: "memory");
-    for (int i = 0; i < NB; ++i) Dinv[i * NB + tid] = sm0[i][tid];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256)
+    k_gj_diag(int64_t n, const float *M, int64_t lda, int64_t k0, float *Dinv, int32_t *info,
+              const float *Dprev, float *stage)
+{
+    __shared__ __align__(16) float sraw[2 * GJ_NB * (GJ_NB + 4)];
+    gj_diag_block(n, M, lda, k0, Dinv, info, Dprev, stage, sraw);
 }
 
 // Prep of step K.  grid.y = 0: R[:, j] = D^{-1} M[K, j] for one 64-column tile
@@ -277,21 +289,24 @@ __global__ void __launch_bounds__(256)
 // With `stage` given (K > 0), the tiles M[K-1,K] and M[K,K-1] as left by step
 // K-1 are read from there (the diagonal inverse of this step wrote them; the
 // finish of step K-1 skips them in M).
-__global__ void __launch_bounds__(256)
-    k_gj_prep(int64_t n, const float *__restrict__ M, int64_t lda, int64_t k0,
-              const float *__restrict__ Dinv, float *__restrict__ Rt, float *__restrict__ Cb,
-              const float *__restrict__ stage)
+// One tile (t0, y) of the prep; sbuf: two 64 x 68 float buffers in shared
+// memory.  Ends with every thread past its last shared-memory access.  With
+// Rt_lo / Cb_lo given, the panels are stored split for the tensor cores:
+// Rt = TF32 rounding of R (cvt.rna) and Rt_lo = the rest, which is exact, so
+// that Rt + Rt_lo = R (the same for C).
+__device__ __forceinline__ void gj_prep_tile(int64_t n, const float *M, int64_t lda, int64_t k0,
+                                             const float *Dinv, float *Rt, float *Cb,
+                                             const float *stage, int64_t t0, int y, float *sbuf,
+                                             float *Rt_lo = nullptr, float *Cb_lo = nullptr)
 {
     constexpr int NB = GJ_NB;
-    __shared__ __align__(16) float Ds[NB][NB + 4];
-    __shared__ __align__(16) float Ms[NB][NB + 4];
+    float(*Ds)[NB + 4] = reinterpret_cast<float(*)[NB + 4]>(sbuf);
+    float(*Ms)[NB + 4] = reinterpret_cast<float(*)[NB + 4]>(sbuf + NB * (NB + 4));
     const int tid = threadIdx.x;
     const int kb = (int)min((int64_t)NB, n - k0);
-    const int64_t t0 = (int64_t)blockIdx.x * NB;
-    if (t0 >= n) return;
     const int nt = (int)min((int64_t)NB, n - t0);
     const bool staged = stage && t0 == k0 - NB;
-    if (blockIdx.y == 1) {
+    if (y == 1) {
         const bool in_k = (t0 == k0);
         // M[t0 + i][K + c], or column-major 64 x 64 in stage for the tile above
         const float *src = staged ? stage : M + t0 + k0 * lda;
@@ -300,7 +315,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const int idx = tid + 256 * q, i = idx & 63, c = idx >> 6;
-            v[q] = (i < nt && c < kb && !in_k) ? src[i + c * ld] : 0.0f;
+            v[q] = (i < nt && c < kb && !in_k) ? __ldcg(src + i + c * ld) : 0.0f;
         }
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
@@ -310,14 +325,24 @@ __global__ void __launch_bounds__(256)
         __syncthreads();
         for (int idx = tid; idx < NB * NB; idx += 256) {
             const int c = idx & 63, i = idx >> 6;
-            if (i < nt) Cb[(t0 + i) * NB + c] = Ms[i][c];
+            if (i < nt) {
+                if (Cb_lo) {
+                    float h, l;
+                    tcp::split_tf32(Ms[i][c], h, l);
+                    Cb[(t0 + i) * NB + c] = h;
+                    Cb_lo[(t0 + i) * NB + c] = l;
+                } else {
+                    Cb[(t0 + i) * NB + c] = Ms[i][c];
+                }
+            }
         }
+        __syncthreads();
         return;
     }
     const bool tile_is_k = (t0 == k0);
     // D^{-1} transposed and the block row, rows of 68 floats (16-byte loads)
-    float(*DT)[NB + 4] = reinterpret_cast<float(*)[NB + 4]>(&Ds[0][0]);
-    float(*MK)[NB + 4] = reinterpret_cast<float(*)[NB + 4]>(&Ms[0][0]);
+    float(*DT)[NB + 4] = Ds;
+    float(*MK)[NB + 4] = Ms;
     {
         // M[K + a][t0 + b], or column-major 64 x 64 in stage for the tile left of K
         const float *src = staged ? stage + NB * NB : M + k0 + t0 * lda;
@@ -326,8 +351,8 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
-            dv[q] = Dinv[b * NB + a];                               // D^{-1}[b][a]
-            mv[q] = (a < kb && b < nt) ? src[a + b * ld] : 0.0f;  // M[K+a][t0+b]
+            dv[q] = __ldcg(Dinv + b * NB + a);                              // D^{-1}[b][a]
+            mv[q] = (a < kb && b < nt) ? __ldcg(src + a + b * ld) : 0.0f;  // M[K+a][t0+b]
         }
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
@@ -349,17 +374,36 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-            for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+            for (int yy = 0; yy < 4; ++yy) acc[x][yy] = fmaf(a[x], b[yy], acc[x][yy]);
     }
+    __syncthreads();
 #pragma unroll
-    for (int y = 0; y < 4; ++y) {
-        const int c = c0 + y;
+    for (int yy = 0; yy < 4; ++yy) {
+        const int c = c0 + yy;
         if (c >= nt) continue;
         float v[4];
 #pragma unroll
-        for (int x = 0; x < 4; ++x) v[x] = (tile_is_k || r0 + x >= kb) ? 0.0f : acc[x][y];
-        *reinterpret_cast<float4 *>(&Rt[(t0 + c) * NB + r0]) = make_float4(v[0], v[1], v[2], v[3]);
+        for (int x = 0; x < 4; ++x) v[x] = (tile_is_k || r0 + x >= kb) ? 0.0f : acc[x][yy];
+        if (Rt_lo) {
+            float h[4], l[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) tcp::split_tf32(v[x], h[x], l[x]);
+            *reinterpret_cast<float4 *>(&Rt[(t0 + c) * NB + r0]) = make_float4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<float4 *>(&Rt_lo[(t0 + c) * NB + r0]) =
+                make_float4(l[0], l[1], l[2], l[3]);
+        } else {
+            *reinterpret_cast<float4 *>(&Rt[(t0 + c) * NB + r0]) = make_float4(v[0], v[1], v[2], v[3]);
+        }
     }
+}
+
+__global__ void __launch_bounds__(256)
+    k_gj_prep(int64_t n, const float *M, int64_t lda, int64_t k0, const float *Dinv, float *Rt,
+              float *Cb, const float *stage)
+{
+    __shared__ __align__(16) float sbuf[2 * GJ_NB * (GJ_NB + 4)];
+    const int64_t t0 = (int64_t)blockIdx.x * GJ_NB;
+    if (t0 < n) gj_prep_tile(n, M, lda, k0, Dinv, Rt, Cb, stage, t0, (int)blockIdx.y, sbuf);
 }
 
 // M[i, j] -= sum_c Cb[i,c] Rt[j,c] on the CUDA cores (64 x 64 tiles); tiles in
@@ -418,31 +462,36 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// Block row K <- R, block column K <- -C D^{-1}, M[K,K] <- D^{-1}, in 64-wide
-// tiles.  grid.y = 0: column tile t0 of block row K; grid.y = 1: row tile t0
-// of block column K.  The tiles at skip_t0 (the next block, whose diagonal
-// inverse computes them and leaves them for the next prep) are not written.
-__global__ void __launch_bounds__(256)
-    k_gj_finish(int64_t n, float *__restrict__ M, int64_t lda, int64_t k0,
-                const float *__restrict__ Dinv, const float *__restrict__ Rt,
-                const float *__restrict__ Cb, int64_t skip_t0)
+// hi + lo of a split panel entry: the value itself (lo == 0 keeps the sign of a zero)
+__device__ __forceinline__ float gj_join(const float *hi, const float *lo, int64_t i)
+{
+    const float h = __ldcg(hi + i);
+    if (!lo) return h;
+    const float l = __ldcg(lo + i);
+    return l == 0.0f ? h : h + l;
+}
+
+// One tile (t0, y) of the finish; sbuf as for the prep; Rt_lo / Cb_lo as
+// written by the prep.
+__device__ __forceinline__ void gj_finish_tile(int64_t n, float *M, int64_t lda, int64_t k0,
+                                               const float *Dinv, const float *Rt,
+                                               const float *Cb, int64_t t0, int y, float *sbuf,
+                                               const float *Rt_lo = nullptr,
+                                               const float *Cb_lo = nullptr)
 {
     constexpr int NB = GJ_NB;
-    __shared__ __align__(16) float Ds[NB][NB + 4];
-    __shared__ __align__(16) float Cs[NB][NB + 4];
     const int tid = threadIdx.x;
     const int kb = (int)min((int64_t)NB, n - k0);
-    const int64_t t0 = (int64_t)blockIdx.x * NB;
-    if (t0 >= n || t0 == skip_t0) return;
     const int nt = (int)min((int64_t)NB, n - t0);
-    if (blockIdx.y == 0) {
+    if (y == 0) {
         const bool tile_is_k = (t0 == k0);
         float v[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const int idx = tid + 256 * q, rr = idx & 63, c = idx >> 6;
             const bool in = rr < kb && c < nt;
-            v[q] = !in ? 0.0f : (tile_is_k ? Dinv[rr * NB + c] : Rt[(t0 + c) * NB + rr]);
+            v[q] = !in ? 0.0f
+                       : (tile_is_k ? __ldcg(Dinv + rr * NB + c) : gj_join(Rt, Rt_lo, (t0 + c) * NB + rr));
         }
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
@@ -453,15 +502,15 @@ __global__ void __launch_bounds__(256)
     }
     if (t0 == k0) return;
     // C transposed and D^{-1}, rows of 68 floats (16-byte loads)
-    float(*CT)[NB + 4] = reinterpret_cast<float(*)[NB + 4]>(&Cs[0][0]);
-    float(*DD)[NB + 4] = reinterpret_cast<float(*)[NB + 4]>(&Ds[0][0]);
+    float(*CT)[NB + 4] = reinterpret_cast<float(*)[NB + 4]>(sbuf + NB * (NB + 4));
+    float(*DD)[NB + 4] = reinterpret_cast<float(*)[NB + 4]>(sbuf);
     {
         float dv[16], cv[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
-            dv[q] = Dinv[b * NB + a];                             // D^{-1}[b][a]
-            cv[q] = b < nt ? Cb[(t0 + b) * NB + a] : 0.0f;       // C[t0+b][a]
+            dv[q] = __ldcg(Dinv + b * NB + a);                          // D^{-1}[b][a]
+            cv[q] = b < nt ? gj_join(Cb, Cb_lo, (t0 + b) * NB + a) : 0.0f;  // C[t0+b][a]
         }
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
@@ -483,22 +532,37 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-            for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+            for (int yy = 0; yy < 4; ++yy) acc[x][yy] = fmaf(a[x], b[yy], acc[x][yy]);
     }
+    __syncthreads();
 #pragma unroll
-    for (int y = 0; y < 4; ++y) {
-        const int c = c0 + y;
+    for (int yy = 0; yy < 4; ++yy) {
+        const int c = c0 + yy;
         if (c >= kb) continue;
         float *col = M + t0 + (k0 + c) * lda;
         if (i0 + 3 < nt) {
             *reinterpret_cast<float4 *>(col + i0) =
-                make_float4(-acc[0][y], -acc[1][y], -acc[2][y], -acc[3][y]);
+                make_float4(-acc[0][yy], -acc[1][yy], -acc[2][yy], -acc[3][yy]);
         } else {
 #pragma unroll
             for (int x = 0; x < 4; ++x)
-                if (i0 + x < nt) col[i0 + x] = -acc[x][y];
+                if (i0 + x < nt) col[i0 + x] = -acc[x][yy];
         }
     }
+}
+
+// Block row K <- R, block column K <- -C D^{-1}, M[K,K] <- D^{-1}, in 64-wide
+// tiles.  grid.y = 0: column tile t0 of block row K; grid.y = 1: row tile t0
+// of block column K.  The tiles at skip_t0 (the next block, whose diagonal
+// inverse computes them and leaves them for the next prep) are not written.
+__global__ void __launch_bounds__(256)
+    k_gj_finish(int64_t n, float *M, int64_t lda, int64_t k0, const float *Dinv, const float *Rt,
+                const float *Cb, int64_t skip_t0)
+{
+    __shared__ __align__(16) float sbuf[2 * GJ_NB * (GJ_NB + 4)];
+    const int64_t t0 = (int64_t)blockIdx.x * GJ_NB;
+    if (t0 < n && t0 != skip_t0)
+        gj_finish_tile(n, M, lda, k0, Dinv, Rt, Cb, t0, (int)blockIdx.y, sbuf);
 }
 
 // Tensor-core version of the update (tc_gemm.cu); false if not available for
@@ -512,6 +576,382 @@ void launch_simt_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *C
     // k0 = -GJ_NB: no tile is skipped
     k_gj_update_simt<<<dim3(g, g), 256, 0, c.stream>>>(n, M, lda, -GJ_NB, Cb, Rt, -GJ_NB);
     c.launches += 1;
+}
+
+// ---- the fused factorisation -----------------------------------------------
+//
+// The whole inversion as ONE cooperative launch, one CTA per SM: CTA 0 runs
+// the chain of diagonal inverses (each with its lookahead), the other W CTAs
+// ("workers") run prep + finish and the tensor-core update of every step.
+// The hand-offs are counters in global memory instead of kernel boundaries
+// and stream events:
+//   flagD  = diagonal inverses done (CTA 0, after D^{-1} of block k: k + 1),
+//   cntP   = workers done with the prep/finish of some step (W per step),
+//   cntU   = workers done with the update of some step (W per step).
+// Worker, step k:  wait flagD >= k + 1 and cntU >= k W;  prep + finish tiles;
+//                  cntP += 1;  wait cntP >= (k + 1) W;  update tiles;  cntU += 1.
+// CTA 0, block k:  wait cntU >= (k - 1) W (the update of step k - 2, the last
+//                  one that touches the tiles its lookahead reads);  inverse;
+//                  flagD = k + 1.
+// The same device functions (the same arithmetic, in the same order) as the
+// separate kernels below.  Every wait is bounded: a CTA that gives up sets
+// ST_TIMEOUT, and every CTA leaves at its next wait once that bit is set.
+struct GjFusedArgs {
+    int64_t n, lda;
+    float *M;
+    float *dinv;   // 2 x 64 x 64
+    float *rt, *cb;        // the panels, TF32-rounded part
+    float *rt_lo, *cb_lo;  // the panels, the rest
+    float *stage;  // 2 x 8192
+    int32_t *info, *status;
+    int32_t *sync;  // [0] flagD, [1] cntP, [2] cntU
+    int nblk;
+};
+
+constexpr int GJF_THREADS = 256;
+// shared memory of a worker: both 32-wide K blocks of a tile's panels (A, B,
+// A lo, B lo: 128 KB) and the 128 x 128 tile of M (64 KB)
+constexpr int GJF_PANEL_BYTES = 8 * tcp::TC_TILE_BYTES;
+constexpr int GJF_MTILE_BYTES = 128 * 128 * 4;
+constexpr int GJF_SMEM = GJF_PANEL_BYTES + GJF_MTILE_BYTES + 1024;
+
+__device__ __forceinline__ int32_t gjf_ld_acquire(const int32_t *p)
+{
+    int32_t v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Thread 0: wait until sync[i] >= v (and sync[j] >= u when j >= 0).  Returns
+// false (after setting ST_TIMEOUT) if that takes too long, or if another CTA
+// already gave up.
+__device__ bool gjf_wait(const GjFusedArgs &a, int i, int32_t v, int j, int32_t u)
+{
+    long long spins = 0;
+    while (gjf_ld_acquire(a.sync + i) < v || (j >= 0 && gjf_ld_acquire(a.sync + j) < u)) {
+        ++spins;
+        if (spins > kSpinLimit || ((spins & 1023) == 0 && (*(volatile int32_t *)a.status & ST_TIMEOUT))) {
+            atomicOr(a.status, ST_TIMEOUT);
+            return false;
+        }
+        __nanosleep(32);
+    }
+    return true;
+}
+
+__device__ __forceinline__ void gjf_signal(int32_t *p)
+{
+    __threadfence();
+    atomicAdd(p, 1);
+}
+
+// The update of one step on this worker's tiles (t = first, first + stride,
+// ...; 128 x 128 tiles of M, column tile t / rtiles), split TF32 on the
+// tensor cores from panels the prep stored already split (hi, lo), pipelined
+// over the tiles:
+//   thread 0 issues the TMA loads of a tile's panels (hi and lo of both
+//   32-wide K blocks) and of its tile of M; once both K blocks are in it
+//   issues the 12 MMAs of each; once they are done the next tile's panels are
+//   requested; the epilogue subtracts the accumulator (TMEM) from the tile of
+//   M (shared memory) and stores the result with coalesced global stores
+//   (entries the step must not change are not stored); once every thread has
+//   read the tile of M, the next one is requested.
+// ph: this CTA's barrier parity, advanced per tile.  Returns false on timeout
+// (after bounded waits for its own copies in flight).
+__device__ bool gjf_update_step(const CUtensorMap *tmAh, const CUtensorMap *tmAl,
+                                const CUtensorMap *tmBh, const CUtensorMap *tmBl,
+                                const CUtensorMap *tmM, uint8_t *base, uint64_t *bars,
+                                uint32_t tmem, uint32_t &ph, int64_t n, float *M, int64_t lda,
+                                int64_t skip0, int64_t kblk, int first, int stride,
+                                int32_t *status, int *s_ok)
+{
+    using namespace tcp;
+    uint64_t *bar_pan = bars, *bar_m = bars + 2, *bar_mma = bars + 3;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rtiles = (int)ceil_div(n, TC_BM), total = rtiles * (int)ceil_div(n, TC_BN);
+    float *sA[2], *sB[2], *sAl[2], *sBl[2];
+#pragma unroll
+    for (int kb = 0; kb < 2; ++kb) {
+        uint8_t *p = base + (size_t)kb * 4 * TC_TILE_BYTES;
+        sA[kb] = reinterpret_cast<float *>(p);
+        sB[kb] = reinterpret_cast<float *>(p + TC_TILE_BYTES);
+        sAl[kb] = reinterpret_cast<float *>(p + 2 * TC_TILE_BYTES);
+        sBl[kb] = reinterpret_cast<float *>(p + 3 * TC_TILE_BYTES);
+    }
+    const float *Mt = reinterpret_cast<const float *>(base + GJF_PANEL_BYTES);  // [128 cols][128 rows]
+    auto load_panels = [&](int t) {
+        const int row0 = (t % rtiles) * TC_BM, col0 = (t / rtiles) * TC_BN;
+#pragma unroll
+        for (int kb = 0; kb < 2; ++kb) {
+            mbar_expect_tx(&bar_pan[kb], 4 * TC_TILE_BYTES);
+            tma_load_2d(sA[kb], tmAh, kb * TC_KB, row0, &bar_pan[kb]);
+            tma_load_2d(sAl[kb], tmAl, kb * TC_KB, row0, &bar_pan[kb]);
+            tma_load_2d(sB[kb], tmBh, kb * TC_KB, col0, &bar_pan[kb]);
+            tma_load_2d(sBl[kb], tmBl, kb * TC_KB, col0, &bar_pan[kb]);
+        }
+    };
+    auto load_m = [&](int t) {
+        mbar_expect_tx(bar_m, GJF_MTILE_BYTES);
+        tma_load_2d(const_cast<float *>(Mt), tmM, (t % rtiles) * TC_BM, (t / rtiles) * TC_BN, bar_m);
+    };
+    if (first >= total) return true;
+    if (threadIdx.x == 0) {
+        load_panels(first);
+        load_m(first);
+    }
+    constexpr uint32_t idesc = idesc_tf32(TC_BM, TC_BN);
+    bool ok = true;
+    for (int t = first; t < total; t += stride) {
+        const int tn = t + stride;
+        const int64_t row0 = (int64_t)(t % rtiles) * TC_BM, col0 = (int64_t)(t / rtiles) * TC_BN;
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int kb = 0; kb < 2; ++kb) {
+                if (!mbar_wait(&bar_pan[kb], ph)) {
+                    atomicOr(status, ST_TIMEOUT);
+                    *s_ok = 0;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint32_t kofs = (uint32_t)kk * 32u;
+                    const uint64_t ah = desc_sw128_kmajor(smem_u32(sA[kb]) + kofs);
+                    const uint64_t bh = desc_sw128_kmajor(smem_u32(sB[kb]) + kofs);
+                    const uint64_t al = desc_sw128_kmajor(smem_u32(sAl[kb]) + kofs);
+                    const uint64_t bl = desc_sw128_kmajor(smem_u32(sBl[kb]) + kofs);
+                    mma_tf32(tmem, al, bh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                    mma_tf32(tmem, ah, bl, idesc, 1u);
+                    mma_tf32(tmem, ah, bh, idesc, 1u);
+                }
+            }
+            if (*s_ok) {
+                mma_commit(bar_mma);
+                if (!mbar_wait(bar_mma, ph)) {
+                    atomicOr(status, ST_TIMEOUT);
+                    *s_ok = 0;
+                } else if (tn < total) {
+                    load_panels(tn);  // the panels' shared memory is free
+                }
+            }
+        }
+        __syncthreads();
+        if (!*s_ok) {
+            ok = false;
+            break;
+        }
+        if (!mbar_wait(bar_m, ph)) {
+            atomicOr(status, ST_TIMEOUT);
+            *s_ok = 0;
+        }
+        __syncthreads();
+        if (!*s_ok) {
+            ok = false;
+            break;
+        }
+        tc_fence_after();
+        {
+            const int rl = (warp & 3) * 32 + lane;
+            const int64_t row = row0 + rl;
+            const int half = warp >> 2;
+            const bool row_skip = row >= skip0 && row < skip0 + 64;
+            // block row and column kblk were finished by this step's finish
+            const bool row_k = row >= kblk && row < kblk + 64;
+            const bool row_ok = row < n && !row_k;
+            // the accumulator's 64 columns of this thread's row, one wait for all four loads
+            uint32_t acc[4][16];
+            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(half * 64);
+#pragma unroll
+            for (int chunk = 0; chunk < 4; ++chunk)
+                tmem_ld_16cols_async(taddr + (uint32_t)(chunk * 16), acc[chunk]);
+            tmem_wait_ld();
+#pragma unroll
+            for (int chunk = 0; chunk < 4; ++chunk) {
+                const int cl0 = half * 64 + chunk * 16;
+                const int64_t cbeg = col0 + cl0;
+                const uint32_t *v = acc[chunk];
+                if (!row_ok || (cbeg >= kblk && cbeg < kblk + 64)) continue;
+                const bool dskip = row_skip && cbeg >= skip0 && cbeg < skip0 + 64;
+                if (dskip) continue;  // the 64-aligned diagonal block of the lookahead
+                float *p = M + row + cbeg * lda;
+                const int64_t ncol = n - cbeg;
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (j < ncol) p[j * lda] = Mt[(cl0 + j) * TC_BM + rl] - __uint_as_float(v[j]);
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        // every thread has read the tile of M and its accumulator columns
+        if (threadIdx.x == 0 && tn < total) load_m(tn);
+        ph ^= 1u;
+    }
+    if (!ok && threadIdx.x == 0) {
+        // bounded waits for this CTA's copies and MMAs still in flight
+        mbar_wait(&bar_pan[0], ph);
+        mbar_wait(&bar_pan[1], ph);
+        mbar_wait(bar_m, ph);
+        mbar_wait(bar_mma, ph);
+    }
+    // the stores of M are read by TMA (the async proxy) in the next step
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncthreads();
+    return ok;
+}
+
+__global__ void __launch_bounds__(GJF_THREADS, 2)
+    k_gj_fused(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+               const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+               const __grid_constant__ CUtensorMap tmM, GjFusedArgs a)
+{
+    using namespace tcp;
+    extern __shared__ uint8_t gjf_smem[];
+    __shared__ uint64_t bars[4];  // panels K block 0, 1; tile of M; MMAs
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_ok;
+    uint8_t *base = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(gjf_smem) + 1023) & ~static_cast<uintptr_t>(1023));
+    float *sbuf = reinterpret_cast<float *>(base);
+    const int64_t n = a.n, lda = a.lda;
+    const int nblk = a.nblk;
+    const int W = (int)gridDim.x - 1;
+    constexpr int NB = GJ_NB;
+    if (threadIdx.x == 0) s_ok = 1;
+    __syncthreads();
+    if (blockIdx.x == 0) {
+        // the chain of diagonal inverses
+        for (int k = 0; k < nblk; ++k) {
+            if (threadIdx.x == 0 && k >= 2 && !gjf_wait(a, 2, (k - 1) * W, -1, 0)) s_ok = 0;
+            __syncthreads();
+            if (!s_ok) return;
+            const int b = k & 1;
+            gj_diag_block(n, a.M, lda, (int64_t)k * NB, a.dinv + b * NB * NB, a.info,
+                          k ? a.dinv + (b ^ 1) * NB * NB : nullptr,
+                          k ? a.stage + b * 2 * NB * NB : nullptr, sbuf);
+            if (threadIdx.x == 0) {
+                __threadfence();
+                asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(a.sync), "r"(k + 1)
+                             : "memory");
+            }
+        }
+        return;
+    }
+    // workers
+    const int wid = (int)blockIdx.x - 1;
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_slot)),
+                     "r"(TC_BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    uint32_t ph = 0;
+    for (int k = 0; k < nblk; ++k) {
+        const int64_t k0 = (int64_t)k * NB, k1 = k0 + NB;
+        const bool next = k1 < n;
+        const int b = k & 1;
+        const float *dk = a.dinv + b * NB * NB;
+        if (threadIdx.x == 0 && !gjf_wait(a, 0, k + 1, 2, k * W)) s_ok = 0;
+        __syncthreads();
+        if (!s_ok) break;
+        // prep (and, from the same CTA's panel tile, finish) of step k
+        for (int it = wid; it < 2 * nblk; it += W) {
+            const int y = it & 1;
+            const int64_t t0 = (int64_t)(it >> 1) * NB;
+            gj_prep_tile(n, a.M, lda, k0, dk, a.rt, a.cb, k ? a.stage + b * 2 * NB * NB : nullptr,
+                         t0, y, sbuf, a.rt_lo, a.cb_lo);
+            __syncthreads();
+            if (!(next && t0 == k1))
+                gj_finish_tile(n, a.M, lda, k0, dk, a.rt, a.cb, t0, y, sbuf, a.rt_lo, a.cb_lo);
+            __syncthreads();
+        }
+        // the panels are read by TMA (the async proxy) in the update, and TMA
+        // overwrites the shared memory the prep and finish used
+        asm volatile("fence.proxy.async;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            gjf_signal(a.sync + 1);
+            if (!gjf_wait(a, 1, (k + 1) * W, -1, 0)) s_ok = 0;
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        const int64_t skip0 = next ? k1 : -NB;
+        if (!gjf_update_step(&tmAh, &tmAl, &tmBh, &tmBl, &tmM, base, bars, tmem, ph, n, a.M, lda,
+                             skip0, k0, wid, W, a.status, &s_ok))
+            break;
+        __syncthreads();
+        if (threadIdx.x == 0) gjf_signal(a.sync + 2);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN)
+                     : "memory");
+}
+
+// The fused inversion, if this device and precision allow it (split TF32,
+// tensor memory, cooperative launch with one CTA per SM); false otherwise.
+bool run_gj_fused(Ctx &c, float *M, int64_t lda)
+{
+    if (!c.gj_fused || !tc_available()) return false;
+    static int attr_state = 0;  // 0 untried, 1 ok, -1 unavailable
+    if (attr_state == 0) {
+        attr_state = cudaFuncSetAttribute(k_gj_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          GJF_SMEM) == cudaSuccess
+                         ? 1
+                         : -1;
+        cudaGetLastError();
+    }
+    if (attr_state < 0) return false;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_fused, GJF_THREADS, GJF_SMEM) !=
+            cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    const int G = c.num_sms;
+    if (G < 2) return false;
+    // the two panel buffers of the separate-kernel path hold hi and lo here
+    float *rt_lo = c.d_gj_rt + (size_t)GJ_NB * c.lda, *cb_lo = c.d_gj_cb + (size_t)GJ_NB * c.lda;
+    CUtensorMap tmAh, tmAl, tmBh, tmBl, tmM;
+    if (!make_panel_map(&tmAh, c.d_gj_cb, c.n) || !make_panel_map(&tmAl, cb_lo, c.n) ||
+        !make_panel_map(&tmBh, c.d_gj_rt, c.n) || !make_panel_map(&tmBl, rt_lo, c.n) ||
+        !make_matrix_map(&tmM, M, c.n, lda))
+        return false;
+    GjFusedArgs a{};
+    a.n = c.n;
+    a.lda = lda;
+    a.M = M;
+    a.dinv = c.d_gj_dinv;
+    a.rt = c.d_gj_rt;
+    a.cb = c.d_gj_cb;
+    a.rt_lo = rt_lo;
+    a.cb_lo = cb_lo;
+    a.stage = c.d_gj_stage;
+    a.info = c.d_info;
+    a.status = c.d_status;
+    a.sync = c.d_gj_sync;
+    a.nblk = (int)ceil_div(c.n, GJ_NB);
+    cudaMemsetAsync(c.d_info, 0, sizeof(int32_t), c.stream);
+    cudaMemsetAsync(c.d_gj_sync, 0, 4 * sizeof(int32_t), c.stream);
+    void *args[] = {&tmAh, &tmAl, &tmBh, &tmBl, &tmM, &a};
+    c.tbeg(PH_LU_UPDATE);
+    const cudaError_t e =
+        cudaLaunchCooperativeKernel((void *)k_gj_fused, G, GJF_THREADS, args, GJF_SMEM, c.stream);
+    c.tend(PH_LU_UPDATE);
+    c.launches += 1;
+    return e == cudaSuccess;
 }
 
 // One inversion.  Streams: main (S), lookahead (S2), finish (S4).  Step k
@@ -541,6 +981,7 @@ constexpr int GJ_DIAG_EXCL_SMEM = 164 * 1024;
 
 int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
 {
+    if (prec == NRS_TF32 && run_gj_fused(c, M, lda)) return 0;
     static bool diag_attr = false;
     if (!diag_attr) {
         cudaFuncSetAttribute(k_gj_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,

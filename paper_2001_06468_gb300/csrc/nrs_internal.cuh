@@ -180,6 +180,8 @@ struct Ctx {
     float *d_gj_rt = nullptr;      //   scaled block row, transposed (2 buffers of n x 64)
     float *d_gj_cb = nullptr;      //   block column (2 buffers of n x 64)
     float *d_gj_stage = nullptr;   //   two finished 64 x 64 tiles (2 buffers)
+    int32_t *d_gj_sync = nullptr;  //   counters of the fused factorisation (4)
+    bool gj_fused = false;         //   use the fused (one-launch) factorisation when possible
     int32_t *d_info = nullptr;
     int factored_prec = -1;
     bool assembled = false;
