@@ -50,9 +50,10 @@ struct PgArgs {
     double *x;            // in: starting guess unless cold; out: solution
     double *V;            // Krylov basis, n x (m+1), leading dimension ldv
     double *w;            // n: A v, then the residual
-    double *part;         // matrix-vector partial sums [splits][n]
+    double *part;         // partial sums of the FP64 products [splits][n]
+    double *part32;       // partial sums of the FP32 products [splits][n]
     double *dpart;        // reduction partials [3][PG_MAXCH][m+2]
-    int32_t *bar;         // grid barrier: [0] arrivals, [1] generation
+    int32_t *bar;         // grid barrier: [0] arrivals since the launch ([1] unused)
     int32_t *status;
     double *out;          // [0] outer steps, [1] inner iterations, [2] converged,
                           // [3] ||d||_inf, [4] ||x||_inf
@@ -81,29 +82,30 @@ __device__ __forceinline__ int32_t pg_ld_relaxed(const int32_t *p)
     return v;
 }
 
-// Grid-wide barrier (bounded).  Returns false when the solve must stop.
-__device__ bool grid_sync(const PgArgs &a, int *s_ok)
+// Grid-wide barrier (bounded).  Returns false when the solve must stop.  One
+// monotonic arrival counter per launch (zeroed before it): barrier number k
+// is passed once the counter reaches k * gridDim.x, so the last arrival
+// releases everyone with its own atomic (no reset, no second flag); tgt is
+// the calling thread's running target.  Busy polling first, then polling
+// with short sleeps.
+__device__ bool grid_sync(const PgArgs &a, int *s_ok, int32_t &tgt)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
+        tgt += (int32_t)gridDim.x;
         __threadfence();
-        const int32_t gen = pg_ld_acquire(&a.bar[1]);
-        if (atomicAdd(&a.bar[0], 1) == (int)gridDim.x - 1) {
-            atomicExch(&a.bar[0], 0);
-            pg_st_release(&a.bar[1], gen + 1);
-        } else {
-            long long spins = 0;
-            while (pg_ld_acquire(&a.bar[1]) == gen) {
-                ++spins;
-                if (spins > kSpinLimit ||
-                    ((spins & 1023) == 0 && (pg_ld_relaxed(a.status) & ST_TIMEOUT))) {
-                    atomicOr(a.status, ST_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
+        atomicAdd(&a.bar[0], 1);
+        long long spins = 0;
+        while (pg_ld_acquire(&a.bar[0]) < tgt) {
+            ++spins;
+            if (spins > kSpinLimit ||
+                ((spins & 1023) == 0 && (pg_ld_relaxed(a.status) & ST_TIMEOUT))) {
+                atomicOr(a.status, ST_TIMEOUT);
+                ok = 0;
+                break;
             }
+            if (spins > 64) __nanosleep(32);
         }
         *s_ok = ok;
     }
@@ -154,8 +156,8 @@ __device__ void mv64_partial(const PgArgs &a, const double *v, double scale, dou
     }
 }
 
-// part[s][i] = sum_{j in split s} M[i, j] v[j] (FP32 products and sums): 128
-// rows per tile, lane l takes rows 4l..4l+3 (one 16-byte load per column).
+// part32[s][i] = sum_{j in split s} M[i, j] v[j] (FP32 products and sums):
+// 128 rows per tile, lane l takes rows 4l..4l+3 (one 16-byte load per column).
 __device__ void mv32_partial(const PgArgs &a, const double *v, float *sm)
 {
     const int64_t tiles = (int64_t)a.rc32 * a.s32;
@@ -188,7 +190,7 @@ __device__ void mv32_partial(const PgArgs &a, const double *v, float *sm)
             double acc = 0.0;
 #pragma unroll
             for (int g = 0; g < MV_GROUPS; ++g) acc += (double)sm[g * MV32_ROWS + threadIdx.x];
-            if (r < a.n) a.part[s * a.n + r] = acc;
+            if (r < a.n) a.part32[s * a.n + r] = acc;
         }
         __syncthreads();
     }
@@ -198,6 +200,13 @@ __device__ __forceinline__ double sum_parts(const PgArgs &a, int splits, int64_t
 {
     double s = 0.0;
     for (int k = 0; k < splits; ++k) s += __ldcg(a.part + k * a.n + e);
+    return s;
+}
+
+__device__ __forceinline__ double sum_parts32(const PgArgs &a, int64_t e)
+{
+    double s = 0.0;
+    for (int k = 0; k < a.s32; ++k) s += __ldcg(a.part32 + k * a.n + e);
     return s;
 }
 
@@ -287,6 +296,7 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
     __shared__ double sred[PG_THREADS / 32];
     __shared__ __align__(16) double smv[MV_GROUPS * MV64_ROWS];  // product tiles (FP64 or FP32 view)
     __shared__ int s_ok;
+    int32_t tgt = 0;  // grid barrier target (thread 0)
     float *smv32 = reinterpret_cast<float *>(smv);
     static_assert(MV_GROUPS * MV32_ROWS * sizeof(float) <= sizeof(double) * MV_GROUPS * MV64_ROWS,
                   "shared product tile");
@@ -303,9 +313,9 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
 
     if (a.cold) {  // x = M b
         mv32_partial(a, a.b, smv32);
-        if (!grid_sync(a, &s_ok)) return;
-        for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) a.x[e] = sum_parts(a, a.s32, e);
-        if (!grid_sync(a, &s_ok)) return;
+        if (!grid_sync(a, &s_ok, tgt)) return;
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) a.x[e] = sum_parts32(a, e);
+        if (!grid_sync(a, &s_ok, tgt)) return;
     }
     int outer = 0, inner_total = 0, converged = 0;
     double dn = 0.0, xn = 0.0, dn_prev = 0.0, normA = -1.0;
@@ -313,7 +323,7 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
     for (outer = 0; outer < a.max_outer; ++outer) {
         // r = b - A x (FP64), with ||r||_inf and ||b||_inf per chunk
         mv64_partial<false>(a, a.x, 1.0, smv);
-        if (!grid_sync(a, &s_ok)) return;
+        if (!grid_sync(a, &s_ok, tgt)) return;
         {
             double rmax = 0.0, bmax = 0.0;
             for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
@@ -330,7 +340,7 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
                 dp1[1] = bmax;
             }
         }
-        if (!grid_sync(a, &s_ok)) return;
+        if (!grid_sync(a, &s_ok, tgt)) return;
         if (stagnant) {
             // The corrections stopped shrinking.  If x already solves a nearby
             // system to working precision (normwise backward error
@@ -338,13 +348,13 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
             // chase rounding noise: stop.  ||A||_inf is computed once, here.
             if (normA < 0.0) {
                 mv64_partial<true>(a, nullptr, 1.0, smv);
-                if (!grid_sync(a, &s_ok)) return;
+                if (!grid_sync(a, &s_ok, tgt)) return;
                 double amax = 0.0;
                 for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS)
                     amax = fmax(amax, sum_parts(a, a.s64, e));
                 amax = block_max_all(amax, sred);
                 if (owner && threadIdx.x == 0) dp1[2] = amax;
-                if (!grid_sync(a, &s_ok)) return;
+                if (!grid_sync(a, &s_ok, tgt)) return;
                 normA = chunk_total(a, 1, 2, true, sred);
             }
             const double rn = chunk_total(a, 1, 0, true, sred);
@@ -356,18 +366,18 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
         }
         // V_0 = M r (raw), beta = ||V_0||
         mv32_partial(a, a.w, smv32);
-        if (!grid_sync(a, &s_ok)) return;
+        if (!grid_sync(a, &s_ok, tgt)) return;
         {
             double s = 0.0;
             for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
-                const double v = sum_parts(a, a.s32, e);
+                const double v = sum_parts32(a, e);
                 a.V[e] = v;
                 s = fma(v, v, s);
             }
             s = block_sum_all(s, sred);
             if (owner && threadIdx.x == 0) dp2[nslot] = s;
         }
-        if (!grid_sync(a, &s_ok)) return;
+        if (!grid_sync(a, &s_ok, tgt)) return;
         const double beta = sqrt(chunk_total(a, 2, nslot, false, sred));
         if (!isfinite(beta)) {
             if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.status, ST_NONFINITE);
@@ -383,19 +393,19 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
             double *u = a.V + (int64_t)(j + 1) * a.ldv;
             // w = A v_j
             mv64_partial<false>(a, Vj, sv, smv);
-            if (!grid_sync(a, &s_ok)) return;
+            if (!grid_sync(a, &s_ok, tgt)) return;
             for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
                 Vj[e] = __ldcg(Vj + e) * sv;  // v_j normalised in place (own chunk)
                 a.w[e] = sum_parts(a, a.s64, e);
             }
-            if (!grid_sync(a, &s_ok)) return;
+            if (!grid_sync(a, &s_ok, tgt)) return;
             // u = M w, then two classical Gram-Schmidt passes and the norm
             mv32_partial(a, a.w, smv32);
-            if (!grid_sync(a, &s_ok)) return;
-            for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) u[e] = sum_parts(a, a.s32, e);
+            if (!grid_sync(a, &s_ok, tgt)) return;
+            for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) u[e] = sum_parts32(a, e);
             __syncthreads();
             if (owner) chunk_dots(a, 0, j, u, e0, e1);
-            if (!grid_sync(a, &s_ok)) return;
+            if (!grid_sync(a, &s_ok, tgt)) return;
             sum_dots(a, 0, j, sh1);
             for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
                 double s = __ldcg(u + e);
@@ -404,7 +414,7 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
             }
             __syncthreads();
             if (owner) chunk_dots(a, 1, j, u, e0, e1);
-            if (!grid_sync(a, &s_ok)) return;
+            if (!grid_sync(a, &s_ok, tgt)) return;
             sum_dots(a, 1, j, sh2);
             {
                 double s2 = 0.0;
@@ -418,7 +428,7 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
                 s2 = block_sum_all(s2, sred);
                 if (owner && threadIdx.x == 0) dp2[nslot] = s2;
             }
-            if (!grid_sync(a, &s_ok)) return;
+            if (!grid_sync(a, &s_ok, tgt)) return;
             const double hn = sqrt(chunk_total(a, 2, nslot, false, sred));
             // column j of H, previous rotations, the new rotation (every CTA, same order)
             double res = 0.0;
@@ -485,7 +495,7 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
                 dp0[1] = xmax;
             }
         }
-        if (!grid_sync(a, &s_ok)) return;
+        if (!grid_sync(a, &s_ok, tgt)) return;
         dn = chunk_total(a, 0, 0, true, sred);
         xn = chunk_total(a, 0, 1, true, sred);
         // stopping rule of k_outer_check (solve.cu)
@@ -558,6 +568,7 @@ cudaError_t launch_gmres_persistent(Ctx &c, const double *b, double *x, bool col
     a.V = c.d_V;
     a.w = c.d_w;
     a.part = c.d_part;
+    a.part32 = c.d_part32;
     a.dpart = c.d_dpart;
     a.bar = c.d_bar;
     a.status = c.d_status;

@@ -240,6 +240,7 @@ struct Ctx {
     double *d_gv = nullptr;    // Givens state: cs[m], sn[m], g[m+1], y[m]
     double *d_scal = nullptr;  // scalars (norms, flags as doubles)
     double *d_part = nullptr;  // partial sums of matrix-vector products
+    double *d_part32 = nullptr;  // partial sums of the FP32 products of the persistent solve
     int splits64 = 1, splits32 = 1;  // column splits of the FP64 / FP32 matrix-vector products
     float *d_t32 = nullptr;    // FP32 work vector for the triangular solves
     double *d_t64 = nullptr;   // FP64 work vector for the triangular solves
