@@ -1014,8 +1014,20 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
             cudaStreamWaitEvent(c.stream2, c.ev_upd, 0);
             if (kstep > 0) cudaStreamWaitEvent(c.stream2, c.ev_fin[b ^ 1], 0);
             c.tbeg(PH_LU_DIAG, c.stream2);
-            k_gj_diag<<<1, 256, GJ_DIAG_EXCL_SMEM, c.stream2>>>(n, M, lda, k1, dinv[b ^ 1], c.d_info, dinv[b],
-                                                stg[b ^ 1]);
+            // a programmatic dependent of the previous inverse on this stream
+            // (it loads its tiles of M while that one finishes)
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(1);
+            cfg.blockDim = dim3(256);
+            cfg.dynamicSmemBytes = GJ_DIAG_EXCL_SMEM;
+            cfg.stream = c.stream2;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            cudaLaunchKernelEx(&cfg, k_gj_diag, (int64_t)n, (const float *)M, (int64_t)lda, (int64_t)k1,
+                               dinv[b ^ 1], c.d_info, (const float *)dinv[b], stg[b ^ 1]);
             c.tend(PH_LU_DIAG, c.stream2);
             cudaEventRecord(c.ev_diag, c.stream2);
             c.launches += 1;
