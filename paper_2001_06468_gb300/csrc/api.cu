@@ -76,8 +76,8 @@ nrs_status alloc_all(Ctx *c)
         {(void **)&c->d_rowperm, sizeof(int32_t) * n},
         {(void **)&c->d_lperm, sizeof(int32_t) * 64},
         {(void **)&c->d_gj_dinv, sizeof(float) * 2 * 64 * 64},
-        {(void **)&c->d_gj_rt, sizeof(float) * 2 * 64 * lda},
-        {(void **)&c->d_gj_cb, sizeof(float) * 2 * 64 * lda},
+        {(void **)&c->d_gj_rt, sizeof(float) * 4 * 64 * lda},
+        {(void **)&c->d_gj_cb, sizeof(float) * 4 * 64 * lda},
         {(void **)&c->d_gj_stage, sizeof(float) * 4 * 64 * 64},
         {(void **)&c->d_gj_sync, sizeof(int32_t) * 4},
         {(void **)&c->d_info, sizeof(int32_t)},

@@ -104,9 +104,22 @@ __device__ __forceinline__ void gj_diag_block(int64_t n, const float *M, int64_t
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
-                dv[q] = __ldcg(Dprev + b * NB + a);                              // Dprev[b][a]
                 mv[q] = b < kb ? __ldcg(M + (kp + a) + (k0 + b) * lda) : 0.0f;  // M[P+a][K+b]
                 cv[q] = a < kb ? __ldcg(M + (k0 + a) + (kp + b) * lda) : 0.0f;  // M[K+a][P+b]
+            }
+            // Launched as a programmatic dependent of the previous diagonal
+            // inverse, this kernel may start while that one still runs: the
+            // tiles of M above are final already (the previous inverse writes
+            // only D^{-1}, the staged tiles and info), Dprev is not until the
+            // previous grid has completed and flushed.  Then the next inverse
+            // may launch.  (Both instructions do nothing in a kernel launched
+            // otherwise.)
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
+                dv[q] = __ldcg(Dprev + b * NB + a);  // Dprev[b][a]
             }
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
@@ -399,11 +412,12 @@ __device__ __forceinline__ void gj_prep_tile(int64_t n, const float *M, int64_t 
 
 __global__ void __launch_bounds__(256)
     k_gj_prep(int64_t n, const float *M, int64_t lda, int64_t k0, const float *Dinv, float *Rt,
-              float *Cb, const float *stage)
+              float *Cb, const float *stage, float *Rt_lo, float *Cb_lo)
 {
     __shared__ __align__(16) float sbuf[2 * GJ_NB * (GJ_NB + 4)];
     const int64_t t0 = (int64_t)blockIdx.x * GJ_NB;
-    if (t0 < n) gj_prep_tile(n, M, lda, k0, Dinv, Rt, Cb, stage, t0, (int)blockIdx.y, sbuf);
+    if (t0 < n)
+        gj_prep_tile(n, M, lda, k0, Dinv, Rt, Cb, stage, t0, (int)blockIdx.y, sbuf, Rt_lo, Cb_lo);
 }
 
 // M[i, j] -= sum_c Cb[i,c] Rt[j,c] on the CUDA cores (64 x 64 tiles); tiles in
@@ -557,18 +571,19 @@ __device__ __forceinline__ void gj_finish_tile(int64_t n, float *M, int64_t lda,
 // inverse computes them and leaves them for the next prep) are not written.
 __global__ void __launch_bounds__(256)
     k_gj_finish(int64_t n, float *M, int64_t lda, int64_t k0, const float *Dinv, const float *Rt,
-                const float *Cb, int64_t skip_t0)
+                const float *Cb, int64_t skip_t0, const float *Rt_lo, const float *Cb_lo)
 {
     __shared__ __align__(16) float sbuf[2 * GJ_NB * (GJ_NB + 4)];
     const int64_t t0 = (int64_t)blockIdx.x * GJ_NB;
     if (t0 < n && t0 != skip_t0)
-        gj_finish_tile(n, M, lda, k0, Dinv, Rt, Cb, t0, (int)blockIdx.y, sbuf);
+        gj_finish_tile(n, M, lda, k0, Dinv, Rt, Cb, t0, (int)blockIdx.y, sbuf, Rt_lo, Cb_lo);
 }
 
 // Tensor-core version of the update (tc_gemm.cu); false if not available for
 // this precision.
 bool launch_tc_gj_update(Ctx &c, float *M, int64_t lda, int64_t k0, const float *Cb,
-                         const float *Rt, int prec, int64_t skip0);
+                         const float *Rt, int prec, int64_t skip0, const float *Cb_lo,
+                         const float *Rt_lo);
 
 void launch_simt_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb, const float *Rt)
 {
@@ -922,8 +937,8 @@ bool run_gj_fused(Ctx &c, float *M, int64_t lda)
     }
     const int G = c.num_sms;
     if (G < 2) return false;
-    // the two panel buffers of the separate-kernel path hold hi and lo here
-    float *rt_lo = c.d_gj_rt + (size_t)GJ_NB * c.lda, *cb_lo = c.d_gj_cb + (size_t)GJ_NB * c.lda;
+    // the first of the separate-kernel path's panel buffers, split as there
+    float *rt_lo = c.d_gj_rt + (size_t)2 * GJ_NB * c.lda, *cb_lo = c.d_gj_cb + (size_t)2 * GJ_NB * c.lda;
     CUtensorMap tmAh, tmAl, tmBh, tmBl, tmM;
     if (!make_panel_map(&tmAh, c.d_gj_cb, c.n) || !make_panel_map(&tmAl, cb_lo, c.n) ||
         !make_panel_map(&tmBh, c.d_gj_rt, c.n) || !make_panel_map(&tmBl, rt_lo, c.n) ||
@@ -999,6 +1014,11 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
     float *dinv[2] = {c.d_gj_dinv, c.d_gj_dinv + GJ_NB * GJ_NB};
     float *rt[2] = {c.d_gj_rt, c.d_gj_rt + (size_t)GJ_NB * c.lda};
     float *cb[2] = {c.d_gj_cb, c.d_gj_cb + (size_t)GJ_NB * c.lda};
+    // with the tensor-core update the prep stores the panels split into TF32
+    // hi (rt, cb) and lo (these) for it, and the finish joins them again
+    const bool split = (prec == NRS_TF32) && tc_available();
+    float *rt_lo[2] = {c.d_gj_rt + (size_t)2 * GJ_NB * c.lda, c.d_gj_rt + (size_t)3 * GJ_NB * c.lda};
+    float *cb_lo[2] = {c.d_gj_cb + (size_t)2 * GJ_NB * c.lda, c.d_gj_cb + (size_t)3 * GJ_NB * c.lda};
     float *stg[2] = {c.d_gj_stage, c.d_gj_stage + 2 * GJ_NB * GJ_NB};
     c.tbeg(PH_LU_DIAG);
     k_gj_diag<<<1, 256, GJ_DIAG_EXCL_SMEM, c.stream>>>(n, M, lda, 0, dinv[0], c.d_info, nullptr, nullptr);
@@ -1034,24 +1054,30 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
         }
         c.tbeg(PH_LU_PANEL);
         k_gj_prep<<<dim3(gcols, 2), 256, 0, c.stream>>>(n, M, lda, k0, dinv[b], rt[b], cb[b],
-                                                        kstep > 0 ? stg[b] : nullptr);
+                                                        kstep > 0 ? stg[b] : nullptr,
+                                                        split ? rt_lo[b] : nullptr,
+                                                        split ? cb_lo[b] : nullptr);
         c.tend(PH_LU_PANEL);
         cudaEventRecord(c.ev_fin_ready, c.stream);
         cudaStreamWaitEvent(c.stream4, c.ev_fin_ready, 0);
         c.tbeg(PH_LU_PANEL, c.stream4);
         k_gj_finish<<<dim3(gcols, 2), 256, 0, c.stream4>>>(n, M, lda, k0, dinv[b], rt[b], cb[b],
-                                                           next ? k1 : -1);
+                                                           next ? k1 : -1,
+                                                           split ? rt_lo[b] : nullptr,
+                                                           split ? cb_lo[b] : nullptr);
         c.tend(PH_LU_PANEL, c.stream4);
         cudaEventRecord(c.ev_fin[b], c.stream4);
         if (kstep > 0) cudaStreamWaitEvent(c.stream, c.ev_fin[b ^ 1], 0);
         const int64_t skip0 = next ? k1 : -GJ_NB;
         c.tbeg(PH_LU_UPDATE);
-        bool done = false;
-        if (prec == NRS_TF32 || prec == NRS_BF16)
-            done = launch_tc_gj_update(c, M, lda, k0, cb[b], rt[b], prec, skip0);
-        if (!done)
+        if (split) {
+            // split panels have no CUDA-core fallback: a failed launch is an error
+            if (!launch_tc_gj_update(c, M, lda, k0, cb[b], rt[b], prec, skip0, cb_lo[b], rt_lo[b]))
+                cudaMemsetAsync(c.d_info, 0xff, sizeof(int32_t), c.stream);
+        } else {
             k_gj_update_simt<<<dim3(gcols, gcols), 256, 0, c.stream>>>(n, M, lda, k0, cb[b], rt[b],
                                                                         skip0);
+        }
         c.tend(PH_LU_UPDATE);
         cudaEventRecord(c.ev_upd, c.stream);
         if (next) cudaStreamWaitEvent(c.stream, c.ev_diag, 0);

@@ -82,7 +82,8 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec);
 
 bool tc_available();
 bool launch_tc_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb, const float *Rt,
-                      int prec, int64_t skip0, int64_t kblk);
+                      int prec, int64_t skip0, int64_t kblk, const float *Cb_lo = nullptr,
+                      const float *Rt_lo = nullptr);
 void launch_simt_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb, const float *Rt);
 
 // ---- solve (solve.cu) ------------------------------------------------------
@@ -177,8 +178,8 @@ struct Ctx {
     int32_t *d_lperm = nullptr;    // row exchange of the current diagonal block
     bool a32_fresh = false;        // d_A32 holds the last assembly (not yet factored)
     float *d_gj_dinv = nullptr;    // Gauss-Jordan workspaces: D^{-1} (64 x 64)
-    float *d_gj_rt = nullptr;      //   scaled block row, transposed (2 buffers of n x 64)
-    float *d_gj_cb = nullptr;      //   block column (2 buffers of n x 64)
+    float *d_gj_rt = nullptr;      //   scaled block row, transposed (2 buffers of n x 64, then their TF32 lo parts)
+    float *d_gj_cb = nullptr;      //   block column (2 buffers of n x 64, then their TF32 lo parts)
     float *d_gj_stage = nullptr;   //   two finished 64 x 64 tiles (2 buffers)
     int32_t *d_gj_sync = nullptr;  //   counters of the fused factorisation (4)
     bool gj_fused = false;         //   use the fused (one-launch) factorisation when possible

@@ -27,8 +27,13 @@ namespace {
 
 using namespace tcp;
 
+// PRESPLIT: the panels arrive already split (hi in tmA/tmB, lo in tmAl/tmBl,
+// as the prep stores them for this kernel), so the tiles go to the tensor
+// cores as loaded; otherwise the FP32 panels are split here.
+template <bool PRESPLIT>
 __global__ void __launch_bounds__(128, 1)
     k_tc_gj_update(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmAl, const __grid_constant__ CUtensorMap tmBl,
                    int64_t n, float *__restrict__ M, int64_t lda, int32_t *status, int64_t skip0,
                    int64_t kblk)
 {
@@ -76,9 +81,13 @@ __global__ void __launch_bounds__(128, 1)
                 s_ok = 0;
             }
             if (s_ok) {
-                mbar_expect_tx(&bar_load[kb], 2 * TC_TILE_BYTES);
+                mbar_expect_tx(&bar_load[kb], (PRESPLIT ? 4 : 2) * TC_TILE_BYTES);
                 tma_load_2d(sA, &tmA, kb * TC_KB, (int)row0, &bar_load[kb]);
                 tma_load_2d(sB, &tmB, kb * TC_KB, (int)col0, &bar_load[kb]);
+                if (PRESPLIT) {
+                    tma_load_2d(sAl, &tmAl, kb * TC_KB, (int)row0, &bar_load[kb]);
+                    tma_load_2d(sBl, &tmBl, kb * TC_KB, (int)col0, &bar_load[kb]);
+                }
             }
         }
         __syncthreads();
@@ -89,18 +98,20 @@ __global__ void __launch_bounds__(128, 1)
         }
         __syncthreads();
         if (!s_ok) break;
-        // split both tiles in place (element-wise: the swizzled layout is kept)
-        for (int i = threadIdx.x; i < kElems; i += 128) {
-            float h, l;
-            split_tf32(sA[i], h, l);
-            sA[i] = h;
-            sAl[i] = l;
-            split_tf32(sB[i], h, l);
-            sB[i] = h;
-            sBl[i] = l;
+        if (!PRESPLIT) {
+            // split both tiles in place (element-wise: the swizzled layout is kept)
+            for (int i = threadIdx.x; i < kElems; i += 128) {
+                float h, l;
+                split_tf32(sA[i], h, l);
+                sA[i] = h;
+                sAl[i] = l;
+                split_tf32(sB[i], h, l);
+                sB[i] = h;
+                sBl[i] = l;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
         if (threadIdx.x == 0) {
             tc_fence_after();
 #pragma unroll
@@ -246,28 +257,45 @@ bool tc_available()
 }
 
 bool launch_tc_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb, const float *Rt,
-                      int prec, int64_t skip0, int64_t kblk)
+                      int prec, int64_t skip0, int64_t kblk, const float *Cb_lo, const float *Rt_lo)
 {
     if (prec != NRS_TF32) return false;
-    CUtensorMap a, b;
+    const bool split = Cb_lo != nullptr;
+    CUtensorMap a, b, al, bl;
     if (!make_panel_map(&a, Cb, n) || !make_panel_map(&b, Rt, n)) return false;
+    if (split && (!make_panel_map(&al, Cb_lo, n) || !make_panel_map(&bl, Rt_lo, n))) return false;
+    if (!split) {
+        al = a;
+        bl = b;
+    }
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_tc_gj_update, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-        cudaFuncSetAttribute(k_tc_gj_update, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_tc_gj_update<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TC_SMEM);
+        cudaFuncSetAttribute(k_tc_gj_update<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TC_SMEM);
+        cudaFuncSetAttribute(k_tc_gj_update<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_tc_gj_update<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
         attr = true;
     }
     dim3 grid((unsigned)ceil_div(n, TC_BM), (unsigned)ceil_div(n, TC_BN));
-    k_tc_gj_update<<<grid, 128, TC_SMEM, c.stream>>>(a, b, n, M, lda, c.d_status, skip0, kblk);
+    if (split)
+        k_tc_gj_update<true><<<grid, 128, TC_SMEM, c.stream>>>(a, b, al, bl, n, M, lda, c.d_status,
+                                                                skip0, kblk);
+    else
+        k_tc_gj_update<false><<<grid, 128, TC_SMEM, c.stream>>>(a, b, al, bl, n, M, lda, c.d_status,
+                                                                 skip0, kblk);
     c.launches += 1;
     return true;
 }
 
 bool launch_tc_gj_update(Ctx &c, float *M, int64_t lda, int64_t k0, const float *Cb,
-                         const float *Rt, int prec, int64_t skip0)
+                         const float *Rt, int prec, int64_t skip0, const float *Cb_lo,
+                         const float *Rt_lo)
 {
-    return launch_tc_rank64(c, M, lda, c.n, Cb, Rt, prec, skip0, k0);
+    return launch_tc_rank64(c, M, lda, c.n, Cb, Rt, prec, skip0, k0, Cb_lo, Rt_lo);
 }
 
 }  // namespace nrs
