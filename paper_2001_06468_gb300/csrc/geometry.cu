@@ -109,9 +109,16 @@ void launch_kinematics(Ctx &c, const D4 *xi, const D4 *Xiw, const D4 *xidot, D4 
 // index order.  The 1e-6 factors dominate every FP32 rounding of the bound
 // itself (u = 2^-24 ~ 6e-8), so the result equals an exhaustive FP64 search.
 
-constexpr int NN_THREADS = 128;
+constexpr int NN_QPB = 128;    // quadrature points per task (one block)
+constexpr int NN_SPLIT = 4;    // threads per quadrature point, each taking every 4th candidate
+constexpr int NN_THREADS = NN_QPB * NN_SPLIT;
 constexpr int NN_TILE = 512;
 
+// The NN_SPLIT threads of a quadrature point are consecutive lanes; each scans
+// the candidates i = sub, sub + NN_SPLIT, ... of every tile in ascending order,
+// and the lanes combine their results: the FP32 minimum (exact, order-free)
+// and, in pass 2, the lexicographic minimum of (FP64 distance, index), which
+// is the first strict minimum of the ascending scan.
 __global__ void __launch_bounds__(NN_THREADS)
     k_nearest(const NNTask *__restrict__ tasks, const int64_t *__restrict__ n_off, int nbodies,
               int global, const D4 *__restrict__ x, const D4 *__restrict__ X,
@@ -122,7 +129,8 @@ __global__ void __launch_bounds__(NN_THREADS)
     const NNTask t = tasks[blockIdx.x];
     const int64_t n_lo = global ? 0 : n_off[t.body];
     const int64_t n_hi = global ? n_off[nbodies] : n_off[t.body + 1];
-    const int64_t q = (int64_t)t.q0 + threadIdx.x;
+    const int sub = threadIdx.x % NN_SPLIT;
+    const int64_t q = (int64_t)t.q0 + threadIdx.x / NN_SPLIT;
     const bool active = q < t.q1;
     double qx = 0.0, qy = 0.0, qz = 0.0;
     if (active) {
@@ -151,7 +159,7 @@ __global__ void __launch_bounds__(NN_THREADS)
         __syncthreads();
         if (active) {
 #pragma unroll 8
-            for (int i = 0; i < cnt; ++i) {
+            for (int i = sub; i < cnt; i += NN_SPLIT) {
                 float4 v = tile[i];
                 float dx = v.x - fx, dy = v.y - fy, dz = v.z - fz;
                 float d2 = dx * dx + dy * dy + dz * dz;
@@ -159,6 +167,8 @@ __global__ void __launch_bounds__(NN_THREADS)
             }
         }
     }
+#pragma unroll
+    for (int o = 1; o < NN_SPLIT; o <<= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
     __syncthreads();
     const float cmax =
         fmaxf(__uint_as_float(s_cmax), fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
@@ -178,7 +188,7 @@ __global__ void __launch_bounds__(NN_THREADS)
         }
         __syncthreads();
         if (active) {
-            for (int i = 0; i < cnt; ++i) {
+            for (int i = sub; i < cnt; i += NN_SPLIT) {
                 float4 v = tile[i];
                 float dx = v.x - fx, dy = v.y - fy, dz = v.z - fz;
                 float d2 = dx * dx + dy * dy + dz * dz;
@@ -195,7 +205,16 @@ __global__ void __launch_bounds__(NN_THREADS)
             }
         }
     }
-    if (active) {
+#pragma unroll
+    for (int o = 1; o < NN_SPLIT; o <<= 1) {
+        const double os = __shfl_xor_sync(0xffffffffu, best64, o);
+        const int64_t oa = __shfl_xor_sync(0xffffffffu, arg, o);
+        if (oa >= 0 && (arg < 0 || os < best64 || (os == best64 && oa < arg))) {
+            best64 = os;
+            arg = oa;
+        }
+    }
+    if (active && sub == 0) {
         nn[q] = (int32_t)arg;  // -1 only when no distance was finite (NaN/Inf input)
         if (arg < 0) atomicOr(status, ST_NONFINITE);
     }
