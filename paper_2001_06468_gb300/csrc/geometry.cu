@@ -110,7 +110,7 @@ void launch_kinematics(Ctx &c, const D4 *xi, const D4 *Xiw, const D4 *xidot, D4 
 // itself (u = 2^-24 ~ 6e-8), so the result equals an exhaustive FP64 search.
 
 constexpr int NN_QPB = 128;    // quadrature points per task (one block)
-constexpr int NN_SPLIT = 4;    // threads per quadrature point, each taking every 4th candidate
+constexpr int NN_SPLIT = 4;    // threads per quadrature point, each taking every NN_SPLIT-th candidate
 constexpr int NN_THREADS = NN_QPB * NN_SPLIT;
 constexpr int NN_TILE = 512;
 
@@ -326,24 +326,22 @@ void launch_segments(Ctx &c, const int32_t *nn, int32_t *seg_ptr, int32_t *perm)
 }
 
 // Lab-frame quadrature points in segment order, and per-segment moments
-// W_n = sum w_q, R_n = sum w_q (X_q - x0_b) accumulated in ascending q.
-__global__ void k_gather(int64_t Q, const int32_t *__restrict__ perm, const D4 *__restrict__ Xw,
-                         D4 *__restrict__ Xs)
-{
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < Q) Xs[p] = Xw[perm[p]];
-}
-
-__global__ void k_moments(int64_t N, const int32_t *__restrict__ seg_ptr, const D4 *__restrict__ Xs,
-                          const int32_t *__restrict__ body_x, const double *__restrict__ x0,
-                          double *__restrict__ W, double *__restrict__ R)
+// W_n = sum w_q, R_n = sum w_q (X_q - x0_b) accumulated in ascending q: one
+// thread per segment gathers its points and sums them.  Quadrature points
+// left out of every segment (no valid nearest force point) are not gathered.
+__global__ void k_gather_moments(int64_t N, const int32_t *__restrict__ seg_ptr,
+                                 const int32_t *__restrict__ perm, const D4 *__restrict__ Xw,
+                                 D4 *__restrict__ Xs, const int32_t *__restrict__ body_x,
+                                 const double *__restrict__ x0, double *__restrict__ W,
+                                 double *__restrict__ R)
 {
     int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     const double *o = x0 + 3 * body_x[n];
     double w_sum = 0.0, r0 = 0.0, r1 = 0.0, r2 = 0.0;
     for (int32_t p = seg_ptr[n]; p < seg_ptr[n + 1]; ++p) {
-        D4 X = Xs[p];
+        const D4 X = Xw[perm[p]];
+        Xs[p] = X;
         w_sum = __dadd_rn(w_sum, X.w);
         r0 = __dadd_rn(r0, __dmul_rn(X.w, __dsub_rn(X.x, o[0])));
         r1 = __dadd_rn(r1, __dmul_rn(X.w, __dsub_rn(X.y, o[1])));
@@ -357,13 +355,12 @@ __global__ void k_moments(int64_t N, const int32_t *__restrict__ seg_ptr, const 
 
 void launch_gather(Ctx &c, const D4 *Xw_lab, const int32_t *seg_ptr, const int32_t *perm)
 {
-    int threads = 256;
+    int threads = 128;
     c.tbeg(PH_SEGMENTS);
-    k_gather<<<(unsigned)ceil_div(c.Q, threads), threads, 0, c.stream>>>(c.Q, perm, Xw_lab, c.d_Xs);
-    k_moments<<<(unsigned)ceil_div(c.N, threads), threads, 0, c.stream>>>(
-        c.N, seg_ptr, c.d_Xs, c.d_body_x, c.d_x0, c.d_W, c.d_R);
+    k_gather_moments<<<(unsigned)ceil_div(c.N, threads), threads, 0, c.stream>>>(
+        c.N, seg_ptr, perm, Xw_lab, c.d_Xs, c.d_body_x, c.d_x0, c.d_W, c.d_R);
     c.tend(PH_SEGMENTS);
-    c.launches += 2;
+    c.launches += 1;
 }
 
 // ---------------------------------------------------------------------------
