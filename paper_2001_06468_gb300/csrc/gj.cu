@@ -410,14 +410,88 @@ __device__ __forceinline__ void gj_prep_tile(int64_t n, const float *M, int64_t 
     }
 }
 
+// The R part of a prep tile for one 16-column slice (columns t0 + 16 s ..
+// t0 + 16 s + 15): four CTAs share a tile's product.  Each entry gets the same
+// FMA sequence as in gj_prep_tile.
+__device__ __forceinline__ void gj_prep_slice(int64_t n, const float *M, int64_t lda, int64_t k0,
+                                              const float *Dinv, float *Rt, const float *stage,
+                                              int64_t t0, int s, float *sbuf, float *Rt_lo)
+{
+    constexpr int NB = GJ_NB, SW = 16;
+    float(*DT)[NB + 4] = reinterpret_cast<float(*)[NB + 4]>(sbuf);
+    float(*MK)[NB + 4] = reinterpret_cast<float(*)[NB + 4]>(sbuf + NB * (NB + 4));
+    const int tid = threadIdx.x;
+    const int kb = (int)min((int64_t)NB, n - k0);
+    const int nt = (int)min((int64_t)NB, n - t0);
+    const bool staged = stage && t0 == k0 - NB;
+    const bool tile_is_k = (t0 == k0);
+    {
+        const float *src = staged ? stage + NB * NB : M + k0 + t0 * lda;
+        const int64_t ld = staged ? NB : lda;
+        float dv[16], mv[4];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int idx = tid + 256 * q, a = idx & 63, b = idx >> 6;
+            dv[q] = __ldcg(Dinv + b * NB + a);  // D^{-1}[b][a]
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int idx = tid + 256 * q, a = idx & 63, b = SW * s + (idx >> 6);
+            mv[q] = (a < kb && b < nt) ? __ldcg(src + a + b * ld) : 0.0f;  // M[K+a][t0+b]
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int idx = tid + 256 * q;
+            DT[idx & 63][idx >> 6] = dv[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int idx = tid + 256 * q;
+            MK[idx & 63][idx >> 6] = mv[q];
+        }
+    }
+    __syncthreads();
+    // thread computes R[r0 + x][t0 + 16 s + c] for x = 0..3
+    const int r0 = 4 * (tid & 15), c = tid >> 4;
+    float acc[4] = {};
+#pragma unroll 8
+    for (int t = 0; t < NB; ++t) {
+        const float4 a4 = *reinterpret_cast<const float4 *>(&DT[t][r0]);
+        const float b = MK[t][c];
+        acc[0] = fmaf(a4.x, b, acc[0]);
+        acc[1] = fmaf(a4.y, b, acc[1]);
+        acc[2] = fmaf(a4.z, b, acc[2]);
+        acc[3] = fmaf(a4.w, b, acc[3]);
+    }
+    const int col = SW * s + c;
+    if (col >= nt) return;
+    float v[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) v[x] = (tile_is_k || r0 + x >= kb) ? 0.0f : acc[x];
+    if (Rt_lo) {
+        float h[4], l[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) tcp::split_tf32(v[x], h[x], l[x]);
+        *reinterpret_cast<float4 *>(&Rt[(t0 + col) * NB + r0]) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4 *>(&Rt_lo[(t0 + col) * NB + r0]) = make_float4(l[0], l[1], l[2], l[3]);
+    } else {
+        *reinterpret_cast<float4 *>(&Rt[(t0 + col) * NB + r0]) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
+// grid.y = 0..3: the R panel of tile t0, one 16-column slice each; grid.y = 4:
+// the C panel of tile t0.
 __global__ void __launch_bounds__(256)
     k_gj_prep(int64_t n, const float *M, int64_t lda, int64_t k0, const float *Dinv, float *Rt,
               float *Cb, const float *stage, float *Rt_lo, float *Cb_lo)
 {
     __shared__ __align__(16) float sbuf[2 * GJ_NB * (GJ_NB + 4)];
     const int64_t t0 = (int64_t)blockIdx.x * GJ_NB;
-    if (t0 < n)
-        gj_prep_tile(n, M, lda, k0, Dinv, Rt, Cb, stage, t0, (int)blockIdx.y, sbuf, Rt_lo, Cb_lo);
+    if (t0 >= n) return;
+    if (blockIdx.y == 4)
+        gj_prep_tile(n, M, lda, k0, Dinv, Rt, Cb, stage, t0, 1, sbuf, Rt_lo, Cb_lo);
+    else
+        gj_prep_slice(n, M, lda, k0, Dinv, Rt, stage, t0, (int)blockIdx.y, sbuf, Rt_lo);
 }
 
 // M[i, j] -= sum_c Cb[i,c] Rt[j,c] on the CUDA cores (64 x 64 tiles); tiles in
@@ -1053,7 +1127,7 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
             c.launches += 1;
         }
         c.tbeg(PH_LU_PANEL);
-        k_gj_prep<<<dim3(gcols, 2), 256, 0, c.stream>>>(n, M, lda, k0, dinv[b], rt[b], cb[b],
+        k_gj_prep<<<dim3(gcols, 5), 256, 0, c.stream>>>(n, M, lda, k0, dinv[b], rt[b], cb[b],
                                                         kstep > 0 ? stg[b] : nullptr,
                                                         split ? rt_lo[b] : nullptr,
                                                         split ? cb_lo[b] : nullptr);
