@@ -278,13 +278,13 @@ __device__ __forceinline__ void gj_diag_block(int64_t n, const float *M, int64_t
         }
         // row mypos of D^{-1}, column pivrow[d] = T[d] * scale: through shared
         // memory (B0, read into the registers before the loop) so that the global
-        // stores are coalesced
+        // stores are coalesced and shared by all 256 threads
 #pragma unroll
         for (int d = 0; d < NB; ++d) sm0[mypos][pivrow[d]] = T[d] * scale;
-        asm volatile("bar.sync 1, 64;" ::: "memory");
-        for (int i = 0; i < NB; ++i) Dinv[i * NB + tid] = sm0[i][tid];
     }
     __syncthreads();
+    for (int i = tid; i < NB * NB; i += 256) Dinv[i] = sm0[i >> 6][i & 63];
+    __syncthreads();  // the caller may reuse sraw
 }
 
 __global__ void __launch_bounds__(256)
