@@ -534,8 +534,9 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
     // nearest-neighbour tasks: 128 quadrature points of one body each
     std::vector<nrs::NNTask> all, deform;
     for (int b = 0; b < d->nbodies; ++b)
-        for (int64_t q0 = d->q_off[b]; q0 < d->q_off[b + 1]; q0 += 128) {
-            nrs::NNTask t{b, (int32_t)q0, (int32_t)std::min<int64_t>(q0 + 128, d->q_off[b + 1]), 0};
+        for (int64_t q0 = d->q_off[b]; q0 < d->q_off[b + 1]; q0 += nrs::NN_QPB) {
+            nrs::NNTask t{b, (int32_t)q0,
+                          (int32_t)std::min<int64_t>(q0 + nrs::NN_QPB, d->q_off[b + 1]), 0};
             all.push_back(t);
             if (!c->rigid[b] || c->nn_global) deform.push_back(t);
         }

@@ -109,9 +109,6 @@ void launch_kinematics(Ctx &c, const D4 *xi, const D4 *Xiw, const D4 *xidot, D4 
 // index order.  The 1e-6 factors dominate every FP32 rounding of the bound
 // itself (u = 2^-24 ~ 6e-8), so the result equals an exhaustive FP64 search.
 
-constexpr int NN_QPB = 128;    // quadrature points per task (one block)
-constexpr int NN_SPLIT = 4;    // threads per quadrature point, each taking every NN_SPLIT-th candidate
-constexpr int NN_THREADS = NN_QPB * NN_SPLIT;
 constexpr int NN_TILE = 512;
 
 // The NN_SPLIT threads of a quadrature point are consecutive lanes; each scans

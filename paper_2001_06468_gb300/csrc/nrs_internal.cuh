@@ -38,6 +38,11 @@ constexpr long long kSpinLimit = 1LL << 24;
 struct NNTask {
     int32_t body, q0, q1, pad;
 };
+// A nearest-neighbour task (one block of k_nearest) covers NN_QPB quadrature
+// points of one body, with NN_SPLIT threads per point.
+constexpr int NN_QPB = 128;
+constexpr int NN_SPLIT = 4;
+constexpr int NN_THREADS = NN_QPB * NN_SPLIT;
 
 struct Ctx;
 

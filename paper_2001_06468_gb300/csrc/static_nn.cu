@@ -31,7 +31,7 @@ namespace {
 constexpr int64_t kMaxN = NRS_STATIC_MAX_N;
 constexpr int64_t kMaxQ = NRS_STATIC_MAX_Q;
 constexpr int kMaxBodies = NRS_STATIC_MAX_BODIES;
-constexpr int64_t kMaxTasks = kMaxQ / 128 + kMaxBodies;
+constexpr int64_t kMaxTasks = kMaxQ / NN_QPB + kMaxBodies;
 
 // The scratch.  Host code must not pass these names to a kernel: on the host
 // they are stand-ins, not device addresses.  Their device addresses come from
@@ -74,7 +74,7 @@ cudaError_t setup_device(int dev, DevScratch **out)
     return cudaSuccess;
 }
 
-// Block tasks (128 quadrature points of one body each) from the body offsets,
+// Block tasks (NN_QPB quadrature points of one body each) from the body offsets,
 // written by one thread into the static task table.
 __global__ void k_static_tasks(int nbodies, const int64_t *__restrict__ q_off,
                                NNTask *__restrict__ tasks)
@@ -82,8 +82,8 @@ __global__ void k_static_tasks(int nbodies, const int64_t *__restrict__ q_off,
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     int64_t t = 0;
     for (int b = 0; b < nbodies; ++b)
-        for (int64_t q0 = q_off[b]; q0 < q_off[b + 1]; q0 += 128)
-            tasks[t++] = NNTask{b, (int32_t)q0, (int32_t)min(q0 + 128, q_off[b + 1]), 0};
+        for (int64_t q0 = q_off[b]; q0 < q_off[b + 1]; q0 += NN_QPB)
+            tasks[t++] = NNTask{b, (int32_t)q0, (int32_t)min(q0 + NN_QPB, q_off[b + 1]), 0};
 }
 
 }  // namespace
@@ -102,7 +102,7 @@ extern "C" nrs_status nrs_nearest_build_static(const double *x, const double *Xw
     for (int b = 0; b < nbodies; ++b) {
         if (n_off[b + 1] < n_off[b] || q_off[b + 1] < q_off[b]) return NRS_EINVAL;
         if (!global && q_off[b + 1] > q_off[b] && n_off[b + 1] == n_off[b]) return NRS_EINVAL;
-        ntasks += (q_off[b + 1] - q_off[b] + 127) / 128;
+        ntasks += (q_off[b + 1] - q_off[b] + NN_QPB - 1) / NN_QPB;
     }
     const int64_t N = n_off[nbodies], Q = q_off[nbodies];
     if (N <= 0 || Q <= 0 || N > kMaxN || Q > kMaxQ || ntasks > kMaxTasks) return NRS_EINVAL;
@@ -120,7 +120,7 @@ extern "C" nrs_status nrs_nearest_build_static(const double *x, const double *Xw
     cudaMemsetAsync(s->cursor, 0, sizeof(int32_t) * (N + 1), st);
     cudaMemsetAsync(perm, 0, sizeof(int32_t) * Q, st);
     k_static_tasks<<<1, 1, 0, st>>>(nbodies, s->q_off, s->tasks);
-    k_nearest<<<(unsigned)ntasks, 128, 0, st>>>(s->tasks, s->n_off, nbodies, global ? 1 : 0,
+    k_nearest<<<(unsigned)ntasks, NN_THREADS, 0, st>>>(s->tasks, s->n_off, nbodies, global ? 1 : 0,
                                                  (const D4 *)x, (const D4 *)Xw, nn, s->status);
     const int threads = 256;
     k_count<<<(unsigned)ceil_div(Q, threads), threads, 0, st>>>(Q, N, nn, s->cursor);
