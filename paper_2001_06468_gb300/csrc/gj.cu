@@ -413,9 +413,13 @@ __device__ __forceinline__ void gj_prep_tile(int64_t n, const float *M, int64_t 
 // The R part of a prep tile for one 16-column slice (columns t0 + 16 s ..
 // t0 + 16 s + 15): four CTAs share a tile's product.  Each entry gets the same
 // FMA sequence as in gj_prep_tile.
-__device__ __forceinline__ void gj_prep_slice(int64_t n, const float *M, int64_t lda, int64_t k0,
+// It also finishes block row K for these columns (M[K, :] <- R, M[K,K] <-
+// D^{-1}), except for the tile at skip_t0 (the next block's, which its
+// diagonal inverse stages): the finish then only does the block column.
+__device__ __forceinline__ void gj_prep_slice(int64_t n, float *M, int64_t lda, int64_t k0,
                                               const float *Dinv, float *Rt, const float *stage,
-                                              int64_t t0, int s, float *sbuf, float *Rt_lo)
+                                              int64_t t0, int s, float *sbuf, float *Rt_lo,
+                                              int64_t skip_t0)
 {
     constexpr int NB = GJ_NB, SW = 16;
     float(*DT)[NB + 4] = reinterpret_cast<float(*)[NB + 4]>(sbuf);
@@ -468,6 +472,21 @@ __device__ __forceinline__ void gj_prep_slice(int64_t n, const float *M, int64_t
     float v[4];
 #pragma unroll
     for (int x = 0; x < 4; ++x) v[x] = (tile_is_k || r0 + x >= kb) ? 0.0f : acc[x];
+    if (t0 != skip_t0) {
+        // block row K of M, column t0 + col: R, or D^{-1} in the diagonal tile
+        float mo[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+            mo[x] = tile_is_k ? (col < kb ? __ldcg(Dinv + (r0 + x) * NB + col) : 0.0f) : v[x];
+        float *dst = M + (k0 + r0) + (t0 + col) * lda;
+        if (r0 + 3 < kb && !(tile_is_k && col >= kb)) {
+            *reinterpret_cast<float4 *>(dst) = make_float4(mo[0], mo[1], mo[2], mo[3]);
+        } else {
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+                if (r0 + x < kb && !(tile_is_k && col >= kb)) dst[x] = mo[x];
+        }
+    }
     if (Rt_lo) {
         float h[4], l[4];
 #pragma unroll
@@ -482,8 +501,8 @@ __device__ __forceinline__ void gj_prep_slice(int64_t n, const float *M, int64_t
 // grid.y = 0..3: the R panel of tile t0, one 16-column slice each; grid.y = 4:
 // the C panel of tile t0.
 __global__ void __launch_bounds__(256)
-    k_gj_prep(int64_t n, const float *M, int64_t lda, int64_t k0, const float *Dinv, float *Rt,
-              float *Cb, const float *stage, float *Rt_lo, float *Cb_lo)
+    k_gj_prep(int64_t n, float *M, int64_t lda, int64_t k0, const float *Dinv, float *Rt,
+              float *Cb, const float *stage, float *Rt_lo, float *Cb_lo, int64_t skip_t0)
 {
     __shared__ __align__(16) float sbuf[2 * GJ_NB * (GJ_NB + 4)];
     const int64_t t0 = (int64_t)blockIdx.x * GJ_NB;
@@ -491,7 +510,7 @@ __global__ void __launch_bounds__(256)
     if (blockIdx.y == 4)
         gj_prep_tile(n, M, lda, k0, Dinv, Rt, Cb, stage, t0, 1, sbuf, Rt_lo, Cb_lo);
     else
-        gj_prep_slice(n, M, lda, k0, Dinv, Rt, stage, t0, (int)blockIdx.y, sbuf, Rt_lo);
+        gj_prep_slice(n, M, lda, k0, Dinv, Rt, stage, t0, (int)blockIdx.y, sbuf, Rt_lo, skip_t0);
 }
 
 // M[i, j] -= sum_c Cb[i,c] Rt[j,c] on the CUDA cores (64 x 64 tiles); tiles in
@@ -639,10 +658,9 @@ __device__ __forceinline__ void gj_finish_tile(int64_t n, float *M, int64_t lda,
     }
 }
 
-// Block row K <- R, block column K <- -C D^{-1}, M[K,K] <- D^{-1}, in 64-wide
-// tiles.  grid.y = 0: column tile t0 of block row K; grid.y = 1: row tile t0
-// of block column K.  The tiles at skip_t0 (the next block, whose diagonal
-// inverse computes them and leaves them for the next prep) are not written.
+// Block column K <- -C D^{-1}, in 64-row tiles (the prep has finished block
+// row K and the diagonal tile).  The tile at skip_t0 (the next block, whose
+// diagonal inverse computes it and leaves it for the next prep) is not written.
 __global__ void __launch_bounds__(256)
     k_gj_finish(int64_t n, float *M, int64_t lda, int64_t k0, const float *Dinv, const float *Rt,
                 const float *Cb, int64_t skip_t0, const float *Rt_lo, const float *Cb_lo)
@@ -650,7 +668,7 @@ __global__ void __launch_bounds__(256)
     __shared__ __align__(16) float sbuf[2 * GJ_NB * (GJ_NB + 4)];
     const int64_t t0 = (int64_t)blockIdx.x * GJ_NB;
     if (t0 < n && t0 != skip_t0)
-        gj_finish_tile(n, M, lda, k0, Dinv, Rt, Cb, t0, (int)blockIdx.y, sbuf, Rt_lo, Cb_lo);
+        gj_finish_tile(n, M, lda, k0, Dinv, Rt, Cb, t0, 1, sbuf, Rt_lo, Cb_lo);
 }
 
 // Tensor-core version of the update (tc_gemm.cu); false if not available for
@@ -1049,9 +1067,10 @@ bool run_gj_fused(Ctx &c, float *M, int64_t lda)
 //       diagonal inverse of K+1 with its lookahead from D_K^{-1} and the
 //       un-finished block row and column K; it also leaves the two finished
 //       tiles M[K,K+1], M[K+1,K] in stage[k+1 mod 2]              -> ev_diag
-//   S : prep_k: the panels R = D_K^{-1} M[K,:], C = M[:,K]    -> ev_fin_ready
-//   S4: finish_k: block row K <- R, block column K <- -C D_K^{-1},
-//       M[K,K] <- D_K^{-1}, all but the two staged tiles      -> ev_fin[k mod 2]
+//   S : prep_k: the panels R = D_K^{-1} M[K,:], C = M[:,K]; block row K
+//       <- R and M[K,K] <- D_K^{-1} (but the staged tile)     -> ev_fin_ready
+//   S4: finish_k: block column K <- -C D_K^{-1} (but the staged
+//       tile)                                                 -> ev_fin[k mod 2]
 //   S : (waits finish_{k-1}) update_k, M -= C R over all of M but block row
 //       and column K and the block (K+1,K+1)                       -> ev_upd
 //   S : waits ev_diag before prep_{k+1}.
@@ -1130,12 +1149,13 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
         k_gj_prep<<<dim3(gcols, 5), 256, 0, c.stream>>>(n, M, lda, k0, dinv[b], rt[b], cb[b],
                                                         kstep > 0 ? stg[b] : nullptr,
                                                         split ? rt_lo[b] : nullptr,
-                                                        split ? cb_lo[b] : nullptr);
+                                                        split ? cb_lo[b] : nullptr,
+                                                        next ? k1 : -1);
         c.tend(PH_LU_PANEL);
         cudaEventRecord(c.ev_fin_ready, c.stream);
         cudaStreamWaitEvent(c.stream4, c.ev_fin_ready, 0);
         c.tbeg(PH_LU_PANEL, c.stream4);
-        k_gj_finish<<<dim3(gcols, 2), 256, 0, c.stream4>>>(n, M, lda, k0, dinv[b], rt[b], cb[b],
+        k_gj_finish<<<dim3(gcols, 1), 256, 0, c.stream4>>>(n, M, lda, k0, dinv[b], rt[b], cb[b],
                                                            next ? k1 : -1,
                                                            split ? rt_lo[b] : nullptr,
                                                            split ? cb_lo[b] : nullptr);
