@@ -199,7 +199,8 @@ nrs_status do_factor(Ctx *c, int prec)
             c->tend(nrs::PH_CONVERT);
             c->launches += 1;
         }
-        nrs::run_gj_fp32(*c, c->d_A32, c->lda, prec);
+        if (nrs::run_gj_fp32(*c, c->d_A32, c->lda, prec) != 0)
+            return fail(c, NRS_EINVAL, "nrs_factor: the tensor-core update could not be launched");
         c->a32_fresh = false;
     }
     CK(cudaGetLastError());

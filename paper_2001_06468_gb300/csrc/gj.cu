@@ -1119,6 +1119,7 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
     cudaEventRecord(c.ev_upd, c.stream);
     c.launches += 1;
     int kstep = 0;
+    bool failed = false;
     for (int64_t k0 = 0; k0 < n; k0 += GJ_NB, ++kstep) {
         const int b = kstep & 1;
         const int64_t k1 = k0 + GJ_NB;
@@ -1167,7 +1168,7 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
         if (split) {
             // split panels have no CUDA-core fallback: a failed launch is an error
             if (!launch_tc_gj_update(c, M, lda, k0, cb[b], rt[b], prec, skip0, cb_lo[b], rt_lo[b]))
-                cudaMemsetAsync(c.d_info, 0xff, sizeof(int32_t), c.stream);
+                failed = true;
         } else {
             k_gj_update_simt<<<dim3(gcols, gcols), 256, 0, c.stream>>>(n, M, lda, k0, cb[b], rt[b],
                                                                         skip0);
@@ -1178,7 +1179,7 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
         else cudaStreamWaitEvent(c.stream, c.ev_fin[b], 0);
         c.launches += 3;
     }
-    return 0;
+    return failed ? -1 : 0;
 }
 
 }  // namespace nrs
