@@ -179,36 +179,40 @@ __global__ void __launch_bounds__(AS_THREADS)
     const int32_t qbeg = sp[0], qend = sp[nt];
     for (int32_t c0 = qbeg; c0 < qend; c0 += AS_CHUNK) {
         const int cnt = min(AS_CHUNK, qend - c0);
+        const int32_t cend = c0 + cnt;
         __syncthreads();
         for (int i = threadIdx.x; i < cnt; i += AS_THREADS) {
             sH[i] = Xh[c0 + i];
             sL[i] = Xl[c0 + i];
         }
         __syncthreads();
-        int32_t next = sp[cur + 1];
-        for (int i = 0; i < cnt; ++i) {
-            const int32_t q = c0 + i;
-            while (q >= next) {  // uniform across the block
-                if (active) flush(n0 + cur);
-                axx = axy = axz = ayy = ayz = azz = ad = 0.0f;
-                ++cur;
-                next = sp[cur + 1];
+        // segment by segment (bounds uniform across the block), so that the
+        // loop over a segment's points has no branch and the independent work
+        // of consecutive points overlaps; the sums still run in ascending q
+        while (cur < nt) {
+            const int32_t sb = max(sp[cur], c0), se = min(sp[cur + 1], cend);
+#pragma unroll 4
+            for (int32_t q = sb; q < se; ++q) {
+                const float4 H = sH[q - c0], Lo = sL[q - c0];
+                const float rx = (ph.x - H.x) + (pl.x - Lo.x);
+                const float ry = (ph.y - H.y) + (pl.y - Lo.y);
+                const float rz = (ph.z - H.z) + (pl.z - Lo.z);
+                const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                const float inv = rsqrtf(r2 + eps2);
+                const float t = H.w * (inv * inv * inv);
+                const float tx = rx * t, ty = ry * t, tz = rz * t;
+                axx = fmaf(rx, tx, axx);
+                axy = fmaf(rx, ty, axy);
+                axz = fmaf(rx, tz, axz);
+                ayy = fmaf(ry, ty, ayy);
+                ayz = fmaf(ry, tz, ayz);
+                azz = fmaf(rz, tz, azz);
+                ad = fmaf(r2 + two_e2, t, ad);
             }
-            const float4 H = sH[i], Lo = sL[i];
-            const float rx = (ph.x - H.x) + (pl.x - Lo.x);
-            const float ry = (ph.y - H.y) + (pl.y - Lo.y);
-            const float rz = (ph.z - H.z) + (pl.z - Lo.z);
-            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-            const float inv = rsqrtf(r2 + eps2);
-            const float t = H.w * (inv * inv * inv);
-            const float tx = rx * t, ty = ry * t, tz = rz * t;
-            axx = fmaf(rx, tx, axx);
-            axy = fmaf(rx, ty, axy);
-            axz = fmaf(rx, tz, axz);
-            ayy = fmaf(ry, ty, ayy);
-            ayz = fmaf(ry, tz, ayz);
-            azz = fmaf(rz, tz, azz);
-            ad = fmaf(r2 + two_e2, t, ad);
+            if (sp[cur + 1] > cend) break;  // the segment continues in the next chunk
+            if (active) flush(n0 + cur);
+            axx = axy = axz = ayy = ayz = azz = ad = 0.0f;
+            ++cur;
         }
     }
     while (cur < nt) {
