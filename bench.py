@@ -64,6 +64,27 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(x: float, ws: int, device: str = "cuda") -> float:
+    """The largest x over the ranks of the default process group (x itself
+    on one rank): the whole job's time is that of its slowest rank."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _rank_share(costs, ws: int, rank: int):
+    """The problems a rank steps when a batch is split over ws ranks: the
+    longest-processing-time-first plan of the library (nrs_batch_plan) with
+    one chain per rank, no collective in the data path."""
+    from paper_2001_06468_gb300 import nrs
+    chain_of, _ = nrs.batch_plan(list(costs), ws)
+    return [i for i, ch in enumerate(chain_of) if ch == rank]
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -381,12 +402,7 @@ def run_nrs(args):
         "inner_mean": float(np.mean([r["stages"][i]["inner"] for r in instr_reports for i in (0, 1)]))}
     ctx_t.set_timing(False)
     t_local = sum(step_ms) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t_local], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-    else:
-        t_max = t_local
+    t_max = _max_over_ranks(t_local, ws)
     s_per_step = t_max / K / ws  # whole job: ws replicas each advance K steps
 
     # end to end through the C ABI from pinned host buffers: H2D of both
