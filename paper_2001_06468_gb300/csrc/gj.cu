@@ -21,6 +21,224 @@ namespace nrs {
 
 constexpr int GJ_NB = 64;
 
+// Shared state of the pipelined elimination below (dynamic shared memory of
+// k_gj_diag): per pivot step c an mbarrier, the 64 multipliers, the pivot row
+// and 1/pivot; per warp a double-buffered copy of the pivot row's half.
+struct GjElimSmem {
+    uint64_t bar[GJ_NB];             // step c published (32 arrivals of the leader's lanes)
+    float2 f[GJ_NB][32];             // step c: multipliers of rows l (x) and l + 32 (y)
+    __align__(16) float prow[2][2][36];  // [warp][step parity]: the pivot row's half, 1/pivot
+    int piv[GJ_NB];                  // pivot row of step c
+    float rpiv[GJ_NB];               // 1/pivot of step c
+};
+
+__device__ __forceinline__ void gje_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tcp::smem_u32(bar)) : "memory");
+}
+
+// The elimination of gj_diag_block (threads 0..63) as a two-warp pipeline.
+// Warp w holds columns [32 w, 32 w + 32) of all 64 rows; lane l holds rows l
+// (X0) and l + 32 (X1).  The 32 steps of the columns in a warp's own half are
+// led by that warp: it finds the pivot by itself (the unused row of largest
+// |T[c]|, lowest row on ties: one warp max-reduction and two ballots, no
+// barrier), passes the pivot row's half to its lanes through shared memory,
+// updates its half with its registers rotating as in the one-row-per-lane
+// form, and publishes the step -- pivot row, 1/pivot and the 64 multipliers
+// f_i = T_i[c] / T_p[c] (0 for the pivot row) -- in a slot of its own,
+// completed by an mbarrier.  The other warp follows: it waits for each slot
+// (reading the next one while the current update runs), passes the pivot
+// row's other half among its lanes and applies T_i[j] -= f_i T_p[j] to all of
+// its columns.  The leader never waits for the follower (one slot per step),
+// so the two warps' updates overlap and a pivot step costs one warp's search
+// plus half a row of updates.  At column 32 the warps swap roles.  Every
+// element goes through the same operations as in the one-row-per-lane form
+// (same pivot, same multiplier, same fmaf, same deferred scaling), so the
+// result is the same bit for bit.  A slot wait that runs out sets
+// ST_TIMEOUT in `status` and ends the elimination.
+__device__ __forceinline__ void gj_elim_split(float (*sm0)[GJ_NB + 1], GjElimSmem &E, int64_t k0,
+                                              int32_t *info, int32_t *status)
+{
+    constexpr int NB = GJ_NB, H = 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __shared__ unsigned zat[2];
+    float X0[H], X1[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        X0[j] = sm0[lane][H * w + j];
+        X1[j] = sm0[lane + H][H * w + j];
+    }
+    bool used0 = false, used1 = false;
+    float scale0 = 1.0f, scale1 = 1.0f;
+    int pos0 = 0, pos1 = 0;
+    unsigned zero_at = 0xffffffffu;  // step of a zero pivot in this lane's rows, if any
+    bool ok = true;
+    for (int ph = 0; ph < 2 && ok; ++ph) {
+        if (w == ph) {
+#pragma unroll 8
+            for (int s = 0; s < H; ++s) {
+                const int c = H * ph + s, b = c & 1;
+                const float colv0 = X0[0], colv1 = X1[0];
+                const float myr0 = 1.0f / colv0, myr1 = 1.0f / colv1;
+                const unsigned key0 = used0 ? 0u : (0x80000000u | __float_as_uint(fabsf(colv0)));
+                const unsigned key1 = used1 ? 0u : (0x80000000u | __float_as_uint(fabsf(colv1)));
+                const unsigned mx = __reduce_max_sync(0xffffffffu, max(key0, key1));
+                const unsigned bal0 = __ballot_sync(0xffffffffu, key0 == mx);
+                const unsigned bal1 = __ballot_sync(0xffffffffu, key1 == mx);
+                // rows l come before rows l + 32
+                const int p = bal0 ? __ffs(bal0) - 1 : H - 1 + __ffs(bal1);
+                const bool in1 = p >= H;
+                float4 *buf = reinterpret_cast<float4 *>(&E.prow[w][b][0]);
+                if (lane == (p & (H - 1))) {
+                    if (in1) {
+#pragma unroll
+                        for (int q = 0; q < H / 4; ++q)
+                            buf[q] = make_float4(X1[4 * q], X1[4 * q + 1], X1[4 * q + 2], X1[4 * q + 3]);
+                        buf[H / 4] = make_float4(myr1, 0.0f, 0.0f, 0.0f);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < H / 4; ++q)
+                            buf[q] = make_float4(X0[4 * q], X0[4 * q + 1], X0[4 * q + 2], X0[4 * q + 3]);
+                        buf[H / 4] = make_float4(myr0, 0.0f, 0.0f, 0.0f);
+                    }
+                }
+                __syncwarp();
+                const float rpiv = E.prow[w][b][H];
+                float4 v[H / 4];
+#pragma unroll
+                for (int q = 0; q < H / 4; ++q) v[q] = buf[q];
+                const bool is0 = !in1 && lane == p, is1 = in1 && lane == p - H;
+                const float f0 = is0 ? 0.0f : colv0 * rpiv;
+                const float f1 = is1 ? 0.0f : colv1 * rpiv;
+                E.f[c][lane] = make_float2(f0, f1);
+                if (lane == 0) {
+                    E.piv[c] = p;
+                    E.rpiv[c] = rpiv;
+                }
+                gje_arrive(&E.bar[c]);
+                if (is0) {
+                    used0 = true;
+                    scale0 = rpiv;
+                    pos0 = c;
+                    if (colv0 == 0.0f) zero_at = (unsigned)c;
+                }
+                if (is1) {
+                    used1 = true;
+                    scale1 = rpiv;
+                    pos1 = c;
+                    if (colv1 == 0.0f) zero_at = (unsigned)c;
+                }
+                // the next pivot column first
+                X0[1] = fmaf(-f0, v[0].y, X0[1]);
+                X1[1] = fmaf(-f1, v[0].y, X1[1]);
+                X0[2] = fmaf(-f0, v[0].z, X0[2]);
+                X1[2] = fmaf(-f1, v[0].z, X1[2]);
+                X0[3] = fmaf(-f0, v[0].w, X0[3]);
+                X1[3] = fmaf(-f1, v[0].w, X1[3]);
+#pragma unroll
+                for (int q = 1; q < H / 4; ++q) {
+                    X0[4 * q] = fmaf(-f0, v[q].x, X0[4 * q]);
+                    X0[4 * q + 1] = fmaf(-f0, v[q].y, X0[4 * q + 1]);
+                    X0[4 * q + 2] = fmaf(-f0, v[q].z, X0[4 * q + 2]);
+                    X0[4 * q + 3] = fmaf(-f0, v[q].w, X0[4 * q + 3]);
+                    X1[4 * q] = fmaf(-f1, v[q].x, X1[4 * q]);
+                    X1[4 * q + 1] = fmaf(-f1, v[q].y, X1[4 * q + 1]);
+                    X1[4 * q + 2] = fmaf(-f1, v[q].z, X1[4 * q + 2]);
+                    X1[4 * q + 3] = fmaf(-f1, v[q].w, X1[4 * q + 3]);
+                }
+#pragma unroll
+                for (int j = 0; j < H - 1; ++j) {
+                    X0[j] = X0[j + 1];
+                    X1[j] = X1[j + 1];
+                }
+                X0[H - 1] = is0 ? 1.0f : -f0;
+                X1[H - 1] = is1 ? 1.0f : -f1;
+            }
+        } else {
+            const int c0 = H * ph;
+            bool got = tcp::mbar_wait(&E.bar[c0], 0);
+            if (!__all_sync(0xffffffffu, got)) {
+                ok = false;
+                break;
+            }
+            int pn = E.piv[c0];
+            float rpn = E.rpiv[c0];
+            float2 fn = E.f[c0][lane];
+#pragma unroll 4
+            for (int s = 0; s < H; ++s) {
+                const int c = c0 + s, b = c & 1;
+                const int p = pn;
+                const float rp = rpn;
+                const float2 f = fn;
+                const bool in1 = p >= H;
+                float4 *buf = reinterpret_cast<float4 *>(&E.prow[w][b][0]);
+                if (lane == (p & (H - 1))) {
+                    if (in1) {
+#pragma unroll
+                        for (int q = 0; q < H / 4; ++q)
+                            buf[q] = make_float4(X1[4 * q], X1[4 * q + 1], X1[4 * q + 2], X1[4 * q + 3]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < H / 4; ++q)
+                            buf[q] = make_float4(X0[4 * q], X0[4 * q + 1], X0[4 * q + 2], X0[4 * q + 3]);
+                    }
+                }
+                __syncwarp();
+                float4 v[H / 4];
+#pragma unroll
+                for (int q = 0; q < H / 4; ++q) v[q] = buf[q];
+                if (s + 1 < H) {
+                    got = tcp::mbar_wait(&E.bar[c + 1], 0);
+                    if (!__all_sync(0xffffffffu, got)) {
+                        ok = false;
+                        break;
+                    }
+                    pn = E.piv[c + 1];
+                    rpn = E.rpiv[c + 1];
+                    fn = E.f[c + 1][lane];
+                }
+                if (!in1 && lane == p) {
+                    used0 = true;
+                    scale0 = rp;
+                    pos0 = c;
+                }
+                if (in1 && lane == p - H) {
+                    used1 = true;
+                    scale1 = rp;
+                    pos1 = c;
+                }
+#pragma unroll
+                for (int q = 0; q < H / 4; ++q) {
+                    X0[4 * q] = fmaf(-f.x, v[q].x, X0[4 * q]);
+                    X0[4 * q + 1] = fmaf(-f.x, v[q].y, X0[4 * q + 1]);
+                    X0[4 * q + 2] = fmaf(-f.x, v[q].z, X0[4 * q + 2]);
+                    X0[4 * q + 3] = fmaf(-f.x, v[q].w, X0[4 * q + 3]);
+                    X1[4 * q] = fmaf(-f.y, v[q].x, X1[4 * q]);
+                    X1[4 * q + 1] = fmaf(-f.y, v[q].y, X1[4 * q + 1]);
+                    X1[4 * q + 2] = fmaf(-f.y, v[q].z, X1[4 * q + 2]);
+                    X1[4 * q + 3] = fmaf(-f.y, v[q].w, X1[4 * q + 3]);
+                }
+            }
+        }
+    }
+    if (!ok && lane == 0 && status) atomicOr(status, ST_TIMEOUT);
+    zero_at = __reduce_min_sync(0xffffffffu, zero_at);
+    if (lane == 0) zat[w] = zero_at;
+    asm volatile("bar.sync 1, 64;" ::: "memory");  // the pivot order is complete
+    if (threadIdx.x == 0 && info) {
+        const unsigned z = min(zat[0], zat[1]);
+        if (z != 0xffffffffu) atomicCAS(info, 0, (int)(k0 + z + 1));
+    }
+    // row pos of D^{-1}; this warp's column 32 w + j stands for original row
+    // piv[32 w + j] (masked: after a timeout not every slot was written)
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        const int col = E.piv[H * w + j] & (NB - 1);
+        sm0[pos0][col] = X0[j] * scale0;
+        sm0[pos1][col] = X1[j] * scale1;
+    }
+}
+
 // D^{-1} of the 64 x 64 diagonal block by Gauss-Jordan elimination with
 // partial pivoting, written for the latency of one pivot step (this kernel is
 // the critical path of the factorisation: one launch per block column).
@@ -36,8 +254,10 @@ constexpr int GJ_NB = 64;
 // there): stage[0..4096) = R_PK (column-major, 64 x 64) is M[P,K] after step
 // P, and stage[4096..8192) = -M[K,P] Dprev is M[K,P] after step P; the latter
 // is computed by warps 2, 3, 6 and 7 while warps 0 and 1 do the elimination.
-// The elimination: two warps, lane l of warp w holding row r = 32 w + l in
-// registers T[64]:
+// The elimination (SPLIT = false, the fused factorisation, whose 128-register
+// budget it fits; SPLIT = true, k_gj_diag, runs the same arithmetic as the
+// two-warp pipeline gj_elim_split above): two warps, lane l of warp w holding
+// row r = 32 w + l in registers T[64]:
 //  * exchange (sweep) form, in place: at the step for column c with pivot row
 //    p, every other row i gets T_i[j] -= (T_i[c] / T_p[c]) T_p[j] (j != c) and
 //    T_i[c] = -T_i[c] / T_p[c]; the pivot row is divided by T_p[c] and gets
@@ -59,9 +279,11 @@ constexpr int GJ_NB = 64;
 // that other CTAs write is an L2 load (ld.global.cg), so the same code runs
 // inside the fused factorisation.  sraw: two 64 x 68 float buffers in shared
 // memory.
+template <bool SPLIT>
 __device__ __forceinline__ void gj_diag_block(int64_t n, const float *M, int64_t lda,
                                               int64_t k0, float *Dinv, int32_t *info,
-                                              const float *Dprev, float *stage, float *sraw)
+                                              const float *Dprev, float *stage, float *sraw,
+                                              GjElimSmem *E = nullptr, int32_t *status = nullptr)
 {
     constexpr int NB = GJ_NB, LDT = NB + 4;
     // two 64 x 68 buffers: B0 = Dprev^T, then R_PK, then the block D (rows of
@@ -77,6 +299,8 @@ __device__ __forceinline__ void gj_diag_block(int64_t n, const float *M, int64_t
     const int tid = threadIdx.x;
     const int kb = (int)min((int64_t)NB, n - k0);
     const int64_t kp = k0 - NB;
+    if (SPLIT && tid == 0)
+        for (int c = 0; c < NB; ++c) tcp::mbar_init(&E->bar[c], 32);  // ordered by the barriers below
     {
         // thread owns the 4 x 4 tile rows r0..r0+3, columns j0..j0+3
         const int r0 = 4 * (tid >> 4), j0 = 4 * (tid & 15);
@@ -209,6 +433,8 @@ __device__ __forceinline__ void gj_diag_block(int64_t n, const float *M, int64_t
                 *reinterpret_cast<float4 *>(&stx[i0 + (c0 + y) * NB]) =
                     make_float4(-acc[0][y], -acc[1][y], -acc[2][y], -acc[3][y]);
         }
+    } else if (SPLIT) {
+        gj_elim_split(sm0, *E, k0, info, status);
     } else {
         const int w = tid >> 5, r = tid;
         float T[NB];
@@ -287,12 +513,17 @@ __device__ __forceinline__ void gj_diag_block(int64_t n, const float *M, int64_t
     __syncthreads();  // the caller may reuse sraw
 }
 
-__global__ void __launch_bounds__(256)
+// The separate-kernel diagonal inverse, with the pipelined elimination (its
+// slots in the dynamic shared memory, which the launch makes large enough to
+// keep the SM to itself).
+__global__ void __launch_bounds__(256, 1)
     k_gj_diag(int64_t n, const float *M, int64_t lda, int64_t k0, float *Dinv, int32_t *info,
-              const float *Dprev, float *stage)
+              const float *Dprev, float *stage, int32_t *status)
 {
     __shared__ __align__(16) float sraw[2 * GJ_NB * (GJ_NB + 4)];
-    gj_diag_block(n, M, lda, k0, Dinv, info, Dprev, stage, sraw);
+    extern __shared__ __align__(16) uint8_t gj_diag_dyn[];
+    gj_diag_block<true>(n, M, lda, k0, Dinv, info, Dprev, stage, sraw,
+                        reinterpret_cast<GjElimSmem *>(gj_diag_dyn), status);
 }
 
 // Prep of step K.  grid.y = 0: R[:, j] = D^{-1} M[K, j] for one 64-column tile
@@ -932,7 +1163,7 @@ __global__ void __launch_bounds__(GJF_THREADS, 2)
             __syncthreads();
             if (!s_ok) return;
             const int b = k & 1;
-            gj_diag_block(n, a.M, lda, (int64_t)k * NB, a.dinv + b * NB * NB, a.info,
+            gj_diag_block<false>(n, a.M, lda, (int64_t)k * NB, a.dinv + b * NB * NB, a.info,
                           k ? a.dinv + (b ^ 1) * NB * NB : nullptr,
                           k ? a.stage + b * 2 * NB * NB : nullptr, sbuf);
             if (threadIdx.x == 0) {
@@ -1086,6 +1317,7 @@ bool run_gj_fused(Ctx &c, float *M, int64_t lda)
 // largest shared-memory carveout, so that an SM running one of them can
 // still take the diagonal inverse.
 constexpr int GJ_DIAG_EXCL_SMEM = 164 * 1024;
+static_assert(sizeof(GjElimSmem) <= GJ_DIAG_EXCL_SMEM, "the elimination's slots fit");
 
 int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
 {
@@ -1114,7 +1346,8 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
     float *cb_lo[2] = {c.d_gj_cb + (size_t)2 * GJ_NB * c.lda, c.d_gj_cb + (size_t)3 * GJ_NB * c.lda};
     float *stg[2] = {c.d_gj_stage, c.d_gj_stage + 2 * GJ_NB * GJ_NB};
     c.tbeg(PH_LU_DIAG);
-    k_gj_diag<<<1, 256, GJ_DIAG_EXCL_SMEM, c.stream>>>(n, M, lda, 0, dinv[0], c.d_info, nullptr, nullptr);
+    k_gj_diag<<<1, 256, GJ_DIAG_EXCL_SMEM, c.stream>>>(n, M, lda, 0, dinv[0], c.d_info, nullptr, nullptr,
+                                                       c.d_status);
     c.tend(PH_LU_DIAG);
     cudaEventRecord(c.ev_upd, c.stream);
     c.launches += 1;
@@ -1141,7 +1374,7 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             cudaLaunchKernelEx(&cfg, k_gj_diag, (int64_t)n, (const float *)M, (int64_t)lda, (int64_t)k1,
-                               dinv[b ^ 1], c.d_info, (const float *)dinv[b], stg[b ^ 1]);
+                               dinv[b ^ 1], c.d_info, (const float *)dinv[b], stg[b ^ 1], c.d_status);
             c.tend(PH_LU_DIAG, c.stream2);
             cudaEventRecord(c.ev_diag, c.stream2);
             c.launches += 1;
