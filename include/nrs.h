@@ -225,7 +225,10 @@ nrs_status nrs_assemble(nrs_ctx *ctx, const double *x, const double *Xw, double 
  * which preconditions the FP64 refinement of nrs_solve.
  * info (host, may be NULL) receives 0 or the 1-based column of the first
  * exactly-zero pivot; that case also returns NRS_ESINGULAR.  Synchronises
- * when info is requested. */
+ * when info is requested.  Every device-side wait of the factorisation (the
+ * pivot-step slots of the diagonal-block inverse, the counters of the fused
+ * schedule) is bounded: one that runs out sets the context's status word,
+ * returned as NRS_ETIMEOUT by the next nrs_sync or solve report. */
 nrs_status nrs_factor(nrs_ctx *ctx, int32_t prec, int32_t *info);
 
 /* Solve A x = b (device b, x [n*nrhs], column-major) by GMRES-based iterative
