@@ -203,7 +203,9 @@ def _traffic(kernel, n):
 def _rooflines(ph_ms, ph_spans, pr, peaks, peak_src, clocks, solve_stats=None):
     """Roofline records of the kernel families of the step, from the live
     per-phase CUDA-event times.  Algorithmic work per launch:
-      k_gj_diag       2*64^3 flops (inverse) + 2*64^3 (lookahead block update)
+      k_gj_diag       2*64^3 flops (inverse) + 6*64^3 (lookahead: R = Dprev M[P,K],
+                      D -= M[K,P] R, and the staged tile -M[K,P] Dprev); the first
+                      block of a factorisation has no lookahead (2*64^3)
       k_tc_gj_update  8 n^2 bytes (read and write of the FP32 matrix), HBM-bound at K = 64
       k_assemble64    29 FP64 operations per (force point, quadrature point) pair
       k_gemv_part     8 n^2 bytes (FP64 matrix)
@@ -250,7 +252,8 @@ def _rooflines(ph_ms, ph_spans, pr, peaks, peak_src, clocks, solve_stats=None):
 def _separate_factor_rooflines(recs, per_launch, ph_spans, n, peaks, peak_src, fp32_peak,
                                tf32_peak, sm_mhz):
     t = per_launch("lu_diag")
-    w = 4.0 * 64 ** 3
+    nblk = -(-n // 64)
+    w = (2.0 + 8.0 * (nblk - 1)) / nblk * 64 ** 3  # mean over one factorisation's launches
     sm_peak = fp32_peak / SM_COUNT_NOMINAL
     recs["lu_diag"] = {"kernel": "k_gj_diag (64 x 64 diagonal-block inverse, one CTA)",
                        "bound": "alu", "achieved": w / t / 1e12, "peak": sm_peak,

@@ -43,8 +43,12 @@ def test_separate_kernel_schedule():
     assert {"lu_diag", "lu_update", "assemble", "solve"} <= set(recs)
     for r in recs.values():
         _check(r)
-    # per launch: 0.9 ms / 38 diagonal inverses of 4 * 64^3 flops each
-    assert recs["lu_diag"]["achieved"] == pytest.approx(4 * 64 ** 3 / (0.9e-3 / 38) / 1e12)
+    # per launch: 0.9 ms / 38 diagonal inverses; the first of a factorisation is the
+    # inverse alone (2 * 64^3 flops), the other 37 add the lookahead and staged-tile
+    # products (8 * 64^3 flops)
+    w = (2 * 64 ** 3 + 37 * 8 * 64 ** 3) / 38
+    assert recs["lu_diag"]["work_per_launch"] == pytest.approx(w)
+    assert recs["lu_diag"]["achieved"] == pytest.approx(w / (0.9e-3 / 38) / 1e12)
 
 
 def test_fused_schedule():
