@@ -2,9 +2,13 @@
 
 Both factorisation schedules must give well-formed records: the separate
 kernels (a diagonal-inverse phase and an update phase per block) and the fused
-launch (one update-phase span per inversion, no diagonal-inverse spans).
+launch (one update-phase span per inversion, no diagonal-inverse spans).  The
+DRAM-traffic figures come from ncu captures and are used only while each
+kernel's source file is unchanged.
 """
 
+import hashlib
+import os
 import types
 
 import pytest
@@ -62,3 +66,26 @@ def test_fused_schedule():
     assert rec["blocks"] == nblk
     assert rec["us_per_block"] == pytest.approx(1.05e3 / nblk)
     assert rec["work_per_launch"] == pytest.approx(8.0 * PROBLEM.n ** 2 * nblk)
+
+
+def test_traffic_record_follows_its_source(tmp_path, monkeypatch):
+    # DRAM bytes from an ncu capture are reported only while the kernel's
+    # source file is the one captured (SHA-1 prefix); n^2 scaling from the
+    # captured size
+    src = tmp_path / "k.cu"
+    src.write_bytes(b"kernel, as captured")
+    sha = hashlib.sha1(b"kernel, as captured").hexdigest()[:12]
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "k_test", {"bytes": 1000.0, "file": "k.cu",
+                                                      "sha1": sha, "n": 100})
+    assert bench._traffic("k_test", 200) == pytest.approx(4000.0)
+    src.write_bytes(b"kernel, edited since")
+    assert bench._traffic("k_test", 200) is None
+    assert bench._traffic("k_unknown", 200) is None
+
+
+def test_traffic_records_name_existing_sources():
+    for kernel, rec in bench.NCU_TRAFFIC.items():
+        assert os.path.exists(os.path.join(bench.ROOT, rec["file"])), kernel
+        if rec["bytes"] is not None:
+            assert len(rec["sha1"]) == 12, kernel
