@@ -173,7 +173,7 @@ nrs_status do_factor(Ctx *c, int prec)
 {
     if (!c->assembled) return fail(c, NRS_EINVAL, "nrs_factor before nrs_assemble");
     if ((prec == NRS_TF32 || prec == NRS_BF16) && !nrs::tc_available())
-        return fail(c, NRS_EINVAL, "tensor-core factor precision not available in this build");
+        return fail(c, NRS_EINVAL, "tensor-core factor precision needs a tcgen05 device and the tensor-map driver entry point");
     const size_t elems = (size_t)c->lda * c->n;
     if (prec == NRS_FP64) {
         nrs::join_assembly(*c);
