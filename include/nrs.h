@@ -125,6 +125,12 @@ typedef struct {
                               every SM (the chain of diagonal inverses on one CTA, the updates
                               on the others, hand-offs by counters in global memory), else as
                               0.  Both give the same result bit for bit. */
+    int32_t residual;      /* the refinement's residual b - A x: 0 = double-double (every
+                              product exact, sums carried in two doubles, rounded once at the
+                              end: the residual precision u^2 of three-precision GMRES-IR,
+                              which reaches working accuracy in the solution up to
+                              kappa(A) ~ 1/u); 1 = plain FP64 (the solution is then only
+                              accurate to about kappa(A) u) */
 } nrs_problem_desc;
 
 typedef struct {

@@ -69,6 +69,8 @@ def _load():
                 "or_segments": (None, [i64, i64, I32, I32, I32]),
                 "or_rigid_map": (None, [i64, D, D, D, D]),
                 "or_assemble_stokeslet": (None, [i64, D, i64, D, I32, c_double, c_double, D, i64]),
+                "or_assemble_rows": (None, [i64, I64, i64, D, i64, D, I32, c_double, c_double, D,
+                                            i64]),
                 "or_border": (None, [c_int, I64, I64, I32, D, D, I32, D, D, i64]),
                 "or_rhs": (None, [c_int, I64, I32, D, D, D, D, D, D, D, D]),
                 "or_lu": (c_int, [i64, D, i64, I32]),
@@ -207,6 +209,21 @@ def assemble_stokeslet(x: np.ndarray, Xw: np.ndarray, nn: np.ndarray, eps: float
     return A
 
 
+def assemble_rows(rows, x: np.ndarray, Xw: np.ndarray, nn: np.ndarray, eps: float,
+                  mu: float) -> np.ndarray:
+    """Rows 3m..3m+2 of A_s (Sec. 3, eq. nnrsbie) for the force points m in
+    ``rows``, as a (3 len(rows), 3N) array: out[3r+j, 3n+k] = A[3m+j, 3n+k]
+    with m = rows[r], the same sums as assemble_stokeslet."""
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    N = len(x)
+    out = np.zeros((3 * len(rows), 3 * N), order="F")
+    _load().or_assemble_rows(len(rows), _i64(rows), N, _d(np.ascontiguousarray(x)), len(Xw),
+                             _d(np.ascontiguousarray(Xw)),
+                             _i32(np.ascontiguousarray(nn, dtype=np.int32)), float(eps), float(mu),
+                             _d(out), 3 * len(rows))
+    return out
+
+
 def border(A: np.ndarray, x: np.ndarray, Xw: np.ndarray, nn: np.ndarray, n_off, q_off, kind,
            x0: np.ndarray) -> None:
     """Fill the rigid-body rows/columns of the swimming problem in place
@@ -288,6 +305,36 @@ def solve(A: np.ndarray, b: np.ndarray, maxit: int = 10, tol: float = 1e-16,
     if return_info:
         return X, {"refine_steps": its, "LU": LU, "ipiv": ipiv}
     return X
+
+
+def solve_lapack(A: np.ndarray, b: np.ndarray, maxit: int = 30, tol: float = 1e-16,
+                 return_info: bool = False):
+    """x = A^{-1} b for systems too large for the unblocked LU above (the
+    full-size swimming problems, n ~ 2.5e4): LAPACK's partial-pivoting LU
+    (scipy getrf/getrs, a library step) gives the first solution and the
+    corrections; the residual b - A x of every refinement step is the
+    double-double one of nrs_oracle.c.  Stops when the correction is below
+    tol * ||x||_inf, or when it no longer halves (the limit of the
+    refinement: the corrections are then rounding noise of x).  This is the
+    Sec. 4 step 3 solve carried to working accuracy; the refinement converges
+    for kappa(A) u < 1."""
+    import scipy.linalg as sla
+    A = np.asfortranarray(A, dtype=np.float64)
+    lu_piv = sla.lu_factor(A, overwrite_a=False, check_finite=False)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = sla.lu_solve(lu_piv, b, check_finite=False)
+    steps, dprev = 0, np.inf
+    for steps in range(1, maxit + 1):
+        r = residual_dd(A, x, b)
+        d = sla.lu_solve(lu_piv, r, check_finite=False)
+        x = x + d
+        dn, xn = np.max(np.abs(d)), np.max(np.abs(x))
+        if dn <= tol * xn or dn >= 0.5 * dprev:
+            break
+        dprev = dn
+    if return_info:
+        return x, {"refine_steps": steps, "last_update": float(dn / xn)}
+    return x
 
 
 def cond1(A: np.ndarray, LU: Optional[np.ndarray] = None, ipiv: Optional[np.ndarray] = None) -> float:

@@ -170,27 +170,47 @@ void or_rigid_map(int64_t count, const double *p, const double *x0, const double
  * included) with the 0/1 nearest-neighbour matrix.  Every force point m is
  * paired with every quadrature point q of every body.  The block is first
  * accumulated as sum_q S w_q, then multiplied by 1/(8 pi mu). */
+/* Rows 3m..3m+2 of A_s for one force point m, written to dst[j + col*ld]
+ * (col = 0..3N-1): zeroed, accumulated over every q in ascending order,
+ * then scaled by c = 1/(8 pi mu). */
+static void assemble_row(int64_t m, int64_t N, const double *x, int64_t Q, const double *Xw,
+                         const int32_t *nn, double eps, double c, double *dst, int64_t ld)
+{
+    for (int64_t jj = 0; jj < 3 * N; ++jj)
+        for (int j = 0; j < 3; ++j) dst[j + jj * ld] = 0.0;
+    for (int64_t q = 0; q < Q; ++q) {
+        double r[3] = {x[4 * m + 0] - Xw[4 * q + 0], x[4 * m + 1] - Xw[4 * q + 1],
+                       x[4 * m + 2] - Xw[4 * q + 2]};
+        double S[9];
+        or_stokeslet(r, eps, S);
+        int64_t n = nn[q];
+        double w = Xw[4 * q + 3];
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) dst[j + (3 * n + k) * ld] += S[3 * j + k] * w;
+    }
+    for (int64_t jj = 0; jj < 3 * N; ++jj)
+        for (int j = 0; j < 3; ++j) dst[j + jj * ld] *= c;
+}
+
 void or_assemble_stokeslet(int64_t N, const double *x, int64_t Q, const double *Xw,
                            const int32_t *nn, double eps, double mu, double *A, int64_t lda)
 {
     double c = 1.0 / (8.0 * OR_PI * mu);
 #pragma omp parallel for schedule(static)
-    for (int64_t m = 0; m < N; ++m) {
-        for (int64_t jj = 0; jj < 3 * N; ++jj)
-            for (int j = 0; j < 3; ++j) A[(3 * m + j) + jj * lda] = 0.0;
-        for (int64_t q = 0; q < Q; ++q) {
-            double r[3] = {x[4 * m + 0] - Xw[4 * q + 0], x[4 * m + 1] - Xw[4 * q + 1],
-                           x[4 * m + 2] - Xw[4 * q + 2]};
-            double S[9];
-            or_stokeslet(r, eps, S);
-            int64_t n = nn[q];
-            double w = Xw[4 * q + 3];
-            for (int j = 0; j < 3; ++j)
-                for (int k = 0; k < 3; ++k) A[(3 * m + j) + (3 * n + k) * lda] += S[3 * j + k] * w;
-        }
-        for (int64_t jj = 0; jj < 3 * N; ++jj)
-            for (int j = 0; j < 3; ++j) A[(3 * m + j) + jj * lda] *= c;
-    }
+    for (int64_t m = 0; m < N; ++m) assemble_row(m, N, x, Q, Xw, nn, eps, c, A + 3 * m, lda);
+}
+
+/* The same rows for a subset of force points: rows[r] = m gives
+ * out[(3r+j) + (3n+k)*ldo] = A[3m+j, 3n+k] (ldo >= 3*nrows), the sampled
+ * check of a matrix too large to assemble whole. */
+void or_assemble_rows(int64_t nrows, const int64_t *rows, int64_t N, const double *x, int64_t Q,
+                      const double *Xw, const int32_t *nn, double eps, double mu, double *out,
+                      int64_t ldo)
+{
+    double c = 1.0 / (8.0 * OR_PI * mu);
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < nrows; ++r)
+        assemble_row(rows[r], N, x, Q, Xw, nn, eps, c, out + 3 * r, ldo);
 }
 
 /* Rigid-body border of the swimming problem (Sec. 2 last paragraph, Sec. 4).

@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libnrs.so")
 SOURCES = ["geometry.cu", "assemble.cu", "lu.cu", "gj.cu", "solve.cu", "tc_gemm.cu", "api.cu",
            "static_nn.cu", "mlp.cu",
            "gmres_persistent.cu", "batch.cu"]
-HEADERS = ["nrs_internal.cuh", "tc_ptx.cuh"]
+HEADERS = ["nrs_internal.cuh", "tc_prims.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

@@ -89,6 +89,7 @@ nrs_status alloc_all(Ctx *c)
         {(void **)&c->d_scal, sizeof(double) * (16 + 2 * (m + 1))},
         {(void **)&c->d_part, sizeof(double) * 64 * lda},
         {(void **)&c->d_part32, sizeof(double) * 64 * lda},
+        {(void **)&c->d_part_lo, sizeof(double) * 64 * lda},
         {(void **)&c->d_t32, sizeof(float) * 2 * lda},
         {(void **)&c->d_t64, sizeof(double) * 2 * lda},
         {(void **)&c->d_flags, sizeof(int32_t) * nrs::ceil_div(n, 64)},
@@ -126,7 +127,8 @@ void free_all(Ctx *c)
                     c->d_V,      c->d_H,      c->d_gv,     c->d_scal,       c->d_part,
                     c->d_t32,    c->d_t64,    c->d_flags,  c->d_status,     c->d_gj_dinv,
                     c->d_gj_rt,  c->d_gj_cb,  c->d_dpart,  c->d_bar,        c->d_pg_stats,
-                    c->d_step_stats, c->d_Xsh, c->d_Xsl, c->d_xh, c->d_xl, c->d_gj_stage, c->d_gj_sync, c->d_part32};
+                    c->d_step_stats, c->d_Xsh, c->d_Xsl, c->d_xh, c->d_xl, c->d_gj_stage, c->d_gj_sync, c->d_part32,
+                    c->d_part_lo};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *mlp[] = {c->d_mlp_params, c->d_mlp_m,  c->d_mlp_v,     c->d_mlp_g,    c->d_mlp_x,
@@ -495,6 +497,7 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
     }
     c->tol_in = d->inner_tol > 0.0 ? d->inner_tol : 1e-4;
     c->lo_eval = d->factor_input ? 1 : 0;
+    c->residual_dd = d->residual == 0 ? 1 : 0;
     c->gj_fused = d->factor_schedule == 1;
     c->graph_mode = d->graph ? 1 : 0;
     if (c->graph_mode && (d->factor_prec == NRS_FP64 || c->solve_mode != 0 || d->reuse_factor ||

@@ -35,17 +35,25 @@ constexpr int AS_CHUNK = 512;
 // does not depend on the chunk)
 constexpr int AS64_CHUNK = 256;
 
-struct Acc7 {
-    double xx, xy, xz, yy, yz, zz, d;
+struct Acc6 {
+    double xx, xy, xz, yy, yz, zz;
 };
 
-__device__ __forceinline__ void flush_block(int64_t m, int64_t n, const Acc7 &a, double c,
+// The FP64 entries are the definition evaluated term by term in one fixed
+// order, with every operation rounded on its own (no fused multiply-add,
+// correctly rounded square root and division):
+//   r = x_m - X_q,  |r|^2 = (r0 r0 + r1 r1) + r2 r2,  rho = |r|^2 + eps^2,
+//   s = 1 / (rho sqrt(rho)),  S_jk = (r_j r_k [+ (|r|^2 + 2 eps^2) if j = k]) s,
+//   acc_jk += S_jk w_q  (q ascending within the segment),  A = acc_jk / (8 pi mu)
+// so each entry is a deterministic function of the inputs, independent of
+// the tiling and of the device.
+__device__ __forceinline__ void flush_block(int64_t m, int64_t n, const Acc6 &a, double c,
                                             double *__restrict__ A64, float *__restrict__ A32,
                                             int64_t lda)
 {
-    const double v[9] = {c * (a.xx + a.d), c * a.xy,          c * a.xz,
-                         c * a.xy,          c * (a.yy + a.d), c * a.yz,
-                         c * a.xz,          c * a.yz,          c * (a.zz + a.d)};
+    const double v[9] = {__dmul_rn(a.xx, c), __dmul_rn(a.xy, c), __dmul_rn(a.xz, c),
+                         __dmul_rn(a.xy, c), __dmul_rn(a.yy, c), __dmul_rn(a.yz, c),
+                         __dmul_rn(a.xz, c), __dmul_rn(a.yz, c), __dmul_rn(a.zz, c)};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int64_t col = (3 * n + k) * lda + 3 * m;
@@ -55,6 +63,23 @@ __device__ __forceinline__ void flush_block(int64_t m, int64_t n, const Acc7 &a,
             if (A32) A32[col + j] = (float)v[3 * j + k];
         }
     }
+}
+
+__device__ __forceinline__ void add_pair(double mx, double my, double mz, const D4 &X,
+                                         double eps2, double two_e2, Acc6 &a)
+{
+    const double rx = __dsub_rn(mx, X.x), ry = __dsub_rn(my, X.y), rz = __dsub_rn(mz, X.z);
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz));
+    const double rho = __dadd_rn(r2, eps2);
+    const double s = __ddiv_rn(1.0, __dmul_rn(rho, __dsqrt_rn(rho)));
+    const double dg = __dadd_rn(r2, two_e2);
+    const double w = X.w;
+    a.xx = __dadd_rn(a.xx, __dmul_rn(__dmul_rn(__dadd_rn(__dmul_rn(rx, rx), dg), s), w));
+    a.xy = __dadd_rn(a.xy, __dmul_rn(__dmul_rn(__dmul_rn(rx, ry), s), w));
+    a.xz = __dadd_rn(a.xz, __dmul_rn(__dmul_rn(__dmul_rn(rx, rz), s), w));
+    a.yy = __dadd_rn(a.yy, __dmul_rn(__dmul_rn(__dadd_rn(__dmul_rn(ry, ry), dg), s), w));
+    a.yz = __dadd_rn(a.yz, __dmul_rn(__dmul_rn(__dmul_rn(ry, rz), s), w));
+    a.zz = __dadd_rn(a.zz, __dmul_rn(__dmul_rn(__dadd_rn(__dmul_rn(rz, rz), dg), s), w));
 }
 
 // One tile = AS_THREADS collocation points x AS_NT segments; tiles are taken
@@ -82,43 +107,31 @@ __global__ void __launch_bounds__(AS_THREADS)
         my = p.y;
         mz = p.z;
     }
-    const double two_e2 = 2.0 * eps2;
-    Acc7 a = {0, 0, 0, 0, 0, 0, 0};
+    const double two_e2 = __dmul_rn(2.0, eps2);
+    Acc6 a = {0, 0, 0, 0, 0, 0};
     __syncthreads();
     int cur = 0;
     const int32_t qbeg = sp[0], qend = sp[nt];
     for (int32_t c0 = qbeg; c0 < qend; c0 += AS64_CHUNK) {
         const int cnt = min(AS64_CHUNK, qend - c0);
+        const int32_t cend = c0 + cnt;
         __syncthreads();
         for (int i = threadIdx.x; i < cnt; i += AS_THREADS) sX[i] = Xs[c0 + i];
         __syncthreads();
-        int32_t next = sp[cur + 1];
-        for (int i = 0; i < cnt; ++i) {
-            const int32_t q = c0 + i;
-            while (q >= next) {  // uniform across the block
-                if (active) flush_block(m, n0 + cur, a, c, A64, A32, lda);
-                a = Acc7{0, 0, 0, 0, 0, 0, 0};
-                ++cur;
-                next = sp[cur + 1];
-            }
-            const D4 X = sX[i];
-            const double rx = mx - X.x, ry = my - X.y, rz = mz - X.z;
-            const double r2 = rx * rx + ry * ry + rz * rz;
-            const double inv = rsqrt(r2 + eps2);
-            const double t = X.w * (inv * inv * inv);
-            const double tx = rx * t, ty = ry * t, tz = rz * t;
-            a.xx += rx * tx;
-            a.xy += rx * ty;
-            a.xz += rx * tz;
-            a.yy += ry * ty;
-            a.yz += ry * tz;
-            a.zz += rz * tz;
-            a.d += (r2 + two_e2) * t;
+        // segment by segment (bounds uniform across the block): the sums run
+        // in ascending q within each segment
+        while (cur < nt) {
+            const int32_t sb = max(sp[cur], c0), se = min(sp[cur + 1], cend);
+            for (int32_t q = sb; q < se; ++q) add_pair(mx, my, mz, sX[q - c0], eps2, two_e2, a);
+            if (sp[cur + 1] > cend) break;  // the segment continues in the next chunk
+            if (active) flush_block(m, n0 + cur, a, c, A64, A32, lda);
+            a = Acc6{0, 0, 0, 0, 0, 0};
+            ++cur;
         }
     }
     while (cur < nt) {
         if (active) flush_block(m, n0 + cur, a, c, A64, A32, lda);
-        a = Acc7{0, 0, 0, 0, 0, 0, 0};
+        a = Acc6{0, 0, 0, 0, 0, 0};
         ++cur;
     }
     }  // tile loop

@@ -19,6 +19,10 @@
 // the same values, so all CTAs take the same branches without a broadcast.
 // Every reduction has a fixed order: the result is deterministic.
 //
+// The residual b - A x is carried in double-double by default (precision
+// u^2: the three-precision form of Carson & Higham, whose solution reaches
+// working accuracy for kappa(A) up to about 1/u), or in FP64.
+//
 // Stopping rule: that of k_outer_check (solve.cu), plus one for very
 // ill-conditioned systems, where an FP64 residual leaves corrections of about
 // kappa(A) u that never shrink: once the corrections stagnate, the iteration
@@ -52,6 +56,8 @@ struct PgArgs {
     double *w;            // n: A v, then the residual
     double *part;         // partial sums of the FP64 products [splits][n]
     double *part32;       // partial sums of the FP32 products [splits][n]
+    double *part_lo;      // low parts of the double-double residual's partial sums [splits][n]
+    int dd;               // residual b - A x in double-double (1) or FP64 (0)
     double *dpart;        // reduction partials [3][PG_MAXCH][m+2]
     int32_t *bar;         // grid barrier: [0] arrivals since the launch ([1] unused)
     int32_t *status;
@@ -154,6 +160,58 @@ __device__ void mv64_partial(const PgArgs &a, const double *v, double scale, dou
         }
         __syncthreads();
     }
+}
+
+// The residual's product in double-double: (part, part_lo)[s][i] = sum_{j in
+// split s} A[i, j] v[j], every product exact and every sum carried in two
+// doubles (dd_fma), the tile layout of mv64_partial; the 8 column groups are
+// added in double-double in a fixed order.
+__device__ void mv64dd_partial(const PgArgs &a, const double *v, double *sm, double *sm_lo)
+{
+    const int64_t tiles = (int64_t)a.rc64 * a.s64;
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t rc = t % a.rc64, s = t / a.rc64;
+        const int64_t i = rc * MV64_ROWS + 2 * lane;
+        const int64_t j0 = s * a.cps64, j1 = min(a.n, j0 + a.cps64);
+        double h0 = 0.0, l0 = 0.0, h1 = 0.0, l1 = 0.0;
+        if (i < a.n) {
+            const double *col = a.A + i;
+#pragma unroll 4
+            for (int64_t j = j0 + grp; j < j1; j += MV_GROUPS) {
+                const double2 x = __ldg(reinterpret_cast<const double2 *>(col + j * a.lda));
+                const double vj = __ldcg(v + j);
+                dd_fma(x.x, vj, h0, l0);
+                dd_fma(x.y, vj, h1, l1);
+            }
+        }
+        sm[grp * MV64_ROWS + 2 * lane] = h0;
+        sm[grp * MV64_ROWS + 2 * lane + 1] = h1;
+        sm_lo[grp * MV64_ROWS + 2 * lane] = l0;
+        sm_lo[grp * MV64_ROWS + 2 * lane + 1] = l1;
+        __syncthreads();
+        if (threadIdx.x < MV64_ROWS) {
+            const int64_t r = rc * MV64_ROWS + threadIdx.x;
+            double hi = 0.0, lo = 0.0;
+#pragma unroll
+            for (int g = 0; g < MV_GROUPS; ++g)
+                dd_add(hi, lo, sm[g * MV64_ROWS + threadIdx.x], sm_lo[g * MV64_ROWS + threadIdx.x]);
+            if (r < a.n) {
+                a.part[s * a.n + r] = hi;
+                a.part_lo[s * a.n + r] = lo;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// b[e] - sum over the column splits of (part + part_lo)[.][e], in double-double
+__device__ __forceinline__ double residual_dd_at(const PgArgs &a, double be, int64_t e)
+{
+    double hi = be, lo = 0.0;
+    for (int k = 0; k < a.s64; ++k)
+        dd_add(hi, lo, -__ldcg(a.part + k * a.n + e), -__ldcg(a.part_lo + k * a.n + e));
+    return __dadd_rn(hi, lo);
 }
 
 // part32[s][i] = sum_{j in split s} M[i, j] v[j] (FP32 products and sums):
@@ -295,6 +353,7 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
     __shared__ double sh1[PG_MAXM + 1], sh2[PG_MAXM + 1];
     __shared__ double sred[PG_THREADS / 32];
     __shared__ __align__(16) double smv[MV_GROUPS * MV64_ROWS];  // product tiles (FP64 or FP32 view)
+    __shared__ double smv_lo[MV_GROUPS * MV64_ROWS];             // low parts (double-double residual)
     __shared__ int s_ok;
     int32_t tgt = 0;  // grid barrier target (thread 0)
     float *smv32 = reinterpret_cast<float *>(smv);
@@ -321,13 +380,17 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
     double dn = 0.0, xn = 0.0, dn_prev = 0.0, normA = -1.0;
     bool stagnant = false;
     for (outer = 0; outer < a.max_outer; ++outer) {
-        // r = b - A x (FP64), with ||r||_inf and ||b||_inf per chunk
-        mv64_partial<false>(a, a.x, 1.0, smv);
+        // r = b - A x (double-double, or FP64), with ||r||_inf and ||b||_inf per chunk
+        if (a.dd)
+            mv64dd_partial(a, a.x, smv, smv_lo);
+        else
+            mv64_partial<false>(a, a.x, 1.0, smv);
         if (!grid_sync(a, &s_ok, tgt)) return;
         {
             double rmax = 0.0, bmax = 0.0;
             for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
-                const double be = __ldg(a.b + e), re = be - sum_parts(a, a.s64, e);
+                const double be = __ldg(a.b + e);
+                const double re = a.dd ? residual_dd_at(a, be, e) : be - sum_parts(a, a.s64, e);
                 a.w[e] = re;
                 rmax = fmax(rmax, fabs(re));
                 bmax = fmax(bmax, fabs(be));
@@ -569,6 +632,8 @@ cudaError_t launch_gmres_persistent(Ctx &c, const double *b, double *x, bool col
     a.w = c.d_w;
     a.part = c.d_part;
     a.part32 = c.d_part32;
+    a.part_lo = c.d_part_lo;
+    a.dd = c.residual_dd;
     a.dpart = c.d_dpart;
     a.bar = c.d_bar;
     a.status = c.d_status;

@@ -247,6 +247,8 @@ struct Ctx {
     double *d_scal = nullptr;  // scalars (norms, flags as doubles)
     double *d_part = nullptr;  // partial sums of matrix-vector products
     double *d_part32 = nullptr;  // partial sums of the FP32 products of the persistent solve
+    double *d_part_lo = nullptr; // low parts of the double-double residual's partial sums
+    int residual_dd = 1;       // refinement residual b - A x: 1 double-double, 0 FP64
     int splits64 = 1, splits32 = 1;  // column splits of the FP64 / FP32 matrix-vector products
     float *d_t32 = nullptr;    // FP32 work vector for the triangular solves
     double *d_t64 = nullptr;   // FP64 work vector for the triangular solves
@@ -294,5 +296,36 @@ struct Ctx {
 };
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ---- double-double arithmetic of the refinement's residual -----------------
+// Error-free transformations: Knuth's TwoSum (s + e = a + b exactly) and the
+// product with one fused multiply-add (p + e = a b exactly).  Every step is
+// an explicitly rounded intrinsic, so the compiler cannot fuse or reorder.
+__device__ __forceinline__ void dd_two_sum(double a, double b, double &s, double &e)
+{
+    s = __dadd_rn(a, b);
+    const double bb = __dsub_rn(s, a);
+    e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+
+// (hi, lo) += a b, the product exact and the sum carried in two doubles
+__device__ __forceinline__ void dd_fma(double a, double b, double &hi, double &lo)
+{
+    const double p = __dmul_rn(a, b);
+    const double pe = __fma_rn(a, b, -p);
+    double s, se;
+    dd_two_sum(hi, p, s, se);
+    hi = s;
+    lo = __dadd_rn(lo, __dadd_rn(se, pe));
+}
+
+// (hi, lo) += (h2, l2)
+__device__ __forceinline__ void dd_add(double &hi, double &lo, double h2, double l2)
+{
+    double s, e;
+    dd_two_sum(hi, h2, s, e);
+    hi = s;
+    lo = __dadd_rn(lo, __dadd_rn(e, l2));
+}
 
 }  // namespace nrs

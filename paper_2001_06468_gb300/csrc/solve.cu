@@ -248,6 +248,48 @@ __global__ void __launch_bounds__(MV_THREADS)
     if (i + 3 < n) p[3] = s3;
 }
 
+// The residual's product in double-double: (part, part_lo)[s*n + i] =
+// sum_{j in split s} A[i,j] v[j] with every product exact and the sum carried
+// in two doubles (dd_fma), two rows per thread as in k_gemv_part.
+__global__ void __launch_bounds__(MV_THREADS)
+    k_gemv_part_dd(int64_t n, const double *__restrict__ A, int64_t lda,
+                   const double *__restrict__ v, double *__restrict__ part,
+                   double *__restrict__ part_lo, int64_t cols_per_split)
+{
+    const int64_t i = ((int64_t)blockIdx.x * MV_THREADS + threadIdx.x) * 2;
+    const int64_t j0 = (int64_t)blockIdx.y * cols_per_split;
+    const int64_t j1 = min(n, j0 + cols_per_split);
+    if (i >= n) return;
+    double h0 = 0.0, l0 = 0.0, h1 = 0.0, l1 = 0.0;
+    const double *a = A + i;
+#pragma unroll 4
+    for (int64_t j = j0; j < j1; ++j) {
+        const double2 x = __ldg(reinterpret_cast<const double2 *>(a + j * lda));
+        const double vj = __ldg(&v[j]);
+        dd_fma(x.x, vj, h0, l0);
+        dd_fma(x.y, vj, h1, l1);
+    }
+    part[blockIdx.y * n + i] = h0;
+    part_lo[blockIdx.y * n + i] = l0;
+    if (i + 1 < n) {
+        part[blockIdx.y * n + i + 1] = h1;
+        part_lo[blockIdx.y * n + i + 1] = l1;
+    }
+}
+
+// out[i] = b[i] - sum_s (part + part_lo), carried in double-double and
+// rounded once
+__global__ void k_gemv_finish_dd(int64_t n, const double *__restrict__ part,
+                                 const double *__restrict__ part_lo, int splits,
+                                 const double *__restrict__ b, double *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double hi = b[i], lo = 0.0;
+    for (int k = 0; k < splits; ++k) dd_add(hi, lo, -part[k * n + i], -part_lo[k * n + i]);
+    out[i] = __dadd_rn(hi, lo);
+}
+
 // out[i] = b[i] - sum_s part (b != NULL), or sum_s part
 __global__ void k_gemv_finish(int64_t n, const double *__restrict__ part, int splits,
                               const double *__restrict__ b, double *__restrict__ out)
@@ -506,6 +548,25 @@ static void gemv(Ctx &c, const double *v, const double *b, double *out)
     c.launches += 2;
 }
 
+// r = b - A x with the FP64 matrix: double-double unless the context asks for
+// a plain FP64 residual
+static void residual(Ctx &c, const double *x, const double *b, double *r)
+{
+    if (!c.residual_dd) {
+        gemv(c, x, b, r);
+        return;
+    }
+    const int64_t cps = ceil_div(c.n, c.splits64);
+    dim3 grid((unsigned)ceil_div(c.n, 2 * MV_THREADS), (unsigned)c.splits64);
+    c.tbeg(PH_GEMV);
+    k_gemv_part_dd<<<grid, MV_THREADS, 0, c.stream>>>(c.n, c.d_A64, c.lda, x, c.d_part,
+                                                      c.d_part_lo, cps);
+    k_gemv_finish_dd<<<(unsigned)ceil_div(c.n, 256), 256, 0, c.stream>>>(
+        c.n, c.d_part, c.d_part_lo, c.splits64, b, r);
+    c.tend(PH_GEMV);
+    c.launches += 2;
+}
+
 static double read_scalar(Ctx &c, int slot, cudaError_t *err)
 {
     double v = 0.0;
@@ -516,7 +577,7 @@ static double read_scalar(Ctx &c, int slot, cudaError_t *err)
 
 void enqueue_backward_error(Ctx &c, const double *b, const double *x, double *out3)
 {
-    gemv(c, x, b, c.d_r);
+    residual(c, x, b, c.d_r);
     k_nrm_inf<<<1, RED_THREADS, 0, c.stream>>>(c.n, c.d_r, out3, 0);
     const int64_t cps = ceil_div(c.n, c.splits64);
     dim3 grid((unsigned)ceil_div(c.n, 2 * MV_THREADS), (unsigned)c.splits64);
@@ -599,7 +660,7 @@ nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0, nr
     double *h2 = h1 + (m + 1);
     bool have_an = false;
     for (outer = 0; outer < c.max_outer; ++outer) {
-        gemv(c, x, b, c.d_r);  // r = b - A x
+        residual(c, x, b, c.d_r);  // r = b - A x
         if (outer > 0) {
             // stagnating corrections: stop once the normwise backward error of
             // x is at most 1e-15 (as in gmres_persistent.cu)
@@ -706,7 +767,7 @@ static nrs_status finish_solve(Ctx &c, const double *b, double *x, nrs_solve_rep
     if (inner_out) *inner_out = inner_total;
     if (rep) {
         // backward error ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf)
-        gemv(c, x, b, c.d_r);
+        residual(c, x, b, c.d_r);
         k_nrm_inf<<<1, RED_THREADS, 0, c.stream>>>(n, c.d_r, c.d_scal, SC_RN);
         k_nrm_inf<<<1, RED_THREADS, 0, c.stream>>>(n, b, c.d_scal, SC_BN);
         {

@@ -1,24 +1,32 @@
 """The full-size configurations (four interacting swimmers, n = 24024; eight
 sperm-like swimmers in a closed channel, n = 27648) through the C ABI, with
-the launch configuration of the time step, checked against the FP64 oracle
-where it is affordable at these sizes:
+the launch configuration of the time step, checked against the FP64 oracle:
 
 * nearest neighbours: the whole map, bit for bit (the oracle's exhaustive
-  search per body is cheap);
-* the assembled matrix: a seeded sample of 3 x 3 blocks against the
-  definition of eq. nnrsbie summed in numpy over the block's segment, within
-  1e-13 of the sum of the absolute values of its terms;
-* the solve: the GPU solution put into the oracle's own FP64 system (its
-  assembly, border and right-hand side), backward error
-  ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= 1e-14 with a
-  double-double residual; a solution of that quality has forward error at
-  most kappa(A) times it, the property that holds at any size.  (These
-  systems are ill-conditioned -- kappa_1 about 1e13 for the four swimmers --
-  so the forward error an FP64 residual can deliver is bounded by that, for
-  any solver; the oracle itself refines with a double-double residual.)
+  search per body is cheap); lab-frame clouds and right-hand side bit for bit;
+* the assembled matrix: a seeded sample of 48 force points' rows of A_s, bit
+  for bit against the oracle's own sums (oracle.assemble_rows), and a sample
+  of 3 x 3 blocks against the definition summed in numpy, within 1e-13 of
+  the sum of the absolute values of the terms;
+* the solve: backward error of the GPU solution in the oracle's own FP64
+  system (double-double residual) at most 1e-15;
+* the first explicit-midpoint step through nrs_step: both stages' forces f
+  and rigid velocities V within a relative error of 1e-10 of the oracle's
+  (LAPACK LU refined with a double-double residual to working accuracy),
+  fresh factor and factor reuse, and the new state.  The oracle's answer
+  for the channel is stored in tests/golden (written by
+  make_fullsize_golden.py from oracle/ alone) with the digest of its
+  inputs; where the inputs generated here differ from those (the transcendental
+  functions of numpy may round differently on another machine), the oracle
+  is run here.  These systems are ill-conditioned (kappa_1 about 1e13 for
+  the four swimmers), so agreement to 1e-10 needs the same FP64 matrix on
+  both sides -- which the bit-exact assembly gives -- and a residual
+  computed in double-double.
 """
 
 import math
+import os
+import sys
 
 import numpy as np
 import pytest
@@ -83,9 +91,19 @@ def test_full_size_nearest_assembly_and_solve(N, name):
     # nearest neighbours: all of them, bit for bit
     nn_or = O.nearest(sh["x"], sh["Xw"], sh["n_off"], sh["q_off"], False)
     assert np.array_equal(nn.cpu().numpy(), nn_or)
-    # sampled blocks of A_s against the definition
+    # sampled rows of A_s against the oracle's sums, bit for bit
     x_lab, Xw_lab = O.lab_frame(sh, Y)
     assert np.array_equal(x.cpu().numpy(), x_lab)
+    assert np.array_equal(Xw.cpu().numpy(), Xw_lab)
+    b_or = O.rhs(x_lab, sh, tab, Y)
+    assert np.array_equal(b.cpu().numpy(), b_or)
+    rng = np.random.Generator(np.random.PCG64(21))
+    rows = np.sort(rng.choice(pr.N, size=48, replace=False))
+    sub_or = O.assemble_rows(rows, x_lab, Xw_lab, nn_or, pr.eps, pr.mu)
+    cols = np.concatenate([[3 * m, 3 * m + 1, 3 * m + 2] for m in rows])
+    sub = At[:3 * pr.N, torch.as_tensor(cols, device=At.device)].T.cpu().numpy()
+    assert np.array_equal(sub, sub_or), np.abs(sub - sub_or).max()
+    # sampled blocks of A_s against the definition
     seg_or, perm_or = O.segments(nn_or, pr.N)
     coef = 1.0 / (8.0 * math.pi * pr.mu)
     rng = np.random.Generator(np.random.PCG64(20))
@@ -108,5 +126,62 @@ def test_full_size_nearest_assembly_and_solve(N, name):
     r = O.residual_dd(A_or, xs, b_or)
     berr = np.max(np.abs(r)) / (np.max(np.sum(np.abs(A_or), axis=1)) * np.max(np.abs(xs))
                                 + np.max(np.abs(b_or)))
-    assert berr <= 1e-14, berr
-    assert rep[0]["backward_err"] <= 1e-14, rep
+    assert berr <= 1e-15, berr
+    assert rep[0]["backward_err"] <= 1e-15, rep
+
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+_ORACLE_STEP = {}
+
+
+def _oracle_first_step(name, pr):
+    """The oracle's first RK2 step (stage solutions, new state): the stored
+    answer when its input digest matches the inputs generated here, else
+    computed now."""
+    if name in _ORACLE_STEP:
+        return _ORACLE_STEP[name]
+    sys.path.insert(0, GOLDEN)
+    import make_fullsize_golden as mg
+    path = os.path.join(GOLDEN, f"{name}_step0.npz")
+    ref = None
+    if os.path.exists(path):
+        z = np.load(path)
+        if str(z["digest"]) == mg.input_digest(pr, pr.dt):
+            ref = {k: z[k] for k in ("sol1", "sol2", "x0", "B")}
+    if ref is None:
+        Yn, st = O.rk2_step(pr, g.initial_state(pr), 0.0, pr.dt, solver=O.solve_lapack,
+                            return_stages=True)
+        ref = {"sol1": st["sol1"], "sol2": st["sol2"], "x0": Yn["x0"], "B": Yn["B"]}
+    _ORACLE_STEP[name] = ref
+    return ref
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("reuse", [False, True])
+def test_full_size_first_step_matches_oracle(N, name, reuse):
+    pr = CASES[name]()
+    ref = _oracle_first_step(name, pr)
+    kw = dict(SOLVER[name])
+    if reuse:
+        kw.update(reuse_factor=True, warm_start=True)
+    ctx = N.Context.from_problem(pr, factor_prec="tf32", **kw)
+    Y = g.initial_state(pr)
+    ctx.set_state(Y["x0"], Y["B"])
+    d0 = N.shapes_to_device(g.pack_shapes(pr, 0.0))
+    dh = N.shapes_to_device(g.pack_shapes(pr, 0.5 * pr.dt))
+    sol = torch.empty(2 * pr.n, dtype=torch.float64, device="cuda")
+    rep = ctx.step(N.Context.shapes(*d0), N.Context.shapes(*dh), pr.dt, sol=sol)
+    s = sol.cpu().numpy()
+    n3 = 3 * pr.N
+    for k, key in enumerate(("sol1", "sol2")):
+        got, want = s[k * pr.n:(k + 1) * pr.n], ref[key]
+        ef, eV = _rel(got[:n3], want[:n3]), _rel(got[n3:], want[n3:])
+        assert ef <= 1e-10 and eV <= 1e-10, (key, ef, eV, rep)
+    Yg = ctx.get_state()
+    assert _rel(Yg["x0"], ref["x0"]) <= 1e-12
+    assert _rel(Yg["B"], ref["B"]) <= 1e-12
+    assert rep["factorizations"] == 2 or reuse, rep

@@ -1,11 +1,11 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
 Integer work (nearest neighbours, segments) must match bit for bit.  Floating
-point: lab-frame clouds bit for bit (the kernels round step by step in the
-oracle's order); matrix entries to 1e-12 of their row's scale (the kernels
-use rsqrt and a different association inside each pair term); solutions to a
-relative error of 1e-10 in the forces f and in the rigid velocities V, the
-accuracy the mixed-precision refinement promises.
+point: lab-frame clouds, right-hand side and the FP64 system matrix bit for
+bit (the kernels round every operation on its own, in the oracle's order,
+with correctly rounded square root and division); solutions to a relative
+error of 1e-10 in the forces f and in the rigid velocities V, the accuracy
+the mixed-precision refinement promises.
 """
 
 import math
@@ -20,7 +20,6 @@ from synth import geometry as g
 pytestmark = pytest.mark.gpu
 
 TOL_SOL = 1e-10
-TOL_A_ROW = 1e-12
 
 
 @pytest.fixture(scope="module")
@@ -81,14 +80,13 @@ def test_kinematics_nearest_segments_bit_exact(N, name):
     A_or, b_or, nn_or, x_or, Xw_or = _oracle_system(pr, sh, Y)
     assert np.array_equal(x.cpu().numpy(), x_or)
     assert np.array_equal(Xw.cpu().numpy(), Xw_or)
-    assert np.allclose(b.cpu().numpy(), b_or, rtol=1e-15, atol=1e-15 * np.abs(b_or).max())
+    assert np.array_equal(b.cpu().numpy(), b_or)
     assert np.array_equal(nn.cpu().numpy(), nn_or)
     sp_or, perm_or = O.segments(nn_or, pr.N)
     assert np.array_equal(seg_ptr.cpu().numpy(), sp_or)
     assert np.array_equal(perm.cpu().numpy(), perm_or)
     A = At.T.cpu().numpy()
-    row_scale = np.abs(A_or).max(axis=1, keepdims=True)
-    assert np.all(np.abs(A - A_or) <= TOL_A_ROW * row_scale)
+    assert np.array_equal(A, A_or), np.abs(A - A_or).max()
 
 
 def test_nearest_global_mode_bit_exact(N):
