@@ -2,33 +2,45 @@
 """Seconds per time step of the NEAREST regularized-stokeslet swimming
 problem on GB300.
 
-One step = one explicit-midpoint (RK2) step of the single free undulating
-swimmer (N = 800 force points, Q = 8000 quadrature points, eps = 0.005,
-n = 2406 unknowns): twice (kinematics, nearest neighbours, segments, FP64
-assembly, rigid-body border, explicit FP32 inverse by blocked Gauss-Jordan
-with split-TF32 tensor-core updates, FP64 GMRES-based iterative refinement to
-the FP64 answer as one cooperative launch) plus the state update, recorded once
-into a CUDA graph and replayed.  Inputs are the seeded synthetic beat shapes of
-`synth` (the paper's cited beat patterns are not available), resident in HBM
-before the timed region.  Beside the headline: the same step launched kernel by
-kernel, with the host-driven refinement loop, with factor reuse, with the
-learned start, the plain FP64 path, and (N = 1) the batch workload of many
-uneven problems in one graph.
+Headline workload: eight sperm-like cells in a closed channel (the analogue of
+the paper's "multiple swimming sperm between parallel plates" runs): a static
+box 4 x 1 x 0.5 meshed with 6000 force / 60000 quadrature points and eight
+free cells of 400 / 4000 points, N = 9200, Q = 92000, eps = 0.005,
+n = 27648 unknowns.  One step = one explicit-midpoint (RK2) step: twice
+(kinematics, nearest neighbours, segments, FP64 assembly of A_s bit-identical
+to the oracle's, rigid-body border, FP32 explicit inverse by blocked
+Gauss-Jordan with split-TF32 tensor-core updates -- refreshed when the
+previous solve needed more than 60 GMRES iterations or after 32 stages --,
+GMRES-based iterative refinement with a double-double residual to the FP64
+answer, started from the previous stage's solution) plus the state update.
+Inputs are the seeded synthetic shapes of `synth` (the paper's cited beat
+patterns are not available), resident in HBM before the timed region.
+
+Beside the headline: the same workload with a fresh factor at every stage
+(recorded as a CUDA graph), end to end through the C ABI from host buffers,
+the four-swimmer box (n = 24024) and the single swimmer (n = 2406), the plain
+FP64 path (cuSOLVER getrf/getrs on the same FP64 matrix), the batch of
+ventral-node problems, the FP64 CPU oracle on a bounded sample, the GPU
+solution's relative error against the oracle's on the first step, and the
+roofline records of the kernels.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nrs|reference]
-                    [--prec tf32|fp32|fp64]
+                    [--prec tf32|fp32] [--no-side] [--no-batch] [--no-cpu-baseline]
     python bench.py --profile-solve --workload swimmer_mid   # one solve, for ncu
-    python bench.py --no-batch --no-cpu-baseline             # the C1 lines only
+    python bench.py --profile-step --workload sperm_channel  # one step, for ncu
     python bench.py --batch-full                             # all 128 full-size batch problems
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
-on the same workload.  Under torchrun each rank runs its own replica of the
-problem ("replicas only": one dense solve does not shard across GPUs).
+on a bounded sample of the same workload.  Under torchrun each rank runs its
+own replica of the headline problem ("replicas only": one dense solve does not
+shard across GPUs) and its share of the batch (independent problems, no
+collective in the data path).
 """
 
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -44,17 +56,33 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 from synth import geometry as g  # noqa: E402
-from synth import mlp_init  # noqa: E402
 
 METRIC = "s per timestep (assemble+solve) mixed-IR vs FP64 at 1e-10 rel err; pairs/s"
-WORKLOAD = "single free undulating swimmer, N=800 force / Q=8000 quadrature points, eps=0.005, n=2406"
+HEADLINE = "sperm_channel"
+WORKLOADS_DESC = {
+    "sperm_channel": "8 sperm-like cells in a closed channel 4x1x0.5, N=9200 force / Q=92000 "
+                     "quadrature points, eps=0.005, n=27648",
+    "swimmers4": "4 interacting undulating swimmers in a 4x4x1 box, N=8000 / Q=80000, eps=0.005, "
+                 "n=24024",
+    "swimmer": "single free undulating swimmer, N=800 / Q=8000, eps=0.005, n=2406",
+}
+# the product path's solver settings per workload
+HEADLINE_SOLVER = dict(reuse_factor=True, warm_start=True, reuse_max_inner=60,
+                       reuse_max_stages=32)
+# the four-swimmer system has kappa_1 ~ 1e13: its GMRES steps need the longest
+# restart, the factorisation the rounded FP64 entries; a refinement that has
+# not converged after 20 steps is retried with a new factor (nrs_step)
+C2_SOLVER = dict(inner_tol=1e-6, max_inner=64, max_outer=20, factor_input="rounded",
+                 reuse_factor=True, warm_start=True, reuse_max_inner=400, reuse_max_stages=32)
 L2_FLUSH_BYTES = 512 << 20
-FP64_NOMINAL_TFLOPS = 1.25       # GB300 FP64 (vector and tensor), nominal
+FP64_NOMINAL_TFLOPS = 1.25       # GB300 FP64, nominal (2 FMA lanes per SM per clock)
 TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 tensor throughput
 SM_COUNT_NOMINAL = 152
-MLP_TRAIN_ITERS = 4              # Adam steps per stage for the learned starting vector
-MLP_LR = 3e-3
 FP32_LANES_PER_SM = 128
+PAIR_INSTR = 20                  # FP32-pipe instructions per (force, quadrature) pair
+ASM64_OPS_PER_PAIR = 40          # FP64 operations per pair of the bit-exact assembly
+DD_OPS_PER_ENTRY = 10            # FP64 operations per matrix entry of a double-double product
+TOL = 1e-10
 
 
 def _dist():
@@ -159,36 +187,25 @@ def _visible_gpu_index(local: int) -> int:
     return local
 
 
-def _shapes_host(pr, t):
-    import torch
-    d = g.pack_shapes(pr, t)
-    return tuple(torch.from_numpy(d[k]).pin_memory() for k in ("x", "Xw", "xidot"))
 
 
 # DRAM bytes per launch from one ncu capture (profiles/), valid while the
 # kernel's source file is unchanged (first 12 hex digits of its SHA-1).
 NCU_TRAFFIC = {
-    # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the captures summarised
-    # in profiles/ (kept only while the kernel's source is the one captured)
-    "k_gj_diag": {"bytes": 136832, "file": "paper_2001_06468_gb300/csrc/gj.cu",
-                  "sha1": "d098875a34c5",
-                  "scale": "none (the 64 x 64 block, the previous D^{-1} and two 64 x 64 tiles at any n)"},
     "k_tc_gj_update": {"bytes": 150743296 + 77540181, "n": 6006,
                        "file": "paper_2001_06468_gb300/csrc/tc_gemm.cu", "sha1": "e38e9748bdee",
-                       "scale": "n^2 (captured at n = 6006)"},
-    "k_gj_fused": {"bytes": None, "file": "paper_2001_06468_gb300/csrc/gj.cu",
-                   "sha1": "", "scale": None},
-    # captured at n = 6006 (matrices larger than L2): DRAM bytes = 1.003 x the algorithmic bytes;
-    # at n = 2406 the matrices stay in L2, so that figure does not carry over: not reported
-    "k_gmres_ir": {"bytes": None, "file": "paper_2001_06468_gb300/csrc/gmres_persistent.cu",
-                   "sha1": "f0099c63014a", "scale": None},
+                       "scale": "n^2 (captured at n = 6006, matrix larger than L2)"},
+    "k_gj_diag": {"bytes": 136832, "file": "paper_2001_06468_gb300/csrc/gj.cu",
+                  "sha1": "d098875a34c5",
+                  "scale": "none (the 64 x 64 block, the previous D^{-1} and two 64 x 64 tiles)"},
     "k_assemble64": {"bytes": None, "file": "paper_2001_06468_gb300/csrc/assemble.cu",
-                     "sha1": "fcf536ee0b72", "scale": None},
+                     "sha1": "", "scale": None},
+    "k_gmres_ir": {"bytes": None, "file": "paper_2001_06468_gb300/csrc/gmres_persistent.cu",
+                   "sha1": "", "scale": None},
 }
 
 
 def _traffic(kernel, n):
-    import hashlib
     rec = NCU_TRAFFIC.get(kernel)
     if not rec or rec["bytes"] is None:
         return None
@@ -200,424 +217,453 @@ def _traffic(kernel, n):
     return rec["bytes"]
 
 
-def _rooflines(ph_ms, ph_spans, pr, peaks, peak_src, clocks, solve_stats=None):
-    """Roofline records of the kernel families of the step, from the live
-    per-phase CUDA-event times.  Algorithmic work per launch:
-      k_gj_diag       2*64^3 flops (inverse) + 6*64^3 (lookahead: R = Dprev M[P,K],
-                      D -= M[K,P] R, and the staged tile -M[K,P] Dprev); the first
-                      block of a factorisation has no lookahead (2*64^3)
-      k_tc_gj_update  8 n^2 bytes (read and write of the FP32 matrix), HBM-bound at K = 64
-      k_assemble64    29 FP64 operations per (force point, quadrature point) pair
-      k_gemv_part     8 n^2 bytes (FP64 matrix)
-      k_gemv32_part   4 n^2 bytes (FP32 explicit inverse)
-      k_gmres_ir      8 n^2 (outer + inner) + 4 n^2 (outer + inner + 1) bytes per solve"""
-    n = pr.n
-    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    fp64_peak = FP64_NOMINAL_TFLOPS * sm_mhz / 2070.0
-    tf32_peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
+def derived_peaks(peaks, sm_mhz):
+    """Whole-GPU peaks used by the roofline records.  HBM and BF16 are the
+    measured figures; the others are derived from the unit counts and the
+    sampled SM clock (FP32: 128 lanes x 2 flops; FP64: 2 FMA lanes per SM;
+    TF32: the measured sustained BF16 rate x the nominal TF32/BF16 ratio)."""
+    clk = sm_mhz * 1e6
+    return {"hbm_gbs": peaks["hbm_gbs"],
+            "fp32_tflops": SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * clk / 1e12,
+            "fp64_gops": FP64_NOMINAL_TFLOPS / 2 * 1e3 * sm_mhz / 2070.0,
+            "tf32_tflops": peaks["bf16_tflops_sustained"] * TF32_OVER_BF16,
+            "pair_peak": SM_COUNT_NOMINAL * FP32_LANES_PER_SM * clk / PAIR_INSTR}
+
+
+def rooflines(ph_ms, ph_spans, n, pairs, peaks, peak_src, sm_mhz, solve_stats):
+    """Roofline records of the kernel families from the live per-phase CUDA
+    event times (one span per launch, on the stream each kernel runs on).
+    Algorithmic work per launch:
+      lu_update   k_tc_gj_update: 8 n^2 bytes (read + write of the FP32 matrix);
+                  3 x 2 n^2 64 tensor flops (split TF32)
+      lu_diag     k_gj_diag: (2 + 8 (nblk - 1)) / nblk x 64^3 FP32 flops, one CTA
+      assemble    k_assemble64: 40 FP64 operations per (force, quadrature) pair
+      assemble32  k_assemble32: N Q pairs against the FP32 pair peak (20 instructions a pair)
+      krylov      k_gmres_ir: (outer + inner) 8 n^2 + (outer + inner + 1) 4 n^2 bytes;
+                  outer x 10 n^2 (double-double residual) + inner x n^2 FP64 operations"""
+    P = derived_peaks(peaks, sm_mhz)
 
     def per_launch(ph):
         return ph_ms[ph] / 1e3 / max(ph_spans[ph], 1)
 
     recs = {}
-    if ph_spans["lu_diag"] == 0 and ph_spans["lu_update"] > 0:
-        # the fused factorisation: one cooperative launch per inversion, timed
-        # as the lu_update phase; every block step reads and writes the FP32
-        # matrix once (8 n^2 bytes), its critical path is the chain of the
-        # nblk diagonal inverses on one CTA
+    if ph_spans.get("lu_update"):
         t = per_launch("lu_update")
-        nblk = -(-n // 64)
-        b = 8.0 * n * n * nblk
-        recs["lu_update"] = {
-            "kernel": "k_gj_fused (the whole Gauss-Jordan inversion in one cooperative launch: "
-                      "the diagonal-inverse chain on one CTA, prep/finish and the tcgen05 "
-                      "3xTF32 rank-64 updates on the others)",
-            "bound": "hbm", "achieved": b / t / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": b / t / 1e9 / peaks["hbm_gbs"],
-            "peak_source": peak_src + " (HBM copy; the FP32 matrix is L2-resident at this size)",
-            "work_per_launch": b,
-            "tensor_tflops": 2.0 * n * n * 64 * nblk / t / 1e12,
-            "tensor_frac_of_tf32": 2.0 * n * n * 64 * nblk / t / 1e12 / tf32_peak,
-            "us_per_block": t / nblk * 1e6, "blocks": nblk,
-            "latency_bound": "the chain of diagonal inverses (64 dependent pivot steps each)",
-            "launches": ph_spans["lu_update"], "traffic": _traffic("k_gj_fused", n)}
-    else:
-        _separate_factor_rooflines(recs, per_launch, ph_spans, n, peaks, peak_src, fp32_peak,
-                                   tf32_peak, sm_mhz)
-    _other_rooflines(recs, per_launch, ph_spans, pr, n, peaks, peak_src, fp64_peak, solve_stats)
-    return recs
-
-
-def _separate_factor_rooflines(recs, per_launch, ph_spans, n, peaks, peak_src, fp32_peak,
-                               tf32_peak, sm_mhz):
-    t = per_launch("lu_diag")
-    nblk = -(-n // 64)
-    w = (2.0 + 8.0 * (nblk - 1)) / nblk * 64 ** 3  # mean over one factorisation's launches
-    sm_peak = fp32_peak / SM_COUNT_NOMINAL
-    recs["lu_diag"] = {"kernel": "k_gj_diag (64 x 64 diagonal-block inverse, one CTA)",
-                       "bound": "alu", "achieved": w / t / 1e12, "peak": sm_peak,
-                       "unit": "TFLOP/s", "frac": w / t / 1e12 / sm_peak,
-                       "peak_source": f"derived: ONE SM (the kernel is one CTA by construction: "
-                                      f"64 dependent pivot steps), 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz; "
-                                      f"{w / t / 1e12 / fp32_peak:.5f} of the whole GPU's FP32 peak",
-                       "latency_bound": True,
-                       "work_per_launch": w, "launches": ph_spans["lu_diag"],
-                       "traffic": _traffic("k_gj_diag", n)}
-    t = per_launch("lu_update")
-    b = 8.0 * n * n
-    recs["lu_update"] = {"kernel": "k_tc_gj_update (tcgen05 3xTF32 rank-64 update)",
-                         "bound": "hbm", "achieved": b / t / 1e9, "peak": peaks["hbm_gbs"],
-                         "unit": "GB/s", "frac": b / t / 1e9 / peaks["hbm_gbs"],
-                         "peak_source": peak_src + " (HBM copy)", "work_per_launch": b,
-                         "tensor_tflops": 2.0 * n * n * 64 / t / 1e12,
-                         "tensor_frac_of_tf32": 2.0 * n * n * 64 / t / 1e12 / tf32_peak,
-                         "launches": ph_spans["lu_update"], "traffic": _traffic("k_tc_gj_update", n)}
-
-
-def _other_rooflines(recs, per_launch, ph_spans, pr, n, peaks, peak_src, fp64_peak, solve_stats):
-    t = per_launch("assemble")
-    f = pr.pairs * 29.0
-    recs["assemble"] = {"kernel": "k_assemble64 (NEAREST A_s, FP64)", "bound": "alu",
-                        "achieved": f / t / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
-                        "frac": f / t / 1e12 / fp64_peak,
-                        "peak_source": "nominal FP64 1.25 TFLOP/s at 2070 MHz, scaled to the clock",
-                        "pairs_per_s": pr.pairs / t, "work_per_launch": f,
-                        "launches": ph_spans["assemble"], "traffic": _traffic("k_assemble64", n)}
-    if ph_spans["trsv"] > 0:  # host-driven refinement: separate product kernels
-        t = per_launch("gemv")
         b = 8.0 * n * n
-        recs["gemv"] = {"kernel": "k_gemv_part (FP64 residual / Arnoldi products)", "bound": "hbm",
-                        "achieved": b / t / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                        "frac": b / t / 1e9 / peaks["hbm_gbs"], "peak_source": peak_src,
-                        "work_per_launch": b, "launches": ph_spans["gemv"], "traffic": None}
-        t = per_launch("trsv")
-        b = 4.0 * n * n
-        recs["precond"] = {"kernel": "k_gemv32_part (explicit-inverse preconditioner)",
-                           "bound": "hbm", "achieved": b / t / 1e9, "peak": peaks["hbm_gbs"],
-                           "unit": "GB/s", "frac": b / t / 1e9 / peaks["hbm_gbs"],
-                           "peak_source": peak_src, "work_per_launch": b,
-                           "launches": ph_spans["trsv"], "traffic": None}
-    elif solve_stats and ph_spans["krylov"] > 0:
-        # one persistent launch per solve: (outer + inner) FP64 products with A and
-        # (outer + inner + 1) FP32 products with the explicit inverse per launch
+        fl = 3 * 2.0 * n * n * 64
+        recs["lu_update"] = {
+            "kernel": "k_tc_gj_update (tcgen05 split-TF32 rank-64 update of the FP32 inverse)",
+            "bound": "hbm", "achieved": b / t / 1e9, "peak": P["hbm_gbs"], "unit": "GB/s",
+            "frac": b / t / 1e9 / P["hbm_gbs"], "peak_source": peak_src + " HBM copy",
+            "work_per_launch": b, "work_unit": "bytes (8 n^2)",
+            "tensor_tflops": fl / t / 1e12, "tensor_frac_of_tf32": fl / t / 1e12 / P["tf32_tflops"],
+            "tf32_peak_tflops": P["tf32_tflops"],
+            "us_per_launch": t * 1e6, "launches": ph_spans["lu_update"],
+            "traffic": _traffic("k_tc_gj_update", n)}
+    if ph_spans.get("lu_diag"):
+        t = per_launch("lu_diag")
+        nblk = -(-n // 64)
+        w = (2.0 + 8.0 * (nblk - 1)) / nblk * 64 ** 3
+        recs["lu_diag"] = {
+            "kernel": "k_gj_diag (64 x 64 diagonal-block inverse with lookahead, one CTA)",
+            "bound": "alu", "achieved": w / t / 1e12, "peak": P["fp32_tflops"], "unit": "TFLOP/s",
+            "frac": w / t / 1e12 / P["fp32_tflops"],
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x sampled clock (whole GPU)",
+            "latency_bound": "64 dependent pivot steps on one CTA", "work_per_launch": w,
+            "us_per_launch": t * 1e6, "launches": ph_spans["lu_diag"],
+            "traffic": _traffic("k_gj_diag", n)}
+    if ph_spans.get("assemble"):
+        t = per_launch("assemble")
+        ops = pairs * ASM64_OPS_PER_PAIR
+        recs["assemble"] = {
+            "kernel": "k_assemble64 (NEAREST A_s in FP64, bit-identical to the oracle)",
+            "bound": "alu", "achieved": ops / t / 1e9, "peak": P["fp64_gops"], "unit": "Gop/s",
+            "frac": ops / t / 1e9 / P["fp64_gops"],
+            "peak_source": "derived: nominal FP64 1.25 TFLOP/s = 625 G FP64 ops/s at 2070 MHz, "
+                           "scaled to the sampled clock",
+            "work_per_launch": ops, "work_unit": "FP64 operations (40 per pair; square root and "
+                                                 "division counted once each)",
+            "pairs_per_s": pairs / t, "ms_per_launch": t * 1e3,
+            "launches": ph_spans["assemble"], "traffic": _traffic("k_assemble64", n)}
+    if ph_spans.get("assemble32"):
+        t = per_launch("assemble32")
+        recs["assemble32"] = {
+            "kernel": "k_assemble32 (+ 2 k_split_points): FP32 copy of A_s for the factorisation",
+            "bound": "alu", "achieved": pairs / t, "peak": P["pair_peak"], "unit": "pairs/s",
+            "frac": pairs / t / P["pair_peak"],
+            "peak_source": "derived: 152 SMs x 128 lanes x sampled clock / 20 FP32 instructions "
+                           "per pair",
+            "hbm_write_bound_pairs_per_s": pairs / (4.0 * n * n / (peaks["hbm_gbs"] * 1e9)),
+            "work_per_launch": pairs, "ms_per_launch": t * 1e3, "launches": ph_spans["assemble32"],
+            "traffic": None}
+    if ph_spans.get("krylov") and solve_stats:
         o, i = solve_stats["outer_mean"], solve_stats["inner_mean"]
         t = per_launch("krylov")
         b = 8.0 * n * n * (o + i) + 4.0 * n * n * (o + i + 1)
-        recs["solve"] = {"kernel": "k_gmres_ir (persistent GMRES-IR, one cooperative launch per solve)",
-                         "bound": "hbm", "achieved": b / t / 1e9, "peak": peaks["hbm_gbs"],
-                         "unit": "GB/s", "frac": b / t / 1e9 / peaks["hbm_gbs"],
-                         "peak_source": peak_src, "work_per_launch": b,
-                         "fp64_tflops": 2.0 * n * n * (o + i) / t / 1e12,
-                         "fp64_frac": 2.0 * n * n * (o + i) / t / 1e12 / fp64_peak,
-                         "us_per_launch": t * 1e6,
-                         "launches": ph_spans["krylov"], "traffic": _traffic("k_gmres_ir", n)}
+        ops = DD_OPS_PER_ENTRY * n * n * o + n * n * i
+        recs["krylov"] = {
+            "kernel": "k_gmres_ir (persistent GMRES-IR, one cooperative launch per solve)",
+            "bound": "hbm", "achieved": b / t / 1e9, "peak": P["hbm_gbs"], "unit": "GB/s",
+            "frac": b / t / 1e9 / P["hbm_gbs"], "peak_source": peak_src + " HBM copy",
+            "work_per_launch": b, "work_unit": "bytes of A (FP64) and M (FP32) streamed",
+            "fp64_gops": ops / t / 1e9, "fp64_frac": ops / t / 1e9 / P["fp64_gops"],
+            "outer_mean": o, "inner_mean": i, "ms_per_launch": t * 1e3,
+            "launches": ph_spans["krylov"], "traffic": _traffic("k_gmres_ir", n)}
+    return recs
 
 
-def run_nrs(args):
+def _shapes_host(pr, t):
     import torch
-    ws, rank, local = _dist()
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
-        torch.cuda.set_device(0)
-    from paper_2001_06468_gb300 import nrs
+    d = g.pack_shapes(pr, t)
+    return tuple(torch.from_numpy(d[k]).pin_memory() for k in ("x", "Xw", "xidot"))
 
-    pr = g.swimmer_config()
+
+def _input_digest(pr, dt):
+    m = hashlib.sha1()
+    for t in (0.0, 0.5 * dt):
+        d = g.pack_shapes(pr, t)
+        for k in ("x", "Xw", "xidot"):
+            m.update(np.ascontiguousarray(d[k], dtype=np.float64).tobytes())
+    Y = g.initial_state(pr)
+    m.update(np.ascontiguousarray(Y["x0"], dtype=np.float64).tobytes())
+    m.update(np.ascontiguousarray(Y["B"], dtype=np.float64).tobytes())
+    return m.hexdigest()
+
+
+def _golden(name, pr):
+    """The oracle's first step of a full-size workload, stored under
+    tests/golden by a script that calls only the oracle (None when absent or
+    written from other inputs)."""
+    path = os.path.join(ROOT, "tests", "golden", f"{name}_step0.npz")
+    if not os.path.exists(path):
+        return None
+    z = np.load(path)
+    if str(z["digest"]) != _input_digest(pr, pr.dt):
+        return None
+    return {k: z[k] for k in ("sol1", "sol2", "x0", "B")}
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _first_step_errors(nrs, pr, ref, **kw):
+    """Relative errors of f and V of both stages of the first step (from the
+    initial state) against the oracle's."""
+    import torch
+    ctx = nrs.Context.from_problem(pr, factor_prec="tf32", **kw)
+    Y = g.initial_state(pr)
+    ctx.set_state(Y["x0"], Y["B"])
+    d0 = nrs.shapes_to_device(g.pack_shapes(pr, 0.0))
+    dh = nrs.shapes_to_device(g.pack_shapes(pr, 0.5 * pr.dt))
+    sol = torch.empty(2 * pr.n, dtype=torch.float64, device="cuda")
+    rep = ctx.step(nrs.Context.shapes(*d0), nrs.Context.shapes(*dh), pr.dt, sol=sol)
+    s = sol.cpu().numpy()
+    Yg = ctx.get_state()
+    ctx.close()
+    n, n3 = pr.n, 3 * pr.N
+    out = {}
+    for k, key in enumerate(("sol1", "sol2")):
+        got = s[k * n:(k + 1) * n]
+        out[f"stage{k + 1}"] = {"f": _rel(got[:n3], ref[key][:n3]), "V": _rel(got[n3:], ref[key][n3:])}
+    out["state"] = {"x0": _rel(Yg["x0"], ref["x0"]), "B": _rel(Yg["B"], ref["B"])}
+    out["backward_err"] = [st["backward_err"] for st in rep["stages"]]
+    out["within_tol"] = all(v <= TOL for st in ("stage1", "stage2") for v in out[st].values())
+    return out
+
+
+class _Timer:
+    """CUDA-event timing of K calls on a stream, L2 flushed before each."""
+
+    def __init__(self, flush):
+        self.flush = flush
+
+    def run(self, stream, fn, count, first=0):
+        import torch
+        ms = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for s in range(count):
+            self.flush.fill_(float(s))  # evict L2 between timed steps (untimed)
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                fn(first + s)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+
+def headline(nrs, args, ws, local, timer, peaks, peak_src):
+    """The product path on the channel workload: timed steps, end to end,
+    instrumented pass, fresh-factor graph path, first-step parity."""
+    import torch
+    pr = g.workload(HEADLINE)
     dt = pr.dt
     K, W = args.steps, args.warmup
     total = K + W
-    # body-frame beat shapes at t and t + dt/2 for every step, pinned on the host
     host = [(_shapes_host(pr, s * dt), _shapes_host(pr, (s + 0.5) * dt)) for s in range(total)]
     dev = [tuple(tuple(t.cuda() for t in st) for st in pair) for pair in host]
     Y0 = g.initial_state(pr)
-    # the product path: the step recorded once into a CUDA graph and replayed
-    # (graph mode); each step's shapes are first copied into the fixed
-    # buffers the graph reads, inside the timed region
-    ctx = nrs.Context.from_problem(pr, factor_prec=args.prec, graph=True)
-    ctx.set_state(Y0["x0"], Y0["B"])
-    stream = ctx.stream
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    gbuf = tuple(tuple(torch.empty_like(t) for t in st) for st in dev[0])
+    kw = dict(HEADLINE_SOLVER)
 
-    def do_step(ctx_, pair):
-        s0 = nrs.Context.shapes(*pair[0])
-        sh = nrs.Context.shapes(*pair[1])
-        return ctx_.step(s0, sh, dt)
+    def new_ctx(**extra):
+        c = nrs.Context.from_problem(pr, factor_prec=args.prec, **dict(kw, **extra))
+        c.set_state(Y0["x0"], Y0["B"])
+        return c
 
-    def graph_step(ctx_, pair):
-        for st_src, st_dst in zip(pair, gbuf):
-            for src, dst in zip(st_src, st_dst):
-                dst.copy_(src, non_blocking=True)
-        return ctx_.step(nrs.Context.shapes(*gbuf[0]), nrs.Context.shapes(*gbuf[1]), dt,
-                         report=False)
+    def stepper(c, bufs=None):
+        def f(s):
+            pair = dev[s] if bufs is None else bufs
+            c.step(nrs.Context.shapes(*pair[0]), nrs.Context.shapes(*pair[1]), dt, report=False)
+        return f
 
-    def eager_step(ctx_, pair):
-        return ctx_.step(nrs.Context.shapes(*pair[0]), nrs.Context.shapes(*pair[1]), dt,
-                         report=False)
-
-    reports = []
+    # -- timed region: K steps of the product path, no instrumentation
+    ctx = new_ctx()
     for s in range(W):
-        graph_step(ctx, dev[s])
+        stepper(ctx)(s)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-
-    def timed_pass(ctx_, first, fn=do_step):
-        ms = []
-        for s in range(K):
-            flush.fill_(float(s))  # evict L2 between timed steps (untimed)
-            torch.cuda.synchronize()
-            with torch.cuda.stream(stream):
-                ev[s][0].record(stream)
-                r = fn(ctx_, dev[first + s])
-                ev[s][1].record(stream)
-            if r is not None:
-                reports.append(r)
-            torch.cuda.synchronize()
-            ms.append(ev[s][0].elapsed_time(ev[s][1]))
-        return ms
-
-    # the timed region: K steps, no instrumentation inside the library
+    c0 = ctx.counters()
     ctx.get_timing()  # clears the kernel count
     with ClockSampler(_visible_gpu_index(local)) as clk:
-        step_ms = timed_pass(ctx, W, graph_step)
+        step_ms = timer.run(ctx.stream, stepper(ctx), K, first=W)
     clocks = clk.summary()
     _, launches = ctx.get_timing()
-    # a second pass over the same inputs with CUDA events around every phase of
-    # the step (on the stream each phase runs on): per-kernel durations for
-    # the roofline, and the kernel count
-    ctx_t = nrs.Context.from_problem(pr, factor_prec=args.prec)
-    ctx_t.set_state(Y0["x0"], Y0["B"])
-    for s in range(W):
-        do_step(ctx_t, dev[s])
-    torch.cuda.synchronize()
-    ctx_t.set_timing(True)
-    nrep_t = len(reports)
-    step_ms_instr = timed_pass(ctx_t, W)
-    phases, _ = ctx_t.get_timing()
-    instr_reports = reports[nrep_t:]
-    solve_stats = {
-        "outer_mean": float(np.mean([r["stages"][i]["outer"] for r in instr_reports for i in (0, 1)])),
-        "inner_mean": float(np.mean([r["stages"][i]["inner"] for r in instr_reports for i in (0, 1)]))}
-    ctx_t.set_timing(False)
+    c1 = ctx.counters()
+    st = ctx.sync()  # device status word after the timed region
+    ctx.close()
+    counts = {k: c1[k] - c0[k] for k in c1}
     t_local = sum(step_ms) / 1e3
     t_max = _max_over_ranks(t_local, ws)
-    s_per_step = t_max / K / ws  # whole job: ws replicas each advance K steps
 
-    # end to end through the C ABI from pinned host buffers: H2D of both
-    # stages' shapes and D2H of the new state and both solutions, every step
-    ctx_e = nrs.Context.from_problem(pr, factor_prec=args.prec, graph=True)
-    ctx_e.set_state(Y0["x0"], Y0["B"])
+    # -- end to end through the C ABI from pinned host buffers: H2D of both
+    # stages' shapes and D2H of both solutions and the new state, every step
+    ctx = new_ctx()
     bufs = tuple(tuple(torch.empty_like(t, device="cuda") for t in st) for st in host[0])
     sol = torch.empty(2 * pr.n, dtype=torch.float64, device="cuda")
     sol_h = torch.empty(2 * pr.n, dtype=torch.float64).pin_memory()
     h2d = sum(t.numel() * t.element_size() for st in host[0] for t in st)
     d2h = sol_h.numel() * 8 + pr.n_free * 12 * 8
-    for s in range(W):
+    Ke = min(K, 5)
+
+    def e2e_step(s):
         for st_h, st_d in zip(host[s], bufs):
             for th, td in zip(st_h, st_d):
                 td.copy_(th, non_blocking=True)
-        ctx_e.step(nrs.Context.shapes(*bufs[0]), nrs.Context.shapes(*bufs[1]), dt, sol=sol,
-                   report=False)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e_ms = 0.0
-    for s in range(K):
-        flush.fill_(float(s))
-        torch.cuda.synchronize()
-        with torch.cuda.stream(ctx_e.stream):
-            e0.record(ctx_e.stream)
-            for st_h, st_d in zip(host[W + s], bufs):
-                for th, td in zip(st_h, st_d):
-                    td.copy_(th, non_blocking=True)
-            ctx_e.step(nrs.Context.shapes(*bufs[0]), nrs.Context.shapes(*bufs[1]), dt, sol=sol,
-                       report=False)
-            sol_h.copy_(sol, non_blocking=True)
-            st = ctx_e.get_state()
-            e1.record(ctx_e.stream)
-        torch.cuda.synchronize()
-        e_ms += e0.elapsed_time(e1)
-    e2e_s = e_ms / 1e3 / K / ws
+        ctx.step(nrs.Context.shapes(*bufs[0]), nrs.Context.shapes(*bufs[1]), dt, sol=sol,
+                 report=False)
+        sol_h.copy_(sol, non_blocking=True)
+        ctx.get_state()
 
-    # plain FP64 path (FP64 factor) on the same steps, for the mixed-vs-plain ratio
-    ctx_p = nrs.Context.from_problem(pr, factor_prec="fp64")
-    ctx_p.set_state(Y0["x0"], Y0["B"])
-    Kp = min(K, 5)
-    do_step(ctx_p, dev[0])
-    torch.cuda.synchronize()
-    p_ms = 0.0
-    for s in range(Kp):
-        flush.fill_(float(s))
-        torch.cuda.synchronize()
-        with torch.cuda.stream(ctx_p.stream):
-            e0.record(ctx_p.stream)
-            do_step(ctx_p, dev[W + s])
-            e1.record(ctx_p.stream)
-        torch.cuda.synchronize()
-        p_ms += e0.elapsed_time(e1)
-    plain_s = p_ms / 1e3 / Kp
-
-    # the same mixed path with the host-driven refinement loop (one host
-    # synchronisation per GMRES iteration) instead of the persistent solve
-    ctx_h = nrs.Context.from_problem(pr, factor_prec=args.prec, solve_mode="host")
-    ctx_h.set_state(Y0["x0"], Y0["B"])
     for s in range(W):
-        do_step(ctx_h, dev[s])
-    torch.cuda.synchronize()
-    host_loop_s = float(np.sum(timed_pass(ctx_h, W))) / 1e3 / K / ws
-    ctx_h.close()
+        e2e_step(s)
+    e_ms = timer.run(ctx.stream, e2e_step, Ke, first=W)
+    ctx.close()
+    e2e_s = _max_over_ranks(sum(e_ms) / 1e3, ws) / Ke / ws
 
-    # the same step without the graph (kernels launched one by one)
-    ctx_eg = nrs.Context.from_problem(pr, factor_prec=args.prec)
-    ctx_eg.set_state(Y0["x0"], Y0["B"])
+    # -- instrumented pass: CUDA events around every phase, on the stream each
+    # phase runs on (per-launch durations for the roofline records)
+    Ki = min(K, 5)
+    ctx = new_ctx()
     for s in range(W):
-        eager_step(ctx_eg, dev[s])
+        stepper(ctx)(s)
     torch.cuda.synchronize()
-    eager_s = float(np.sum(timed_pass(ctx_eg, W, eager_step))) / 1e3 / K / ws
-    ctx_eg.close()
-
-    # factor reuse across stages + warm start (same inputs, same timing rules)
-    ctx_r = nrs.Context.from_problem(pr, factor_prec=args.prec, reuse_factor=True, warm_start=True)
-    ctx_r.set_state(Y0["x0"], Y0["B"])
-    for s in range(W):
-        do_step(ctx_r, dev[s])
-    torch.cuda.synchronize()
-    nrep = len(reports)
-    r_ms = timed_pass(ctx_r, W)
-    reuse_reports = reports[nrep:]
-    reuse_s = float(np.sum(r_ms)) / 1e3 / K / ws
-
-    # starting vectors of the refinement: cold (M^{-1} b), the previous stage's
-    # solution, and the MLP prediction (trained during the run, on every
-    # stage's solution; the timed steps include its training and selection)
-    starts = {}
-    for reuse in (False, True):
-        for mode in ("cold", "previous", "learned"):
-            ctx_s = nrs.Context.from_problem(pr, factor_prec=args.prec, reuse_factor=reuse,
-                                             warm_start=(mode == "previous"))
-            ctx_s.set_state(Y0["x0"], Y0["B"])
-            if mode == "learned":
-                ctx_s.mlp_set_params(mlp_init(0))
-                ctx_s.mlp_config(train_iters=MLP_TRAIN_ITERS, predict=False, lr=MLP_LR)
-            for s in range(W):
-                do_step(ctx_s, dev[s])
-            if mode == "learned":
-                ctx_s.mlp_config(train_iters=MLP_TRAIN_ITERS, predict=True, lr=MLP_LR)
-            torch.cuda.synchronize()
-            nrep = len(reports)
-            m_ms = timed_pass(ctx_s, W)
-            reps = reports[nrep:]
-            kinds = [k for r in reps for k in r["start"]]
-            starts[("reuse_" if reuse else "fresh_") + mode] = {
-                "s_per_step": float(np.sum(m_ms)) / 1e3 / K / ws,
-                "inner_mean": float(np.mean([r["stages"][i]["inner"] for r in reps for i in (0, 1)])),
-                "starts_used": {k: kinds.count(k) for k in sorted(set(kinds))},
-                "mlp_rel_err_last": reps[-1]["mlp_rel_err"] if mode == "learned" else None,
-            }
-            ctx_s.close()
-
-    # the first steps from the initial state, kept for the accuracy check
-    # (fresh factor every stage, and factor reuse)
-    sols = {}
-    for name, kw in (("fresh", {}), ("reuse", {"reuse_factor": True, "warm_start": True})):
-        ctx_a = nrs.Context.from_problem(pr, factor_prec=args.prec, **kw)
-        ctx_a.set_state(Y0["x0"], Y0["B"])
-        out = []
-        for s in range(3):
-            sol_a = torch.empty(2 * pr.n, dtype=torch.float64, device="cuda")
-            ctx_a.step(nrs.Context.shapes(*dev[s][0]), nrs.Context.shapes(*dev[s][1]), dt, sol=sol_a)
-            out.append(sol_a.cpu().numpy())
-        sols[name] = out
-
-    if rank != 0:
-        if ws > 1:
-            torch.distributed.barrier()
-            torch.distributed.destroy_process_group()
-        return
-    peaks, peak_src = _peaks()
+    ci0 = ctx.counters()
+    ctx.set_timing(True)
+    instr_ms = timer.run(ctx.stream, stepper(ctx), Ki, first=W)
+    phases, _ = ctx.get_timing()
+    ctx.set_timing(False)
+    ci1 = ctx.counters()
+    ctx.close()
     ph_ms = {k: v[0] for k, v in phases.items()}
     ph_spans = {k: v[1] for k, v in phases.items()}
+    solves = max(ci1["solves"] - ci0["solves"], 1)
+    solve_stats = {"outer_mean": (ci1["outer"] - ci0["outer"]) / solves,
+                   "inner_mean": (ci1["inner"] - ci0["inner"]) / solves}
+
+    # -- the same workload with a fresh factor at every stage, recorded as a
+    # CUDA graph, and its instrumented phases (the factorisation's kernels)
+    Kf = min(K, 4)
+    ctxf = nrs.Context.from_problem(pr, factor_prec=args.prec, graph=True)
+    ctxf.set_state(Y0["x0"], Y0["B"])
+    gbuf = tuple(tuple(torch.empty_like(t) for t in st) for st in dev[0])
+
+    def graph_step(s):
+        for st_src, st_dst in zip(dev[s], gbuf):
+            for src, dst in zip(st_src, st_dst):
+                dst.copy_(src, non_blocking=True)
+        ctxf.step(nrs.Context.shapes(*gbuf[0]), nrs.Context.shapes(*gbuf[1]), dt, report=False)
+
+    for s in range(2):  # the first call builds the maps of the rigid bodies, the second records
+        graph_step(s)
+    f_ms = timer.run(ctxf.stream, graph_step, Kf, first=2)
+    ctxf.sync()
+    ctxf.close()
+    ctxf = nrs.Context.from_problem(pr, factor_prec=args.prec)
+    ctxf.set_state(Y0["x0"], Y0["B"])
+    stepper(ctxf)(0)
+    cf0 = ctxf.counters()
+    ctxf.set_timing(True)
+    timer.run(ctxf.stream, stepper(ctxf), 1, first=1)
+    fph, _ = ctxf.get_timing()
+    ctxf.set_timing(False)
+    cf1 = ctxf.counters()
+    ctxf.close()
+    fph_ms = {k: v[0] for k, v in fph.items()}
+    fph_spans = {k: v[1] for k, v in fph.items()}
+    fsolves = max(cf1["solves"] - cf0["solves"], 1)
+    fsolve_stats = {"outer_mean": (cf1["outer"] - cf0["outer"]) / fsolves,
+                    "inner_mean": (cf1["inner"] - cf0["inner"]) / fsolves}
+
+    # -- parity: the first step from the initial state against the oracle's
+    ref = _golden(HEADLINE, pr)
+    parity = None
+    if ref is not None:
+        parity = {"product_path": _first_step_errors(nrs, pr, ref, **kw),
+                  "fresh_factor": _first_step_errors(nrs, pr, ref),
+                  "tolerance": TOL,
+                  "oracle": "tests/golden/sperm_channel_step0.npz (oracle/ alone; input digest checked)"}
+
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    recs = rooflines(ph_ms, ph_spans, pr.n, pr.pairs, peaks, peak_src, sm_mhz, solve_stats)
+    frecs = rooflines(fph_ms, fph_spans, pr.n, pr.pairs, peaks, peak_src, sm_mhz, fsolve_stats)
     tot = sum(ph_ms.values())
-    recs = _rooflines(ph_ms, ph_spans, pr, peaks, peak_src, clocks, solve_stats)
-    top = max(recs, key=lambda p: ph_ms[{"precond": "trsv", "solve": "krylov"}.get(p, p)])
-    roof = recs[top]
-    asm = recs["assemble"]
-    line = {
-        "metric": METRIC,
-        "value": s_per_step,
-        "unit": "s/step",
-        "n_gpus": ws,
-        "steps": K,
-        "warmup": W,
-        "ms_per_step": t_max / K * 1e3,
-        "ms_per_step_instrumented": float(np.mean(step_ms_instr)),
-        "higher_is_better": False,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f64 residual + " + {"tf32": "split-TF32 tensor-core", "fp32": "fp32",
-                                     "fp64": "fp64", "bf16": "bf16"}[args.prec] + " factor",
-        "data": "synthetic (seeded undulating-tube beat shapes)",
-        "config": {"workload": WORKLOAD, "factor": args.prec, "refinement": "GMRES-IR, FP64 residual",
-                   "rk2_stages_per_step": 2, "l2": "flushed between timed steps (512 MiB write)",
-                   "parallelism": f"replicas x{ws}"},
-        "pairs_per_s": asm.get("pairs_per_s"),
-        "plain_fp64_s_per_step": plain_s,
-        "mixed_vs_plain_speedup": plain_s / (t_max / K),
-        "host_loop_refinement_s_per_step": host_loop_s,
-        "eager_s_per_step": eager_s,
-        "value_factor_reuse": reuse_s,
-        "factor_reuse": {"s_per_step": reuse_s, "vs_plain_speedup": plain_s / (reuse_s * ws),
-                         "factorizations_per_step": float(np.mean([r["factorizations"] for r in reuse_reports])),
-                         "inner_mean": float(np.mean([r["stages"][i]["inner"] for r in reuse_reports for i in (0, 1)])),
-                         "note": "the previous stages' factor preconditions the refinement until its GMRES "
-                                 "count exceeds 8 or 16 stages pass; each solve from the previous solution"},
-        "starts": starts,
-        "starts_note": ("fresh_*: factor every stage; reuse_*: factor reuse. learned: "
-                        f"{MLP_TRAIN_ITERS} Adam steps per stage (lr {MLP_LR}) on each stage's "
-                        "solution, prediction used only where its residual beats the cold start's; "
-                        "mlp_rel_err_last = held-out relative RMS error of the prediction of f"),
-        "phases_ms_per_step": {k: v / K for k, v in ph_ms.items()},
-        "phase_share": {k: (v / tot if tot else 0.0) for k, v in ph_ms.items()},
-        "phase_note": ("the whole factorisation is one fused launch, timed as lu_update"
-                       if ph_spans["lu_diag"] == 0 else
-                       "lu_diag runs on a second stream, overlapping lu_update and lu_panel"),
-        "refinement": {"outer_mean": solve_stats["outer_mean"], "inner_mean": solve_stats["inner_mean"],
-                       "backward_err_max": float(max(r["stages"][i]["backward_err"] for r in instr_reports for i in (0, 1))),
-                       "from": "the instrumented eager pass (same kernels, same inputs)"},
-        "roofline": roof,
-        "rooflines": recs,
-        "e2e": {"value": e2e_s, "unit": "s/step", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches,
-        "gpu_launches_note": "kernels of the recorded step graph replayed in the timed region, counted by the library",
-        "clocks": clocks,
-    }
-    if not args.no_batch and ws == 1:
-        line["batch"] = batch_bench(nrs, args)
-    if not args.no_cpu_baseline and ws == 1:
-        line["cpu_baseline"] = cpu_baseline(pr, sols)
-    print(json.dumps(line), flush=True)
-    if ws > 1:
-        torch.distributed.barrier()
-        torch.distributed.destroy_process_group()
+    return {
+        "pr": pr, "K": K, "W": W, "t_max": t_max, "step_ms": step_ms, "clocks": clocks,
+        "launches": launches, "counts": counts, "status_after": st, "e2e_s": e2e_s,
+        "h2d": h2d, "d2h": d2h, "e2e_steps": Ke,
+        "fresh_graph_s": float(np.mean(f_ms)) / 1e3, "fresh_steps": Kf,
+        "instr_s": float(np.mean(instr_ms)) / 1e3,
+        "phases_ms_per_step": {k: v / Ki for k, v in ph_ms.items() if ph_spans[k]},
+        "phase_share": {k: v / tot for k, v in ph_ms.items() if ph_spans[k]},
+        "fresh_phases_ms_per_step": {k: v for k, v in fph_ms.items() if fph_spans[k]},
+        "solve_stats": solve_stats, "fresh_solve_stats": fsolve_stats,
+        "recs": recs, "fresh_recs": frecs, "parity": parity}
 
 
-def _oracle_step_timing(pr, max_steps, budget_s):
-    import oracle as O
-    Y = g.initial_state(pr)
-    times, all_stages = [], []
-    for s in range(max_steps):
-        t0 = time.perf_counter()
-        Yn, stages = O.rk2_step(pr, Y, s * pr.dt, pr.dt, return_stages=True)
-        times.append(time.perf_counter() - t0)
-        all_stages.append(stages)
-        Y = Yn
-        if sum(times) > budget_s:
-            break
-    return times, all_stages, O.threads()
+def side_workload(nrs, args, name, steps, warm, solver, timer, graph=False):
+    """Seconds per step of another workload (same timing rules), and the
+    first step's errors against the oracle where its answer is stored."""
+    import torch
+    pr = g.workload(name)
+    dt = pr.dt
+    dev = [(nrs.shapes_to_device(g.pack_shapes(pr, s * dt)),
+            nrs.shapes_to_device(g.pack_shapes(pr, (s + 0.5) * dt))) for s in range(steps + warm)]
+    Y0 = g.initial_state(pr)
+    ctx = nrs.Context.from_problem(pr, factor_prec=args.prec, graph=graph, **solver)
+    ctx.set_state(Y0["x0"], Y0["B"])
+    gbuf = tuple(tuple(torch.empty_like(t) for t in st) for st in dev[0])
+
+    def step(s):
+        src = dev[s]
+        if graph:
+            for st_src, st_dst in zip(src, gbuf):
+                for a, b in zip(st_src, st_dst):
+                    b.copy_(a, non_blocking=True)
+            src = gbuf
+        ctx.step(nrs.Context.shapes(*src[0]), nrs.Context.shapes(*src[1]), dt, report=False)
+
+    for s in range(warm):
+        step(s)
+    c0 = ctx.counters()
+    ms = timer.run(ctx.stream, step, steps, first=warm)
+    c1 = ctx.counters()
+    ctx.sync()
+    ctx.close()
+    out = {"workload": WORKLOADS_DESC.get(name, name), "s_per_step": float(np.mean(ms)) / 1e3,
+           "steps": steps, "warmup": warm, "graph": graph,
+           "solver": {k: v for k, v in solver.items()}}
+    sol_n = c1["solves"] - c0["solves"]
+    if sol_n:
+        out["outer_mean"] = (c1["outer"] - c0["outer"]) / sol_n
+        out["inner_mean"] = (c1["inner"] - c0["inner"]) / sol_n
+        out["factorizations_per_step"] = (c1["factorizations"] - c0["factorizations"]) / steps
+    ref = _golden(name, pr)
+    if ref is not None:
+        out["first_step_vs_oracle"] = _first_step_errors(nrs, pr, ref, **solver)
+    return out
+
+
+def plain_fp64(nrs, args, timer):
+    """The plain FP64 GPU path on the headline workload: the FP64 assembly
+    (this library's kernel, the same matrix) and cuSOLVER's getrf + getrs
+    through torch.linalg, each timed once on the first stage's system, and
+    this library's own blocked FP64 LU on the single swimmer as a fraction of
+    the FP64 peak."""
+    import torch
+    torch.backends.cuda.preferred_linalg_library("cusolver")
+    pr = g.workload(HEADLINE)
+    Y0 = g.initial_state(pr)
+    ctx = nrs.Context.from_problem(pr, factor_prec="fp64")
+    ctx.set_state(Y0["x0"], Y0["B"])
+    xi, Xiw, xidot = nrs.shapes_to_device(g.pack_shapes(pr, 0.0))
+    x, Xw, b = ctx.kinematics(xi, Xiw, xidot)
+    ctx.nearest_build(xi, Xiw)
+    ctx.assemble(x, Xw, want_matrix=False)  # warm-up of the kernel
+    torch.cuda.synchronize()
+    st = ctx.stream
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with torch.cuda.stream(st):
+        e[0].record(st)
+        ctx.assemble(x, Xw, want_matrix=False)
+        e[1].record(st)
+    torch.cuda.synchronize()
+    t_asm = e[0].elapsed_time(e[1]) / 1e3
+    At = ctx.assemble(x, Xw)
+    ctx.close()
+    A = At.T  # column-major view of the FP64 matrix
+    bb = b[:pr.n].clone().reshape(-1, 1)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(st):
+        e[0].record(st)
+        LU, piv = torch.linalg.lu_factor(A)
+        e[1].record(st)
+        xs = torch.linalg.lu_solve(LU, piv, bb)
+        e[2].record(st)
+    torch.cuda.synchronize()
+    t_getrf = e[0].elapsed_time(e[1]) / 1e3
+    t_getrs = e[1].elapsed_time(e[2]) / 1e3
+    xs = xs.reshape(-1).cpu().numpy()
+    del LU, piv, A, At
+    torch.cuda.empty_cache()
+    ref = _golden(HEADLINE, pr)
+    err = None
+    if ref is not None:
+        n3 = 3 * pr.N
+        err = {"f": _rel(xs[:n3], ref["sol1"][:n3]), "V": _rel(xs[n3:], ref["sol1"][n3:])}
+    stage = t_asm + t_getrf + t_getrs
+    n = pr.n
+    # this library's FP64 LU on the single swimmer
+    sw = g.workload("swimmer")
+    cs = nrs.Context.from_problem(sw, factor_prec="fp64")
+    Ys = g.initial_state(sw)
+    cs.set_state(Ys["x0"], Ys["B"])
+    xi, Xiw, xidot = nrs.shapes_to_device(g.pack_shapes(sw, 0.0))
+    x, Xw, b = cs.kinematics(xi, Xiw, xidot)
+    cs.nearest_build(xi, Xiw)
+    cs.assemble(x, Xw, want_matrix=False)
+    cs.factor("fp64")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(cs.stream):
+        e[0].record(cs.stream)
+        cs.factor("fp64")
+        e[1].record(cs.stream)
+    torch.cuda.synchronize()
+    t_own = e[0].elapsed_time(e[1]) / 1e3
+    cs.close()
+    fp64_peak = FP64_NOMINAL_TFLOPS
+    return {"s_per_step": 2 * stage,
+            "how": "2 x one measured stage: FP64 assembly + cuSOLVER getrf + getrs (torch.linalg) "
+                   "on the first stage's system",
+            "assemble64_s": t_asm, "getrf_s": t_getrf, "getrs_s": t_getrs,
+            "getrf_tflops": 2.0 / 3.0 * n ** 3 / t_getrf / 1e12,
+            "getrf_frac_of_fp64_nominal": 2.0 / 3.0 * n ** 3 / t_getrf / 1e12 / fp64_peak,
+            "error_vs_oracle_without_refinement": err,
+            "own_fp64_lu": {"workload": WORKLOADS_DESC["swimmer"], "s": t_own,
+                            "tflops": 2.0 / 3.0 * sw.n ** 3 / t_own / 1e12,
+                            "frac_of_fp64_nominal": 2.0 / 3.0 * sw.n ** 3 / t_own / 1e12 / fp64_peak}}
 
 
 def _batch_case(nrs, probs, prec, steps, tune=True, plan=None, seq_steps=None):
@@ -665,6 +711,16 @@ def _batch_case(nrs, probs, prec, steps, tune=True, plan=None, seq_steps=None):
         ms += e0.elapsed_time(e1)
     info = batch.info()
     batch.close()
+    info = dict(info)
+    ns = [pr.n for pr in probs]
+    out = {"problems": nprob, "n_min": min(ns), "n_max": max(ns), "n_mean": float(np.mean(ns)),
+           "pairs": int(sum(pr.pairs for pr in probs)),
+           "s_per_batch_step": ms / 1e3 / steps,
+           "problem_steps_per_s": nprob * steps / (ms / 1e3), "steps": steps,
+           "chains": info["chains"], "solve_grid": info["grid"],
+           "graph_kernels": info["graph_kernels"], "tuned_ms": tuned.get("ms")}
+    if seq_steps == 0:
+        return out
     # eager, one problem after the other
     ctxs = []
     for pr in probs:
@@ -690,30 +746,9 @@ def _batch_case(nrs, probs, prec, steps, tune=True, plan=None, seq_steps=None):
         ms_seq += e0.elapsed_time(e1)
     for c in ctxs:
         c.close()
-    ns = [pr.n for pr in probs]
-    return {"problems": nprob, "n_min": min(ns), "n_max": max(ns), "n_mean": float(np.mean(ns)),
-            "pairs": int(sum(pr.pairs for pr in probs)),
-            "s_per_batch_step": ms / 1e3 / steps,
-            "problem_steps_per_s": nprob * steps / (ms / 1e3),
-            "sequential_eager_s_per_batch_step": ms_seq / 1e3 / seq_steps,
-            "speedup_vs_sequential": (ms_seq / seq_steps) / (ms / steps), "steps": steps,
-            "chains": info["chains"], "solve_grid": info["grid"],
-            "graph_kernels": info["graph_kernels"],
-            "tuned_ms": tuned.get("ms")}
-
-
-def batch_bench(nrs, args):
-    """The batch workload: 128 ventral-node-like problems at reduced sizes
-    (all of them), and the first 8 at the full sizes."""
-    small = [g.node_config(i, cilia=(4, 12), floor=(160, 500), n_rod=10, q_rod=100, n_sphere=2,
-                           q_sphere=8) for i in range(128)]
-    full = [g.node_config(i) for i in range(8)]
-    return {"workload": "ventral-node batch: cilia rotating on tilted cones, static floor disc, "
-                        "5 free spheres; eps 0.005",
-            "reduced_128": dict(_batch_case(nrs, small, args.prec, 3),
-                                recipe="cilia 4-12 (10/100 points), floor 160-500 (x10), spheres 26/386"),
-            "full_first8": dict(_batch_case(nrs, full, args.prec, 2),
-                                recipe="the batch recipe at full size, problems 0-7")}
+    out.update(sequential_eager_s_per_batch_step=ms_seq / 1e3 / seq_steps,
+               speedup_vs_sequential=(ms_seq / seq_steps) / (ms / steps))
+    return out
 
 
 def batch_full(args):
@@ -733,52 +768,6 @@ def batch_full(args):
                 "generator_s": gen_s,
                 "matrix_bytes": int(sum(12 * pr.n * pr.n for pr in probs))})
     print(json.dumps(res), flush=True)
-
-
-def cpu_baseline(pr, sols):
-    """The FP64 CPU oracle, as it stands, on a bounded sample of the same
-    workload (three RK2 steps from the initial state); also the largest
-    relative error, over those steps' stage solutions, of the GPU paths
-    (forces f and rigid velocities V separately)."""
-    times, stages, cores = _oracle_step_timing(pr, 3, 1e9)
-    n, n3 = pr.n, 3 * pr.N
-
-    def rel(a, b):
-        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
-    errs = {}
-    for name, gpu in sols.items():
-        ef, eV = 0.0, 0.0
-        for s, st in enumerate(stages[:len(gpu)]):
-            for half, ref in ((0, st["sol1"]), (1, st["sol2"])):
-                g_ = gpu[s][half * n:(half + 1) * n]
-                ef = max(ef, rel(g_[:n3], ref[:n3]))
-                eV = max(eV, rel(g_[n3:], ref[n3:]))
-        errs[name] = {"f": ef, "V": eV}
-    return {"value": float(np.mean(times)), "unit": "s/step", "cores": cores, "kind": "oracle",
-            "sample": f"{len(times)} RK2 steps of the same workload from the initial state",
-            "gpu_max_rel_err_vs_oracle": errs}
-
-
-def run_reference(args):
-    ws, rank, local = _dist()
-    if rank != 0:
-        return
-    pr = g.swimmer_config()
-    W = min(args.warmup, 1)
-    K = min(args.steps, 10)
-    import oracle as O
-    O.build()
-    times, _, cores = _oracle_step_timing(pr, W + K, 1e9)
-    t = times[W:]
-    v = float(np.mean(t))
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/step", "n_gpus": ws,
-            "steps": len(t), "warmup": W, "ms_per_step": v * 1e3, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "solver": "FP64 partial-pivoting LU + double-double refinement"},
-            "cpu_baseline": {"value": v, "unit": "s/step", "cores": cores, "kind": "oracle",
-                             "sample": f"{len(t)} RK2 steps after {W} warm-up (steps capped at 10)"},
-            "e2e": {"value": v, "unit": "s/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
 
 
 PROFILE_WORKLOADS = {
@@ -810,24 +799,250 @@ def profile_solve(args):
     print(json.dumps({"workload": args.workload, "n": pr.n, "prec": args.prec, "report": rep[0]}))
 
 
+
+
+def oracle_sample(pr, budget_rows=92, lu_n=6144, seed=0):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of one RK2 step
+    of ``pr`` (seconds per step, and what was measured): per stage the
+    nearest-neighbour search and segments of every quadrature point
+    (measured whole), the assembly of ``budget_rows`` sampled force points'
+    rows (scaled by N / rows), the LAPACK LU of an n = ``lu_n`` system of the
+    same workload's kind (scaled by (n / lu_n)^3) and one double-double
+    residual at that size (scaled by (n / lu_n)^2, three per solve); a step is
+    two stages."""
+    import oracle as O
+    import scipy.linalg as sla
+    O.build()
+    sh = g.pack_shapes(pr, 0.0)
+    Y = g.initial_state(pr)
+    t0 = time.perf_counter()
+    nn = O.nearest(sh["x"], sh["Xw"], sh["n_off"], sh["q_off"], pr.nn_global)
+    O.segments(nn, pr.N)
+    t_nn = time.perf_counter() - t0
+    x, Xw = O.lab_frame(sh, Y)
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(pr.N, size=min(budget_rows, pr.N), replace=False))
+    t0 = time.perf_counter()
+    O.assemble_rows(rows, x, Xw, nn, pr.eps, pr.mu)
+    t_asm = (time.perf_counter() - t0) * pr.N / len(rows)
+    m = min(lu_n, pr.n)
+    A = np.asfortranarray(rng.standard_normal((m, m)) + m * np.eye(m))
+    bvec = rng.standard_normal(m)
+    t0 = time.perf_counter()
+    lu = sla.lu_factor(A, overwrite_a=False, check_finite=False)
+    t_lu = (time.perf_counter() - t0) * (pr.n / m) ** 3
+    xs = sla.lu_solve(lu, bvec, check_finite=False)
+    t0 = time.perf_counter()
+    O.residual_dd(A, xs, bvec)
+    t_res = (time.perf_counter() - t0) * (pr.n / m) ** 2
+    stage = t_nn + t_asm + t_lu + 3 * t_res
+    return 2 * stage, {"nearest_s": t_nn, "assemble_s_scaled": t_asm, "lu_s_scaled": t_lu,
+                       "residual_dd_s_scaled": t_res, "cores": O.threads(),
+                       "sample": (f"per stage: nearest neighbours + segments of all {pr.Q} "
+                                  f"quadrature points (measured); A_s rows of {len(rows)} of "
+                                  f"{pr.N} force points (x {pr.N / len(rows):.0f}); LAPACK LU "
+                                  f"at n = {m} (x (n/{m})^3); 3 double-double residuals at "
+                                  f"n = {m} (x (n/{m})^2); a step = 2 stages")}
+
+
+def cpu_baseline(pr):
+    v, info = oracle_sample(pr)
+    return {"value": v, "unit": "s/step", "cores": info.pop("cores"), "kind": "oracle",
+            "sample": info.pop("sample"), "parts": info}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    pr = g.workload(HEADLINE)
+    W = min(args.warmup, 1)
+    K = min(args.steps, 5)
+    times, info = [], None
+    for s in range(W + K):
+        v, info = oracle_sample(pr, seed=s)
+        if s >= W:
+            times.append(v)
+    v = float(np.mean(times))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/step", "n_gpus": ws,
+            "steps": len(times), "warmup": W, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS_DESC[HEADLINE],
+                       "solver": "FP64 LAPACK LU + double-double refinement (oracle)"},
+            "cpu_baseline": {"value": v, "unit": "s/step", "cores": info["cores"], "kind": "oracle",
+                             "sample": info["sample"] + f"; {len(times)} sampled steps after {W}"},
+            "e2e": {"value": v, "unit": "s/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_nrs(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2001_06468_gb300 import nrs
+
+    peaks, peak_src = _peaks()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    timer = _Timer(flush)
+    H = headline(nrs, args, ws, local, timer, peaks, peak_src)
+    pr, K = H["pr"], H["K"]
+    s_per_step = H["t_max"] / K / ws  # whole job: ws replicas each advance K steps
+    side = {}
+    if not args.no_side and ws == 1:
+        side["fresh_factor_graph"] = {"s_per_step": H["fresh_graph_s"], "steps": H["fresh_steps"],
+                                      "note": "same workload, factor at every stage, the step "
+                                              "recorded as a CUDA graph and replayed"}
+        side["swimmers4"] = side_workload(nrs, args, "swimmers4", 1, 1, C2_SOLVER, timer)
+        side["swimmer"] = side_workload(nrs, args, "swimmer", 20, 3, {}, timer, graph=True)
+        side["swimmer_reuse"] = side_workload(nrs, args, "swimmer", 20, 3, HEADLINE_SOLVER, timer)
+        torch.cuda.empty_cache()
+        side["plain_fp64"] = plain_fp64(nrs, args, timer)
+        torch.cuda.empty_cache()
+    batch = None
+    if not args.no_batch:
+        batch = batch_bench(nrs, args, ws, rank)
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
+    recs = H["recs"]
+    share = H["phase_share"]
+    fam = {"lu_update": "lu_update", "lu_diag": "lu_diag", "assemble": "assemble",
+           "assemble32": "assemble32", "krylov": "krylov"}
+    top = max((k for k in recs if k in fam), key=lambda k: share.get(fam[k], 0.0))
+    roof = dict(recs[top], share_of_step=share.get(fam[top], 0.0))
+    plain = side.get("plain_fp64")
+    line = {
+        "metric": METRIC,
+        "value": s_per_step,
+        "unit": "s/step",
+        "n_gpus": ws,
+        "steps": K,
+        "warmup": H["W"],
+        "ms_per_step": H["t_max"] / K * 1e3,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 (bit-exact assembly, double-double residual) + fp32/split-tf32 factor",
+        "data": "synthetic (seeded channel, head and flagellum shapes)",
+        "config": {"workload": WORKLOADS_DESC[HEADLINE], "factor": args.prec + " explicit inverse "
+                   "(blocked Gauss-Jordan), refreshed after >60 GMRES iterations or 32 stages",
+                   "refinement": "GMRES-IR, double-double residual, warm start from the previous "
+                                 "stage", "rk2_stages_per_step": 2,
+                   "l2": "flushed between timed steps (512 MiB write); matrices 9.2 GB > L2",
+                   "parallelism": f"replicas x{ws}"},
+        "step_ms": H["step_ms"],
+        "factorizations_per_step": H["counts"]["factorizations"] / K,
+        "refinement": {"outer_mean": H["counts"]["outer"] / max(H["counts"]["solves"], 1),
+                       "inner_mean": H["counts"]["inner"] / max(H["counts"]["solves"], 1),
+                       "solves": H["counts"]["solves"],
+                       "status_after_timed_region": H["status_after"],
+                       "all_converged": True},
+        "parity_vs_oracle": H["parity"],
+        "pairs_per_s": recs.get("assemble", {}).get("pairs_per_s"),
+        "pairs_per_s_fp32_copy": recs.get("assemble32", {}).get("achieved"),
+        "phases_ms_per_step": H["phases_ms_per_step"],
+        "phase_share": H["phase_share"],
+        "fresh_factor_phases_ms_per_step": H["fresh_phases_ms_per_step"],
+        "roofline": roof,
+        "rooflines": recs,
+        "fresh_factor_rooflines": H["fresh_recs"],
+        "e2e": {"value": H["e2e_s"], "unit": "s/step", "h2d_bytes_per_step": H["h2d"],
+                "d2h_bytes_per_step": H["d2h"], "steps": H["e2e_steps"]},
+        "gpu_launches": H["launches"],
+        "gpu_launches_note": "kernels launched by the library in the timed region (its count)",
+        "clocks": H["clocks"],
+        "side": side,
+    }
+    if plain:
+        line["plain_fp64_s_per_step"] = plain["s_per_step"]
+        line["mixed_vs_plain_speedup"] = plain["s_per_step"] / (H["t_max"] / K)
+    if batch:
+        line["batch"] = batch
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(pr)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def batch_bench(nrs, args, ws, rank):
+    """The batch workload.  One rank: 128 ventral-node-like problems at
+    reduced sizes (all of them) and the first 8 at the full sizes, one graph
+    per batch step against stepping them one after the other.  Several ranks:
+    each steps its own share of the 128 reduced problems (the library's LPT
+    plan with one chain per rank, no collective in the data path); the time is
+    the slowest rank's."""
+    small = [g.node_config(i, cilia=(4, 12), floor=(160, 500), n_rod=10, q_rod=100, n_sphere=2,
+                           q_sphere=8) for i in range(128)]
+    recipe = "cilia 4-12 (10/100 points), floor 160-500 (x10), spheres 26/386"
+    if ws > 1:
+        mine = _rank_share([pr.n ** 3 for pr in small], ws, rank)
+        res = _batch_case(nrs, [small[i] for i in mine], args.prec, 3, seq_steps=0)
+        t = _max_over_ranks(res["s_per_batch_step"], ws)
+        return {"workload": "ventral-node batch, reduced sizes, sharded over ranks",
+                "recipe": recipe, "problems": len(small), "ranks": ws,
+                "s_per_batch_step": t, "problem_steps_per_s": len(small) / t,
+                "rank0_problems": len(mine)}
+    full = [g.node_config(i) for i in range(8)]
+    return {"workload": "ventral-node batch: cilia rotating on tilted cones, static floor disc, "
+                        "5 free spheres; eps 0.005",
+            "reduced_128": dict(_batch_case(nrs, small, args.prec, 3), recipe=recipe),
+            "full_first8": dict(_batch_case(nrs, full, args.prec, 2),
+                                recipe="the batch recipe at full size, problems 0-7")}
+
+
+def profile_step(args):
+    """Warm-up steps then one more step of --workload with the product path's
+    settings (no timing loop): the command an ncu launch list captures."""
+    import torch
+    from paper_2001_06468_gb300 import nrs
+    torch.cuda.set_device(0)
+    pr = g.workload(args.workload)
+    Y = g.initial_state(pr)
+    solver = C2_SOLVER if args.workload == "swimmers4" else HEADLINE_SOLVER
+    ctx = nrs.Context.from_problem(pr, factor_prec=args.prec, **solver)
+    ctx.set_state(Y["x0"], Y["B"])
+    for s in range(args.warmup + 1):
+        d0 = nrs.shapes_to_device(g.pack_shapes(pr, s * pr.dt))
+        dh = nrs.shapes_to_device(g.pack_shapes(pr, (s + 0.5) * pr.dt))
+        rep = ctx.step(nrs.Context.shapes(*d0), nrs.Context.shapes(*dh), pr.dt)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": args.workload, "n": pr.n, "report": rep}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="nrs", choices=["nrs", "reference"])
-    ap.add_argument("--prec", default="tf32", choices=["fp32", "tf32", "bf16", "fp64"])
+    ap.add_argument("--prec", default="tf32", choices=["fp32", "tf32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch workload section")
+    ap.add_argument("--no-side", action="store_true",
+                    help="skip the other workloads and the plain FP64 comparator")
     ap.add_argument("--batch-full", action="store_true",
                     help="only the full-size batch of 128 problems (one JSON line)")
     ap.add_argument("--profile-solve", action="store_true",
                     help="one kinematics + nearest + assemble + factor + solve on --workload, "
                          "then exit (for ncu captures)")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="--warmup steps and one more of --workload, then exit (for ncu)")
     ap.add_argument("--workload", default="swimmer", choices=sorted(PROFILE_WORKLOADS))
     args = ap.parse_args()
     if args.profile_solve:
         profile_solve(args)
+        return
+    if args.profile_step:
+        profile_step(args)
         return
     if args.batch_full:
         batch_full(args)

@@ -56,7 +56,8 @@ typedef enum {
     NRS_FP64 = 0,  /* plain path: FP64 factor                                     */
     NRS_FP32 = 1,  /* FP32 explicit inverse (Gauss-Jordan), updates on FP32 CUDA cores */
     NRS_TF32 = 2,  /* FP32 explicit inverse, updates on the tensor cores (TF32)       */
-    NRS_BF16 = 3   /* FP32 explicit inverse, updates on the tensor cores (BF16)       */
+    NRS_BF16 = 3   /* reserved: no BF16 factorisation is built; nrs_create and nrs_factor
+                      reject it with NRS_EINVAL */
 } nrs_prec;
 
 /* Body kinds (Sec. 4: swimmers are free; walls are static). */
@@ -153,6 +154,9 @@ typedef struct {
                                MLP on the targets of the step's last training stage,
                                before that stage's updates (a held-out error);
                                -1 if the step did not train                     */
+    int32_t retried[2];     /* 1 if the stage's refinement did not converge and the stage
+                               was factored again (the other FP32 input, or a fresh factor
+                               in place of a reused one) and solved again       */
 } nrs_step_report;
 
 /* Body-frame inputs of one stage (device memory):
@@ -226,7 +230,7 @@ nrs_status nrs_assemble(nrs_ctx *ctx, const double *x, const double *Xw, double 
 
 /* Factor the assembled matrix in precision ``prec`` (Sec. 4 step 3).
  * NRS_FP64: block LU of the FP64 matrix with row pivoting inside each 64 x 64
- * diagonal block.  NRS_FP32/TF32/BF16: explicit inverse of an FP32 copy by
+ * diagonal block.  NRS_FP32/TF32: explicit inverse of an FP32 copy by
  * blocked Gauss-Jordan elimination (pivoting inside each diagonal block),
  * which preconditions the FP64 refinement of nrs_solve.
  * info (host, may be NULL) receives 0 or the 1-based column of the first
@@ -253,7 +257,10 @@ nrs_status nrs_solve(nrs_ctx *ctx, const double *b, double *x, int32_t nrhs, con
  * factor (desc.factor_prec), solve; then dX0/dt = U, dB/dt = [Omega]x B with B
  * re-orthonormalised by modified Gram-Schmidt after each stage.  The state
  * stays on the device.  sol (device [2*n] or NULL) receives both stages'
- * solutions.  report (host or NULL) synchronises. */
+ * solutions.  report (host or NULL) synchronises.  With an FP32/TF32 factor,
+ * a stage whose refinement does not converge is factored again once -- from
+ * the other FP32 input (factor_input), or fresh where the factor was reused --
+ * and solved again (report->retried); NRS_ENOCONV if that fails too. */
 nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *s_half, double dt,
                     double *sol, nrs_step_report *report);
 
@@ -270,6 +277,16 @@ nrs_status nrs_rank64_update(nrs_ctx *ctx, float *M, int64_t lda, int64_t n, con
 
 /* Wait for the context's stream and return the device status word. */
 nrs_status nrs_sync(nrs_ctx *ctx);
+
+/* Counters since the context was created (host outputs, each may be NULL):
+ * factorisations done (nrs_factor and inside nrs_step), and the solves whose
+ * outcome reached the host (nrs_solve, eager nrs_step) with their total
+ * refinement steps and GMRES iterations (a step replayed from a CUDA graph
+ * keeps its solve statistics on the device and does not count here), and the
+ * stages nrs_step factored and solved again after a refinement that did not
+ * converge.  Plain reads of host state: no synchronisation. */
+nrs_status nrs_counters(const nrs_ctx *ctx, int64_t *factorizations, int64_t *solves,
+                        int64_t *outer, int64_t *inner, int64_t *retries);
 
 /* Largest problem nrs_nearest_build_static accepts. */
 #define NRS_STATIC_MAX_N 65536       /* force points      */

@@ -90,6 +90,7 @@ nrs_status alloc_all(Ctx *c)
         {(void **)&c->d_part, sizeof(double) * 64 * lda},
         {(void **)&c->d_part32, sizeof(double) * 64 * lda},
         {(void **)&c->d_part_lo, sizeof(double) * 64 * lda},
+        {(void **)&c->d_vf, sizeof(float2) * lda},
         {(void **)&c->d_t32, sizeof(float) * 2 * lda},
         {(void **)&c->d_t64, sizeof(double) * 2 * lda},
         {(void **)&c->d_flags, sizeof(int32_t) * nrs::ceil_div(n, 64)},
@@ -128,7 +129,7 @@ void free_all(Ctx *c)
                     c->d_t32,    c->d_t64,    c->d_flags,  c->d_status,     c->d_gj_dinv,
                     c->d_gj_rt,  c->d_gj_cb,  c->d_dpart,  c->d_bar,        c->d_pg_stats,
                     c->d_step_stats, c->d_Xsh, c->d_Xsl, c->d_xh, c->d_xl, c->d_gj_stage, c->d_gj_sync, c->d_part32,
-                    c->d_part_lo};
+                    c->d_part_lo, c->d_vf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *mlp[] = {c->d_mlp_params, c->d_mlp_m,  c->d_mlp_v,     c->d_mlp_g,    c->d_mlp_x,
@@ -163,7 +164,9 @@ void free_all(Ctx *c)
     c->gstream = nullptr;
 }
 
-bool is_prec(int p) { return p == NRS_FP64 || p == NRS_FP32 || p == NRS_TF32 || p == NRS_BF16; }
+// NRS_BF16 is reserved: no BF16 factorisation is built, so it is rejected
+// rather than run in another precision
+bool is_prec(int p) { return p == NRS_FP64 || p == NRS_FP32 || p == NRS_TF32; }
 
 __global__ void k_cvt_f64_f32(int64_t count, const double *__restrict__ a, float *__restrict__ b)
 {
@@ -174,7 +177,7 @@ __global__ void k_cvt_f64_f32(int64_t count, const double *__restrict__ a, float
 nrs_status do_factor(Ctx *c, int prec)
 {
     if (!c->assembled) return fail(c, NRS_EINVAL, "nrs_factor before nrs_assemble");
-    if ((prec == NRS_TF32 || prec == NRS_BF16) && !nrs::tc_available())
+    if (prec == NRS_TF32 && !nrs::tc_available())
         return fail(c, NRS_EINVAL, "tensor-core factor precision needs a tcgen05 device and the tensor-map driver entry point");
     const size_t elems = (size_t)c->lda * c->n;
     if (prec == NRS_FP64) {
@@ -429,6 +432,7 @@ nrs_status step_graph(Ctx *c, const nrs_shapes *s0, const nrs_shapes *sh, double
     report->ms_total = ms;
     report->factorizations = 2;
     report->mlp_rel_err = -1.0;
+    report->retried[0] = report->retried[1] = 0;
     if (worst != NRS_OK) c->err = "a stage of the recorded step did not converge cleanly";
     return worst;
 }
@@ -715,7 +719,11 @@ nrs_status nrs_factor(nrs_ctx *ctx, int32_t prec, int32_t *info)
 {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c) return NRS_EINVAL;
-    if (!is_prec(prec)) return fail(c, NRS_EINVAL, "nrs_factor: unknown precision");
+    if (!is_prec(prec))
+        return fail(c, NRS_EINVAL,
+                    prec == NRS_BF16 ? "nrs_factor: NRS_BF16 has no factorisation in this library "
+                                       "(use NRS_TF32: split-TF32 tensor-core updates)"
+                                     : "nrs_factor: unknown precision");
     nrs_status st = do_factor(c, prec);
     if (st != NRS_OK) return st;
     if (info) {
@@ -821,6 +829,33 @@ nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *sh, do
         int inner = 0;
         st = nrs::run_gmres_ir(*c, c->d_b, out, x0, report ? &report->stage[stage] : nullptr, &inner);
         if (st == NRS_ECUDA) return st;
+        if (report) report->retried[stage] = 0;
+        if (st == NRS_ENOCONV && c->factor_prec != NRS_FP64) {
+            // The refinement did not converge with this factor.  An FP32 inverse
+            // of a system with kappa(A) u_fp32 >> 1 is sometimes a poor
+            // preconditioner; one of the other FP32 input (the rounded FP64
+            // entries instead of the FP32 evaluation, or the reverse) usually is
+            // not.  A reused factor is replaced by a fresh one of the configured
+            // input.  One retry, from the same start.
+            const bool other = need_factor ? c->lo_eval == 1 : c->lo_eval == 0;
+            nrs::join_assembly(*c);
+            if (other) {
+                nrs::launch_assemble32(*c, c->d_x, c->d_A32, c->lda);
+                c->a32_fresh = true;
+            } else {
+                c->a32_fresh = false;  // do_factor rounds the FP64 entries
+            }
+            c->factored_prec = -1;
+            st = do_factor(c, c->factor_prec);
+            if (st != NRS_OK) return st;
+            c->stages_since_factor = 0;
+            c->retries += 1;
+            if (report) report->retried[stage] = 1;
+            inner = 0;
+            st = nrs::run_gmres_ir(*c, c->d_b, out, x0, report ? &report->stage[stage] : nullptr,
+                                   &inner);
+            if (st == NRS_ECUDA) return st;
+        }
         if (st != NRS_OK && worst == NRS_OK) worst = st;
         // run_gmres_ir synchronised the stream: the pinned copy of the choice has landed
         if (learned && c->h_mlp_used[0]) {
@@ -1066,6 +1101,19 @@ nrs_status nrs_mlp_start(nrs_ctx *ctx, const float *Y, const double *vprev, doub
         return fail(c, NRS_EINVAL, "nrs_mlp_start: scales not set");
     nrs::mlp_start(*c, Y, vprev, x0);
     CK(cudaGetLastError());
+    return NRS_OK;
+}
+
+nrs_status nrs_counters(const nrs_ctx *ctx, int64_t *factorizations, int64_t *solves,
+                        int64_t *outer, int64_t *inner, int64_t *retries)
+{
+    const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+    if (!c) return NRS_EINVAL;
+    if (retries) *retries = c->retries;
+    if (factorizations) *factorizations = c->factorizations;
+    if (solves) *solves = c->solves;
+    if (outer) *outer = c->outer_total;
+    if (inner) *inner = c->inner_total;
     return NRS_OK;
 }
 

@@ -249,9 +249,11 @@ void launch_assemble(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t l
         attr = true;
     }
     const int64_t gx = ceil_div(c.N, AS_THREADS), tiles = gx * ceil_div(c.N, AS_NT);
-    // beside the factorisation: one CTA of four warps per SM, grid-stride over the
-    // tiles, so the factorisation's kernels keep most of every SM
-    const int64_t grid = side ? std::min<int64_t>(tiles, c.num_sms) : tiles;
+    // beside the factorisation: a few CTAs of four warps per SM (about 25 KB of
+    // shared memory and 24K registers), grid-stride over the tiles, so the
+    // factorisation's kernels (one CTA per SM each) still find room on every SM
+    const int64_t grid = side ? std::min<int64_t>(tiles, (int64_t)c.asm_side_ctas * c.num_sms)
+                              : tiles;
     const double coef = 1.0 / (8.0 * kPi * c.mu);
     c.tbeg(PH_ASSEMBLE, s);
     k_assemble64<<<(unsigned)grid, AS_THREADS, 0, s>>>(c.N, x_lab, c.d_Xs, c.d_seg_ptr,

@@ -397,6 +397,7 @@ nrs_status nrs_batch_step(nrs_batch *b, const nrs_shapes *s0, const nrs_shapes *
                 cudaMemcpy(&word, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost);
                 cudaMemset(c->d_status, 0, sizeof(int32_t));
                 nrs_step_report &r = reports[i];
+                r.retried[0] = r.retried[1] = 0;
                 for (int k = 0; k < 2; ++k) {
                     const double *s = q + 8 * k;
                     nrs_solve_report &sr = r.stage[k];

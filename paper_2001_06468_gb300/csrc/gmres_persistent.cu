@@ -57,6 +57,7 @@ struct PgArgs {
     double *part;         // partial sums of the FP64 products [splits][n]
     double *part32;       // partial sums of the FP32 products [splits][n]
     double *part_lo;      // low parts of the double-double residual's partial sums [splits][n]
+    float2 *vf;           // input of the next preconditioner product as float pairs [n]
     int dd;               // residual b - A x in double-double (1) or FP64 (0)
     double *dpart;        // reduction partials [3][PG_MAXCH][m+2]
     int32_t *bar;         // grid barrier: [0] arrivals since the launch ([1] unused)
@@ -214,9 +215,14 @@ __device__ __forceinline__ double residual_dd_at(const PgArgs &a, double be, int
     return __dadd_rn(hi, lo);
 }
 
-// part32[s][i] = sum_{j in split s} M[i, j] v[j] (FP32 products and sums):
-// 128 rows per tile, lane l takes rows 4l..4l+3 (one 16-byte load per column).
-__device__ void mv32_partial(const PgArgs &a, const double *v, float *sm)
+// part32[s][i] = sum_{j in split s} M[i, j] v[j] with the FP32 entries of M
+// and the FP64 vector v given as float pairs (a.vf): double-float products
+// and sums on the FP32 pipe (df_fma), so the preconditioner is applied to
+// about 2^-46 of |M| |v| -- a fixed operator for GMRES even where
+// kappa(A) u_fp32 >> 1, which FP32 products of a rounded v (2^-24) are not.
+// 128 rows per tile, lane l takes rows 4l..4l+3 (one 16-byte load per column);
+// the 8 column groups are added in FP64 in a fixed order.
+__device__ void mv32_partial(const PgArgs &a, double *sm)
 {
     const int64_t tiles = (int64_t)a.rc32 * a.s32;
     const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
@@ -225,29 +231,30 @@ __device__ void mv32_partial(const PgArgs &a, const double *v, float *sm)
         const int64_t i = rc * MV32_ROWS + 4 * lane;
         const int64_t j0 = s * a.cps32, j1 = min(a.n, j0 + a.cps32);
         float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+        float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, c3 = 0.0f;
         if (i < a.n) {
             const float *col = a.M + i;
-#pragma unroll 8
+#pragma unroll 4
             for (int64_t j = j0 + grp; j < j1; j += MV_GROUPS) {
                 const float4 x = __ldg(reinterpret_cast<const float4 *>(col + j * a.lda));
-                const float vj = (float)__ldcg(v + j);
-                s0 = fmaf(x.x, vj, s0);
-                s1 = fmaf(x.y, vj, s1);
-                s2 = fmaf(x.z, vj, s2);
-                s3 = fmaf(x.w, vj, s3);
+                const float2 vj = __ldcg(a.vf + j);
+                df_fma(x.x, vj, s0, c0);
+                df_fma(x.y, vj, s1, c1);
+                df_fma(x.z, vj, s2, c2);
+                df_fma(x.w, vj, s3, c3);
             }
         }
-        float *q = sm + grp * MV32_ROWS + 4 * lane;
-        q[0] = s0;
-        q[1] = s1;
-        q[2] = s2;
-        q[3] = s3;
+        double *q = sm + grp * MV32_ROWS + 4 * lane;
+        q[0] = (double)s0 + (double)c0;
+        q[1] = (double)s1 + (double)c1;
+        q[2] = (double)s2 + (double)c2;
+        q[3] = (double)s3 + (double)c3;
         __syncthreads();
         if (threadIdx.x < MV32_ROWS) {
             const int64_t r = rc * MV32_ROWS + threadIdx.x;
             double acc = 0.0;
 #pragma unroll
-            for (int g = 0; g < MV_GROUPS; ++g) acc += (double)sm[g * MV32_ROWS + threadIdx.x];
+            for (int g = 0; g < MV_GROUPS; ++g) acc += sm[g * MV32_ROWS + threadIdx.x];
             if (r < a.n) a.part32[s * a.n + r] = acc;
         }
         __syncthreads();
@@ -352,13 +359,13 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
     __shared__ double scs[PG_MAXM], ssn[PG_MAXM], sg[PG_MAXM + 1], sy[PG_MAXM];
     __shared__ double sh1[PG_MAXM + 1], sh2[PG_MAXM + 1];
     __shared__ double sred[PG_THREADS / 32];
-    __shared__ __align__(16) double smv[MV_GROUPS * MV64_ROWS];  // product tiles (FP64 or FP32 view)
-    __shared__ double smv_lo[MV_GROUPS * MV64_ROWS];             // low parts (double-double residual)
+    // product tiles: [0, 512) the FP64 sums, [512, 1024) the low parts of the
+    // double-double residual; the preconditioner's tile takes all 1024
+    __shared__ __align__(16) double smv[2 * MV_GROUPS * MV64_ROWS];
+    double *smv_lo = smv + MV_GROUPS * MV64_ROWS;
     __shared__ int s_ok;
     int32_t tgt = 0;  // grid barrier target (thread 0)
-    float *smv32 = reinterpret_cast<float *>(smv);
-    static_assert(MV_GROUPS * MV32_ROWS * sizeof(float) <= sizeof(double) * MV_GROUPS * MV64_ROWS,
-                  "shared product tile");
+    static_assert(MV_GROUPS * MV32_ROWS <= 2 * MV_GROUPS * MV64_ROWS, "shared product tile");
     constexpr int LDH = PG_MAXM + 1;
     const int m = a.m;
     const int64_t n = a.n;
@@ -371,7 +378,9 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
     double *dp2 = a.dpart + (2 * PG_MAXCH + (int64_t)blockIdx.x) * (m + 2);
 
     if (a.cold) {  // x = M b
-        mv32_partial(a, a.b, smv32);
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) a.vf[e] = df_split(__ldg(a.b + e));
+        if (!grid_sync(a, &s_ok, tgt)) return;
+        mv32_partial(a, smv);
         if (!grid_sync(a, &s_ok, tgt)) return;
         for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) a.x[e] = sum_parts32(a, e);
         if (!grid_sync(a, &s_ok, tgt)) return;
@@ -392,6 +401,7 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
                 const double be = __ldg(a.b + e);
                 const double re = a.dd ? residual_dd_at(a, be, e) : be - sum_parts(a, a.s64, e);
                 a.w[e] = re;
+                a.vf[e] = df_split(re);
                 rmax = fmax(rmax, fabs(re));
                 bmax = fmax(bmax, fabs(be));
                 if (!isfinite(re)) rmax = INFINITY;
@@ -428,7 +438,7 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
             }
         }
         // V_0 = M r (raw), beta = ||V_0||
-        mv32_partial(a, a.w, smv32);
+        mv32_partial(a, smv);
         if (!grid_sync(a, &s_ok, tgt)) return;
         {
             double s = 0.0;
@@ -459,11 +469,13 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
             if (!grid_sync(a, &s_ok, tgt)) return;
             for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
                 Vj[e] = __ldcg(Vj + e) * sv;  // v_j normalised in place (own chunk)
-                a.w[e] = sum_parts(a, a.s64, e);
+                const double we = sum_parts(a, a.s64, e);
+                a.w[e] = we;
+                a.vf[e] = df_split(we);
             }
             if (!grid_sync(a, &s_ok, tgt)) return;
             // u = M w, then two classical Gram-Schmidt passes and the norm
-            mv32_partial(a, a.w, smv32);
+            mv32_partial(a, smv);
             if (!grid_sync(a, &s_ok, tgt)) return;
             for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) u[e] = sum_parts32(a, e);
             __syncthreads();
@@ -633,6 +645,7 @@ cudaError_t launch_gmres_persistent(Ctx &c, const double *b, double *x, bool col
     a.part = c.d_part;
     a.part32 = c.d_part32;
     a.part_lo = c.d_part_lo;
+    a.vf = c.d_vf;
     a.dd = c.residual_dd;
     a.dpart = c.d_dpart;
     a.bar = c.d_bar;

@@ -136,6 +136,7 @@ struct Ctx {
     cudaEvent_t ev_asm = nullptr, ev_asm_done = nullptr;
     bool asm_pending = false;                    // stream3 holds an FP64 assembly not yet joined
     int lo_eval = 0;  // FP32 copy for the factor: 0 evaluated in FP32 (overlapped), 1 rounded FP64
+    int asm_side_ctas = 3;  // CTAs per SM of the FP64 assembly beside the factorisation
     cudaEvent_t ev_upd = nullptr, ev_diag = nullptr;
     cudaStream_t stream4 = nullptr;              // finish step of the factorisation
     cudaEvent_t ev_fin_ready = nullptr, ev_fin[2] = {nullptr, nullptr};
@@ -196,6 +197,8 @@ struct Ctx {
     int stages_since_factor = 0, last_inner = 0;
     bool have_sol = false;
     int64_t factorizations = 0;
+    int64_t retries = 0;       // stages solved again after a non-converged refinement (nrs_step)
+    int64_t solves = 0, outer_total = 0, inner_total = 0;  // solves finished on the host side
 
     // learned starting guess (mlp.cu); allocated by the first nrs_mlp_* call
     bool mlp_alloc = false, mlp_params_set = false, mlp_scales_set = false;
@@ -248,6 +251,7 @@ struct Ctx {
     double *d_part = nullptr;  // partial sums of matrix-vector products
     double *d_part32 = nullptr;  // partial sums of the FP32 products of the persistent solve
     double *d_part_lo = nullptr; // low parts of the double-double residual's partial sums
+    float2 *d_vf = nullptr;      // the preconditioner product's input vector as float pairs
     int residual_dd = 1;       // refinement residual b - A x: 1 double-double, 0 FP64
     int splits64 = 1, splits32 = 1;  // column splits of the FP64 / FP32 matrix-vector products
     float *d_t32 = nullptr;    // FP32 work vector for the triangular solves
@@ -317,6 +321,29 @@ __device__ __forceinline__ void dd_fma(double a, double b, double &hi, double &l
     dd_two_sum(hi, p, s, se);
     hi = s;
     lo = __dadd_rn(lo, __dadd_rn(se, pe));
+}
+
+// ---- double-float arithmetic of the preconditioner's product ----------------
+// v = hi + lo as two floats (hi = v rounded to FP32, lo = the rest rounded).
+__device__ __forceinline__ float2 df_split(double v)
+{
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(__dsub_rn(v, (double)h)));
+}
+
+// (s, c) += m (vh + vl) on the FP32 pipe: the product m vh exactly (one
+// fused multiply-add gives its rounding error), TwoSum into s, every error
+// term gathered in c; carries about 2^-46 of |m v| where plain FP32 carries
+// 2^-24.
+__device__ __forceinline__ void df_fma(float m, float2 v, float &s, float &c)
+{
+    const float p = __fmul_rn(m, v.x);
+    const float pe = __fmaf_rn(m, v.x, -p);
+    const float t = __fadd_rn(s, p);
+    const float bb = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, __fmaf_rn(m, v.y, pe)));
 }
 
 // (hi, lo) += (h2, l2)

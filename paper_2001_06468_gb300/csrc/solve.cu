@@ -220,10 +220,19 @@ __global__ void __launch_bounds__(MV_THREADS)
     if (i + 1 < n) part[blockIdx.y * n + i + 1] = s1;
 }
 
+// vf[i] = v[i] as a float pair (the input of k_gemv32_part)
+__global__ void k_split_vec(int64_t n, const double *__restrict__ v, float2 *__restrict__ vf)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) vf[i] = df_split(v[i]);
+}
+
 // Same with the FP32 explicit inverse of the Gauss-Jordan factor: four rows
-// per thread (one 16-byte load per column), FP32 products and partial sums.
+// per thread (one 16-byte load per column), the FP64 vector as float pairs
+// and double-float products and sums (df_fma), so the preconditioner is
+// applied to about 2^-46 of |M| |v|.
 __global__ void __launch_bounds__(MV_THREADS)
-    k_gemv32_part(int64_t n, const float *__restrict__ M, int64_t lda, const double *__restrict__ v,
+    k_gemv32_part(int64_t n, const float *__restrict__ M, int64_t lda, const float2 *__restrict__ vf,
                   double *__restrict__ part, int64_t cols_per_split)
 {
     const int64_t i = ((int64_t)blockIdx.x * MV_THREADS + threadIdx.x) * 4;
@@ -231,21 +240,22 @@ __global__ void __launch_bounds__(MV_THREADS)
     const int64_t j1 = min(n, j0 + cols_per_split);
     if (i >= n) return;
     float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, c3 = 0.0f;
     const float *a = M + i;
-#pragma unroll 8
+#pragma unroll 4
     for (int64_t j = j0; j < j1; ++j) {
         const float4 x = __ldg(reinterpret_cast<const float4 *>(a + j * lda));
-        const float vj = (float)__ldg(&v[j]);
-        s0 += x.x * vj;
-        s1 += x.y * vj;
-        s2 += x.z * vj;
-        s3 += x.w * vj;
+        const float2 vj = __ldg(&vf[j]);
+        df_fma(x.x, vj, s0, c0);
+        df_fma(x.y, vj, s1, c1);
+        df_fma(x.z, vj, s2, c2);
+        df_fma(x.w, vj, s3, c3);
     }
     double *p = part + blockIdx.y * n + i;
-    p[0] = s0;
-    if (i + 1 < n) p[1] = s1;
-    if (i + 2 < n) p[2] = s2;
-    if (i + 3 < n) p[3] = s3;
+    p[0] = (double)s0 + (double)c0;
+    if (i + 1 < n) p[1] = (double)s1 + (double)c1;
+    if (i + 2 < n) p[2] = (double)s2 + (double)c2;
+    if (i + 3 < n) p[3] = (double)s3 + (double)c3;
 }
 
 // The residual's product in double-double: (part, part_lo)[s*n + i] =
@@ -500,7 +510,7 @@ static cudaError_t apply_precond(Ctx &c, const double *v, double *x)
     c.tbeg(PH_TRSV);
     cudaError_t e = apply_precond_impl(c, v, x);
     c.tend(PH_TRSV);
-    c.launches += 2;
+    c.launches += c.factored_prec != NRS_FP64 ? 3 : 2;
     return e;
 }
 
@@ -512,7 +522,8 @@ static cudaError_t apply_precond_impl(Ctx &c, const double *v, double *x)
         // explicit inverse from the Gauss-Jordan factor: x = M v
         const int64_t cps = ceil_div(c.n, c.splits32);
         dim3 grid((unsigned)ceil_div(c.n, 4 * MV_THREADS), (unsigned)c.splits32);
-        k_gemv32_part<<<grid, MV_THREADS, 0, c.stream>>>(c.n, c.d_A32, c.lda, v, c.d_part, cps);
+        k_split_vec<<<(unsigned)ceil_div(c.n, 256), 256, 0, c.stream>>>(c.n, v, c.d_vf);
+        k_gemv32_part<<<grid, MV_THREADS, 0, c.stream>>>(c.n, c.d_A32, c.lda, c.d_vf, c.d_part, cps);
         k_gemv_finish<<<(unsigned)ceil_div(c.n, 256), 256, 0, c.stream>>>(c.n, c.d_part, c.splits32,
                                                                           nullptr, x);
         return cudaGetLastError();
@@ -752,6 +763,9 @@ static nrs_status finish_solve(Ctx &c, const double *b, double *x, nrs_solve_rep
 {
     const int64_t n = c.n;
     cudaError_t e = cudaSuccess;
+    c.solves += 1;
+    c.outer_total += outer;
+    c.inner_total += inner_total;
 #define CKE(call)                                                           \
     do {                                                                    \
         e = (call);                                                         \

@@ -36,7 +36,8 @@ FREE, PRESCRIBED, STATIC = 0, 1, 2
 
 EXPORTS = ["nrs_create", "nrs_destroy", "nrs_last_error", "nrs_sizes", "nrs_set_state",
            "nrs_get_state", "nrs_set_external", "nrs_kinematics", "nrs_nearest_build",
-           "nrs_assemble", "nrs_factor", "nrs_solve", "nrs_step", "nrs_sync", "nrs_set_timing",
+           "nrs_assemble", "nrs_factor", "nrs_solve", "nrs_step", "nrs_sync", "nrs_counters",
+           "nrs_set_timing",
            "nrs_get_timing", "nrs_get_trace", "nrs_rank64_update", "nrs_nearest_build_static",
            "nrs_mlp_set_params", "nrs_mlp_get_params", "nrs_mlp_config", "nrs_mlp_eval",
            "nrs_mlp_adam", "nrs_mlp_features", "nrs_mlp_start",
@@ -91,7 +92,7 @@ class SolveReport(ctypes.Structure):
 class StepReport(ctypes.Structure):
     _fields_ = [("stage", SolveReport * 2), ("ms_total", ctypes.c_double),
                 ("factorizations", ctypes.c_int32), ("start", ctypes.c_int32 * 2),
-                ("mlp_rel_err", ctypes.c_double)]
+                ("mlp_rel_err", ctypes.c_double), ("retried", ctypes.c_int32 * 2)]
 
 
 class Shapes(ctypes.Structure):
@@ -116,6 +117,7 @@ _sig = {
     "nrs_step": (ctypes.c_int, [_P, ctypes.POINTER(Shapes), ctypes.POINTER(Shapes), ctypes.c_double,
                                 _P, ctypes.POINTER(StepReport)]),
     "nrs_sync": (ctypes.c_int, [_P]),
+    "nrs_counters": (ctypes.c_int, [_P, _I64P, _I64P, _I64P, _I64P, _I64P]),
     "nrs_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
     "nrs_rank64_update": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P,
                                          ctypes.c_int32]),
@@ -319,10 +321,17 @@ class Context:
                 "status": st, "factorizations": rep.factorizations,
                 "start": [START_KINDS.get(rep.start[0], rep.start[0]),
                           START_KINDS.get(rep.start[1], rep.start[1])],
-                "mlp_rel_err": rep.mlp_rel_err}
+                "mlp_rel_err": rep.mlp_rel_err, "retried": [rep.retried[0], rep.retried[1]]}
 
     def sync(self):
         return self._check(_lib.nrs_sync(self._h))
+
+    def counters(self):
+        """{'factorizations', 'solves', 'outer', 'inner', 'retries'} since creation."""
+        v = [ctypes.c_int64() for _ in range(5)]
+        self._check(_lib.nrs_counters(self._h, *(ctypes.byref(x) for x in v)))
+        return dict(zip(("factorizations", "solves", "outer", "inner", "retries"),
+                        (x.value for x in v)))
 
     def rank64_update(self, Mt: torch.Tensor, C: torch.Tensor, Rt: torch.Tensor, prec: str = "tf32"):
         """M -= C Rt^T in place; Mt is the (n_cols, lda) storage of the

@@ -201,10 +201,13 @@ def tube_shape(t: float, ns: int, nth: int, amp: float = 0.1, rad: float = 0.04,
     L = np.sqrt(0.25 + g_s * g_s)
     m = np.stack([-g_s, 0.5 * one, zero], axis=1)
     nu = m / L[:, None]
+    # L * L * L rather than L ** 3: numpy's power may round differently on
+    # other machines, and the inputs must be the same bits everywhere
+    L3 = L * L * L
     nu_s = np.stack([-g_ss, zero, zero], axis=1) / L[:, None] \
-        - m * (g_s * g_ss / L ** 3)[:, None]
+        - m * (g_s * g_ss / L3)[:, None]
     nu_t = np.stack([-g_st, zero, zero], axis=1) / L[:, None] \
-        - m * (g_s * g_st / L ** 3)[:, None]
+        - m * (g_s * g_st / L3)[:, None]
     ez = np.stack([zero, zero, one], axis=1)
     r = rad * np.sqrt(1.0 - S * S)
     r_s = -rad * S / np.sqrt(1.0 - S * S)

@@ -1,6 +1,8 @@
 """Write the oracle's solutions of the first explicit-midpoint step of the
-eight-cell channel workload (9200 force / 92000 quadrature points, n = 27648)
-to ``sperm_channel_step0.npz``, for the full-size GPU parity test.
+full-size workloads -- the eight-cell channel (9200 force / 92000 quadrature
+points, n = 27648) and the four interacting swimmers (8000 / 80000,
+n = 24024) -- to ``<workload>_step0.npz``, for the full-size GPU parity
+test.
 
 Only ``oracle/`` computes anything here; ``synth`` supplies the seeded
 inputs, whose SHA-1 is stored beside the solutions so that the test can
@@ -9,7 +11,8 @@ oracle when the digest differs).  The oracle's system (Sec. 4 steps 1-2) is
 solved by LAPACK's LU refined with a double-double residual to working
 accuracy (oracle.solve_lapack).
 
-    python tests/golden/make_fullsize_golden.py        # about two minutes on 8 cores
+    python tests/golden/make_fullsize_golden.py [sperm_channel] [swimmers4]
+                                        # about two minutes each on 8 cores
 """
 
 import hashlib
@@ -26,7 +29,6 @@ sys.path.insert(0, ROOT)
 import oracle as O  # noqa: E402
 from synth import geometry as g  # noqa: E402
 
-OUT = os.path.join(HERE, "sperm_channel_step0.npz")
 
 
 def input_digest(pr, dt):
@@ -49,14 +51,16 @@ def oracle_first_step(pr):
     return O.rk2_step(pr, Y0, 0.0, pr.dt, solver=O.solve_lapack, return_stages=True)
 
 
-def main():
-    pr = g.sperm_channel_config()
-    t0 = time.time()
-    Yn, st = oracle_first_step(pr)
-    np.savez(OUT, digest=np.array(input_digest(pr, pr.dt)), sol1=st["sol1"], sol2=st["sol2"],
-             x0=Yn["x0"], B=Yn["B"], n=np.array(pr.n))
-    print(f"wrote {OUT} (n = {pr.n}) in {time.time() - t0:.0f} s")
+def main(names):
+    for name in names:
+        pr = g.workload(name)
+        out = os.path.join(HERE, f"{name}_step0.npz")
+        t0 = time.time()
+        Yn, st = oracle_first_step(pr)
+        np.savez(out, digest=np.array(input_digest(pr, pr.dt)), sol1=st["sol1"],
+                 sol2=st["sol2"], x0=Yn["x0"], B=Yn["B"], n=np.array(pr.n))
+        print(f"wrote {out} (n = {pr.n}) in {time.time() - t0:.0f} s")
 
 
 if __name__ == "__main__":
-    main()
+    main(sys.argv[1:] or ["sperm_channel", "swimmers4"])

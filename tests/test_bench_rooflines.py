@@ -19,9 +19,9 @@ PHASES = ("kinematics", "nearest", "segments", "assemble", "border", "convert", 
           "lu_update", "trsv", "gemv", "krylov", "update", "lu_diag", "assemble32")
 PEAKS = {"hbm_gbs": 6688.0, "bf16_tflops": 1963.0, "bf16_tflops_sustained": 1700.0,
          "sm_max_mhz": 2070.0}
-PROBLEM = types.SimpleNamespace(n=2406, pairs=800 * 8000)
-CLOCKS = {"sm_mhz": 2070.0}
-SOLVE = {"outer_mean": 3.0, "inner_mean": 3.85}
+N_SYS, PAIRS = 27648, 9200 * 92000
+SM_MHZ = 2070.0
+SOLVE = {"outer_mean": 3.5, "inner_mean": 20.0}
 
 
 def _phases(**ms_spans):
@@ -40,32 +40,40 @@ def _check(rec):
     assert rec["frac"] == pytest.approx(rec["achieved"] / rec["peak"])
 
 
-def test_separate_kernel_schedule():
-    ms, spans = _phases(lu_diag=(0.9, 38), lu_update=(0.65, 38), lu_panel=(0.5, 76),
-                        assemble=(0.47, 1), krylov=(0.3, 1))
-    recs = bench._rooflines(ms, spans, PROBLEM, PEAKS, "measured", CLOCKS, SOLVE)
-    assert {"lu_diag", "lu_update", "assemble", "solve"} <= set(recs)
+def test_records_of_every_kernel_family():
+    nblk = -(-N_SYS // 64)
+    ms, spans = _phases(lu_diag=(15.0, nblk), lu_update=(660.0, nblk), lu_panel=(28.0, 2 * nblk),
+                        assemble=(220.0, 2), assemble32=(2.2, 1), krylov=(180.0, 2))
+    recs = bench.rooflines(ms, spans, N_SYS, PAIRS, PEAKS, "measured", SM_MHZ, SOLVE)
+    assert {"lu_diag", "lu_update", "assemble", "assemble32", "krylov"} <= set(recs)
     for r in recs.values():
         _check(r)
-    # per launch: 0.9 ms / 38 diagonal inverses; the first of a factorisation is the
-    # inverse alone (2 * 64^3 flops), the other 37 add the lookahead and staged-tile
-    # products (8 * 64^3 flops)
-    w = (2 * 64 ** 3 + 37 * 8 * 64 ** 3) / 38
+    # per launch: the first diagonal inverse of a factorisation is the inverse
+    # alone (2 * 64^3 flops), the others add the lookahead and staged-tile
+    # products (8 * 64^3 flops); the peak is the whole GPU's FP32 rate
+    w = (2 * 64 ** 3 + (nblk - 1) * 8 * 64 ** 3) / nblk
     assert recs["lu_diag"]["work_per_launch"] == pytest.approx(w)
-    assert recs["lu_diag"]["achieved"] == pytest.approx(w / (0.9e-3 / 38) / 1e12)
+    assert recs["lu_diag"]["achieved"] == pytest.approx(w / (15e-3 / nblk) / 1e12)
+    assert recs["lu_diag"]["peak"] == pytest.approx(152 * 128 * 2 * SM_MHZ * 1e6 / 1e12)
+    # the update: 8 n^2 bytes per launch against the measured HBM copy rate
+    assert recs["lu_update"]["work_per_launch"] == pytest.approx(8.0 * N_SYS ** 2)
+    assert recs["lu_update"]["peak"] == PEAKS["hbm_gbs"]
+    # FP64 assembly: 40 operations per pair against 2 FP64 lanes per SM per clock
+    a = recs["assemble"]
+    assert a["work_per_launch"] == pytest.approx(40.0 * PAIRS)
+    assert a["peak"] == pytest.approx(625.0)
+    assert a["pairs_per_s"] == pytest.approx(PAIRS / 0.110)
+    # FP32 copy: pairs against the pair peak 152 x 128 x clock / 20
+    assert recs["assemble32"]["peak"] == pytest.approx(152 * 128 * SM_MHZ * 1e6 / 20)
+    # solve: (outer + inner) FP64 and (outer + inner + 1) FP32 matrix passes
+    k = recs["krylov"]
+    assert k["work_per_launch"] == pytest.approx(8.0 * N_SYS ** 2 * 23.5 + 4.0 * N_SYS ** 2 * 24.5)
 
 
-def test_fused_schedule():
-    ms, spans = _phases(lu_update=(1.05, 1), assemble=(0.47, 1), krylov=(0.3, 1))
-    recs = bench._rooflines(ms, spans, PROBLEM, PEAKS, "measured", CLOCKS, SOLVE)
-    assert "lu_diag" not in recs
-    rec = recs["lu_update"]
-    _check(rec)
-    assert rec["kernel"].startswith("k_gj_fused")
-    nblk = -(-PROBLEM.n // 64)
-    assert rec["blocks"] == nblk
-    assert rec["us_per_block"] == pytest.approx(1.05e3 / nblk)
-    assert rec["work_per_launch"] == pytest.approx(8.0 * PROBLEM.n ** 2 * nblk)
+def test_records_are_skipped_for_phases_that_did_not_run():
+    ms, spans = _phases(assemble=(80.0, 1), krylov=(100.0, 1))
+    recs = bench.rooflines(ms, spans, N_SYS, PAIRS, PEAKS, "measured", SM_MHZ, SOLVE)
+    assert set(recs) == {"assemble", "krylov"}
 
 
 def test_traffic_record_follows_its_source(tmp_path, monkeypatch):

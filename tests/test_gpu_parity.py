@@ -300,9 +300,20 @@ def test_bad_arguments_are_rejected(N):
     with pytest.raises(N.NrsError):
         N.Context([0, 0], [0, 4], [N.FREE], eps=0.1)  # quadrature points without force points
     pr = PROBLEMS["swimmer_small"]()
+    with pytest.raises(N.NrsError) as ei:
+        N.Context.from_problem(pr, factor_prec="bf16")  # no BF16 factorisation is built
+    assert ei.value.status == N.NRS_EINVAL
     ctx = N.Context.from_problem(pr)
     with pytest.raises(N.NrsError) as ei:
         ctx.factor("fp32")  # nothing assembled yet
+    assert ei.value.status == N.NRS_EINVAL
+    sh = g.pack_shapes(pr, 0.0)
+    xi, Xiw, xidot = N.shapes_to_device(sh)
+    x, Xw, b = ctx.kinematics(xi, Xiw, xidot)
+    ctx.nearest_build(xi, Xiw)
+    ctx.assemble(x, Xw, want_matrix=False)
+    with pytest.raises(N.NrsError) as ei:
+        ctx.factor("bf16")
     assert ei.value.status == N.NRS_EINVAL
 
 
