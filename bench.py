@@ -195,6 +195,8 @@ NCU_TRAFFIC = {
     "k_tc_gj_update": {"bytes": 150743296 + 77540181, "n": 6006,
                        "file": "paper_2001_06468_gb300/csrc/tc_gemm.cu", "sha1": "e38e9748bdee",
                        "scale": "n^2 (captured at n = 6006, matrix larger than L2)"},
+    "k_tc_gj2_update": {"bytes": None, "file": "paper_2001_06468_gb300/csrc/gj2.cu",
+                        "sha1": "", "scale": None},
     "k_gj_diag": {"bytes": 136832, "file": "paper_2001_06468_gb300/csrc/gj.cu",
                   "sha1": "d098875a34c5",
                   "scale": "none (the 64 x 64 block, the previous D^{-1} and two 64 x 64 tiles)"},
@@ -247,7 +249,35 @@ def rooflines(ph_ms, ph_spans, n, pairs, peaks, peak_src, sm_mhz, solve_stats):
         return ph_ms[ph] / 1e3 / max(ph_spans[ph], 1)
 
     recs = {}
-    if ph_spans.get("lu_update"):
+    two_level = (ph_spans.get("lu_update") and not ph_spans.get("lu_diag")
+                 and ph_spans.get("lu_panel") == ph_spans.get("lu_update"))
+    if two_level:
+        # k_tc_gj2_update: one rank-256 product per 256-column block
+        t = per_launch("lu_update")
+        b = 8.0 * n * n
+        fl = 3 * 2.0 * n * n * 256
+        recs["lu_update"] = {
+            "kernel": "k_tc_gj2_update (persistent tcgen05 split-TF32 rank-256 update of the "
+                      "FP32 inverse, two-level Gauss-Jordan)",
+            "bound": "tensor", "achieved": fl / t / 1e12, "peak": P["tf32_tflops"],
+            "unit": "TFLOP/s", "frac": fl / t / 1e12 / P["tf32_tflops"],
+            "peak_source": peak_src + " BF16 sustained x nominal TF32/BF16 (1.1/2.25)",
+            "work_per_launch": fl, "work_unit": "tensor flops (3 split-TF32 passes x 2 n^2 256)",
+            "useful_tflops": fl / 3 / t / 1e12,
+            "hbm_gbs": b / t / 1e9, "hbm_frac": b / t / 1e9 / P["hbm_gbs"],
+            "us_per_launch": t * 1e6, "launches": ph_spans["lu_update"],
+            "traffic": _traffic("k_tc_gj2_update", n)}
+        t = per_launch("lu_panel")
+        recs["lu_panel"] = {
+            "kernel": "column-panel elimination (4 x k_gj_diag, k_gj2_rpanel, k_gj2_panel_update) "
+                      "and k_gj2_prep",
+            "bound": "alu", "achieved": 2.0 * n * 256 * 256 / t / 1e12, "peak": P["fp32_tflops"],
+            "unit": "TFLOP/s", "frac": 2.0 * n * 256 * 256 / t / 1e12 / P["fp32_tflops"],
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x sampled clock",
+            "latency_bound": "4 dependent 64-column steps of 3 launches each per block",
+            "work_per_launch": 2.0 * n * 256 * 256, "us_per_launch": t * 1e6,
+            "launches": ph_spans["lu_panel"], "traffic": None}
+    elif ph_spans.get("lu_update"):
         t = per_launch("lu_update")
         b = 8.0 * n * n
         fl = 3 * 2.0 * n * n * 64
@@ -786,7 +816,7 @@ def profile_solve(args):
     torch.cuda.set_device(0)
     pr = PROFILE_WORKLOADS[args.workload]()
     sh = g.pack_shapes(pr, 0.25)
-    ctx = nrs.Context.from_problem(pr, factor_prec=args.prec)
+    ctx = nrs.Context.from_problem(pr, factor_prec=args.prec, factor_schedule=args.factor_schedule)
     Y = g.initial_state(pr)
     ctx.set_state(Y["x0"], Y["B"])
     xi, Xiw, xidot = nrs.shapes_to_device(sh)
@@ -913,8 +943,8 @@ def run_nrs(args):
         return
     recs = H["recs"]
     share = H["phase_share"]
-    fam = {"lu_update": "lu_update", "lu_diag": "lu_diag", "assemble": "assemble",
-           "assemble32": "assemble32", "krylov": "krylov"}
+    fam = {"lu_update": "lu_update", "lu_diag": "lu_diag", "lu_panel": "lu_panel",
+           "assemble": "assemble", "assemble32": "assemble32", "krylov": "krylov"}
     top = max((k for k in recs if k in fam), key=lambda k: share.get(fam[k], 0.0))
     roof = dict(recs[top], share_of_step=share.get(fam[top], 0.0))
     plain = side.get("plain_fp64")
@@ -1037,6 +1067,9 @@ def main():
     ap.add_argument("--profile-step", action="store_true",
                     help="--warmup steps and one more of --workload, then exit (for ncu)")
     ap.add_argument("--workload", default="swimmer", choices=sorted(PROFILE_WORKLOADS))
+    ap.add_argument("--factor-schedule", default="auto",
+                    choices=["auto", "fused", "streams", "two_level"],
+                    help="factorisation schedule of --profile-solve")
     args = ap.parse_args()
     if args.profile_solve:
         profile_solve(args)

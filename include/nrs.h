@@ -120,12 +120,17 @@ typedef struct {
                               without the graph.  backward_err is reported as computed in the
                               graph. */
     int32_t factor_schedule; /* FP32/TF32 factorisation (Gauss-Jordan explicit inverse):
-                              0 = separate kernels on three streams (the chain of diagonal
-                              inverses on one of them); 1 = with TF32 on a device with tensor
-                              memory, the whole inversion as ONE cooperative launch taking
-                              every SM (the chain of diagonal inverses on one CTA, the updates
-                              on the others, hand-offs by counters in global memory), else as
-                              0.  Both give the same result bit for bit. */
+                              0 = automatic: as 3 with TF32 from n = 8192 on, else as 2;
+                              1 = with TF32 on a device with tensor memory, the whole
+                              inversion as ONE cooperative launch taking every SM (the chain
+                              of diagonal inverses on one CTA, the updates on the others,
+                              hand-offs by counters in global memory), else as 2; 2 = one
+                              level of 64-column blocks, separate kernels on three streams
+                              (the chain of diagonal inverses on one of them); 1 and 2 give
+                              the same result bit for bit; 3 = two levels (TF32, n >= 512):
+                              256-column blocks whose column panel is eliminated in 64-column
+                              steps, then one rank-256 tensor-core update of the rest of the
+                              matrix (a persistent tcgen05 kernel).  Other values: NRS_EINVAL. */
     int32_t residual;      /* the refinement's residual b - A x: 0 = double-double (every
                               product exact, sums carried in two doubles, rounded once at the
                               end: the residual precision u^2 of three-precision GMRES-IR,
@@ -155,8 +160,7 @@ typedef struct {
                                before that stage's updates (a held-out error);
                                -1 if the step did not train                     */
     int32_t retried[2];     /* 1 if the stage's refinement did not converge and the stage
-                               was factored again (the other FP32 input, or a fresh factor
-                               in place of a reused one) and solved again       */
+                               was factored again (see nrs_step) and solved again */
 } nrs_step_report;
 
 /* Body-frame inputs of one stage (device memory):
@@ -258,9 +262,10 @@ nrs_status nrs_solve(nrs_ctx *ctx, const double *b, double *x, int32_t nrhs, con
  * re-orthonormalised by modified Gram-Schmidt after each stage.  The state
  * stays on the device.  sol (device [2*n] or NULL) receives both stages'
  * solutions.  report (host or NULL) synchronises.  With an FP32/TF32 factor,
- * a stage whose refinement does not converge is factored again once -- from
- * the other FP32 input (factor_input), or fresh where the factor was reused --
- * and solved again (report->retried); NRS_ENOCONV if that fails too. */
+ * a stage whose refinement does not converge is factored again once -- by the
+ * one-level elimination where the factor was the two-level one, else from the
+ * other FP32 input (factor_input), or fresh where the factor was reused -- and
+ * solved again (report->retried); NRS_ENOCONV if that fails too. */
 nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *s_half, double dt,
                     double *sol, nrs_step_report *report);
 

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnrs.so")
-SOURCES = ["geometry.cu", "assemble.cu", "lu.cu", "gj.cu", "solve.cu", "tc_gemm.cu", "api.cu",
+SOURCES = ["geometry.cu", "assemble.cu", "lu.cu", "gj.cu", "gj2.cu", "solve.cu", "tc_gemm.cu", "api.cu",
            "static_nn.cu", "mlp.cu",
            "gmres_persistent.cu", "batch.cu"]
 HEADERS = ["nrs_internal.cuh", "tc_prims.cuh"]

@@ -42,6 +42,9 @@ cudaError_t dalloc(T **p, size_t count)
 nrs_status alloc_all(Ctx *c)
 {
     const int64_t N = c->N, Q = c->Q, n = c->n, lda = c->lda, m = c->max_inner;
+    // workspaces of the two-level factorisation where it may run
+    const bool gj2 = c->factor_prec == NRS_TF32 && n >= 512 &&
+                     (c->gj_schedule == 3 || (c->gj_schedule == 0 && n >= nrs::GJ2_MIN_N));
     const int nb = c->nbodies;
     struct {
         void **p;
@@ -91,6 +94,8 @@ nrs_status alloc_all(Ctx *c)
         {(void **)&c->d_part32, sizeof(double) * 64 * lda},
         {(void **)&c->d_part_lo, sizeof(double) * 64 * lda},
         {(void **)&c->d_vf, sizeof(float2) * lda},
+        {(void **)&c->d_gj2, gj2 ? sizeof(float) * 4 * nrs::gj2_panel_floats(n) : 0},
+        {(void **)&c->d_gj2_r, gj2 ? sizeof(float) * 64 * 256 : 0},
         {(void **)&c->d_t32, sizeof(float) * 2 * lda},
         {(void **)&c->d_t64, sizeof(double) * 2 * lda},
         {(void **)&c->d_flags, sizeof(int32_t) * nrs::ceil_div(n, 64)},
@@ -129,7 +134,7 @@ void free_all(Ctx *c)
                     c->d_t32,    c->d_t64,    c->d_flags,  c->d_status,     c->d_gj_dinv,
                     c->d_gj_rt,  c->d_gj_cb,  c->d_dpart,  c->d_bar,        c->d_pg_stats,
                     c->d_step_stats, c->d_Xsh, c->d_Xsl, c->d_xh, c->d_xl, c->d_gj_stage, c->d_gj_sync, c->d_part32,
-                    c->d_part_lo, c->d_vf};
+                    c->d_part_lo, c->d_vf, c->d_gj2, c->d_gj2_r};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *mlp[] = {c->d_mlp_params, c->d_mlp_m,  c->d_mlp_v,     c->d_mlp_g,    c->d_mlp_x,
@@ -502,6 +507,11 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
     c->tol_in = d->inner_tol > 0.0 ? d->inner_tol : 1e-4;
     c->lo_eval = d->factor_input ? 1 : 0;
     c->residual_dd = d->residual == 0 ? 1 : 0;
+    if (d->factor_schedule < 0 || d->factor_schedule > 3) {
+        delete c;
+        return NRS_EINVAL;
+    }
+    c->gj_schedule = d->factor_schedule;
     c->gj_fused = d->factor_schedule == 1;
     c->graph_mode = d->graph ? 1 : 0;
     if (c->graph_mode && (d->factor_prec == NRS_FP64 || c->solve_mode != 0 || d->reuse_factor ||
@@ -833,11 +843,15 @@ nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *sh, do
         if (st == NRS_ENOCONV && c->factor_prec != NRS_FP64) {
             // The refinement did not converge with this factor.  An FP32 inverse
             // of a system with kappa(A) u_fp32 >> 1 is sometimes a poor
-            // preconditioner; one of the other FP32 input (the rounded FP64
-            // entries instead of the FP32 evaluation, or the reverse) usually is
-            // not.  A reused factor is replaced by a fresh one of the configured
-            // input.  One retry, from the same start.
-            const bool other = need_factor ? c->lo_eval == 1 : c->lo_eval == 0;
+            // preconditioner; another one usually is not: a two-level factor
+            // is replaced by the one-level elimination of the same input (the
+            // more robust of the two on such systems), a one-level one by that
+            // of the other FP32 input (the rounded FP64 entries instead of the
+            // FP32 evaluation, or the reverse), a reused factor by a fresh one
+            // of the configured input.  One retry, from the same start.
+            const bool was_two = need_factor && c->last_factor_two_level;
+            const bool other = need_factor && !was_two ? c->lo_eval == 1 : c->lo_eval == 0;
+            if (was_two) c->gj_force_one_level = true;
             nrs::join_assembly(*c);
             if (other) {
                 nrs::launch_assemble32(*c, c->d_x, c->d_A32, c->lda);
@@ -847,6 +861,7 @@ nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *sh, do
             }
             c->factored_prec = -1;
             st = do_factor(c, c->factor_prec);
+            c->gj_force_one_level = false;
             if (st != NRS_OK) return st;
             c->stages_since_factor = 0;
             c->retries += 1;

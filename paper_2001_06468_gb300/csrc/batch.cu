@@ -271,13 +271,13 @@ nrs_status nrs_batch_create(nrs_batch **out, const nrs_problem_desc *descs, int3
         b->ev.push_back(ev);
         nrs_problem_desc d = descs[i];
         d.graph = 0;
+        // the problems of a batch run side by side: the fused and the two-level
+        // factorisations (which take every SM) would serialise them
+        d.factor_schedule = 2;
         nrs_ctx *h = nullptr;
         st = nrs_create(&h, &d, s);
         if (st == NRS_OK) {
             b->ctx.push_back(reinterpret_cast<Ctx *>(h));
-            // the problems of a batch run side by side: the fused factorisation
-            // (which takes every SM) would serialise them
-            b->ctx.back()->gj_fused = false;
         }
     }
     if (e != cudaSuccess && st == NRS_OK) st = NRS_ECUDA;

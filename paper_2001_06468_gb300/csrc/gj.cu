@@ -1319,9 +1319,36 @@ bool run_gj_fused(Ctx &c, float *M, int64_t lda)
 constexpr int GJ_DIAG_EXCL_SMEM = 164 * 1024;
 static_assert(sizeof(GjElimSmem) <= GJ_DIAG_EXCL_SMEM, "the elimination's slots fit");
 
+size_t gj_diag_smem() { return (sizeof(GjElimSmem) + 1023) / 1024 * 1024; }
+
+void gj_diag_prepare()
+{
+    static bool done = false;
+    if (!done) {
+        cudaFuncSetAttribute(k_gj_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             GJ_DIAG_EXCL_SMEM);
+        done = true;
+    }
+}
+
+// D^{-1} of the diagonal block at (k0, k0) alone (no lookahead), for the
+// panel elimination of gj2.cu.
+void k_gj_diag_launch(Ctx &c, int64_t n, const float *M, int64_t lda, int64_t k0, float *Dinv,
+                      size_t smem)
+{
+    k_gj_diag<<<1, 256, smem, c.stream>>>(n, M, lda, k0, Dinv, c.d_info, nullptr, nullptr,
+                                          c.d_status);
+}
+
 int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
 {
+    c.last_factor_two_level = false;
     if (prec == NRS_TF32 && run_gj_fused(c, M, lda)) return 0;
+    // large systems: the two-level elimination whose updates are rank-256 products
+    const bool two = !c.gj_force_one_level &&
+                     (c.gj_schedule == 3 || (c.gj_schedule == 0 && c.n >= GJ2_MIN_N));
+    c.last_factor_two_level = prec == NRS_TF32 && two && gj2_supported(c) && c.d_gj2;
+    if (c.last_factor_two_level) return run_gj2_fp32(c, M, lda);
     static bool diag_attr = false;
     if (!diag_attr) {
         cudaFuncSetAttribute(k_gj_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -1,0 +1,526 @@
+// gj2.cu -- the explicit FP32 inverse of gj.cu for large systems, by
+// Gauss-Jordan elimination blocked on two levels, so that the updates of the
+// whole matrix are rank-256 products on the tensor cores rather than rank-64
+// ones (which move 8 n^2 bytes of M for only 2 n^2 64 flops: HBM-bound).
+//
+// Outer step b (block K = [k0, k0 + W), W <= 256 columns):
+//   1. the column panel P = M[:, K] is eliminated by four inner Gauss-Jordan
+//      steps of 64 columns that touch only P (each: the 64 x 64 diagonal
+//      block's inverse with partial pivoting inside the block, k_gj_diag; the
+//      scaled block row R = D^{-1} P[Kk, :]; P -= C R, P[Kk, :] = R,
+//      P[:, Kk] = -C D^{-1}, P[Kk, Kk] = D^{-1}).  A Gauss-Jordan step acts on
+//      a column only through that column's own entries, so these are exactly
+//      the inner steps' action on the panel, and P ends as the block column
+//      G = E[:, K] of their product E.
+//   2. every other column j takes the same four steps at once:
+//      M[:, j] <- E M[:, j] = M[:, j] + (G - I_K) M[K, j]
+//      (rows K included: they become D_K^{-1} M[K, j]), a rank-W product of
+//      the panel G' = G - I_K (n x W) with the old block row T = M[K, :]
+//      (W x n), both stored K-major and split into TF32 hi + lo for the
+//      split-precision tensor-core product (hi hi + hi lo + lo hi).
+// After the last outer step M holds A^{-1}.  Pivoting stays inside 64 x 64
+// diagonal blocks, as in gj.cu and lu.cu.
+//
+// The update (k_tc_gj2_update) is a persistent kernel, one CTA per SM, warp
+// specialised: warp 0 loads the operand tiles with TMA (128-byte swizzle)
+// into two shared-memory stages, warp 1 issues tcgen05.mma kind::tf32 into
+// one of two 128 x 256 FP32 accumulators in tensor memory, warps 2-9 add the
+// finished accumulator to M (tcgen05.ld, coalesced column-major
+// read-modify-write, two warps per 32 rows) while the next tile's products run.  Every wait is
+// bounded: one that runs out sets ST_TIMEOUT, the roles stop, and the CTA
+// waits (bounded) for its own copies and products before freeing tensor memory.
+#include <cuda.h>
+
+#include "tc_prims.cuh"
+
+namespace nrs {
+
+using namespace tcp;
+
+namespace {
+
+constexpr int G2_W = 256;                  // outer block (columns of the panel, K of the product)
+constexpr int G2_BM = 128, G2_BN = 256;    // output tile of the update
+constexpr int G2_KC = 32;                  // K per pipeline stage (128 bytes of FP32)
+constexpr int G2_NCH = G2_W / G2_KC;       // stages per tile
+constexpr uint32_t G2_A_BYTES = G2_BM * G2_KC * 4;                       // 16 KB
+constexpr uint32_t G2_B_BYTES = G2_BN * G2_KC * 4;                       // 32 KB
+constexpr uint32_t G2_STAGE_BYTES = 2 * G2_A_BYTES + 2 * G2_B_BYTES;     // 96 KB
+constexpr int G2_STAGES = 2;
+constexpr int G2_SMEM = G2_STAGES * G2_STAGE_BYTES + 1024;
+constexpr int G2_EPI_WARPS = 8;          // two per accumulator lane quarter, half the columns each
+constexpr int G2_THREADS = 64 + 32 * G2_EPI_WARPS;
+constexpr int G2_TMEM_COLS = 2 * G2_BN;    // two accumulators
+
+__device__ __forceinline__ void g2_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Output tile t of the update: row tile t % nrt, column tile t / nrt
+// counted over the column tiles other than `skip`.
+__device__ __forceinline__ void g2_tile(int64_t t, int nrt, int skip, int &rt, int &ct)
+{
+    rt = (int)(t % nrt);
+    const int c = (int)(t / nrt);
+    ct = c < skip ? c : c + 1;
+}
+
+// M[i, j] += sum_{c < 256} A[i][c] B[j][c] for all rows i < n and the columns
+// j of every 256-wide column tile but `skip`, A = Ah + Al and B = Bh + Bl the
+// split panels (row-major, 256 floats a row), products hi hi + hi lo + lo hi.
+__global__ void __launch_bounds__(G2_THREADS, 1)
+    k_tc_gj2_update(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                    const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                    int64_t n, float *__restrict__ M, int64_t lda, int nrt, int nct, int skip,
+                    int32_t *status)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t full[G2_STAGES], empty[G2_STAGES], tfull[2], tempty[2], drain;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int s_abort;
+    uint8_t *base = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ntiles = (int64_t)nrt * (skip >= 0 && skip < nct ? nct - 1 : nct);
+    const int skip_eff = (skip >= 0 && skip < nct) ? skip : nct;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < G2_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], G2_EPI_WARPS);
+        }
+        mbar_init(&drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_slot)),
+                     "r"(G2_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        // ---- producer: TMA loads of the four operand tiles of every stage
+        if (lane == 0) {
+            int64_t it = 0;
+            int last_k[G2_STAGES] = {-1, -1};
+            for (int64_t t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x) {
+                int rt, ct;
+                g2_tile(t, nrt, skip_eff, rt, ct);
+                for (int ch = 0; ch < G2_NCH; ++ch, ++it) {
+                    const int s = (int)(it & 1), k = (int)(it >> 1);
+                    if (!mbar_wait(&empty[s], (uint32_t)((k & 1) ^ 1))) {
+                        atomicOr(status, ST_TIMEOUT);
+                        s_abort = 1;
+                        break;
+                    }
+                    uint8_t *st = base + (size_t)s * G2_STAGE_BYTES;
+                    mbar_expect_tx(&full[s], G2_STAGE_BYTES);
+                    tma_load_2d(st, &tmAh, ch * G2_KC, rt * G2_BM, &full[s]);
+                    tma_load_2d(st + G2_A_BYTES, &tmAl, ch * G2_KC, rt * G2_BM, &full[s]);
+                    tma_load_2d(st + 2 * G2_A_BYTES, &tmBh, ch * G2_KC, ct * G2_BN, &full[s]);
+                    tma_load_2d(st + 2 * G2_A_BYTES + G2_B_BYTES, &tmBl, ch * G2_KC, ct * G2_BN,
+                                &full[s]);
+                    last_k[s] = k;
+                }
+                if (s_abort) break;
+            }
+            if (s_abort) {
+                // the copies already issued land by themselves: wait for them
+                for (int s = 0; s < G2_STAGES; ++s)
+                    if (last_k[s] >= 0) mbar_wait(&full[s], (uint32_t)(last_k[s] & 1));
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer: 4 K-steps of 8 x 3 products per stage
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_tf32(G2_BM, G2_BN);
+            int64_t it = 0;
+            int lt = 0;
+            for (int64_t t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x, ++lt) {
+                const int a = lt & 1, u = lt >> 1;
+                if (!mbar_wait(&tempty[a], (uint32_t)((u & 1) ^ 1))) {
+                    atomicOr(status, ST_TIMEOUT);
+                    s_abort = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(a * G2_BN);
+                bool ok = true;
+                for (int ch = 0; ch < G2_NCH; ++ch, ++it) {
+                    const int s = (int)(it & 1), k = (int)(it >> 1);
+                    if (!mbar_wait(&full[s], (uint32_t)(k & 1))) {
+                        atomicOr(status, ST_TIMEOUT);
+                        s_abort = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = smem_u32(base + (size_t)s * G2_STAGE_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < G2_KC / 8; ++kk) {
+                        const uint32_t kofs = (uint32_t)kk * 32u;
+                        const uint64_t ah = desc_sw128_kmajor(st + kofs);
+                        const uint64_t al = desc_sw128_kmajor(st + G2_A_BYTES + kofs);
+                        const uint64_t bh = desc_sw128_kmajor(st + 2 * G2_A_BYTES + kofs);
+                        const uint64_t bl = desc_sw128_kmajor(st + 2 * G2_A_BYTES + G2_B_BYTES + kofs);
+                        mma_tf32(d, al, bh, idesc, (ch > 0 || kk > 0) ? 1u : 0u);
+                        mma_tf32(d, ah, bl, idesc, 1u);
+                        mma_tf32(d, ah, bh, idesc, 1u);
+                    }
+                    mma_commit(&empty[s]);  // the stage is free once these have read it
+                }
+                if (!ok) break;
+                mma_commit(&tfull[a]);
+            }
+            // every product issued by this thread is complete before teardown
+            mma_commit(&drain);
+            mbar_wait(&drain, 0);
+        }
+    } else {
+        // ---- epilogue: warp w reads accumulator lanes 32 (w % 4) .. + 31 and
+        // half of the 256 columns; the next 16 columns of M are loaded while
+        // the current ones are added and stored
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        int lt = 0;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+            const int a = lt & 1, u = lt >> 1;
+            const bool got = mbar_wait(&tfull[a], (uint32_t)(u & 1));
+            if (!__all_sync(0xffffffffu, got) || s_abort) {
+                if (lane == 0) {
+                    atomicOr(status, ST_TIMEOUT);
+                    s_abort = 1;
+                }
+                break;
+            }
+            tc_fence_after();
+            int rt, ct;
+            g2_tile(t, nrt, skip_eff, rt, ct);
+            const int64_t row = (int64_t)rt * G2_BM + q * 32 + lane;
+            const int cbeg = half * (G2_BN / 2);
+            const int64_t col0 = (int64_t)ct * G2_BN + cbeg;
+            const uint32_t tb = tmem + (uint32_t)(a * G2_BN + cbeg) + ((uint32_t)(q * 32) << 16);
+            float *p = M + row + col0 * lda;
+            const int64_t ncol = n - col0;
+            const bool live = row < n;
+            float cur[16], nxt[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) cur[j] = (live && j < ncol) ? __ldcs(p + j * lda) : 0.0f;
+#pragma unroll 1
+            for (int chunk = 0; chunk < G2_BN / 32; ++chunk) {
+                uint32_t v[16];
+                tmem_ld_16cols_async(tb + (uint32_t)(chunk * 16), v);
+                if (chunk + 1 < G2_BN / 32) {
+                    const float *pn = p + (int64_t)(chunk + 1) * 16 * lda;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        nxt[j] = (live && (chunk + 1) * 16 + j < ncol) ? __ldcs(pn + j * lda) : 0.0f;
+                }
+                tmem_wait_ld();
+                if (live) {
+                    float *pc = p + (int64_t)chunk * 16 * lda;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (chunk * 16 + j < ncol) __stcs(pc + j * lda, cur[j] + __uint_as_float(v[j]));
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) cur[j] = nxt[j];
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) g2_arrive(&tempty[a]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(G2_TMEM_COLS)
+                     : "memory");
+}
+
+// R[a][j] = sum_b Dinv[a][b] M[r0 + b, k0 + j] for the 64 columns
+// j in [64 blockIdx.x, +64) of the panel (R[:, own block] = 0), FP32, R
+// row-major 64 x 256.  Dinv: row-major 64 x 64 (k_gj_diag).
+__global__ void __launch_bounds__(256)
+    k_gj2_rpanel(int64_t n, const float *__restrict__ M, int64_t lda, int64_t k0, int W, int64_t r0,
+                 const float *__restrict__ Dinv, float *__restrict__ R)
+{
+    __shared__ float Ds[64][65], Ms[64][65];
+    const int tid = threadIdx.x;
+    const int j0 = blockIdx.x * 64;
+    const int kb = (int)min((int64_t)64, n - r0);
+    const int own = (int)(r0 - k0);
+    for (int i = tid; i < 64 * 64; i += 256) {
+        const int a = i >> 6, b = i & 63;
+        Ds[a][b] = Dinv[i];
+        // Ms[b][j] = M[r0 + b, k0 + j0 + j] (column j contiguous in b)
+        const int jj = i >> 6, bb = i & 63;
+        Ms[bb][jj] = (bb < kb && j0 + jj < W) ? __ldcg(M + (r0 + bb) + (k0 + j0 + jj) * lda) : 0.0f;
+    }
+    __syncthreads();
+    const bool own_blk = (j0 == own);
+    // thread: rows a0..a0+3, columns jj0..jj0+3
+    const int a0 = 4 * (tid >> 4), jj0 = 4 * (tid & 15);
+    float acc[4][4] = {};
+#pragma unroll 8
+    for (int b = 0; b < 64; ++b) {
+        float d[4], m[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            d[x] = Ds[a0 + x][b];
+            m[x] = Ms[b][jj0 + x];
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(d[x], m[y], acc[x][y]);
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+            R[(a0 + x) * G2_W + j0 + jj0 + y] = own_blk ? 0.0f : acc[x][y];
+}
+
+// One inner step on the panel, rows [64 blockIdx.x, +64):
+//   rows of Kk:      P[Kk, j] = R[:, j] (j outside the own block), P[Kk, Kk] = D^{-1}
+//   the other rows:  P[i, j] -= C_i R[:, j],  P[i, Kk] = -C_i D^{-1},  C_i = P[i, Kk]
+// FP32 fused multiply-adds; P = M[:, k0 .. k0 + W).
+__global__ void __launch_bounds__(256)
+    k_gj2_panel_update(int64_t n, float *__restrict__ M, int64_t lda, int64_t k0, int W, int64_t r0,
+                       const float *__restrict__ Dinv, const float *__restrict__ R)
+{
+    __shared__ float Cs[64][65];
+    __shared__ __align__(16) float Rs[64][64 + 4];
+    const int tid = threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * 64;
+    const int kb = (int)min((int64_t)64, n - r0);
+    const int own = (int)(r0 - k0);
+    const int rows = (int)min((int64_t)64, n - i0);
+    if (i0 == r0) {
+        // the diagonal block's rows: R outside the own block, D^{-1} inside
+        for (int idx = tid; idx < 64 * W; idx += 256) {
+            const int a = idx & 63, j = idx >> 6;
+            if (a >= kb) continue;
+            const bool in_own = j >= own && j < own + 64;
+            const float v = in_own ? (j - own < kb ? Dinv[a * 64 + (j - own)] : 0.0f) : R[a * G2_W + j];
+            if (!in_own || j - own < kb) M[(r0 + a) + (k0 + j) * lda] = v;
+        }
+        return;
+    }
+    // C = P[i0 .. i0 + 63, Kk]
+    for (int idx = tid; idx < 64 * 64; idx += 256) {
+        const int r = idx & 63, c = idx >> 6;
+        Cs[r][c] = (r < rows && c < kb) ? M[(i0 + r) + (r0 + c) * lda] : 0.0f;
+    }
+    // thread: rows rr0..rr0+3 (of 64), columns of a 64-wide slice jj0..jj0+3
+    const int rr0 = 4 * (tid & 15), jj0 = 4 * (tid >> 4);
+    for (int js = 0; js < W; js += 64) {
+        __syncthreads();
+        // the slice's R (or D^{-1} for the own block), 64 x 64
+        const bool in_own = (js == own);
+        for (int idx = tid; idx < 64 * 64; idx += 256) {
+            const int c = idx >> 6, j = idx & 63;
+            float v = 0.0f;
+            if (c < kb) {
+                if (in_own) v = (j < kb) ? Dinv[c * 64 + j] : 0.0f;
+                else if (js + j < W) v = R[c * G2_W + js + j];
+            }
+            Rs[c][j] = v;
+        }
+        __syncthreads();
+        float acc[4][4] = {};
+#pragma unroll 8
+        for (int c = 0; c < 64; ++c) {
+            float cv[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) cv[x] = Cs[rr0 + x][c];
+            const float4 rv = *reinterpret_cast<const float4 *>(&Rs[c][jj0]);
+            const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(cv[x], rr[y], acc[x][y]);
+        }
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            const int j = js + jj0 + y;
+            if (j >= W) continue;
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                const int r = rr0 + x;
+                if (r >= rows) continue;
+                float *p = M + (i0 + r) + (k0 + j) * lda;
+                if (in_own) {
+                    if (jj0 + y < kb) *p = -acc[x][y];
+                } else {
+                    *p = *p - acc[x][y];
+                }
+            }
+        }
+    }
+}
+
+// The product's operands, split into TF32 hi (cvt.rna) and lo = x - hi:
+//   blockIdx.y <  4: A[i][c] = M[i, k0 + c] - (i == k0 + c) for c < W (0 for c >= W
+//                    and rows >= n), 64 rows x 64 columns a CTA through shared memory;
+//   blockIdx.y == 4: B[j][c] = M[k0 + c, j] for c < W, j outside [k0, k0 + W)
+//                    (0 otherwise), 64 columns j a CTA: one contiguous run of M each.
+// Both row-major with 256 floats a row, rows up to `rows_pad`.
+__global__ void __launch_bounds__(256)
+    k_gj2_prep(int64_t n, const float *__restrict__ M, int64_t lda, int64_t k0, int W,
+               int64_t rows_pad, float *__restrict__ Ah, float *__restrict__ Al,
+               float *__restrict__ Bh, float *__restrict__ Bl)
+{
+    __shared__ float T[64][65];
+    const int tid = threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * 64;
+    if (i0 >= rows_pad) return;
+    if (blockIdx.y < 4) {
+        const int c0 = blockIdx.y * 64;
+        for (int idx = tid; idx < 64 * 64; idx += 256) {
+            const int r = idx & 63, c = idx >> 6;
+            const int64_t i = i0 + r;
+            float v = 0.0f;
+            if (i < n && c0 + c < W) {
+                v = M[i + (k0 + c0 + c) * lda];
+                if (i == k0 + c0 + c) v -= 1.0f;
+            }
+            T[r][c] = v;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < 64 * 64; idx += 256) {
+            const int c = idx & 63, r = idx >> 6;
+            float h, l;
+            split_tf32(T[r][c], h, l);
+            Ah[(i0 + r) * G2_W + c0 + c] = h;
+            Al[(i0 + r) * G2_W + c0 + c] = l;
+        }
+    } else {
+        for (int idx = tid; idx < 64 * G2_W; idx += 256) {
+            const int c = idx & (G2_W - 1), jr = idx >> 8;
+            const int64_t j = i0 + jr;
+            float v = 0.0f;
+            if (j < n && c < W && !(j >= k0 && j < k0 + W)) v = M[(k0 + c) + j * lda];
+            float h, l;
+            split_tf32(v, h, l);
+            Bh[j * G2_W + c] = h;
+            Bl[j * G2_W + c] = l;
+        }
+    }
+}
+
+typedef CUresult (*EncodeTiledFn2)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn2 encode_fn2()
+{
+    static EncodeTiledFn2 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn2>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2-D map over a row-major [rows][256] FP32 panel, boxes of 32 x box_rows with
+// 128-byte swizzle; rows >= `rows` read as zero.
+bool make_panel256_map(CUtensorMap *tm, const float *ptr, int64_t rows, int box_rows)
+{
+    EncodeTiledFn2 enc = encode_fn2();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)G2_W, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)G2_W * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)G2_KC, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool gj2_supported(const Ctx &c)
+{
+    return tc_available() && encode_fn2() != nullptr && c.n >= 2 * G2_W;
+}
+
+size_t gj2_panel_floats(int64_t n)
+{
+    // rows of the panels padded to the update's 256-row tiles
+    return (size_t)ceil_div(n, G2_BN) * G2_BN * G2_W;
+}
+
+// The two-level factorisation of the FP32 matrix M (n x n, column-major) in
+// place; the split panels live in c.d_gj2 (4 x gj2_panel_floats(n) floats), the
+// inner scaled block row in c.d_gj2_r (64 x 256 floats).  Returns 0, or -1 if
+// the tensor maps could not be made.
+int run_gj2_fp32(Ctx &c, float *M, int64_t lda)
+{
+    const int64_t n = c.n;
+    const int64_t rows_pad = ceil_div(n, G2_BN) * G2_BN;
+    const size_t pf = gj2_panel_floats(n);
+    float *Ah = c.d_gj2, *Al = c.d_gj2 + pf, *Bh = c.d_gj2 + 2 * pf, *Bl = c.d_gj2 + 3 * pf;
+    CUtensorMap mAh, mAl, mBh, mBl;
+    if (!make_panel256_map(&mAh, Ah, rows_pad, G2_BM) || !make_panel256_map(&mAl, Al, rows_pad, G2_BM) ||
+        !make_panel256_map(&mBh, Bh, rows_pad, G2_BN) || !make_panel256_map(&mBl, Bl, rows_pad, G2_BN))
+        return -1;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_tc_gj2_update, cudaFuncAttributeMaxDynamicSharedMemorySize, G2_SMEM);
+        attr = true;
+    }
+    const size_t diag_smem = gj_diag_smem();
+    gj_diag_prepare();
+    cudaMemsetAsync(c.d_info, 0, sizeof(int32_t), c.stream);
+    const int nrt = (int)ceil_div(n, G2_BM), nct = (int)ceil_div(n, G2_BN);
+    const int64_t tiles = (int64_t)nrt * (nct - 1);
+    const int grid = (int)std::min<int64_t>(tiles, c.num_sms);
+    for (int64_t k0 = 0; k0 < n; k0 += G2_W) {
+        const int W = (int)std::min<int64_t>(G2_W, n - k0);
+        c.tbeg(PH_LU_PANEL);
+        for (int64_t r0 = k0; r0 < k0 + W; r0 += 64) {
+            k_gj_diag_launch(c, n, M, lda, r0, c.d_gj_dinv, diag_smem);
+            k_gj2_rpanel<<<(unsigned)ceil_div(W, 64), 256, 0, c.stream>>>(n, M, lda, k0, W, r0,
+                                                                         c.d_gj_dinv, c.d_gj2_r);
+            k_gj2_panel_update<<<(unsigned)ceil_div(n, 64), 256, 0, c.stream>>>(
+                n, M, lda, k0, W, r0, c.d_gj_dinv, c.d_gj2_r);
+            c.launches += 3;
+        }
+        k_gj2_prep<<<dim3((unsigned)ceil_div(rows_pad, 64), 5), 256, 0, c.stream>>>(
+            n, M, lda, k0, W, rows_pad, Ah, Al, Bh, Bl);
+        c.launches += 1;
+        c.tend(PH_LU_PANEL);
+        c.tbeg(PH_LU_UPDATE);
+        k_tc_gj2_update<<<grid, G2_THREADS, G2_SMEM, c.stream>>>(mAh, mAl, mBh, mBl, n, M, lda, nrt,
+                                                                nct, (int)(k0 / G2_W), c.d_status);
+        c.tend(PH_LU_UPDATE);
+        c.launches += 1;
+    }
+    return 0;
+}
+
+}  // namespace nrs

@@ -627,6 +627,26 @@ int pg_max_coresident(const Ctx &c)
 
 size_t pg_dpart_doubles(int max_inner) { return (size_t)3 * PG_MAXCH * (max_inner + 2); }
 
+// The number of column splits s in [lo, 64] of a product with rc row tiles on a
+// grid of G CTAs: the smallest whose rc s tiles fill their last wave to 97 %,
+// else the best fill.
+static int pick_splits(int64_t rc, int G, int lo)
+{
+    lo = std::max(1, std::min(lo, 64));
+    int best = lo;
+    double best_fill = -1.0;
+    for (int s = lo; s <= 64; ++s) {
+        const int64_t t = rc * s;
+        const double fill = (double)t / (double)(ceil_div(t, G) * G);
+        if (fill > best_fill + 1e-12) {
+            best_fill = fill;
+            best = s;
+        }
+        if (fill >= 0.97) break;
+    }
+    return best;
+}
+
 // One refinement of A x = b on the device.  Fills stats[0..4] (device) as
 // described in PgArgs::out.
 cudaError_t launch_gmres_persistent(Ctx &c, const double *b, double *x, bool cold, double *stats)
@@ -659,10 +679,13 @@ cudaError_t launch_gmres_persistent(Ctx &c, const double *b, double *x, bool col
     a.cold = cold ? 1 : 0;
     a.rc64 = (int)ceil_div(c.n, MV64_ROWS);
     a.rc32 = (int)ceil_div(c.n, MV32_ROWS);
-    a.s64 = (int)std::max<int64_t>(1, std::min<int64_t>(64, ceil_div(G, a.rc64)));
-    // at least 8 column splits for the FP32 product: each FP32 partial sum then
-    // covers at most n / 64 columns, and the splits are added in FP64
-    a.s32 = (int)std::max<int64_t>(8, std::min<int64_t>(64, ceil_div(G, a.rc32)));
+    // column splits: at least one tile per CTA, then the fewest splits whose
+    // tiles fill the last wave of the grid to 97 % (at n = 27648: 432 row
+    // tiles on 304 CTAs fill 71 % with one split, 99.5 % with seven)
+    a.s64 = pick_splits(a.rc64, G, (int)std::max<int64_t>(1, ceil_div(G, a.rc64)));
+    // at least 8 column splits for the FP32 product: each partial sum then
+    // covers at most n / 8 columns before the splits are added in FP64
+    a.s32 = pick_splits(a.rc32, G, (int)std::max<int64_t>(8, ceil_div(G, a.rc32)));
     a.s64 = (int)std::min<int64_t>(a.s64, c.n);
     a.s32 = (int)std::min<int64_t>(a.s32, c.n);
     a.cps64 = ceil_div(c.n, a.s64);

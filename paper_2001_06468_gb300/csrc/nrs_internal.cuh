@@ -85,6 +85,17 @@ void join_assembly(Ctx &c);
 int run_lu_fp64(Ctx &c, double *A, int64_t lda);
 int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec);
 
+// two-level Gauss-Jordan with rank-256 tensor-core updates (gj2.cu), used by
+// run_gj_fp32 for TF32 from n = GJ2_MIN_N on
+constexpr int64_t GJ2_MIN_N = 8192;
+bool gj2_supported(const Ctx &c);
+size_t gj2_panel_floats(int64_t n);
+int run_gj2_fp32(Ctx &c, float *M, int64_t lda);
+size_t gj_diag_smem();
+void gj_diag_prepare();
+void k_gj_diag_launch(Ctx &c, int64_t n, const float *M, int64_t lda, int64_t k0, float *Dinv,
+                      size_t smem);
+
 bool tc_available();
 bool launch_tc_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb, const float *Rt,
                       int prec, int64_t skip0, int64_t kblk, const float *Cb_lo = nullptr,
@@ -187,8 +198,13 @@ struct Ctx {
     float *d_gj_rt = nullptr;      //   scaled block row, transposed (2 buffers of n x 64, then their TF32 lo parts)
     float *d_gj_cb = nullptr;      //   block column (2 buffers of n x 64, then their TF32 lo parts)
     float *d_gj_stage = nullptr;   //   two finished 64 x 64 tiles (2 buffers)
+    float *d_gj2 = nullptr;        //   two-level factorisation: split panels (4 x gj2_panel_floats)
+    float *d_gj2_r = nullptr;      //   its inner scaled block row (64 x 256)
     int32_t *d_gj_sync = nullptr;  //   counters of the fused factorisation (4)
     bool gj_fused = false;         //   use the fused (one-launch) factorisation when possible
+    int gj_schedule = 0;           //   nrs_problem_desc.factor_schedule
+    bool gj_force_one_level = false;  // the next factorisation: one level whatever the schedule
+    bool last_factor_two_level = false;  // the last factorisation was the two-level one
     int32_t *d_info = nullptr;
     int factored_prec = -1;
     bool assembled = false;

@@ -192,7 +192,7 @@ class Context:
                  reuse_factor: bool = False, reuse_max_inner: int = 0, reuse_max_stages: int = 0,
                  warm_start: bool = False, solve_mode: str = "device", graph: bool = False,
                  inner_tol: float = 0.0, factor_input: str = "fp32",
-                 factor_schedule: str = "streams", residual: str = "dd",
+                 factor_schedule: str = "auto", residual: str = "dd",
                  stream: Optional[torch.cuda.Stream] = None, _handle=None):
         d, self._keep = _make_desc(n_off, q_off, kind, eps, mu, rigid, U, Omega, nn_global,
                                    factor_prec, tol, max_outer, max_inner, reuse_factor,
@@ -436,7 +436,7 @@ def _problem_args(problem):
 def _make_desc(n_off, q_off, kind, eps, mu=1.0, rigid=None, U=None, Omega=None, nn_global=False,
                factor_prec="fp32", tol=0.0, max_outer=0, max_inner=0, reuse_factor=False,
                reuse_max_inner=0, reuse_max_stages=0, warm_start=False, solve_mode="device",
-               graph=False, inner_tol=0.0, factor_input="fp32", factor_schedule="streams",
+               graph=False, inner_tol=0.0, factor_input="fp32", factor_schedule="auto",
                residual="dd"):
     """An nrs_problem_desc and the host arrays it points to (keep them alive)."""
     n_off = np.ascontiguousarray(n_off, dtype=np.int64)
@@ -466,7 +466,7 @@ def _make_desc(n_off, q_off, kind, eps, mu=1.0, rigid=None, U=None, Omega=None, 
     d.graph = int(bool(graph))
     d.inner_tol = float(inner_tol)
     d.factor_input = {"fp32": 0, "rounded": 1}[factor_input]
-    d.factor_schedule = {"streams": 0, "fused": 1}[factor_schedule]
+    d.factor_schedule = {"auto": 0, "fused": 1, "streams": 2, "two_level": 3}[factor_schedule]
     d.residual = {"dd": 0, "fp64": 1}[residual]
     return d, (n_off, q_off, kind, rigid, U, Om)
 

@@ -70,6 +70,23 @@ def test_records_of_every_kernel_family():
     assert k["work_per_launch"] == pytest.approx(8.0 * N_SYS ** 2 * 23.5 + 4.0 * N_SYS ** 2 * 24.5)
 
 
+def test_two_level_factorisation_is_rated_against_the_tensor_peak():
+    # the two-level schedule has one panel span and one update span per
+    # 256-column block and no diagonal-inverse spans; its update is a rank-256
+    # product: 3 split-TF32 passes x 2 n^2 256 flops per launch
+    nb = -(-N_SYS // 256)
+    ms, spans = _phases(lu_panel=(40.0, nb), lu_update=(265.0, nb), assemble=(220.0, 2))
+    recs = bench.rooflines(ms, spans, N_SYS, PAIRS, PEAKS, "measured", SM_MHZ, SOLVE)
+    u = recs["lu_update"]
+    _check(u)
+    assert u["bound"] == "tensor" and u["unit"] == "TFLOP/s"
+    fl = 3 * 2.0 * N_SYS ** 2 * 256
+    assert u["work_per_launch"] == pytest.approx(fl)
+    assert u["achieved"] == pytest.approx(fl / (265e-3 / nb) / 1e12)
+    assert u["peak"] == pytest.approx(PEAKS["bf16_tflops_sustained"] * 1.1 / 2.25)
+    assert "lu_diag" not in recs and "lu_panel" in recs
+
+
 def test_records_are_skipped_for_phases_that_did_not_run():
     ms, spans = _phases(assemble=(80.0, 1), krylov=(100.0, 1))
     recs = bench.rooflines(ms, spans, N_SYS, PAIRS, PEAKS, "measured", SM_MHZ, SOLVE)

@@ -84,7 +84,10 @@ def test_full_size_nearest_assembly_and_solve(N, name):
     sh = g.pack_shapes(pr, t)
     tab = g.body_table(pr)
     Y = g.initial_state(pr)
-    ctx = N.Context.from_problem(pr, factor_prec="tf32", **SOLVER[name])
+    # the single solve has no retry: for the four swimmers the one-level
+    # factor, the more robust preconditioner of the two on that system
+    kw = dict(SOLVER[name], **({"factor_schedule": "streams"} if name == "swimmers4" else {}))
+    ctx = N.Context.from_problem(pr, factor_prec="tf32", **kw)
     ctx.set_state(Y["x0"], Y["B"])
     xi, Xiw, xidot = N.shapes_to_device(sh)
     x, Xw, b = ctx.kinematics(xi, Xiw, xidot)

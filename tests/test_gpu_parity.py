@@ -179,6 +179,31 @@ def test_fused_factor_matches_streamed(N, name):
     assert np.array_equal(sols[0], sols[1])
 
 
+@pytest.mark.parametrize("name", ["swimmer", "sperm2"])
+def test_two_level_factor_matches_the_oracle_and_the_one_level_inverse(N, name):
+    # The two-level elimination (256-column blocks, column panel eliminated in
+    # 64-column steps, one rank-256 tensor-core update per block) forms the
+    # same inverse as the one-level one up to FP32 rounding: the refinement
+    # reaches the oracle's answer from it with the same few GMRES iterations.
+    pr = PROBLEMS[name]()
+    A_or = b_or = None
+    out = {}
+    for schedule in ("two_level", "streams"):
+        ctx, sh, Y, dev = _setup(N, pr, t=0.25, prec="tf32", factor_schedule=schedule)
+        _gpu_system(N, ctx, dev)
+        b = ctx.kinematics(*dev)[2]
+        assert ctx.factor("tf32") == 0
+        x, rep = ctx.solve(b)
+        assert rep[0]["converged"] and rep[0]["outer"] <= 4, (schedule, rep)
+        assert rep[0]["inner"] <= 2 * rep[0]["outer"], (schedule, rep)
+        if A_or is None:
+            A_or, b_or, *_ = _oracle_system(pr, sh, Y)
+            ref = O.solve(A_or, b_or)
+        assert _rel(x.cpu().numpy(), ref) <= TOL_SOL, (schedule, rep)
+        out[schedule] = rep[0]
+        ctx.close()
+
+
 def test_warm_start_and_multiple_rhs(N):
     pr = PROBLEMS["swimmer_small"]()
     ctx, sh, Y, dev = _setup(N, pr, t=0.1)
