@@ -71,6 +71,7 @@ def _load():
                 "or_assemble_stokeslet": (None, [i64, D, i64, D, I32, c_double, c_double, D, i64]),
                 "or_assemble_rows": (None, [i64, I64, i64, D, i64, D, I32, c_double, c_double, D,
                                             i64]),
+                "or_velocity": (None, [i64, D, i64, D, I32, D, c_double, c_double, D]),
                 "or_border": (None, [c_int, I64, I64, I32, D, D, I32, D, D, i64]),
                 "or_rhs": (None, [c_int, I64, I32, D, D, D, D, D, D, D, D]),
                 "or_lu": (c_int, [i64, D, i64, I32]),
@@ -222,6 +223,21 @@ def assemble_rows(rows, x: np.ndarray, Xw: np.ndarray, nn: np.ndarray, eps: floa
                              _i32(np.ascontiguousarray(nn, dtype=np.int32)), float(eps), float(mu),
                              _d(out), 3 * len(rows))
     return out
+
+
+def velocity(xp: np.ndarray, Xw: np.ndarray, nn: np.ndarray, f: np.ndarray, eps: float,
+             mu: float) -> np.ndarray:
+    """Fluid velocity at field points xp (P x 4) induced by the force density
+    f (N x 3 or 3N) through the NEAREST boundary integral (Sec. 3):
+    u(x_p) = (1/8 pi mu) sum_q S^eps(x_p - X_q) w_q f_{n(q)}, summed in
+    ascending q.  Returns P x 4 (u, 0)."""
+    xp = np.ascontiguousarray(xp, dtype=np.float64).reshape(-1, 4)
+    u = np.empty_like(xp)
+    _load().or_velocity(len(xp), _d(xp), len(Xw), _d(np.ascontiguousarray(Xw)),
+                        _i32(np.ascontiguousarray(nn, dtype=np.int32)),
+                        _d(np.ascontiguousarray(f, dtype=np.float64).reshape(-1)),
+                        float(eps), float(mu), _d(u))
+    return u
 
 
 def border(A: np.ndarray, x: np.ndarray, Xw: np.ndarray, nn: np.ndarray, n_off, q_off, kind,
@@ -405,6 +421,41 @@ def mgs(B: np.ndarray) -> np.ndarray:
             Q[:, j] -= (Q[:, i] @ Q[:, j]) * Q[:, i]
         Q[:, j] /= math.sqrt(Q[:, j] @ Q[:, j])
     return Q
+
+
+def rk2_step_tracers(problem, Y, tracers, t: float, dt: float, solver=None):
+    """One explicit-midpoint step of the bodies (rk2_step) and of passive
+    tracers carried by the flow, dx_p/dt = u(x_p) (the particle tracking of
+    the paper's mouse-node and sperm examples): the tracers' stage velocities
+    come from each stage's force density and geometry,
+      x_half = x + dt/2 u(x; stage 1),  x_new = x + dt u(x_half; stage 2).
+    Returns (Y_new, tracers_new (P x 4), stages)."""
+    from synth.geometry import pack_shapes, body_table
+    solver = solver or solve
+    table = body_table(problem)
+    st = pack_shapes(problem, t)
+    sh = pack_shapes(problem, t + 0.5 * dt)
+    N = problem.N
+    xt = np.ascontiguousarray(tracers, dtype=np.float64).reshape(-1, 4)
+    A, b, nn1, _, Xw1 = system(problem, st, table, Y)
+    sol1 = solver(A, b)
+    u1 = velocity(xt, Xw1, nn1, sol1[:3 * N], problem.eps, problem.mu)
+    _, V1 = split_solution(sol1, N)
+    d1 = rates(problem, table, Y, V1)
+    Yh = {"x0": Y["x0"] + 0.5 * dt * d1[0],
+          "B": np.array([mgs(B) for B in Y["B"] + 0.5 * dt * d1[1]])}
+    xh = xt.copy()
+    xh[:, :3] = xt[:, :3] + 0.5 * dt * u1[:, :3]
+    A2, b2, nn2, _, Xw2 = system(problem, sh, table, Yh)
+    sol2 = solver(A2, b2)
+    u2 = velocity(xh, Xw2, nn2, sol2[:3 * N], problem.eps, problem.mu)
+    _, V2 = split_solution(sol2, N)
+    d2 = rates(problem, table, Yh, V2)
+    Yn = {"x0": Y["x0"] + dt * d2[0],
+          "B": np.array([mgs(B) for B in Y["B"] + dt * d2[1]])}
+    xn = xt.copy()
+    xn[:, :3] = xt[:, :3] + dt * u2[:, :3]
+    return Yn, xn, {"sol1": sol1, "sol2": sol2, "u1": u1, "u2": u2}
 
 
 def rk2_step(problem, Y, t: float, dt: float, shapes_t=None, shapes_half=None,

@@ -314,6 +314,42 @@ void or_rhs(int nbodies, const int64_t *n_off, const int32_t *kind, const double
 }
 
 /* ------------------------------------------------------------------------ */
+/* Velocity at field points (Sec. 3: the NEAREST boundary integral evaluated  */
+/* off the body, as used for particle tracking)                              */
+/* ------------------------------------------------------------------------ */
+
+/* u_j(x_p) = (1/(8 pi mu)) sum_q sum_k S^eps_jk(x_p - X_q) w_q f_k(n(q)) for
+ * P field points xp (rows of 4 doubles), summed in ascending q; per q the
+ * three terms (S_jk w_q) f_k are added in k order before joining the sum.
+ * f holds 3 values per force point (the first 3N unknowns of the solution),
+ * nn the nearest force point of each quadrature point.  u: rows of 4 doubles
+ * (u_x, u_y, u_z, 0). */
+void or_velocity(int64_t P, const double *xp, int64_t Q, const double *Xw, const int32_t *nn,
+                 const double *f, double eps, double mu, double *u)
+{
+    double c = 1.0 / (8.0 * OR_PI * mu);
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < P; ++p) {
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int64_t q = 0; q < Q; ++q) {
+            double r[3] = {xp[4 * p + 0] - Xw[4 * q + 0], xp[4 * p + 1] - Xw[4 * q + 1],
+                           xp[4 * p + 2] - Xw[4 * q + 2]};
+            double S[9];
+            or_stokeslet(r, eps, S);
+            double w = Xw[4 * q + 3];
+            const double *fq = f + 3 * (int64_t)nn[q];
+            for (int j = 0; j < 3; ++j) {
+                double v = (S[3 * j + 0] * w) * fq[0] + (S[3 * j + 1] * w) * fq[1] +
+                           (S[3 * j + 2] * w) * fq[2];
+                acc[j] += v;
+            }
+        }
+        for (int j = 0; j < 3; ++j) u[4 * p + j] = acc[j] * c;
+        u[4 * p + 3] = 0.0;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Dense solve (Sec. 4 step 3: the backslash solve)                          */
 /* ------------------------------------------------------------------------ */
 

@@ -487,3 +487,82 @@ def test_rk2_translates_a_prescribed_body_exactly():
     for s in range(5):
         Y = O.rk2_step(pr, Y, s * 0.1, 0.1)
     assert np.allclose(Y["x0"][0], 0.5 * np.array([0.5, -1.0, 2.0]), rtol=1e-15, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# velocity at field points and passive tracers (particle tracking)
+# --------------------------------------------------------------------------
+
+def test_velocity_far_from_a_point_force_is_the_oseen_flow():
+    # one quadrature point of weight w at X carrying the force density f:
+    # u(x) = w S^eps(x - X) f / (8 pi mu) -> w (f/r + (f.r) r/r^3) / (8 pi mu)
+    # for r >> eps (Sec. 3: the blob solution tends to the stokeslet)
+    X = np.array([[0.3, -0.2, 0.1, 0.7]])
+    f = np.array([0.4, -1.3, 2.2])
+    eps, mu = 1e-3, 1.7
+    rng = np.random.default_rng(11)
+    xp = np.zeros((6, 4))
+    d = rng.normal(size=(6, 3))
+    xp[:, :3] = X[0, :3] + 10.0 * d / np.linalg.norm(d, axis=1, keepdims=True)
+    u = O.velocity(xp, X, np.array([0], dtype=np.int32), f, eps, mu)
+    for p in range(6):
+        r = xp[p, :3] - X[0, :3]
+        rn = np.linalg.norm(r)
+        ref = X[0, 3] * (f / rn + (f @ r) * r / rn ** 3) / (8 * math.pi * mu)
+        # the regularisation changes the flow by O(eps^2 / r^2) = 1e-8 of its size
+        assert np.linalg.norm(u[p, :3] - ref) <= 1e-7 * np.linalg.norm(ref)
+        assert u[p, 3] == 0.0
+
+
+def test_velocity_at_collocation_points_is_the_assembled_operator():
+    # at the force points the boundary integral is the assembled A_s: u(x_m) = (A_s f)_m
+    pr = g.swimmer_config(ns_f=20, nth_f=4, ns_q=100, nth_q=8)
+    sh = g.pack_shapes(pr, 0.15)
+    Y = g.initial_state(pr)
+    x, Xw = O.lab_frame(sh, Y)
+    nn = O.nearest(sh["x"], sh["Xw"], sh["n_off"], sh["q_off"])
+    A = O.assemble_stokeslet(x, Xw, nn, pr.eps, pr.mu)
+    f = np.random.default_rng(12).normal(size=3 * pr.N)
+    u = O.velocity(x, Xw, nn, f, pr.eps, pr.mu)
+    ref = (A @ f).reshape(-1, 3)
+    assert np.allclose(u[:, :3], ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+def test_velocity_around_a_translating_sphere_is_the_stokes_flow():
+    # the paper's sphere (N = 864, Q = 3456, eps = 0.01) translating with U:
+    # off the sphere the computed flow is the exact Stokes solution
+    #   u = 3a/4 (U/r + (U.x) x / r^3) + a^3/4 (U/r^3 - 3 (U.x) x / r^5)
+    # to the discretisation's accuracy (the drag is within 2 %)
+    pr = g.sphere_cells_config(12, 24, eps=0.01, U=(1.0, 0.0, 0.0))
+    sh = g.pack_shapes(pr, 0.0)
+    Y = g.initial_state(pr)
+    A, b, nn, x, Xw = O.system(pr, sh, g.body_table(pr), Y)
+    sol = O.solve_lapack(A, b)
+    U = np.array([1.0, 0.0, 0.0])
+    rng = np.random.default_rng(13)
+    d = rng.normal(size=(12, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    xp = np.zeros((24, 4))
+    xp[:12, :3] = 1.5 * d
+    xp[12:, :3] = 3.0 * d
+    u = O.velocity(xp, Xw, nn, sol[:3 * pr.N], pr.eps, pr.mu)
+    for p in range(24):
+        xv = xp[p, :3]
+        r = np.linalg.norm(xv)
+        ref = 0.75 * (U / r + (U @ xv) * xv / r ** 3) + 0.25 * (U / r ** 3 - 3 * (U @ xv) * xv / r ** 5)
+        assert np.linalg.norm(u[p, :3] - ref) <= 0.02 * np.linalg.norm(U), (p, u[p], ref)
+
+
+def test_tracer_on_a_translating_body_is_carried_with_it():
+    # a tracer at a force point of a rigidly translating body sees the body's
+    # velocity at both stages (the collocation condition), so one step moves
+    # it by dt U, like the body
+    U = np.array([0.5, -1.0, 2.0])
+    pr = g.sphere_config(U=tuple(U))
+    Y = g.initial_state(pr)
+    sh = g.pack_shapes(pr, 0.0)
+    tr = np.array(sh["x"][[0, 7, 40]], dtype=np.float64)
+    Yn, trn, st = O.rk2_step_tracers(pr, Y, tr, 0.0, 0.1, solver=O.solve_lapack)
+    assert np.allclose(st["u1"][:, :3], U, rtol=0, atol=1e-11)
+    assert np.allclose(trn[:, :3], tr[:, :3] + 0.1 * U, rtol=0, atol=1e-12)
+    assert np.allclose(Yn["x0"][0], 0.1 * U, rtol=0, atol=1e-15)
