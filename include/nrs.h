@@ -293,6 +293,38 @@ nrs_status nrs_sync(nrs_ctx *ctx);
 nrs_status nrs_counters(const nrs_ctx *ctx, int64_t *factorizations, int64_t *solves,
                         int64_t *outer, int64_t *inner, int64_t *retries);
 
+/* Fluid velocity at field points (Sec. 3: the NEAREST boundary integral
+ * evaluated off the body, the quantity the paper's particle-tracking
+ * examples integrate):
+ *   u(x_p) = (1/(8 pi mu)) sum_q S^eps(x_p - X_q) w_q f_{n(q)},
+ * each term evaluated as the FP64 assembly evaluates it (correctly rounded
+ * square root and division, no fused multiply-add), the sum over q in
+ * contiguous ranges whose partial sums are added in ascending order
+ * (deterministic).
+ *   Xw [Q*4]  device, lab-frame quadrature points (x, y, z, w) as nrs_kinematics
+ *             writes them, or NULL for those of the last nrs_step stage
+ *   xp [P*4]  device, field points (x, y, z, unused)
+ *   f         device, the force density: 3 values per force point (the first
+ *             3N unknowns of a solution)
+ *   u [P*4]   device output (u_x, u_y, u_z, 0)
+ * n(q) is the nearest-neighbour map of the last nrs_nearest_build or
+ * nrs_step.  NRS_EINVAL before there is one (or, with Xw NULL, before the
+ * first nrs_step).  The first call with a larger P allocates the partial-sum
+ * workspace (synchronises). */
+nrs_status nrs_velocity(nrs_ctx *ctx, const double *Xw, const double *xp, int64_t P, const double *f,
+                        double *u);
+
+/* Passive tracers carried by the flow: nrs_step advances them with the
+ * bodies by the same explicit midpoint, x_half = x + dt/2 u(x; stage 1),
+ * x_new = x + dt u(x_half; stage 2), u from nrs_velocity with each stage's
+ * geometry and force density.  xp: host [P*4] (x, y, z, anything; column 3
+ * is kept); P = 0 removes them.  Allocates the tracer workspaces and
+ * synchronises; a step recorded as a CUDA graph is recorded again. */
+nrs_status nrs_set_tracers(nrs_ctx *ctx, const double *xp, int64_t P);
+
+/* Synchronise and copy the tracers' current positions out (host [P*4]). */
+nrs_status nrs_get_tracers(nrs_ctx *ctx, double *xp);
+
 /* Largest problem nrs_nearest_build_static accepts. */
 #define NRS_STATIC_MAX_N 65536       /* force points      */
 #define NRS_STATIC_MAX_Q 1048576     /* quadrature points */

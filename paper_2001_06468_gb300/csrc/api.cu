@@ -137,6 +137,9 @@ void free_all(Ctx *c)
                     c->d_part_lo, c->d_vf, c->d_gj2, c->d_gj2_r};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    void *tr[] = {c->d_tr, c->d_tr_save, c->d_tr_u, c->d_tr_part, c->d_vel_part};
+    for (void *p : tr)
+        if (p) cudaFree(p);
     void *mlp[] = {c->d_mlp_params, c->d_mlp_m,  c->d_mlp_v,     c->d_mlp_g,    c->d_mlp_x,
                    c->d_mlp_t,      c->d_mlp_y,  c->d_mlp_z1,    c->d_mlp_z2,   c->d_mlp_dy,
                    c->d_mlp_d1,     c->d_mlp_d2, c->d_mlp_part,  c->d_mlp_wmean, c->d_mlp_scal,
@@ -319,10 +322,14 @@ nrs_status enqueue_step(Ctx *c, const nrs_shapes *s0, const nrs_shapes *sh, doub
                        cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_B_save, c->d_B, sizeof(double) * 9 * c->nbodies,
                        cudaMemcpyDeviceToDevice, c->stream));
+    if (c->n_tracers > 0)
+        CK(cudaMemcpyAsync(c->d_tr_save, c->d_tr, sizeof(D4) * c->n_tracers,
+                           cudaMemcpyDeviceToDevice, c->stream));
     for (int stage = 0; stage < 2; ++stage) {
         const nrs_shapes *s = stage ? sh : s0;
         launch_kinematics(*c, (const D4 *)s->xi, (const D4 *)s->Xiw, (const D4 *)s->xidot, c->d_x,
                           c->d_Xw, c->d_b);
+        c->kin_valid = true;
         if (c->nn_global) {
             launch_nearest(*c, c->d_x, c->d_Xw, c->d_nn, false);
             launch_segments(*c, c->d_nn, c->d_seg_ptr, c->d_perm);
@@ -344,6 +351,11 @@ nrs_status enqueue_step(Ctx *c, const nrs_shapes *s0, const nrs_shapes *sh, doub
         join_assembly(*c);
         CK(launch_gmres_persistent(*c, c->d_b, out, !warm, so));
         if (berr) enqueue_backward_error(*c, c->d_b, out, so + 5);
+        if (c->n_tracers > 0) {
+            launch_velocity(*c, c->d_Xw, c->d_tr, c->n_tracers, out, c->d_tr_u, c->d_tr_part,
+                            c->stream);
+            launch_tracer_update(*c, stage, dt, c->stream);
+        }
         launch_rk2(*c, stage, dt, out);
         CK(cudaGetLastError());
     }
@@ -697,6 +709,7 @@ nrs_status nrs_nearest_build(nrs_ctx *ctx, const double *x, const double *Xw, in
     nrs::launch_nearest(*c, (const D4 *)x, (const D4 *)Xw, c->d_nn, false);
     nrs::launch_segments(*c, c->d_nn, c->d_seg_ptr, c->d_perm);
     CK(cudaGetLastError());
+    c->map_built = true;
     if (nn) CK(cudaMemcpyAsync(nn, c->d_nn, sizeof(int32_t) * c->Q, cudaMemcpyDeviceToDevice, c->stream));
     if (seg_ptr)
         CK(cudaMemcpyAsync(seg_ptr, c->d_seg_ptr, sizeof(int32_t) * (c->N + 1),
@@ -779,6 +792,9 @@ nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *sh, do
                        cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_B_save, c->d_B, sizeof(double) * 9 * c->nbodies,
                        cudaMemcpyDeviceToDevice, c->stream));
+    if (c->n_tracers > 0)
+        CK(cudaMemcpyAsync(c->d_tr_save, c->d_tr, sizeof(D4) * c->n_tracers,
+                           cudaMemcpyDeviceToDevice, c->stream));
     nrs_status worst = NRS_OK;
     const int64_t fact0 = c->factorizations;
     bool trained = false;
@@ -787,6 +803,7 @@ nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *sh, do
         const nrs_shapes *s = stage ? sh : s0;
         nrs::launch_kinematics(*c, (const D4 *)s->xi, (const D4 *)s->Xiw, (const D4 *)s->xidot,
                                c->d_x, c->d_Xw, c->d_b);
+        c->kin_valid = true;
         bool ran = true;
         if (c->nn_global) {
             nrs::launch_nearest(*c, c->d_x, c->d_Xw, c->d_nn, false);
@@ -903,6 +920,13 @@ nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *sh, do
         }
         c->last_inner = inner;
         c->have_sol = true;
+        if (c->n_tracers > 0) {
+            // tracers: the stage's velocity at their current positions, then
+            // the explicit-midpoint update (x_half, then x_new)
+            nrs::launch_velocity(*c, c->d_Xw, c->d_tr, c->n_tracers, out, c->d_tr_u, c->d_tr_part,
+                                 c->stream);
+            nrs::launch_tracer_update(*c, stage, dt, c->stream);
+        }
         nrs::launch_rk2(*c, stage, dt, out);
         CK(cudaGetLastError());
     }
@@ -1115,6 +1139,77 @@ nrs_status nrs_mlp_start(nrs_ctx *ctx, const float *Y, const double *vprev, doub
     if (!c->mlp_alloc || !c->mlp_scales_set)
         return fail(c, NRS_EINVAL, "nrs_mlp_start: scales not set");
     nrs::mlp_start(*c, Y, vprev, x0);
+    CK(cudaGetLastError());
+    return NRS_OK;
+}
+
+nrs_status nrs_set_tracers(nrs_ctx *ctx, const double *xp, int64_t P)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return NRS_EINVAL;
+    if (P < 0 || (P > 0 && !xp)) return fail(c, NRS_EINVAL, "nrs_set_tracers: bad arguments");
+    CK(cudaStreamSynchronize(c->stream));
+    // a recorded step does not carry a changed tracer set: record it again
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    void *old[] = {c->d_tr, c->d_tr_save, c->d_tr_u, c->d_tr_part};
+    for (void *p : old)
+        if (p) cudaFree(p);
+    c->d_tr = c->d_tr_save = c->d_tr_u = nullptr;
+    c->d_tr_part = nullptr;
+    c->n_tracers = 0;
+    if (P == 0) return NRS_OK;
+    const size_t part = (size_t)nrs::velocity_splits(*c, P) * (size_t)P * 3;
+    cudaError_t e = cudaMalloc(&c->d_tr, sizeof(D4) * P);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_tr_save, sizeof(D4) * P);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_tr_u, sizeof(D4) * P);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_tr_part, sizeof(double) * part);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, NRS_ENOMEM, "tracer workspace allocation failed");
+    }
+    CK(cudaMemcpy(c->d_tr, xp, sizeof(D4) * P, cudaMemcpyHostToDevice));
+    c->n_tracers = P;
+    return NRS_OK;
+}
+
+nrs_status nrs_get_tracers(nrs_ctx *ctx, double *xp)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return NRS_EINVAL;
+    if (c->n_tracers == 0) return NRS_OK;
+    if (!xp) return fail(c, NRS_EINVAL, "nrs_get_tracers: null output");
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(xp, c->d_tr, sizeof(D4) * c->n_tracers, cudaMemcpyDeviceToHost));
+    return NRS_OK;
+}
+
+nrs_status nrs_velocity(nrs_ctx *ctx, const double *Xw, const double *xp, int64_t P, const double *f,
+                        double *u)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return NRS_EINVAL;
+    if (P < 0 || (P > 0 && (!xp || !f || !u)))
+        return fail(c, NRS_EINVAL, "nrs_velocity: bad arguments");
+    if (!(c->nn_valid || c->map_built) || (!Xw && !c->kin_valid))
+        return fail(c, NRS_EINVAL, "nrs_velocity: no nearest-neighbour map or quadrature points yet");
+    const D4 *Xq = Xw ? reinterpret_cast<const D4 *>(Xw) : c->d_Xw;
+    if (P == 0) return NRS_OK;
+    const size_t need = (size_t)nrs::velocity_splits(*c, P) * (size_t)P * 3;
+    if (need > c->vel_part_doubles) {
+        CK(cudaStreamSynchronize(c->stream));
+        if (c->d_vel_part) cudaFree(c->d_vel_part);
+        c->d_vel_part = nullptr;
+        c->vel_part_doubles = 0;
+        if (cudaMalloc(&c->d_vel_part, sizeof(double) * need) != cudaSuccess) {
+            cudaGetLastError();
+            c->d_vel_part = nullptr;
+            return fail(c, NRS_ENOMEM, "velocity workspace allocation failed");
+        }
+        c->vel_part_doubles = need;
+    }
+    nrs::launch_velocity(*c, Xq, reinterpret_cast<const D4 *>(xp), P, f, reinterpret_cast<D4 *>(u),
+                         c->d_vel_part, c->stream);
     CK(cudaGetLastError());
     return NRS_OK;
 }

@@ -81,6 +81,12 @@ void launch_assemble32(Ctx &c, const D4 *x_lab, float *A32, int64_t lda);
 // make c.stream wait for the FP64 assembly running on the side stream, if any
 void join_assembly(Ctx &c);
 
+// ---- velocity at field points and tracers (velocity.cu) --------------------
+int velocity_splits(const Ctx &c, int64_t P);
+void launch_velocity(Ctx &c, const D4 *Xw, const D4 *xp, int64_t P, const double *f, D4 *u,
+                     double *part, cudaStream_t s);
+void launch_tracer_update(Ctx &c, int stage, double dt, cudaStream_t s);
+
 // ---- factorisation (lu.cu) -------------------------------------------------
 int run_lu_fp64(Ctx &c, double *A, int64_t lda);
 int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec);
@@ -177,6 +183,16 @@ struct Ctx {
     // clouds and right-hand side (lab frame)
     D4 *d_x = nullptr, *d_Xw = nullptr;
     double *d_b = nullptr, *d_sol = nullptr;
+
+    // passive tracers carried by the flow (nrs_set_tracers), and the workspace
+    // of nrs_velocity
+    int64_t n_tracers = 0;
+    bool kin_valid = false;    // d_Xw holds the lab-frame quadrature points of the last stage
+    bool map_built = false;    // d_nn holds a map from nrs_nearest_build
+    D4 *d_tr = nullptr, *d_tr_save = nullptr, *d_tr_u = nullptr;
+    double *d_tr_part = nullptr;
+    double *d_vel_part = nullptr;
+    size_t vel_part_doubles = 0;
 
     // nearest neighbours and segments
     int32_t *d_nn = nullptr, *d_seg_ptr = nullptr, *d_perm = nullptr, *d_cursor = nullptr;

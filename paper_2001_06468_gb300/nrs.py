@@ -37,6 +37,7 @@ FREE, PRESCRIBED, STATIC = 0, 1, 2
 EXPORTS = ["nrs_create", "nrs_destroy", "nrs_last_error", "nrs_sizes", "nrs_set_state",
            "nrs_get_state", "nrs_set_external", "nrs_kinematics", "nrs_nearest_build",
            "nrs_assemble", "nrs_factor", "nrs_solve", "nrs_step", "nrs_sync", "nrs_counters",
+           "nrs_velocity", "nrs_set_tracers", "nrs_get_tracers",
            "nrs_set_timing",
            "nrs_get_timing", "nrs_get_trace", "nrs_rank64_update", "nrs_nearest_build_static",
            "nrs_mlp_set_params", "nrs_mlp_get_params", "nrs_mlp_config", "nrs_mlp_eval",
@@ -118,6 +119,9 @@ _sig = {
                                 _P, ctypes.POINTER(StepReport)]),
     "nrs_sync": (ctypes.c_int, [_P]),
     "nrs_counters": (ctypes.c_int, [_P, _I64P, _I64P, _I64P, _I64P, _I64P]),
+    "nrs_velocity": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
+    "nrs_set_tracers": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    "nrs_get_tracers": (ctypes.c_int, [_P, _P]),
     "nrs_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
     "nrs_rank64_update": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P,
                                          ctypes.c_int32]),
@@ -325,6 +329,27 @@ class Context:
 
     def sync(self):
         return self._check(_lib.nrs_sync(self._h))
+
+    def velocity(self, xp: torch.Tensor, f: torch.Tensor, Xw: Optional[torch.Tensor] = None):
+        """Fluid velocity (P, 4) at device field points xp (P, 4) from the force
+        density f (device, 3 per force point); Xw: lab-frame quadrature points
+        (None = those of the last step stage)."""
+        P = xp.shape[0]
+        u = torch.empty((P, 4), dtype=torch.float64, device=xp.device)
+        self._check(_lib.nrs_velocity(self._h, _ptr(Xw, torch.float64), _ptr(xp, torch.float64), P,
+                                      _ptr(f, torch.float64), _ptr(u)))
+        return u
+
+    def set_tracers(self, xp):
+        """Tracers (host array (P, 4)) advanced by nrs_step; None or empty removes them."""
+        a = np.zeros((0, 4)) if xp is None else np.ascontiguousarray(xp, dtype=np.float64).reshape(-1, 4)
+        self._check(_lib.nrs_set_tracers(self._h, a.ctypes.data if len(a) else None, len(a)))
+        self.n_tracers = len(a)
+
+    def get_tracers(self):
+        out = np.empty((getattr(self, "n_tracers", 0), 4), dtype=np.float64)
+        self._check(_lib.nrs_get_tracers(self._h, out.ctypes.data if len(out) else None))
+        return out
 
     def counters(self):
         """{'factorizations', 'solves', 'outer', 'inner', 'retries'} since creation."""
