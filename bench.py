@@ -616,6 +616,48 @@ def side_workload(nrs, args, name, steps, warm, solver, timer, graph=False):
     return out
 
 
+def tracers_line(nrs, args, timer, count=2000, steps=3, warm=1):
+    """The channel workload with passive tracers (the paper's particle
+    tracking): seconds per step of the product path carrying ``count``
+    tracers seeded in the channel, and the velocity kernel on its own
+    (pairs/s = tracers x quadrature points per evaluation)."""
+    import torch
+    pr = g.workload(HEADLINE)
+    dt = pr.dt
+    rng = np.random.default_rng(0)
+    tr = np.zeros((count, 4))
+    tr[:, :3] = rng.uniform([0.1, 0.1, 0.05], [3.9, 0.9, 0.45], size=(count, 3))
+    dev = [(nrs.shapes_to_device(g.pack_shapes(pr, s * dt)),
+            nrs.shapes_to_device(g.pack_shapes(pr, (s + 0.5) * dt))) for s in range(steps + warm)]
+    Y0 = g.initial_state(pr)
+    ctx = nrs.Context.from_problem(pr, factor_prec=args.prec, **HEADLINE_SOLVER)
+    ctx.set_state(Y0["x0"], Y0["B"])
+    ctx.set_tracers(tr)
+
+    def step(s):
+        ctx.step(nrs.Context.shapes(*dev[s][0]), nrs.Context.shapes(*dev[s][1]), dt, report=False)
+
+    for s in range(warm):
+        step(s)
+    ms = timer.run(ctx.stream, step, steps, first=warm)
+    # the velocity kernel alone, on the last stage's geometry
+    xp = torch.from_numpy(tr).cuda()
+    f = torch.from_numpy(rng.normal(size=3 * pr.N)).cuda()
+    ctx.velocity(xp, f)
+    vms = timer.run(ctx.stream, lambda s: ctx.velocity(xp, f), 5)
+    moved = float(np.abs(ctx.get_tracers()[:, :3] - tr[:, :3]).max())
+    ctx.close()
+    t = float(np.median(vms)) / 1e3
+    pairs = count * pr.Q
+    return {"workload": WORKLOADS_DESC[HEADLINE] + f", {count} tracers",
+            "s_per_step": float(np.mean(ms)) / 1e3, "steps": steps,
+            "velocity_ms": t * 1e3, "velocity_pairs_per_s": pairs / t,
+            "velocity_fp64_gops": pairs * 52 / t / 1e9,
+            "velocity_note": "52 FP64 operations per (tracer, quadrature point) pair; two "
+                             "evaluations per step",
+            "max_tracer_displacement": moved}
+
+
 def plain_fp64(nrs, args, timer):
     """The plain FP64 GPU path on the headline workload: the FP64 assembly
     (this library's kernel, the same matrix) and cuSOLVER's getrf + getrs
@@ -930,6 +972,7 @@ def run_nrs(args):
         side["swimmers4"] = side_workload(nrs, args, "swimmers4", 1, 1, C2_SOLVER, timer)
         side["swimmer"] = side_workload(nrs, args, "swimmer", 20, 3, {}, timer, graph=True)
         side["swimmer_reuse"] = side_workload(nrs, args, "swimmer", 20, 3, HEADLINE_SOLVER, timer)
+        side["tracers"] = tracers_line(nrs, args, timer)
         torch.cuda.empty_cache()
         side["plain_fp64"] = plain_fp64(nrs, args, timer)
         torch.cuda.empty_cache()
