@@ -423,6 +423,97 @@ def mgs(B: np.ndarray) -> np.ndarray:
     return Q
 
 
+# Dormand & Prince (1980), the RK5(4)7M pair behind ode45 (Sec. 4 integrates
+# the IVP with ode45): nodes, stage coefficients, fifth- and fourth-order weights
+DP_C = [0.0, 1 / 5, 3 / 10, 4 / 5, 8 / 9, 1.0, 1.0]
+DP_A = [[],
+        [1 / 5],
+        [3 / 40, 9 / 40],
+        [44 / 45, -56 / 15, 32 / 9],
+        [19372 / 6561, -25360 / 2187, 64448 / 6561, -212 / 729],
+        [9017 / 3168, -355 / 33, 46732 / 5247, 49 / 176, -5103 / 18656],
+        [35 / 384, 0.0, 500 / 1113, 125 / 192, -2187 / 6784, 11 / 84]]
+DP_B5 = [35 / 384, 0.0, 500 / 1113, 125 / 192, -2187 / 6784, 11 / 84, 0.0]
+DP_B4 = [5179 / 57600, 0.0, 7571 / 16695, 393 / 640, -92097 / 339200, 187 / 2100, 1 / 40]
+
+
+def _dp_state(Y, table):
+    """The integrated components per non-static body: x0 (3) and B (9)."""
+    return np.concatenate([Y["x0"], Y["B"].reshape(-1, 9)], axis=1)
+
+
+def dp_step(problem, Y, t: float, h: float, rtol: float, atol: float, K0=None, solver=None):
+    """One trial step of the Dormand-Prince pair for dY/dt = F(Y, t): the
+    stage states Y_i = Y + h sum_j a_ij K_j (B re-orthonormalised by modified
+    Gram-Schmidt, as the RK2 step does), K_i = dY/dt from each stage's solve;
+    Y_new = the seventh stage's state; the error norm
+    max_c |h sum_j (b5_j - b4_j) K_j,c| / (atol + rtol max(|Y_c|, |Y_new,c|))
+    over the components of the non-static bodies.
+    Returns (Y_new, K (7 rates per body as (dx0, dB)), err)."""
+    from synth.geometry import pack_shapes, body_table
+    solver = solver or solve
+    table = body_table(problem)
+    N = problem.N
+    K = []
+    Ys = []
+    for i in range(7):
+        if i == 0:
+            Yi = Y
+        else:
+            x0 = Y["x0"] + h * sum(DP_A[i][j] * K[j][0] for j in range(i))
+            B = Y["B"] + h * sum(DP_A[i][j] * K[j][1] for j in range(i))
+            Yi = {"x0": x0, "B": np.array([mgs(b) for b in B])}
+            for b, kind in enumerate(table["kind"]):
+                if kind == STATIC:
+                    Yi["x0"][b] = Y["x0"][b]
+                    Yi["B"][b] = Y["B"][b]
+        Ys.append(Yi)
+        if i == 0 and K0 is not None:
+            K.append(K0)
+            continue
+        sh = pack_shapes(problem, t + DP_C[i] * h)
+        A, b, *_ = system(problem, sh, table, Yi)
+        sol = solver(A, b)
+        _, V = split_solution(sol, N)
+        K.append(rates(problem, table, Yi, V))
+    Yn = Ys[6]
+    e = [DP_B5[j] - DP_B4[j] for j in range(7)]
+    E0 = h * sum(e[j] * K[j][0] for j in range(7))
+    E1 = h * sum(e[j] * K[j][1] for j in range(7))
+    E = np.concatenate([E0, E1.reshape(-1, 9)], axis=1)
+    y0, y1 = _dp_state(Y, table), _dp_state(Yn, table)
+    live = np.array([k != STATIC for k in table["kind"]])
+    sc = atol + rtol * np.maximum(np.abs(y0), np.abs(y1))
+    err = float(np.max(np.abs(E[live]) / sc[live])) if live.any() else 0.0
+    return Yn, K, err
+
+
+def dp_integrate(problem, Y, t0: float, t_end: float, h0: float, rtol: float, atol: float,
+                 h_min: float = 1e-8, h_max: float = None, solver=None):
+    """Adaptive integration with dp_step: a trial with err <= 1 is accepted
+    (its last stage's rates start the next step), and every trial sets the
+    next step to h min(5 (accepted) or 1 (rejected), max(0.2, 0.9 err^(-1/5))),
+    within [h_min, h_max] and the interval.  Returns (Y, t, accepted, rejected)."""
+    h_max = t_end - t0 if h_max is None else h_max
+    t, h = t0, min(h0, h_max, t_end - t0)
+    K0 = None
+    acc = rej = 0
+    while t < t_end * (1 - 1e-14):
+        Yn, K, err = dp_step(problem, Y, t, h, rtol, atol, K0=K0, solver=solver)
+        ok = np.isfinite(err) and err <= 1.0
+        f = 0.9 * err ** -0.2 if err > 0 else 5.0
+        f = min(5.0 if ok else 1.0, max(0.2, f))
+        if ok:
+            t, Y, K0 = t + h, Yn, K[6]
+            acc += 1
+        else:
+            rej += 1
+            if h <= h_min:
+                raise RuntimeError("step rejected at the smallest step size")
+        h = min(h_max, max(h_min, h * f), t_end - t)
+    return Y, t, acc, rej
+
+
 def rk2_step_tracers(problem, Y, tracers, t: float, dt: float, solver=None):
     """One explicit-midpoint step of the bodies (rk2_step) and of passive
     tracers carried by the flow, dx_p/dt = u(x_p) (the particle tracking of

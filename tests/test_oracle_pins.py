@@ -566,3 +566,62 @@ def test_tracer_on_a_translating_body_is_carried_with_it():
     assert np.allclose(st["u1"][:, :3], U, rtol=0, atol=1e-11)
     assert np.allclose(trn[:, :3], tr[:, :3] + 0.1 * U, rtol=0, atol=1e-12)
     assert np.allclose(Yn["x0"][0], 0.1 * U, rtol=0, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# adaptive Dormand-Prince stepping (the ode45 of Sec. 4)
+# --------------------------------------------------------------------------
+
+def _rot(axis_rate, angle):
+    k = np.asarray(axis_rate, float) / np.linalg.norm(axis_rate)
+    Kx = np.array([[0.0, -k[2], k[1]], [k[2], 0.0, -k[0]], [-k[1], k[0], 0.0]])
+    return np.eye(3) + math.sin(angle) * Kx + (1 - math.cos(angle)) * (Kx @ Kx)
+
+
+def test_dormand_prince_is_fifth_order_for_a_prescribed_rotation():
+    # fixed steps (tolerance never binding): the global error of B(T) against
+    # the exact rotation falls by at least 2^5 per halving of the step (for
+    # this linear problem it falls a little faster, ~2^5.8); a wrong
+    # coefficient of the tableau drops the order
+    Om = np.array([0.3, -1.1, 2.0])
+    pr = g.sphere_config(n_force=2, n_quad=4, U=(0.0, 0.0, 0.0), Omega=tuple(Om))
+    T = 1.0
+    errs = []
+    for steps in (4, 8, 16):
+        Y = g.initial_state(pr)
+        h = T / steps
+        K0 = None
+        for s in range(steps):
+            Y, K, _ = O.dp_step(pr, Y, s * h, h, 1.0, 1.0, K0=K0)
+            K0 = K[6]
+        errs.append(np.abs(Y["B"][0] - _rot(Om, np.linalg.norm(Om) * T)).max())
+    assert errs[0] / errs[1] > 28.0 and errs[1] / errs[2] > 28.0, errs
+    assert errs[2] < 1e-9
+
+
+def test_dormand_prince_error_estimate_scales_as_h5_and_translation_is_exact():
+    # the embedded estimate of one step shrinks at least as h^5; a prescribed
+    # translation is integrated exactly (every stage has the same rate)
+    Om = np.array([0.0, 0.0, 1.5])
+    pr = g.sphere_config(n_force=2, n_quad=4, U=(0.4, 0.0, -0.2), Omega=tuple(Om))
+    Y0 = g.initial_state(pr)
+    e1 = O.dp_step(pr, Y0, 0.0, 0.2, 1e-10, 1e-10)[2]
+    e2 = O.dp_step(pr, Y0, 0.0, 0.1, 1e-10, 1e-10)[2]
+    assert e1 / e2 > 28.0, (e1, e2)
+    Yn = O.dp_step(pr, Y0, 0.0, 0.3, 1.0, 1.0)[0]
+    assert np.allclose(Yn["x0"][0], 0.3 * np.array([0.4, 0.0, -0.2]), rtol=0, atol=1e-15)
+
+
+def test_adaptive_dormand_prince_meets_its_tolerance():
+    # a fast rotation over one period: the controller adapts h (steps get
+    # rejected from a too-large first step) and the end state is within a
+    # small multiple of the tolerance of the exact rotation
+    Om = np.array([1.0, 2.0, -2.0])
+    pr = g.sphere_config(n_force=2, n_quad=4, U=(0.0, 0.0, 0.0), Omega=tuple(Om))
+    T = 2 * math.pi / np.linalg.norm(Om)
+    for tol in (1e-6, 1e-9):
+        Y, t, acc, rej = O.dp_integrate(pr, g.initial_state(pr), 0.0, T, 1.0, tol, tol)
+        assert abs(t - T) <= 1e-12
+        err = np.abs(Y["B"][0] - np.eye(3)).max()
+        assert err <= 50 * tol, (tol, err, acc, rej)
+        assert rej >= 1
