@@ -658,6 +658,40 @@ def tracers_line(nrs, args, timer, count=2000, steps=3, warm=1):
             "max_tracer_displacement": moved}
 
 
+def dormand_prince_line(nrs, args, name="swimmer", T=0.1, tol=1e-8):
+    """Adaptive Dormand-Prince 5(4) (the paper's ode45) on a workload over
+    [0, T] with rtol = atol = tol: steps, stage evaluations and seconds per
+    simulated time unit (wall clock of the whole integration, device
+    synchronised at its ends), beside the explicit midpoint's cost per unit
+    time at the bench's dt."""
+    import torch
+    pr = g.workload(name)
+    Y0 = g.initial_state(pr)
+    cache = {}
+
+    def at(t):
+        key = round(t, 15)
+        if key not in cache:
+            cache[key] = nrs.shapes_to_device(g.pack_shapes(pr, t))
+        return nrs.Context.shapes(*cache[key])
+
+    for warm in (True, False):
+        ctx = nrs.Context.from_problem(pr, factor_prec=args.prec, **HEADLINE_SOLVER)
+        ctx.set_state(Y0["x0"], Y0["B"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = ctx.dp_integrate(at, 0.0, T if not warm else pr.dt, pr.dt, tol, tol)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ctx.close()
+    stages = 7 + 6 * (info["accepted"] + info["rejected"] - 1)
+    return {"workload": WORKLOADS_DESC.get(name, name), "interval": T, "rtol": tol, "atol": tol,
+            "accepted": info["accepted"], "rejected": info["rejected"], "stage_evaluations": stages,
+            "s_per_time_unit": wall / T, "s_per_accepted_step": wall / max(info["accepted"], 1),
+            "mean_step": T / max(info["accepted"], 1),
+            "rk2_stage_evaluations_per_time_unit_at_dt": 2.0 / pr.dt}
+
+
 def plain_fp64(nrs, args, timer):
     """The plain FP64 GPU path on the headline workload: the FP64 assembly
     (this library's kernel, the same matrix) and cuSOLVER's getrf + getrs
@@ -973,6 +1007,7 @@ def run_nrs(args):
         side["swimmer"] = side_workload(nrs, args, "swimmer", 20, 3, {}, timer, graph=True)
         side["swimmer_reuse"] = side_workload(nrs, args, "swimmer", 20, 3, HEADLINE_SOLVER, timer)
         side["tracers"] = tracers_line(nrs, args, timer)
+        side["dormand_prince"] = dormand_prince_line(nrs, args)
         torch.cuda.empty_cache()
         side["plain_fp64"] = plain_fp64(nrs, args, timer)
         torch.cuda.empty_cache()

@@ -269,6 +269,53 @@ nrs_status nrs_solve(nrs_ctx *ctx, const double *b, double *x, int32_t nrhs, con
 nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *s_half, double dt,
                     double *sol, nrs_step_report *report);
 
+/* ---- adaptive Dormand-Prince stepping ------------------------------------
+ * The paper integrates the swimming IVP dY/dt = F(Y, t), Y = [X0; B], with
+ * MATLAB's ode45, the Dormand-Prince 5(4) pair with step-size control
+ * (Sec. 4).  This is that integrator on the device, one stage evaluation
+ * (kinematics, nearest neighbours, assembly, factor or reuse, solve, as in
+ * nrs_step) per call: the caller supplies the body-frame shapes at the time
+ * nrs_dp_next_time names, because the beat kinematics are an input.
+ * Stage states Y_i = Y_n + h sum_j a_ij K_j (B re-orthonormalised by modified
+ * Gram-Schmidt), K_i = (U, [Omega]x B) from the stage's solution; after the
+ * seventh stage the error norm max_c |h sum_j (b5_j - b4_j) K_j,c| /
+ * (atol + rtol max(|Y_n,c|, |Y_n+1,c|)) over the state's components decides:
+ * err <= 1 accepts Y_n+1 (the seventh stage's state; its rates start the next
+ * step), otherwise the step is retried; either way h <- h min(5 or 1,
+ * max(0.2, 0.9 err^(-1/5))), clamped to [h_min, h_max] and to the interval's
+ * end.  The context's state is the stage state during a step and Y_n+1 after
+ * an accepted one.  Not in graph mode; nrs_step overwrites the integrator's
+ * saved state (call nrs_dp_start again after it).  Tracers are not carried. */
+typedef struct {
+    double t;               /* time of the last accepted state                    */
+    double h;               /* step size of the step in progress                  */
+    double err;             /* error norm of the last completed trial             */
+    int32_t stage;          /* next stage to evaluate (0: the first step's first) */
+    int32_t accepted, rejected;  /* steps accepted and rejected so far            */
+    int32_t last_accepted;  /* 1 if the last completed trial was accepted         */
+    int32_t done;           /* 1 once t reached t_end                             */
+} nrs_dp_info;
+
+/* Begin an integration from the context's state at t0 to t_end with initial
+ * step h0, tolerances rtol (> 0) and atol (>= 0), step bounds 0 < h_min <=
+ * h_max.  NRS_EINVAL for bad arguments or a context in graph mode. */
+nrs_status nrs_dp_start(nrs_ctx *ctx, double t0, double t_end, double h0, double rtol, double atol,
+                        double h_min, double h_max);
+
+/* Time at which the next nrs_dp_stage needs the body-frame shapes. */
+nrs_status nrs_dp_next_time(const nrs_ctx *ctx, double *t_stage);
+
+/* Evaluate the next stage with the shapes at nrs_dp_next_time; sol (device
+ * [n] or NULL) receives the stage's solution; info (host or NULL) the
+ * integrator's state after the call.  The seventh stage synchronises (the
+ * error norm is read on the host).  NRS_ENOCONV when a step is rejected at
+ * h_min, or a stage's refinement fails; NRS_EINVAL when no integration is in
+ * progress (or it is done). */
+nrs_status nrs_dp_stage(nrs_ctx *ctx, const nrs_shapes *s, double *sol, nrs_dp_info *info);
+
+/* The integrator's state (host). */
+nrs_status nrs_dp_info_get(const nrs_ctx *ctx, nrs_dp_info *info);
+
 /* The rank-64 update of the Gauss-Jordan inverse on its own (the kernel that
  * nrs_factor runs once per 64-column block):
  *   M[i, j] -= sum_{c < 64} C[i*64 + c] * Rt[j*64 + c]      for 0 <= i, j < n,

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnrs.so")
 SOURCES = ["geometry.cu", "assemble.cu", "lu.cu", "gj.cu", "gj2.cu", "solve.cu", "tc_gemm.cu", "api.cu",
-           "static_nn.cu", "mlp.cu", "velocity.cu",
+           "static_nn.cu", "mlp.cu", "velocity.cu", "dp.cu",
            "gmres_persistent.cu", "batch.cu"]
 HEADERS = ["nrs_internal.cuh", "tc_prims.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 #include <string>
 #include <vector>
@@ -137,7 +138,8 @@ void free_all(Ctx *c)
                     c->d_part_lo, c->d_vf, c->d_gj2, c->d_gj2_r};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    void *tr[] = {c->d_tr, c->d_tr_save, c->d_tr_u, c->d_tr_part, c->d_vel_part};
+    void *tr[] = {c->d_tr, c->d_tr_save, c->d_tr_u, c->d_tr_part, c->d_vel_part, c->d_dp_K,
+                  c->d_dp_err};
     for (void *p : tr)
         if (p) cudaFree(p);
     void *mlp[] = {c->d_mlp_params, c->d_mlp_m,  c->d_mlp_v,     c->d_mlp_g,    c->d_mlp_x,
@@ -774,6 +776,89 @@ nrs_status nrs_solve(nrs_ctx *ctx, const double *b, double *x, int32_t nrhs, con
     return worst;
 }
 
+namespace {
+
+// One evaluation of the swimming problem's right-hand side up to the factor
+// (Sec. 4 steps 1-3): kinematics at the context's state, nearest neighbours
+// (deforming bodies; rigid ones keep their map), segments, assembly, border,
+// and the factorisation if the reuse policy asks for one (*need_factor).
+nrs_status prepare_stage(Ctx *c, const nrs_shapes *s, bool *need_factor)
+{
+    nrs::launch_kinematics(*c, (const D4 *)s->xi, (const D4 *)s->Xiw, (const D4 *)s->xidot, c->d_x,
+                           c->d_Xw, c->d_b);
+    c->kin_valid = true;
+    bool ran = true;
+    if (c->nn_global) {
+        nrs::launch_nearest(*c, c->d_x, c->d_Xw, c->d_nn, false);
+    } else if (!c->nn_valid) {
+        nrs::launch_nearest(*c, (const D4 *)s->xi, (const D4 *)s->Xiw, c->d_nn, false);
+        c->nn_valid = true;
+    } else if (c->n_tasks_deform > 0) {
+        nrs::launch_nearest(*c, (const D4 *)s->xi, (const D4 *)s->Xiw, c->d_nn, true);
+    } else {
+        ran = false;
+    }
+    if (ran || !c->seg_valid) nrs::launch_segments(*c, c->d_nn, c->d_seg_ptr, c->d_perm);
+    c->seg_valid = true;
+    *need_factor = !c->reuse_factor || c->factored_prec != c->factor_prec ||
+                   c->stages_since_factor >= c->reuse_max_stages ||
+                   c->last_inner > c->reuse_max_inner;
+    nrs_status st = do_segments_and_assemble(c, c->d_x, c->d_Xw, *need_factor);
+    if (st != NRS_OK) return st;
+    if (*need_factor) {
+        st = do_factor(c, c->factor_prec);
+        if (st != NRS_OK) return st;
+        c->stages_since_factor = 0;
+    } else {
+        c->stages_since_factor += 1;
+    }
+    return NRS_OK;
+}
+
+// The stage's refinement, and the retry of nrs_step when it does not converge.
+nrs_status solve_stage(Ctx *c, double *out, const double *x0, bool need_factor,
+                       nrs_solve_report *rep, int *inner_out, int *retried)
+{
+    int inner = 0;
+    *retried = 0;
+    nrs_status st = nrs::run_gmres_ir(*c, c->d_b, out, x0, rep, &inner);
+    if (st == NRS_ECUDA) return st;
+    if (st == NRS_ENOCONV && c->factor_prec != NRS_FP64) {
+        // The refinement did not converge with this factor.  An FP32 inverse
+        // of a system with kappa(A) u_fp32 >> 1 is sometimes a poor
+        // preconditioner; another one usually is not: a two-level factor
+        // is replaced by the one-level elimination of the same input (the
+        // more robust of the two on such systems), a one-level one by that
+        // of the other FP32 input (the rounded FP64 entries instead of the
+        // FP32 evaluation, or the reverse), a reused factor by a fresh one
+        // of the configured input.  One retry, from the same start.
+        const bool was_two = need_factor && c->last_factor_two_level;
+        const bool other = need_factor && !was_two ? c->lo_eval == 1 : c->lo_eval == 0;
+        if (was_two) c->gj_force_one_level = true;
+        nrs::join_assembly(*c);
+        if (other) {
+            nrs::launch_assemble32(*c, c->d_x, c->d_A32, c->lda);
+            c->a32_fresh = true;
+        } else {
+            c->a32_fresh = false;  // do_factor rounds the FP64 entries
+        }
+        c->factored_prec = -1;
+        st = do_factor(c, c->factor_prec);
+        c->gj_force_one_level = false;
+        if (st != NRS_OK) return st;
+        c->stages_since_factor = 0;
+        c->retries += 1;
+        *retried = 1;
+        inner = 0;
+        st = nrs::run_gmres_ir(*c, c->d_b, out, x0, rep, &inner);
+        if (st == NRS_ECUDA) return st;
+    }
+    *inner_out = inner;
+    return st;
+}
+
+}  // namespace
+
 nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *sh, double dt, double *sol,
                     nrs_step_report *report)
 {
@@ -801,34 +886,9 @@ nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *sh, do
     if (report) report->mlp_rel_err = -1.0;
     for (int stage = 0; stage < 2; ++stage) {
         const nrs_shapes *s = stage ? sh : s0;
-        nrs::launch_kinematics(*c, (const D4 *)s->xi, (const D4 *)s->Xiw, (const D4 *)s->xidot,
-                               c->d_x, c->d_Xw, c->d_b);
-        c->kin_valid = true;
-        bool ran = true;
-        if (c->nn_global) {
-            nrs::launch_nearest(*c, c->d_x, c->d_Xw, c->d_nn, false);
-        } else if (!c->nn_valid) {
-            nrs::launch_nearest(*c, (const D4 *)s->xi, (const D4 *)s->Xiw, c->d_nn, false);
-            c->nn_valid = true;
-        } else if (c->n_tasks_deform > 0) {
-            nrs::launch_nearest(*c, (const D4 *)s->xi, (const D4 *)s->Xiw, c->d_nn, true);
-        } else {
-            ran = false;
-        }
-        if (ran || !c->seg_valid) nrs::launch_segments(*c, c->d_nn, c->d_seg_ptr, c->d_perm);
-        c->seg_valid = true;
-        const bool need_factor = !c->reuse_factor || c->factored_prec != c->factor_prec ||
-                                 c->stages_since_factor >= c->reuse_max_stages ||
-                                 c->last_inner > c->reuse_max_inner;
-        nrs_status st = do_segments_and_assemble(c, c->d_x, c->d_Xw, need_factor);
+        bool need_factor = false;
+        nrs_status st = prepare_stage(c, s, &need_factor);
         if (st != NRS_OK) return st;
-        if (need_factor) {
-            st = do_factor(c, c->factor_prec);
-            if (st != NRS_OK) return st;
-            c->stages_since_factor = 0;
-        } else {
-            c->stages_since_factor += 1;
-        }
         double *out = c->d_sol + (int64_t)stage * c->lda;
         const double *prev = c->have_sol ? c->d_sol + (int64_t)(1 - stage) * c->lda : nullptr;
         const double *vprev = (prev && c->F) ? prev + 3 * c->N : nullptr;
@@ -854,40 +914,11 @@ nrs_status nrs_step(nrs_ctx *ctx, const nrs_shapes *s0, const nrs_shapes *sh, do
             }
         }
         int inner = 0;
-        st = nrs::run_gmres_ir(*c, c->d_b, out, x0, report ? &report->stage[stage] : nullptr, &inner);
+        int retried = 0;
+        st = solve_stage(c, out, x0, need_factor, report ? &report->stage[stage] : nullptr, &inner,
+                         &retried);
         if (st == NRS_ECUDA) return st;
-        if (report) report->retried[stage] = 0;
-        if (st == NRS_ENOCONV && c->factor_prec != NRS_FP64) {
-            // The refinement did not converge with this factor.  An FP32 inverse
-            // of a system with kappa(A) u_fp32 >> 1 is sometimes a poor
-            // preconditioner; another one usually is not: a two-level factor
-            // is replaced by the one-level elimination of the same input (the
-            // more robust of the two on such systems), a one-level one by that
-            // of the other FP32 input (the rounded FP64 entries instead of the
-            // FP32 evaluation, or the reverse), a reused factor by a fresh one
-            // of the configured input.  One retry, from the same start.
-            const bool was_two = need_factor && c->last_factor_two_level;
-            const bool other = need_factor && !was_two ? c->lo_eval == 1 : c->lo_eval == 0;
-            if (was_two) c->gj_force_one_level = true;
-            nrs::join_assembly(*c);
-            if (other) {
-                nrs::launch_assemble32(*c, c->d_x, c->d_A32, c->lda);
-                c->a32_fresh = true;
-            } else {
-                c->a32_fresh = false;  // do_factor rounds the FP64 entries
-            }
-            c->factored_prec = -1;
-            st = do_factor(c, c->factor_prec);
-            c->gj_force_one_level = false;
-            if (st != NRS_OK) return st;
-            c->stages_since_factor = 0;
-            c->retries += 1;
-            if (report) report->retried[stage] = 1;
-            inner = 0;
-            st = nrs::run_gmres_ir(*c, c->d_b, out, x0, report ? &report->stage[stage] : nullptr,
-                                   &inner);
-            if (st == NRS_ECUDA) return st;
-        }
+        if (report) report->retried[stage] = retried;
         if (st != NRS_OK && worst == NRS_OK) worst = st;
         // run_gmres_ir synchronised the stream: the pinned copy of the choice has landed
         if (learned && c->h_mlp_used[0]) {
@@ -1140,6 +1171,150 @@ nrs_status nrs_mlp_start(nrs_ctx *ctx, const float *Y, const double *vprev, doub
         return fail(c, NRS_EINVAL, "nrs_mlp_start: scales not set");
     nrs::mlp_start(*c, Y, vprev, x0);
     CK(cudaGetLastError());
+    return NRS_OK;
+}
+
+namespace {
+
+void dp_fill(const Ctx *c, nrs_dp_info *info)
+{
+    if (!info) return;
+    info->t = c->dp_t;
+    info->h = c->dp_h;
+    info->err = c->dp_err;
+    info->stage = c->dp_stage;
+    info->accepted = c->dp_accepted;
+    info->rejected = c->dp_rejected;
+    info->last_accepted = c->dp_last_accepted;
+    info->done = c->dp_done;
+}
+
+// the next trial step: h grown or shrunk by 0.9 err^(-1/5) within [0.2, 5],
+// clamped to [h_min, h_max] and to the end of the interval
+double dp_next_h(const Ctx *c, double h, double err, bool accepted)
+{
+    double f = err > 0.0 && std::isfinite(err) ? 0.9 * std::pow(err, -0.2) : (err == 0.0 ? 5.0 : 0.2);
+    f = std::min(accepted ? 5.0 : 1.0, std::max(0.2, f));
+    double hn = std::min(c->dp_hmax, std::max(c->dp_hmin, h * f));
+    return std::min(hn, c->dp_t_end - c->dp_t);
+}
+
+}  // namespace
+
+nrs_status nrs_dp_start(nrs_ctx *ctx, double t0, double t_end, double h0, double rtol, double atol,
+                        double h_min, double h_max)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return NRS_EINVAL;
+    if (!(t_end > t0) || !(h0 > 0.0) || !(rtol > 0.0) || !(atol >= 0.0) || !(h_min > 0.0) ||
+        !(h_max >= h_min) || c->graph_mode)
+        return fail(c, NRS_EINVAL, "nrs_dp_start: bad arguments (or a context in graph mode)");
+    if (!c->d_dp_K) {
+        if (cudaMalloc(&c->d_dp_K, sizeof(double) * 7 * 12 * c->nbodies) != cudaSuccess ||
+            cudaMalloc(&c->d_dp_err, sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, NRS_ENOMEM, "Dormand-Prince workspace allocation failed");
+        }
+    }
+    // Y_n = the context's state
+    CK(cudaMemcpyAsync(c->d_x0_save, c->d_x0, sizeof(double) * 3 * c->nbodies,
+                       cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_B_save, c->d_B, sizeof(double) * 9 * c->nbodies,
+                       cudaMemcpyDeviceToDevice, c->stream));
+    c->dp_active = true;
+    c->dp_t = t0;
+    c->dp_t_end = t_end;
+    c->dp_rtol = rtol;
+    c->dp_atol = atol;
+    c->dp_hmin = h_min;
+    c->dp_hmax = h_max;
+    c->dp_h = std::min(std::min(h0, h_max), t_end - t0);
+    c->dp_stage = 0;
+    c->dp_accepted = c->dp_rejected = c->dp_last_accepted = c->dp_done = 0;
+    c->dp_err = 0.0;
+    return NRS_OK;
+}
+
+nrs_status nrs_dp_next_time(const nrs_ctx *ctx, double *t_stage)
+{
+    const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+    if (!c || !t_stage || !c->dp_active) return NRS_EINVAL;
+    *t_stage = c->dp_t + nrs::dp_node(c->dp_stage) * c->dp_h;
+    return NRS_OK;
+}
+
+nrs_status nrs_dp_info_get(const nrs_ctx *ctx, nrs_dp_info *info)
+{
+    const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+    if (!c || !info) return NRS_EINVAL;
+    dp_fill(c, info);
+    return NRS_OK;
+}
+
+nrs_status nrs_dp_stage(nrs_ctx *ctx, const nrs_shapes *s, double *sol, nrs_dp_info *info)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !s || !s->xi || !s->Xiw || !s->xidot) return fail(c, NRS_EINVAL, "nrs_dp_stage: null argument");
+    if (!c->dp_active || c->dp_done) return fail(c, NRS_EINVAL, "nrs_dp_stage: no integration in progress");
+    const int i = c->dp_stage;
+    if (i >= 1) nrs::launch_dp_combine(*c, i, c->dp_h);  // the stage's state
+    bool need_factor = false;
+    nrs_status st = prepare_stage(c, s, &need_factor);
+    if (st != NRS_OK) return st;
+    double *out = c->d_sol + (int64_t)(i & 1) * c->lda;
+    const double *prev = c->have_sol ? c->d_sol + (int64_t)(1 - (i & 1)) * c->lda : nullptr;
+    const double *x0 = (c->warm_start && prev) ? prev : nullptr;
+    int inner = 0, retried = 0;
+    st = solve_stage(c, out, x0, need_factor, nullptr, &inner, &retried);
+    if (st != NRS_OK) return st;
+    c->last_inner = inner;
+    c->have_sol = true;
+    if (sol) CK(cudaMemcpyAsync(sol, out, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+    nrs::launch_dp_rates(*c, i, out);
+    CK(cudaGetLastError());
+    if (i < 6) {
+        c->dp_stage = i + 1;
+        dp_fill(c, info);
+        return NRS_OK;
+    }
+    // all seven stages: error estimate, accept or reject, next step size
+    nrs::launch_dp_error(*c, c->dp_h, c->dp_rtol, c->dp_atol, c->d_dp_err);
+    double err = 0.0;
+    CK(cudaMemcpyAsync(&err, c->d_dp_err, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->dp_err = err;
+    const bool ok = std::isfinite(err) && err <= 1.0;
+    const int64_t nb = c->nbodies;
+    if (ok) {
+        // Y_n+1 = the last stage's state (first same as last: its rates are K_0 of the next step)
+        c->dp_t += c->dp_h;
+        CK(cudaMemcpyAsync(c->d_x0_save, c->d_x0, sizeof(double) * 3 * nb, cudaMemcpyDeviceToDevice,
+                           c->stream));
+        CK(cudaMemcpyAsync(c->d_B_save, c->d_B, sizeof(double) * 9 * nb, cudaMemcpyDeviceToDevice,
+                           c->stream));
+        CK(cudaMemcpyAsync(c->d_dp_K, c->d_dp_K + 6 * 12 * nb, sizeof(double) * 12 * nb,
+                           cudaMemcpyDeviceToDevice, c->stream));
+        c->dp_accepted += 1;
+        c->dp_last_accepted = 1;
+        if (c->dp_t >= c->dp_t_end * (1.0 - 1e-14) - 1e-300) c->dp_done = 1;
+    } else {
+        CK(cudaMemcpyAsync(c->d_x0, c->d_x0_save, sizeof(double) * 3 * nb, cudaMemcpyDeviceToDevice,
+                           c->stream));
+        CK(cudaMemcpyAsync(c->d_B, c->d_B_save, sizeof(double) * 9 * nb, cudaMemcpyDeviceToDevice,
+                           c->stream));
+        c->dp_rejected += 1;
+        c->dp_last_accepted = 0;
+    }
+    const double h_old = c->dp_h;
+    if (!c->dp_done) {
+        c->dp_h = dp_next_h(c, h_old, err, ok);
+        if (!ok && h_old <= c->dp_hmin * (1.0 + 1e-12)) {
+            dp_fill(c, info);
+            return fail(c, NRS_ENOCONV, "nrs_dp_stage: error above tolerance at the smallest step");
+        }
+    }
+    c->dp_stage = 1;
+    dp_fill(c, info);
     return NRS_OK;
 }
 

@@ -87,6 +87,12 @@ void launch_velocity(Ctx &c, const D4 *Xw, const D4 *xp, int64_t P, const double
                      double *part, cudaStream_t s);
 void launch_tracer_update(Ctx &c, int stage, double dt, cudaStream_t s);
 
+// ---- Dormand-Prince 5(4) stepping (dp.cu) ----------------------------------
+double dp_node(int stage);
+void launch_dp_rates(Ctx &c, int stage, const double *sol);
+void launch_dp_combine(Ctx &c, int stage, double h);
+void launch_dp_error(Ctx &c, double h, double rtol, double atol, double *err);
+
 // ---- factorisation (lu.cu) -------------------------------------------------
 int run_lu_fp64(Ctx &c, double *A, int64_t lda);
 int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec);
@@ -193,6 +199,14 @@ struct Ctx {
     double *d_tr_part = nullptr;
     double *d_vel_part = nullptr;
     size_t vel_part_doubles = 0;
+
+    // adaptive Dormand-Prince integration (nrs_dp_*): the accepted state Y_n
+    // lives in d_x0_save / d_B_save, the stage rates K in d_dp_K [7][nbodies][12]
+    bool dp_active = false;
+    int dp_stage = 0, dp_accepted = 0, dp_rejected = 0, dp_last_accepted = 0, dp_done = 0;
+    double dp_t = 0, dp_t_end = 0, dp_h = 0, dp_rtol = 0, dp_atol = 0, dp_hmin = 0, dp_hmax = 0;
+    double dp_err = 0;
+    double *d_dp_K = nullptr, *d_dp_err = nullptr;
 
     // nearest neighbours and segments
     int32_t *d_nn = nullptr, *d_seg_ptr = nullptr, *d_perm = nullptr, *d_cursor = nullptr;

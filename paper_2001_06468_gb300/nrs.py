@@ -37,7 +37,8 @@ FREE, PRESCRIBED, STATIC = 0, 1, 2
 EXPORTS = ["nrs_create", "nrs_destroy", "nrs_last_error", "nrs_sizes", "nrs_set_state",
            "nrs_get_state", "nrs_set_external", "nrs_kinematics", "nrs_nearest_build",
            "nrs_assemble", "nrs_factor", "nrs_solve", "nrs_step", "nrs_sync", "nrs_counters",
-           "nrs_velocity", "nrs_set_tracers", "nrs_get_tracers",
+           "nrs_velocity", "nrs_set_tracers", "nrs_get_tracers", "nrs_dp_start",
+           "nrs_dp_next_time", "nrs_dp_stage", "nrs_dp_info_get",
            "nrs_set_timing",
            "nrs_get_timing", "nrs_get_trace", "nrs_rank64_update", "nrs_nearest_build_static",
            "nrs_mlp_set_params", "nrs_mlp_get_params", "nrs_mlp_config", "nrs_mlp_eval",
@@ -96,6 +97,16 @@ class StepReport(ctypes.Structure):
                 ("mlp_rel_err", ctypes.c_double), ("retried", ctypes.c_int32 * 2)]
 
 
+class DpInfo(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("h", ctypes.c_double), ("err", ctypes.c_double),
+                ("stage", ctypes.c_int32), ("accepted", ctypes.c_int32),
+                ("rejected", ctypes.c_int32), ("last_accepted", ctypes.c_int32),
+                ("done", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Shapes(ctypes.Structure):
     _fields_ = [("xi", ctypes.c_void_p), ("Xiw", ctypes.c_void_p), ("xidot", ctypes.c_void_p)]
 
@@ -122,6 +133,10 @@ _sig = {
     "nrs_velocity": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
     "nrs_set_tracers": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
     "nrs_get_tracers": (ctypes.c_int, [_P, _P]),
+    "nrs_dp_start": (ctypes.c_int, [_P] + [ctypes.c_double] * 7),
+    "nrs_dp_next_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "nrs_dp_stage": (ctypes.c_int, [_P, ctypes.POINTER(Shapes), _P, ctypes.POINTER(DpInfo)]),
+    "nrs_dp_info_get": (ctypes.c_int, [_P, ctypes.POINTER(DpInfo)]),
     "nrs_set_timing": (ctypes.c_int, [_P, ctypes.c_int32]),
     "nrs_rank64_update": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P,
                                          ctypes.c_int32]),
@@ -350,6 +365,39 @@ class Context:
         out = np.empty((getattr(self, "n_tracers", 0), 4), dtype=np.float64)
         self._check(_lib.nrs_get_tracers(self._h, out.ctypes.data if len(out) else None))
         return out
+
+    # -- adaptive Dormand-Prince stepping ----------------------------------
+    def dp_start(self, t0, t_end, h0, rtol, atol, h_min=1e-8, h_max=None):
+        self._check(_lib.nrs_dp_start(self._h, float(t0), float(t_end), float(h0), float(rtol),
+                                      float(atol), float(h_min),
+                                      float(h_max if h_max is not None else t_end - t0)))
+
+    def dp_next_time(self) -> float:
+        t = ctypes.c_double()
+        self._check(_lib.nrs_dp_next_time(self._h, ctypes.byref(t)))
+        return t.value
+
+    def dp_stage(self, s: "Shapes", sol: Optional[torch.Tensor] = None):
+        info = DpInfo()
+        self._check(_lib.nrs_dp_stage(self._h, ctypes.byref(s), _ptr(sol), ctypes.byref(info)))
+        return info.as_dict()
+
+    def dp_info(self):
+        info = DpInfo()
+        self._check(_lib.nrs_dp_info_get(self._h, ctypes.byref(info)))
+        return info.as_dict()
+
+    def dp_integrate(self, shapes_at, t0, t_end, h0, rtol, atol, h_min=1e-8, h_max=None,
+                     max_stages=100000):
+        """Integrate from the current state to t_end: ``shapes_at(t)`` returns the
+        device shapes (an nrs.Shapes) at time t.  Returns the final dp_info."""
+        self.dp_start(t0, t_end, h0, rtol, atol, h_min, h_max)
+        info = self.dp_info()
+        for _ in range(max_stages):
+            if info["done"]:
+                break
+            info = self.dp_stage(shapes_at(self.dp_next_time()))
+        return info
 
     def counters(self):
         """{'factorizations', 'solves', 'outer', 'inner', 'retries'} since creation."""
