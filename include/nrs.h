@@ -393,9 +393,16 @@ nrs_status nrs_get_tracers(nrs_ctx *ctx, double *xp);
  *                          global == 0, lab frame for global != 0)
  *   nbodies, n_off, q_off  host offsets as in nrs_problem_desc
  *   nn [Q], seg_ptr [N+1], perm [Q]   device outputs
+ *   status                 device int32 or NULL, caller-owned: receives, in
+ *                          stream order, the call's device status word -- 0,
+ *                          or 4 (non-finite input: those quadrature points get
+ *                          nn < 0 and belong to no segment).  The library
+ *                          cannot report it through its return value without
+ *                          synchronising; read it after the stream work.
  *   stream                 cudaStream_t (NULL = legacy default stream)
  * Returns NRS_EINVAL for sizes above NRS_STATIC_MAX_N / _Q / _BODIES or bad
- * offsets, before any work is enqueued.  The first call on a device looks up
+ * offsets, before any work is enqueued; NRS_ECUDA if a copy or clear of the
+ * scratch or a launch fails.  The first call on a device looks up
  * the scratch's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture.  Every call shares
  * the same scratch, which keeps the last call's contents (each call clears
@@ -404,7 +411,8 @@ nrs_status nrs_get_tracers(nrs_ctx *ctx, double *xp);
  * caller. */
 nrs_status nrs_nearest_build_static(const double *x, const double *Xw, int32_t nbodies,
                                     const int64_t *n_off, const int64_t *q_off, int32_t global,
-                                    int32_t *nn, int32_t *seg_ptr, int32_t *perm, void *stream);
+                                    int32_t *nn, int32_t *seg_ptr, int32_t *perm, int32_t *status,
+                                    void *stream);
 
 /* ---- learned starting guess -------------------------------------------------
  * The paper has no learned component: this is an extension of the refinement

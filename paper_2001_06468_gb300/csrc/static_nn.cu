@@ -92,7 +92,7 @@ __global__ void k_static_tasks(int nbodies, const int64_t *__restrict__ q_off,
 extern "C" nrs_status nrs_nearest_build_static(const double *x, const double *Xw, int32_t nbodies,
                                                const int64_t *n_off, const int64_t *q_off,
                                                int32_t global, int32_t *nn, int32_t *seg_ptr,
-                                               int32_t *perm, void *stream)
+                                               int32_t *perm, int32_t *status, void *stream)
 {
     using namespace nrs;
     if (!x || !Xw || !n_off || !q_off || !nn || !seg_ptr || !perm) return NRS_EINVAL;
@@ -116,9 +116,10 @@ extern "C" nrs_status nrs_nearest_build_static(const double *x, const double *Xw
         cudaMemcpyAsync(s->q_off, q_off, ob, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return NRS_ECUDA;
     // the shared scratch keeps the previous call's contents: clear what must start at zero
-    cudaMemsetAsync(s->status, 0, sizeof(int32_t), st);
-    cudaMemsetAsync(s->cursor, 0, sizeof(int32_t) * (N + 1), st);
-    cudaMemsetAsync(perm, 0, sizeof(int32_t) * Q, st);
+    if (cudaMemsetAsync(s->status, 0, sizeof(int32_t), st) != cudaSuccess ||
+        cudaMemsetAsync(s->cursor, 0, sizeof(int32_t) * (N + 1), st) != cudaSuccess ||
+        cudaMemsetAsync(perm, 0, sizeof(int32_t) * Q, st) != cudaSuccess)
+        return NRS_ECUDA;
     k_static_tasks<<<1, 1, 0, st>>>(nbodies, s->q_off, s->tasks);
     k_nearest<<<(unsigned)ntasks, NN_THREADS, 0, st>>>(s->tasks, s->n_off, nbodies, global ? 1 : 0,
                                                  (const D4 *)x, (const D4 *)Xw, nn, s->status);
@@ -128,5 +129,11 @@ extern "C" nrs_status nrs_nearest_build_static(const double *x, const double *Xw
     k_scatter<<<(unsigned)ceil_div(Q, threads), threads, 0, st>>>(Q, N, nn, s->cursor, perm);
     k_sort_segments<<<(unsigned)ceil_div(N, threads), threads, 0, st>>>(N, seg_ptr, perm);
     if (cudaGetLastError() != cudaSuccess) return NRS_ECUDA;
+    // the device status word (ST_NONFINITE: a non-finite coordinate; those
+    // quadrature points have nn < 0 and belong to no segment) to the caller's
+    // word, in stream order, before a later call clears the shared one
+    if (status &&
+        cudaMemcpyAsync(status, s->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return NRS_ECUDA;
     return NRS_OK;
 }

@@ -141,7 +141,7 @@ _sig = {
     "nrs_rank64_update": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P,
                                          ctypes.c_int32]),
     "nrs_nearest_build_static": (ctypes.c_int, [_P, _P, ctypes.c_int32, _I64P, _I64P, ctypes.c_int32,
-                                                _P, _P, _P, _P]),
+                                                _P, _P, _P, _P, _P]),
     "nrs_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), _I64P, _I64P]),
     "nrs_get_trace": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_double),
@@ -645,27 +645,43 @@ def batch_plan(cost, chains: int):
 
 def nearest_build_static(x: torch.Tensor, Xw: torch.Tensor, n_off, q_off, global_: bool = False,
                          nn: Optional[torch.Tensor] = None, seg_ptr: Optional[torch.Tensor] = None,
-                         perm: Optional[torch.Tensor] = None,
-                         stream: Optional[torch.cuda.Stream] = None):
+                         perm: Optional[torch.Tensor] = None, status: Optional[torch.Tensor] = None,
+                         stream: Optional[torch.cuda.Stream] = None, check: bool = True):
     """nrs_nearest_build_static: the nearest-neighbour map and segments with
     no device allocation inside the library (the outputs are the caller's;
-    pass preallocated tensors to allocate nothing at all).  Returns
-    (nn, seg_ptr, perm)."""
+    pass preallocated tensors, status included, to allocate nothing at all).
+    The tensors are checked against the offsets and must live on the current
+    device (the one the library uses) before anything is launched.  With
+    ``check``, the stream is synchronised and a non-finite input raises
+    NRS_ENONFINITE.  Returns (nn, seg_ptr, perm)."""
     n_off = np.ascontiguousarray(n_off, dtype=np.int64)
     q_off = np.ascontiguousarray(q_off, dtype=np.int64)
     N, Q = int(n_off[-1]), int(q_off[-1])
-    dev = x.device
+    dev = torch.device("cuda", torch.cuda.current_device())
     nn = nn if nn is not None else torch.empty(Q, dtype=torch.int32, device=dev)
     seg_ptr = seg_ptr if seg_ptr is not None else torch.empty(N + 1, dtype=torch.int32, device=dev)
     perm = perm if perm is not None else torch.empty(Q, dtype=torch.int32, device=dev)
+    status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=dev)
+    if tuple(x.shape) != (N, 4) or tuple(Xw.shape) != (Q, 4):
+        raise ValueError(f"x must be ({N}, 4) and Xw ({Q}, 4), got {tuple(x.shape)}, {tuple(Xw.shape)}")
+    if nn.numel() < Q or perm.numel() < Q or seg_ptr.numel() < N + 1 or status.numel() < 1:
+        raise ValueError("nn and perm need Q entries, seg_ptr N + 1, status 1")
+    for t in (x, Xw, nn, seg_ptr, perm, status):
+        if t.device != dev:
+            raise ValueError(f"every tensor must be on the current device {dev}, got {t.device}")
     st = stream or torch.cuda.current_stream()
     rc = _lib.nrs_nearest_build_static(_ptr(x, torch.float64), _ptr(Xw, torch.float64),
                                        len(n_off) - 1, _np_ptr(n_off, ctypes.c_int64),
                                        _np_ptr(q_off, ctypes.c_int64), int(bool(global_)),
                                        _ptr(nn, torch.int32), _ptr(seg_ptr, torch.int32),
-                                       _ptr(perm, torch.int32), ctypes.c_void_p(st.cuda_stream))
+                                       _ptr(perm, torch.int32), _ptr(status, torch.int32),
+                                       ctypes.c_void_p(st.cuda_stream))
     if rc != NRS_OK:
         raise NrsError(rc, "nrs_nearest_build_static failed")
+    if check:
+        st.synchronize()
+        if int(status[0].item()) & 4:
+            raise NrsError(NRS_ENONFINITE, "nrs_nearest_build_static: non-finite coordinates")
     return nn, seg_ptr, perm
 
 
