@@ -139,7 +139,7 @@ void free_all(Ctx *c)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *tr[] = {c->d_tr, c->d_tr_save, c->d_tr_u, c->d_tr_part, c->d_vel_part, c->d_dp_K,
-                  c->d_dp_err};
+                  c->d_dp_err, c->d_mblk_keep, c->d_nblk_keep};
     for (void *p : tr)
         if (p) cudaFree(p);
     void *mlp[] = {c->d_mlp_params, c->d_mlp_m,  c->d_mlp_v,     c->d_mlp_g,    c->d_mlp_x,
@@ -226,7 +226,8 @@ nrs_status do_factor(Ctx *c, int prec)
 
 // write_lo: also write the FP32 copy (which a Gauss-Jordan factor replaces by
 // its inverse: writing it destroys that factor).
-nrs_status do_segments_and_assemble(Ctx *c, const D4 *x_lab, const D4 *Xw_lab, bool write_lo = true)
+nrs_status do_segments_and_assemble(Ctx *c, const D4 *x_lab, const D4 *Xw_lab, bool write_lo = true,
+                                    bool from_state = false)
 {
     nrs::launch_gather(*c, Xw_lab, c->d_seg_ptr, c->d_perm);
     float *a32 = (c->factor_prec == NRS_FP64 || !write_lo) ? nullptr : c->d_A32;
@@ -239,12 +240,12 @@ nrs_status do_segments_and_assemble(Ctx *c, const D4 *x_lab, const D4 *Xw_lab, b
         nrs::launch_assemble32(*c, x_lab, a32, c->lda);
         CK(cudaEventRecord(c->ev_asm, c->stream));
         CK(cudaStreamWaitEvent(c->stream3, c->ev_asm, 0));
-        nrs::launch_assemble(*c, x_lab, c->d_A64, nullptr, c->lda, c->stream3);
+        nrs::launch_assemble(*c, x_lab, c->d_A64, nullptr, c->lda, c->stream3, from_state);
         CK(cudaEventRecord(c->ev_asm_done, c->stream3));
         c->asm_pending = true;
     } else {
         // one FP64 pass; with an FP32 copy, that copy is the rounded FP64 entries
-        nrs::launch_assemble(*c, x_lab, c->d_A64, a32, c->lda);
+        nrs::launch_assemble(*c, x_lab, c->d_A64, a32, c->lda, nullptr, from_state);
     }
     // the border rows and columns: disjoint from the block the side stream writes
     nrs::launch_border(*c, x_lab, c->d_A64, a32, c->lda);
@@ -339,7 +340,7 @@ nrs_status enqueue_step(Ctx *c, const nrs_shapes *s0, const nrs_shapes *sh, doub
             launch_nearest(*c, (const D4 *)s->xi, (const D4 *)s->Xiw, c->d_nn, true);
             launch_segments(*c, c->d_nn, c->d_seg_ptr, c->d_perm);
         }
-        nrs_status st = do_segments_and_assemble(c, c->d_x, c->d_Xw, true);
+        nrs_status st = do_segments_and_assemble(c, c->d_x, c->d_Xw, true, true);
         if (st != NRS_OK) return st;
         st = do_factor(c, c->factor_prec);
         if (st != NRS_OK) return st;
@@ -574,8 +575,34 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
         }
     c->n_tasks_all = (int)all.size();
     c->n_tasks_deform = (int)deform.size();
+    // blocks of the assembly made only of static rigid bodies' points (per-body
+    // nearest neighbours: their segments hold only their own quadrature points)
+    std::vector<uint8_t> keep_pt(N, 0);
+    if (!c->nn_global)
+        for (int b = 0; b < d->nbodies; ++b)
+            if (c->kind[b] == NRS_STATIC && c->rigid[b])
+                for (int64_t i = d->n_off[b]; i < d->n_off[b + 1]; ++i) keep_pt[i] = 1;
+    auto blocks = [&](int64_t bs) {
+        std::vector<uint8_t> f((size_t)nrs::ceil_div(N, bs), 0);
+        for (size_t k = 0; k < f.size(); ++k) {
+            uint8_t all_keep = 1;
+            for (int64_t i = (int64_t)k * bs; i < std::min<int64_t>(N, (int64_t)(k + 1) * bs); ++i)
+                all_keep &= keep_pt[i];
+            f[k] = all_keep;
+        }
+        return f;
+    };
+    const std::vector<uint8_t> mblk = blocks(nrs::kAssembleTileM), nblk = blocks(nrs::kAssembleTileN);
+    for (uint8_t v : mblk) c->have_static |= v != 0;
     cudaError_t e = cudaSuccess;
-    e = cudaMalloc(&c->d_tasks_all, sizeof(nrs::NNTask) * std::max<size_t>(1, all.size()));
+    if (c->have_static) {
+        e = cudaMalloc(&c->d_mblk_keep, mblk.size());
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_nblk_keep, nblk.size());
+        if (e == cudaSuccess) e = cudaMemcpy(c->d_mblk_keep, mblk.data(), mblk.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->d_nblk_keep, nblk.data(), nblk.size(), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess)
+        e = cudaMalloc(&c->d_tasks_all, sizeof(nrs::NNTask) * std::max<size_t>(1, all.size()));
     if (e == cudaSuccess)
         e = cudaMalloc(&c->d_tasks_deform, sizeof(nrs::NNTask) * std::max<size_t>(1, deform.size()));
     auto h2d = [&](void *dst, const void *src, size_t bytes) {
@@ -664,6 +691,10 @@ nrs_status nrs_set_state(nrs_ctx *ctx, const double *x0, const double *B)
                        c->stream));
     CK(cudaMemcpyAsync(c->d_B, B, sizeof(double) * 9 * c->nbodies, cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    // static bodies may have moved: the kept blocks of A_s and a recorded step are stale
+    c->static_cache_valid = false;
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
     return NRS_OK;
 }
 
@@ -803,7 +834,7 @@ nrs_status prepare_stage(Ctx *c, const nrs_shapes *s, bool *need_factor)
     *need_factor = !c->reuse_factor || c->factored_prec != c->factor_prec ||
                    c->stages_since_factor >= c->reuse_max_stages ||
                    c->last_inner > c->reuse_max_inner;
-    nrs_status st = do_segments_and_assemble(c, c->d_x, c->d_Xw, *need_factor);
+    nrs_status st = do_segments_and_assemble(c, c->d_x, c->d_Xw, *need_factor, true);
     if (st != NRS_OK) return st;
     if (*need_factor) {
         st = do_factor(c, c->factor_prec);

@@ -26,8 +26,8 @@
 
 namespace nrs {
 
-constexpr int AS_THREADS = 128;
-constexpr int AS_NT = 16;
+constexpr int AS_THREADS = (int)kAssembleTileM;
+constexpr int AS_NT = (int)kAssembleTileN;
 constexpr int AS_CHUNK = 512;
 // the FP64 kernel runs beside the fused factorisation, whose CTA takes about
 // 195 KB of an SM's shared memory: its staging chunk is kept at 8 KB so that
@@ -89,11 +89,15 @@ __global__ void __launch_bounds__(AS_THREADS)
     k_assemble64(int64_t N, const D4 *__restrict__ x, const D4 *__restrict__ Xs,
                  const int32_t *__restrict__ seg_ptr, double eps2, double c,
                  double *__restrict__ A64, float *__restrict__ A32, int64_t lda, int64_t gx,
-                 int64_t tiles)
+                 int64_t tiles, const uint8_t *__restrict__ mblk_keep,
+                 const uint8_t *__restrict__ nblk_keep)
 {
     __shared__ D4 sX[AS64_CHUNK];
     __shared__ int32_t sp[AS_NT + 1];
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    // a tile whose collocation points and segments all belong to static rigid
+    // bodies keeps the entries of the previous assembly (the same values)
+    if (mblk_keep && mblk_keep[tile % gx] && nblk_keep[tile / gx]) continue;
     __syncthreads();  // the previous tile is done with sp and sX
     const int64_t m = (tile % gx) * AS_THREADS + threadIdx.x;
     const int64_t n0 = (tile / gx) * AS_NT;
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(AS_THREADS)
 }
 
 void launch_assemble(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t lda,
-                     cudaStream_t s)
+                     cudaStream_t s, bool from_state)
 {
     const bool side = s != nullptr;
     s = side ? s : c.stream;
@@ -256,9 +260,16 @@ void launch_assemble(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t l
                               : tiles;
     const double coef = 1.0 / (8.0 * kPi * c.mu);
     c.tbeg(PH_ASSEMBLE, s);
+    // the blocks among static rigid bodies do not change from one state to the
+    // next: kept in the context's FP64 matrix once it holds them (only for an
+    // FP64-only pass over the context's own state)
+    const bool keep = from_state && A32 == nullptr && A64 == c.d_A64 && c.have_static &&
+                      c.static_cache_valid;
     k_assemble64<<<(unsigned)grid, AS_THREADS, 0, s>>>(c.N, x_lab, c.d_Xs, c.d_seg_ptr,
                                                        c.eps * c.eps, coef, A64, A32, lda, gx,
-                                                       tiles);
+                                                       tiles, keep ? c.d_mblk_keep : nullptr,
+                                                       keep ? c.d_nblk_keep : nullptr);
+    c.static_cache_valid = from_state && A64 == c.d_A64;
     c.tend(PH_ASSEMBLE, s);
     c.launches += 1;
 }

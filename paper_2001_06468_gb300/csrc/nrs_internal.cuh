@@ -30,6 +30,9 @@ enum : int32_t {
 
 constexpr double kPi = 3.14159265358979323846;
 
+// tile of the FP64 assembly: collocation points x segments
+constexpr int64_t kAssembleTileM = 128, kAssembleTileN = 16;
+
 // Upper bound on spins of any device-side wait (each spin sleeps ~100 ns):
 // a wait that runs out sets ST_TIMEOUT and returns instead of hanging.
 constexpr long long kSpinLimit = 1LL << 24;
@@ -75,8 +78,11 @@ void launch_border(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t lda
 void launch_rk2(Ctx &c, int stage, double dt, const double *sol);
 
 // ---- assembly (assemble.cu) ----------------------------------------------
+// from_state: x_lab and the quadrature points come from the context's state
+// (nrs_step, the Dormand-Prince stages), so the blocks among static rigid
+// bodies may be kept from the previous assembly of that matrix
 void launch_assemble(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t lda,
-                     cudaStream_t s = nullptr);
+                     cudaStream_t s = nullptr, bool from_state = false);
 void launch_assemble32(Ctx &c, const D4 *x_lab, float *A32, int64_t lda);
 // make c.stream wait for the FP64 assembly running on the side stream, if any
 void join_assembly(Ctx &c);
@@ -219,6 +225,10 @@ struct Ctx {
 
     // matrices
     double *d_A64 = nullptr;   // FP64 system (residual)
+    // 128-point collocation blocks and 16-segment blocks made only of static
+    // rigid bodies' points: their A_s entries never change (k_assemble64 keeps them)
+    uint8_t *d_mblk_keep = nullptr, *d_nblk_keep = nullptr;
+    bool have_static = false, static_cache_valid = false;
     float *d_A32 = nullptr;    // FP32 copy, factored in place for the FP32/TF32/BF16 paths
     double *d_LU64 = nullptr;  // FP64 factor (plain path)
     int32_t *d_rowperm = nullptr;  // row order after pivoting: position i holds original row
@@ -358,13 +368,22 @@ __device__ __forceinline__ void dd_two_sum(double a, double b, double &s, double
     e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
 }
 
-// (hi, lo) += a b, the product exact and the sum carried in two doubles
+// (hi, lo) += a b, the product exact and the sum carried in two doubles.  The
+// sum hi + p is split exactly by Dekker's Fast2Sum (3 operations), valid when
+// the first operand is the larger in magnitude: the operands are ordered by an
+// integer compare of their absolute bit patterns (monotone in |x| for finite
+// doubles), which runs on the integer pipe; 7 FP64 operations in all where
+// TwoSum needs 10.
 __device__ __forceinline__ void dd_fma(double a, double b, double &hi, double &lo)
 {
     const double p = __dmul_rn(a, b);
     const double pe = __fma_rn(a, b, -p);
-    double s, se;
-    dd_two_sum(hi, p, s, se);
+    const unsigned long long mh = (unsigned long long)__double_as_longlong(hi) & 0x7fffffffffffffffULL;
+    const unsigned long long mp = (unsigned long long)__double_as_longlong(p) & 0x7fffffffffffffffULL;
+    const bool hb = mh >= mp;
+    const double big = hb ? hi : p, small = hb ? p : hi;
+    const double s = __dadd_rn(big, small);
+    const double se = __dsub_rn(small, __dsub_rn(s, big));
     hi = s;
     lo = __dadd_rn(lo, __dadd_rn(se, pe));
 }
