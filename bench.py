@@ -1120,7 +1120,8 @@ def run_nrs(args):
 def batch_bench(nrs, args, ws, rank):
     """The batch workload.  One rank: 128 ventral-node-like problems at
     reduced sizes (all of them) and the first 8 at the full sizes, one graph
-    per batch step against stepping them one after the other.  Several ranks:
+    per batch step against stepping them one after the other, and all 128 at
+    the full sizes (one timed batch step; --no-batch-full skips it).  Several ranks:
     each steps its own share of the 128 reduced problems (the library's LPT
     plan with one chain per rank, no collective in the data path); the time is
     the slowest rank's."""
@@ -1136,11 +1137,24 @@ def batch_bench(nrs, args, ws, rank):
                 "s_per_batch_step": t, "problem_steps_per_s": len(small) / t,
                 "rank0_problems": len(mine)}
     full = [g.node_config(i) for i in range(8)]
-    return {"workload": "ventral-node batch: cilia rotating on tilted cones, static floor disc, "
-                        "5 free spheres; eps 0.005",
-            "reduced_128": dict(_batch_case(nrs, small, args.prec, 3), recipe=recipe),
-            "full_first8": dict(_batch_case(nrs, full, args.prec, 2),
-                                recipe="the batch recipe at full size, problems 0-7")}
+    out = {"workload": "ventral-node batch: cilia rotating on tilted cones, static floor disc, "
+                       "5 free spheres; eps 0.005",
+           "reduced_128": dict(_batch_case(nrs, small, args.prec, 3), recipe=recipe),
+           "full_first8": dict(_batch_case(nrs, full, args.prec, 2),
+                               recipe="the batch recipe at full size, problems 0-7")}
+    if not args.no_batch_full:
+        import torch
+        torch.cuda.empty_cache()
+        probs = g.node_batch(128)
+        res = _batch_case(nrs, probs, args.prec, 1, tune=False, plan=(8, 38), seq_steps=0)
+        out["full_128"] = dict(res, recipe="all 128 problems at full size (n 5322-15771), plan "
+                                           "K = 8 chains, G = 38 (the autotuner's choice on the "
+                                           "first 8), one timed batch step after the eager first "
+                                           "step and the recorded second",
+                               matrix_bytes=int(sum(12 * pr.n * pr.n for pr in probs)))
+        del probs
+        torch.cuda.empty_cache()
+    return out
 
 
 def profile_step(args):
@@ -1171,6 +1185,8 @@ def main():
     ap.add_argument("--prec", default="tf32", choices=["fp32", "tf32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch workload section")
+    ap.add_argument("--no-batch-full", action="store_true",
+                    help="skip the 128 full-size batch problems (about 180 GB of matrices)")
     ap.add_argument("--no-side", action="store_true",
                     help="skip the other workloads and the plain FP64 comparator")
     ap.add_argument("--batch-full", action="store_true",

@@ -155,3 +155,31 @@ def test_batch_tune_restores_state_and_uses_its_cache(N, tmp_path):
     with pytest.raises(N.NrsError):
         batch.config(len(probs) + 1, 10)
     batch.close()
+
+
+def test_full_size_node_problems_in_a_batch_match_the_oracle(N):
+    # the two smallest full-size ventral-node problems of the 128 (n = 5322
+    # and 5466) and a reduced one, stepped twice as a batch (the second step
+    # replayed from the recorded graph), against the oracle's trajectory
+    probs = [g.node_config(4), g.node_config(106), small_node(0)]
+    assert (probs[0].n, probs[1].n) == (5322, 5466)
+    dt = 0.01
+    batch = N.Batch(probs, factor_prec="tf32")
+    Ys = [g.initial_state(pr) for pr in probs]
+    for c, Y in zip(batch.contexts, Ys):
+        c.set_state(Y["x0"], Y["B"])
+    bufs = [Buffers(N, pr) for pr in probs]
+    sols = [torch.empty(2 * pr.n, dtype=torch.float64, device="cuda") for pr in probs]
+    Yo = list(Ys)
+    for k in range(2):
+        reps = batch.step([b.load(k * dt, dt) for b in bufs], dt, sols=sols, report=True)
+        assert all(r["stages"][s]["status"] == 0 for r in reps for s in (0, 1))
+        for i in range(2):
+            pr = probs[i]
+            Yo[i], stg = O.rk2_step(pr, Yo[i], k * dt, dt, solver=O.solve_lapack,
+                                    return_stages=True)
+            s = sols[i].cpu().numpy()
+            assert _rel(s[:pr.n], stg["sol1"]) <= TOL_SOL, (i, k)
+            assert _rel(s[pr.n:], stg["sol2"]) <= TOL_SOL, (i, k)
+    assert batch.info()["graph_kernels"] > 0
+    batch.close()
