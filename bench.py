@@ -10,8 +10,10 @@ n = 27648 unknowns.  One step = one explicit-midpoint (RK2) step: twice
 (kinematics, nearest neighbours, segments, FP64 assembly of A_s bit-identical
 to the oracle's, rigid-body border, FP32 explicit inverse by blocked
 Gauss-Jordan with split-TF32 tensor-core updates -- refreshed when the
-previous solve needed more than 60 GMRES iterations or after 32 stages --,
-GMRES-based iterative refinement with a double-double residual to the FP64
+previous solve needed more than 40 GMRES iterations or after 32 stages --,
+GMRES-based iterative refinement with an extended-precision residual (every
+product's rounded value summed exactly as a fixed-point integer, the rounding
+errors in FP64) to the FP64
 answer, started from the previous stage's solution) plus the state update.
 Inputs are the seeded synthetic shapes of `synth` (the paper's cited beat
 patterns are not available), resident in HBM before the timed region.
@@ -67,7 +69,7 @@ WORKLOADS_DESC = {
     "swimmer": "single free undulating swimmer, N=800 / Q=8000, eps=0.005, n=2406",
 }
 # the product path's solver settings per workload
-HEADLINE_SOLVER = dict(reuse_factor=True, warm_start=True, reuse_max_inner=60,
+HEADLINE_SOLVER = dict(reuse_factor=True, warm_start=True, reuse_max_inner=40,
                        reuse_max_stages=32)
 # the four-swimmer system has kappa_1 ~ 1e13: its GMRES steps need the longest
 # restart, the factorisation the rounded FP64 entries; a refinement that has
@@ -81,7 +83,7 @@ SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 PAIR_INSTR = 20                  # FP32-pipe instructions per (force, quadrature) pair
 ASM64_OPS_PER_PAIR = 40          # FP64 operations per pair of the bit-exact assembly
-DD_OPS_PER_ENTRY = 7            # FP64 operations per matrix entry of a double-double product
+RES_OPS_PER_ENTRY = 3           # FP64 operations per matrix entry of the extended residual
 TOL = 1e-10
 
 
@@ -273,7 +275,10 @@ def rooflines(ph_ms, ph_spans, n, pairs, peaks, peak_src, sm_mhz, solve_stats, p
       assemble    k_assemble64: 40 FP64 operations per (force, quadrature) pair
       assemble32  k_assemble32: N Q pairs against the FP32 pair peak (20 instructions a pair)
       krylov      k_gmres_ir: (outer + inner) 8 n^2 + (outer + inner + 1) 4 n^2 bytes;
-                  outer x 7 n^2 (double-double residual) + inner x n^2 FP64 operations"""
+                  + 8 n^2 (||A||_inf, once per launch);
+                  outer x 3 n^2 (extended residual: product, its error, the error
+                  sum; the products' sum on the integer pipe) + (inner + 1) x n^2
+                  FP64 operations"""
     P = derived_peaks(peaks, sm_mhz)
 
     def per_launch(ph):
@@ -362,8 +367,8 @@ def rooflines(ph_ms, ph_spans, n, pairs, peaks, peak_src, sm_mhz, solve_stats, p
     if ph_spans.get("krylov") and solve_stats:
         o, i = solve_stats["outer_mean"], solve_stats["inner_mean"]
         t = per_launch("krylov")
-        b = 8.0 * n * n * (o + i) + 4.0 * n * n * (o + i + 1)
-        ops = DD_OPS_PER_ENTRY * n * n * o + n * n * i
+        b = 8.0 * n * n * (o + i + 1) + 4.0 * n * n * (o + i + 1)
+        ops = RES_OPS_PER_ENTRY * n * n * o + n * n * (i + 1)
         recs["krylov"] = {
             "kernel": "k_gmres_ir (persistent GMRES-IR, one cooperative launch per solve)",
             "bound": "hbm", "achieved": b / t / 1e9, "peak": P["hbm_gbs"], "unit": "GB/s",
@@ -1073,11 +1078,11 @@ def run_nrs(args):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64 (bit-exact assembly, double-double residual) + fp32/split-tf32 factor",
+        "dtype": "f64 (bit-exact assembly, extended-precision residual) + fp32/split-tf32 factor",
         "data": "synthetic (seeded channel, head and flagellum shapes)",
         "config": {"workload": WORKLOADS_DESC[HEADLINE], "factor": args.prec + " explicit inverse "
-                   "(blocked Gauss-Jordan), refreshed after >60 GMRES iterations or 32 stages",
-                   "refinement": "GMRES-IR, double-double residual, warm start from the previous "
+                   "(blocked Gauss-Jordan), refreshed after >40 GMRES iterations or 32 stages",
+                   "refinement": "GMRES-IR, extended residual (exact fixed-point product sums), warm start from the previous "
                                  "stage", "rk2_stages_per_step": 2,
                    "l2": "flushed between timed steps (512 MiB write); matrices 9.2 GB > L2",
                    "parallelism": f"replicas x{ws}"},

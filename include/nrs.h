@@ -131,12 +131,13 @@ typedef struct {
                               256-column blocks whose column panel is eliminated in 64-column
                               steps, then one rank-256 tensor-core update of the rest of the
                               matrix (a persistent tcgen05 kernel).  Other values: NRS_EINVAL. */
-    int32_t residual;      /* the refinement's residual b - A x: 0 = double-double (every
-                              product exact, sums carried in two doubles, rounded once at the
-                              end: the residual precision u^2 of three-precision GMRES-IR,
-                              which reaches working accuracy in the solution up to
-                              kappa(A) ~ 1/u); 1 = plain FP64 (the solution is then only
-                              accurate to about kappa(A) u) */
+    int32_t residual;      /* the refinement's residual b - A x: 0 = to about u^2 (every
+                              product's rounded value summed exactly as a fixed-point
+                              integer, the products' rounding errors in FP64, rounded once
+                              at the end; see nrs_residual): the residual precision of
+                              three-precision GMRES-IR, which reaches working accuracy in
+                              the solution up to kappa(A) ~ 1/u; 1 = plain FP64 (the
+                              solution is then only accurate to about kappa(A) u) */
 } nrs_problem_desc;
 
 typedef struct {
@@ -246,14 +247,26 @@ nrs_status nrs_assemble(nrs_ctx *ctx, const double *x, const double *Xw, double 
 nrs_status nrs_factor(nrs_ctx *ctx, int32_t prec, int32_t *info);
 
 /* Solve A x = b (device b, x [n*nrhs], column-major) by GMRES-based iterative
- * refinement (Carson & Higham 2018): residual b - A x in FP64 with the FP64
- * matrix, correction by GMRES preconditioned with the factor, x += d.
+ * refinement (Carson & Higham 2018): residual b - A x with the FP64 matrix
+ * (nrs_residual), correction by GMRES preconditioned with the factor, x += d.
  * x0 (device [n*nrhs] or NULL) is the starting guess, else x0 = LU^{-1} b.
  * report (host, may be NULL; one per right-hand side) synchronises and
  * returns the device status (NRS_ENOCONV when max_outer steps did not reach
  * the tolerance). */
 nrs_status nrs_solve(nrs_ctx *ctx, const double *b, double *x, int32_t nrhs, const double *x0,
                      nrs_solve_report *report);
+
+/* r = b - A x with the context's FP64 matrix (that of the last assembly):
+ * the residual of the refinement's outer step (Carson & Higham 2018).  With
+ * desc.residual = 0 it is accurate to about u^2 ||A||_inf ||x||_inf (u =
+ * 2^-53): each product A_ij x_j is rounded in FP64, the rounded products are
+ * summed EXACTLY as a 192-bit fixed-point integer anchored at a power of two
+ * above ||A||_inf ||x||_inf, the products' rounding errors (one fused
+ * multiply-add each) are summed in FP64, and b minus the two sums is rounded
+ * once.  With desc.residual = 1 it is a plain FP64 product.  b, x, r: device
+ * [n] doubles; r may be b or x.  Asynchronous on the context's stream.
+ * Errors: NRS_EINVAL for a NULL pointer or before the first assembly. */
+nrs_status nrs_residual(nrs_ctx *ctx, const double *b, const double *x, double *r);
 
 /* One explicit-midpoint (RK2) step of dY/dt = F(Y, t) (Sec. 4): stage 1 at
  * the shapes ``s0`` (time t), stage 2 at ``s_half`` (time t + dt/2), each

@@ -93,7 +93,7 @@ nrs_status alloc_all(Ctx *c)
         {(void **)&c->d_scal, sizeof(double) * (16 + 2 * (m + 1))},
         {(void **)&c->d_part, sizeof(double) * 64 * lda},
         {(void **)&c->d_part32, sizeof(double) * 64 * lda},
-        {(void **)&c->d_part_lo, sizeof(double) * 64 * lda},
+        {(void **)&c->d_part_fx, sizeof(unsigned long long) * 3 * 64 * lda},
         {(void **)&c->d_vf, sizeof(float2) * lda},
         {(void **)&c->d_gj2, gj2 ? sizeof(float) * 4 * nrs::gj2_panel_floats(n) : 0},
         {(void **)&c->d_gj2_r, gj2 ? sizeof(float) * 64 * 256 : 0},
@@ -135,7 +135,7 @@ void free_all(Ctx *c)
                     c->d_t32,    c->d_t64,    c->d_flags,  c->d_status,     c->d_gj_dinv,
                     c->d_gj_rt,  c->d_gj_cb,  c->d_dpart,  c->d_bar,        c->d_pg_stats,
                     c->d_step_stats, c->d_Xsh, c->d_Xsl, c->d_xh, c->d_xl, c->d_gj_stage, c->d_gj_sync, c->d_part32,
-                    c->d_part_lo, c->d_vf, c->d_gj2, c->d_gj2_r};
+                    c->d_part_fx, c->d_vf, c->d_gj2, c->d_gj2_r};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *tr[] = {c->d_tr, c->d_tr_save, c->d_tr_u, c->d_tr_part, c->d_vel_part, c->d_dp_K,
@@ -805,6 +805,17 @@ nrs_status nrs_solve(nrs_ctx *ctx, const double *b, double *x, int32_t nrhs, con
         if (st != NRS_OK && worst == NRS_OK) worst = st;
     }
     return worst;
+}
+
+nrs_status nrs_residual(nrs_ctx *ctx, const double *b, const double *x, double *r)
+{
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !b || !x || !r) return fail(c, NRS_EINVAL, "nrs_residual: null argument");
+    if (!c->assembled) return fail(c, NRS_EINVAL, "nrs_residual before an assembly");
+    nrs::join_assembly(*c);
+    nrs::enqueue_residual(*c, x, b, r);
+    CK(cudaGetLastError());
+    return NRS_OK;
 }
 
 namespace {

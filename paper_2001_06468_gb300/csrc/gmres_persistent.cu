@@ -19,9 +19,11 @@
 // the same values, so all CTAs take the same branches without a broadcast.
 // Every reduction has a fixed order: the result is deterministic.
 //
-// The residual b - A x is carried in double-double by default (precision
-// u^2: the three-precision form of Carson & Higham, whose solution reaches
-// working accuracy for kappa(A) up to about 1/u), or in FP64.
+// The residual b - A x is computed to about u^2 by default (the
+// three-precision form of Carson & Higham, whose solution reaches working
+// accuracy for kappa(A) up to about 1/u) -- every product's rounded value
+// summed exactly as an integer, its rounding error in FP64 (fx_add) -- or in
+// FP64.
 //
 // Stopping rule: that of k_outer_check (solve.cu), plus one for very
 // ill-conditioned systems, where an FP64 residual leaves corrections of about
@@ -56,9 +58,9 @@ struct PgArgs {
     double *w;            // n: A v, then the residual
     double *part;         // partial sums of the FP64 products [splits][n]
     double *part32;       // partial sums of the FP32 products [splits][n]
-    double *part_lo;      // low parts of the double-double residual's partial sums [splits][n]
+    unsigned long long *part_fx;  // the exact residual's integer partial sums [splits][3][n]
     float2 *vf;           // input of the next preconditioner product as float pairs [n]
-    int dd;               // residual b - A x in double-double (1) or FP64 (0)
+    int dd;               // residual b - A x to u^2 (1: exact products, mv64fx_partial) or FP64 (0)
     double *dpart;        // reduction partials [3][PG_MAXCH][m+2]
     int32_t *bar;         // grid barrier: [0] arrivals since the launch ([1] unused)
     int32_t *status;
@@ -163,56 +165,87 @@ __device__ void mv64_partial(const PgArgs &a, const double *v, double scale, dou
     }
 }
 
-// The residual's product in double-double: (part, part_lo)[s][i] = sum_{j in
-// split s} A[i, j] v[j], every product exact and every sum carried in two
-// doubles (dd_fma), the tile layout of mv64_partial; the 8 column groups are
-// added in double-double in a fixed order.
-__device__ void mv64dd_partial(const PgArgs &a, const double *v, double *sm, double *sm_lo)
+// The residual's product, exact: fx[s][.][i] = sum_{j in split s} fl(A[i, j]
+// v[j]) as a 192-bit integer (fx_add, anchor c) and part[s][i] = the FP64 sum
+// of the products' rounding errors; the tile layout of mv64_partial.  The 8
+// column groups are merged by a tree in shared memory (groups g + h into g,
+// h = 4, 2, 1): exact for the integers, a fixed order for the error sums.
+__device__ void mv64fx_partial(const PgArgs &a, const double *v, int c, double *sm)
 {
     const int64_t tiles = (int64_t)a.rc64 * a.s64;
     const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    unsigned long long *su = reinterpret_cast<unsigned long long *>(sm);
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         const int64_t rc = t % a.rc64, s = t / a.rc64;
         const int64_t i = rc * MV64_ROWS + 2 * lane;
         const int64_t j0 = s * a.cps64, j1 = min(a.n, j0 + a.cps64);
-        double h0 = 0.0, l0 = 0.0, h1 = 0.0, l1 = 0.0;
+        Fx192 s0{0, 0, 0}, s1{0, 0, 0};
+        double e0 = 0.0, e1 = 0.0;
         if (i < a.n) {
             const double *col = a.A + i;
 #pragma unroll 4
             for (int64_t j = j0 + grp; j < j1; j += MV_GROUPS) {
                 const double2 x = __ldg(reinterpret_cast<const double2 *>(col + j * a.lda));
                 const double vj = __ldcg(v + j);
-                dd_fma(x.x, vj, h0, l0);
-                dd_fma(x.y, vj, h1, l1);
+                const double p0 = __dmul_rn(x.x, vj), p1 = __dmul_rn(x.y, vj);
+                e0 = __dadd_rn(e0, __fma_rn(x.x, vj, -p0));
+                e1 = __dadd_rn(e1, __fma_rn(x.y, vj, -p1));
+                fx_add(s0, p0, c);
+                fx_add(s1, p1, c);
             }
         }
-        sm[grp * MV64_ROWS + 2 * lane] = h0;
-        sm[grp * MV64_ROWS + 2 * lane + 1] = h1;
-        sm_lo[grp * MV64_ROWS + 2 * lane] = l0;
-        sm_lo[grp * MV64_ROWS + 2 * lane + 1] = l1;
-        __syncthreads();
-        if (threadIdx.x < MV64_ROWS) {
-            const int64_t r = rc * MV64_ROWS + threadIdx.x;
-            double hi = 0.0, lo = 0.0;
-#pragma unroll
-            for (int g = 0; g < MV_GROUPS; ++g)
-                dd_add(hi, lo, sm[g * MV64_ROWS + threadIdx.x], sm_lo[g * MV64_ROWS + threadIdx.x]);
-            if (r < a.n) {
-                a.part[s * a.n + r] = hi;
-                a.part_lo[s * a.n + r] = lo;
+        // tree over the column groups: slot k holds rows 2l, 2l+1 of group
+        // h + k as 8 values (3 + 3 integer words, 2 error sums)
+        for (int h = MV_GROUPS / 2; h >= 1; h >>= 1) {
+            unsigned long long *q = su + ((grp - h) * 32 + lane) * 8;
+            if (grp >= h && grp < 2 * h) {
+                q[0] = s0.w0;
+                q[1] = s0.w1;
+                q[2] = s0.w2;
+                q[3] = s1.w0;
+                q[4] = s1.w1;
+                q[5] = s1.w2;
+                q[6] = (unsigned long long)__double_as_longlong(e0);
+                q[7] = (unsigned long long)__double_as_longlong(e1);
+            }
+            __syncthreads();
+            if (grp < h) {
+                const unsigned long long *r = su + (grp * 32 + lane) * 8;
+                fx_merge(s0, Fx192{r[0], r[1], r[2]});
+                fx_merge(s1, Fx192{r[3], r[4], r[5]});
+                e0 = __dadd_rn(e0, __longlong_as_double((long long)r[6]));
+                e1 = __dadd_rn(e1, __longlong_as_double((long long)r[7]));
+            }
+            __syncthreads();
+        }
+        if (grp == 0 && i < a.n) {
+            unsigned long long *f = a.part_fx + s * 3 * a.n;
+            f[i] = s0.w0;
+            f[a.n + i] = s0.w1;
+            f[2 * a.n + i] = s0.w2;
+            a.part[s * a.n + i] = e0;
+            if (i + 1 < a.n) {
+                f[i + 1] = s1.w0;
+                f[a.n + i + 1] = s1.w1;
+                f[2 * a.n + i + 1] = s1.w2;
+                a.part[s * a.n + i + 1] = e1;
             }
         }
-        __syncthreads();
     }
 }
 
-// b[e] - sum over the column splits of (part + part_lo)[.][e], in double-double
-__device__ __forceinline__ double residual_dd_at(const PgArgs &a, double be, int64_t e)
+// b[e] - sum over the column splits of the exact products and their error
+// sums (mv64fx_partial), rounded once
+__device__ __forceinline__ double residual_fx_at(const PgArgs &a, double be, int64_t e, int c)
 {
-    double hi = be, lo = 0.0;
-    for (int k = 0; k < a.s64; ++k)
-        dd_add(hi, lo, -__ldcg(a.part + k * a.n + e), -__ldcg(a.part_lo + k * a.n + e));
-    return __dadd_rn(hi, lo);
+    Fx192 S{0, 0, 0};
+    double es = 0.0;
+    for (int k = 0; k < a.s64; ++k) {
+        const unsigned long long *f = a.part_fx + (int64_t)k * 3 * a.n;
+        fx_merge(S, Fx192{__ldcg(f + e), __ldcg(f + a.n + e), __ldcg(f + 2 * a.n + e)});
+        es = __dadd_rn(es, __ldcg(a.part + k * a.n + e));
+    }
+    return fx_residual(be, S, c, es);
 }
 
 // part32[s][i] = sum_{j in split s} M[i, j] v[j] with the FP32 entries of M
@@ -359,10 +392,9 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
     __shared__ double scs[PG_MAXM], ssn[PG_MAXM], sg[PG_MAXM + 1], sy[PG_MAXM];
     __shared__ double sh1[PG_MAXM + 1], sh2[PG_MAXM + 1];
     __shared__ double sred[PG_THREADS / 32];
-    // product tiles: [0, 512) the FP64 sums, [512, 1024) the low parts of the
-    // double-double residual; the preconditioner's tile takes all 1024
+    // product tiles: [0, 512) the FP64 sums; the preconditioner's tile and
+    // the exact residual's group tree take all 1024
     __shared__ __align__(16) double smv[2 * MV_GROUPS * MV64_ROWS];
-    double *smv_lo = smv + MV_GROUPS * MV64_ROWS;
     __shared__ int s_ok;
     int32_t tgt = 0;  // grid barrier target (thread 0)
     static_assert(MV_GROUPS * MV32_ROWS <= 2 * MV_GROUPS * MV64_ROWS, "shared product tile");
@@ -388,10 +420,31 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
     int outer = 0, inner_total = 0, converged = 0;
     double dn = 0.0, xn = 0.0, dn_prev = 0.0, normA = -1.0;
     bool stagnant = false;
+    if (a.dd) {
+        // the exact residual's anchor needs ||A||_inf and ||x||_inf up front
+        mv64_partial<true>(a, nullptr, 1.0, smv);
+        if (!grid_sync(a, &s_ok, tgt)) return;
+        double amax = 0.0, xmax = 0.0;
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
+            amax = fmax(amax, sum_parts(a, a.s64, e));
+            xmax = fmax(xmax, fabs(__ldcg(a.x + e)));
+        }
+        amax = block_max_all(amax, sred);
+        xmax = block_max_all(xmax, sred);
+        if (owner && threadIdx.x == 0) {
+            dp1[2] = amax;
+            dp0[1] = xmax;
+        }
+        if (!grid_sync(a, &s_ok, tgt)) return;
+        normA = chunk_total(a, 1, 2, true, sred);
+        xn = chunk_total(a, 0, 1, true, sred);
+    }
     for (outer = 0; outer < a.max_outer; ++outer) {
-        // r = b - A x (double-double, or FP64), with ||r||_inf and ||b||_inf per chunk
+        // r = b - A x (exact products and error sums, or FP64), with ||r||_inf
+        // and ||b||_inf per chunk; xn is ||x||_inf of this x
+        const int fxc = a.dd ? fx_anchor(normA, xn) : 0;
         if (a.dd)
-            mv64dd_partial(a, a.x, smv, smv_lo);
+            mv64fx_partial(a, a.x, fxc, smv);
         else
             mv64_partial<false>(a, a.x, 1.0, smv);
         if (!grid_sync(a, &s_ok, tgt)) return;
@@ -399,7 +452,8 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
             double rmax = 0.0, bmax = 0.0;
             for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
                 const double be = __ldg(a.b + e);
-                const double re = a.dd ? residual_dd_at(a, be, e) : be - sum_parts(a, a.s64, e);
+                const double re =
+                    a.dd ? residual_fx_at(a, be, e, fxc) : be - sum_parts(a, a.s64, e);
                 a.w[e] = re;
                 a.vf[e] = df_split(re);
                 rmax = fmax(rmax, fabs(re));
@@ -418,7 +472,8 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
             // The corrections stopped shrinking.  If x already solves a nearby
             // system to working precision (normwise backward error
             // ||r|| / (||A|| ||x|| + ||b||) <= 1e-15), further steps only
-            // chase rounding noise: stop.  ||A||_inf is computed once, here.
+            // chase rounding noise: stop.  ||A||_inf is computed once (at the start
+            // when the residual is exact).
             if (normA < 0.0) {
                 mv64_partial<true>(a, nullptr, 1.0, smv);
                 if (!grid_sync(a, &s_ok, tgt)) return;
@@ -664,7 +719,7 @@ cudaError_t launch_gmres_persistent(Ctx &c, const double *b, double *x, bool col
     a.w = c.d_w;
     a.part = c.d_part;
     a.part32 = c.d_part32;
-    a.part_lo = c.d_part_lo;
+    a.part_fx = c.d_part_fx;
     a.vf = c.d_vf;
     a.dd = c.residual_dd;
     a.dpart = c.d_dpart;

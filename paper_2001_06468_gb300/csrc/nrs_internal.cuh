@@ -131,6 +131,8 @@ int pg_max_coresident(const Ctx &c);  // CTAs of the solve kernel that fit on th
 cudaError_t launch_gmres_persistent(Ctx &c, const double *b, double *x, bool cold, double *stats);
 // out3[0..2] (device) = ||b - A x||_inf, ||A||_inf, ||b||_inf
 void enqueue_backward_error(Ctx &c, const double *b, const double *x, double *out3);
+// r = b - A x with the FP64 matrix, in the context's residual precision
+void enqueue_residual(Ctx &c, const double *x, const double *b, double *r);
 // One RK2 step enqueued with no host synchronisation (api.cu); valid when
 // graph_capable(c).  stats: 8 doubles per stage (outer, inner, converged,
 // ||d||, ||x||, then with berr ||b - A x||, ||A||, ||b||).
@@ -306,7 +308,7 @@ struct Ctx {
     double *d_scal = nullptr;  // scalars (norms, flags as doubles)
     double *d_part = nullptr;  // partial sums of matrix-vector products
     double *d_part32 = nullptr;  // partial sums of the FP32 products of the persistent solve
-    double *d_part_lo = nullptr; // low parts of the double-double residual's partial sums
+    unsigned long long *d_part_fx = nullptr; // the residual's exact partial sums [splits][3][n]
     float2 *d_vf = nullptr;      // the preconditioner product's input vector as float pairs
     int residual_dd = 1;       // refinement residual b - A x: 1 double-double, 0 FP64
     int splits64 = 1, splits32 = 1;  // column splits of the FP64 / FP32 matrix-vector products
@@ -357,10 +359,9 @@ struct Ctx {
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// ---- double-double arithmetic of the refinement's residual -----------------
-// Error-free transformations: Knuth's TwoSum (s + e = a + b exactly) and the
-// product with one fused multiply-add (p + e = a b exactly).  Every step is
-// an explicitly rounded intrinsic, so the compiler cannot fuse or reorder.
+// ---- error-free sum --------------------------------------------------------
+// Knuth's TwoSum: s + e = a + b exactly.  Every step is an explicitly rounded
+// intrinsic, so the compiler cannot fuse or reorder.
 __device__ __forceinline__ void dd_two_sum(double a, double b, double &s, double &e)
 {
     s = __dadd_rn(a, b);
@@ -368,24 +369,120 @@ __device__ __forceinline__ void dd_two_sum(double a, double b, double &s, double
     e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
 }
 
-// (hi, lo) += a b, the product exact and the sum carried in two doubles.  The
-// sum hi + p is split exactly by Dekker's Fast2Sum (3 operations), valid when
-// the first operand is the larger in magnitude: the operands are ordered by an
-// integer compare of their absolute bit patterns (monotone in |x| for finite
-// doubles), which runs on the integer pipe; 7 FP64 operations in all where
-// TwoSum needs 10.
-__device__ __forceinline__ void dd_fma(double a, double b, double &hi, double &lo)
+// ---- exact fixed-point sums of FP64 products (the refinement's residual) ----
+// The residual b - A x is needed to about u^2 of |A| |x| (the extended
+// residual precision of three-precision GMRES-IR).  Double-double sums cost 7
+// FP64 operations per matrix entry, and GB300 issues FP64 at about two lanes
+// per SM per clock, so they bound the product far above its memory time.
+// Here each product p = A_ij x_j is rounded in FP64 (one multiply), its
+// rounding error e = A_ij x_j - p taken exactly by one fused multiply-add, and
+// the errors summed in FP64 (one add): 3 FP64 operations.  The rounded
+// products themselves are added EXACTLY on the integer pipe to a 192-bit
+// two's-complement integer S standing for S 2^L.  The anchor L comes from a
+// bound on every partial sum, |sum_j A_ij x_j| <= ||A||_inf ||x||_inf < 2^E:
+// with L = E - 189 the sums never overflow (|S| < 2^191), and a product loses
+// less than 2^L (about 2^-187 ||A|| ||x||) when its bits below 2^L are
+// dropped.  Integer addition is associative, so splitting the sum over
+// threads, column groups and column splits changes nothing: the product's
+// integer part is exact and deterministic whatever the order.  A non-finite
+// product makes its FP64 error term NaN, so it still reaches the residual.
+struct Fx192 {
+    unsigned long long w0, w1, w2;  // little-endian 64-bit words
+};
+
+// c = 1075 + L for sums bounded by an * xn (an, xn >= 0).  When the bound is
+// zero every product is zero; when it is not finite, products overflow to
+// non-finite error terms; any anchor serves then (E = 0).
+__device__ __forceinline__ int fx_anchor(double an, double xn)
 {
-    const double p = __dmul_rn(a, b);
-    const double pe = __fma_rn(a, b, -p);
-    const unsigned long long mh = (unsigned long long)__double_as_longlong(hi) & 0x7fffffffffffffffULL;
-    const unsigned long long mp = (unsigned long long)__double_as_longlong(p) & 0x7fffffffffffffffULL;
-    const bool hb = mh >= mp;
-    const double big = hb ? hi : p, small = hb ? p : hi;
-    const double s = __dadd_rn(big, small);
-    const double se = __dsub_rn(small, __dsub_rn(s, big));
+    const bool ok = an > 0.0 && xn > 0.0 && isfinite(an) && isfinite(xn);
+    const int E = ok ? ilogb(an) + ilogb(xn) + 2 : 0;
+    return 1075 + E - 189;
+}
+
+// S += p 2^-L exactly, truncated toward zero below bit 0 (c = 1075 + L).  The
+// double is m 2^(e - 1075) with m its 53-bit integer significand (no implicit
+// bit for subnormals, e raised to 1), so m lands at bit s = e - c of S; the
+// magnitude is placed in three words and added, or subtracted as its one's
+// complement with a carry in, by one chain of extended-precision adds.
+__device__ __forceinline__ void fx_add(Fx192 &a, double p, int c)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(p);
+    const int ex = (int)(bits >> 52) & 0x7ff;
+    unsigned long long m = (bits & 0xfffffffffffffULL) | ((unsigned long long)(ex != 0) << 52);
+    int s = max(ex, 1) - c;
+    m >>= min(max(-s, 0), 63);  // the bits below 2^L
+    s = max(s, 0);
+    const int wi = s >> 6, b = s & 63;
+    const unsigned long long lo = m << b, hi = (m >> 1) >> (63 - b);
+    const unsigned long long neg = (unsigned long long)((long long)bits >> 63);
+    const unsigned long long x0 = (wi == 0 ? lo : 0ULL) ^ neg;
+    const unsigned long long x1 = (wi == 0 ? hi : (wi == 1 ? lo : 0ULL)) ^ neg;
+    const unsigned long long x2 = (wi == 1 ? hi : (wi == 2 ? lo : 0ULL)) ^ neg;
+    // carry in = 1 for negative p: neg + neg carries out exactly when neg != 0
+    asm("{\n\t.reg .u64 t;\n\t"
+        "add.cc.u64 t, %3, %3;\n\t"
+        "addc.cc.u64 %0, %0, %4;\n\t"
+        "addc.cc.u64 %1, %1, %5;\n\t"
+        "addc.u64 %2, %2, %6;\n\t}"
+        : "+l"(a.w0), "+l"(a.w1), "+l"(a.w2)
+        : "l"(neg), "l"(x0), "l"(x1), "l"(x2));
+}
+
+// a += b (exact, modulo 2^192)
+__device__ __forceinline__ void fx_merge(Fx192 &a, const Fx192 &b)
+{
+    asm("add.cc.u64 %0, %0, %3;\n\t"
+        "addc.cc.u64 %1, %1, %4;\n\t"
+        "addc.u64 %2, %2, %5;"
+        : "+l"(a.w0), "+l"(a.w1), "+l"(a.w2)
+        : "l"(b.w0), "l"(b.w1), "l"(b.w2));
+}
+
+// (hi, lo) = S 2^L as an unevaluated sum of two doubles (relative error about
+// 2^-104): the magnitude's six 32-bit limbs, each exact in FP64, scaled and
+// added from the top by TwoSum.
+__device__ __forceinline__ void fx_to_dd(Fx192 a, int c, double &hi, double &lo)
+{
+    const bool negative = (long long)a.w2 < 0;
+    if (negative) {
+        a.w0 = ~a.w0;
+        a.w1 = ~a.w1;
+        a.w2 = ~a.w2;
+        const Fx192 one{1ULL, 0ULL, 0ULL};
+        fx_merge(a, one);
+    }
+    const int L = c - 1075;
+    const unsigned long long w[3] = {a.w0, a.w1, a.w2};
+    hi = 0.0;
+    lo = 0.0;
+#pragma unroll
+    for (int k = 5; k >= 0; --k) {
+        const unsigned int limb = (unsigned int)(w[k >> 1] >> (32 * (k & 1)));
+        const double t = scalbn((double)limb, L + 32 * k);
+        double s, e;
+        dd_two_sum(hi, t, s, e);
+        hi = s;
+        lo = __dadd_rn(lo, e);
+    }
+    const double s = __dadd_rn(hi, lo);
+    lo = __dsub_rn(lo, __dsub_rn(s, hi));
     hi = s;
-    lo = __dadd_rn(lo, __dadd_rn(se, pe));
+    if (negative) {
+        hi = -hi;
+        lo = -lo;
+    }
+}
+
+// b - (S 2^L + es) in double-double, rounded once: the residual of one row
+// from its exact integer product sum S and the FP64 sum es of the products'
+// rounding errors.
+__device__ __forceinline__ double fx_residual(double b, const Fx192 &S, int c, double es)
+{
+    double h, l, s, e;
+    fx_to_dd(S, c, h, l);
+    dd_two_sum(b, -h, s, e);
+    return __dadd_rn(s, __dsub_rn(__dsub_rn(e, l), es));
 }
 
 // ---- double-float arithmetic of the preconditioner's product ----------------
@@ -411,13 +508,5 @@ __device__ __forceinline__ void df_fma(float m, float2 v, float &s, float &c)
     c = __fadd_rn(c, __fadd_rn(e, __fmaf_rn(m, v.y, pe)));
 }
 
-// (hi, lo) += (h2, l2)
-__device__ __forceinline__ void dd_add(double &hi, double &lo, double h2, double l2)
-{
-    double s, e;
-    dd_two_sum(hi, h2, s, e);
-    hi = s;
-    lo = __dadd_rn(lo, __dadd_rn(e, l2));
-}
 
 }  // namespace nrs

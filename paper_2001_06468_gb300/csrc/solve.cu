@@ -37,6 +37,8 @@ enum {
     SC_RES = 8,
     SC_DNPREV = 10,
     SC_STAG = 11,  // the last correction did not halve
+    SC_FXA = 12,   // ||A||_inf and ||x||_inf: the anchor of the exact residual
+    SC_FXX = 13,
     SC_COUNT = 16
 };
 
@@ -258,46 +260,65 @@ __global__ void __launch_bounds__(MV_THREADS)
     if (i + 3 < n) p[3] = (double)s3 + (double)c3;
 }
 
-// The residual's product in double-double: (part, part_lo)[s*n + i] =
-// sum_{j in split s} A[i,j] v[j] with every product exact and the sum carried
-// in two doubles (dd_fma), two rows per thread as in k_gemv_part.
+// The residual's product, exact (fx_add): fx[(s*3 + w)*n + i] = word w of
+// sum_{j in split s} fl(A[i,j] v[j]) as a 192-bit integer with the anchor of
+// ||A||_inf = scal[SC_FXA], ||v||_inf = scal[SC_FXX]; part[s*n + i] = the
+// FP64 sum of the products' rounding errors.  Two rows per thread as in
+// k_gemv_part.
 __global__ void __launch_bounds__(MV_THREADS)
-    k_gemv_part_dd(int64_t n, const double *__restrict__ A, int64_t lda,
-                   const double *__restrict__ v, double *__restrict__ part,
-                   double *__restrict__ part_lo, int64_t cols_per_split)
+    k_gemv_part_fx(int64_t n, const double *__restrict__ A, int64_t lda,
+                   const double *__restrict__ v, const double *__restrict__ scal,
+                   unsigned long long *__restrict__ fx, double *__restrict__ part,
+                   int64_t cols_per_split)
 {
     const int64_t i = ((int64_t)blockIdx.x * MV_THREADS + threadIdx.x) * 2;
     const int64_t j0 = (int64_t)blockIdx.y * cols_per_split;
     const int64_t j1 = min(n, j0 + cols_per_split);
     if (i >= n) return;
-    double h0 = 0.0, l0 = 0.0, h1 = 0.0, l1 = 0.0;
+    const int c = fx_anchor(scal[SC_FXA], scal[SC_FXX]);
+    Fx192 s0{0, 0, 0}, s1{0, 0, 0};
+    double e0 = 0.0, e1 = 0.0;
     const double *a = A + i;
 #pragma unroll 4
     for (int64_t j = j0; j < j1; ++j) {
         const double2 x = __ldg(reinterpret_cast<const double2 *>(a + j * lda));
         const double vj = __ldg(&v[j]);
-        dd_fma(x.x, vj, h0, l0);
-        dd_fma(x.y, vj, h1, l1);
+        const double p0 = __dmul_rn(x.x, vj), p1 = __dmul_rn(x.y, vj);
+        e0 = __dadd_rn(e0, __fma_rn(x.x, vj, -p0));
+        e1 = __dadd_rn(e1, __fma_rn(x.y, vj, -p1));
+        fx_add(s0, p0, c);
+        fx_add(s1, p1, c);
     }
-    part[blockIdx.y * n + i] = h0;
-    part_lo[blockIdx.y * n + i] = l0;
+    unsigned long long *f = fx + blockIdx.y * 3 * n;
+    f[i] = s0.w0;
+    f[n + i] = s0.w1;
+    f[2 * n + i] = s0.w2;
+    part[blockIdx.y * n + i] = e0;
     if (i + 1 < n) {
-        part[blockIdx.y * n + i + 1] = h1;
-        part_lo[blockIdx.y * n + i + 1] = l1;
+        f[i + 1] = s1.w0;
+        f[n + i + 1] = s1.w1;
+        f[2 * n + i + 1] = s1.w2;
+        part[blockIdx.y * n + i + 1] = e1;
     }
 }
 
-// out[i] = b[i] - sum_s (part + part_lo), carried in double-double and
-// rounded once
-__global__ void k_gemv_finish_dd(int64_t n, const double *__restrict__ part,
-                                 const double *__restrict__ part_lo, int splits,
-                                 const double *__restrict__ b, double *__restrict__ out)
+// out[i] = b[i] - (sum_s fx + sum_s part), the integer sums exact, rounded once
+__global__ void k_gemv_finish_fx(int64_t n, const unsigned long long *__restrict__ fx,
+                                 const double *__restrict__ part, int splits,
+                                 const double *__restrict__ scal, const double *__restrict__ b,
+                                 double *__restrict__ out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double hi = b[i], lo = 0.0;
-    for (int k = 0; k < splits; ++k) dd_add(hi, lo, -part[k * n + i], -part_lo[k * n + i]);
-    out[i] = __dadd_rn(hi, lo);
+    const int c = fx_anchor(scal[SC_FXA], scal[SC_FXX]);
+    Fx192 S{0, 0, 0};
+    double es = 0.0;
+    for (int k = 0; k < splits; ++k) {
+        const unsigned long long *f = fx + (int64_t)k * 3 * n;
+        fx_merge(S, Fx192{f[i], f[n + i], f[2 * n + i]});
+        es = __dadd_rn(es, part[k * n + i]);
+    }
+    out[i] = fx_residual(b[i], S, c, es);
 }
 
 // out[i] = b[i] - sum_s part (b != NULL), or sum_s part
@@ -491,6 +512,21 @@ __global__ void __launch_bounds__(RED_THREADS)
     if (threadIdx.x == 0) scal[slot] = m;
 }
 
+// scal[slot] = max_i sum_s part[s*n + i] (||A||_inf from k_gemv_part<true>)
+__global__ void __launch_bounds__(RED_THREADS)
+    k_rowsum_max(int64_t n, const double *__restrict__ part, int splits, double *__restrict__ scal,
+                 int slot)
+{
+    double m = 0.0;
+    for (int64_t e = threadIdx.x; e < n; e += RED_THREADS) {
+        double s = 0.0;
+        for (int k = 0; k < splits; ++k) s += part[k * n + e];
+        m = fmax(m, s);
+    }
+    m = block_max(m);
+    if (threadIdx.x == 0) scal[slot] = m;
+}
+
 // ---- host side ---------------------------------------------------------------
 
 template <typename K>
@@ -559,8 +595,8 @@ static void gemv(Ctx &c, const double *v, const double *b, double *out)
     c.launches += 2;
 }
 
-// r = b - A x with the FP64 matrix: double-double unless the context asks for
-// a plain FP64 residual
+// r = b - A x with the FP64 matrix: to about u^2 (exact products, fx_add)
+// unless the context asks for a plain FP64 residual
 static void residual(Ctx &c, const double *x, const double *b, double *r)
 {
     if (!c.residual_dd) {
@@ -570,13 +606,19 @@ static void residual(Ctx &c, const double *x, const double *b, double *r)
     const int64_t cps = ceil_div(c.n, c.splits64);
     dim3 grid((unsigned)ceil_div(c.n, 2 * MV_THREADS), (unsigned)c.splits64);
     c.tbeg(PH_GEMV);
-    k_gemv_part_dd<<<grid, MV_THREADS, 0, c.stream>>>(c.n, c.d_A64, c.lda, x, c.d_part,
-                                                      c.d_part_lo, cps);
-    k_gemv_finish_dd<<<(unsigned)ceil_div(c.n, 256), 256, 0, c.stream>>>(
-        c.n, c.d_part, c.d_part_lo, c.splits64, b, r);
+    // the anchor: ||A||_inf and ||x||_inf
+    k_gemv_part<true><<<grid, MV_THREADS, 0, c.stream>>>(c.n, c.d_A64, c.lda, nullptr, c.d_part, cps);
+    k_rowsum_max<<<1, RED_THREADS, 0, c.stream>>>(c.n, c.d_part, c.splits64, c.d_scal, SC_FXA);
+    k_nrm_inf<<<1, RED_THREADS, 0, c.stream>>>(c.n, x, c.d_scal, SC_FXX);
+    k_gemv_part_fx<<<grid, MV_THREADS, 0, c.stream>>>(c.n, c.d_A64, c.lda, x, c.d_scal,
+                                                      c.d_part_fx, c.d_part, cps);
+    k_gemv_finish_fx<<<(unsigned)ceil_div(c.n, 256), 256, 0, c.stream>>>(
+        c.n, c.d_part_fx, c.d_part, c.splits64, c.d_scal, b, r);
     c.tend(PH_GEMV);
-    c.launches += 2;
+    c.launches += 5;
 }
+
+void enqueue_residual(Ctx &c, const double *x, const double *b, double *r) { residual(c, x, b, r); }
 
 static double read_scalar(Ctx &c, int slot, cudaError_t *err)
 {

@@ -36,7 +36,7 @@ FREE, PRESCRIBED, STATIC = 0, 1, 2
 
 EXPORTS = ["nrs_create", "nrs_destroy", "nrs_last_error", "nrs_sizes", "nrs_set_state",
            "nrs_get_state", "nrs_set_external", "nrs_kinematics", "nrs_nearest_build",
-           "nrs_assemble", "nrs_factor", "nrs_solve", "nrs_step", "nrs_sync", "nrs_counters",
+           "nrs_assemble", "nrs_factor", "nrs_solve", "nrs_residual", "nrs_step", "nrs_sync", "nrs_counters",
            "nrs_velocity", "nrs_set_tracers", "nrs_get_tracers", "nrs_dp_start",
            "nrs_dp_next_time", "nrs_dp_stage", "nrs_dp_info_get",
            "nrs_set_timing",
@@ -126,6 +126,7 @@ _sig = {
     "nrs_assemble": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64]),
     "nrs_factor": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "nrs_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P, ctypes.POINTER(SolveReport)]),
+    "nrs_residual": (ctypes.c_int, [_P, _P, _P, _P]),
     "nrs_step": (ctypes.c_int, [_P, ctypes.POINTER(Shapes), ctypes.POINTER(Shapes), ctypes.c_double,
                                 _P, ctypes.POINTER(StepReport)]),
     "nrs_sync": (ctypes.c_int, [_P]),
@@ -211,7 +212,7 @@ class Context:
                  reuse_factor: bool = False, reuse_max_inner: int = 0, reuse_max_stages: int = 0,
                  warm_start: bool = False, solve_mode: str = "device", graph: bool = False,
                  inner_tol: float = 0.0, factor_input: str = "fp32",
-                 factor_schedule: str = "auto", residual: str = "dd",
+                 factor_schedule: str = "auto", residual: str = "extended",
                  stream: Optional[torch.cuda.Stream] = None, _handle=None):
         d, self._keep = _make_desc(n_off, q_off, kind, eps, mu, rigid, U, Omega, nn_global,
                                    factor_prec, tol, max_outer, max_inner, reuse_factor,
@@ -326,6 +327,16 @@ class Context:
         if check:
             self._check(st)
         return x, [r.as_dict() for r in reps]
+
+    def residual(self, b: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
+        """r = b - A x (device float64, length n) with the last assembled FP64
+        matrix, in the context's residual precision."""
+        if b.shape != (self.n,) or x.shape != (self.n,):
+            raise ValueError(f"residual: b and x must have shape ({self.n},)")
+        r = torch.empty_like(b)
+        self._check(_lib.nrs_residual(self._h, _ptr(b, torch.float64), _ptr(x, torch.float64),
+                                      _ptr(r)))
+        return r
 
     def step(self, s0: Shapes, s_half: Shapes, dt: float, sol: Optional[torch.Tensor] = None,
              report: bool = True, check: bool = True):
@@ -510,7 +521,7 @@ def _make_desc(n_off, q_off, kind, eps, mu=1.0, rigid=None, U=None, Omega=None, 
                factor_prec="fp32", tol=0.0, max_outer=0, max_inner=0, reuse_factor=False,
                reuse_max_inner=0, reuse_max_stages=0, warm_start=False, solve_mode="device",
                graph=False, inner_tol=0.0, factor_input="fp32", factor_schedule="auto",
-               residual="dd"):
+               residual="extended"):
     """An nrs_problem_desc and the host arrays it points to (keep them alive)."""
     n_off = np.ascontiguousarray(n_off, dtype=np.int64)
     q_off = np.ascontiguousarray(q_off, dtype=np.int64)
@@ -540,7 +551,8 @@ def _make_desc(n_off, q_off, kind, eps, mu=1.0, rigid=None, U=None, Omega=None, 
     d.inner_tol = float(inner_tol)
     d.factor_input = {"fp32": 0, "rounded": 1}[factor_input]
     d.factor_schedule = {"auto": 0, "fused": 1, "streams": 2, "two_level": 3}[factor_schedule]
-    d.residual = {"dd": 0, "fp64": 1}[residual]
+    # "extended": to about u^2 (exact products, see nrs_residual); "fp64": plain
+    d.residual = {"extended": 0, "fp64": 1}[residual]
     return d, (n_off, q_off, kind, rigid, U, Om)
 
 

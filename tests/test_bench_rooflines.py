@@ -65,9 +65,13 @@ def test_records_of_every_kernel_family():
     assert a["pairs_per_s"] == pytest.approx(PAIRS / 0.110)
     # FP32 copy: pairs against the pair peak 152 x 128 x clock / 20
     assert recs["assemble32"]["peak"] == pytest.approx(152 * 128 * SM_MHZ * 1e6 / 20)
-    # solve: (outer + inner) FP64 and (outer + inner + 1) FP32 matrix passes
+    # solve: (outer + inner + 1) FP64 matrix passes (the extra one for the
+    # extended residual's ||A||_inf) and (outer + inner + 1) FP32 ones; FP64
+    # operations: 3 per entry and outer step, 1 per entry and inner step + 1
     k = recs["krylov"]
-    assert k["work_per_launch"] == pytest.approx(8.0 * N_SYS ** 2 * 23.5 + 4.0 * N_SYS ** 2 * 24.5)
+    assert k["work_per_launch"] == pytest.approx(8.0 * N_SYS ** 2 * 24.5 + 4.0 * N_SYS ** 2 * 24.5)
+    assert k["fp64_gops"] * 1e9 * (k["ms_per_launch"] / 1e3) == pytest.approx(
+        (3 * SOLVE["outer_mean"] + SOLVE["inner_mean"] + 1) * N_SYS ** 2)
 
 
 def test_two_level_factorisation_is_rated_against_the_tensor_peak():
