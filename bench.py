@@ -9,7 +9,8 @@ free cells of 400 / 4000 points, N = 9200, Q = 92000, eps = 0.005,
 n = 27648 unknowns.  One step = one explicit-midpoint (RK2) step: twice
 (kinematics, nearest neighbours, segments, FP64 assembly of A_s bit-identical
 to the oracle's, rigid-body border, FP32 explicit inverse by blocked
-Gauss-Jordan with split-TF32 tensor-core updates -- refreshed when the
+Gauss-Jordan, two levels, whose rank-256 updates run on the tensor cores
+from power-of-two-scaled FP16 pairs -- refreshed when the
 previous solve needed more than 40 GMRES iterations or after 32 stages --,
 GMRES-based iterative refinement with an extended-precision residual (every
 product's rounded value summed exactly as a fixed-point integer, the rounding
@@ -225,12 +226,14 @@ def derived_peaks(peaks, sm_mhz):
     """Whole-GPU peaks used by the roofline records.  HBM and BF16 are the
     measured figures; the others are derived from the unit counts and the
     sampled SM clock (FP32: 128 lanes x 2 flops; FP64: 2 FMA lanes per SM;
-    TF32: the measured sustained BF16 rate x the nominal TF32/BF16 ratio)."""
+    TF32: the measured sustained BF16 rate x the nominal TF32/BF16 ratio;
+    FP16: the measured sustained BF16 rate, the same nominal dense rate)."""
     clk = sm_mhz * 1e6
     return {"hbm_gbs": peaks["hbm_gbs"],
             "fp32_tflops": SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * clk / 1e12,
             "fp64_gops": FP64_NOMINAL_TFLOPS / 2 * 1e3 * sm_mhz / 2070.0,
             "tf32_tflops": peaks["bf16_tflops_sustained"] * TF32_OVER_BF16,
+            "f16_tflops": peaks["bf16_tflops_sustained"],
             "pair_peak": SM_COUNT_NOMINAL * FP32_LANES_PER_SM * clk / PAIR_INSTR}
 
 
@@ -265,7 +268,8 @@ def kept_pairs(nrs, pr):
     return m_kept * q_kept
 
 
-def rooflines(ph_ms, ph_spans, n, pairs, peaks, peak_src, sm_mhz, solve_stats, pairs64=None):
+def rooflines(ph_ms, ph_spans, n, pairs, peaks, peak_src, sm_mhz, solve_stats, pairs64=None,
+              update_f16=True):
     """Roofline records of the kernel families from the live per-phase CUDA
     event times (one span per launch, on the stream each kernel runs on).
     Algorithmic work per launch:
@@ -288,19 +292,33 @@ def rooflines(ph_ms, ph_spans, n, pairs, peaks, peak_src, sm_mhz, solve_stats, p
     two_level = (ph_spans.get("lu_update") and not ph_spans.get("lu_diag")
                  and ph_spans.get("lu_panel") == ph_spans.get("lu_update"))
     if two_level:
-        # k_tc_gj2_update: one rank-256 product per 256-column block
+        # k_tc_gj2_update: one rank-256 product per 256-column block, from
+        # scaled FP16 pairs (kind::f16, rated against the BF16/FP16 tensor
+        # peak) or split TF32; it also reads and writes the FP32 matrix once
+        # (8 n^2 bytes).  The record's bound is the roofline it is closer to.
         t = per_launch("lu_update")
         b = 8.0 * n * n
         fl = 3 * 2.0 * n * n * 256
+        tp = P["f16_tflops"] if update_f16 else P["tf32_tflops"]
+        pieces = "scaled FP16 pairs" if update_f16 else "split TF32"
+        tfrac, hfrac = fl / t / 1e12 / tp, b / t / 1e9 / P["hbm_gbs"]
+        tensor_rec = {"bound": "tensor", "achieved": fl / t / 1e12, "peak": tp, "unit": "TFLOP/s",
+                      "frac": tfrac,
+                      "peak_source": peak_src + (" BF16 sustained (FP16 runs at the BF16 rate)"
+                                                 if update_f16 else
+                                                 " BF16 sustained x nominal TF32/BF16 (1.1/2.25)"),
+                      "work_per_launch": fl,
+                      "work_unit": f"tensor flops (3 passes of {pieces} x 2 n^2 256)"}
+        hbm_rec = {"bound": "hbm", "achieved": b / t / 1e9, "peak": P["hbm_gbs"], "unit": "GB/s",
+                   "frac": hfrac, "peak_source": peak_src + " HBM copy", "work_per_launch": b,
+                   "work_unit": "bytes (8 n^2: read and write of the FP32 matrix)"}
         recs["lu_update"] = {
-            "kernel": "k_tc_gj2_update (persistent tcgen05 split-TF32 rank-256 update of the "
-                      "FP32 inverse, two-level Gauss-Jordan)",
-            "bound": "tensor", "achieved": fl / t / 1e12, "peak": P["tf32_tflops"],
-            "unit": "TFLOP/s", "frac": fl / t / 1e12 / P["tf32_tflops"],
-            "peak_source": peak_src + " BF16 sustained x nominal TF32/BF16 (1.1/2.25)",
-            "work_per_launch": fl, "work_unit": "tensor flops (3 split-TF32 passes x 2 n^2 256)",
+            "kernel": "k_tc_gj2_update (persistent tcgen05 rank-256 update of the FP32 inverse "
+                      f"from {pieces}, two-level Gauss-Jordan)",
+            **(hbm_rec if hfrac >= tfrac else tensor_rec),
+            "tensor_tflops": fl / t / 1e12, "tensor_frac": tfrac, "tensor_peak": tp,
             "useful_tflops": fl / 3 / t / 1e12,
-            "hbm_gbs": b / t / 1e9, "hbm_frac": b / t / 1e9 / P["hbm_gbs"],
+            "hbm_gbs": b / t / 1e9, "hbm_frac": hfrac,
             "us_per_launch": t * 1e6, "launches": ph_spans["lu_update"],
             "traffic": _traffic("k_tc_gj2_update", n)}
         t = per_launch("lu_panel")
@@ -921,6 +939,10 @@ PROFILE_WORKLOADS = {
     "swimmer": lambda: g.swimmer_config(),
     # n = 6006: FP64 matrix 289 MB, FP32 copy 144 MB, both larger than L2
     "swimmer_mid": lambda: g.swimmer_config(ns_f=200, nth_f=10, ns_q=1000, nth_q=20),
+    # n = 13824: four cells in a coarser channel; 54 blocks of the two-level
+    # factorisation, 38 update tiles per SM and block; FP64 matrix 1.5 GB, FP32 768 MB
+    "channel_half": lambda: g.sperm_channel_config(count=4, wall_f=(60, 15, 8),
+                                                   wall_q=(186, 46, 24)),
     "swimmers4": lambda: g.swimmers_config(),
     "sperm_channel": lambda: g.sperm_channel_config(),
 }
@@ -1078,10 +1100,12 @@ def run_nrs(args):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64 (bit-exact assembly, extended-precision residual) + fp32/split-tf32 factor",
+        "dtype": "f64 (bit-exact assembly, extended-precision residual) + fp32 inverse "
+                 "(tensor-core updates from scaled fp16 pairs)",
         "data": "synthetic (seeded channel, head and flagellum shapes)",
-        "config": {"workload": WORKLOADS_DESC[HEADLINE], "factor": args.prec + " explicit inverse "
-                   "(blocked Gauss-Jordan), refreshed after >40 GMRES iterations or 32 stages",
+        "config": {"workload": WORKLOADS_DESC[HEADLINE], "factor": "FP32 explicit inverse (two-level "
+                   "blocked Gauss-Jordan, rank-256 tensor-core updates from scaled FP16 pairs; "
+                   f"--prec {args.prec}), refreshed after >40 GMRES iterations or 32 stages",
                    "refinement": "GMRES-IR, extended residual (exact fixed-point product sums), warm start from the previous "
                                  "stage", "rk2_stages_per_step": 2,
                    "l2": "flushed between timed steps (512 MiB write); matrices 9.2 GB > L2",
@@ -1203,7 +1227,7 @@ def main():
                     help="--warmup steps and one more of --workload, then exit (for ncu)")
     ap.add_argument("--workload", default="swimmer", choices=sorted(PROFILE_WORKLOADS))
     ap.add_argument("--factor-schedule", default="auto",
-                    choices=["auto", "fused", "streams", "two_level"],
+                    choices=["auto", "fused", "streams", "two_level", "two_level_tf32"],
                     help="factorisation schedule of --profile-solve")
     args = ap.parse_args()
     if args.profile_solve:

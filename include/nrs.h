@@ -120,7 +120,7 @@ typedef struct {
                               without the graph.  backward_err is reported as computed in the
                               graph. */
     int32_t factor_schedule; /* FP32/TF32 factorisation (Gauss-Jordan explicit inverse):
-                              0 = automatic: as 3 with TF32 from n = 8192 on, else as 2;
+                              0 = automatic: as 4 with TF32 from n = 8192 on, else as 2;
                               1 = with TF32 on a device with tensor memory, the whole
                               inversion as ONE cooperative launch taking every SM (the chain
                               of diagonal inverses on one CTA, the updates on the others,
@@ -130,7 +130,12 @@ typedef struct {
                               the same result bit for bit; 3 = two levels (TF32, n >= 512):
                               256-column blocks whose column panel is eliminated in 64-column
                               steps, then one rank-256 tensor-core update of the rest of the
-                              matrix (a persistent tcgen05 kernel).  Other values: NRS_EINVAL. */
+                              matrix (a persistent tcgen05 kernel) from split-TF32 operands
+                              (hi hi + hi lo + lo hi, kind::tf32); 4 = as 3 with the update's
+                              operands as FP16 pairs (kind::f16: twice the tensor rate and
+                              half the operand bytes of TF32), every operand row scaled by a
+                              power of two that puts its largest entry in [2^14, 2^15) and
+                              unscaled exactly in the update.  Other values: NRS_EINVAL. */
     int32_t residual;      /* the refinement's residual b - A x: 0 = to about u^2 (every
                               product's rounded value summed exactly as a fixed-point
                               integer, the products' rounding errors in FP64, rounded once

@@ -45,7 +45,7 @@ nrs_status alloc_all(Ctx *c)
     const int64_t N = c->N, Q = c->Q, n = c->n, lda = c->lda, m = c->max_inner;
     // workspaces of the two-level factorisation where it may run
     const bool gj2 = c->factor_prec == NRS_TF32 && n >= 512 &&
-                     (c->gj_schedule == 3 || (c->gj_schedule == 0 && n >= nrs::GJ2_MIN_N));
+                     (c->gj_schedule >= 3 || (c->gj_schedule == 0 && n >= nrs::GJ2_MIN_N));
     const int nb = c->nbodies;
     struct {
         void **p;
@@ -522,7 +522,7 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
     c->tol_in = d->inner_tol > 0.0 ? d->inner_tol : 1e-4;
     c->lo_eval = d->factor_input ? 1 : 0;
     c->residual_dd = d->residual == 0 ? 1 : 0;
-    if (d->factor_schedule < 0 || d->factor_schedule > 3) {
+    if (d->factor_schedule < 0 || d->factor_schedule > 4) {
         delete c;
         return NRS_EINVAL;
     }

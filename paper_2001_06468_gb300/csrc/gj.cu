@@ -1346,9 +1346,10 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)
     if (prec == NRS_TF32 && run_gj_fused(c, M, lda)) return 0;
     // large systems: the two-level elimination whose updates are rank-256 products
     const bool two = !c.gj_force_one_level &&
-                     (c.gj_schedule == 3 || (c.gj_schedule == 0 && c.n >= GJ2_MIN_N));
+                     (c.gj_schedule >= 3 || (c.gj_schedule == 0 && c.n >= GJ2_MIN_N));
     c.last_factor_two_level = prec == NRS_TF32 && two && gj2_supported(c) && c.d_gj2;
-    if (c.last_factor_two_level) return run_gj2_fp32(c, M, lda);
+    // the update's pieces: TF32 (schedule 3), scaled FP16 (schedule 4 and auto)
+    if (c.last_factor_two_level) return run_gj2_fp32(c, M, lda, c.gj_schedule != 3);
     static bool diag_attr = false;
     if (!diag_attr) {
         cudaFuncSetAttribute(k_gj_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -24,12 +24,13 @@
 // The update (k_tc_gj2_update) is a persistent kernel, one CTA per SM, warp
 // specialised: warp 0 loads the operand tiles with TMA (128-byte swizzle)
 // into two shared-memory stages, warp 1 issues tcgen05.mma kind::tf32 into
-// one of two 128 x 256 FP32 accumulators in tensor memory, warps 2-9 add the
+// one of two 128 x 256 FP32 accumulators in tensor memory, warps 2-17 add the
 // finished accumulator to M (tcgen05.ld, coalesced column-major
-// read-modify-write, two warps per 32 rows) while the next tile's products run.  Every wait is
+// read-modify-write, four warps per 32 rows) while the next tile's products run.  Every wait is
 // bounded: one that runs out sets ST_TIMEOUT, the roles stop, and the CTA
 // waits (bounded) for its own copies and products before freeing tensor memory.
 #include <cuda.h>
+#include <cuda_fp16.h>
 
 #include "tc_prims.cuh"
 
@@ -41,14 +42,13 @@ namespace {
 
 constexpr int G2_W = 256;                  // outer block (columns of the panel, K of the product)
 constexpr int G2_BM = 128, G2_BN = 256;    // output tile of the update
-constexpr int G2_KC = 32;                  // K per pipeline stage (128 bytes of FP32)
-constexpr int G2_NCH = G2_W / G2_KC;       // stages per tile
-constexpr uint32_t G2_A_BYTES = G2_BM * G2_KC * 4;                       // 16 KB
-constexpr uint32_t G2_B_BYTES = G2_BN * G2_KC * 4;                       // 32 KB
+constexpr int G2_KB = 128;                 // bytes of K per pipeline stage and operand row
+constexpr uint32_t G2_A_BYTES = G2_BM * G2_KB;                           // 16 KB
+constexpr uint32_t G2_B_BYTES = G2_BN * G2_KB;                           // 32 KB
 constexpr uint32_t G2_STAGE_BYTES = 2 * G2_A_BYTES + 2 * G2_B_BYTES;     // 96 KB
 constexpr int G2_STAGES = 2;
 constexpr int G2_SMEM = G2_STAGES * G2_STAGE_BYTES + 1024;
-constexpr int G2_EPI_WARPS = 8;          // two per accumulator lane quarter, half the columns each
+constexpr int G2_EPI_WARPS = 16;         // four per accumulator lane quarter, 64 columns each
 constexpr int G2_THREADS = 64 + 32 * G2_EPI_WARPS;
 constexpr int G2_TMEM_COLS = 2 * G2_BN;    // two accumulators
 
@@ -68,17 +68,24 @@ __device__ __forceinline__ void g2_tile(int64_t t, int nrt, int skip, int &rt, i
 
 // M[i, j] += sum_{c < 256} A[i][c] B[j][c] for all rows i < n and the columns
 // j of every 256-wide column tile but `skip`, A = Ah + Al and B = Bh + Bl the
-// split panels (row-major, 256 floats a row), products hi hi + hi lo + lo hi.
+// split panels (row-major, 256 elements a row), products hi hi + hi lo + lo hi.
+// F16 = false: TF32 pieces (FP32 storage, kind::tf32, 32 K a stage); true:
+// scaled FP16 pieces (kind::f16, 64 K a stage), row i of A and row j of B
+// stored times 2^e_i, 2^f_j, undone by sA[i] = 2^-e_i, sB[j] = 2^-f_j here.
+template <bool F16>
 __global__ void __launch_bounds__(G2_THREADS, 1)
     k_tc_gj2_update(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                     const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
                     int64_t n, float *__restrict__ M, int64_t lda, int nrt, int nct, int skip,
-                    int32_t *status)
+                    const float *__restrict__ sA, const float *__restrict__ sB, int32_t *status)
 {
+    constexpr int KC = F16 ? 64 : 32;      // K elements per stage (128 bytes)
+    constexpr int NCH = G2_W / KC;         // stages per tile
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full[G2_STAGES], empty[G2_STAGES], tfull[2], tempty[2], drain;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
+    __shared__ float s_scale[G2_EPI_WARPS][G2_BN / 4];  // FP16 variant: column scales per warp
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -118,7 +125,7 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
             for (int64_t t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x) {
                 int rt, ct;
                 g2_tile(t, nrt, skip_eff, rt, ct);
-                for (int ch = 0; ch < G2_NCH; ++ch, ++it) {
+                for (int ch = 0; ch < NCH; ++ch, ++it) {
                     const int s = (int)(it & 1), k = (int)(it >> 1);
                     if (!mbar_wait(&empty[s], (uint32_t)((k & 1) ^ 1))) {
                         atomicOr(status, ST_TIMEOUT);
@@ -127,10 +134,10 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
                     }
                     uint8_t *st = base + (size_t)s * G2_STAGE_BYTES;
                     mbar_expect_tx(&full[s], G2_STAGE_BYTES);
-                    tma_load_2d(st, &tmAh, ch * G2_KC, rt * G2_BM, &full[s]);
-                    tma_load_2d(st + G2_A_BYTES, &tmAl, ch * G2_KC, rt * G2_BM, &full[s]);
-                    tma_load_2d(st + 2 * G2_A_BYTES, &tmBh, ch * G2_KC, ct * G2_BN, &full[s]);
-                    tma_load_2d(st + 2 * G2_A_BYTES + G2_B_BYTES, &tmBl, ch * G2_KC, ct * G2_BN,
+                    tma_load_2d(st, &tmAh, ch * KC, rt * G2_BM, &full[s]);
+                    tma_load_2d(st + G2_A_BYTES, &tmAl, ch * KC, rt * G2_BM, &full[s]);
+                    tma_load_2d(st + 2 * G2_A_BYTES, &tmBh, ch * KC, ct * G2_BN, &full[s]);
+                    tma_load_2d(st + 2 * G2_A_BYTES + G2_B_BYTES, &tmBl, ch * KC, ct * G2_BN,
                                 &full[s]);
                     last_k[s] = k;
                 }
@@ -143,9 +150,9 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
             }
         }
     } else if (warp == 1) {
-        // ---- MMA issuer: 4 K-steps of 8 x 3 products per stage
+        // ---- MMA issuer: 4 K-steps of 32 bytes (8 TF32 or 16 FP16) x 3 products per stage
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_tf32(G2_BM, G2_BN);
+            constexpr uint32_t idesc = F16 ? idesc_f16(G2_BM, G2_BN) : idesc_tf32(G2_BM, G2_BN);
             int64_t it = 0;
             int lt = 0;
             for (int64_t t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x, ++lt) {
@@ -158,7 +165,7 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(a * G2_BN);
                 bool ok = true;
-                for (int ch = 0; ch < G2_NCH; ++ch, ++it) {
+                for (int ch = 0; ch < NCH; ++ch, ++it) {
                     const int s = (int)(it & 1), k = (int)(it >> 1);
                     if (!mbar_wait(&full[s], (uint32_t)(k & 1))) {
                         atomicOr(status, ST_TIMEOUT);
@@ -169,15 +176,21 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
                     tc_fence_after();
                     const uint32_t st = smem_u32(base + (size_t)s * G2_STAGE_BYTES);
 #pragma unroll
-                    for (int kk = 0; kk < G2_KC / 8; ++kk) {
+                    for (int kk = 0; kk < G2_KB / 32; ++kk) {
                         const uint32_t kofs = (uint32_t)kk * 32u;
                         const uint64_t ah = desc_sw128_kmajor(st + kofs);
                         const uint64_t al = desc_sw128_kmajor(st + G2_A_BYTES + kofs);
                         const uint64_t bh = desc_sw128_kmajor(st + 2 * G2_A_BYTES + kofs);
                         const uint64_t bl = desc_sw128_kmajor(st + 2 * G2_A_BYTES + G2_B_BYTES + kofs);
-                        mma_tf32(d, al, bh, idesc, (ch > 0 || kk > 0) ? 1u : 0u);
-                        mma_tf32(d, ah, bl, idesc, 1u);
-                        mma_tf32(d, ah, bh, idesc, 1u);
+                        if (F16) {
+                            mma_f16(d, al, bh, idesc, (ch > 0 || kk > 0) ? 1u : 0u);
+                            mma_f16(d, ah, bl, idesc, 1u);
+                            mma_f16(d, ah, bh, idesc, 1u);
+                        } else {
+                            mma_tf32(d, al, bh, idesc, (ch > 0 || kk > 0) ? 1u : 0u);
+                            mma_tf32(d, ah, bl, idesc, 1u);
+                            mma_tf32(d, ah, bh, idesc, 1u);
+                        }
                     }
                     mma_commit(&empty[s]);  // the stage is free once these have read it
                 }
@@ -189,13 +202,45 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
             mbar_wait(&drain, 0);
         }
     } else {
-        // ---- epilogue: warp w reads accumulator lanes 32 (w % 4) .. + 31 and
-        // half of the 256 columns; the next 16 columns of M are loaded while
-        // the current ones are added and stored
-        const int q = warp & 3, half = (warp - 2) >> 2;
+        // ---- epilogue: warp w reads accumulator lanes 32 (w % 4) .. + 31 (the
+        // quarter its rank in the warpgroup may access) and 64 of the 256
+        // columns, 16 at a time; the next 16 columns of M (of this tile, or the
+        // first ones of the CTA's next tile) are loaded while the current ones
+        // are added and stored.  The FP16 variant's column scales of the tile
+        // are staged once per tile in shared memory.
+        constexpr int CW = 16, CPW = G2_BN / 4, NCHK = CPW / CW;
+        const int q = warp & 3, part = (warp - 2) >> 2;
+        float *scl = s_scale[warp - 2];
+        float *p = nullptr;
+        int64_t ncol = 0, row = 0, col0 = 0;
+        bool live = false;
+        auto setup = [&](int64_t tt) {
+            int rt, ct;
+            g2_tile(tt, nrt, skip_eff, rt, ct);
+            row = (int64_t)rt * G2_BM + q * 32 + lane;
+            col0 = (int64_t)ct * G2_BN + part * CPW;
+            p = M + row + col0 * lda;
+            ncol = n - col0;
+            live = row < n;
+        };
+        float cur[CW], nxt[CW];
+        if ((int64_t)blockIdx.x < ntiles) {
+            setup(blockIdx.x);
+#pragma unroll
+            for (int j = 0; j < CW; ++j) cur[j] = (live && j < ncol) ? __ldcs(p + j * lda) : 0.0f;
+        }
         int lt = 0;
         for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
             const int a = lt & 1, u = lt >> 1;
+            // this tile's geometry (setup() moves on to the next tile below)
+            float *const pt = p;
+            const int64_t nc = ncol, c0 = col0;
+            const bool lv = live;
+            const float sa = (F16 && lv) ? __ldg(sA + row) : 1.0f;
+            if (F16) {
+                for (int c = lane; c < CPW; c += 32) scl[c] = c < nc ? __ldg(sB + c0 + c) : 0.0f;
+                __syncwarp();
+            }
             const bool got = mbar_wait(&tfull[a], (uint32_t)(u & 1));
             if (!__all_sync(0xffffffffu, got) || s_abort) {
                 if (lane == 0) {
@@ -205,37 +250,45 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
                 break;
             }
             tc_fence_after();
-            int rt, ct;
-            g2_tile(t, nrt, skip_eff, rt, ct);
-            const int64_t row = (int64_t)rt * G2_BM + q * 32 + lane;
-            const int cbeg = half * (G2_BN / 2);
-            const int64_t col0 = (int64_t)ct * G2_BN + cbeg;
-            const uint32_t tb = tmem + (uint32_t)(a * G2_BN + cbeg) + ((uint32_t)(q * 32) << 16);
-            float *p = M + row + col0 * lda;
-            const int64_t ncol = n - col0;
-            const bool live = row < n;
-            float cur[16], nxt[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) cur[j] = (live && j < ncol) ? __ldcs(p + j * lda) : 0.0f;
+            const uint32_t tb =
+                tmem + (uint32_t)(a * G2_BN + part * CPW) + ((uint32_t)(q * 32) << 16);
+            const bool full = lv && nc >= CPW;
 #pragma unroll 1
-            for (int chunk = 0; chunk < G2_BN / 32; ++chunk) {
-                uint32_t v[16];
-                tmem_ld_16cols_async(tb + (uint32_t)(chunk * 16), v);
-                if (chunk + 1 < G2_BN / 32) {
-                    const float *pn = p + (int64_t)(chunk + 1) * 16 * lda;
+            for (int chunk = 0; chunk < NCHK; ++chunk) {
+                uint32_t v[CW];
+                tmem_ld_16cols_async(tb + (uint32_t)(chunk * CW), v);
+                if (chunk + 1 < NCHK) {
+                    const float *pn = pt + (int64_t)(chunk + 1) * CW * lda;
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        nxt[j] = (live && (chunk + 1) * 16 + j < ncol) ? __ldcs(pn + j * lda) : 0.0f;
+                    for (int j = 0; j < CW; ++j)
+                        nxt[j] = (lv && (chunk + 1) * CW + j < nc) ? __ldcs(pn + j * lda) : 0.0f;
+                } else if (t + (int64_t)gridDim.x < ntiles) {
+                    setup(t + gridDim.x);
+#pragma unroll
+                    for (int j = 0; j < CW; ++j)
+                        nxt[j] = (live && j < ncol) ? __ldcs(p + j * lda) : 0.0f;
                 }
                 tmem_wait_ld();
-                if (live) {
-                    float *pc = p + (int64_t)chunk * 16 * lda;
+                float *pc = pt + (int64_t)chunk * CW * lda;
+                if (full) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (chunk * 16 + j < ncol) __stcs(pc + j * lda, cur[j] + __uint_as_float(v[j]));
+                    for (int j = 0; j < CW; ++j) {
+                        float d = __uint_as_float(v[j]);
+                        // undo the operands' power-of-two scaling (exact)
+                        if (F16) d = (d * sa) * scl[chunk * CW + j];
+                        __stcs(pc + j * lda, cur[j] + d);
+                    }
+                } else if (lv) {
+#pragma unroll
+                    for (int j = 0; j < CW; ++j) {
+                        if (chunk * CW + j >= nc) continue;
+                        float d = __uint_as_float(v[j]);
+                        if (F16) d = (d * sa) * scl[chunk * CW + j];
+                        __stcs(pc + j * lda, cur[j] + d);
+                    }
                 }
 #pragma unroll
-                for (int j = 0; j < 16; ++j) cur[j] = nxt[j];
+                for (int j = 0; j < CW; ++j) cur[j] = nxt[j];
             }
             tc_fence_before();
             __syncwarp();
@@ -422,6 +475,117 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Power of two 2^e bringing the magnitude m > 0 into [2^14, 2^15) (e clamped
+// to [-100, 100]; 0 for m = 0), as e.
+__device__ __forceinline__ int g2_scale_exp(float m)
+{
+    if (!(m > 0.0f) || !isfinite(m)) return 0;
+    return max(-100, min(100, 14 - ilogbf(m)));
+}
+
+__device__ __forceinline__ float g2_pow2(int e) { return __int_as_float((127 + e) << 23); }
+
+// x (already scaled) as hi = fp16(x) and lo = fp16(x - hi): about 22 bits of x,
+// the FP16 analogue of split_tf32 (x - hi is exact in FP32).
+__device__ __forceinline__ void split_f16(float x, __half &hi, __half &lo)
+{
+    hi = __float2half_rn(x);
+    lo = __float2half_rn(x - __half2float(hi));
+}
+
+// The product's operands as scaled FP16 pairs (the FP16 variant of k_gj2_prep):
+// row i of A = G - I_K and row j of B (column j of the block row) are each
+// multiplied by the power of two 2^e that brings their largest magnitude into
+// [2^14, 2^15) -- so no piece overflows FP16 and the low pieces stay above
+// its subnormal range except for entries below 2^-24 of their row's maximum --
+// then split (split_f16); sA[i] = 2^-e_i, sB[j] = 2^-f_j.
+//   blockIdx.y == 0: A rows [64 blockIdx.x, +64): the row maxima first (a
+//                    thread per row and quarter of the 256 columns), then 64 x
+//                    64 column chunks transposed through shared memory;
+//   blockIdx.y == 1: B rows j in [64 blockIdx.x, +64), a warp per 8 of them.
+// Both row-major with 256 halves a row, rows up to `rows_pad`.
+__global__ void __launch_bounds__(256)
+    k_gj2_prep16(int64_t n, const float *__restrict__ M, int64_t lda, int64_t k0, int W,
+                 int64_t rows_pad, __half *__restrict__ Ah, __half *__restrict__ Al,
+                 __half *__restrict__ Bh, __half *__restrict__ Bl, float *__restrict__ sA,
+                 float *__restrict__ sB)
+{
+    __shared__ float T[64][65];
+    __shared__ float smax[4][64];
+    __shared__ float sscale[64];
+    const int tid = threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * 64;
+    if (i0 >= rows_pad) return;
+    if (blockIdx.y == 0) {
+        {
+            const int r = tid & 63, qc = tid >> 6;
+            const int64_t i = i0 + r;
+            float m = 0.0f;
+            if (i < n)
+                for (int c = qc * 64; c < qc * 64 + 64 && c < W; ++c) {
+                    float v = M[i + (k0 + c) * lda];
+                    if (i == k0 + c) v -= 1.0f;
+                    m = fmaxf(m, fabsf(v));
+                }
+            smax[qc][r] = m;
+        }
+        __syncthreads();
+        if (tid < 64) {
+            const float m = fmaxf(fmaxf(smax[0][tid], smax[1][tid]), fmaxf(smax[2][tid], smax[3][tid]));
+            const int e = g2_scale_exp(m);
+            sscale[tid] = g2_pow2(e);
+            sA[i0 + tid] = g2_pow2(-e);
+        }
+        for (int c0 = 0; c0 < G2_W; c0 += 64) {
+            __syncthreads();
+            for (int idx = tid; idx < 64 * 64; idx += 256) {
+                const int r = idx & 63, c = idx >> 6;
+                const int64_t i = i0 + r;
+                float v = 0.0f;
+                if (i < n && c0 + c < W) {
+                    v = M[i + (k0 + c0 + c) * lda];
+                    if (i == k0 + c0 + c) v -= 1.0f;
+                }
+                T[r][c] = v;
+            }
+            __syncthreads();
+            for (int idx = tid; idx < 64 * 64; idx += 256) {
+                const int c = idx & 63, r = idx >> 6;
+                __half h, l;
+                split_f16(T[r][c] * sscale[r], h, l);
+                Ah[(i0 + r) * G2_W + c0 + c] = h;
+                Al[(i0 + r) * G2_W + c0 + c] = l;
+            }
+        }
+    } else {
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int jr = warp; jr < 64; jr += 8) {
+            const int64_t j = i0 + jr;
+            const bool col_live = j < n && !(j >= k0 && j < k0 + W);
+            float v[G2_W / 32];
+            float m = 0.0f;
+#pragma unroll
+            for (int t = 0; t < G2_W / 32; ++t) {
+                const int c = lane + 32 * t;
+                v[t] = (col_live && c < W) ? M[(k0 + c) + j * lda] : 0.0f;
+                m = fmaxf(m, fabsf(v[t]));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            const int e = g2_scale_exp(m);
+            const float sc = g2_pow2(e);
+#pragma unroll
+            for (int t = 0; t < G2_W / 32; ++t) {
+                __half h, l;
+                split_f16(v[t] * sc, h, l);
+                Bh[j * G2_W + lane + 32 * t] = h;
+                Bl[j * G2_W + lane + 32 * t] = l;
+            }
+            if (lane == 0) sB[j] = g2_pow2(-e);
+        }
+    }
+}
+
 typedef CUresult (*EncodeTiledFn2)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -445,19 +609,21 @@ EncodeTiledFn2 encode_fn2()
     return fn;
 }
 
-// 2-D map over a row-major [rows][256] FP32 panel, boxes of 32 x box_rows with
-// 128-byte swizzle; rows >= `rows` read as zero.
-bool make_panel256_map(CUtensorMap *tm, const float *ptr, int64_t rows, int box_rows)
+// 2-D map over a row-major [rows][256] panel of FP32 (f16 = false) or FP16
+// elements, boxes of 128 bytes x box_rows with 128-byte swizzle; rows >=
+// `rows` read as zero.
+bool make_panel256_map(CUtensorMap *tm, const void *ptr, int64_t rows, int box_rows, bool f16)
 {
     EncodeTiledFn2 enc = encode_fn2();
     if (!enc) return false;
+    const size_t es = f16 ? 2 : 4;
     cuuint64_t dims[2] = {(cuuint64_t)G2_W, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)G2_W * sizeof(float)};
-    cuuint32_t box[2] = {(cuuint32_t)G2_KC, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)G2_W * es};
+    cuuint32_t box[2] = {(cuuint32_t)(G2_KB / es), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box,
-               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    return enc(tm, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+               const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -475,22 +641,34 @@ size_t gj2_panel_floats(int64_t n)
 }
 
 // The two-level factorisation of the FP32 matrix M (n x n, column-major) in
-// place; the split panels live in c.d_gj2 (4 x gj2_panel_floats(n) floats), the
-// inner scaled block row in c.d_gj2_r (64 x 256 floats).  Returns 0, or -1 if
-// the tensor maps could not be made.
-int run_gj2_fp32(Ctx &c, float *M, int64_t lda)
+// place; the split panels live in c.d_gj2 (4 x gj2_panel_floats(n) floats: the
+// FP16 variant uses half of it for the panels and two scale vectors after
+// them), the inner scaled block row in c.d_gj2_r (64 x 256 floats).  f16: the
+// update's products from scaled FP16 pieces instead of TF32 ones.  Returns 0,
+// or -1 if the tensor maps could not be made.
+int run_gj2_fp32(Ctx &c, float *M, int64_t lda, bool f16)
 {
     const int64_t n = c.n;
     const int64_t rows_pad = ceil_div(n, G2_BN) * G2_BN;
     const size_t pf = gj2_panel_floats(n);
-    float *Ah = c.d_gj2, *Al = c.d_gj2 + pf, *Bh = c.d_gj2 + 2 * pf, *Bl = c.d_gj2 + 3 * pf;
+    const size_t es = f16 ? 2 : 4;
+    uint8_t *w = reinterpret_cast<uint8_t *>(c.d_gj2);
+    void *Ah = w, *Al = w + pf * es, *Bh = w + 2 * pf * es, *Bl = w + 3 * pf * es;
+    // the FP16 variant's row and column scales, after its panels
+    float *sA = f16 ? reinterpret_cast<float *>(w + 4 * pf * es) : nullptr;
+    float *sB = f16 ? sA + rows_pad : nullptr;
     CUtensorMap mAh, mAl, mBh, mBl;
-    if (!make_panel256_map(&mAh, Ah, rows_pad, G2_BM) || !make_panel256_map(&mAl, Al, rows_pad, G2_BM) ||
-        !make_panel256_map(&mBh, Bh, rows_pad, G2_BN) || !make_panel256_map(&mBl, Bl, rows_pad, G2_BN))
+    if (!make_panel256_map(&mAh, Ah, rows_pad, G2_BM, f16) ||
+        !make_panel256_map(&mAl, Al, rows_pad, G2_BM, f16) ||
+        !make_panel256_map(&mBh, Bh, rows_pad, G2_BN, f16) ||
+        !make_panel256_map(&mBl, Bl, rows_pad, G2_BN, f16))
         return -1;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_tc_gj2_update, cudaFuncAttributeMaxDynamicSharedMemorySize, G2_SMEM);
+        cudaFuncSetAttribute(k_tc_gj2_update<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             G2_SMEM);
+        cudaFuncSetAttribute(k_tc_gj2_update<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             G2_SMEM);
         attr = true;
     }
     const size_t diag_smem = gj_diag_smem();
@@ -510,13 +688,22 @@ int run_gj2_fp32(Ctx &c, float *M, int64_t lda)
                 n, M, lda, k0, W, r0, c.d_gj_dinv, c.d_gj2_r);
             c.launches += 3;
         }
-        k_gj2_prep<<<dim3((unsigned)ceil_div(rows_pad, 64), 5), 256, 0, c.stream>>>(
-            n, M, lda, k0, W, rows_pad, Ah, Al, Bh, Bl);
+        if (f16)
+            k_gj2_prep16<<<dim3((unsigned)ceil_div(rows_pad, 64), 2), 256, 0, c.stream>>>(
+                n, M, lda, k0, W, rows_pad, (__half *)Ah, (__half *)Al, (__half *)Bh, (__half *)Bl,
+                sA, sB);
+        else
+            k_gj2_prep<<<dim3((unsigned)ceil_div(rows_pad, 64), 5), 256, 0, c.stream>>>(
+                n, M, lda, k0, W, rows_pad, (float *)Ah, (float *)Al, (float *)Bh, (float *)Bl);
         c.launches += 1;
         c.tend(PH_LU_PANEL);
         c.tbeg(PH_LU_UPDATE);
-        k_tc_gj2_update<<<grid, G2_THREADS, G2_SMEM, c.stream>>>(mAh, mAl, mBh, mBl, n, M, lda, nrt,
-                                                                nct, (int)(k0 / G2_W), c.d_status);
+        if (f16)
+            k_tc_gj2_update<true><<<grid, G2_THREADS, G2_SMEM, c.stream>>>(
+                mAh, mAl, mBh, mBl, n, M, lda, nrt, nct, (int)(k0 / G2_W), sA, sB, c.d_status);
+        else
+            k_tc_gj2_update<false><<<grid, G2_THREADS, G2_SMEM, c.stream>>>(
+                mAh, mAl, mBh, mBl, n, M, lda, nrt, nct, (int)(k0 / G2_W), sA, sB, c.d_status);
         c.tend(PH_LU_UPDATE);
         c.launches += 1;
     }

@@ -108,7 +108,7 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec);
 constexpr int64_t GJ2_MIN_N = 8192;
 bool gj2_supported(const Ctx &c);
 size_t gj2_panel_floats(int64_t n);
-int run_gj2_fp32(Ctx &c, float *M, int64_t lda);
+int run_gj2_fp32(Ctx &c, float *M, int64_t lda, bool f16);
 size_t gj_diag_smem();
 void gj_diag_prepare();
 void k_gj_diag_launch(Ctx &c, int64_t n, const float *M, int64_t lda, int64_t k0, float *Dinv,

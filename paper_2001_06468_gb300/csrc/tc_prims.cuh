@@ -1,7 +1,7 @@
 // tc_prims.cuh -- the tcgen05 / TMA / mbarrier building blocks shared by the
 // tensor-core update kernel (tc_gemm.cu) and the fused factorisation (gj.cu):
 // inline PTX for 128-byte-swizzled K-major operands staged by TMA, kind::tf32
-// MMAs accumulating in tensor memory, and bounded mbarrier waits.
+// and kind::f16 MMAs accumulating in tensor memory, and bounded mbarrier waits.
 #pragma once
 #include <cuda.h>
 
@@ -23,6 +23,12 @@ constexpr uint32_t idesc_tf32(int M, int N)
 {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
+}
+
+// The same for kind::f16 with FP16 A and B (formats 0) and an F32 accumulator.
+constexpr uint32_t idesc_f16(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -97,6 +103,18 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// D (+)= A B^T with FP16 A and B (both the same type) and an FP32 accumulator
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
 }

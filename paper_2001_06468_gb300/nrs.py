@@ -550,7 +550,9 @@ def _make_desc(n_off, q_off, kind, eps, mu=1.0, rigid=None, U=None, Omega=None, 
     d.graph = int(bool(graph))
     d.inner_tol = float(inner_tol)
     d.factor_input = {"fp32": 0, "rounded": 1}[factor_input]
-    d.factor_schedule = {"auto": 0, "fused": 1, "streams": 2, "two_level": 3}[factor_schedule]
+    # two-level updates from split-TF32 operands (3) or scaled FP16 pairs (4)
+    d.factor_schedule = {"auto": 0, "fused": 1, "streams": 2, "two_level_tf32": 3,
+                         "two_level": 4}[factor_schedule]
     # "extended": to about u^2 (exact products, see nrs_residual); "fp64": plain
     d.residual = {"extended": 0, "fp64": 1}[residual]
     return d, (n_off, q_off, kind, rigid, U, Om)

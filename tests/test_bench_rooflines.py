@@ -74,21 +74,30 @@ def test_records_of_every_kernel_family():
         (3 * SOLVE["outer_mean"] + SOLVE["inner_mean"] + 1) * N_SYS ** 2)
 
 
-def test_two_level_factorisation_is_rated_against_the_tensor_peak():
+@pytest.mark.parametrize("f16", [True, False])
+def test_two_level_factorisation_is_rated_against_its_closer_roofline(f16):
     # the two-level schedule has one panel span and one update span per
     # 256-column block and no diagonal-inverse spans; its update is a rank-256
-    # product: 3 split-TF32 passes x 2 n^2 256 flops per launch
+    # product, 3 passes x 2 n^2 256 tensor flops per launch (FP16 pairs at the
+    # BF16 rate, or split TF32 at the derived TF32 rate), which also reads and
+    # writes the FP32 matrix (8 n^2 bytes); the record takes the larger fraction
     nb = -(-N_SYS // 256)
-    ms, spans = _phases(lu_panel=(40.0, nb), lu_update=(265.0, nb), assemble=(220.0, 2))
-    recs = bench.rooflines(ms, spans, N_SYS, PAIRS, PEAKS, "measured", SM_MHZ, SOLVE)
-    u = recs["lu_update"]
-    _check(u)
-    assert u["bound"] == "tensor" and u["unit"] == "TFLOP/s"
-    fl = 3 * 2.0 * N_SYS ** 2 * 256
-    assert u["work_per_launch"] == pytest.approx(fl)
-    assert u["achieved"] == pytest.approx(fl / (265e-3 / nb) / 1e12)
-    assert u["peak"] == pytest.approx(PEAKS["bf16_tflops_sustained"] * 1.1 / 2.25)
-    assert "lu_diag" not in recs and "lu_panel" in recs
+    for upd_ms in (265.0, 40.0):
+        ms, spans = _phases(lu_panel=(40.0, nb), lu_update=(upd_ms, nb), assemble=(220.0, 2))
+        recs = bench.rooflines(ms, spans, N_SYS, PAIRS, PEAKS, "measured", SM_MHZ, SOLVE,
+                               update_f16=f16)
+        u = recs["lu_update"]
+        _check(u)
+        t = upd_ms * 1e-3 / nb
+        fl = 3 * 2.0 * N_SYS ** 2 * 256
+        tp = PEAKS["bf16_tflops_sustained"] * (1.0 if f16 else 1.1 / 2.25)
+        assert u["tensor_tflops"] == pytest.approx(fl / t / 1e12)
+        assert u["tensor_peak"] == pytest.approx(tp)
+        assert u["hbm_gbs"] == pytest.approx(8.0 * N_SYS ** 2 / t / 1e9)
+        tfrac, hfrac = fl / t / 1e12 / tp, 8.0 * N_SYS ** 2 / t / 1e9 / PEAKS["hbm_gbs"]
+        assert u["frac"] == pytest.approx(max(tfrac, hfrac))
+        assert u["bound"] == ("hbm" if hfrac >= tfrac else "tensor")
+        assert "lu_diag" not in recs and "lu_panel" in recs
 
 
 def test_records_are_skipped_for_phases_that_did_not_run():

@@ -182,13 +182,14 @@ def test_fused_factor_matches_streamed(N, name):
 @pytest.mark.parametrize("name", ["swimmer", "sperm2"])
 def test_two_level_factor_matches_the_oracle_and_the_one_level_inverse(N, name):
     # The two-level elimination (256-column blocks, column panel eliminated in
-    # 64-column steps, one rank-256 tensor-core update per block) forms the
-    # same inverse as the one-level one up to FP32 rounding: the refinement
-    # reaches the oracle's answer from it with the same few GMRES iterations.
+    # 64-column steps, one rank-256 tensor-core update per block, from scaled
+    # FP16 pairs or split TF32) forms the same inverse as the one-level one up
+    # to FP32-level rounding: the refinement reaches the oracle's answer from it
+    # with the same few GMRES iterations.
     pr = PROBLEMS[name]()
     A_or = b_or = None
     out = {}
-    for schedule in ("two_level", "streams"):
+    for schedule in ("two_level", "two_level_tf32", "streams"):
         ctx, sh, Y, dev = _setup(N, pr, t=0.25, prec="tf32", factor_schedule=schedule)
         _gpu_system(N, ctx, dev)
         b = ctx.kinematics(*dev)[2]
