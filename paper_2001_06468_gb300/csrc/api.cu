@@ -95,7 +95,7 @@ nrs_status alloc_all(Ctx *c)
         {(void **)&c->d_part32, sizeof(double) * 64 * lda},
         {(void **)&c->d_part_fx, sizeof(unsigned long long) * 3 * 64 * lda},
         {(void **)&c->d_vf, sizeof(float2) * lda},
-        {(void **)&c->d_gj2, gj2 ? sizeof(float) * 4 * nrs::gj2_panel_floats(n) : 0},
+        {(void **)&c->d_gj2, gj2 ? nrs::gj2_workspace_bytes(n) : 0},
         {(void **)&c->d_gj2_r, gj2 ? sizeof(float) * 64 * 256 : 0},
         {(void **)&c->d_t32, sizeof(float) * 2 * lda},
         {(void **)&c->d_t64, sizeof(double) * 2 * lda},

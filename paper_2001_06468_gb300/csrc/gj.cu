@@ -1334,10 +1334,10 @@ void gj_diag_prepare()
 // D^{-1} of the diagonal block at (k0, k0) alone (no lookahead), for the
 // panel elimination of gj2.cu.
 void k_gj_diag_launch(Ctx &c, int64_t n, const float *M, int64_t lda, int64_t k0, float *Dinv,
-                      size_t smem)
+                      size_t smem, cudaStream_t s)
 {
-    k_gj_diag<<<1, 256, smem, c.stream>>>(n, M, lda, k0, Dinv, c.d_info, nullptr, nullptr,
-                                          c.d_status);
+    k_gj_diag<<<1, 256, smem, s ? s : c.stream>>>(n, M, lda, k0, Dinv, c.d_info, nullptr, nullptr,
+                                                 c.d_status);
 }
 
 int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec)

@@ -47,6 +47,10 @@ constexpr uint32_t G2_A_BYTES = G2_BM * G2_KB;                           // 16 K
 constexpr uint32_t G2_B_BYTES = G2_BN * G2_KB;                           // 32 KB
 constexpr uint32_t G2_STAGE_BYTES = 2 * G2_A_BYTES + 2 * G2_B_BYTES;     // 96 KB
 constexpr int G2_STAGES = 2;
+constexpr int G2_RING = 4;                 // claimed tile indices in flight (producer -> MMA, epilogue)
+// SMs the two-level factorisation leaves to the next block's panel elimination
+// while the bulk of the current block's update runs
+constexpr int GJ2_PANEL_SMS = 24;
 constexpr int G2_SMEM = G2_STAGES * G2_STAGE_BYTES + 1024;
 constexpr int G2_EPI_WARPS = 16;         // four per accumulator lane quarter, 64 columns each
 constexpr int G2_THREADS = 64 + 32 * G2_EPI_WARPS;
@@ -57,17 +61,23 @@ __device__ __forceinline__ void g2_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Output tile t of the update: row tile t % nrt, column tile t / nrt
-// counted over the column tiles other than `skip`.
-__device__ __forceinline__ void g2_tile(int64_t t, int nrt, int skip, int &rt, int &ct)
+// Column tiles of one update launch: [c_lo, c_hi) without [s_lo, s_hi) (an
+// empty exclusion has s_lo = s_hi).
+struct G2Cols {
+    int c_lo, c_hi, s_lo, s_hi;
+};
+
+// Output tile t of the update: row tile t % nrt, the (t / nrt)-th column tile
+// of the launch's range.
+__device__ __forceinline__ void g2_tile(int64_t t, int nrt, const G2Cols &cc, int &rt, int &ct)
 {
     rt = (int)(t % nrt);
-    const int c = (int)(t / nrt);
-    ct = c < skip ? c : c + 1;
+    ct = cc.c_lo + (int)(t / nrt);
+    if (ct >= cc.s_lo) ct += cc.s_hi - cc.s_lo;
 }
 
 // M[i, j] += sum_{c < 256} A[i][c] B[j][c] for all rows i < n and the columns
-// j of every 256-wide column tile but `skip`, A = Ah + Al and B = Bh + Bl the
+// j of the 256-wide column tiles `cc`, A = Ah + Al and B = Bh + Bl the
 // split panels (row-major, 256 elements a row), products hi hi + hi lo + lo hi.
 // F16 = false: TF32 pieces (FP32 storage, kind::tf32, 32 K a stage); true:
 // scaled FP16 pieces (kind::f16, 64 K a stage), row i of A and row j of B
@@ -76,21 +86,23 @@ template <bool F16>
 __global__ void __launch_bounds__(G2_THREADS, 1)
     k_tc_gj2_update(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                     const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
-                    int64_t n, float *__restrict__ M, int64_t lda, int nrt, int nct, int skip,
-                    const float *__restrict__ sA, const float *__restrict__ sB, int32_t *status)
+                    int64_t n, float *__restrict__ M, int64_t lda, int nrt, G2Cols cc,
+                    const float *__restrict__ sA, const float *__restrict__ sB,
+                    unsigned long long *__restrict__ claim, int max_tiles, int32_t *status)
 {
     constexpr int KC = F16 ? 64 : 32;      // K elements per stage (128 bytes)
     constexpr int NCH = G2_W / KC;         // stages per tile
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full[G2_STAGES], empty[G2_STAGES], tfull[2], tempty[2], drain;
+    __shared__ uint64_t ifull[G2_RING], iempty[G2_RING];  // the ring of claimed tile indices
+    __shared__ long long s_tile[G2_RING];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
     __shared__ float s_scale[G2_EPI_WARPS][G2_BN / 4];  // FP16 variant: column scales per warp
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t ntiles = (int64_t)nrt * (skip >= 0 && skip < nct ? nct - 1 : nct);
-    const int skip_eff = (skip >= 0 && skip < nct) ? skip : nct;
+    const int64_t ntiles = (int64_t)nrt * ((cc.c_hi - cc.c_lo) - (cc.s_hi - cc.s_lo));
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < G2_STAGES; ++s) {
@@ -100,6 +112,10 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
             mbar_init(&tempty[a], G2_EPI_WARPS);
+        }
+        for (int r = 0; r < G2_RING; ++r) {
+            mbar_init(&ifull[r], 1);
+            mbar_init(&iempty[r], 1 + G2_EPI_WARPS);
         }
         mbar_init(&drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -118,13 +134,31 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
     const uint32_t tmem = tmem_slot;
 
     if (warp == 0) {
-        // ---- producer: TMA loads of the four operand tiles of every stage
+        // ---- producer: claims the next tile from the launch's counter (CTAs
+        // that start late, beside other kernels, simply take fewer tiles; at
+        // most max_tiles), hands its index to the MMA and epilogue warps
+        // through the ring, and loads the four operand tiles of each of its
+        // stages by TMA
         if (lane == 0) {
             int64_t it = 0;
             int last_k[G2_STAGES] = {-1, -1};
-            for (int64_t t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x) {
+            for (int64_t lt = 0; !s_abort; ++lt) {
+                const int r = (int)(lt % G2_RING), ru = (int)(lt / G2_RING);
+                if (!mbar_wait(&iempty[r], (uint32_t)((ru & 1) ^ 1))) {
+                    atomicOr(status, ST_TIMEOUT);
+                    s_abort = 1;
+                    break;
+                }
+                long long t = -1;
+                if (lt < max_tiles) {
+                    t = (long long)atomicAdd(claim, 1ULL);
+                    if (t >= ntiles) t = -1;
+                }
+                s_tile[r] = t;
+                g2_arrive(&ifull[r]);
+                if (t < 0) break;
                 int rt, ct;
-                g2_tile(t, nrt, skip_eff, rt, ct);
+                g2_tile(t, nrt, cc, rt, ct);
                 for (int ch = 0; ch < NCH; ++ch, ++it) {
                     const int s = (int)(it & 1), k = (int)(it >> 1);
                     if (!mbar_wait(&empty[s], (uint32_t)((k & 1) ^ 1))) {
@@ -141,7 +175,6 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
                                 &full[s]);
                     last_k[s] = k;
                 }
-                if (s_abort) break;
             }
             if (s_abort) {
                 // the copies already issued land by themselves: wait for them
@@ -154,9 +187,17 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
         if (lane == 0) {
             constexpr uint32_t idesc = F16 ? idesc_f16(G2_BM, G2_BN) : idesc_tf32(G2_BM, G2_BN);
             int64_t it = 0;
-            int lt = 0;
-            for (int64_t t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x, ++lt) {
-                const int a = lt & 1, u = lt >> 1;
+            for (int64_t lt = 0; !s_abort; ++lt) {
+                const int r = (int)(lt % G2_RING), ru = (int)(lt / G2_RING);
+                if (!mbar_wait(&ifull[r], (uint32_t)(ru & 1))) {
+                    atomicOr(status, ST_TIMEOUT);
+                    s_abort = 1;
+                    break;
+                }
+                const long long t = s_tile[r];
+                g2_arrive(&iempty[r]);
+                if (t < 0) break;
+                const int a = (int)(lt & 1), u = (int)(lt >> 1);
                 if (!mbar_wait(&tempty[a], (uint32_t)((u & 1) ^ 1))) {
                     atomicOr(status, ST_TIMEOUT);
                     s_abort = 1;
@@ -205,9 +246,10 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
         // ---- epilogue: warp w reads accumulator lanes 32 (w % 4) .. + 31 (the
         // quarter its rank in the warpgroup may access) and 64 of the 256
         // columns, 16 at a time; the next 16 columns of M (of this tile, or the
-        // first ones of the CTA's next tile) are loaded while the current ones
-        // are added and stored.  The FP16 variant's column scales of the tile
-        // are staged once per tile in shared memory.
+        // first ones of the CTA's next tile when its index is already out) are
+        // loaded while the current ones are added and stored.  The FP16
+        // variant's column scales of the tile are staged once per tile in
+        // shared memory.
         constexpr int CW = 16, CPW = G2_BN / 4, NCHK = CPW / CW;
         const int q = warp & 3, part = (warp - 2) >> 2;
         float *scl = s_scale[warp - 2];
@@ -216,7 +258,7 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
         bool live = false;
         auto setup = [&](int64_t tt) {
             int rt, ct;
-            g2_tile(tt, nrt, skip_eff, rt, ct);
+            g2_tile(tt, nrt, cc, rt, ct);
             row = (int64_t)rt * G2_BM + q * 32 + lane;
             col0 = (int64_t)ct * G2_BN + part * CPW;
             p = M + row + col0 * lda;
@@ -224,15 +266,30 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
             live = row < n;
         };
         float cur[CW], nxt[CW];
-        if ((int64_t)blockIdx.x < ntiles) {
-            setup(blockIdx.x);
+        bool prefetched = false;  // cur holds the first columns of the next tile
+        for (int64_t lt = 0;; ++lt) {
+            const int r = (int)(lt % G2_RING), ru = (int)(lt / G2_RING);
+            const bool gi = mbar_wait(&ifull[r], (uint32_t)(ru & 1));
+            if (!__all_sync(0xffffffffu, gi) || s_abort) {
+                if (lane == 0) {
+                    atomicOr(status, ST_TIMEOUT);
+                    s_abort = 1;
+                }
+                break;
+            }
+            const long long t = s_tile[r];
+            __syncwarp();
+            if (lane == 0) g2_arrive(&iempty[r]);
+            if (t < 0) break;
+            if (!prefetched) {
+                setup(t);
 #pragma unroll
-            for (int j = 0; j < CW; ++j) cur[j] = (live && j < ncol) ? __ldcs(p + j * lda) : 0.0f;
-        }
-        int lt = 0;
-        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
-            const int a = lt & 1, u = lt >> 1;
-            // this tile's geometry (setup() moves on to the next tile below)
+                for (int j = 0; j < CW; ++j)
+                    cur[j] = (live && j < ncol) ? __ldcs(p + j * lda) : 0.0f;
+            }
+            prefetched = false;
+            const int a = (int)(lt & 1), u = (int)(lt >> 1);
+            // this tile's geometry (setup() may move on to the next tile below)
             float *const pt = p;
             const int64_t nc = ncol, c0 = col0;
             const bool lv = live;
@@ -262,11 +319,19 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
 #pragma unroll
                     for (int j = 0; j < CW; ++j)
                         nxt[j] = (lv && (chunk + 1) * CW + j < nc) ? __ldcs(pn + j * lda) : 0.0f;
-                } else if (t + (int64_t)gridDim.x < ntiles) {
-                    setup(t + gridDim.x);
+                } else {
+                    // the next tile's first columns, if its index is already out
+                    const int r2 = (int)((lt + 1) % G2_RING), ru2 = (int)((lt + 1) / G2_RING);
+                    const bool ready =
+                        __all_sync(0xffffffffu, mbar_try_wait(&ifull[r2], (uint32_t)(ru2 & 1)));
+                    const long long t2 = ready ? s_tile[r2] : -1;
+                    if (t2 >= 0) {
+                        setup(t2);
 #pragma unroll
-                    for (int j = 0; j < CW; ++j)
-                        nxt[j] = (live && j < ncol) ? __ldcs(p + j * lda) : 0.0f;
+                        for (int j = 0; j < CW; ++j)
+                            nxt[j] = (live && j < ncol) ? __ldcs(p + j * lda) : 0.0f;
+                        prefetched = true;
+                    }
                 }
                 tmem_wait_ld();
                 float *pc = pt + (int64_t)chunk * CW * lda;
@@ -427,21 +492,22 @@ __global__ void __launch_bounds__(256)
 }
 
 // The product's operands, split into TF32 hi (cvt.rna) and lo = x - hi:
-//   blockIdx.y <  4: A[i][c] = M[i, k0 + c] - (i == k0 + c) for c < W (0 for c >= W
-//                    and rows >= n), 64 rows x 64 columns a CTA through shared memory;
-//   blockIdx.y == 4: B[j][c] = M[k0 + c, j] for c < W, j outside [k0, k0 + W)
-//                    (0 otherwise), 64 columns j a CTA: one contiguous run of M each.
+//   bpart = 0: A[i][c] = M[i, k0 + c] - (i == k0 + c) for c < W (0 for c >= W
+//              and rows >= n), 64 rows x 64 columns (blockIdx.y) a CTA through
+//              shared memory (grid.y = 4);
+//   bpart = 1: B[j][c] = M[k0 + c, j] for c < W, j outside [k0, k0 + W)
+//              (0 otherwise), 64 columns j a CTA: one contiguous run of M each.
 // Both row-major with 256 floats a row, rows up to `rows_pad`.
 __global__ void __launch_bounds__(256)
     k_gj2_prep(int64_t n, const float *__restrict__ M, int64_t lda, int64_t k0, int W,
-               int64_t rows_pad, float *__restrict__ Ah, float *__restrict__ Al,
+               int64_t rows_pad, int bpart, float *__restrict__ Ah, float *__restrict__ Al,
                float *__restrict__ Bh, float *__restrict__ Bl)
 {
     __shared__ float T[64][65];
     const int tid = threadIdx.x;
     const int64_t i0 = (int64_t)blockIdx.x * 64;
     if (i0 >= rows_pad) return;
-    if (blockIdx.y < 4) {
+    if (!bpart) {
         const int c0 = blockIdx.y * 64;
         for (int idx = tid; idx < 64 * 64; idx += 256) {
             const int r = idx & 63, c = idx >> 6;
@@ -499,14 +565,14 @@ __device__ __forceinline__ void split_f16(float x, __half &hi, __half &lo)
 // [2^14, 2^15) -- so no piece overflows FP16 and the low pieces stay above
 // its subnormal range except for entries below 2^-24 of their row's maximum --
 // then split (split_f16); sA[i] = 2^-e_i, sB[j] = 2^-f_j.
-//   blockIdx.y == 0: A rows [64 blockIdx.x, +64): the row maxima first (a
-//                    thread per row and quarter of the 256 columns), then 64 x
-//                    64 column chunks transposed through shared memory;
-//   blockIdx.y == 1: B rows j in [64 blockIdx.x, +64), a warp per 8 of them.
+//   bpart = 0: A rows [64 blockIdx.x, +64): the row maxima first (a thread
+//              per row and quarter of the 256 columns), then 64 x 64 column
+//              chunks transposed through shared memory;
+//   bpart = 1: B rows j in [64 blockIdx.x, +64), a warp per 8 of them.
 // Both row-major with 256 halves a row, rows up to `rows_pad`.
 __global__ void __launch_bounds__(256)
     k_gj2_prep16(int64_t n, const float *__restrict__ M, int64_t lda, int64_t k0, int W,
-                 int64_t rows_pad, __half *__restrict__ Ah, __half *__restrict__ Al,
+                 int64_t rows_pad, int bpart, __half *__restrict__ Ah, __half *__restrict__ Al,
                  __half *__restrict__ Bh, __half *__restrict__ Bl, float *__restrict__ sA,
                  float *__restrict__ sB)
 {
@@ -516,7 +582,7 @@ __global__ void __launch_bounds__(256)
     const int tid = threadIdx.x;
     const int64_t i0 = (int64_t)blockIdx.x * 64;
     if (i0 >= rows_pad) return;
-    if (blockIdx.y == 0) {
+    if (!bpart) {
         {
             const int r = tid & 63, qc = tid >> 6;
             const int64_t i = i0 + r;
@@ -640,12 +706,33 @@ size_t gj2_panel_floats(int64_t n)
     return (size_t)ceil_div(n, G2_BN) * G2_BN * G2_W;
 }
 
+size_t gj2_workspace_bytes(int64_t n)
+{
+    // two A panels (hi, lo) and one B panel (hi, lo) of FP32 at most, and the
+    // FP16 variant's three scale vectors
+    // and the update launches' tile-claim counters (two per block)
+    return 6 * sizeof(float) * gj2_panel_floats(n) +
+           3 * sizeof(float) * ceil_div(n, G2_BN) * G2_BN +
+           2 * sizeof(unsigned long long) * ceil_div(n, G2_BN);
+}
+
 // The two-level factorisation of the FP32 matrix M (n x n, column-major) in
-// place; the split panels live in c.d_gj2 (4 x gj2_panel_floats(n) floats: the
-// FP16 variant uses half of it for the panels and two scale vectors after
-// them), the inner scaled block row in c.d_gj2_r (64 x 256 floats).  f16: the
-// update's products from scaled FP16 pieces instead of TF32 ones.  Returns 0,
-// or -1 if the tensor maps could not be made.
+// place, in c.d_gj2 (gj2_workspace_bytes(n)): the A operand (the eliminated
+// panel G - I_K, split) in two buffers, the B operand (the block row, split),
+// and for the FP16 pieces the scales; the inner scaled block row in c.d_gj2_r
+// (64 x 256 floats).  f16: the update's products from scaled FP16 pieces
+// instead of TF32 ones.  Returns 0, or -1 if the tensor maps could not be made.
+//
+// Schedule, block b = columns K_b (stream S = c.stream2, U = c.stream):
+//   S: [wait N_{b-1}] panel elimination of K_b, A operand of b -> event A
+//   U: [wait A] B operand of b (block row M[K_b, :]); the update of the
+//      columns K_{b+1} alone -> event N_b; the update of every other column
+//      tile but K_b, on all SMs but GJ2_PANEL_SMS
+// so the panel of b + 1 runs beside the bulk of the update of b.  The panel
+// touches only the columns K_{b+1}, which the bulk does not; the B operand of
+// b + 1 reads the block row after the bulk of b, in stream order.  The A
+// operand alternates between its two buffers: S writes that of b + 1 after
+// N_b, which U records after the bulk of b - 1 (the last reader of that buffer).
 int run_gj2_fp32(Ctx &c, float *M, int64_t lda, bool f16)
 {
     const int64_t n = c.n;
@@ -653,14 +740,24 @@ int run_gj2_fp32(Ctx &c, float *M, int64_t lda, bool f16)
     const size_t pf = gj2_panel_floats(n);
     const size_t es = f16 ? 2 : 4;
     uint8_t *w = reinterpret_cast<uint8_t *>(c.d_gj2);
-    void *Ah = w, *Al = w + pf * es, *Bh = w + 2 * pf * es, *Bl = w + 3 * pf * es;
-    // the FP16 variant's row and column scales, after its panels
-    float *sA = f16 ? reinterpret_cast<float *>(w + 4 * pf * es) : nullptr;
-    float *sB = f16 ? sA + rows_pad : nullptr;
-    CUtensorMap mAh, mAl, mBh, mBl;
-    if (!make_panel256_map(&mAh, Ah, rows_pad, G2_BM, f16) ||
-        !make_panel256_map(&mAl, Al, rows_pad, G2_BM, f16) ||
-        !make_panel256_map(&mBh, Bh, rows_pad, G2_BN, f16) ||
+    void *Ah[2] = {w, w + 2 * pf * es}, *Al[2] = {w + pf * es, w + 3 * pf * es};
+    void *Bh = w + 4 * pf * es, *Bl = w + 5 * pf * es;
+    // the FP16 variant's row scales (one vector per A buffer) and column
+    // scales, then the update launches' tile-claim counters
+    float *sA[2] = {nullptr, nullptr}, *sB = nullptr;
+    unsigned long long *claims = reinterpret_cast<unsigned long long *>(
+        w + 6 * pf * sizeof(float) + 3 * sizeof(float) * rows_pad);
+    if (f16) {
+        sA[0] = reinterpret_cast<float *>(w + 6 * pf * es);
+        sA[1] = sA[0] + rows_pad;
+        sB = sA[1] + rows_pad;
+    }
+    CUtensorMap mAh[2], mAl[2], mBh, mBl;
+    for (int k = 0; k < 2; ++k)
+        if (!make_panel256_map(&mAh[k], Ah[k], rows_pad, G2_BM, f16) ||
+            !make_panel256_map(&mAl[k], Al[k], rows_pad, G2_BM, f16))
+            return -1;
+    if (!make_panel256_map(&mBh, Bh, rows_pad, G2_BN, f16) ||
         !make_panel256_map(&mBl, Bl, rows_pad, G2_BN, f16))
         return -1;
     static bool attr = false;
@@ -675,37 +772,84 @@ int run_gj2_fp32(Ctx &c, float *M, int64_t lda, bool f16)
     gj_diag_prepare();
     cudaMemsetAsync(c.d_info, 0, sizeof(int32_t), c.stream);
     const int nrt = (int)ceil_div(n, G2_BM), nct = (int)ceil_div(n, G2_BN);
-    const int64_t tiles = (int64_t)nrt * (nct - 1);
-    const int grid = (int)std::min<int64_t>(tiles, c.num_sms);
-    for (int64_t k0 = 0; k0 < n; k0 += G2_W) {
+    const unsigned gx = (unsigned)ceil_div(rows_pad, 64);
+    cudaStream_t S = c.stream2, U = c.stream;
+
+    auto panel = [&](int b) {
+        const int64_t k0 = (int64_t)b * G2_W;
         const int W = (int)std::min<int64_t>(G2_W, n - k0);
-        c.tbeg(PH_LU_PANEL);
+        const int buf = b & 1;
+        c.tbeg(PH_LU_PANEL, S);
         for (int64_t r0 = k0; r0 < k0 + W; r0 += 64) {
-            k_gj_diag_launch(c, n, M, lda, r0, c.d_gj_dinv, diag_smem);
-            k_gj2_rpanel<<<(unsigned)ceil_div(W, 64), 256, 0, c.stream>>>(n, M, lda, k0, W, r0,
-                                                                         c.d_gj_dinv, c.d_gj2_r);
-            k_gj2_panel_update<<<(unsigned)ceil_div(n, 64), 256, 0, c.stream>>>(
-                n, M, lda, k0, W, r0, c.d_gj_dinv, c.d_gj2_r);
+            k_gj_diag_launch(c, n, M, lda, r0, c.d_gj_dinv, diag_smem, S);
+            k_gj2_rpanel<<<(unsigned)ceil_div(W, 64), 256, 0, S>>>(n, M, lda, k0, W, r0,
+                                                                 c.d_gj_dinv, c.d_gj2_r);
+            k_gj2_panel_update<<<(unsigned)ceil_div(n, 64), 256, 0, S>>>(n, M, lda, k0, W, r0,
+                                                                       c.d_gj_dinv, c.d_gj2_r);
             c.launches += 3;
         }
         if (f16)
-            k_gj2_prep16<<<dim3((unsigned)ceil_div(rows_pad, 64), 2), 256, 0, c.stream>>>(
-                n, M, lda, k0, W, rows_pad, (__half *)Ah, (__half *)Al, (__half *)Bh, (__half *)Bl,
-                sA, sB);
+            k_gj2_prep16<<<gx, 256, 0, S>>>(n, M, lda, k0, W, rows_pad, 0, (__half *)Ah[buf],
+                                            (__half *)Al[buf], nullptr, nullptr, sA[buf], nullptr);
         else
-            k_gj2_prep<<<dim3((unsigned)ceil_div(rows_pad, 64), 5), 256, 0, c.stream>>>(
-                n, M, lda, k0, W, rows_pad, (float *)Ah, (float *)Al, (float *)Bh, (float *)Bl);
+            k_gj2_prep<<<dim3(gx, 4), 256, 0, S>>>(n, M, lda, k0, W, rows_pad, 0,
+                                                  (float *)Ah[buf], (float *)Al[buf], nullptr,
+                                                  nullptr);
         c.launches += 1;
-        c.tend(PH_LU_PANEL);
-        c.tbeg(PH_LU_UPDATE);
+        c.tend(PH_LU_PANEL, S);
+        cudaEventRecord(c.ev_diag, S);  // A operand of b ready
+    };
+    // Each update launch claims its tiles from its own counter (zeroed once
+    // per factorisation).  The bulk leaves GJ2_PANEL_SMS SMs to the next
+    // block's panel kernels (on the higher-priority stream S); its CTAs are
+    // persistent and claim tiles until none are left, so CTAs that start late
+    // simply take fewer.
+    int launch = 0;
+    auto update = [&](int b, G2Cols cc, bool bulk) {
+        const int buf = b & 1;
+        const int64_t tiles = (int64_t)nrt * ((cc.c_hi - cc.c_lo) - (cc.s_hi - cc.s_lo));
+        const int sms = bulk ? std::max(1, c.num_sms - GJ2_PANEL_SMS) : c.num_sms;
+        const int grid = (int)std::min<int64_t>(tiles, sms);
+        const int cap = (int)tiles;  // no cap: the CTAs run until the counter is spent
+        unsigned long long *ctr = claims + launch++;
         if (f16)
-            k_tc_gj2_update<true><<<grid, G2_THREADS, G2_SMEM, c.stream>>>(
-                mAh, mAl, mBh, mBl, n, M, lda, nrt, nct, (int)(k0 / G2_W), sA, sB, c.d_status);
+            k_tc_gj2_update<true><<<grid, G2_THREADS, G2_SMEM, U>>>(
+                mAh[buf], mAl[buf], mBh, mBl, n, M, lda, nrt, cc, sA[buf], sB, ctr, cap,
+                c.d_status);
         else
-            k_tc_gj2_update<false><<<grid, G2_THREADS, G2_SMEM, c.stream>>>(
-                mAh, mAl, mBh, mBl, n, M, lda, nrt, nct, (int)(k0 / G2_W), sA, sB, c.d_status);
-        c.tend(PH_LU_UPDATE);
+            k_tc_gj2_update<false><<<grid, G2_THREADS, G2_SMEM, U>>>(
+                mAh[buf], mAl[buf], mBh, mBl, n, M, lda, nrt, cc, nullptr, nullptr, ctr, cap,
+                c.d_status);
         c.launches += 1;
+    };
+
+    cudaMemsetAsync(claims, 0, sizeof(unsigned long long) * 2 * nct, U);
+    cudaEventRecord(c.ev_fin_ready, U);  // the FP32 matrix is ready
+    cudaStreamWaitEvent(S, c.ev_fin_ready, 0);
+    panel(0);
+    for (int b = 0; b < nct; ++b) {
+        const int64_t k0 = (int64_t)b * G2_W;
+        const int W = (int)std::min<int64_t>(G2_W, n - k0);
+        cudaStreamWaitEvent(U, c.ev_diag, 0);
+        c.tbeg(PH_LU_UPDATE, U);
+        if (f16)
+            k_gj2_prep16<<<gx, 256, 0, U>>>(n, M, lda, k0, W, rows_pad, 1, nullptr, nullptr,
+                                            (__half *)Bh, (__half *)Bl, nullptr, sB);
+        else
+            k_gj2_prep<<<dim3(gx, 1), 256, 0, U>>>(n, M, lda, k0, W, rows_pad, 1, nullptr,
+                                                  nullptr, (float *)Bh, (float *)Bl);
+        c.launches += 1;
+        const bool next = b + 1 < nct;
+        if (next) {
+            update(b, G2Cols{b + 1, b + 2, b + 2, b + 2}, false);
+            cudaEventRecord(c.ev_upd, U);  // the columns of K_{b+1} are up to date
+            cudaStreamWaitEvent(S, c.ev_upd, 0);
+            panel(b + 1);
+        }
+        // every other column tile but K_b (and K_{b+1}, done above)
+        const int s_hi = next ? b + 2 : b + 1;
+        if ((nct - (s_hi - b)) > 0) update(b, G2Cols{0, nct, b, s_hi}, true);
+        c.tend(PH_LU_UPDATE, U);
     }
     return 0;
 }

@@ -108,11 +108,12 @@ int run_gj_fp32(Ctx &c, float *M, int64_t lda, int prec);
 constexpr int64_t GJ2_MIN_N = 8192;
 bool gj2_supported(const Ctx &c);
 size_t gj2_panel_floats(int64_t n);
+size_t gj2_workspace_bytes(int64_t n);
 int run_gj2_fp32(Ctx &c, float *M, int64_t lda, bool f16);
 size_t gj_diag_smem();
 void gj_diag_prepare();
 void k_gj_diag_launch(Ctx &c, int64_t n, const float *M, int64_t lda, int64_t k0, float *Dinv,
-                      size_t smem);
+                      size_t smem, cudaStream_t s = nullptr);
 
 bool tc_available();
 bool launch_tc_rank64(Ctx &c, float *M, int64_t lda, int64_t n, const float *Cb, const float *Rt,
@@ -240,7 +241,7 @@ struct Ctx {
     float *d_gj_rt = nullptr;      //   scaled block row, transposed (2 buffers of n x 64, then their TF32 lo parts)
     float *d_gj_cb = nullptr;      //   block column (2 buffers of n x 64, then their TF32 lo parts)
     float *d_gj_stage = nullptr;   //   two finished 64 x 64 tiles (2 buffers)
-    float *d_gj2 = nullptr;        //   two-level factorisation: split panels (4 x gj2_panel_floats)
+    float *d_gj2 = nullptr;        //   two-level factorisation: operands (gj2_workspace_bytes)
     float *d_gj2_r = nullptr;      //   its inner scaled block row (64 x 256)
     int32_t *d_gj_sync = nullptr;  //   counters of the fused factorisation (4)
     bool gj_fused = false;         //   use the fused (one-launch) factorisation when possible
