@@ -127,3 +127,9 @@ def test_traffic_records_name_existing_sources():
         assert os.path.exists(os.path.join(bench.ROOT, rec["file"])), kernel
         if rec["bytes"] is not None:
             assert len(rec["sha1"]) == 12, kernel
+
+
+def test_spans_alone_excludes_overlapping_launches():
+    tr = [("assemble", 0.0, 10.0), ("lu_update", 5.0, 20.0), ("assemble", 30.0, 40.0),
+          ("krylov", 35.0, 50.0), ("assemble", 60.0, 65.0), ("lu_panel", 65.0, 70.0)]
+    assert bench.spans_alone(tr, "assemble", ("lu_update", "lu_panel")) == [10.0, 5.0]
