@@ -76,6 +76,26 @@ __device__ __forceinline__ void g2_tile(int64_t t, int nrt, const G2Cols &cc, in
     if (ct >= cc.s_lo) ct += cc.s_hi - cc.s_lo;
 }
 
+// L2 prefetch of the lines of M that epilogue warp (lane quarter q, column
+// part `part`) of tile t will read: 32 rows x 4 bytes = one 128-byte line per
+// column, lane l taking columns l and l + 32 of the part's 64.  Only lines
+// whose first row is below n (and so whole inside the column's lda rows).
+__device__ __forceinline__ void l2_prefetch_part(const float *M, int64_t lda, int64_t n,
+                                                 int64_t t, int nrt, const G2Cols &cc, int q,
+                                                 int part, int lane)
+{
+    int rt, ct;
+    g2_tile(t, nrt, cc, rt, ct);
+    const int64_t r0 = (int64_t)rt * G2_BM + q * 32;
+    if (r0 >= n) return;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int64_t col = (int64_t)ct * G2_BN + part * (G2_BN / 4) + lane + 32 * k;
+        if (col < n)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(M + r0 + col * lda) : "memory");
+    }
+}
+
 // M[i, j] += sum_{c < 256} A[i][c] B[j][c] for all rows i < n and the columns
 // j of the 256-wide column tiles `cc`, A = Ah + Al and B = Bh + Bl the
 // split panels (row-major, 256 elements a row), products hi hi + hi lo + lo hi.
@@ -288,6 +308,19 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
                     cur[j] = (live && j < ncol) ? __ldcs(p + j * lda) : 0.0f;
             }
             prefetched = false;
+            // L2 prefetch of this warp's lines of the tile (one 128-byte line per
+            // column: 32 rows of the lane quarter), and of the next tile's when
+            // its index is already out, so the loads of M below hit L2 (the
+            // FP16 variant, whose products leave the epilogue as the bound;
+            // measured slower for the TF32 one)
+            if (F16) {
+                l2_prefetch_part(M, lda, n, t, nrt, cc, q, part, lane);
+                const int r2 = (int)((lt + 1) % G2_RING), ru2 = (int)((lt + 1) / G2_RING);
+                if (__all_sync(0xffffffffu, mbar_try_wait(&ifull[r2], (uint32_t)(ru2 & 1)))) {
+                    const long long t2 = s_tile[r2];
+                    if (t2 >= 0) l2_prefetch_part(M, lda, n, t2, nrt, cc, q, part, lane);
+                }
+            }
             const int a = (int)(lt & 1), u = (int)(lt >> 1);
             // this tile's geometry (setup() may move on to the next tile below)
             float *const pt = p;
