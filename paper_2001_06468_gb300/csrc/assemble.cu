@@ -159,82 +159,176 @@ __global__ void k_split_points(int64_t count, const D4 *__restrict__ p, float4 *
 // The FP32 copy that the factorisation inverts, on its own: the same sums in
 // FP32, with x_m - X_q = (x_hi - X_hi) + (x_lo - X_lo) from the float pairs
 // (the hi difference is exact for points closer than their own magnitude),
-// so each entry carries a few FP32 roundings.
+// so each entry carries a few FP32 roundings.  Each thread owns two
+// collocation points (m and m + AS_THREADS) and evaluates their two pairs with
+// each staged quadrature point side by side in packed FP32x2 instructions; the
+// staged weights carry the factor 1/(8 pi mu); per segment the thread
+// accumulates r_j r_k t (six sums) and t, and the diagonal term
+// (|r|^2 + 2 eps^2) t is formed at the flush as (r_x^2 + r_y^2 + r_z^2) t +
+// 2 eps^2 t from those sums.
+constexpr int AS32_M = 2 * AS_THREADS;  // collocation points of a CTA
+constexpr int AS32_CHUNK = 256;         // quadrature points staged at a time
+
+// Packed FP32 arithmetic (two lanes of one 64-bit register per instruction,
+// sm_100 and later): the thread's two collocation points go through the same
+// operations side by side, halving the instructions of the pair loop.
+struct F2 {
+    float a, b;
+};
+
+__device__ __forceinline__ F2 f2_add(F2 x, F2 y)
+{
+    F2 d;
+    asm("{\n\t.reg .b64 p, q, r;\n\t"
+        "mov.b64 p, {%2, %3};\n\tmov.b64 q, {%4, %5};\n\t"
+        "add.rn.f32x2 r, p, q;\n\tmov.b64 {%0, %1}, r;\n\t}"
+        : "=f"(d.a), "=f"(d.b)
+        : "f"(x.a), "f"(x.b), "f"(y.a), "f"(y.b));
+    return d;
+}
+
+__device__ __forceinline__ F2 f2_sub(F2 x, F2 y)
+{
+    F2 d;
+    asm("{\n\t.reg .b64 p, q, r;\n\t"
+        "mov.b64 p, {%2, %3};\n\tmov.b64 q, {%4, %5};\n\t"
+        "sub.rn.f32x2 r, p, q;\n\tmov.b64 {%0, %1}, r;\n\t}"
+        : "=f"(d.a), "=f"(d.b)
+        : "f"(x.a), "f"(x.b), "f"(y.a), "f"(y.b));
+    return d;
+}
+
+__device__ __forceinline__ F2 f2_mul(F2 x, F2 y)
+{
+    F2 d;
+    asm("{\n\t.reg .b64 p, q, r;\n\t"
+        "mov.b64 p, {%2, %3};\n\tmov.b64 q, {%4, %5};\n\t"
+        "mul.rn.f32x2 r, p, q;\n\tmov.b64 {%0, %1}, r;\n\t}"
+        : "=f"(d.a), "=f"(d.b)
+        : "f"(x.a), "f"(x.b), "f"(y.a), "f"(y.b));
+    return d;
+}
+
+// x y + z
+__device__ __forceinline__ F2 f2_fma(F2 x, F2 y, F2 z)
+{
+    F2 d;
+    asm("{\n\t.reg .b64 p, q, r, o;\n\t"
+        "mov.b64 p, {%2, %3};\n\tmov.b64 q, {%4, %5};\n\tmov.b64 r, {%6, %7};\n\t"
+        "fma.rn.f32x2 o, p, q, r;\n\tmov.b64 {%0, %1}, o;\n\t}"
+        : "=f"(d.a), "=f"(d.b)
+        : "f"(x.a), "f"(x.b), "f"(y.a), "f"(y.b), "f"(z.a), "f"(z.b));
+    return d;
+}
+
+// A quadrature point staged for the packed loop: every component twice (one
+// register pair per operand), the weight times 1/(8 pi mu).
+struct alignas(16) StagedQ {
+    F2 hx, hy, hz, w;
+    F2 lx, ly, lz, pad;
+};
+
 __global__ void __launch_bounds__(AS_THREADS)
     k_assemble32(int64_t N, const float4 *__restrict__ xh, const float4 *__restrict__ xl,
                  const float4 *__restrict__ Xh, const float4 *__restrict__ Xl,
                  const int32_t *__restrict__ seg_ptr, float eps2, float c, float *__restrict__ A32,
                  int64_t lda)
 {
-    __shared__ float4 sH[AS_CHUNK], sL[AS_CHUNK];
+    __shared__ StagedQ sQ[AS32_CHUNK];
     __shared__ int32_t sp[AS_NT + 1];
-    const int64_t m = (int64_t)blockIdx.x * AS_THREADS + threadIdx.x;
+    const int64_t m0 = (int64_t)blockIdx.x * AS32_M + threadIdx.x, m1 = m0 + AS_THREADS;
     const int64_t n0 = (int64_t)blockIdx.y * AS_NT;
     const int nt = (int)min((int64_t)AS_NT, N - n0);
     if (threadIdx.x <= nt) sp[threadIdx.x] = seg_ptr[n0 + threadIdx.x];
-    const bool active = m < N;
-    float4 ph = make_float4(0.f, 0.f, 0.f, 0.f), pl = ph;
-    if (active) {
-        ph = xh[m];
-        pl = xl[m];
+    const bool act0 = m0 < N, act1 = m1 < N;
+    float4 ph0 = make_float4(0.f, 0.f, 0.f, 0.f), pl0 = ph0, ph1 = ph0, pl1 = ph0;
+    if (act0) {
+        ph0 = xh[m0];
+        pl0 = xl[m0];
     }
+    if (act1) {
+        ph1 = xh[m1];
+        pl1 = xl[m1];
+    }
+    const F2 px{ph0.x, ph1.x}, py{ph0.y, ph1.y}, pz{ph0.z, ph1.z};
+    const F2 qx{pl0.x, pl1.x}, qy{pl0.y, pl1.y}, qz{pl0.z, pl1.z};
+    const F2 e2{eps2, eps2};
     const float two_e2 = 2.0f * eps2;
-    float axx = 0, axy = 0, axz = 0, ayy = 0, ayz = 0, azz = 0, ad = 0;
+    const F2 zero{0.0f, 0.0f};
+    F2 axx = zero, axy = zero, axz = zero, ayy = zero, ayz = zero, azz = zero, at = zero;
     auto flush = [&](int64_t nn) {
-        const float v[9] = {c * (axx + ad), c * axy,        c * axz,
-                            c * axy,        c * (ayy + ad), c * ayz,
-                            c * axz,        c * ayz,        c * (azz + ad)};
+        const float xx[2] = {axx.a, axx.b}, xy[2] = {axy.a, axy.b}, xz[2] = {axz.a, axz.b};
+        const float yy[2] = {ayy.a, ayy.b}, yz[2] = {ayz.a, ayz.b}, zz[2] = {azz.a, azz.b};
+        const float tt[2] = {at.a, at.b};
+        const int64_t ms[2] = {m0, m1};
+        const bool act[2] = {act0, act1};
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int64_t col = (3 * nn + k) * lda + 3 * m;
+        for (int h = 0; h < 2; ++h) {
+            if (!act[h]) continue;
+            const float d = fmaf(two_e2, tt[h], (xx[h] + yy[h]) + zz[h]);
+            const float v[9] = {xx[h] + d, xy[h], xz[h], xy[h], yy[h] + d, yz[h],
+                                xz[h], yz[h], zz[h] + d};
 #pragma unroll
-            for (int j = 0; j < 3; ++j) A32[col + j] = v[3 * j + k];
+            for (int k = 0; k < 3; ++k) {
+                const int64_t col = (3 * nn + k) * lda + 3 * ms[h];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) A32[col + j] = v[3 * j + k];
+            }
         }
+        axx = axy = axz = ayy = ayz = azz = at = zero;
     };
     __syncthreads();
     int cur = 0;
     const int32_t qbeg = sp[0], qend = sp[nt];
-    for (int32_t c0 = qbeg; c0 < qend; c0 += AS_CHUNK) {
-        const int cnt = min(AS_CHUNK, qend - c0);
+    for (int32_t c0 = qbeg; c0 < qend; c0 += AS32_CHUNK) {
+        const int cnt = min(AS32_CHUNK, qend - c0);
         const int32_t cend = c0 + cnt;
         __syncthreads();
         for (int i = threadIdx.x; i < cnt; i += AS_THREADS) {
-            sH[i] = Xh[c0 + i];
-            sL[i] = Xl[c0 + i];
+            const float4 h = Xh[c0 + i], l = Xl[c0 + i];
+            const float w = h.w * c;  // the weight carries 1/(8 pi mu)
+            StagedQ v;
+            v.hx = F2{h.x, h.x};
+            v.hy = F2{h.y, h.y};
+            v.hz = F2{h.z, h.z};
+            v.w = F2{w, w};
+            v.lx = F2{l.x, l.x};
+            v.ly = F2{l.y, l.y};
+            v.lz = F2{l.z, l.z};
+            v.pad = F2{0.0f, 0.0f};
+            sQ[i] = v;
         }
         __syncthreads();
-        // segment by segment (bounds uniform across the block), so that the
-        // loop over a segment's points has no branch and the independent work
-        // of consecutive points overlaps; the sums still run in ascending q
+        // segment by segment (bounds uniform across the block), the sums in
+        // ascending q
         while (cur < nt) {
             const int32_t sb = max(sp[cur], c0), se = min(sp[cur + 1], cend);
-#pragma unroll 4
+#pragma unroll 2
             for (int32_t q = sb; q < se; ++q) {
-                const float4 H = sH[q - c0], Lo = sL[q - c0];
-                const float rx = (ph.x - H.x) + (pl.x - Lo.x);
-                const float ry = (ph.y - H.y) + (pl.y - Lo.y);
-                const float rz = (ph.z - H.z) + (pl.z - Lo.z);
-                const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                const float inv = rsqrtf(r2 + eps2);
-                const float t = H.w * (inv * inv * inv);
-                const float tx = rx * t, ty = ry * t, tz = rz * t;
-                axx = fmaf(rx, tx, axx);
-                axy = fmaf(rx, ty, axy);
-                axz = fmaf(rx, tz, axz);
-                ayy = fmaf(ry, ty, ayy);
-                ayz = fmaf(ry, tz, ayz);
-                azz = fmaf(rz, tz, azz);
-                ad = fmaf(r2 + two_e2, t, ad);
+                const StagedQ Q = sQ[q - c0];
+                const F2 rx = f2_add(f2_sub(px, Q.hx), f2_sub(qx, Q.lx));
+                const F2 ry = f2_add(f2_sub(py, Q.hy), f2_sub(qy, Q.ly));
+                const F2 rz = f2_add(f2_sub(pz, Q.hz), f2_sub(qz, Q.lz));
+                const F2 r2 = f2_fma(rx, rx, f2_fma(ry, ry, f2_mul(rz, rz)));
+                const F2 u = f2_add(r2, e2);
+                const F2 inv{rsqrtf(u.a), rsqrtf(u.b)};
+                const F2 t = f2_mul(Q.w, f2_mul(inv, f2_mul(inv, inv)));
+                const F2 tx = f2_mul(rx, t), ty = f2_mul(ry, t), tz = f2_mul(rz, t);
+                axx = f2_fma(rx, tx, axx);
+                axy = f2_fma(rx, ty, axy);
+                axz = f2_fma(rx, tz, axz);
+                ayy = f2_fma(ry, ty, ayy);
+                ayz = f2_fma(ry, tz, ayz);
+                azz = f2_fma(rz, tz, azz);
+                at = f2_add(at, t);
             }
             if (sp[cur + 1] > cend) break;  // the segment continues in the next chunk
-            if (active) flush(n0 + cur);
-            axx = axy = axz = ayy = ayz = azz = ad = 0.0f;
+            flush(n0 + cur);
             ++cur;
         }
     }
     while (cur < nt) {
-        if (active) flush(n0 + cur);
-        axx = axy = axz = ayy = ayz = azz = ad = 0.0f;
+        flush(n0 + cur);
         ++cur;
     }
 }
@@ -276,7 +370,7 @@ void launch_assemble(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t l
 
 void launch_assemble32(Ctx &c, const D4 *x_lab, float *A32, int64_t lda)
 {
-    dim3 grid((unsigned)ceil_div(c.N, AS_THREADS), (unsigned)ceil_div(c.N, AS_NT));
+    dim3 grid((unsigned)ceil_div(c.N, AS32_M), (unsigned)ceil_div(c.N, AS_NT));
     const float coef = (float)(1.0 / (8.0 * kPi * c.mu));
     c.tbeg(PH_ASSEMBLE32);
     k_split_points<<<(unsigned)ceil_div(c.N, 256), 256, 0, c.stream>>>(c.N, x_lab, c.d_xh, c.d_xl);
