@@ -159,14 +159,15 @@ __global__ void k_split_points(int64_t count, const D4 *__restrict__ p, float4 *
 // The FP32 copy that the factorisation inverts, on its own: the same sums in
 // FP32, with x_m - X_q = (x_hi - X_hi) + (x_lo - X_lo) from the float pairs
 // (the hi difference is exact for points closer than their own magnitude),
-// so each entry carries a few FP32 roundings.  Each thread owns two
-// collocation points (m and m + AS_THREADS) and evaluates their two pairs with
-// each staged quadrature point side by side in packed FP32x2 instructions; the
+// so each entry carries a few FP32 roundings.  Each thread owns four
+// collocation points (m + h AS_THREADS, h < 4) and evaluates their pairs with
+// each staged quadrature point two by two in packed FP32x2 instructions; the
 // staged weights carry the factor 1/(8 pi mu); per segment the thread
 // accumulates r_j r_k t (six sums) and t, and the diagonal term
 // (|r|^2 + 2 eps^2) t is formed at the flush as (r_x^2 + r_y^2 + r_z^2) t +
 // 2 eps^2 t from those sums.
-constexpr int AS32_M = 2 * AS_THREADS;  // collocation points of a CTA
+constexpr int AS32_P = 4;                // collocation points of a thread
+constexpr int AS32_M = AS32_P * AS_THREADS;  // collocation points of a CTA
 constexpr int AS32_CHUNK = 256;         // quadrature points staged at a time
 
 // Packed FP32 arithmetic (two lanes of one 64-bit register per instruction,
@@ -236,38 +237,48 @@ __global__ void __launch_bounds__(AS_THREADS)
 {
     __shared__ StagedQ sQ[AS32_CHUNK];
     __shared__ int32_t sp[AS_NT + 1];
-    const int64_t m0 = (int64_t)blockIdx.x * AS32_M + threadIdx.x, m1 = m0 + AS_THREADS;
+    int64_t ms[AS32_P];
+    bool act[AS32_P];
+    float4 ph[AS32_P], pl[AS32_P];
+#pragma unroll
+    for (int h = 0; h < AS32_P; ++h) {
+        ms[h] = (int64_t)blockIdx.x * AS32_M + threadIdx.x + h * AS_THREADS;
+        act[h] = ms[h] < N;
+        ph[h] = act[h] ? xh[ms[h]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        pl[h] = act[h] ? xl[ms[h]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     const int64_t n0 = (int64_t)blockIdx.y * AS_NT;
     const int nt = (int)min((int64_t)AS_NT, N - n0);
     if (threadIdx.x <= nt) sp[threadIdx.x] = seg_ptr[n0 + threadIdx.x];
-    const bool act0 = m0 < N, act1 = m1 < N;
-    float4 ph0 = make_float4(0.f, 0.f, 0.f, 0.f), pl0 = ph0, ph1 = ph0, pl1 = ph0;
-    if (act0) {
-        ph0 = xh[m0];
-        pl0 = xl[m0];
+    // two packed streams: points (0, 1) and (2, 3)
+    F2 px[2], py[2], pz[2], qx[2], qy[2], qz[2];
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+        px[g] = F2{ph[2 * g].x, ph[2 * g + 1].x};
+        py[g] = F2{ph[2 * g].y, ph[2 * g + 1].y};
+        pz[g] = F2{ph[2 * g].z, ph[2 * g + 1].z};
+        qx[g] = F2{pl[2 * g].x, pl[2 * g + 1].x};
+        qy[g] = F2{pl[2 * g].y, pl[2 * g + 1].y};
+        qz[g] = F2{pl[2 * g].z, pl[2 * g + 1].z};
     }
-    if (act1) {
-        ph1 = xh[m1];
-        pl1 = xl[m1];
-    }
-    const F2 px{ph0.x, ph1.x}, py{ph0.y, ph1.y}, pz{ph0.z, ph1.z};
-    const F2 qx{pl0.x, pl1.x}, qy{pl0.y, pl1.y}, qz{pl0.z, pl1.z};
     const F2 e2{eps2, eps2};
     const float two_e2 = 2.0f * eps2;
     const F2 zero{0.0f, 0.0f};
-    F2 axx = zero, axy = zero, axz = zero, ayy = zero, ayz = zero, azz = zero, at = zero;
-    auto flush = [&](int64_t nn) {
-        const float xx[2] = {axx.a, axx.b}, xy[2] = {axy.a, axy.b}, xz[2] = {axz.a, axz.b};
-        const float yy[2] = {ayy.a, ayy.b}, yz[2] = {ayz.a, ayz.b}, zz[2] = {azz.a, azz.b};
-        const float tt[2] = {at.a, at.b};
-        const int64_t ms[2] = {m0, m1};
-        const bool act[2] = {act0, act1};
+    F2 axx[2], axy[2], axz[2], ayy[2], ayz[2], azz[2], at[2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+    for (int g = 0; g < 2; ++g) axx[g] = axy[g] = axz[g] = ayy[g] = ayz[g] = azz[g] = at[g] = zero;
+    auto flush = [&](int64_t nn) {
+#pragma unroll
+        for (int h = 0; h < AS32_P; ++h) {
+            const int g = h >> 1;
+            const bool lo = (h & 1) == 0;
+            const float xx = lo ? axx[g].a : axx[g].b, xy = lo ? axy[g].a : axy[g].b;
+            const float xz = lo ? axz[g].a : axz[g].b, yy = lo ? ayy[g].a : ayy[g].b;
+            const float yz = lo ? ayz[g].a : ayz[g].b, zz = lo ? azz[g].a : azz[g].b;
+            const float tt = lo ? at[g].a : at[g].b;
             if (!act[h]) continue;
-            const float d = fmaf(two_e2, tt[h], (xx[h] + yy[h]) + zz[h]);
-            const float v[9] = {xx[h] + d, xy[h], xz[h], xy[h], yy[h] + d, yz[h],
-                                xz[h], yz[h], zz[h] + d};
+            const float d = fmaf(two_e2, tt, (xx + yy) + zz);
+            const float v[9] = {xx + d, xy, xz, xy, yy + d, yz, xz, yz, zz + d};
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const int64_t col = (3 * nn + k) * lda + 3 * ms[h];
@@ -275,7 +286,9 @@ __global__ void __launch_bounds__(AS_THREADS)
                 for (int j = 0; j < 3; ++j) A32[col + j] = v[3 * j + k];
             }
         }
-        axx = axy = axz = ayy = ayz = azz = at = zero;
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+            axx[g] = axy[g] = axz[g] = ayy[g] = ayz[g] = azz[g] = at[g] = zero;
     };
     __syncthreads();
     int cur = 0;
@@ -303,24 +316,26 @@ __global__ void __launch_bounds__(AS_THREADS)
         // ascending q
         while (cur < nt) {
             const int32_t sb = max(sp[cur], c0), se = min(sp[cur + 1], cend);
-#pragma unroll 2
             for (int32_t q = sb; q < se; ++q) {
                 const StagedQ Q = sQ[q - c0];
-                const F2 rx = f2_add(f2_sub(px, Q.hx), f2_sub(qx, Q.lx));
-                const F2 ry = f2_add(f2_sub(py, Q.hy), f2_sub(qy, Q.ly));
-                const F2 rz = f2_add(f2_sub(pz, Q.hz), f2_sub(qz, Q.lz));
-                const F2 r2 = f2_fma(rx, rx, f2_fma(ry, ry, f2_mul(rz, rz)));
-                const F2 u = f2_add(r2, e2);
-                const F2 inv{rsqrtf(u.a), rsqrtf(u.b)};
-                const F2 t = f2_mul(Q.w, f2_mul(inv, f2_mul(inv, inv)));
-                const F2 tx = f2_mul(rx, t), ty = f2_mul(ry, t), tz = f2_mul(rz, t);
-                axx = f2_fma(rx, tx, axx);
-                axy = f2_fma(rx, ty, axy);
-                axz = f2_fma(rx, tz, axz);
-                ayy = f2_fma(ry, ty, ayy);
-                ayz = f2_fma(ry, tz, ayz);
-                azz = f2_fma(rz, tz, azz);
-                at = f2_add(at, t);
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    const F2 rx = f2_add(f2_sub(px[g], Q.hx), f2_sub(qx[g], Q.lx));
+                    const F2 ry = f2_add(f2_sub(py[g], Q.hy), f2_sub(qy[g], Q.ly));
+                    const F2 rz = f2_add(f2_sub(pz[g], Q.hz), f2_sub(qz[g], Q.lz));
+                    const F2 r2 = f2_fma(rx, rx, f2_fma(ry, ry, f2_mul(rz, rz)));
+                    const F2 u = f2_add(r2, e2);
+                    const F2 inv{rsqrtf(u.a), rsqrtf(u.b)};
+                    const F2 t = f2_mul(Q.w, f2_mul(inv, f2_mul(inv, inv)));
+                    const F2 tx = f2_mul(rx, t), ty = f2_mul(ry, t), tz = f2_mul(rz, t);
+                    axx[g] = f2_fma(rx, tx, axx[g]);
+                    axy[g] = f2_fma(rx, ty, axy[g]);
+                    axz[g] = f2_fma(rx, tz, axz[g]);
+                    ayy[g] = f2_fma(ry, ty, ayy[g]);
+                    ayz[g] = f2_fma(ry, tz, ayz[g]);
+                    azz[g] = f2_fma(rz, tz, azz[g]);
+                    at[g] = f2_add(at[g], t);
+                }
             }
             if (sp[cur + 1] > cend) break;  // the segment continues in the next chunk
             flush(n0 + cur);
