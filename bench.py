@@ -943,16 +943,19 @@ def _batch_case(nrs, probs, prec, steps, tune=True, plan=None, seq_steps=None):
 def batch_full(args):
     """The whole batch workload at full size (128 ventral-node problems, n 5322-15771,
     about 173 GB of FP64 + FP32 matrices on the device): seconds per batch step through
-    one graph with a fixed plan (K = 8 chains, G = 38: the autotuner's choice on the
-    first 8 problems; tuning all 128 would take minutes), and one step of the same
-    problems one after the other.  Not part of the default run."""
+    one graph with the plan the autotuner chooses on the first 8 problems (tuning all
+    128 would take minutes), and one step of the same problems one after the other.
+    Not part of the default run."""
     import torch
     from paper_2001_06468_gb300 import nrs
     torch.cuda.set_device(0)
     t0 = time.time()
     probs = g.node_batch(128)
     gen_s = time.time() - t0
-    res = _batch_case(nrs, probs, args.prec, 2, tune=False, plan=(8, 38), seq_steps=1)
+    first8 = _batch_case(nrs, probs[:8], args.prec, 1, seq_steps=0)
+    plan = (first8["chains"], first8["solve_grid"])
+    torch.cuda.empty_cache()
+    res = _batch_case(nrs, probs, args.prec, 2, tune=False, plan=plan, seq_steps=1)
     res.update({"workload": "ventral-node batch, all 128 problems at full size",
                 "generator_s": gen_s,
                 "matrix_bytes": int(sum(12 * pr.n * pr.n for pr in probs))})
@@ -1199,11 +1202,12 @@ def batch_bench(nrs, args, ws, rank):
         import torch
         torch.cuda.empty_cache()
         probs = g.node_batch(128)
-        res = _batch_case(nrs, probs, args.prec, 1, tune=False, plan=(8, 38), seq_steps=0)
+        plan = (out["full_first8"]["chains"], out["full_first8"]["solve_grid"])
+        res = _batch_case(nrs, probs, args.prec, 1, tune=False, plan=plan, seq_steps=0)
         out["full_128"] = dict(res, recipe="all 128 problems at full size (n 5322-15771), plan "
-                                           "K = 8 chains, G = 38 (the autotuner's choice on the "
-                                           "first 8), one timed batch step after the eager first "
-                                           "step and the recorded second",
+                                           f"K = {plan[0]} chains, G = {plan[1]} (the autotuner's "
+                                           "choice on the first 8), one timed batch step after "
+                                           "the eager first step and the recorded second",
                                matrix_bytes=int(sum(12 * pr.n * pr.n for pr in probs)))
         del probs
         torch.cuda.empty_cache()

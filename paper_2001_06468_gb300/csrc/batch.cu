@@ -271,9 +271,12 @@ nrs_status nrs_batch_create(nrs_batch **out, const nrs_problem_desc *descs, int3
         b->ev.push_back(ev);
         nrs_problem_desc d = descs[i];
         d.graph = 0;
-        // the problems of a batch run side by side: the fused and the two-level
-        // factorisations (which take every SM) would serialise them
-        d.factor_schedule = 2;
+        // the problems of a batch run side by side: the fused factorisation,
+        // one cooperative launch taking every SM, would serialise them; the
+        // automatic choice stays (two-level from n = 8192 on: its update CTAs
+        // claim their tiles dynamically, so they share the SMs with the other
+        // chains' kernels instead of waiting for all of them)
+        if (d.factor_schedule == 1) d.factor_schedule = 2;
         nrs_ctx *h = nullptr;
         st = nrs_create(&h, &d, s);
         if (st == NRS_OK) {
