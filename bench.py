@@ -71,15 +71,16 @@ WORKLOADS_DESC = {
 }
 # the product path's solver settings per workload
 # (swept on the channel: refresh after 40 GMRES iterations or 32 stages, each
-# GMRES call reducing the preconditioned residual 1e5-fold)
+# GMRES call reducing the preconditioned residual 1e5-fold; the GMRES products
+# with the float-pair copy of A)
 HEADLINE_SOLVER = dict(reuse_factor=True, warm_start=True, reuse_max_inner=40,
-                       reuse_max_stages=32, inner_tol=1e-5)
+                       reuse_max_stages=32, inner_tol=1e-5, arnoldi="df")
 # the four-swimmer system has kappa_1 ~ 1e13: its GMRES steps need the longest
 # restart and a tighter inner tolerance; a refinement that has not converged
 # after 20 steps is retried with a new factor (nrs_step).  Swept: refresh after
 # 60 GMRES iterations, the FP32 copy evaluated in FP32
-C2_SOLVER = dict(inner_tol=1e-6, max_inner=64, max_outer=20,
-                 reuse_factor=True, warm_start=True, reuse_max_inner=60, reuse_max_stages=32)
+C2_SOLVER = dict(inner_tol=1e-6, max_inner=64, max_outer=20, reuse_factor=True,
+                 warm_start=True, reuse_max_inner=60, reuse_max_stages=32, arnoldi="df")
 L2_FLUSH_BYTES = 512 << 20
 FP64_NOMINAL_TFLOPS = 1.25       # GB300 FP64, nominal (2 FMA lanes per SM per clock)
 TF32_OVER_BF16 = 1.1 / 2.25      # nominal dense TF32 / BF16 tensor throughput
@@ -283,7 +284,7 @@ def kept_pairs(nrs, pr):
 
 
 def rooflines(ph_ms, ph_spans, n, pairs, peaks, peak_src, sm_mhz, solve_stats, pairs64=None,
-              update_f16=True):
+              update_f16=True, arnoldi_df=False):
     """Roofline records of the kernel families from the live per-phase CUDA
     event times (one span per launch, on the stream each kernel runs on).
     Algorithmic work per launch:
@@ -292,11 +293,12 @@ def rooflines(ph_ms, ph_spans, n, pairs, peaks, peak_src, sm_mhz, solve_stats, p
       lu_diag     k_gj_diag: (2 + 8 (nblk - 1)) / nblk x 64^3 FP32 flops, one CTA
       assemble    k_assemble64: 40 FP64 operations per (force, quadrature) pair
       assemble32  k_assemble32: N Q pairs against the FP32 pair peak (20 instructions a pair)
-      krylov      k_gmres_ir: (outer + inner) 8 n^2 + (outer + inner + 1) 4 n^2 bytes;
-                  + 8 n^2 (||A||_inf, once per launch);
+      krylov      k_gmres_ir: (outer + inner) 8 n^2 (A in FP64, or its float-pair copy
+                  for the GMRES products: also 8 bytes an entry) + (outer + inner + 1)
+                  4 n^2 bytes; + 8 n^2 (||A||_inf, once per launch);
                   outer x 3 n^2 (extended residual: product, its error, the error
-                  sum; the products' sum on the integer pipe) + (inner + 1) x n^2
-                  FP64 operations"""
+                  sum; the products' sum on the integer pipe) + n^2 (||A||_inf) +
+                  inner x n^2 (the GMRES products, when in FP64) FP64 operations"""
     P = derived_peaks(peaks, sm_mhz)
 
     def per_launch(ph):
@@ -402,7 +404,9 @@ def rooflines(ph_ms, ph_spans, n, pairs, peaks, peak_src, sm_mhz, solve_stats, p
         o, i = solve_stats["outer_mean"], solve_stats["inner_mean"]
         t = per_launch("krylov")
         b = 8.0 * n * n * (o + i + 1) + 4.0 * n * n * (o + i + 1)
-        ops = RES_OPS_PER_ENTRY * n * n * o + n * n * (i + 1)
+        # FP64 operations: the residuals, the ||A||_inf pass, and the GMRES
+        # products unless they run on the float-pair copy (FP32 pipe)
+        ops = RES_OPS_PER_ENTRY * n * n * o + n * n * (1 + (0 if arnoldi_df else i))
         recs["krylov"] = {
             "kernel": "k_gmres_ir (persistent GMRES-IR, one cooperative launch per solve)",
             "bound": "hbm", "achieved": b / t / 1e9, "peak": P["hbm_gbs"], "unit": "GB/s",
@@ -633,7 +637,8 @@ def headline(nrs, args, ws, local, timer, peaks, peak_src):
     # every instrumented assembly follows at least one full one: the static
     # blocks are kept in all of them
     p64 = pr.pairs - kept_pairs(nrs, pr)
-    recs = rooflines(ph_ms, ph_spans, pr.n, pr.pairs, peaks, peak_src, sm_mhz, solve_stats, p64)
+    recs = rooflines(ph_ms, ph_spans, pr.n, pr.pairs, peaks, peak_src, sm_mhz, solve_stats, p64,
+                     arnoldi_df=kw.get("arnoldi") == "df")
     # the FP64 assembly runs beside the factorisation in factored stages: its
     # launches that overlapped no factorisation span, rated on their own
     alone = spans_alone(trace, "assemble", ("lu_panel", "lu_update", "assemble32"))
@@ -1137,7 +1142,8 @@ def run_nrs(args):
                    "blocked Gauss-Jordan, rank-256 tensor-core updates from scaled FP16 pairs; "
                    f"--prec {args.prec}), refreshed after >40 GMRES iterations or 32 stages",
                    "refinement": "GMRES-IR, extended residual (exact fixed-point product sums), "
-                                 "inner tolerance 1e-5, warm start from the previous stage",
+                                 "GMRES products with the float-pair copy of A, inner tolerance "
+                                 "1e-5, warm start from the previous stage",
                    "rk2_stages_per_step": 2,
                    "l2": "flushed between timed steps (512 MiB write); matrices 9.2 GB > L2",
                    "parallelism": f"replicas x{ws}"},

@@ -143,6 +143,16 @@ typedef struct {
                               three-precision GMRES-IR, which reaches working accuracy in
                               the solution up to kappa(A) ~ 1/u; 1 = plain FP64 (the
                               solution is then only accurate to about kappa(A) u) */
+    int32_t arnoldi;       /* the matrix-vector products A v of the GMRES iterations inside
+                              the refinement (the one-launch mode, solve_mode 0): 0 = with the
+                              FP64 matrix (FP64 pipe); 1 = with a float-pair copy of A
+                              (hi = fl32(a), lo = fl32(a - hi), about 48 bits) that the
+                              assembly writes beside the FP64 matrix (8 more bytes per entry
+                              on the device), in double-float arithmetic on the FP32 pipe.
+                              The residual always uses the FP64 matrix, so the answer keeps
+                              its accuracy; the products' relative error (about 2^-46) only
+                              slows the refinement where kappa(A) 2^-46 is not small.  Other
+                              values: NRS_EINVAL. */
 } nrs_problem_desc;
 
 typedef struct {

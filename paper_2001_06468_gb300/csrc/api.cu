@@ -95,6 +95,8 @@ nrs_status alloc_all(Ctx *c)
         {(void **)&c->d_part32, sizeof(double) * 64 * lda},
         {(void **)&c->d_part_fx, sizeof(unsigned long long) * 3 * 64 * lda},
         {(void **)&c->d_vf, sizeof(float2) * lda},
+        {(void **)&c->d_vf2, sizeof(float2) * lda},
+        {(void **)&c->d_Adf, c->arnoldi_df ? sizeof(float2) * (size_t)lda * (size_t)n : 0},
         {(void **)&c->d_gj2, gj2 ? nrs::gj2_workspace_bytes(n) : 0},
         {(void **)&c->d_gj2_r, gj2 ? sizeof(float) * 64 * 256 : 0},
         {(void **)&c->d_t32, sizeof(float) * 2 * lda},
@@ -135,7 +137,8 @@ void free_all(Ctx *c)
                     c->d_t32,    c->d_t64,    c->d_flags,  c->d_status,     c->d_gj_dinv,
                     c->d_gj_rt,  c->d_gj_cb,  c->d_dpart,  c->d_bar,        c->d_pg_stats,
                     c->d_step_stats, c->d_Xsh, c->d_Xsl, c->d_xh, c->d_xl, c->d_gj_stage, c->d_gj_sync, c->d_part32,
-                    c->d_part_fx, c->d_vf, c->d_gj2, c->d_gj2_r};
+                    c->d_part_fx, c->d_vf, c->d_gj2, c->d_gj2_r,
+                    c->d_vf2, c->d_Adf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *tr[] = {c->d_tr, c->d_tr_save, c->d_tr_u, c->d_tr_part, c->d_vel_part, c->d_dp_K,
@@ -522,6 +525,11 @@ nrs_status nrs_create(nrs_ctx **out, const nrs_problem_desc *d, void *stream)
     c->tol_in = d->inner_tol > 0.0 ? d->inner_tol : 1e-4;
     c->lo_eval = d->factor_input ? 1 : 0;
     c->residual_dd = d->residual == 0 ? 1 : 0;
+    if (d->arnoldi < 0 || d->arnoldi > 1) {
+        delete c;
+        return NRS_EINVAL;
+    }
+    c->arnoldi_df = d->arnoldi == 1 && d->factor_prec != NRS_FP64;
     if (d->factor_schedule < 0 || d->factor_schedule > 4) {
         delete c;
         return NRS_EINVAL;

@@ -49,7 +49,7 @@ struct Acc6 {
 // the tiling and of the device.
 __device__ __forceinline__ void flush_block(int64_t m, int64_t n, const Acc6 &a, double c,
                                             double *__restrict__ A64, float *__restrict__ A32,
-                                            int64_t lda)
+                                            float2 *__restrict__ Adf, int64_t lda)
 {
     const double v[9] = {__dmul_rn(a.xx, c), __dmul_rn(a.xy, c), __dmul_rn(a.xz, c),
                          __dmul_rn(a.xy, c), __dmul_rn(a.yy, c), __dmul_rn(a.yz, c),
@@ -61,6 +61,7 @@ __device__ __forceinline__ void flush_block(int64_t m, int64_t n, const Acc6 &a,
         for (int j = 0; j < 3; ++j) {
             A64[col + j] = v[3 * j + k];
             if (A32) A32[col + j] = (float)v[3 * j + k];
+            if (Adf) Adf[col + j] = df_split(v[3 * j + k]);
         }
     }
 }
@@ -88,7 +89,8 @@ __device__ __forceinline__ void add_pair(double mx, double my, double mz, const 
 __global__ void __launch_bounds__(AS_THREADS)
     k_assemble64(int64_t N, const D4 *__restrict__ x, const D4 *__restrict__ Xs,
                  const int32_t *__restrict__ seg_ptr, double eps2, double c,
-                 double *__restrict__ A64, float *__restrict__ A32, int64_t lda, int64_t gx,
+                 double *__restrict__ A64, float *__restrict__ A32, float2 *__restrict__ Adf,
+                 int64_t lda, int64_t gx,
                  int64_t tiles, const uint8_t *__restrict__ mblk_keep,
                  const uint8_t *__restrict__ nblk_keep)
 {
@@ -128,13 +130,13 @@ __global__ void __launch_bounds__(AS_THREADS)
             const int32_t sb = max(sp[cur], c0), se = min(sp[cur + 1], cend);
             for (int32_t q = sb; q < se; ++q) add_pair(mx, my, mz, sX[q - c0], eps2, two_e2, a);
             if (sp[cur + 1] > cend) break;  // the segment continues in the next chunk
-            if (active) flush_block(m, n0 + cur, a, c, A64, A32, lda);
+            if (active) flush_block(m, n0 + cur, a, c, A64, A32, Adf, lda);
             a = Acc6{0, 0, 0, 0, 0, 0};
             ++cur;
         }
     }
     while (cur < nt) {
-        if (active) flush_block(m, n0 + cur, a, c, A64, A32, lda);
+        if (active) flush_block(m, n0 + cur, a, c, A64, A32, Adf, lda);
         a = Acc6{0, 0, 0, 0, 0, 0};
         ++cur;
     }
@@ -375,7 +377,10 @@ void launch_assemble(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t l
     const bool keep = from_state && A32 == nullptr && A64 == c.d_A64 && c.have_static &&
                       c.static_cache_valid;
     k_assemble64<<<(unsigned)grid, AS_THREADS, 0, s>>>(c.N, x_lab, c.d_Xs, c.d_seg_ptr,
-                                                       c.eps * c.eps, coef, A64, A32, lda, gx,
+                                                       c.eps * c.eps, coef, A64, A32,
+                                                       (c.arnoldi_df && A64 == c.d_A64) ? c.d_Adf
+                                                                                        : nullptr,
+                                                       lda, gx,
                                                        tiles, keep ? c.d_mblk_keep : nullptr,
                                                        keep ? c.d_nblk_keep : nullptr);
     c.static_cache_valid = from_state && A64 == c.d_A64;

@@ -377,7 +377,7 @@ __global__ void k_border(int64_t N, int64_t n, const int32_t *__restrict__ free_
                          const int32_t *__restrict__ body_x, const D4 *__restrict__ x,
                          const double *__restrict__ x0, const double *__restrict__ W,
                          const double *__restrict__ R, double *__restrict__ A64,
-                         float *__restrict__ A32, int64_t lda)
+                         float *__restrict__ A32, float2 *__restrict__ Adf, int64_t lda)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -409,6 +409,10 @@ __global__ void k_border(int64_t N, int64_t n, const int32_t *__restrict__ free_
         A32[i + (base + cc) * lda] = (float)col;
         A32[(base + cc) + i * lda] = (float)row;
     }
+    if (Adf) {
+        Adf[i + (base + cc) * lda] = df_split(col);
+        Adf[(base + cc) + i * lda] = df_split(row);
+    }
 }
 
 void launch_border(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t lda)
@@ -419,7 +423,9 @@ void launch_border(Ctx &c, const D4 *x_lab, double *A64, float *A32, int64_t lda
     // d_free_index holds nbodies entries (body -> free index) then F entries (free index -> body)
     c.tbeg(PH_BORDER);
     k_border<<<grid, threads, 0, c.stream>>>(c.N, c.n, c.d_free_index + c.nbodies, c.d_body_x, x_lab,
-                                             c.d_x0, c.d_W, c.d_R, A64, A32, lda);
+                                             c.d_x0, c.d_W, c.d_R, A64, A32,
+                                             (c.arnoldi_df && A64 == c.d_A64) ? c.d_Adf : nullptr,
+                                             lda);
     c.tend(PH_BORDER);
     c.launches += 1;
 }

@@ -60,6 +60,8 @@ struct PgArgs {
     double *part32;       // partial sums of the FP32 products [splits][n]
     unsigned long long *part_fx;  // the exact residual's integer partial sums [splits][3][n]
     float2 *vf;           // input of the next preconditioner product as float pairs [n]
+    const float2 *Adf;    // float-pair copy of A for the GMRES products, or null (FP64 A)
+    float2 *Vf;           // the raw Krylov vector of the next product as float pairs [n]
     int dd;               // residual b - A x to u^2 (1: exact products, mv64fx_partial) or FP64 (0)
     double *dpart;        // reduction partials [3][PG_MAXCH][m+2]
     int32_t *bar;         // grid barrier: [0] arrivals since the launch ([1] unused)
@@ -153,6 +155,46 @@ __device__ void mv64_partial(const PgArgs &a, const double *v, double scale, dou
         }
         sm[grp * MV64_ROWS + 2 * lane] = s0;
         sm[grp * MV64_ROWS + 2 * lane + 1] = s1;
+        __syncthreads();
+        if (threadIdx.x < MV64_ROWS) {
+            const int64_t r = rc * MV64_ROWS + threadIdx.x;
+            double acc = 0.0;
+#pragma unroll
+            for (int g = 0; g < MV_GROUPS; ++g) acc += sm[g * MV64_ROWS + threadIdx.x];
+            if (r < a.n) a.part[s * a.n + r] = acc * scale;
+        }
+        __syncthreads();
+    }
+}
+
+// part[s][i] = scale * sum_{j in split s} A[i, j] v[j] from the float-pair copy
+// of A (a.Adf: hi + lo per entry, about 48 bits) and the raw Krylov vector as
+// float pairs (a.Vf): double-float products and sums on the FP32 pipe (df_fma,
+// plus the lo hi term), about 2^-46 of |A| |v|; the tile layout of
+// mv64_partial, one 16-byte load per column for the two rows of a lane.
+__device__ void mv64df_partial(const PgArgs &a, double scale, double *sm)
+{
+    const int64_t tiles = (int64_t)a.rc64 * a.s64;
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t rc = t % a.rc64, s = t / a.rc64;
+        const int64_t i = rc * MV64_ROWS + 2 * lane;
+        const int64_t j0 = s * a.cps64, j1 = min(a.n, j0 + a.cps64);
+        float s0 = 0.0f, c0 = 0.0f, s1 = 0.0f, c1 = 0.0f;
+        if (i < a.n) {
+            const float2 *col = a.Adf + i;
+#pragma unroll 4
+            for (int64_t j = j0 + grp; j < j1; j += MV_GROUPS) {
+                const float4 x = __ldg(reinterpret_cast<const float4 *>(col + j * a.lda));
+                const float2 vj = __ldcg(a.Vf + j);
+                df_fma(x.x, vj, s0, c0);
+                c0 = __fmaf_rn(x.y, vj.x, c0);
+                df_fma(x.z, vj, s1, c1);
+                c1 = __fmaf_rn(x.w, vj.x, c1);
+            }
+        }
+        sm[grp * MV64_ROWS + 2 * lane] = (double)s0 + (double)c0;
+        sm[grp * MV64_ROWS + 2 * lane + 1] = (double)s1 + (double)c1;
         __syncthreads();
         if (threadIdx.x < MV64_ROWS) {
             const int64_t r = rc * MV64_ROWS + threadIdx.x;
@@ -500,6 +542,7 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
             for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
                 const double v = sum_parts32(a, e);
                 a.V[e] = v;
+                if (a.Adf) a.Vf[e] = df_split(v);
                 s = fma(v, v, s);
             }
             s = block_sum_all(s, sred);
@@ -519,8 +562,11 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
         for (int j = 0; j < m; ++j) {
             double *Vj = a.V + (int64_t)j * a.ldv;
             double *u = a.V + (int64_t)(j + 1) * a.ldv;
-            // w = A v_j
-            mv64_partial<false>(a, Vj, sv, smv);
+            // w = A v_j (the FP64 matrix, or its float-pair copy and a.Vf)
+            if (a.Adf)
+                mv64df_partial(a, sv, smv);
+            else
+                mv64_partial<false>(a, Vj, sv, smv);
             if (!grid_sync(a, &s_ok, tgt)) return;
             for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
                 Vj[e] = __ldcg(Vj + e) * sv;  // v_j normalised in place (own chunk)
@@ -553,6 +599,7 @@ __global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
                     for (int i = 0; i <= j; ++i)
                         s = fma(-sh2[i], __ldcg(a.V + (int64_t)i * a.ldv + e), s);
                     u[e] = s;
+                    if (a.Adf) a.Vf[e] = df_split(s);
                     s2 = fma(s, s, s2);
                 }
                 s2 = block_sum_all(s2, sred);
@@ -721,6 +768,8 @@ cudaError_t launch_gmres_persistent(Ctx &c, const double *b, double *x, bool col
     a.part32 = c.d_part32;
     a.part_fx = c.d_part_fx;
     a.vf = c.d_vf;
+    a.Adf = c.arnoldi_df ? c.d_Adf : nullptr;
+    a.Vf = c.d_vf2;
     a.dd = c.residual_dd;
     a.dpart = c.d_dpart;
     a.bar = c.d_bar;

@@ -310,6 +310,9 @@ struct Ctx {
     double *d_part = nullptr;  // partial sums of matrix-vector products
     double *d_part32 = nullptr;  // partial sums of the FP32 products of the persistent solve
     unsigned long long *d_part_fx = nullptr; // the residual's exact partial sums [splits][3][n]
+    int arnoldi_df = 0;            // GMRES products with the float-pair copy of A (desc.arnoldi)
+    float2 *d_Adf = nullptr;       //   that copy: (hi, lo) per entry, A64's layout
+    float2 *d_vf2 = nullptr;       //   the raw Krylov vector as float pairs
     float2 *d_vf = nullptr;      // the preconditioner product's input vector as float pairs
     int residual_dd = 1;       // refinement residual b - A x: 1 double-double, 0 FP64
     int splits64 = 1, splits32 = 1;  // column splits of the FP64 / FP32 matrix-vector products

@@ -79,7 +79,8 @@ class ProblemDesc(ctypes.Structure):
                 ("factor_input", ctypes.c_int32),
                 ("graph", ctypes.c_int32),
                 ("factor_schedule", ctypes.c_int32),
-                ("residual", ctypes.c_int32)]
+                ("residual", ctypes.c_int32),
+                ("arnoldi", ctypes.c_int32)]
 
 
 class SolveReport(ctypes.Structure):
@@ -213,11 +214,13 @@ class Context:
                  warm_start: bool = False, solve_mode: str = "device", graph: bool = False,
                  inner_tol: float = 0.0, factor_input: str = "fp32",
                  factor_schedule: str = "auto", residual: str = "extended",
+                 arnoldi: str = "fp64",
                  stream: Optional[torch.cuda.Stream] = None, _handle=None):
         d, self._keep = _make_desc(n_off, q_off, kind, eps, mu, rigid, U, Omega, nn_global,
                                    factor_prec, tol, max_outer, max_inner, reuse_factor,
                                    reuse_max_inner, reuse_max_stages, warm_start, solve_mode,
-                                   graph, inner_tol, factor_input, factor_schedule, residual)
+                                   graph, inner_tol, factor_input, factor_schedule, residual,
+                                   arnoldi)
         self.stream = stream or torch.cuda.current_stream()
         self._owner = _handle is None
         if _handle is None:
@@ -521,7 +524,7 @@ def _make_desc(n_off, q_off, kind, eps, mu=1.0, rigid=None, U=None, Omega=None, 
                factor_prec="fp32", tol=0.0, max_outer=0, max_inner=0, reuse_factor=False,
                reuse_max_inner=0, reuse_max_stages=0, warm_start=False, solve_mode="device",
                graph=False, inner_tol=0.0, factor_input="fp32", factor_schedule="auto",
-               residual="extended"):
+               residual="extended", arnoldi="fp64"):
     """An nrs_problem_desc and the host arrays it points to (keep them alive)."""
     n_off = np.ascontiguousarray(n_off, dtype=np.int64)
     q_off = np.ascontiguousarray(q_off, dtype=np.int64)
@@ -555,6 +558,8 @@ def _make_desc(n_off, q_off, kind, eps, mu=1.0, rigid=None, U=None, Omega=None, 
                          "two_level": 4}[factor_schedule]
     # "extended": to about u^2 (exact products, see nrs_residual); "fp64": plain
     d.residual = {"extended": 0, "fp64": 1}[residual]
+    # GMRES products with the FP64 matrix, or with its float-pair copy ("df")
+    d.arnoldi = {"fp64": 0, "df": 1}[arnoldi]
     return d, (n_off, q_off, kind, rigid, U, Om)
 
 

@@ -133,3 +133,14 @@ def test_spans_alone_excludes_overlapping_launches():
     tr = [("assemble", 0.0, 10.0), ("lu_update", 5.0, 20.0), ("assemble", 30.0, 40.0),
           ("krylov", 35.0, 50.0), ("assemble", 60.0, 65.0), ("lu_panel", 65.0, 70.0)]
     assert bench.spans_alone(tr, "assemble", ("lu_update", "lu_panel")) == [10.0, 5.0]
+
+
+def test_float_pair_gmres_products_leave_the_fp64_count():
+    ms, spans = _phases(assemble=(80.0, 1), krylov=(100.0, 1))
+    a = bench.rooflines(ms, spans, N_SYS, PAIRS, PEAKS, "measured", SM_MHZ, SOLVE)["krylov"]
+    b = bench.rooflines(ms, spans, N_SYS, PAIRS, PEAKS, "measured", SM_MHZ, SOLVE,
+                        arnoldi_df=True)["krylov"]
+    assert a["work_per_launch"] == b["work_per_launch"]  # the same bytes either way
+    t = a["ms_per_launch"] / 1e3
+    assert (a["fp64_gops"] - b["fp64_gops"]) * 1e9 * t == pytest.approx(
+        SOLVE["inner_mean"] * N_SYS ** 2)

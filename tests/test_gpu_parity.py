@@ -355,3 +355,33 @@ def test_single_force_point(N):
     At = ctx.assemble(xd, Xd)
     A_or = O.assemble_stokeslet(x, Xw, np.zeros(5, dtype=np.int32), 0.05, 1.0)
     assert np.allclose(At.T.cpu().numpy(), A_or, rtol=1e-13)
+
+
+@pytest.mark.parametrize("name", ["swimmer", "sperm2"])
+def test_float_pair_arnoldi_keeps_the_oracle_trajectory(N, name):
+    # GMRES products with the float-pair copy of A (about 2^-46 of |A||v|):
+    # the residual still uses the FP64 matrix, so every solve reaches the
+    # oracle's answer; the iteration counts stay those of the FP64 products
+    pr = PROBLEMS[name]()
+    dt = 0.01
+    runs = {}
+    for arnoldi in ("fp64", "df"):
+        ctx, sh, Y, dev = _setup(N, pr, t=0.0, prec="tf32", reuse_factor=True, warm_start=True,
+                                 reuse_max_inner=40, arnoldi=arnoldi)
+        Yo = Y
+        inner = 0
+        for k in range(3):
+            t = k * dt
+            d0 = N.shapes_to_device(g.pack_shapes(pr, t))
+            dh = N.shapes_to_device(g.pack_shapes(pr, t + 0.5 * dt))
+            sol = torch.empty(2 * pr.n, dtype=torch.float64, device="cuda")
+            rep = ctx.step(N.Context.shapes(*d0), N.Context.shapes(*dh), dt, sol=sol)
+            inner += rep["stages"][0]["inner"] + rep["stages"][1]["inner"]
+            Yn, stages = O.rk2_step(pr, Yo, t, dt, return_stages=True)
+            s = sol.cpu().numpy()
+            assert _rel(s[:pr.n], stages["sol1"]) <= TOL_SOL, (arnoldi, rep)
+            assert _rel(s[pr.n:], stages["sol2"]) <= TOL_SOL, (arnoldi, rep)
+            Yo = Yn
+        runs[arnoldi] = inner
+        ctx.close()
+    assert runs["df"] <= runs["fp64"] + 3, runs
