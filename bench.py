@@ -202,25 +202,37 @@ NCU_TRAFFIC = {
     "k_tc_gj_update": {"bytes": 150743296 + 77540181, "n": 6006,
                        "file": "paper_2001_06468_gb300/csrc/tc_gemm.cu", "sha1": "e38e9748bdee",
                        "scale": "n^2 (captured at n = 6006, matrix larger than L2)"},
-    "k_tc_gj2_update": {"bytes": None, "file": "paper_2001_06468_gb300/csrc/gj2.cu",
-                        "sha1": "", "scale": None},
+    # the bulk launch of block 5 at n = 13824: 817.4 + 674.6 MB against 8 x 13824 x
+    # 13312 = 1.472 GB of M read and written
+    "k_tc_gj2_update": {"bytes": None, "ratio": (817380352 + 674585088) / (8.0 * 13824 * 13312),
+                        "file": "paper_2001_06468_gb300/csrc/gj2.cu", "sha1": "c707d500eb55",
+                        "scale": "traffic / algorithmic bytes at n = 13824, times the record's bytes"},
     "k_gj_diag": {"bytes": 136832, "file": "paper_2001_06468_gb300/csrc/gj.cu",
                   "sha1": "d098875a34c5",
                   "scale": "none (the 64 x 64 block, the previous D^{-1} and two 64 x 64 tiles)"},
     "k_assemble64": {"bytes": None, "file": "paper_2001_06468_gb300/csrc/assemble.cu",
                      "sha1": "", "scale": None},
-    "k_gmres_ir": {"bytes": None, "file": "paper_2001_06468_gb300/csrc/gmres_persistent.cu",
-                   "sha1": "", "scale": None},
+    # one solve at n = 13824 (cold start, 2 refinement steps, 4 GMRES iterations):
+    # 16.072 + 0.024 GB against 7 passes over A (8 n^2) and M (4 n^2) = 16.05 GB
+    "k_gmres_ir": {"bytes": None, "ratio": (16071619072 + 24146432) / (12.0 * 13824 ** 2 * 7),
+                   "file": "paper_2001_06468_gb300/csrc/gmres_persistent.cu", "sha1": "199b596e099d",
+                   "scale": "traffic / algorithmic bytes at n = 13824, times the record's bytes"},
 }
 
 
-def _traffic(kernel, n):
+def _traffic(kernel, n, work=None):
+    """DRAM bytes per launch from the ncu capture in NCU_TRAFFIC: scaled by n^2
+    from the captured size, or as the captured ratio of traffic to algorithmic
+    bytes times `work` (the record's algorithmic bytes per launch); None when
+    there is no capture or the kernel's source changed since."""
     rec = NCU_TRAFFIC.get(kernel)
-    if not rec or rec["bytes"] is None:
+    if not rec or (rec["bytes"] is None and rec.get("ratio") is None):
         return None
     src = open(os.path.join(ROOT, rec["file"]), "rb").read()
     if hashlib.sha1(src).hexdigest()[:12] != rec["sha1"]:
         return None  # the kernel changed since the counters were taken
+    if rec.get("ratio") is not None:
+        return None if work is None else rec["ratio"] * work
     if "n" in rec:
         return rec["bytes"] * (n / rec["n"]) ** 2
     return rec["bytes"]
@@ -336,7 +348,7 @@ def rooflines(ph_ms, ph_spans, n, pairs, peaks, peak_src, sm_mhz, solve_stats, p
             "useful_tflops": fl / 3 / t / 1e12,
             "hbm_gbs": b / t / 1e9, "hbm_frac": hfrac,
             "us_per_launch": t * 1e6, "launches": ph_spans["lu_update"],
-            "traffic": _traffic("k_tc_gj2_update", n)}
+            "traffic": _traffic("k_tc_gj2_update", n, b)}
         t = per_launch("lu_panel")
         recs["lu_panel"] = {
             "kernel": "column-panel elimination (4 x k_gj_diag, k_gj2_rpanel, k_gj2_panel_update) "
@@ -414,7 +426,7 @@ def rooflines(ph_ms, ph_spans, n, pairs, peaks, peak_src, sm_mhz, solve_stats, p
             "work_per_launch": b, "work_unit": "bytes of A (FP64) and M (FP32) streamed",
             "fp64_gops": ops / t / 1e9, "fp64_frac": ops / t / 1e9 / P["fp64_gops"],
             "outer_mean": o, "inner_mean": i, "ms_per_launch": t * 1e3,
-            "launches": ph_spans["krylov"], "traffic": _traffic("k_gmres_ir", n)}
+            "launches": ph_spans["krylov"], "traffic": _traffic("k_gmres_ir", n, b)}
     return recs
 
 
