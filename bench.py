@@ -1242,7 +1242,7 @@ def profile_step(args):
     import torch
     from paper_2001_06468_gb300 import nrs
     torch.cuda.set_device(0)
-    pr = g.workload(args.workload)
+    pr = PROFILE_WORKLOADS[args.workload]()
     Y = g.initial_state(pr)
     solver = C2_SOLVER if args.workload == "swimmers4" else HEADLINE_SOLVER
     ctx = nrs.Context.from_problem(pr, factor_prec=args.prec, **solver)

@@ -93,6 +93,27 @@ __device__ __forceinline__ int32_t pg_ld_relaxed(const int32_t *p)
     return v;
 }
 
+// L2 prefetch for the matrix-vector products: the products stream each matrix
+// once, with only 16 warps an SM (the cooperative launch's occupancy), so
+// the loads alone keep too few bytes in flight.  A warp's tile spans 512
+// bytes of a column (64 rows of 8 bytes, or 128 rows of 4); lanes 0-3 each
+// prefetch one of its four 128-byte lines six of its columns ahead of the
+// warp's current one.  Lines whose first row is at or beyond n are skipped
+// (such a line could run past the column's lda rows).
+constexpr int PF_COLS = 6 * MV_GROUPS;
+
+template <int ELEM>
+__device__ __forceinline__ void pf_line(const void *m, int64_t lda, int64_t n, int64_t row0,
+                                        int64_t j, int64_t j1, int lane)
+{
+    constexpr int rows_per_line = 128 / ELEM;
+    const int64_t jp = j + PF_COLS, r = row0 + (int64_t)lane * rows_per_line;
+    if (lane < 4 && jp < j1 && r < n) {
+        const char *p = reinterpret_cast<const char *>(m) + (r + jp * lda) * ELEM;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    }
+}
+
 // Grid-wide barrier (bounded).  Returns false when the solve must stop.  One
 // monotonic arrival counter per launch (zeroed before it): barrier number k
 // is passed once the counter reaches k * gridDim.x, so the last arrival
@@ -142,6 +163,7 @@ __device__ void mv64_partial(const PgArgs &a, const double *v, double scale, dou
             const double *col = a.A + i;
 #pragma unroll 8
             for (int64_t j = j0 + grp; j < j1; j += MV_GROUPS) {
+                pf_line<8>(a.A, a.lda, a.n, rc * MV64_ROWS, j, j1, lane);
                 const double2 x = __ldg(reinterpret_cast<const double2 *>(col + j * a.lda));
                 if (ABS) {  // row sums of |A|
                     s0 += fabs(x.x);
@@ -185,6 +207,7 @@ __device__ void mv64df_partial(const PgArgs &a, double scale, double *sm)
             const float2 *col = a.Adf + i;
 #pragma unroll 4
             for (int64_t j = j0 + grp; j < j1; j += MV_GROUPS) {
+                pf_line<8>(a.Adf, a.lda, a.n, rc * MV64_ROWS, j, j1, lane);
                 const float4 x = __ldg(reinterpret_cast<const float4 *>(col + j * a.lda));
                 const float2 vj = __ldcg(a.Vf + j);
                 df_fma(x.x, vj, s0, c0);
@@ -227,6 +250,7 @@ __device__ void mv64fx_partial(const PgArgs &a, const double *v, int c, double *
             const double *col = a.A + i;
 #pragma unroll 4
             for (int64_t j = j0 + grp; j < j1; j += MV_GROUPS) {
+                pf_line<8>(a.A, a.lda, a.n, rc * MV64_ROWS, j, j1, lane);
                 const double2 x = __ldg(reinterpret_cast<const double2 *>(col + j * a.lda));
                 const double vj = __ldcg(v + j);
                 const double p0 = __dmul_rn(x.x, vj), p1 = __dmul_rn(x.y, vj);
@@ -311,6 +335,7 @@ __device__ void mv32_partial(const PgArgs &a, double *sm)
             const float *col = a.M + i;
 #pragma unroll 4
             for (int64_t j = j0 + grp; j < j1; j += MV_GROUPS) {
+                pf_line<4>(a.M, a.lda, a.n, rc * MV32_ROWS, j, j1, lane);
                 const float4 x = __ldg(reinterpret_cast<const float4 *>(col + j * a.lda));
                 const float2 vj = __ldcg(a.vf + j);
                 df_fma(x.x, vj, s0, c0);
