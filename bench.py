@@ -217,6 +217,8 @@ NCU_TRAFFIC = {
     "k_gmres_ir": {"bytes": None, "ratio": (16071996928 + 24118784) / (12.0 * 13824 ** 2 * 7),
                    "file": "paper_2001_06468_gb300/csrc/gmres_persistent.cu", "sha1": "a46ad6c35efa",
                    "scale": "traffic / algorithmic bytes at n = 13824, times the record's bytes"},
+}
+
 
 def _traffic(kernel, n, work=None):
     """DRAM bytes per launch from the ncu capture in NCU_TRAFFIC: scaled by n^2
