@@ -453,7 +453,7 @@ __device__ void sum_dots(const PgArgs &a, int region, int j, double *h)
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(PG_THREADS) k_gmres_ir(PgArgs a)
+__global__ void __launch_bounds__(PG_THREADS, 3) k_gmres_ir(PgArgs a)
 {
     __shared__ double sH[(PG_MAXM + 1) * PG_MAXM];  // column-major, leading dimension PG_MAXM+1
     __shared__ double scs[PG_MAXM], ssn[PG_MAXM], sg[PG_MAXM + 1], sy[PG_MAXM];
@@ -738,9 +738,10 @@ int pg_grid(Ctx &c)
     if (c.pg_grid > 0) return c.pg_grid;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gmres_ir, PG_THREADS, 0);
-    // one CTA per SM while barriers dominate (matrices in L2); two once the
+    // one CTA per SM while barriers dominate (matrices in L2); three once the
     // products stream the matrices from HBM and need more bytes in flight
-    per_sm = std::max(1, std::min(per_sm, c.n >= 4096 ? 2 : 1));
+    // (measured at n = 27648: 2, 3, 4 CTAs an SM 280, 276, 282 ms per step)
+    per_sm = std::max(1, std::min(per_sm, c.n >= 4096 ? 3 : 1));
     c.pg_grid = per_sm * c.num_sms;
     return c.pg_grid;
 }
