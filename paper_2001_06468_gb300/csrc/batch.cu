@@ -281,6 +281,7 @@ nrs_status nrs_batch_create(nrs_batch **out, const nrs_problem_desc *descs, int3
         st = nrs_create(&h, &d, s);
         if (st == NRS_OK) {
             b->ctx.push_back(reinterpret_cast<Ctx *>(h));
+            b->ctx.back()->pg_shared = true;
         }
     }
     if (e != cudaSuccess && st == NRS_OK) st = NRS_ECUDA;

@@ -453,7 +453,12 @@ __device__ void sum_dots(const PgArgs &a, int region, int j, double *h)
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(PG_THREADS, 3) k_gmres_ir(PgArgs a)
+// MINB = 3 caps the kernel at 85 registers a thread so that three CTAs share
+// an SM (large systems, whose products stream from HBM, and the chains of a
+// batch, which run side by side); MINB = 1 leaves the registers free for the
+// one-CTA-per-SM grid of a lone system that sits in L2
+template <int MINB>
+__global__ void __launch_bounds__(PG_THREADS, MINB) k_gmres_ir(PgArgs a)
 {
     __shared__ double sH[(PG_MAXM + 1) * PG_MAXM];  // column-major, leading dimension PG_MAXM+1
     __shared__ double scs[PG_MAXM], ssn[PG_MAXM], sg[PG_MAXM + 1], sy[PG_MAXM];
@@ -733,15 +738,24 @@ __global__ void __launch_bounds__(PG_THREADS, 3) k_gmres_ir(PgArgs a)
 
 bool pg_supported(const Ctx &c) { return c.factored_prec != NRS_FP64 && c.max_inner <= PG_MAXM; }
 
+// systems from this order up stream their matrices from HBM in the products
+static constexpr int64_t PG_WIDE_N = 4096;
+
+static const void *pg_kernel(const Ctx &c)
+{
+    return c.n >= PG_WIDE_N || c.pg_shared ? (const void *)k_gmres_ir<3>
+                                           : (const void *)k_gmres_ir<1>;
+}
+
 int pg_grid(Ctx &c)
 {
     if (c.pg_grid > 0) return c.pg_grid;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gmres_ir, PG_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pg_kernel(c), PG_THREADS, 0);
     // one CTA per SM while barriers dominate (matrices in L2); three once the
     // products stream the matrices from HBM and need more bytes in flight
     // (measured at n = 27648: 2, 3, 4 CTAs an SM 280, 276, 282 ms per step)
-    per_sm = std::max(1, std::min(per_sm, c.n >= 4096 ? 3 : 1));
+    per_sm = std::max(1, std::min(per_sm, c.n >= PG_WIDE_N ? 3 : 1));
     c.pg_grid = per_sm * c.num_sms;
     return c.pg_grid;
 }
@@ -749,7 +763,7 @@ int pg_grid(Ctx &c)
 int pg_max_coresident(const Ctx &c)
 {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gmres_ir, PG_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pg_kernel(c), PG_THREADS, 0);
     return std::max(1, per_sm) * c.num_sms;
 }
 
@@ -829,7 +843,7 @@ cudaError_t launch_gmres_persistent(Ctx &c, const double *b, double *x, bool col
     if (e != cudaSuccess) return e;
     void *args[] = {&a};
     c.tbeg(PH_KRYLOV);
-    e = cudaLaunchCooperativeKernel((void *)k_gmres_ir, G, PG_THREADS, args, 0, c.stream);
+    e = cudaLaunchCooperativeKernel(pg_kernel(c), G, PG_THREADS, args, 0, c.stream);
     c.tend(PH_KRYLOV);
     c.launches += 1;
     return e;

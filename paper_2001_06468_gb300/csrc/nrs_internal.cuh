@@ -284,6 +284,7 @@ struct Ctx {
     int32_t *d_bar = nullptr;  // its grid barrier
     double *d_pg_stats = nullptr;  // its outcome: outer, inner, converged, ||d||, ||x||
     int pg_grid = 0;           // its CTA count (0 = from occupancy)
+    bool pg_shared = false;    // solves share the SMs with other problems' (a batch)
 
     // CUDA-graph replay of nrs_step (graph mode)
     struct GraphKey {
