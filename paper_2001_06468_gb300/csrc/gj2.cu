@@ -448,13 +448,23 @@ __global__ void __launch_bounds__(256)
 // One inner step on the panel, rows [64 blockIdx.x, +64):
 //   rows of Kk:      P[Kk, j] = R[:, j] (j outside the own block), P[Kk, Kk] = D^{-1}
 //   the other rows:  P[i, j] -= C_i R[:, j],  P[i, Kk] = -C_i D^{-1},  C_i = P[i, Kk]
-// FP32 fused multiply-adds; P = M[:, k0 .. k0 + W).
-__global__ void __launch_bounds__(256)
+// FP32 fused multiply-adds in ascending c; P = M[:, k0 .. k0 + W).  A CTA
+// computes its 64 rows x all 256 columns at once from shared memory (C^T
+// 64 x 64 and the right-hand factor 64 x 256: 80 KB, two CTAs an SM): warp w
+// takes rows 8 w .. 8 w + 7, lane l the columns 4 l + {0..3} and 128 + 4 l +
+// {0..3}, so each step of c is four 16-byte shared loads (the C ones a
+// broadcast, the others conflict-free) for 64 FMAs, and each thread's
+// read-modify-write of a column is one 32-byte sector.
+constexpr int PU_SMEM = (64 * 64 + 64 * G2_W) * (int)sizeof(float);
+static_assert(G2_W == 256, "the panel update's thread layout covers 256 columns");
+
+__global__ void __launch_bounds__(256, 2)
     k_gj2_panel_update(int64_t n, float *__restrict__ M, int64_t lda, int64_t k0, int W, int64_t r0,
                        const float *__restrict__ Dinv, const float *__restrict__ R)
 {
-    __shared__ float Cs[64][65];
-    __shared__ __align__(16) float Rs[64][64 + 4];
+    extern __shared__ __align__(16) float pu_smem[];
+    float *Cs = pu_smem;            // [c][r] = P[i0 + r, r0 + c]
+    float *Rs = pu_smem + 64 * 64;  // [c][j]
     const int tid = threadIdx.x;
     const int64_t i0 = (int64_t)blockIdx.x * 64;
     const int kb = (int)min((int64_t)64, n - r0);
@@ -471,54 +481,99 @@ __global__ void __launch_bounds__(256)
         }
         return;
     }
-    // C = P[i0 .. i0 + 63, Kk]
-    for (int idx = tid; idx < 64 * 64; idx += 256) {
-        const int r = idx & 63, c = idx >> 6;
-        Cs[r][c] = (r < rows && c < kb) ? M[(i0 + r) + (r0 + c) * lda] : 0.0f;
+    // staging: every load of a thread issued before the first store (16-byte
+    // loads, all in flight together), then the stores
+    {
+        // C^T: four runs of 4 rows of one column each (rows i0 + 4 (t & 15) ..
+        // + 3 of column r0 + (t >> 4) + 16 u)
+        float4 cv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int idx = tid + 256 * u, r = 4 * (idx & 15), c = idx >> 4;
+            const float *src = M + (i0 + r) + (r0 + c) * lda;
+            if (c < kb && r + 4 <= rows)
+                cv[u] = *reinterpret_cast<const float4 *>(src);
+            else
+                cv[u] = make_float4(c < kb && r < rows ? src[0] : 0.0f,
+                                    c < kb && r + 1 < rows ? src[1] : 0.0f,
+                                    c < kb && r + 2 < rows ? src[2] : 0.0f,
+                                    c < kb && r + 3 < rows ? src[3] : 0.0f);
+        }
+        // the right-hand factor: R outside the own block, D^{-1} inside (zero
+        // beyond kb rows and W columns), 16 runs of 4 columns of one row
+        float4 rv[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int idx = tid + 256 * u, j = 4 * (idx & 63), c = idx >> 6;
+            const bool in_own = j >= own && j < own + 64;
+            const float *src = in_own ? Dinv + c * 64 + (j - own) : R + c * G2_W + j;
+            const int lim = in_own ? own + kb : W;  // columns below lim are live
+            if (c < kb && j + 4 <= lim)
+                rv[u] = *reinterpret_cast<const float4 *>(src);
+            else
+                rv[u] = make_float4(c < kb && j < lim ? src[0] : 0.0f,
+                                    c < kb && j + 1 < lim ? src[1] : 0.0f,
+                                    c < kb && j + 2 < lim ? src[2] : 0.0f,
+                                    c < kb && j + 3 < lim ? src[3] : 0.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int idx = tid + 256 * u, r = 4 * (idx & 15), c = idx >> 4;
+            *reinterpret_cast<float4 *>(Cs + c * 64 + r) = cv[u];
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int idx = tid + 256 * u, j = 4 * (idx & 63), c = idx >> 6;
+            *reinterpret_cast<float4 *>(Rs + c * G2_W + j) = rv[u];
+        }
     }
-    // thread: rows rr0..rr0+3 (of 64), columns of a 64-wide slice jj0..jj0+3
-    const int rr0 = 4 * (tid & 15), jj0 = 4 * (tid >> 4);
-    for (int js = 0; js < W; js += 64) {
-        __syncthreads();
-        // the slice's R (or D^{-1} for the own block), 64 x 64
-        const bool in_own = (js == own);
-        for (int idx = tid; idx < 64 * 64; idx += 256) {
-            const int c = idx >> 6, j = idx & 63;
-            float v = 0.0f;
-            if (c < kb) {
-                if (in_own) v = (j < kb) ? Dinv[c * 64 + j] : 0.0f;
-                else if (js + j < W) v = R[c * G2_W + js + j];
+    __syncthreads();
+    const int rg = tid >> 5, cg = tid & 31;
+    float acc[8][8];
+#pragma unroll
+    for (int x = 0; x < 8; ++x)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) acc[x][y] = 0.0f;
+#pragma unroll 4
+    for (int c = 0; c < 64; ++c) {
+        const float4 ca = *reinterpret_cast<const float4 *>(Cs + c * 64 + 8 * rg);
+        const float4 cb = *reinterpret_cast<const float4 *>(Cs + c * 64 + 8 * rg + 4);
+        const float4 ba = *reinterpret_cast<const float4 *>(Rs + c * G2_W + 4 * cg);
+        const float4 bb = *reinterpret_cast<const float4 *>(Rs + c * G2_W + 128 + 4 * cg);
+        const float cv[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+        const float rv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+        for (int x = 0; x < 8; ++x)
+#pragma unroll
+            for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(cv[x], rv[y], acc[x][y]);
+    }
+    const bool full = 8 * rg + 8 <= rows;
+#pragma unroll
+    for (int y = 0; y < 8; ++y) {
+        const int j = (y < 4 ? 4 * cg : 128 + 4 * cg) + (y & 3);
+        if (j >= W) continue;
+        const bool in_own = j >= own && j < own + 64;
+        if (in_own && j - own >= kb) continue;
+        float *p = M + (k0 + j) * lda + i0 + 8 * rg;
+        if (full) {
+            // lda is a multiple of 32 and i0 of 64: 32-byte aligned
+            float4 *p4 = reinterpret_cast<float4 *>(p);
+            float4 u = in_own ? make_float4(0.f, 0.f, 0.f, 0.f) : p4[0];
+            float4 v = in_own ? make_float4(0.f, 0.f, 0.f, 0.f) : p4[1];
+            if (in_own) {
+                u = make_float4(-acc[0][y], -acc[1][y], -acc[2][y], -acc[3][y]);
+                v = make_float4(-acc[4][y], -acc[5][y], -acc[6][y], -acc[7][y]);
+            } else {
+                u = make_float4(u.x - acc[0][y], u.y - acc[1][y], u.z - acc[2][y], u.w - acc[3][y]);
+                v = make_float4(v.x - acc[4][y], v.y - acc[5][y], v.z - acc[6][y], v.w - acc[7][y]);
             }
-            Rs[c][j] = v;
-        }
-        __syncthreads();
-        float acc[4][4] = {};
-#pragma unroll 8
-        for (int c = 0; c < 64; ++c) {
-            float cv[4];
+            p4[0] = u;
+            p4[1] = v;
+        } else {
 #pragma unroll
-            for (int x = 0; x < 4; ++x) cv[x] = Cs[rr0 + x][c];
-            const float4 rv = *reinterpret_cast<const float4 *>(&Rs[c][jj0]);
-            const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
-#pragma unroll
-            for (int x = 0; x < 4; ++x)
-#pragma unroll
-                for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(cv[x], rr[y], acc[x][y]);
-        }
-#pragma unroll
-        for (int y = 0; y < 4; ++y) {
-            const int j = js + jj0 + y;
-            if (j >= W) continue;
-#pragma unroll
-            for (int x = 0; x < 4; ++x) {
-                const int r = rr0 + x;
-                if (r >= rows) continue;
-                float *p = M + (i0 + r) + (k0 + j) * lda;
-                if (in_own) {
-                    if (jj0 + y < kb) *p = -acc[x][y];
-                } else {
-                    *p = *p - acc[x][y];
-                }
+            for (int x = 0; x < 8; ++x) {
+                if (8 * rg + x >= rows) continue;
+                p[x] = in_own ? -acc[x][y] : p[x] - acc[x][y];
             }
         }
     }
@@ -799,6 +854,8 @@ int run_gj2_fp32(Ctx &c, float *M, int64_t lda, bool f16)
                              G2_SMEM);
         cudaFuncSetAttribute(k_tc_gj2_update<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              G2_SMEM);
+        cudaFuncSetAttribute(k_gj2_panel_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             PU_SMEM);
         attr = true;
     }
     const size_t diag_smem = gj_diag_smem();
@@ -817,8 +874,8 @@ int run_gj2_fp32(Ctx &c, float *M, int64_t lda, bool f16)
             k_gj_diag_launch(c, n, M, lda, r0, c.d_gj_dinv, diag_smem, S);
             k_gj2_rpanel<<<(unsigned)ceil_div(W, 64), 256, 0, S>>>(n, M, lda, k0, W, r0,
                                                                  c.d_gj_dinv, c.d_gj2_r);
-            k_gj2_panel_update<<<(unsigned)ceil_div(n, 64), 256, 0, S>>>(n, M, lda, k0, W, r0,
-                                                                       c.d_gj_dinv, c.d_gj2_r);
+            k_gj2_panel_update<<<(unsigned)ceil_div(n, 64), 256, PU_SMEM, S>>>(
+                n, M, lda, k0, W, r0, c.d_gj_dinv, c.d_gj2_r);
             c.launches += 3;
         }
         if (f16)
