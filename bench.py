@@ -565,7 +565,7 @@ def headline(nrs, args, ws, local, timer, peaks, peak_src):
     sol_h = torch.empty(2 * pr.n, dtype=torch.float64).pin_memory()
     h2d = sum(t.numel() * t.element_size() for st in host[0] for t in st)
     d2h = sol_h.numel() * 8 + pr.n_free * 12 * 8
-    Ke = min(K, 5)
+    Ke = K  # the same steps as the timed region (refreshed and reused factors alternate)
 
     def e2e_step(s):
         for st_h, st_d in zip(host[s], bufs):

@@ -432,7 +432,9 @@ nrs_status nrs_get_tracers(nrs_ctx *ctx, double *xp);
  * offsets, before any work is enqueued; NRS_ECUDA if a copy or clear of the
  * scratch or a launch fails.  The first call on a device looks up
  * the scratch's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call shares
+ * current.  Every call copies n_off and q_off from the caller's (pageable)
+ * host memory with cudaMemcpyAsync, so no call may be captured into a CUDA
+ * graph: a replay would read host buffers that may be gone.  Every call shares
  * the same scratch, which keeps the last call's contents (each call clears
  * what must start at zero): calls that overlap on the GPU -- on different
  * streams, or from several threads -- race and must be serialised by the
