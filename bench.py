@@ -212,11 +212,12 @@ NCU_TRAFFIC = {
                   "scale": "none (the 64 x 64 block, the previous D^{-1} and two 64 x 64 tiles)"},
     "k_assemble64": {"bytes": None, "file": "paper_2001_06468_gb300/csrc/assemble.cu",
                      "sha1": "", "scale": None},
-    # one solve at n = 13824 (cold start, 2 refinement steps, 4 GMRES iterations;
-    # the three-CTAs-per-SM variant on 456 CTAs): 16.108 + 0.066 GB against 7
-    # passes over A (8 n^2) and M (4 n^2) = 16.05 GB
-    "k_gmres_ir": {"bytes": None, "ratio": (16108150016 + 65733120) / (12.0 * 13824 ** 2 * 7),
-                   "file": "paper_2001_06468_gb300/csrc/gmres_persistent.cu", "sha1": "cdd4d9e600df",
+    # one solve at n = 13824 (cold start, 2 refinement steps -- the first on a
+    # working-precision residual, the second on the exact one -- and 4 GMRES
+    # iterations; the three-CTAs-per-SM variant on 456 CTAs): 16.100 + 0.056 GB
+    # against 7 passes over A (8 n^2) and M (4 n^2) = 16.05 GB
+    "k_gmres_ir": {"bytes": None, "ratio": (16100048384 + 55837184) / (12.0 * 13824 ** 2 * 7),
+                   "file": "paper_2001_06468_gb300/csrc/gmres_persistent.cu", "sha1": "a9a7fde8af4d",
                    "scale": "traffic / algorithmic bytes at n = 13824, times the record's bytes"},
 }
 
@@ -306,12 +307,15 @@ def rooflines(ph_ms, ph_spans, n, pairs, peaks, peak_src, sm_mhz, solve_stats, p
       lu_diag     k_gj_diag: (2 + 8 (nblk - 1)) / nblk x 64^3 FP32 flops, one CTA
       assemble    k_assemble64: 40 FP64 operations per (force, quadrature) pair
       assemble32  k_assemble32: N Q pairs against the FP32 pair peak (20 instructions a pair)
-      krylov      k_gmres_ir: (outer + inner) 8 n^2 (A in FP64, or its float-pair copy
-                  for the GMRES products: also 8 bytes an entry) + (outer + inner + 1)
-                  4 n^2 bytes; + 8 n^2 (||A||_inf, once per launch);
-                  outer x 3 n^2 (extended residual: product, its error, the error
-                  sum; the products' sum on the integer pipe) + n^2 (||A||_inf) +
-                  inner x n^2 (the GMRES products, when in FP64) FP64 operations"""
+      krylov      k_gmres_ir: (exact + working + inner) 8 n^2 (the residuals'
+                  products, exact from A in FP64 or in working precision from its
+                  float-pair copy, and the GMRES products: 8 bytes an entry each)
+                  + (outer + inner + 1) 4 n^2 bytes of M; + 8 n^2 (||A||_inf, once
+                  per launch); exact x 3 n^2 (extended residual: product, its error,
+                  the error sum; the products' sum on the integer pipe) + n^2
+                  (||A||_inf) + (inner + working) x n^2 (the GMRES and residual
+                  products, when in FP64) FP64 operations.  Without the residual
+                  counts, every refinement step counts one exact residual."""
     P = derived_peaks(peaks, sm_mhz)
 
     def per_launch(ph):
@@ -415,11 +419,14 @@ def rooflines(ph_ms, ph_spans, n, pairs, peaks, peak_src, sm_mhz, solve_stats, p
             "traffic": None}
     if ph_spans.get("krylov") and solve_stats:
         o, i = solve_stats["outer_mean"], solve_stats["inner_mean"]
+        ex = solve_stats.get("exact_mean", o)
+        wk = solve_stats.get("working_mean", 0.0)
         t = per_launch("krylov")
-        b = 8.0 * n * n * (o + i + 1) + 4.0 * n * n * (o + i + 1)
-        # FP64 operations: the residuals, the ||A||_inf pass, and the GMRES
-        # products unless they run on the float-pair copy (FP32 pipe)
-        ops = RES_OPS_PER_ENTRY * n * n * o + n * n * (1 + (0 if arnoldi_df else i))
+        b = 8.0 * n * n * (ex + wk + i + 1) + 4.0 * n * n * (o + i + 1)
+        # FP64 operations: the exact residuals, the ||A||_inf pass, and the
+        # GMRES and working-precision residual products unless they run on the
+        # float-pair copy (FP32 pipe)
+        ops = RES_OPS_PER_ENTRY * n * n * ex + n * n * (1 + (0 if arnoldi_df else i + wk))
         recs["krylov"] = {
             "kernel": "k_gmres_ir (persistent GMRES-IR, one cooperative launch per solve)",
             "bound": "hbm", "achieved": b / t / 1e9, "peak": P["hbm_gbs"], "unit": "GB/s",
@@ -589,19 +596,22 @@ def headline(nrs, args, ws, local, timer, peaks, peak_src):
     for s in range(W):
         stepper(ctx)(s)
     torch.cuda.synchronize()
-    ci0 = ctx.counters()
+    ci0, ri0 = ctx.counters(), ctx.residual_counters()
     ctx.set_timing(True)
     instr_ms = timer.run(ctx.stream, stepper(ctx), Ki, first=W)
     trace = ctx.get_trace()
     phases, _ = ctx.get_timing()
     ctx.set_timing(False)
-    ci1 = ctx.counters()
+    ci1, ri1 = ctx.counters(), ctx.residual_counters()
     ctx.close()
     ph_ms = {k: v[0] for k, v in phases.items()}
     ph_spans = {k: v[1] for k, v in phases.items()}
     solves = max(ci1["solves"] - ci0["solves"], 1)
     solve_stats = {"outer_mean": (ci1["outer"] - ci0["outer"]) / solves,
                    "inner_mean": (ci1["inner"] - ci0["inner"]) / solves}
+    if ri1["exact"] + ri1["working"] > ri0["exact"] + ri0["working"]:
+        solve_stats["exact_mean"] = (ri1["exact"] - ri0["exact"]) / solves
+        solve_stats["working_mean"] = (ri1["working"] - ri0["working"]) / solves
 
     # -- the same workload with a fresh factor at every stage, recorded as a
     # CUDA graph, and its instrumented phases (the factorisation's kernels)
@@ -1013,7 +1023,8 @@ def profile_solve(args):
     ctx.factor(args.prec)
     _, rep = ctx.solve(b, check=False)
     torch.cuda.synchronize()
-    print(json.dumps({"workload": args.workload, "n": pr.n, "prec": args.prec, "report": rep[0]}))
+    print(json.dumps({"workload": args.workload, "n": pr.n, "prec": args.prec, "report": rep[0],
+                      "residuals": ctx.residual_counters()}))
 
 
 

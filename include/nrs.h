@@ -368,6 +368,16 @@ nrs_status nrs_sync(nrs_ctx *ctx);
 nrs_status nrs_counters(const nrs_ctx *ctx, int64_t *factorizations, int64_t *solves,
                         int64_t *outer, int64_t *inner, int64_t *retries);
 
+/* Residuals b - A x that the refinement of those solves formed (host
+ * outputs, each may be NULL): `exact` at the residual precision the context
+ * was created with (extended, Sec. 4's three-precision refinement, or FP64),
+ * `working` in working precision from the float-pair copy or the FP64 matrix
+ * (formed while the normwise backward error is at least 1e-8, whether the
+ * step then kept it or formed the exact one as well).  Each refinement step
+ * keeps one of them, so exact + working >= the counted refinement steps.
+ * Plain reads of host state: no synchronisation. */
+nrs_status nrs_residual_counters(const nrs_ctx *ctx, int64_t *exact, int64_t *working);
+
 /* Fluid velocity at field points (Sec. 3: the NEAREST boundary integral
  * evaluated off the body, the quantity the paper's particle-tracking
  * examples integrate):

@@ -1452,6 +1452,15 @@ nrs_status nrs_counters(const nrs_ctx *ctx, int64_t *factorizations, int64_t *so
     return NRS_OK;
 }
 
+nrs_status nrs_residual_counters(const nrs_ctx *ctx, int64_t *exact, int64_t *working)
+{
+    const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+    if (!c) return NRS_EINVAL;
+    if (exact) *exact = c->res_exact_total;
+    if (working) *working = c->res_work_total;
+    return NRS_OK;
+}
+
 nrs_status nrs_sync(nrs_ctx *ctx)
 {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);

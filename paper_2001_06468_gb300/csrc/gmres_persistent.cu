@@ -67,7 +67,8 @@ struct PgArgs {
     int32_t *bar;         // grid barrier: [0] arrivals since the launch ([1] unused)
     int32_t *status;
     double *out;          // [0] outer steps, [1] inner iterations, [2] converged,
-                          // [3] ||d||_inf, [4] ||x||_inf
+                          // [3] ||d||_inf, [4] ||x||_inf, [5] exact residuals,
+                          // [6] working-precision residuals (kept or not)
     double tol, floor, tol_in;
     int m, max_outer, cold, dch;
     int rc64, s64, rc32, s32;
@@ -457,6 +458,12 @@ __device__ void sum_dots(const PgArgs &a, int region, int j, double *h)
 // an SM (large systems, whose products stream from HBM, and the chains of a
 // batch, which run side by side); MINB = 1 leaves the registers free for the
 // one-CTA-per-SM grid of a lone system that sits in L2
+// working-precision residuals in the refinement: the smallest backward error
+// at which one is used, and the expected reduction of the backward error by
+// one correction (negative: ten times the inner tolerance)
+constexpr double PG_CHEAP_ETA = 1e-8;
+constexpr double PG_CHEAP_RED = -1.0;
+
 template <int MINB>
 __global__ void __launch_bounds__(PG_THREADS, MINB) k_gmres_ir(PgArgs a)
 {
@@ -511,10 +518,59 @@ __global__ void __launch_bounds__(PG_THREADS, MINB) k_gmres_ir(PgArgs a)
         normA = chunk_total(a, 1, 2, true, sred);
         xn = chunk_total(a, 0, 1, true, sred);
     }
+    double eta_prev = INFINITY;  // backward error of the previous step's residual
+    int n_exact = 0, n_work = 0;  // residuals formed: exact (or FP64), working precision
     for (outer = 0; outer < a.max_outer; ++outer) {
+        // While the residual is large, a working-precision residual serves the
+        // correction as well as the exact one: its error, about 2^-46 (|A| |x|)_i
+        // (the float-pair product, or the FP64 one), is at most ~1e-4 of r once
+        // the normwise backward error eta = ||r|| / (||A|| ||x|| + ||b||) is at
+        // least PG_CHEAP_ETA, below the correction's own tolerance.  It is tried
+        // first when the previous residual's eta, times the reduction a
+        // correction is expected to bring, is still at least PG_CHEAP_ETA, and
+        // kept if its own eta is; otherwise the exact residual is formed.  A
+        // step on a working-precision residual never ends the refinement.
+        bool cheap = false;
+        const double red = PG_CHEAP_RED < 0.0 ? 10.0 * a.tol_in : PG_CHEAP_RED;
+        if (a.dd && eta_prev * red >= PG_CHEAP_ETA) {
+            if (a.Adf) {
+                for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS)
+                    a.Vf[e] = df_split(__ldcg(a.x + e));
+                if (!grid_sync(a, &s_ok, tgt)) return;
+                mv64df_partial(a, 1.0, smv);
+            } else {
+                mv64_partial<false>(a, a.x, 1.0, smv);
+            }
+            if (!grid_sync(a, &s_ok, tgt)) return;
+            double rmax = 0.0, bmax = 0.0;
+            for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
+                const double be = __ldg(a.b + e);
+                const double re = be - sum_parts(a, a.s64, e);
+                a.w[e] = re;
+                a.vf[e] = df_split(re);
+                rmax = fmax(rmax, fabs(re));
+                bmax = fmax(bmax, fabs(be));
+                if (!isfinite(re)) rmax = INFINITY;
+            }
+            rmax = block_max_all(rmax, sred);
+            bmax = block_max_all(bmax, sred);
+            if (owner && threadIdx.x == 0) {
+                dp1[0] = rmax;
+                dp1[1] = bmax;
+            }
+            if (!grid_sync(a, &s_ok, tgt)) return;
+            const double rn = chunk_total(a, 1, 0, true, sred);
+            const double bn = chunk_total(a, 1, 1, true, sred);
+            const double eta = rn / (normA * xn + bn);
+            cheap = isfinite(rn) && eta >= PG_CHEAP_ETA;
+            eta_prev = eta;
+            ++n_work;
+        }
+        if (!cheap) {
         // r = b - A x (exact products and error sums, or FP64), with ||r||_inf
         // and ||b||_inf per chunk; xn is ||x||_inf of this x
         const int fxc = a.dd ? fx_anchor(normA, xn) : 0;
+        ++n_exact;
         if (a.dd)
             mv64fx_partial(a, a.x, fxc, smv);
         else
@@ -540,7 +596,13 @@ __global__ void __launch_bounds__(PG_THREADS, MINB) k_gmres_ir(PgArgs a)
             }
         }
         if (!grid_sync(a, &s_ok, tgt)) return;
-        if (stagnant) {
+        if (a.dd) {
+            const double rn = chunk_total(a, 1, 0, true, sred);
+            const double bn = chunk_total(a, 1, 1, true, sred);
+            eta_prev = rn / (normA * xn + bn);
+        }
+        }  // exact (or FP64) residual
+        if (stagnant && !cheap) {
             // The corrections stopped shrinking.  If x already solves a nearby
             // system to working precision (normwise backward error
             // ||r|| / (||A|| ||x|| + ||b||) <= 1e-15), further steps only
@@ -710,6 +772,8 @@ __global__ void __launch_bounds__(PG_THREADS, MINB) k_gmres_ir(PgArgs a)
         if (!isfinite(dn) || !isfinite(xn)) {
             if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.status, ST_NONFINITE);
             done = true;
+        } else if (cheap) {
+            // a correction from a working-precision residual: go on
         } else if (dn <= a.tol * xn) {
             done = true;
         } else if (dn_prev > 0.0 && dn * (dn / dn_prev) <= 1e-3 * a.tol * xn) {
@@ -731,6 +795,8 @@ __global__ void __launch_bounds__(PG_THREADS, MINB) k_gmres_ir(PgArgs a)
         a.out[2] = converged;
         a.out[3] = dn;
         a.out[4] = xn;
+        a.out[5] = n_exact;
+        a.out[6] = n_work;
     }
 }
 

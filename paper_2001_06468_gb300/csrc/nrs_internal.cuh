@@ -258,6 +258,7 @@ struct Ctx {
     int64_t factorizations = 0;
     int64_t retries = 0;       // stages solved again after a non-converged refinement (nrs_step)
     int64_t solves = 0, outer_total = 0, inner_total = 0;  // solves finished on the host side
+    int64_t res_exact_total = 0, res_work_total = 0;  // their residuals: exact, working precision
 
     // learned starting guess (mlp.cu); allocated by the first nrs_mlp_* call
     bool mlp_alloc = false, mlp_params_set = false, mlp_scales_set = false;

@@ -671,7 +671,7 @@ static nrs_status run_gmres_ir_device(Ctx &c, const double *b, double *x, const 
     cudaError_t e = cudaSuccess;
     if (x0) e = cudaMemcpyAsync(x, x0, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, c.stream);
     if (e == cudaSuccess) e = launch_gmres_persistent(c, b, x, x0 == nullptr, c.d_pg_stats);
-    double st[5] = {0, 0, 0, 0, 0};
+    double st[7] = {0, 0, 0, 0, 0, 0, 0};
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(st, c.d_pg_stats, sizeof(st), cudaMemcpyDeviceToHost, c.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
@@ -679,6 +679,8 @@ static nrs_status run_gmres_ir_device(Ctx &c, const double *b, double *x, const 
         c.err = std::string("CUDA error in solve: ") + cudaGetErrorString(e);
         return NRS_ECUDA;
     }
+    c.res_exact_total += (int64_t)st[5];
+    c.res_work_total += (int64_t)st[6];
     return finish_solve(c, b, x, rep, inner_out, (int)st[0], (int)st[1], st[2] != 0.0, st + 3);
 }
 
@@ -793,6 +795,7 @@ nrs_status run_gmres_ir(Ctx &c, const double *b, double *x, const double *x0, nr
         }
     }
 #undef CKE
+    c.res_exact_total += outer;  // one residual (exact, or FP64) a refinement step
     return finish_solve(c, b, x, rep, inner_out, outer, inner_total, converged);
 }
 

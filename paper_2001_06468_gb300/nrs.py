@@ -37,6 +37,7 @@ FREE, PRESCRIBED, STATIC = 0, 1, 2
 EXPORTS = ["nrs_create", "nrs_destroy", "nrs_last_error", "nrs_sizes", "nrs_set_state",
            "nrs_get_state", "nrs_set_external", "nrs_kinematics", "nrs_nearest_build",
            "nrs_assemble", "nrs_factor", "nrs_solve", "nrs_residual", "nrs_step", "nrs_sync", "nrs_counters",
+           "nrs_residual_counters",
            "nrs_velocity", "nrs_set_tracers", "nrs_get_tracers", "nrs_dp_start",
            "nrs_dp_next_time", "nrs_dp_stage", "nrs_dp_info_get",
            "nrs_set_timing",
@@ -132,6 +133,7 @@ _sig = {
                                 _P, ctypes.POINTER(StepReport)]),
     "nrs_sync": (ctypes.c_int, [_P]),
     "nrs_counters": (ctypes.c_int, [_P, _I64P, _I64P, _I64P, _I64P, _I64P]),
+    "nrs_residual_counters": (ctypes.c_int, [_P, _I64P, _I64P]),
     "nrs_velocity": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
     "nrs_set_tracers": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
     "nrs_get_tracers": (ctypes.c_int, [_P, _P]),
@@ -419,6 +421,12 @@ class Context:
         self._check(_lib.nrs_counters(self._h, *(ctypes.byref(x) for x in v)))
         return dict(zip(("factorizations", "solves", "outer", "inner", "retries"),
                         (x.value for x in v)))
+
+    def residual_counters(self):
+        """{'exact', 'working'}: residuals the refinement formed since creation."""
+        v = [ctypes.c_int64() for _ in range(2)]
+        self._check(_lib.nrs_residual_counters(self._h, *(ctypes.byref(x) for x in v)))
+        return {"exact": v[0].value, "working": v[1].value}
 
     def rank64_update(self, Mt: torch.Tensor, C: torch.Tensor, Rt: torch.Tensor, prec: str = "tf32"):
         """M -= C Rt^T in place; Mt is the (n_cols, lda) storage of the

@@ -144,3 +144,20 @@ def test_float_pair_gmres_products_leave_the_fp64_count():
     t = a["ms_per_launch"] / 1e3
     assert (a["fp64_gops"] - b["fp64_gops"]) * 1e9 * t == pytest.approx(
         SOLVE["inner_mean"] * N_SYS ** 2)
+
+
+def test_working_precision_residuals_are_counted_as_what_they_are():
+    # 3.5 refinement steps a solve, 2 of them on an exact residual and 2.5
+    # working-precision residuals formed (1.5 kept, 1 rejected): 4.5 + 20 + 1
+    # passes over an 8-byte matrix, 24.5 over M; FP64 work only in the exact
+    # residuals and the ||A||_inf pass when the other products use the
+    # float-pair copy, the working-precision products added when they do not
+    ms, spans = _phases(assemble=(80.0, 1), krylov=(100.0, 1))
+    st = dict(SOLVE, exact_mean=2.0, working_mean=2.5)
+    k = bench.rooflines(ms, spans, N_SYS, PAIRS, PEAKS, "measured", SM_MHZ, st,
+                        arnoldi_df=True)["krylov"]
+    assert k["work_per_launch"] == pytest.approx(8.0 * N_SYS ** 2 * 25.5 + 4.0 * N_SYS ** 2 * 24.5)
+    t = k["ms_per_launch"] / 1e3
+    assert k["fp64_gops"] * 1e9 * t == pytest.approx((3 * 2.0 + 1) * N_SYS ** 2)
+    f = bench.rooflines(ms, spans, N_SYS, PAIRS, PEAKS, "measured", SM_MHZ, st)["krylov"]
+    assert f["fp64_gops"] * 1e9 * t == pytest.approx((3 * 2.0 + 1 + 20.0 + 2.5) * N_SYS ** 2)

@@ -177,3 +177,36 @@ def test_residual_requires_an_assembly(N):
         ctx.residual(z, z)
     assert ei.value.status == N.NRS_EINVAL
     ctx.close()
+
+
+@pytest.mark.parametrize("arnoldi", ["fp64", "df"])
+def test_refinement_ends_on_an_exact_residual(N, arnoldi):
+    # From a cold start (x = M b, backward error far above 1e-8) the first
+    # refinement step keeps a working-precision residual; the refinement may
+    # not end on one, so at least one exact residual follows, every step kept
+    # one of the two, and the answer is the oracle's to working accuracy
+    # (backward error in the oracle's FP64 system, double-double residual).
+    pr = g.swimmer_config(ns_f=40, nth_f=6, ns_q=200, nth_q=10)
+    sh = g.pack_shapes(pr, 0.25)
+    ctx = N.Context.from_problem(pr, factor_prec="tf32", arnoldi=arnoldi)
+    Y = g.initial_state(pr)
+    ctx.set_state(Y["x0"], Y["B"])
+    xi, Xiw, xidot = N.shapes_to_device(sh)
+    x, Xw, b = ctx.kinematics(xi, Xiw, xidot)
+    ctx.nearest_build(xi, Xiw)
+    At = ctx.assemble(x, Xw)
+    assert ctx.factor("tf32") == 0
+    r0, c0 = ctx.residual_counters(), ctx.counters()
+    xg, rep = ctx.solve(b)
+    r1, c1 = ctx.residual_counters(), ctx.counters()
+    assert rep[0]["converged"], rep
+    exact, working = r1["exact"] - r0["exact"], r1["working"] - r0["working"]
+    outer = c1["outer"] - c0["outer"]
+    assert working >= 1 and exact >= 1, (exact, working, rep)
+    assert exact + working >= outer >= 2, (exact, working, outer)
+    A = At.T.cpu().numpy()
+    bh, xs = b.cpu().numpy(), xg.cpu().numpy()
+    r = O.residual_dd(A, xs, bh)
+    berr = np.max(np.abs(r)) / (np.max(np.sum(np.abs(A), axis=1)) * np.max(np.abs(xs))
+                                + np.max(np.abs(bh)))
+    assert berr <= 1e-15, berr
