@@ -53,7 +53,14 @@ constexpr int G2_RING = 4;                 // claimed tile indices in flight (pr
 constexpr int GJ2_PANEL_SMS = 24;
 constexpr int G2_SMEM = G2_STAGES * G2_STAGE_BYTES + 1024;
 constexpr int G2_EPI_WARPS = 16;         // four per accumulator lane quarter, 64 columns each
+constexpr int G2_EPI_PARTS = G2_EPI_WARPS / 4;  // column parts of a tile (one warp a lane quarter each)
+constexpr int G2_CPW = G2_BN / G2_EPI_PARTS;    // columns of an epilogue warp
+static_assert(G2_EPI_WARPS % 4 == 0 && G2_CPW % 32 == 0, "epilogue warps in lane-quarter groups");
 constexpr int G2_THREADS = 64 + 32 * G2_EPI_WARPS;
+// register budget of about 96 a thread whatever the warp count (the launch
+// bound's block count only sets it: one CTA fits an SM), so that the rest of
+// the SM's registers stay with the FP64 assembly beside the factorisation
+constexpr int G2_MINB = 65536 / (G2_THREADS * 96) > 0 ? 65536 / (G2_THREADS * 96) : 1;
 constexpr int G2_TMEM_COLS = 2 * G2_BN;    // two accumulators
 
 __device__ __forceinline__ void g2_arrive(uint64_t *bar)
@@ -78,7 +85,7 @@ __device__ __forceinline__ void g2_tile(int64_t t, int nrt, const G2Cols &cc, in
 
 // L2 prefetch of the lines of M that epilogue warp (lane quarter q, column
 // part `part`) of tile t will read: 32 rows x 4 bytes = one 128-byte line per
-// column, lane l taking columns l and l + 32 of the part's 64.  Only lines
+// column, lane l taking columns l, l + 32, ... of the part's G2_CPW.  Only lines
 // whose first row is below n (and so whole inside the column's lda rows).
 __device__ __forceinline__ void l2_prefetch_part(const float *M, int64_t lda, int64_t n,
                                                  int64_t t, int nrt, const G2Cols &cc, int q,
@@ -89,8 +96,8 @@ __device__ __forceinline__ void l2_prefetch_part(const float *M, int64_t lda, in
     const int64_t r0 = (int64_t)rt * G2_BM + q * 32;
     if (r0 >= n) return;
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int64_t col = (int64_t)ct * G2_BN + part * (G2_BN / 4) + lane + 32 * k;
+    for (int k = 0; k < G2_CPW / 32; ++k) {
+        const int64_t col = (int64_t)ct * G2_BN + part * G2_CPW + lane + 32 * k;
         if (col < n)
             asm volatile("prefetch.global.L2 [%0];" ::"l"(M + r0 + col * lda) : "memory");
     }
@@ -103,7 +110,7 @@ __device__ __forceinline__ void l2_prefetch_part(const float *M, int64_t lda, in
 // scaled FP16 pieces (kind::f16, 64 K a stage), row i of A and row j of B
 // stored times 2^e_i, 2^f_j, undone by sA[i] = 2^-e_i, sB[j] = 2^-f_j here.
 template <bool F16>
-__global__ void __launch_bounds__(G2_THREADS, 1)
+__global__ void __launch_bounds__(G2_THREADS, G2_MINB)
     k_tc_gj2_update(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                     const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
                     int64_t n, float *__restrict__ M, int64_t lda, int nrt, G2Cols cc,
@@ -118,7 +125,7 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
     __shared__ long long s_tile[G2_RING];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
-    __shared__ float s_scale[G2_EPI_WARPS][G2_BN / 4];  // FP16 variant: column scales per warp
+    __shared__ float s_scale[G2_EPI_WARPS][G2_CPW];  // FP16 variant: column scales per warp
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -264,13 +271,13 @@ __global__ void __launch_bounds__(G2_THREADS, 1)
         }
     } else {
         // ---- epilogue: warp w reads accumulator lanes 32 (w % 4) .. + 31 (the
-        // quarter its rank in the warpgroup may access) and 64 of the 256
+        // quarter its rank in the warpgroup may access) and G2_CPW of the 256
         // columns, 16 at a time; the next 16 columns of M (of this tile, or the
         // first ones of the CTA's next tile when its index is already out) are
         // loaded while the current ones are added and stored.  The FP16
         // variant's column scales of the tile are staged once per tile in
         // shared memory.
-        constexpr int CW = 16, CPW = G2_BN / 4, NCHK = CPW / CW;
+        constexpr int CW = 16, CPW = G2_CPW, NCHK = CPW / CW;
         const int q = warp & 3, part = (warp - 2) >> 2;
         float *scl = s_scale[warp - 2];
         float *p = nullptr;
