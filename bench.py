@@ -202,10 +202,10 @@ NCU_TRAFFIC = {
     "k_tc_gj_update": {"bytes": 150743296 + 77540181, "n": 6006,
                        "file": "paper_2001_06468_gb300/csrc/tc_gemm.cu", "sha1": "e38e9748bdee",
                        "scale": "n^2 (captured at n = 6006, matrix larger than L2)"},
-    # the bulk launch of block 5 at n = 13824: 817.4 + 674.6 MB against 8 x 13824 x
+    # the bulk launch of block 5 at n = 13824: 817.7 + 674.5 MB against 8 x 13824 x
     # 13312 = 1.472 GB of M read and written
-    "k_tc_gj2_update": {"bytes": None, "ratio": (817380352 + 674585088) / (8.0 * 13824 * 13312),
-                        "file": "paper_2001_06468_gb300/csrc/gj2.cu", "sha1": "c707d500eb55",
+    "k_tc_gj2_update": {"bytes": None, "ratio": (817686528 + 674459392) / (8.0 * 13824 * 13312),
+                        "file": "paper_2001_06468_gb300/csrc/gj2.cu", "sha1": "d617a4c644e5",
                         "scale": "traffic / algorithmic bytes at n = 13824, times the record's bytes"},
     "k_gj_diag": {"bytes": 136832, "file": "paper_2001_06468_gb300/csrc/gj.cu",
                   "sha1": "d098875a34c5",
@@ -214,10 +214,10 @@ NCU_TRAFFIC = {
                      "sha1": "", "scale": None},
     # one solve at n = 13824 (cold start, 2 refinement steps -- the first on a
     # working-precision residual, the second on the exact one -- and 4 GMRES
-    # iterations; the three-CTAs-per-SM variant on 456 CTAs): 16.100 + 0.056 GB
+    # iterations; the three-CTAs-per-SM variant on 456 CTAs): 16.101 + 0.056 GB
     # against 7 passes over A (8 n^2) and M (4 n^2) = 16.05 GB
-    "k_gmres_ir": {"bytes": None, "ratio": (16100048384 + 55837184) / (12.0 * 13824 ** 2 * 7),
-                   "file": "paper_2001_06468_gb300/csrc/gmres_persistent.cu", "sha1": "a9a7fde8af4d",
+    "k_gmres_ir": {"bytes": None, "ratio": (16100587008 + 56127744) / (12.0 * 13824 ** 2 * 7),
+                   "file": "paper_2001_06468_gb300/csrc/gmres_persistent.cu", "sha1": "b0ab3387af81",
                    "scale": "traffic / algorithmic bytes at n = 13824, times the record's bytes"},
 }
 
@@ -551,16 +551,17 @@ def headline(nrs, args, ws, local, timer, peaks, peak_src):
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
-    c0 = ctx.counters()
+    c0, r0 = ctx.counters(), ctx.residual_counters()
     ctx.get_timing()  # clears the kernel count
     with ClockSampler(_visible_gpu_index(local)) as clk:
         step_ms = timer.run(ctx.stream, stepper(ctx), K, first=W)
     clocks = clk.summary()
     _, launches = ctx.get_timing()
-    c1 = ctx.counters()
+    c1, r1 = ctx.counters(), ctx.residual_counters()
     st = ctx.sync()  # device status word after the timed region
     ctx.close()
     counts = {k: c1[k] - c0[k] for k in c1}
+    counts.update({"residuals_" + k: r1[k] - r0[k] for k in r1})
     t_local = sum(step_ms) / 1e3
     t_max = _max_over_ranks(t_local, ws)
 
@@ -1165,7 +1166,8 @@ def run_nrs(args):
         "config": {"workload": WORKLOADS_DESC[HEADLINE], "factor": "FP32 explicit inverse (two-level "
                    "blocked Gauss-Jordan, rank-256 tensor-core updates from scaled FP16 pairs; "
                    f"--prec {args.prec}), refreshed after >40 GMRES iterations or 32 stages",
-                   "refinement": "GMRES-IR, extended residual (exact fixed-point product sums), "
+                   "refinement": "GMRES-IR, extended residual (exact fixed-point product sums; "
+                                 "a float-pair residual while the backward error is >= 1e-8), "
                                  "GMRES products with the float-pair copy of A, inner tolerance "
                                  "1e-5, warm start from the previous stage",
                    "rk2_stages_per_step": 2,
@@ -1176,6 +1178,10 @@ def run_nrs(args):
         "refinement": {"outer_mean": H["counts"]["outer"] / max(H["counts"]["solves"], 1),
                        "inner_mean": H["counts"]["inner"] / max(H["counts"]["solves"], 1),
                        "solves": H["counts"]["solves"],
+                       "exact_residuals_mean": H["counts"]["residuals_exact"]
+                       / max(H["counts"]["solves"], 1),
+                       "working_residuals_mean": H["counts"]["residuals_working"]
+                       / max(H["counts"]["solves"], 1),
                        "status_after_timed_region": H["status_after"],
                        "all_converged": True},
         "parity_vs_oracle": H["parity"],

@@ -454,6 +454,32 @@ __device__ void sum_dots(const PgArgs &a, int region, int j, double *h)
     __syncthreads();
 }
 
+// The residual r_e = res(e, b_e) of the CTA's own chunk into a.w and, as
+// float pairs, a.vf (the next preconditioner product's input); the chunk's
+// ||r||_inf (infinite if any r_e is not finite) and ||b||_inf into dp1[0],
+// dp1[1] by its owner.
+template <class Res>
+__device__ __forceinline__ void store_residual(const PgArgs &a, int64_t e0, int64_t e1, bool owner,
+                                               double *dp1, double *sred, Res res)
+{
+    double rmax = 0.0, bmax = 0.0;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
+        const double be = __ldg(a.b + e);
+        const double re = res(e, be);
+        a.w[e] = re;
+        a.vf[e] = df_split(re);
+        rmax = fmax(rmax, fabs(re));
+        bmax = fmax(bmax, fabs(be));
+        if (!isfinite(re)) rmax = INFINITY;
+    }
+    rmax = block_max_all(rmax, sred);
+    bmax = block_max_all(bmax, sred);
+    if (owner && threadIdx.x == 0) {
+        dp1[0] = rmax;
+        dp1[1] = bmax;
+    }
+}
+
 // MINB = 3 caps the kernel at 85 registers a thread so that three CTAs share
 // an SM (large systems, whose products stream from HBM, and the chains of a
 // batch, which run side by side); MINB = 1 leaves the registers free for the
@@ -542,22 +568,8 @@ __global__ void __launch_bounds__(PG_THREADS, MINB) k_gmres_ir(PgArgs a)
                 mv64_partial<false>(a, a.x, 1.0, smv);
             }
             if (!grid_sync(a, &s_ok, tgt)) return;
-            double rmax = 0.0, bmax = 0.0;
-            for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
-                const double be = __ldg(a.b + e);
-                const double re = be - sum_parts(a, a.s64, e);
-                a.w[e] = re;
-                a.vf[e] = df_split(re);
-                rmax = fmax(rmax, fabs(re));
-                bmax = fmax(bmax, fabs(be));
-                if (!isfinite(re)) rmax = INFINITY;
-            }
-            rmax = block_max_all(rmax, sred);
-            bmax = block_max_all(bmax, sred);
-            if (owner && threadIdx.x == 0) {
-                dp1[0] = rmax;
-                dp1[1] = bmax;
-            }
+            store_residual(a, e0, e1, owner, dp1, sred,
+                           [&](int64_t e, double be) { return be - sum_parts(a, a.s64, e); });
             if (!grid_sync(a, &s_ok, tgt)) return;
             const double rn = chunk_total(a, 1, 0, true, sred);
             const double bn = chunk_total(a, 1, 1, true, sred);
@@ -567,41 +579,25 @@ __global__ void __launch_bounds__(PG_THREADS, MINB) k_gmres_ir(PgArgs a)
             ++n_work;
         }
         if (!cheap) {
-        // r = b - A x (exact products and error sums, or FP64), with ||r||_inf
-        // and ||b||_inf per chunk; xn is ||x||_inf of this x
-        const int fxc = a.dd ? fx_anchor(normA, xn) : 0;
-        ++n_exact;
-        if (a.dd)
-            mv64fx_partial(a, a.x, fxc, smv);
-        else
-            mv64_partial<false>(a, a.x, 1.0, smv);
-        if (!grid_sync(a, &s_ok, tgt)) return;
-        {
-            double rmax = 0.0, bmax = 0.0;
-            for (int64_t e = e0 + threadIdx.x; e < e1; e += PG_THREADS) {
-                const double be = __ldg(a.b + e);
-                const double re =
-                    a.dd ? residual_fx_at(a, be, e, fxc) : be - sum_parts(a, a.s64, e);
-                a.w[e] = re;
-                a.vf[e] = df_split(re);
-                rmax = fmax(rmax, fabs(re));
-                bmax = fmax(bmax, fabs(be));
-                if (!isfinite(re)) rmax = INFINITY;
-            }
-            rmax = block_max_all(rmax, sred);
-            bmax = block_max_all(bmax, sred);
-            if (owner && threadIdx.x == 0) {
-                dp1[0] = rmax;
-                dp1[1] = bmax;
+            // r = b - A x (exact products and error sums, or FP64), with
+            // ||r||_inf and ||b||_inf per chunk; xn is ||x||_inf of this x
+            const int fxc = a.dd ? fx_anchor(normA, xn) : 0;
+            ++n_exact;
+            if (a.dd)
+                mv64fx_partial(a, a.x, fxc, smv);
+            else
+                mv64_partial<false>(a, a.x, 1.0, smv);
+            if (!grid_sync(a, &s_ok, tgt)) return;
+            store_residual(a, e0, e1, owner, dp1, sred, [&](int64_t e, double be) {
+                return a.dd ? residual_fx_at(a, be, e, fxc) : be - sum_parts(a, a.s64, e);
+            });
+            if (!grid_sync(a, &s_ok, tgt)) return;
+            if (a.dd) {
+                const double rn = chunk_total(a, 1, 0, true, sred);
+                const double bn = chunk_total(a, 1, 1, true, sred);
+                eta_prev = rn / (normA * xn + bn);
             }
         }
-        if (!grid_sync(a, &s_ok, tgt)) return;
-        if (a.dd) {
-            const double rn = chunk_total(a, 1, 0, true, sred);
-            const double bn = chunk_total(a, 1, 1, true, sred);
-            eta_prev = rn / (normA * xn + bn);
-        }
-        }  // exact (or FP64) residual
         if (stagnant && !cheap) {
             // The corrections stopped shrinking.  If x already solves a nearby
             // system to working precision (normwise backward error
