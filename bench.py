@@ -807,6 +807,43 @@ def dormand_prince_line(nrs, args, name="swimmer", T=0.1, tol=1e-8):
             "rk2_stage_evaluations_per_time_unit_at_dt": 2.0 / pr.dt}
 
 
+def factorisation_line(nrs, args, timer, peaks, sm_mhz):
+    """One factorisation alone on the headline workload (the FP32 copy of the
+    first stage's matrix inverted by the product path's schedule), timed with
+    CUDA events after one untimed one, L2 flushed before each.  Work counted:
+    Gauss-Jordan 2 n^3 flops (an LU would need 2/3 n^3); the tensor cores
+    multiply 3 split products of rank 256 into every column for each of the
+    n / 256 blocks (6 n^3 flops); the updates read and write the FP32 matrix
+    once a block (8 n^2 bytes x n / 256)."""
+    pr = g.workload(HEADLINE)
+    n = pr.n
+    Y0 = g.initial_state(pr)
+    ctx = nrs.Context.from_problem(pr, factor_prec=args.prec)
+    ctx.set_state(Y0["x0"], Y0["B"])
+    xi, Xiw, xidot = nrs.shapes_to_device(g.pack_shapes(pr, 0.0))
+    x, Xw, _ = ctx.kinematics(xi, Xiw, xidot)
+    ctx.nearest_build(xi, Xiw)
+    ctx.assemble(x, Xw, want_matrix=False)
+    if ctx.factor(args.prec) != 0:
+        ctx.close()
+        return {"error": "factorisation failed"}
+    ms = timer.run(ctx.stream, lambda s: ctx.factor(args.prec), 4)
+    ctx.close()
+    t = float(np.mean(ms)) / 1e3
+    P = derived_peaks(peaks, sm_mhz)
+    blocks = -(-n // 256)
+    return {"workload": WORKLOADS_DESC[HEADLINE], "n": n, "ms": t * 1e3, "runs": len(ms),
+            "gauss_jordan_tflops": 2.0 * n ** 3 / t / 1e12,
+            "lu_equivalent_tflops": 2.0 / 3.0 * n ** 3 / t / 1e12,
+            "tensor_tflops": 6.0 * n ** 3 / t / 1e12,
+            "tensor_frac": 6.0 * n ** 3 / t / 1e12 / P["f16_tflops"],
+            "hbm_gbs": 8.0 * n * n * blocks / t / 1e9,
+            "hbm_frac": 8.0 * n * n * blocks / t / 1e9 / P["hbm_gbs"],
+            "note": "FP32 explicit inverse, two-level Gauss-Jordan (rank-256 tcgen05 updates from "
+                    "scaled FP16 pairs); tensor and HBM fractions of the measured sustained "
+                    "BF16/FP16 and copy peaks"}
+
+
 def plain_fp64(nrs, args, timer):
     """The plain FP64 GPU path on the headline workload: the FP64 assembly
     (this library's kernel, the same matrix) and cuSOLVER's getrf + getrs
@@ -1133,6 +1170,9 @@ def run_nrs(args):
         side["dormand_prince"] = dormand_prince_line(nrs, args)
         torch.cuda.empty_cache()
         side["plain_fp64"] = plain_fp64(nrs, args, timer)
+        torch.cuda.empty_cache()
+        side["factorisation"] = factorisation_line(
+            nrs, args, timer, peaks, H["clocks"].get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0))
         torch.cuda.empty_cache()
     batch = None
     if not args.no_batch:
