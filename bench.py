@@ -217,7 +217,7 @@ NCU_TRAFFIC = {
     # iterations; the three-CTAs-per-SM variant on 456 CTAs): 16.101 + 0.056 GB
     # against 7 passes over A (8 n^2) and M (4 n^2) = 16.05 GB
     "k_gmres_ir": {"bytes": None, "ratio": (16100587008 + 56127744) / (12.0 * 13824 ** 2 * 7),
-                   "file": "paper_2001_06468_gb300/csrc/gmres_persistent.cu", "sha1": "b0ab3387af81",
+                   "file": "paper_2001_06468_gb300/csrc/gmres_persistent.cu", "sha1": "0a46b9864734",
                    "scale": "traffic / algorithmic bytes at n = 13824, times the record's bytes"},
 }
 

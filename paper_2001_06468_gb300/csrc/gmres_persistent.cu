@@ -95,8 +95,9 @@ __device__ __forceinline__ int32_t pg_ld_relaxed(const int32_t *p)
 }
 
 // L2 prefetch for the matrix-vector products: the products stream each matrix
-// once, with only 16 warps an SM (the cooperative launch's occupancy), so
-// the loads alone keep too few bytes in flight.  A warp's tile spans 512
+// once, with 8 to 24 warps an SM (the cooperative launch's occupancy), so
+// the loads alone keep too few bytes in flight (3, 10 and 16 columns ahead
+// measured slower than 6).  A warp's tile spans 512
 // bytes of a column (64 rows of 8 bytes, or 128 rows of 4); lanes 0-3 each
 // prefetch one of its four 128-byte lines six of its columns ahead of the
 // warp's current one.  Lines whose first row is at or beyond n are skipped
