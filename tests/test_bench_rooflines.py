@@ -161,3 +161,22 @@ def test_working_precision_residuals_are_counted_as_what_they_are():
     assert k["fp64_gops"] * 1e9 * t == pytest.approx((3 * 2.0 + 1) * N_SYS ** 2)
     f = bench.rooflines(ms, spans, N_SYS, PAIRS, PEAKS, "measured", SM_MHZ, st)["krylov"]
     assert f["fp64_gops"] * 1e9 * t == pytest.approx((3 * 2.0 + 1 + 20.0 + 2.5) * N_SYS ** 2)
+
+
+def test_critical_path_charges_overlap_to_the_work_that_ends_last():
+    # the factorisation (a chain: update 0-20 and panel 18-30, one run) with the
+    # FP64 assembly beside it (5-25 ms, ends first: off the critical path),
+    # then the assembly alone (30-40) and the solve (40-60, 62-70); the gap
+    # (60-62) is charged to nothing
+    tr = [("lu_update", 0.0, 20.0), ("lu_panel", 18.0, 30.0), ("assemble", 5.0, 25.0),
+          ("assemble", 30.0, 40.0), ("krylov", 40.0, 60.0), ("krylov", 62.0, 70.0)]
+    c = bench.critical_ms(tr)
+    assert c["lu"] == pytest.approx(30.0)
+    assert c["assemble"] == pytest.approx(10.0)
+    assert c["krylov"] == pytest.approx(28.0)
+    assert sum(c.values()) == pytest.approx(68.0)
+    # an assembly that outlasts the factorisation is on the path for its tail
+    c2 = bench.critical_ms([("lu_update", 0.0, 10.0), ("lu_panel", 10.1, 20.0),
+                            ("assemble", 5.0, 26.0)])
+    assert c2["lu"] == pytest.approx(5.0)
+    assert c2["assemble"] == pytest.approx(21.0)
